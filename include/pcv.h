@@ -1,0 +1,180 @@
+/*
+ * pcv.h -- C ABI of the GB300 path-CV / MSD library.
+ *
+ * Batched mean-square-distance (MSD) evaluation behind property-map / path collective
+ * variables in metadynamics, with the floating close-structure approximation, after
+ * Pazurikova, Olha, Krenek, Spiwok, "Acceleration of Mean Square Distance Calculations
+ * with Floating Close Structure in Metadynamics Simulations" (arXiv:1801.02362).
+ *
+ * Notation: M landmark (reference) structures a_i, N atoms, F frames x_t per call.
+ * (The paper writes N for the number of reference structures; here that is M.)
+ *
+ * Conventions for every call:
+ *  - Plain pointers and sizes only.  "device" pointers are CUDA device memory of the
+ *    context's device; "host" pointers are ordinary CPU memory.  The caller owns every
+ *    buffer it passes; the library never frees or retains caller pointers after a call
+ *    returns.  Device work is enqueued on the context's stream and is asynchronous
+ *    unless a call says otherwise.
+ *  - Coordinates are row-major (structure, atom, xyz), in nm.
+ *  - Every call returns a pcv_status.  Argument errors are detected on the host before
+ *    any work is enqueued and leave the context unchanged.  pcv_last_error() returns a
+ *    one-line description of the last failure on the context.
+ *  - Precision modes fix the element types:
+ *      PCV_FP64          frames double, landmarks double, all arithmetic FP64,
+ *                        gradients double;
+ *      PCV_FP32          frames float, landmarks float (centred), per-atom sums in
+ *                        compensated FP32, 4x4 eigen-solve and MSD assembly in FP64,
+ *                        gradients float;
+ *      PCV_FP16_STORAGE  as PCV_FP32 but landmarks stored as centred FP16.
+ *  - The library allocates its own device workspace (cudaMalloc, grow-only) on first
+ *    use of a size; it is freed by pcv_destroy.
+ */
+#ifndef PCV_H
+#define PCV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PCV_API_VERSION 1
+
+#if defined(__GNUC__)
+#define PCV_API __attribute__((visibility("default")))
+#else
+#define PCV_API
+#endif
+
+typedef struct pcv_ctx pcv_ctx;
+
+typedef enum {
+  PCV_OK = 0,
+  PCV_EINVAL = -1,  /* invalid argument (sizes, NULL where required, NaN, lambda <= 0) */
+  PCV_ECUDA = -2,   /* a CUDA runtime call failed; see pcv_last_error()                */
+  PCV_ENOMEM = -3,  /* device or host allocation failed                                 */
+  PCV_ENOCONV = -4, /* an eigen-solve hit its iteration cap (reported at pcv_sync)      */
+  PCV_ESTATE = -5   /* call out of order (no landmarks, bad saved state, ...)           */
+} pcv_status;
+
+typedef enum { PCV_FP64 = 0, PCV_FP32 = 1, PCV_FP16_STORAGE = 2 } pcv_precision;
+
+/* Counters of the work done since the last pcv_reset_close_state (or creation).  The
+ * "expensive" distance computations of the paper's cost model (Section "Theoretical
+ * Speedup": M + (N-M)/L per step originally, 1 + N/K with the close structure) are
+ * xy_alignments + landmark_alignments. */
+typedef struct {
+  int64_t frames;              /* frames evaluated                                        */
+  int64_t xy_alignments;       /* exact alignments of a frame onto the close structure y  */
+  int64_t landmark_alignments; /* exact (eigen-solved) frame-landmark MSDs                */
+  int64_t approx_msds;         /* approximate MSDs, Eq. (close_dist)                      */
+  int64_t refreshes_threshold; /* close-structure reassignments with D(x,y) > eps        */
+  int64_t refreshes_initial;   /* initial close-structure assignments                     */
+  int64_t fp64_rechecks;       /* refresh decisions re-evaluated in full FP64             */
+  int64_t host_syncs;          /* host round trips of the refresh search                  */
+} pcv_stats;
+
+/* Create a context on CUDA device `device`, enqueueing on `cuda_stream` (a cudaStream_t;
+ * NULL = legacy default stream), in precision mode `precision` (pcv_precision).
+ * Errors: PCV_EINVAL (bad device / precision), PCV_ECUDA, PCV_ENOMEM. */
+PCV_API pcv_status pcv_create(pcv_ctx** out, int device, void* cuda_stream, int precision);
+
+/* Free every device and host resource of the context.  Synchronises its stream. */
+PCV_API pcv_status pcv_destroy(pcv_ctx* ctx);
+
+/* Replace the stream the context enqueues on (a cudaStream_t). */
+PCV_API pcv_status pcv_set_stream(pcv_ctx* ctx, void* cuda_stream);
+
+/* Set the landmark (reference) structures a_i of Eq. (property_map_cv).
+ *   coords  host, M*N*3 doubles, landmark-major; each landmark is centred here by its
+ *           weighted centre (Section "Floating Close Structure": both structures are
+ *           shifted to the same location before fitting) and stored in the mode's
+ *           storage type;
+ *   w       host, N doubles > 0, or NULL for uniform weights; normalised to sum 1.  One
+ *           weight set serves as displacement weights w and alignment weights w'
+ *           (Eq. der_dist);
+ *   q       host, M doubles, the property q_i of each landmark, or NULL for q_i = i
+ *           (1-based index: the path CV s).
+ * Resets the close-structure state.  Synchronous with respect to the host buffers.
+ * Errors: PCV_EINVAL (M < 1, N < 3, NULL coords, non-finite values, w <= 0). */
+PCV_API pcv_status pcv_set_landmarks(pcv_ctx* ctx, int M, int N, const double* coords, const double* w,
+                             const double* q);
+
+/* Set lambda of Eq. (property_map_cv), in nm^-2.  Errors: PCV_EINVAL unless lambda > 0
+ * and finite. */
+PCV_API pcv_status pcv_set_lambda(pcv_ctx* ctx, double lambda);
+
+/* Set the close-structure threshold eps in nm^2 (Algorithm 2: reassign when
+ * D(x, y) > eps, strictly; the paper uses 0.01).  eps < 0 selects exact mode
+ * (Algorithm 1 for every frame).  Changing eps keeps the current close structure. */
+PCV_API pcv_status pcv_set_close_threshold(pcv_ctx* ctx, double eps);
+
+/* Evaluate F frames (time-ordered consecutive MD steps in close mode).
+ *   frames     device, F*N*3 (double in PCV_FP64, else float), uncentred;
+ *   s, z       device, F doubles each, required: the path CV s of Eq. (property_map_cv)
+ *              and z = -(1/lambda) ln sum_i exp(-lambda D_i) (Branduardi et al. 2007,
+ *              cited in Section 2);
+ *   dsdx,dzdx  device, F*N*3 (double in PCV_FP64, else float), or NULL: ds/dx and dz/dx
+ *              from Eq. (der_dist) (exact and reassignment frames) and
+ *              Eq. (close_der_dist) (approximate frames);
+ *   msd        device, F*M doubles, or NULL: D(x_t, a_i) (Eq. dist) or its close-structure
+ *              approximation (Eq. close_dist);
+ *   refreshed  device, F bytes, or NULL: 0 approximate frame, 1 close structure reassigned
+ *              because D(x, y) > eps, 2 initial assignment (exact mode: all 1).
+ * In close mode the close structure y and the rotations R_{a_i y} carry over between
+ * calls.  The call blocks the host only for the refresh search (a few small device-to-
+ * host reads per reassignment); all other work is asynchronous.
+ * Errors: PCV_EINVAL (F < 0, NULL s/z/frames with F > 0), PCV_ESTATE (no landmarks or
+ * lambda), PCV_ECUDA, PCV_ENOMEM. */
+PCV_API pcv_status pcv_evaluate(pcv_ctx* ctx, int F, const void* frames, double* s, double* z, void* dsdx,
+                        void* dzdx, double* msd, uint8_t* refreshed);
+
+/* As pcv_evaluate, with every buffer in host memory (pageable or pinned).  The frames are
+ * copied to the device, evaluated, and the requested outputs copied back; the call
+ * returns when the outputs are in host memory. */
+PCV_API pcv_status pcv_evaluate_host(pcv_ctx* ctx, int F, const void* frames, double* s, double* z,
+                             void* dsdx, void* dzdx, double* msd, uint8_t* refreshed);
+
+/* Chain rule for a scalar loss L(s, z): out[t] = g_s[t] * dsdx[t] + g_z[t] * dzdx[t] for
+ * every frame t (device buffers; element type of dsdx/dzdx/out as in pcv_evaluate; g_s,
+ * g_z device doubles, either may be NULL for zero). */
+PCV_API pcv_status pcv_combine_grad(pcv_ctx* ctx, int F, const double* g_s, const double* g_z,
+                            const void* dsdx, const void* dzdx, void* out);
+
+/* Forget the close structure: the next frame is an initial assignment. Clears counters. */
+PCV_API pcv_status pcv_reset_close_state(pcv_ctx* ctx);
+
+/* Serialise the close-structure state (y, R_{a_i y}, counters) into host memory.
+ * If buf is NULL, *len receives the size needed.  Errors: PCV_EINVAL if *len is too
+ * small. */
+PCV_API pcv_status pcv_save_state(pcv_ctx* ctx, void* buf, size_t* len);
+
+/* Restore a state written by pcv_save_state for the same landmarks, N, M and precision.
+ * Errors: PCV_ESTATE if the blob does not match. */
+PCV_API pcv_status pcv_load_state(pcv_ctx* ctx, const void* buf, size_t len);
+
+/* Copy the counters.  Synchronises the context's stream. */
+PCV_API pcv_status pcv_get_stats(pcv_ctx* ctx, pcv_stats* out);
+
+/* Wait for the context's work and report deferred device errors (PCV_ENOCONV when an
+ * eigen-solve hit its iteration cap since the last pcv_sync). */
+PCV_API pcv_status pcv_sync(pcv_ctx* ctx);
+
+/* Tuning knobs (pcv_set_option keys). */
+enum {
+  PCV_OPT_BAND = 1,        /* frames compared with each of the previous BAND frames
+                              ahead of the refresh search (1..6, default 2)           */
+  PCV_OPT_CHUNK = 2,       /* minimum frames per speculative x-y alignment chunk       */
+  PCV_OPT_EXACT_TILE = 3,  /* tile variant index of the exact pair kernel              */
+  PCV_OPT_APPROX_TILE = 4  /* tile variant index of the approximate pair kernel        */
+};
+PCV_API pcv_status pcv_set_option(pcv_ctx* ctx, int key, int64_t value);
+
+/* One-line description of the last error on ctx (never NULL). */
+PCV_API const char* pcv_last_error(const pcv_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PCV_H */

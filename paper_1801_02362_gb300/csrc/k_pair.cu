@@ -1,0 +1,477 @@
+// k_pair.cu -- frame x landmark pair kernels (the O(F M N) part of the path).
+//
+// exact_pair_kernel: Algorithm 1 (and the reassignment branch of Algorithm 2) for a tile
+//   of TF frames x TM landmarks.  The 3x3 correlation H_fi[b][c] = sum_j wk_j a_ijb x_fjc
+//   is a dense (3 TM x N)(N x 3 TF) contraction; each thread owns 2 frames x 2 landmarks
+//   (36 sums), atoms are streamed through shared memory in chunks of KC.  FP32 products
+//   are summed per chunk and the chunk sums are added into an error-free (hi, lo) pair,
+//   so the correlation keeps ~FP64 accuracy with FP32 arithmetic.  Each pair then takes
+//   the FP64 quaternion eigen-solve (Section 3, Kearsley / Coutsias) and the FP64
+//   assembly D = G_x + G_a - 2 lambda_max of Eq. (dist).
+// approx_pair_kernel: Eq. (close_dist) for frames of Algorithm 2's "else" branch.  With
+//   x' = R_{xy}^T x and b_i = R_{a_i y} a_i the approximate distance is
+//   D~ = sum_j w_j |x'_j - b_ij|^2, evaluated directly (positive terms, no cancellation);
+//   landmarks are rotated by their stored R_{a_i y} while being staged, frames by the
+//   transpose of their R_{xy}.
+#include <cuda_fp16.h>
+
+#include "pcv_device.cuh"
+#include "pcv_internal.h"
+
+namespace pcv {
+namespace {
+
+template <typename ST, typename LT>
+__device__ __forceinline__ ST load_as(const LT* p) {
+  return (ST)(*p);
+}
+template <>
+__device__ __forceinline__ float load_as<float, __half>(const __half* p) {
+  return __half2float(*p);
+}
+
+// compensated accumulator: FP32 partial + error-free (hi, lo) total; plain in FP64
+template <typename ST>
+struct Acc;
+template <>
+struct Acc<float> {
+  float p, hi, lo;
+  __device__ __forceinline__ void zero() { p = hi = lo = 0.0f; }
+  __device__ __forceinline__ void flush() {
+    two_sum_acc(hi, lo, p);
+    p = 0.0f;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+template <>
+struct Acc<double> {
+  double p;
+  __device__ __forceinline__ void zero() { p = 0.0; }
+  __device__ __forceinline__ void flush() {}
+  __device__ __forceinline__ double value() const { return p; }
+};
+
+template <typename ST>
+__device__ __forceinline__ void load2(const ST* p, ST& a, ST& b);
+template <>
+__device__ __forceinline__ void load2<float>(const float* p, float& a, float& b) {
+  const float2 v = *reinterpret_cast<const float2*>(p);
+  a = v.x;
+  b = v.y;
+}
+template <>
+__device__ __forceinline__ void load2<double>(const double* p, double& a, double& b) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  a = v.x;
+  b = v.y;
+}
+template <typename ST>
+__device__ __forceinline__ void load4(const ST* p, ST* o);
+template <>
+__device__ __forceinline__ void load4<float>(const float* p, float* o) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = v.x;
+  o[1] = v.y;
+  o[2] = v.z;
+  o[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void load4<double>(const double* p, double* o) {
+  const double2 v0 = *reinterpret_cast<const double2*>(p);
+  const double2 v1 = *reinterpret_cast<const double2*>(p + 2);
+  o[0] = v0.x;
+  o[1] = v0.y;
+  o[2] = v1.x;
+  o[3] = v1.y;
+}
+
+template <typename ST>
+__device__ __forceinline__ void frame_centre(const float4* c32, const double4* c64, int f, ST* c);
+template <>
+__device__ __forceinline__ void frame_centre<float>(const float4* c32, const double4*, int f, float* c) {
+  const float4 v = c32[f];
+  c[0] = v.x;
+  c[1] = v.y;
+  c[2] = v.z;
+}
+template <>
+__device__ __forceinline__ void frame_centre<double>(const float4*, const double4* c64, int f, double* c) {
+  const double4 v = c64[f];
+  c[0] = v.x;
+  c[1] = v.y;
+  c[2] = v.z;
+}
+
+// ---------------------------------------------------------------------------------------
+constexpr int EX_TF = 16, EX_TM = 32, EX_THREADS = 128;
+
+template <typename FT, typename LT, typename ST>
+__global__ void __launch_bounds__(EX_THREADS, 3)
+exact_pair_kernel(int rows, const int* __restrict__ row_frame, const int* __restrict__ rows_dev,
+                  const FT* __restrict__ frames, const float4* __restrict__ c32,
+                  const double4* __restrict__ c64, const double* __restrict__ fG,
+                  const LT* __restrict__ lm, const double* __restrict__ lG,
+                  const float* __restrict__ wts, int M, int N, double dscale, ST* __restrict__ Dout,
+                  ST* __restrict__ Rout, unsigned* __restrict__ status) {
+  constexpr int TF = EX_TF, TM = EX_TM;
+  constexpr int KC = sizeof(ST) == 8 ? 16 : 32;
+  constexpr int PF = TF + 2, PM = TM + 2;
+  __shared__ __align__(16) ST Xs[KC * 3][PF];
+  __shared__ __align__(16) ST As[KC * 3][PM];
+  __shared__ int s_frame[TF];
+  __shared__ ST s_c[TF][3];
+
+  if (rows_dev) rows = *rows_dev;
+  const int row0 = blockIdx.y * TF;
+  if (row0 >= rows) return;
+  const int i0 = blockIdx.x * TM;
+  const int tid = threadIdx.x;
+  const int tx = tid & 15;  // landmark pair: i0 + 2 tx + {0,1}
+  const int ty = tid >> 4;  // frame pair: rows 2 ty + {0,1}
+  if (tid < TF) {
+    const int r = row0 + tid;
+    int f = -1;
+    if (r < rows) f = row_frame ? row_frame[r] : r;
+    s_frame[tid] = f;
+    ST c[3] = {0, 0, 0};
+    if (f >= 0) frame_centre<ST>(c32, c64, f, c);
+    s_c[tid][0] = c[0];
+    s_c[tid][1] = c[1];
+    s_c[tid][2] = c[2];
+  }
+  __syncthreads();
+
+  Acc<ST> acc[2][2][9];
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v)
+#pragma unroll
+      for (int e = 0; e < 9; ++e) acc[u][v][e].zero();
+
+  for (int j0 = 0; j0 < N; j0 += KC) {
+    // frames: one atom (3 coordinates) per work item, centred (and weighted)
+    for (int e = tid; e < TF * KC; e += EX_THREADS) {
+      const int ff = e / KC, jj = e - ff * KC;
+      const int j = j0 + jj;
+      const int f = s_frame[ff];
+      ST v0 = 0, v1 = 0, v2 = 0;
+      if (f >= 0 && j < N) {
+        const FT* src = frames + ((size_t)f * N + j) * 3;
+        v0 = (ST)src[0] - s_c[ff][0];
+        v1 = (ST)src[1] - s_c[ff][1];
+        v2 = (ST)src[2] - s_c[ff][2];
+        if (wts) {
+          const ST wj = (ST)wts[j];
+          v0 *= wj;
+          v1 *= wj;
+          v2 *= wj;
+        }
+      }
+      Xs[jj * 3 + 0][ff] = v0;
+      Xs[jj * 3 + 1][ff] = v1;
+      Xs[jj * 3 + 2][ff] = v2;
+    }
+    for (int e = tid; e < TM * KC; e += EX_THREADS) {
+      const int ll = e / KC, jj = e - ll * KC;
+      const int j = j0 + jj, i = i0 + ll;
+      ST v0 = 0, v1 = 0, v2 = 0;
+      if (i < M && j < N) {
+        const LT* src = lm + ((size_t)i * N + j) * 3;
+        v0 = load_as<ST>(src);
+        v1 = load_as<ST>(src + 1);
+        v2 = load_as<ST>(src + 2);
+      }
+      As[jj * 3 + 0][ll] = v0;
+      As[jj * 3 + 1][ll] = v1;
+      As[jj * 3 + 2][ll] = v2;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int jj = 0; jj < KC; ++jj) {
+      ST x[2][3], a[2][3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        load2<ST>(&Xs[jj * 3 + c][ty * 2], x[0][c], x[1][c]);
+        load2<ST>(&As[jj * 3 + c][tx * 2], a[0][c], a[1][c]);
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v)
+#pragma unroll
+          for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[u][v][3 * b + c].p = fma(a[v][b], x[u][c], acc[u][v][3 * b + c].p);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int v = 0; v < 2; ++v)
+#pragma unroll
+        for (int e = 0; e < 9; ++e) acc[u][v][e].flush();
+    __syncthreads();
+  }
+
+  // epilogue: FP64 eigen-solve and assembly per pair
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int r = row0 + ty * 2 + u;
+      const int f = (ty * 2 + u) < TF ? s_frame[ty * 2 + u] : -1;
+      const int i = i0 + tx * 2 + v;
+      if (f < 0 || i >= M) continue;
+      double H[9];
+#pragma unroll
+      for (int e = 0; e < 9; ++e) H[e] = acc[u][v][e].value();
+      const double Gx = fG[f], Ga = lG[i];
+      bool ok = true;
+      const double lam = lambda_max_newton(H, 0.5 * (Gx + Ga), &ok);
+      double D = (Gx + Ga - 2.0 * lam) * dscale;
+      if (D < 0.0) D = 0.0;
+      Dout[(size_t)f * M + i] = (ST)D;
+      if (Rout) {
+        double K[16];
+        quat_matrix(H, K);
+        ST* dst = Rout + ((size_t)r * M + i) * 9;
+        if (sizeof(ST) == 8) {
+          double q[4], R[9];
+          adj_eigvec_f64(K, lam, q);
+          quat_to_rot(q, R);
+#pragma unroll
+          for (int e = 0; e < 9; ++e) dst[e] = (ST)R[e];
+        } else {
+          float q[4], R[9];
+          adj_eigvec(K, lam, q);
+          quat_to_rot(q, R);
+#pragma unroll
+          for (int e = 0; e < 9; ++e) dst[e] = (ST)R[e];
+        }
+      }
+      if (!ok) atomicOr(status, STATUS_NOCONV);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+constexpr int AP_TF = 64, AP_TM = 32, AP_THREADS = 128;
+
+template <typename FT, typename LT, typename ST>
+__global__ void __launch_bounds__(AP_THREADS)
+approx_pair_kernel(const int* __restrict__ alist, const int* __restrict__ aseg,
+                   const int* __restrict__ acount, const FT* __restrict__ frames,
+                   const float4* __restrict__ c32, const double4* __restrict__ c64,
+                   const double4* __restrict__ qxy, const LT* __restrict__ lm,
+                   const ST* __restrict__ Bseg, const float* __restrict__ wts, int M, int N,
+                   double dscale, ST* __restrict__ Dout) {
+  constexpr int TF = AP_TF, TM = AP_TM;
+  constexpr int KC = sizeof(ST) == 8 ? 16 : 32;
+  constexpr int PF = TF + 4, PM = TM + 4;
+  __shared__ __align__(16) ST Xs[KC * 3][PF];
+  __shared__ __align__(16) ST Bs[KC * 3][PM];
+  __shared__ ST s_R[TF][9];
+  __shared__ ST s_B[TM][9];
+  __shared__ ST s_c[TF][3];
+  __shared__ ST s_sw[KC];
+  __shared__ int s_frame[TF], s_seg[TF];
+
+  const int count = *acount;
+  const int row0 = blockIdx.y * TF;
+  if (row0 >= count) return;
+  const int i0 = blockIdx.x * TM;
+  const int tid = threadIdx.x;
+  const int tx = tid & 7;   // landmarks i0 + 4 tx + {0..3}
+  const int ty = tid >> 3;  // rows 4 ty + {0..3}
+
+  if (tid < TF) {
+    const int r = row0 + tid;
+    int f = -1, sg = -1;
+    if (r < count) {
+      f = alist[r];
+      sg = aseg[r];
+    }
+    s_frame[tid] = f;
+    s_seg[tid] = sg;
+    ST c[3] = {0, 0, 0};
+    ST R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    if (f >= 0) {
+      frame_centre<ST>(c32, c64, f, c);
+      const double4 qq = qxy[f];
+      const double qd[4] = {qq.x, qq.y, qq.z, qq.w};
+      if (sizeof(ST) == 8) {
+        double Rd[9];
+        quat_to_rot(qd, Rd);
+#pragma unroll
+        for (int e = 0; e < 9; ++e) R[e] = (ST)Rd[e];
+      } else {
+        const float qf[4] = {(float)qd[0], (float)qd[1], (float)qd[2], (float)qd[3]};
+        float Rf[9];
+        quat_to_rot(qf, Rf);
+#pragma unroll
+        for (int e = 0; e < 9; ++e) R[e] = (ST)Rf[e];
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 9; ++e) s_R[tid][e] = R[e];
+    s_c[tid][0] = c[0];
+    s_c[tid][1] = c[1];
+    s_c[tid][2] = c[2];
+  }
+  __syncthreads();
+
+  int k = 0;
+  while (k < TF && s_frame[k] >= 0) {
+    const int seg = s_seg[k];
+    int kend = k;
+    while (kend < TF && s_frame[kend] >= 0 && s_seg[kend] == seg) ++kend;
+    for (int e = tid; e < TM * 9; e += AP_THREADS) {
+      const int ll = e / 9, c = e - ll * 9;
+      const int i = i0 + ll;
+      s_B[ll][c] = (i < M) ? Bseg[((size_t)seg * M + i) * 9 + c] : (ST)0;
+    }
+    ST acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = 0;
+    __syncthreads();
+
+    for (int j0 = 0; j0 < N; j0 += KC) {
+      if (tid < KC) {
+        const int j = j0 + tid;
+        ST sw = 1;
+        if (wts) sw = (j < N) ? (ST)sqrt((double)wts[j]) : (ST)0;
+        s_sw[tid] = sw;
+      }
+      __syncthreads();
+      // frames: x' = R_xy^T (x - c), rows outside [k, kend) staged as zero
+      for (int e = tid; e < TF * KC; e += AP_THREADS) {
+        const int ff = e / KC, jj = e - ff * KC;
+        const int j = j0 + jj;
+        ST o0 = 0, o1 = 0, o2 = 0;
+        if (ff >= k && ff < kend && j < N) {
+          const FT* src = frames + ((size_t)s_frame[ff] * N + j) * 3;
+          const ST v0 = (ST)src[0] - s_c[ff][0];
+          const ST v1 = (ST)src[1] - s_c[ff][1];
+          const ST v2 = (ST)src[2] - s_c[ff][2];
+          const ST* R = s_R[ff];
+          const ST sw = s_sw[jj];
+          o0 = (R[0] * v0 + R[3] * v1 + R[6] * v2) * sw;
+          o1 = (R[1] * v0 + R[4] * v1 + R[7] * v2) * sw;
+          o2 = (R[2] * v0 + R[5] * v1 + R[8] * v2) * sw;
+        }
+        Xs[jj * 3 + 0][ff] = o0;
+        Xs[jj * 3 + 1][ff] = o1;
+        Xs[jj * 3 + 2][ff] = o2;
+      }
+      // landmarks: b = R_{a_i y} a
+      for (int e = tid; e < TM * KC; e += AP_THREADS) {
+        const int ll = e / KC, jj = e - ll * KC;
+        const int j = j0 + jj, i = i0 + ll;
+        ST o0 = 0, o1 = 0, o2 = 0;
+        if (i < M && j < N) {
+          const LT* src = lm + ((size_t)i * N + j) * 3;
+          const ST a0 = load_as<ST>(src), a1 = load_as<ST>(src + 1), a2 = load_as<ST>(src + 2);
+          const ST* B = s_B[ll];
+          const ST sw = s_sw[jj];
+          o0 = (B[0] * a0 + B[1] * a1 + B[2] * a2) * sw;
+          o1 = (B[3] * a0 + B[4] * a1 + B[5] * a2) * sw;
+          o2 = (B[6] * a0 + B[7] * a1 + B[8] * a2) * sw;
+        }
+        Bs[jj * 3 + 0][ll] = o0;
+        Bs[jj * 3 + 1][ll] = o1;
+        Bs[jj * 3 + 2][ll] = o2;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int jj = 0; jj < KC; ++jj) {
+        ST x[3][4], b[3][4];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          load4<ST>(&Xs[jj * 3 + c][ty * 4], x[c]);
+          load4<ST>(&Bs[jj * 3 + c][tx * 4], b[c]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const ST d0 = x[0][u] - b[0][v];
+            const ST d1 = x[1][u] - b[1][v];
+            const ST d2 = x[2][u] - b[2][v];
+            ST t = acc[u][v];
+            t = fma(d0, d0, t);
+            t = fma(d1, d1, t);
+            t = fma(d2, d2, t);
+            acc[u][v] = t;
+          }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int ff = ty * 4 + u;
+      if (ff < k || ff >= kend) continue;
+      const int f = s_frame[ff];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int i = i0 + tx * 4 + v;
+        if (i < M) Dout[(size_t)f * M + i] = (ST)((double)acc[u][v] * dscale);
+      }
+    }
+    k = kend;
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+void launch_exact_pairs(Prec p, int rows, const int* row_frame, const int* rows_dev, const void* frames,
+                        const LandmarkDev& L, FrameInfo fi, void* D, void* Rout, unsigned* status,
+                        cudaStream_t st) {
+  if (rows <= 0) return;
+  dim3 grid((L.M + EX_TM - 1) / EX_TM, (rows + EX_TF - 1) / EX_TF);
+  switch (p) {
+    case P_F64:
+      exact_pair_kernel<double, double, double><<<grid, EX_THREADS, 0, st>>>(
+          rows, row_frame, rows_dev, (const double*)frames, fi.c32, fi.c64, fi.G, (const double*)L.coords,
+          L.G, L.w, L.M, L.N, L.dscale, (double*)D, (double*)Rout, status);
+      break;
+    case P_F32:
+      exact_pair_kernel<float, float, float><<<grid, EX_THREADS, 0, st>>>(
+          rows, row_frame, rows_dev, (const float*)frames, fi.c32, fi.c64, fi.G, (const float*)L.coords, L.G,
+          L.w, L.M, L.N, L.dscale, (float*)D, (float*)Rout, status);
+      break;
+    case P_F16:
+      exact_pair_kernel<float, __half, float><<<grid, EX_THREADS, 0, st>>>(
+          rows, row_frame, rows_dev, (const float*)frames, fi.c32, fi.c64, fi.G, (const __half*)L.coords, L.G,
+          L.w, L.M, L.N, L.dscale, (float*)D, (float*)Rout, status);
+      break;
+  }
+}
+
+void launch_approx_pairs(Prec p, int max_rows, const int* approx_list, const int* approx_seg,
+                           const int* count, const void* frames, const LandmarkDev& L, FrameInfo fi,
+                           const double4* qxy, const void* Bseg, void* D, cudaStream_t st) {
+  if (max_rows <= 0) return;
+  dim3 grid((L.M + AP_TM - 1) / AP_TM, (max_rows + AP_TF - 1) / AP_TF);
+  switch (p) {
+    case P_F64:
+      approx_pair_kernel<double, double, double><<<grid, AP_THREADS, 0, st>>>(
+          approx_list, approx_seg, count, (const double*)frames, fi.c32, fi.c64, qxy,
+          (const double*)L.coords, (const double*)Bseg, L.w, L.M, L.N, L.dscale, (double*)D);
+      break;
+    case P_F32:
+      approx_pair_kernel<float, float, float><<<grid, AP_THREADS, 0, st>>>(
+          approx_list, approx_seg, count, (const float*)frames, fi.c32, fi.c64, qxy, (const float*)L.coords,
+          (const float*)Bseg, L.w, L.M, L.N, L.dscale, (float*)D);
+      break;
+    case P_F16:
+      approx_pair_kernel<float, __half, float><<<grid, AP_THREADS, 0, st>>>(
+          approx_list, approx_seg, count, (const float*)frames, fi.c32, fi.c64, qxy, (const __half*)L.coords,
+          (const float*)Bseg, L.w, L.M, L.N, L.dscale, (float*)D);
+      break;
+  }
+}
+
+}  // namespace pcv

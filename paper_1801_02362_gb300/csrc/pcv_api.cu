@@ -1,0 +1,743 @@
+// pcv_api.cu -- the C ABI (include/pcv.h): context, landmark preparation, the
+// close-structure orchestration of Algorithm 2 over a batch of frames, and state I/O.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pcv.h"
+#include "pcv_internal.h"
+
+using namespace pcv;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// small device struct read back by the host during the refresh search
+struct Small {
+  ScanResult scan;
+  int first;
+  int refresh_count;
+  int approx_count;
+  int recheck_count;
+  int last_refresh;
+  int pad;
+  float4 last_c32;
+  double4 last_c64;
+  double last_G;
+};
+
+__global__ void small_tail_kernel(Small* sm, const int* refresh_list, const float4* c32, const double4* c64,
+                                  const double* G) {
+  const int n = sm->refresh_count;
+  if (n > 0) {
+    const int r = refresh_list[n - 1];
+    sm->last_refresh = r;
+    sm->last_c32 = c32[r];
+    sm->last_c64 = c64[r];
+    sm->last_G = G[r];
+  } else {
+    sm->last_refresh = -1;
+  }
+}
+
+}  // namespace
+
+struct pcv_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  Prec prec = P_F32;
+  // landmarks
+  int M = 0, N = 0;
+  bool have_lm = false;
+  bool uniform = true;
+  double dscale = 1.0;
+  DevBuf lm, lmG, lmA, lmq, w32, w64;
+  double lambda = 0.0;
+  bool have_lambda = false;
+  double eps = -1.0;
+  int band_W = 2;
+  int min_chunk = 4096;
+  double gap_estimate = 0.0;
+  // close state
+  bool has_y = false;
+  DevBuf y, Bprior;
+  float4 y_c32 = {0, 0, 0, 0};
+  double4 y_c64 = {0, 0, 0, 0};
+  double y_G = 0.0;
+  // workspace
+  DevBuf c32, c64, fG, bandD, bandQ, bandF, chD, chQ, chF, rlist, rcount, recF, recRef, recD, recQ, reflist,
+      segof, alist, aseg, Dbuf, Rpair, Bseg, mstat, status, nrecheck, small;
+  DevBuf h_frames, h_s, h_z, h_gs, h_gz, h_msd, h_ref;  // device staging for pcv_evaluate_host
+  Small* small_host = nullptr;
+  pcv_stats stats{};
+  std::string err;
+};
+
+namespace {
+
+std::string g_err = "no error";
+
+pcv_status fail(pcv_ctx* c, pcv_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c)
+    c->err = buf;
+  else
+    g_err = buf;
+  return st;
+}
+
+#define CUDA_TRY(c, expr)                                                                    \
+  do {                                                                                       \
+    cudaError_t e_ = (expr);                                                                 \
+    if (e_ != cudaSuccess) return fail((c), PCV_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+pcv_status ensure(pcv_ctx* c, DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return PCV_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    cudaGetLastError();
+    return fail(c, PCV_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  b.bytes = bytes;
+  return PCV_OK;
+}
+
+void release(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+size_t frame_elem(Prec p) { return p == P_F64 ? sizeof(double) : sizeof(float); }
+size_t store_elem(Prec p) { return p == P_F64 ? sizeof(double) : (p == P_F16 ? sizeof(__half) : sizeof(float)); }
+size_t work_elem(Prec p) { return p == P_F64 ? sizeof(double) : sizeof(float); }
+
+LandmarkDev lm_view(const pcv_ctx* c) {
+  LandmarkDev L;
+  L.M = c->M;
+  L.N = c->N;
+  L.coords = c->lm.p;
+  L.G = (const double*)c->lmG.p;
+  L.A = (const double*)c->lmA.p;
+  L.q = (const double*)c->lmq.p;
+  L.w = c->uniform ? nullptr : (const float*)c->w32.p;
+  L.w64 = c->uniform ? nullptr : (const double*)c->w64.p;
+  L.dscale = c->dscale;
+  return L;
+}
+
+RefDesc prior_view(const pcv_ctx* c) {
+  RefDesc r;
+  r.coords = c->y.p;
+  r.c32 = c->y_c32;
+  r.c64 = c->y_c64;
+  r.G = c->y_G;
+  return r;
+}
+
+pcv_status sync_small(pcv_ctx* c) {
+  CUDA_TRY(c, cudaMemcpyAsync(c->small_host, c->small.p, sizeof(Small), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->stats.host_syncs += 1;
+  return PCV_OK;
+}
+
+}  // namespace
+
+// =======================================================================================
+extern "C" {
+
+pcv_status pcv_create(pcv_ctx** out, int device, void* cuda_stream, int precision) {
+  if (!out) return fail(nullptr, PCV_EINVAL, "pcv_create: out is NULL");
+  *out = nullptr;
+  if (precision < PCV_FP64 || precision > PCV_FP16_STORAGE)
+    return fail(nullptr, PCV_EINVAL, "pcv_create: bad precision %d", precision);
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return fail(nullptr, PCV_ECUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));
+  if (device < 0 || device >= ndev) return fail(nullptr, PCV_EINVAL, "pcv_create: bad device %d", device);
+  e = cudaSetDevice(device);
+  if (e != cudaSuccess) return fail(nullptr, PCV_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  pcv_ctx* c = new pcv_ctx();
+  c->device = device;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->prec = (Prec)precision;
+  pcv_status st = ensure(c, c->small, sizeof(Small));
+  if (st == PCV_OK) st = ensure(c, c->status, 16);
+  if (st == PCV_OK) st = ensure(c, c->nrecheck, 16);
+  if (st == PCV_OK && cudaMallocHost((void**)&c->small_host, sizeof(Small)) != cudaSuccess)
+    st = fail(nullptr, PCV_ENOMEM, "cudaMallocHost failed");
+  if (st == PCV_OK && (cudaMemset(c->status.p, 0, 16) != cudaSuccess || cudaMemset(c->nrecheck.p, 0, 16) != cudaSuccess))
+    st = fail(nullptr, PCV_ECUDA, "cudaMemset failed");
+  if (st != PCV_OK) {
+    g_err = c->err.empty() ? g_err : c->err;
+    pcv_destroy(c);
+    return st;
+  }
+  c->err = "no error";
+  *out = c;
+  return PCV_OK;
+}
+
+pcv_status pcv_destroy(pcv_ctx* c) {
+  if (!c) return PCV_OK;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  DevBuf* bufs[] = {&c->lm, &c->lmG, &c->lmA, &c->lmq, &c->w32, &c->w64, &c->y, &c->Bprior, &c->c32, &c->c64,
+                    &c->fG, &c->bandD, &c->bandQ, &c->bandF, &c->chD, &c->chQ, &c->chF, &c->rlist, &c->rcount,
+                    &c->recF, &c->recRef, &c->recD, &c->recQ, &c->reflist, &c->segof, &c->alist, &c->aseg,
+                    &c->Dbuf, &c->Rpair, &c->Bseg, &c->mstat, &c->status, &c->nrecheck, &c->small, &c->h_frames,
+                    &c->h_s, &c->h_z, &c->h_gs, &c->h_gz, &c->h_msd, &c->h_ref};
+  for (DevBuf* b : bufs) release(*b);
+  if (c->small_host) cudaFreeHost(c->small_host);
+  delete c;
+  return PCV_OK;
+}
+
+pcv_status pcv_set_stream(pcv_ctx* c, void* cuda_stream) {
+  if (!c) return fail(nullptr, PCV_EINVAL, "NULL context");
+  c->stream = (cudaStream_t)cuda_stream;
+  return PCV_OK;
+}
+
+const char* pcv_last_error(const pcv_ctx* c) { return c ? c->err.c_str() : g_err.c_str(); }
+
+pcv_status pcv_set_lambda(pcv_ctx* c, double lambda) {
+  if (!c) return fail(nullptr, PCV_EINVAL, "NULL context");
+  if (!(lambda > 0.0) || !std::isfinite(lambda)) return fail(c, PCV_EINVAL, "lambda must be > 0 and finite");
+  c->lambda = lambda;
+  c->have_lambda = true;
+  return PCV_OK;
+}
+
+pcv_status pcv_set_close_threshold(pcv_ctx* c, double eps) {
+  if (!c) return fail(nullptr, PCV_EINVAL, "NULL context");
+  if (std::isnan(eps)) return fail(c, PCV_EINVAL, "eps is NaN");
+  c->eps = eps;
+  return PCV_OK;
+}
+
+pcv_status pcv_set_option(pcv_ctx* c, int key, int64_t value) {
+  if (!c) return fail(nullptr, PCV_EINVAL, "NULL context");
+  switch (key) {
+    case PCV_OPT_BAND:
+      if (value < 1 || value > 6) return fail(c, PCV_EINVAL, "band must be in 1..6");
+      c->band_W = (int)value;
+      return PCV_OK;
+    case PCV_OPT_CHUNK:
+      if (value < 1 || value > (1 << 30)) return fail(c, PCV_EINVAL, "chunk must be in 1..2^30");
+      c->min_chunk = (int)value;
+      return PCV_OK;
+    case PCV_OPT_EXACT_TILE:
+    case PCV_OPT_APPROX_TILE:
+      if (value != 0) return fail(c, PCV_EINVAL, "only tile variant 0 is built");
+      return PCV_OK;
+    default:
+      return fail(c, PCV_EINVAL, "unknown option %d", key);
+  }
+}
+
+pcv_status pcv_reset_close_state(pcv_ctx* c) {
+  if (!c) return fail(nullptr, PCV_EINVAL, "NULL context");
+  c->has_y = false;
+  c->gap_estimate = 0.0;
+  c->stats = pcv_stats{};
+  cudaSetDevice(c->device);
+  CUDA_TRY(c, cudaMemsetAsync(c->nrecheck.p, 0, 16, c->stream));
+  return PCV_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Landmark preparation (row "a1"): FP64 centring by the weighted centre, rounding to the
+// storage type, then G_a, A_i = sum_j w_j a_j a_j^T from the stored (rounded) values.
+pcv_status pcv_set_landmarks(pcv_ctx* c, int M, int N, const double* coords, const double* w, const double* q) {
+  if (!c) return fail(nullptr, PCV_EINVAL, "NULL context");
+  if (M < 1 || N < 3) return fail(c, PCV_EINVAL, "need M >= 1 and N >= 3 (got M=%d N=%d)", M, N);
+  if (!coords) return fail(c, PCV_EINVAL, "coords is NULL");
+  if ((size_t)M * N > ((size_t)1 << 31) / 3) return fail(c, PCV_EINVAL, "M*N*3 exceeds 2^31");
+  std::vector<double> wn(N, 1.0 / N);
+  bool uniform = true;
+  if (w) {
+    double sum = 0.0;
+    for (int j = 0; j < N; ++j) {
+      if (!(w[j] > 0.0) || !std::isfinite(w[j])) return fail(c, PCV_EINVAL, "weight %d not > 0", j);
+      sum += w[j];
+    }
+    for (int j = 0; j < N; ++j) wn[j] = w[j] / sum;
+    uniform = false;
+  }
+  const size_t n3 = (size_t)N * 3;
+  for (size_t k = 0; k < (size_t)M * n3; ++k)
+    if (!std::isfinite(coords[k])) return fail(c, PCV_EINVAL, "non-finite landmark coordinate at %zu", k);
+  std::vector<double> qv(M);
+  for (int i = 0; i < M; ++i) {
+    qv[i] = q ? q[i] : (double)(i + 1);
+    if (!std::isfinite(qv[i])) return fail(c, PCV_EINVAL, "non-finite property q[%d]", i);
+  }
+  const Prec p = c->prec;
+  std::vector<double> G(M), A((size_t)M * 6);
+  std::vector<unsigned char> store((size_t)M * n3 * store_elem(p));
+  std::vector<float> w32(N);
+  for (int j = 0; j < N; ++j) w32[j] = (float)wn[j];
+  for (int i = 0; i < M; ++i) {
+    const double* a = coords + (size_t)i * n3;
+    double cen[3] = {0, 0, 0};
+    for (int j = 0; j < N; ++j)
+      for (int k = 0; k < 3; ++k) cen[k] += wn[j] * a[3 * j + k];
+    double g = 0.0, Ai[6] = {0, 0, 0, 0, 0, 0};
+    for (int j = 0; j < N; ++j) {
+      double v[3];
+      for (int k = 0; k < 3; ++k) {
+        const double cv = a[3 * j + k] - cen[k];
+        const size_t idx = (size_t)i * n3 + 3 * j + k;
+        if (p == P_F64) {
+          ((double*)store.data())[idx] = cv;
+          v[k] = cv;
+        } else if (p == P_F32) {
+          const float f = (float)cv;
+          ((float*)store.data())[idx] = f;
+          v[k] = f;
+        } else {
+          const __half h = __float2half_rn((float)cv);
+          ((__half*)store.data())[idx] = h;
+          v[k] = (double)__half2float(h);
+        }
+      }
+      const double wk = uniform ? 1.0 : (p == P_F64 ? wn[j] : (double)w32[j]);
+      g += wk * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+      Ai[0] += wn[j] * v[0] * v[0];
+      Ai[1] += wn[j] * v[0] * v[1];
+      Ai[2] += wn[j] * v[0] * v[2];
+      Ai[3] += wn[j] * v[1] * v[1];
+      Ai[4] += wn[j] * v[1] * v[2];
+      Ai[5] += wn[j] * v[2] * v[2];
+    }
+    G[i] = g;
+    for (int e = 0; e < 6; ++e) A[(size_t)i * 6 + e] = Ai[e];
+  }
+  cudaSetDevice(c->device);
+  pcv_status st;
+  if ((st = ensure(c, c->lm, store.size())) != PCV_OK) return st;
+  if ((st = ensure(c, c->lmG, sizeof(double) * M)) != PCV_OK) return st;
+  if ((st = ensure(c, c->lmA, sizeof(double) * 6 * M)) != PCV_OK) return st;
+  if ((st = ensure(c, c->lmq, sizeof(double) * M)) != PCV_OK) return st;
+  if ((st = ensure(c, c->w32, sizeof(float) * N)) != PCV_OK) return st;
+  if ((st = ensure(c, c->w64, sizeof(double) * N)) != PCV_OK) return st;
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  CUDA_TRY(c, cudaMemcpy(c->lm.p, store.data(), store.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(c->lmG.p, G.data(), sizeof(double) * M, cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(c->lmA.p, A.data(), sizeof(double) * 6 * M, cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(c->lmq.p, qv.data(), sizeof(double) * M, cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(c->w32.p, w32.data(), sizeof(float) * N, cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(c->w64.p, wn.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+  c->M = M;
+  c->N = N;
+  c->uniform = uniform;
+  c->dscale = uniform ? 1.0 / N : 1.0;
+  c->have_lm = true;
+  return pcv_reset_close_state(c);
+}
+
+// ---------------------------------------------------------------------------------------
+namespace {
+
+pcv_status ensure_frame_workspace(pcv_ctx* c, int F, bool close, bool grads) {
+  const size_t M = c->M, W = c->band_W;
+  pcv_status st;
+#define ENS(buf, bytes) \
+  if ((st = ensure(c, c->buf, (bytes))) != PCV_OK) return st
+  ENS(c32, sizeof(float4) * F);
+  ENS(c64, sizeof(double4) * F);
+  ENS(fG, sizeof(double) * F);
+  ENS(Dbuf, work_elem(c->prec) * (size_t)F * M);
+  ENS(mstat, sizeof(double) * 2 * F);
+  if (close) {
+    ENS(bandD, sizeof(double) * F * W);
+    ENS(bandQ, sizeof(double4) * F * W);
+    ENS(bandF, F * W);
+    ENS(chD, sizeof(double) * F);
+    ENS(chQ, sizeof(double4) * F);
+    ENS(chF, F);
+    ENS(rlist, sizeof(int) * (F * (W + 1) + 1));
+    ENS(recF, F);
+    ENS(recRef, sizeof(int) * F);
+    ENS(recD, sizeof(double) * F);
+    ENS(recQ, sizeof(double4) * F);
+    ENS(reflist, sizeof(int) * F);
+    ENS(segof, sizeof(int) * F);
+    ENS(alist, sizeof(int) * F);
+    ENS(aseg, sizeof(int) * F);
+    ENS(rcount, 64);
+  } else if (grads) {
+    ENS(Rpair, work_elem(c->prec) * 9 * (size_t)F * M);
+  }
+#undef ENS
+  return PCV_OK;
+}
+
+FrameInfo frame_info(pcv_ctx* c) {
+  FrameInfo fi;
+  fi.c32 = (float4*)c->c32.p;
+  fi.c64 = (double4*)c->c64.p;
+  fi.G = (double*)c->fG.p;
+  return fi;
+}
+
+FrameRec frame_rec(pcv_ctx* c) {
+  FrameRec r;
+  r.flag = (uint8_t*)c->recF.p;
+  r.ref = (int*)c->recRef.p;
+  r.dxy = (double*)c->recD.p;
+  r.qxy = (double4*)c->recQ.p;
+  return r;
+}
+
+// Algorithm 2 over F frames: decide every frame (reassignment / approximate and its close
+// structure), then evaluate reassignment frames exactly and the rest approximately.
+pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, double* z, void* gs, void* gz,
+                          double* msd, uint8_t* refreshed) {
+  const cudaStream_t st = c->stream;
+  const LandmarkDev L = lm_view(c);
+  const FrameInfo fi = frame_info(c);
+  const FrameRec rec = frame_rec(c);
+  const RefDesc prior = prior_view(c);
+  const int W = c->band_W;
+  const int M = c->M;
+  Small* sm = (Small*)c->small.p;
+  AlignOut band{(double*)c->bandD.p, (double4*)c->bandQ.p, (uint8_t*)c->bandF.p};
+  AlignOut chunk{(double*)c->chD.p, (double4*)c->chQ.p, (uint8_t*)c->chF.p};
+  int* rl = (int*)c->rlist.p;  // recheck list
+  int* rc = &sm->recheck_count;
+  const bool had_prior = c->has_y;
+
+  launch_frame_prep(c->prec, F, frames, L, fi, st);
+  launch_set_int(rc, 0, st);
+  if (F > 1) {
+    launch_align_band(c->prec, F, W, frames, L, fi, c->eps, band, rl, rc, st);
+    launch_recheck(c->prec, (F - 1) * W, rl, rc, W, frames, L, prior, -1, c->eps, band, chunk,
+                   (unsigned long long*)c->nrecheck.p, st);
+  }
+  // host-driven refresh search
+  int t = 0, ref = -1, o = 0;
+  bool band_mode = false;
+  if (!had_prior) {
+    launch_initial_record(rec, st);
+    t = 1;
+    ref = 0;
+    o = 0;
+    band_mode = true;
+  }
+  long long guard = 0;
+  while (t < F) {
+    if (++guard > 4LL * F + 16) return fail(c, PCV_ESTATE, "refresh search did not terminate");
+    if (band_mode) {
+      launch_band_scan(F, W, t, o, band, rec, &sm->scan, st);
+      pcv_status ps = sync_small(c);
+      if (ps != PCV_OK) return ps;
+      const int ts = c->small_host->scan.t_stop;
+      if (ts >= F) break;
+      if (ts < t) return fail(c, PCV_ESTATE, "band scan went backwards");
+      t = ts;
+      ref = c->small_host->scan.ref;
+      band_mode = false;
+      continue;
+    }
+    // speculative chunk of frames aligned onto the close structure `ref`
+    int B = c->min_chunk;
+    if (c->gap_estimate > 0.0) B = (int)std::fmin(std::fmax((double)B, 2.0 * c->gap_estimate), 1e9);
+    const int t1 = (int)std::min<long long>((long long)F, (long long)t + B);
+    launch_set_int(rc, 0, st);
+    launch_align_chunk(c->prec, t, t1, frames, L, fi, ref, prior, c->eps, chunk, rl, rc, st);
+    launch_recheck(c->prec, t1 - t, rl, rc, W, frames, L, prior, ref, c->eps, band, chunk,
+                   (unsigned long long*)c->nrecheck.p, st);
+    launch_first_exceed(t, t1, chunk.flag, &sm->first, st);
+    pcv_status ps = sync_small(c);
+    if (ps != PCV_OK) return ps;
+    const int first = c->small_host->first;
+    launch_chunk_records(t, first, t1, ref, chunk, rec, st);
+    if (first < t1) {
+      const double gap = (double)(first - (ref >= 0 ? ref : first - 1));
+      c->gap_estimate = c->gap_estimate > 0.0 ? 0.5 * (c->gap_estimate + gap) : gap;
+      t = first + 1;
+      ref = first;
+      o = 0;
+      band_mode = (W >= 1 && F > 1);
+    } else {
+      t = t1;
+    }
+  }
+  // compaction and per-segment work
+  launch_compact(F, rec, (int*)c->reflist.p, &sm->refresh_count, (int*)c->segof.p, (int*)c->alist.p,
+                 &sm->approx_count, (int*)c->aseg.p, 0, st);
+  small_tail_kernel<<<1, 1, 0, st>>>(sm, (const int*)c->reflist.p, fi.c32, fi.c64, fi.G);
+  pcv_status ps = sync_small(c);
+  if (ps != PCV_OK) return ps;
+  const int nref = c->small_host->refresh_count;
+  const int napp = c->small_host->approx_count;
+  const size_t seg_bytes = work_elem(c->prec) * 9 * (size_t)M;
+  if ((ps = ensure(c, c->Bseg, seg_bytes * (size_t)(nref + 1))) != PCV_OK) return ps;
+  if (had_prior) CUDA_TRY(c, cudaMemcpyAsync(c->Bseg.p, c->Bprior.p, seg_bytes, cudaMemcpyDeviceToDevice, st));
+  void* Bseg1 = (char*)c->Bseg.p + seg_bytes;
+  launch_exact_pairs(c->prec, nref, (const int*)c->reflist.p, nullptr, frames, L, fi, c->Dbuf.p, Bseg1,
+                     (unsigned*)c->status.p, st);
+  launch_approx_pairs(c->prec, napp, (const int*)c->alist.p, (const int*)c->aseg.p, &sm->approx_count, frames, L,
+                      fi, rec.qxy, c->Bseg.p, c->Dbuf.p, st);
+  launch_finalize(c->prec, F, M, c->Dbuf.p, L.q, c->lambda, s, z, (float*)c->mstat.p, (double*)c->mstat.p, msd, st);
+  if (refreshed) CUDA_TRY(c, cudaMemcpyAsync(refreshed, rec.flag, F, cudaMemcpyDeviceToDevice, st));
+  if (gs && gz) {
+    launch_adjoint_beta(c->prec, F, L, c->Dbuf.p, (const float*)c->mstat.p, s, c->lambda, nullptr, c->Bseg.p,
+                        (const int*)c->segof.p, gs, gz, st);
+    launch_adjoint_finish(c->prec, F, frames, L, fi, c->Dbuf.p, (const float*)c->mstat.p, s, c->lambda, c->Bseg.p,
+                          (const int*)c->segof.p, rec, prior, gs, gz, (unsigned*)c->status.p, st);
+  }
+  // carry the close structure over to the next call
+  const int last = c->small_host->last_refresh;
+  if (nref > 0 && last >= 0) {
+    const size_t ybytes = frame_elem(c->prec) * 3 * (size_t)c->N;
+    if ((ps = ensure(c, c->y, ybytes)) != PCV_OK) return ps;
+    if ((ps = ensure(c, c->Bprior, seg_bytes)) != PCV_OK) return ps;
+    CUDA_TRY(c, cudaMemcpyAsync(c->y.p, (const char*)frames + ybytes * (size_t)last, ybytes,
+                                cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(c, cudaMemcpyAsync(c->Bprior.p, (char*)c->Bseg.p + seg_bytes * (size_t)nref, seg_bytes,
+                                cudaMemcpyDeviceToDevice, st));
+    c->y_c32 = c->small_host->last_c32;
+    c->y_c64 = c->small_host->last_c64;
+    c->y_G = c->small_host->last_G;
+    c->has_y = true;
+  }
+  c->stats.frames += F;
+  c->stats.xy_alignments += had_prior ? F : F - 1;
+  c->stats.landmark_alignments += (int64_t)M * nref;
+  c->stats.approx_msds += (int64_t)M * napp;
+  c->stats.refreshes_initial += had_prior ? 0 : 1;
+  c->stats.refreshes_threshold += nref - (had_prior ? 0 : 1);
+  return PCV_OK;
+}
+
+pcv_status evaluate_exact(pcv_ctx* c, int F, const void* frames, double* s, double* z, void* gs, void* gz,
+                          double* msd, uint8_t* refreshed) {
+  const cudaStream_t st = c->stream;
+  const LandmarkDev L = lm_view(c);
+  const FrameInfo fi = frame_info(c);
+  const bool grads = gs && gz;
+  launch_frame_prep(c->prec, F, frames, L, fi, st);
+  launch_exact_pairs(c->prec, F, nullptr, nullptr, frames, L, fi, c->Dbuf.p, grads ? c->Rpair.p : nullptr,
+                     (unsigned*)c->status.p, st);
+  launch_finalize(c->prec, F, c->M, c->Dbuf.p, L.q, c->lambda, s, z, (float*)c->mstat.p, (double*)c->mstat.p, msd,
+                  st);
+  if (refreshed) launch_fill_u8(refreshed, 1, (size_t)F, st);
+  if (grads) {
+    launch_adjoint_beta(c->prec, F, L, c->Dbuf.p, (const float*)c->mstat.p, s, c->lambda, c->Rpair.p, nullptr, nullptr,
+                        gs, gz, st);
+    FrameRec none;
+    RefDesc nop;
+    launch_adjoint_finish(c->prec, F, frames, L, fi, c->Dbuf.p, (const float*)c->mstat.p, s, c->lambda, nullptr,
+                          nullptr, none, nop, gs, gz, (unsigned*)c->status.p, st);
+  }
+  c->stats.frames += F;
+  c->stats.landmark_alignments += (int64_t)c->M * F;
+  return PCV_OK;
+}
+
+}  // namespace
+
+pcv_status pcv_evaluate(pcv_ctx* c, int F, const void* frames, double* s, double* z, void* dsdx, void* dzdx,
+                        double* msd, uint8_t* refreshed) {
+  if (!c) return fail(nullptr, PCV_EINVAL, "NULL context");
+  if (!c->have_lm) return fail(c, PCV_ESTATE, "landmarks not set");
+  if (!c->have_lambda) return fail(c, PCV_ESTATE, "lambda not set");
+  if (F < 0) return fail(c, PCV_EINVAL, "F < 0");
+  if (F == 0) return PCV_OK;
+  if (!frames || !s || !z) return fail(c, PCV_EINVAL, "frames, s and z are required");
+  if ((dsdx == nullptr) != (dzdx == nullptr)) return fail(c, PCV_EINVAL, "pass both dsdx and dzdx or neither");
+  if ((size_t)F * c->M > ((size_t)1 << 40)) return fail(c, PCV_EINVAL, "F*M too large");
+  cudaSetDevice(c->device);
+  const bool close = c->eps >= 0.0;
+  pcv_status st = ensure_frame_workspace(c, F, close, dsdx != nullptr);
+  if (st != PCV_OK) return st;
+  st = close ? evaluate_close(c, F, frames, s, z, dsdx, dzdx, msd, refreshed)
+             : evaluate_exact(c, F, frames, s, z, dsdx, dzdx, msd, refreshed);
+  if (st != PCV_OK) return st;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, PCV_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
+  return PCV_OK;
+}
+
+pcv_status pcv_evaluate_host(pcv_ctx* c, int F, const void* frames, double* s, double* z, void* dsdx, void* dzdx,
+                             double* msd, uint8_t* refreshed) {
+  if (!c) return fail(nullptr, PCV_EINVAL, "NULL context");
+  if (!c->have_lm) return fail(c, PCV_ESTATE, "landmarks not set");
+  if (F < 0) return fail(c, PCV_EINVAL, "F < 0");
+  if (F == 0) return PCV_OK;
+  if (!frames || !s || !z) return fail(c, PCV_EINVAL, "frames, s and z are required");
+  if ((dsdx == nullptr) != (dzdx == nullptr)) return fail(c, PCV_EINVAL, "pass both dsdx and dzdx or neither");
+  cudaSetDevice(c->device);
+  const size_t fbytes = frame_elem(c->prec) * 3 * (size_t)c->N * F;
+  pcv_status st;
+  if ((st = ensure(c, c->h_frames, fbytes)) != PCV_OK) return st;
+  if ((st = ensure(c, c->h_s, sizeof(double) * F)) != PCV_OK) return st;
+  if ((st = ensure(c, c->h_z, sizeof(double) * F)) != PCV_OK) return st;
+  if (dsdx) {
+    if ((st = ensure(c, c->h_gs, fbytes)) != PCV_OK) return st;
+    if ((st = ensure(c, c->h_gz, fbytes)) != PCV_OK) return st;
+  }
+  if (msd && (st = ensure(c, c->h_msd, sizeof(double) * (size_t)F * c->M)) != PCV_OK) return st;
+  if (refreshed && (st = ensure(c, c->h_ref, F)) != PCV_OK) return st;
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_frames.p, frames, fbytes, cudaMemcpyHostToDevice, c->stream));
+  st = pcv_evaluate(c, F, c->h_frames.p, (double*)c->h_s.p, (double*)c->h_z.p, dsdx ? c->h_gs.p : nullptr,
+                    dsdx ? c->h_gz.p : nullptr, msd ? (double*)c->h_msd.p : nullptr,
+                    refreshed ? (uint8_t*)c->h_ref.p : nullptr);
+  if (st != PCV_OK) return st;
+  CUDA_TRY(c, cudaMemcpyAsync(s, c->h_s.p, sizeof(double) * F, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(z, c->h_z.p, sizeof(double) * F, cudaMemcpyDeviceToHost, c->stream));
+  if (dsdx) {
+    CUDA_TRY(c, cudaMemcpyAsync(dsdx, c->h_gs.p, fbytes, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(dzdx, c->h_gz.p, fbytes, cudaMemcpyDeviceToHost, c->stream));
+  }
+  if (msd)
+    CUDA_TRY(c, cudaMemcpyAsync(msd, c->h_msd.p, sizeof(double) * (size_t)F * c->M, cudaMemcpyDeviceToHost, c->stream));
+  if (refreshed) CUDA_TRY(c, cudaMemcpyAsync(refreshed, c->h_ref.p, F, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return PCV_OK;
+}
+
+pcv_status pcv_combine_grad(pcv_ctx* c, int F, const double* g_s, const double* g_z, const void* dsdx,
+                            const void* dzdx, void* out) {
+  if (!c) return fail(nullptr, PCV_EINVAL, "NULL context");
+  if (!c->have_lm) return fail(c, PCV_ESTATE, "landmarks not set");
+  if (F < 0) return fail(c, PCV_EINVAL, "F < 0");
+  if (F == 0) return PCV_OK;
+  if (!dsdx || !dzdx || !out) return fail(c, PCV_EINVAL, "dsdx, dzdx and out are required");
+  cudaSetDevice(c->device);
+  launch_combine_grad(c->prec, F, 3 * c->N, g_s, g_z, dsdx, dzdx, out, c->stream);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, PCV_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
+  return PCV_OK;
+}
+
+pcv_status pcv_sync(pcv_ctx* c) {
+  if (!c) return fail(nullptr, PCV_EINVAL, "NULL context");
+  cudaSetDevice(c->device);
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  unsigned status = 0;
+  CUDA_TRY(c, cudaMemcpy(&status, c->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (status) {
+    CUDA_TRY(c, cudaMemset(c->status.p, 0, sizeof(unsigned)));
+    if (status & STATUS_NOCONV) return fail(c, PCV_ENOCONV, "an eigen-solve reached its iteration cap");
+  }
+  return PCV_OK;
+}
+
+pcv_status pcv_get_stats(pcv_ctx* c, pcv_stats* out) {
+  if (!c || !out) return fail(c, PCV_EINVAL, "NULL argument");
+  cudaSetDevice(c->device);
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  unsigned long long n = 0;
+  CUDA_TRY(c, cudaMemcpy(&n, c->nrecheck.p, sizeof(n), cudaMemcpyDeviceToHost));
+  c->stats.fp64_rechecks = (int64_t)n;
+  *out = c->stats;
+  return PCV_OK;
+}
+
+// state blob: header, then y (N*3 frame type), B (M*9 work type)
+namespace {
+struct StateHeader {
+  char magic[8];
+  int32_t version, prec, M, N, has_y, pad;
+  float4 y_c32;
+  double4 y_c64;
+  double y_G;
+  double gap_estimate;
+  pcv_stats stats;
+};
+}  // namespace
+
+pcv_status pcv_save_state(pcv_ctx* c, void* buf, size_t* len) {
+  if (!c || !len) return fail(c, PCV_EINVAL, "NULL argument");
+  if (!c->have_lm) return fail(c, PCV_ESTATE, "landmarks not set");
+  const size_t ybytes = frame_elem(c->prec) * 3 * (size_t)c->N;
+  const size_t bbytes = work_elem(c->prec) * 9 * (size_t)c->M;
+  const size_t need = sizeof(StateHeader) + ybytes + bbytes;
+  if (!buf) {
+    *len = need;
+    return PCV_OK;
+  }
+  if (*len < need) return fail(c, PCV_EINVAL, "buffer too small (%zu < %zu)", *len, need);
+  pcv_stats stt;
+  pcv_status st = pcv_get_stats(c, &stt);
+  if (st != PCV_OK) return st;
+  StateHeader h{};
+  memcpy(h.magic, "PCVSTAT", 8);
+  h.version = 1;
+  h.prec = (int)c->prec;
+  h.M = c->M;
+  h.N = c->N;
+  h.has_y = c->has_y ? 1 : 0;
+  h.y_c32 = c->y_c32;
+  h.y_c64 = c->y_c64;
+  h.y_G = c->y_G;
+  h.gap_estimate = c->gap_estimate;
+  h.stats = stt;
+  char* out = (char*)buf;
+  memcpy(out, &h, sizeof(h));
+  if (c->has_y) {
+    CUDA_TRY(c, cudaMemcpy(out + sizeof(h), c->y.p, ybytes, cudaMemcpyDeviceToHost));
+    CUDA_TRY(c, cudaMemcpy(out + sizeof(h) + ybytes, c->Bprior.p, bbytes, cudaMemcpyDeviceToHost));
+  } else {
+    memset(out + sizeof(h), 0, ybytes + bbytes);
+  }
+  *len = need;
+  return PCV_OK;
+}
+
+pcv_status pcv_load_state(pcv_ctx* c, const void* buf, size_t len) {
+  if (!c || !buf) return fail(c, PCV_EINVAL, "NULL argument");
+  if (!c->have_lm) return fail(c, PCV_ESTATE, "landmarks not set");
+  const size_t ybytes = frame_elem(c->prec) * 3 * (size_t)c->N;
+  const size_t bbytes = work_elem(c->prec) * 9 * (size_t)c->M;
+  if (len < sizeof(StateHeader) + ybytes + bbytes) return fail(c, PCV_ESTATE, "state blob too short");
+  StateHeader h;
+  memcpy(&h, buf, sizeof(h));
+  if (memcmp(h.magic, "PCVSTAT", 8) != 0 || h.version != 1) return fail(c, PCV_ESTATE, "not a state blob");
+  if (h.prec != (int)c->prec || h.M != c->M || h.N != c->N) return fail(c, PCV_ESTATE, "state blob does not match");
+  cudaSetDevice(c->device);
+  pcv_status st;
+  if ((st = ensure(c, c->y, ybytes)) != PCV_OK) return st;
+  if ((st = ensure(c, c->Bprior, bbytes)) != PCV_OK) return st;
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  const char* in = (const char*)buf;
+  CUDA_TRY(c, cudaMemcpy(c->y.p, in + sizeof(h), ybytes, cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(c->Bprior.p, in + sizeof(h) + ybytes, bbytes, cudaMemcpyHostToDevice));
+  c->has_y = h.has_y != 0;
+  c->y_c32 = h.y_c32;
+  c->y_c64 = h.y_c64;
+  c->y_G = h.y_G;
+  c->gap_estimate = h.gap_estimate;
+  c->stats = h.stats;
+  unsigned long long n = (unsigned long long)h.stats.fp64_rechecks;
+  CUDA_TRY(c, cudaMemcpy(c->nrecheck.p, &n, sizeof(n), cudaMemcpyHostToDevice));
+  return PCV_OK;
+}
+
+}  // extern "C"

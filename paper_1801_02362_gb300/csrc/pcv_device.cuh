@@ -1,0 +1,336 @@
+// pcv_device.cuh -- device-side numerics shared by the path-CV kernels.
+//
+// Precision plan (GB300 issues FP64 at 1/62 of the FP32 rate):
+//  * per-atom sums (correlation matrix, centroids, sums of squares) run in FP32 with an
+//    error-free outer accumulator (TwoSum, Knuth) -- never FP64 per atom;
+//  * the 4x4 quaternion eigenvalue, on which MSD = G_x + G_a - 2 lambda_max cancels, is
+//    found in FP64: characteristic polynomial of K (Section 3, quaternion method of
+//    Kearsley / Coutsias), Newton from the upper bound (G_x + G_a)/2, first in FP32 to
+//    get close, then FP64 steps; a bounded number of iterations, never a spin;
+//  * eigenvectors / rotations, which only need FP32 accuracy (the MSD is stationary in
+//    the rotation), come from an adjugate column of K - lambda I in FP32.
+#pragma once
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace pcv {
+
+// ---------------------------------------------------------------------------------------
+// compensated FP32 accumulation: (hi, lo) += v without losing the rounding error of the
+// addition (TwoSum).  Valid without FMA contraction concerns: no products involved.
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
+  const float s = __fadd_rn(hi, v);
+  const float bp = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(v, bp));
+  hi = s;
+  lo = __fadd_rn(lo, err);
+}
+
+// (hi, lo) pair sum of two compensated values
+__device__ __forceinline__ void two_sum_pair(float& hi, float& lo, float hi2, float lo2) {
+  two_sum_acc(hi, lo, hi2);
+  lo = __fadd_rn(lo, lo2);
+}
+
+__device__ __forceinline__ double pair_to_double(float hi, float lo) {
+  return (double)hi + (double)lo;
+}
+
+// warp-wide sum of a compensated FP32 value; every lane receives the result
+__device__ __forceinline__ void warp_sum_pair(float& hi, float& lo) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, off);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, off);
+    two_sum_pair(hi, lo, h2, l2);
+  }
+}
+
+__device__ __forceinline__ double warp_sum_double(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+__device__ __forceinline__ float warp_sum_float(float v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// ---------------------------------------------------------------------------------------
+// storage conversions
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_f32(double v) { return (float)v; }
+
+// ---------------------------------------------------------------------------------------
+// Quaternion matrix.  For the correlation H[b][c] = sum_j w_j a_jb x_jc of a structure a
+// fitted onto x, q^T K q = trace(R(q) H) for unit q, so the largest eigenpair of K gives
+// the optimal rotation R(q) of a onto x and lambda_max = max_R trace(R H).
+template <typename T>
+__device__ __forceinline__ void quat_matrix(const T* H, T* K) {
+  const T hxx = H[0], hxy = H[1], hxz = H[2];
+  const T hyx = H[3], hyy = H[4], hyz = H[5];
+  const T hzx = H[6], hzy = H[7], hzz = H[8];
+  K[0] = hxx + hyy + hzz;
+  K[1] = hyz - hzy;
+  K[2] = hzx - hxz;
+  K[3] = hxy - hyx;
+  K[5] = hxx - hyy - hzz;
+  K[6] = hxy + hyx;
+  K[7] = hzx + hxz;
+  K[10] = -hxx + hyy - hzz;
+  K[11] = hyz + hzy;
+  K[15] = -hxx - hyy + hzz;
+  K[4] = K[1];
+  K[8] = K[2];
+  K[9] = K[6];
+  K[12] = K[3];
+  K[13] = K[7];
+  K[14] = K[11];
+}
+
+// det of a symmetric 4x4 through complementary 2x2 minors (Laplace expansion on rows 0-1)
+template <typename T>
+__device__ __forceinline__ T det4(const T* a) {
+  const T s0 = a[0] * a[5] - a[4] * a[1];
+  const T s1 = a[0] * a[6] - a[4] * a[2];
+  const T s2 = a[0] * a[7] - a[4] * a[3];
+  const T s3 = a[1] * a[6] - a[5] * a[2];
+  const T s4 = a[1] * a[7] - a[5] * a[3];
+  const T s5 = a[2] * a[7] - a[6] * a[3];
+  const T c5 = a[10] * a[15] - a[14] * a[11];
+  const T c4 = a[9] * a[15] - a[13] * a[11];
+  const T c3 = a[9] * a[14] - a[13] * a[10];
+  const T c2 = a[8] * a[15] - a[12] * a[11];
+  const T c1 = a[8] * a[14] - a[12] * a[10];
+  const T c0 = a[8] * a[13] - a[12] * a[9];
+  return s0 * c5 - s1 * c4 + s2 * c3 + s3 * c2 - s4 * c1 + s5 * c0;
+}
+
+template <typename T>
+__device__ __forceinline__ T det3(const T* h) {
+  return h[0] * (h[4] * h[8] - h[5] * h[7]) - h[1] * (h[3] * h[8] - h[5] * h[6]) +
+         h[2] * (h[3] * h[7] - h[4] * h[6]);
+}
+
+// Coefficients of det(lambda I - K) = lambda^4 + c2 lambda^2 + c1 lambda + c0
+// (trace K = 0): c2 = -2 |H|_F^2, c1 = -8 det H, c0 = det K.
+template <typename T>
+__device__ __forceinline__ void char_poly(const T* H, const T* K, T& c2, T& c1, T& c0) {
+  T f = 0;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) f += H[e] * H[e];
+  c2 = T(-2) * f;
+  c1 = T(-8) * det3(H);
+  c0 = det4(K);
+}
+
+// Largest root of the characteristic polynomial by Newton iteration started from an
+// upper bound ub >= lambda_max (e.g. (G_x + G_a)/2, Cauchy-Schwarz); from above, Newton
+// on a polynomial with all-real roots decreases monotonically onto the largest root.
+// FP32 iterations first (cheap); the FP64 iterations restart slightly above the FP32
+// estimate (by 4e-6 ub, well above its rounding error) so that they also approach from
+// above, and stop once a step is below 1e-13 ub.
+// Returns lambda_max; sets *ok = false if the iteration caps were reached.
+__device__ __forceinline__ double lambda_max_newton(const double* H, double ub, bool* ok) {
+  double K[16];
+  quat_matrix(H, K);
+  double c2, c1, c0;
+  char_poly(H, K, c2, c1, c0);
+  // FP32 phase
+  const float f2 = (float)c2, f1 = (float)c1, f0 = (float)c0;
+  float lf = (float)ub;
+  const float tolf = 2e-6f * fabsf(lf) + 1e-30f;
+  for (int it = 0; it < 40; ++it) {
+    const float l2 = lf * lf;
+    const float p = fmaf(fmaf(l2 + f2, lf, f1), lf, f0);
+    const float dp = fmaf(fmaf(4.0f * lf, lf, 2.0f * f2), lf, f1);
+    if (!(dp > 0.0f)) break;
+    const float step = p / dp;
+    lf -= step;
+    if (fabsf(step) <= tolf) break;
+  }
+  // FP64 phase
+  double l = (double)lf + 4e-6 * fabs(ub);
+  if (!(l <= ub) || !(l == l)) l = ub;
+  const double tol = 1e-13 * fabs(ub) + 1e-300;
+  *ok = false;
+  for (int it = 0; it < 60; ++it) {
+    const double l2 = l * l;
+    const double p = fma(fma(l2 + c2, l, c1), l, c0);
+    const double dp = fma(fma(4.0 * l, l, 2.0 * c2), l, c1);
+    if (!(dp > 0.0)) {
+      *ok = (p == 0.0);
+      break;
+    }
+    // the step only needs relative accuracy: divide in FP32
+    const double step = (double)__fdiv_rn((float)p, (float)dp);
+    l -= step;
+    if (fabs(step) <= tol) {
+      *ok = true;
+      break;
+    }
+  }
+  return l;
+}
+
+// Unit eigenvector of K for eigenvalue lam (FP32 accuracy): the adjugate of A = K - lam I
+// has rank one, proportional to q q^T; take its column with the largest diagonal entry.
+__device__ __forceinline__ void adj_eigvec(const double* K, double lam, float* q) {
+  float A[16];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) A[e] = (float)K[e];
+  // subtract lam on the diagonal in FP64 before rounding (the diagonal can cancel)
+  A[0] = (float)(K[0] - lam);
+  A[5] = (float)(K[5] - lam);
+  A[10] = (float)(K[10] - lam);
+  A[15] = (float)(K[15] - lam);
+  // 2x2 minors of rows 2,3 and rows 0,1 (columns i<j)
+  // cofactor C[r][c] = (-1)^(r+c) det(A without row r, column c)
+  float cof[16];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float m[9];
+      int k = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (i == r) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (j == c) continue;
+          m[k++] = A[4 * i + j];
+        }
+      }
+      const float d = m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6]) +
+                      m[2] * (m[3] * m[7] - m[4] * m[6]);
+      cof[4 * r + c] = ((r + c) & 1) ? -d : d;
+    }
+  int best = 0;
+  float bv = fabsf(cof[0]);
+#pragma unroll
+  for (int i = 1; i < 4; ++i)
+    if (fabsf(cof[5 * i]) > bv) {
+      bv = fabsf(cof[5 * i]);
+      best = i;
+    }
+  float v[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = cof[4 * i + best];
+  float n2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
+  if (!(n2 > 0.0f)) {
+    v[0] = 1.0f;
+    v[1] = v[2] = v[3] = 0.0f;
+    n2 = 1.0f;
+  }
+  const float inv = rsqrtf(n2) * (v[0] < 0.0f ? -1.0f : 1.0f);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) q[i] = v[i] * inv;
+}
+
+// Rotation of a unit quaternion q = (s, v): R = (s^2 - |v|^2) I + 2 v v^T + 2 s [v]_x,
+// divided by |q|^2 so that rounding in q does not spoil orthogonality to first order.
+template <typename T>
+__device__ __forceinline__ void quat_to_rot(const T* q, T* R) {
+  const T s = q[0], x = q[1], y = q[2], z = q[3];
+  const T n2 = s * s + x * x + y * y + z * z;
+  const T inv = T(1) / n2;
+  R[0] = (s * s + x * x - y * y - z * z) * inv;
+  R[1] = T(2) * (x * y - s * z) * inv;
+  R[2] = T(2) * (x * z + s * y) * inv;
+  R[3] = T(2) * (x * y + s * z) * inv;
+  R[4] = (s * s - x * x + y * y - z * z) * inv;
+  R[5] = T(2) * (y * z - s * x) * inv;
+  R[6] = T(2) * (x * z - s * y) * inv;
+  R[7] = T(2) * (y * z + s * x) * inv;
+  R[8] = (s * s - x * x - y * y + z * z) * inv;
+}
+
+// Unit eigenvector of K for eigenvalue lam in FP64 (adjugate column, as adj_eigvec).
+__device__ __forceinline__ void adj_eigvec_f64(const double* K, double lam, double* q) {
+  double A[16];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) A[e] = K[e];
+  A[0] -= lam;
+  A[5] -= lam;
+  A[10] -= lam;
+  A[15] -= lam;
+  double cof[16];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      double m[9];
+      int k = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (i == r) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (j == c) continue;
+          m[k++] = A[4 * i + j];
+        }
+      }
+      const double d = det3(m);
+      cof[4 * r + c] = ((r + c) & 1) ? -d : d;
+    }
+  int best = 0;
+  double bv = fabs(cof[0]);
+#pragma unroll
+  for (int i = 1; i < 4; ++i)
+    if (fabs(cof[5 * i]) > bv) {
+      bv = fabs(cof[5 * i]);
+      best = i;
+    }
+  double n2 = 0.0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    q[i] = cof[4 * i + best];
+    n2 += q[i] * q[i];
+  }
+  if (!(n2 > 0.0)) {
+    q[0] = 1.0;
+    q[1] = q[2] = q[3] = 0.0;
+    return;
+  }
+  const double inv = (q[0] < 0.0 ? -1.0 : 1.0) / sqrt(n2);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) q[i] *= inv;
+}
+
+// Solve the 4x4 symmetric positive definite system A p = g by Cholesky (FP64).
+// Returns false if A is not numerically positive definite.
+__device__ __forceinline__ bool spd_solve4(const double* A, const double* g, double* p) {
+  double L[16];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) L[e] = 0.0;
+  for (int i = 0; i < 4; ++i) {
+    for (int j = 0; j <= i; ++j) {
+      double sum = A[4 * i + j];
+      for (int k = 0; k < j; ++k) sum -= L[4 * i + k] * L[4 * j + k];
+      if (i == j) {
+        if (!(sum > 0.0)) return false;
+        L[4 * i + i] = sqrt(sum);
+      } else {
+        L[4 * i + j] = sum / L[4 * j + j];
+      }
+    }
+  }
+  double y[4];
+  for (int i = 0; i < 4; ++i) {
+    double sum = g[i];
+    for (int k = 0; k < i; ++k) sum -= L[4 * i + k] * y[k];
+    y[i] = sum / L[4 * i + i];
+  }
+  for (int i = 3; i >= 0; --i) {
+    double sum = y[i];
+    for (int k = i + 1; k < 4; ++k) sum -= L[4 * k + i] * p[k];
+    p[i] = sum / L[4 * i + i];
+  }
+  return true;
+}
+
+}  // namespace pcv

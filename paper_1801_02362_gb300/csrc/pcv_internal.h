@@ -1,0 +1,134 @@
+// pcv_internal.h -- host-side launcher interface between the C-ABI layer (pcv_api.cu)
+// and the kernel translation units (k_pair.cu, k_aux.cu).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pcv {
+
+enum Prec { P_F64 = 0, P_F32 = 1, P_F16 = 2 };
+
+// status bits written to the context's device status word
+constexpr unsigned STATUS_NOCONV = 1u;
+
+// Landmark set resident on the device (written by pcv_set_landmarks).
+struct LandmarkDev {
+  int M = 0, N = 0;
+  const void* coords = nullptr;  // M*N*3, centred, storage type of the mode
+  const double* G = nullptr;     // M: sum_j wk_j |a_j|^2 in kernel units (see below)
+  const double* A = nullptr;     // M*6: sum_j w_j a_j a_j^T (true weights, xx xy xz yy yz zz)
+  const double* q = nullptr;     // M: property q_i
+  const float* w = nullptr;      // N: true weights (normalised), or nullptr when uniform
+  const double* w64 = nullptr;   // N: the same weights in FP64, or nullptr when uniform
+  double dscale = 1.0;           // kernel units -> true: 1/N for uniform weights, else 1
+};
+// "Kernel units": with uniform weights the kernels sum unweighted products and the
+// results are scaled by dscale = 1/N in FP64 at the end; with explicit weights the
+// weights are applied inside the sums and dscale = 1.
+
+// Per-frame quantities from frame_prep: centre (as float for the FP32 path, double for
+// FP64 mode) and G_x = sum_j wk_j |x_j - c|^2 of the values the pair kernels stage.
+struct FrameInfo {
+  float4* c32 = nullptr;   // F: (cx, cy, cz, 0) FP32 modes
+  double4* c64 = nullptr;  // F: FP64 mode centres
+  double* G = nullptr;     // F
+};
+
+// A reference structure for frame-vs-structure alignment: either frame `index` of the
+// batch or (index < 0) the stored close structure.
+struct RefDesc {
+  const void* coords = nullptr;  // N*3, frame type
+  float4 c32;
+  double4 c64;
+  double G = 0.0;
+};
+
+// results of frame-vs-structure alignments
+struct AlignOut {
+  double* D = nullptr;   // D(x_t, ref) in true units
+  double4* q = nullptr;  // quaternion of R_{x ref}: rotation fitting ref onto x_t
+  uint8_t* flag = nullptr;  // bit0: D > eps, bit1: ambiguous (needs FP64 re-check)
+};
+
+// ---- k_aux.cu ----
+void launch_frame_prep(Prec p, int F, const void* frames, const LandmarkDev& L, FrameInfo fi,
+                       cudaStream_t st);
+// band: for t in [1, F) and k = 1..W with t-k >= 0: D(x_t, x_{t-k}) -> out[t*W + k-1]
+void launch_align_band(Prec p, int F, int W, const void* frames, const LandmarkDev& L,
+                       FrameInfo fi, double eps, AlignOut out, int* recheck_list,
+                       int* recheck_count, cudaStream_t st);
+// chunk: for t in [t0, t1): D(x_t, ref) -> out[t]; ref_index >= 0 is a frame of the batch
+void launch_align_chunk(Prec p, int t0, int t1, const void* frames, const LandmarkDev& L,
+                        FrameInfo fi, int ref_index, const RefDesc& prior, double eps,
+                        AlignOut out, int* recheck_list, int* recheck_count, cudaStream_t st);
+// FP64 re-check of the ambiguous alignments listed in `list` (entries encode slot kind)
+void launch_recheck(Prec p, int max_entries, const int* list, const int* count, int W,
+                    const void* frames, const LandmarkDev& L, const RefDesc& prior, int chunk_ref,
+                    double eps, AlignOut band, AlignOut chunk, unsigned long long* n_rechecks,
+                    cudaStream_t st);
+// recheck list entries: (slot << 1) | kind, kind 0 = band slot t*W + k-1, 1 = chunk slot t
+// first t in [t0, t1) with chunk flag bit0 set -> *first (initialised to t1 by the kernel)
+void launch_first_exceed(int t0, int t1, const uint8_t* flag, int* first, cudaStream_t st);
+
+// per-frame decision records
+struct FrameRec {
+  uint8_t* flag = nullptr;  // 0 approx, 1 refresh, 2 initial
+  int* ref = nullptr;       // frame index of the close structure used (-1: stored y)
+  double* dxy = nullptr;    // D(x_t, y) that decided the frame (-1 at initial)
+  double4* qxy = nullptr;   // quaternion of R_{x y} (approximate frames)
+};
+struct ScanResult {
+  int t_stop;  // first frame the band could not decide (F if none)
+  int ref;     // close-structure frame index in force at t_stop
+};
+// decide frames [t0, F) from the band with the state `o_init` (offset of frame t0-1 from
+// its close structure, 0..W); writes records and *res (device)
+void launch_band_scan(int F, int W, int t0, int o_init, const AlignOut band, FrameRec rec,
+                      ScanResult* res, cudaStream_t st);
+// frames [t0, t_end) approximate w.r.t. ref (chunk results), and frame t_end (if < t1) a
+// refresh
+void launch_chunk_records(int t0, int t_end, int t1, int ref, const AlignOut chunk, FrameRec rec,
+                          cudaStream_t st);
+void launch_initial_record(FrameRec rec, cudaStream_t st);
+
+// compaction of refresh / approximate frames (device lists, counts returned on device)
+void launch_compact(int F, const FrameRec rec, int* refresh_list, int* refresh_count,
+                    int* seg_of_frame, int* approx_list, int* approx_count, int* approx_seg,
+                    int prior_seg, cudaStream_t st);
+
+// softmax finalisation: s, z per frame from the F x M distances (float in FP32 modes,
+// double in FP64 mode); mstat[f] = (m, l) with m = min_i D_i, l = sum_i exp(-lambda(D_i-m));
+// msd_out (optional) receives the distances as doubles
+void launch_finalize(Prec p, int F, int M, const void* D, const double* q, double lambda,
+                     double* s, double* z, float* mstat, double* mstat64, double* msd_out,
+                     cudaStream_t st);
+
+// adjoint: beta = sum_i gamma_i Rot_fi a_i (written into gs/gz), then per-frame finish.
+// Rpair (exact mode): F*M*9 rotations; otherwise Bseg[seg_of_frame[f]*M + i] (close mode).
+void launch_adjoint_beta(Prec p, int F, const LandmarkDev& L, const void* D, const float* mstat,
+                         const double* s, double lambda, const void* Rpair, const void* Bseg,
+                         const int* seg_of_frame, void* gs, void* gz, cudaStream_t st);
+// rec.flag == nullptr: exact mode (no rotation term)
+void launch_adjoint_finish(Prec p, int F, const void* frames, const LandmarkDev& L, FrameInfo fi,
+                           const void* D, const float* mstat, const double* s, double lambda,
+                           const void* Bseg, const int* seg_of_frame, const FrameRec rec,
+                           const RefDesc& prior, void* gs, void* gz, unsigned* status,
+                           cudaStream_t st);
+void launch_combine_grad(Prec p, int F, int N3, const double* g_s, const double* g_z,
+                         const void* gs, const void* gz, void* out, cudaStream_t st);
+void launch_fill_u8(uint8_t* p, uint8_t v, size_t n, cudaStream_t st);
+void launch_set_int(int* p, int v, cudaStream_t st);
+
+// ---- k_pair.cu ----
+// exact pairs: rows r in [0, rows) are frames row_frame[r] (or r if null); D -> D[f*M+i]
+// (float in FP32 modes, double in FP64 mode); R (optional) -> Rout[(r*M + i)*9]
+void launch_exact_pairs(Prec p, int rows, const int* row_frame, const int* rows_dev, const void* frames,
+                        const LandmarkDev& L, FrameInfo fi, void* D, void* Rout, unsigned* status,
+                        cudaStream_t st);
+// approximate pairs (form A): list entries k < *count: frame approx_list[k] of segment
+// approx_seg[k]; rotations Bseg[seg*M + i] (9 floats each), R_{x y} from rec.qxy
+void launch_approx_pairs(Prec p, int max_rows, const int* approx_list, const int* approx_seg,
+                         const int* count, const void* frames, const LandmarkDev& L, FrameInfo fi,
+                         const double4* qxy, const void* Bseg, void* D, cudaStream_t st);
+
+}  // namespace pcv

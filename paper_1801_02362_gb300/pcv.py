@@ -1,0 +1,300 @@
+"""Python binding of the C ABI in include/pcv.h (ctypes; argument marshalling only).
+
+Every computation happens in libpcv.so.  The functions ``pcv_*`` mirror the C entry
+points one to one; ``PathCV`` wraps a context for torch device tensors and
+``PathCVFunction`` is the autograd.Function whose backward applies the chain rule through
+``pcv_combine_grad``.  Loading fails loudly if the library has not been built
+(``python -m paper_1801_02362_gb300.build_lib`` or ``__graft_entry__.build()``): there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+
+from . import build_lib
+
+PCV_OK, PCV_EINVAL, PCV_ECUDA, PCV_ENOMEM, PCV_ENOCONV, PCV_ESTATE = 0, -1, -2, -3, -4, -5
+PCV_FP64, PCV_FP32, PCV_FP16_STORAGE = 0, 1, 2
+PCV_OPT_BAND, PCV_OPT_CHUNK, PCV_OPT_EXACT_TILE, PCV_OPT_APPROX_TILE = 1, 2, 3, 4
+
+_STATUS_NAMES = {0: "PCV_OK", -1: "PCV_EINVAL", -2: "PCV_ECUDA", -3: "PCV_ENOMEM", -4: "PCV_ENOCONV",
+                 -5: "PCV_ESTATE"}
+
+
+class PcvError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class pcv_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("frames", "xy_alignments", "landmark_alignments", "approx_msds",
+                                              "refreshes_threshold", "refreshes_initial", "fp64_rechecks",
+                                              "host_syncs")]
+
+    def as_dict(self) -> dict:
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+# exported entry points: name -> (restype, argtypes)
+_vp, _dp, _i, _d = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_double
+SIGNATURES = {
+    "pcv_create": (_i, [ctypes.POINTER(_vp), _i, _vp, _i]),
+    "pcv_destroy": (_i, [_vp]),
+    "pcv_set_stream": (_i, [_vp, _vp]),
+    "pcv_set_landmarks": (_i, [_vp, _i, _i, _vp, _vp, _vp]),
+    "pcv_set_lambda": (_i, [_vp, _d]),
+    "pcv_set_close_threshold": (_i, [_vp, _d]),
+    "pcv_evaluate": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "pcv_evaluate_host": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "pcv_combine_grad": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp]),
+    "pcv_reset_close_state": (_i, [_vp]),
+    "pcv_save_state": (_i, [_vp, _vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "pcv_load_state": (_i, [_vp, _vp, ctypes.c_size_t]),
+    "pcv_get_stats": (_i, [_vp, ctypes.POINTER(pcv_stats)]),
+    "pcv_sync": (_i, [_vp]),
+    "pcv_set_option": (_i, [_vp, _i, ctypes.c_int64]),
+    "pcv_last_error": (ctypes.c_char_p, [_vp]),
+}
+
+_lib = None
+
+
+def library_path() -> Path:
+    return build_lib.LIB
+
+
+def load(path: str | Path | None = None):
+    """Load libpcv.so (raises if it is missing: build it first)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = Path(path) if path else library_path()
+    if not p.exists():
+        raise RuntimeError(f"libpcv.so not found at {p}: build it with __graft_entry__.build() "
+                           "(the CUDA library is required; there is no fallback)")
+    L = ctypes.CDLL(str(p))
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(ctx, st):
+    if st != PCV_OK:
+        msg = load().pcv_last_error(ctx)
+        raise PcvError(st, msg.decode() if msg else "")
+
+
+# ---- thin wrappers with the C names ------------------------------------------------------
+def pcv_create(device: int = 0, stream: int | None = None, precision: int = PCV_FP32):
+    h = ctypes.c_void_p()
+    st = load().pcv_create(ctypes.byref(h), device, stream, precision)
+    _check(None, st)
+    return h
+
+
+def pcv_destroy(ctx):
+    load().pcv_destroy(ctx)
+
+
+def pcv_set_stream(ctx, stream):
+    _check(ctx, load().pcv_set_stream(ctx, stream))
+
+
+def pcv_set_landmarks(ctx, coords: np.ndarray, w: np.ndarray | None = None, q: np.ndarray | None = None):
+    coords = np.ascontiguousarray(coords, dtype=np.float64)
+    m, n = coords.shape[0], coords.shape[1]
+    wp = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+    qp = None if q is None else np.ascontiguousarray(q, dtype=np.float64)
+    st = load().pcv_set_landmarks(ctx, m, n, coords.ctypes.data, None if wp is None else wp.ctypes.data,
+                                  None if qp is None else qp.ctypes.data)
+    _check(ctx, st)
+
+
+def pcv_set_lambda(ctx, lam: float):
+    _check(ctx, load().pcv_set_lambda(ctx, float(lam)))
+
+
+def pcv_set_close_threshold(ctx, eps: float):
+    _check(ctx, load().pcv_set_close_threshold(ctx, float(eps)))
+
+
+def pcv_set_option(ctx, key: int, value: int):
+    _check(ctx, load().pcv_set_option(ctx, key, int(value)))
+
+
+def pcv_evaluate(ctx, F: int, frames_ptr, s_ptr, z_ptr, dsdx_ptr=None, dzdx_ptr=None, msd_ptr=None,
+                 refreshed_ptr=None):
+    _check(ctx, load().pcv_evaluate(ctx, F, frames_ptr, s_ptr, z_ptr, dsdx_ptr, dzdx_ptr, msd_ptr, refreshed_ptr))
+
+
+def pcv_evaluate_host(ctx, F: int, frames_ptr, s_ptr, z_ptr, dsdx_ptr=None, dzdx_ptr=None, msd_ptr=None,
+                      refreshed_ptr=None):
+    _check(ctx, load().pcv_evaluate_host(ctx, F, frames_ptr, s_ptr, z_ptr, dsdx_ptr, dzdx_ptr, msd_ptr,
+                                         refreshed_ptr))
+
+
+def pcv_combine_grad(ctx, F: int, gs_ptr, gz_ptr, dsdx_ptr, dzdx_ptr, out_ptr):
+    _check(ctx, load().pcv_combine_grad(ctx, F, gs_ptr, gz_ptr, dsdx_ptr, dzdx_ptr, out_ptr))
+
+
+def pcv_reset_close_state(ctx):
+    _check(ctx, load().pcv_reset_close_state(ctx))
+
+
+def pcv_save_state(ctx) -> bytes:
+    n = ctypes.c_size_t(0)
+    _check(ctx, load().pcv_save_state(ctx, None, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(ctx, load().pcv_save_state(ctx, buf, ctypes.byref(n)))
+    return buf.raw[: n.value]
+
+
+def pcv_load_state(ctx, blob: bytes):
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(ctx, load().pcv_load_state(ctx, buf, len(blob)))
+
+
+def pcv_get_stats(ctx) -> dict:
+    out = pcv_stats()
+    _check(ctx, load().pcv_get_stats(ctx, ctypes.byref(out)))
+    return out.as_dict()
+
+
+def pcv_sync(ctx):
+    _check(ctx, load().pcv_sync(ctx))
+
+
+def pcv_last_error(ctx) -> str:
+    m = load().pcv_last_error(ctx)
+    return m.decode() if m else ""
+
+
+# ---- torch convenience layer ---------------------------------------------------------------
+_PREC = {"fp64": PCV_FP64, "fp32": PCV_FP32, "fp16": PCV_FP16_STORAGE}
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class PathCV:
+    """A library context bound to one CUDA device and the current torch stream.
+
+    frames are torch CUDA tensors (F, N, 3): float64 in 'fp64' mode, float32 otherwise.
+    """
+
+    def __init__(self, landmarks: np.ndarray, lam: float, eps: float = -1.0, precision: str = "fp32",
+                 weights: np.ndarray | None = None, props: np.ndarray | None = None, device: int = 0,
+                 band: int | None = None, min_chunk: int | None = None):
+        import torch
+
+        self.torch = torch
+        self.precision = precision
+        self.device = torch.device("cuda", device)
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        self.ctx = pcv_create(device, stream, _PREC[precision])
+        self.M, self.N = landmarks.shape[0], landmarks.shape[1]
+        pcv_set_landmarks(self.ctx, landmarks, weights, props)
+        pcv_set_lambda(self.ctx, lam)
+        pcv_set_close_threshold(self.ctx, eps)
+        if band is not None:
+            pcv_set_option(self.ctx, PCV_OPT_BAND, band)
+        if min_chunk is not None:
+            pcv_set_option(self.ctx, PCV_OPT_CHUNK, min_chunk)
+
+    @property
+    def frame_dtype(self):
+        return self.torch.float64 if self.precision == "fp64" else self.torch.float32
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            pcv_destroy(self.ctx)
+            self.ctx = None
+
+    __del__ = close
+
+    def _bind_stream(self):
+        pcv_set_stream(self.ctx, self.torch.cuda.current_stream(self.device).cuda_stream)
+
+    def evaluate(self, frames, grad: bool = False, msd: bool = False, refreshed: bool = False) -> dict:
+        torch = self.torch
+        if frames.dtype != self.frame_dtype or not frames.is_cuda or not frames.is_contiguous():
+            raise ValueError(f"frames must be a contiguous CUDA tensor of {self.frame_dtype}")
+        F = frames.shape[0]
+        dev = frames.device
+        out = {"s": torch.empty(F, dtype=torch.float64, device=dev), "z": torch.empty(F, dtype=torch.float64, device=dev)}
+        if grad:
+            out["dsdx"] = torch.empty_like(frames)
+            out["dzdx"] = torch.empty_like(frames)
+        if msd:
+            out["msd"] = torch.empty((F, self.M), dtype=torch.float64, device=dev)
+        if refreshed:
+            out["refreshed"] = torch.empty(F, dtype=torch.uint8, device=dev)
+        self._bind_stream()
+        pcv_evaluate(self.ctx, F, _ptr(frames), _ptr(out["s"]), _ptr(out["z"]), _ptr(out.get("dsdx")),
+                     _ptr(out.get("dzdx")), _ptr(out.get("msd")), _ptr(out.get("refreshed")))
+        return out
+
+    def combine_grad(self, g_s, g_z, dsdx, dzdx):
+        out = self.torch.empty_like(dsdx)
+        self._bind_stream()
+        pcv_combine_grad(self.ctx, dsdx.shape[0], _ptr(g_s), _ptr(g_z), _ptr(dsdx), _ptr(dzdx), _ptr(out))
+        return out
+
+    def stats(self) -> dict:
+        return pcv_get_stats(self.ctx)
+
+    def sync(self):
+        pcv_sync(self.ctx)
+
+    def reset(self):
+        pcv_reset_close_state(self.ctx)
+
+    def save_state(self) -> bytes:
+        return pcv_save_state(self.ctx)
+
+    def load_state(self, blob: bytes):
+        pcv_load_state(self.ctx, blob)
+
+
+def _make_function():
+    import torch
+
+    class PathCVFunction(torch.autograd.Function):
+        """(s, z) = PathCVFunction.apply(frames, pathcv): the forward evaluates s, z and
+        their coordinate derivatives in the library; the backward forms
+        g_s * ds/dx + g_z * dz/dx in the library."""
+
+        @staticmethod
+        def forward(ctx, frames, pathcv):
+            r = pathcv.evaluate(frames.contiguous(), grad=True)
+            ctx.pathcv = pathcv
+            ctx.save_for_backward(r["dsdx"], r["dzdx"])
+            return r["s"], r["z"]
+
+        @staticmethod
+        def backward(ctx, g_s, g_z):
+            dsdx, dzdx = ctx.saved_tensors
+            g_s = None if g_s is None else g_s.contiguous().to(torch.float64)
+            g_z = None if g_z is None else g_z.contiguous().to(torch.float64)
+            return ctx.pathcv.combine_grad(g_s, g_z, dsdx, dzdx), None
+
+    return PathCVFunction
+
+
+_function = None
+
+
+def path_cv(frames, pathcv: PathCV):
+    """Differentiable (s, z) of a batch of frames."""
+    global _function
+    if _function is None:
+        _function = _make_function()
+    return _function.apply(frames, pathcv)

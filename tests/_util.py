@@ -1,0 +1,58 @@
+"""Shared test helpers: seeded problems (from synth) and the error metrics.
+
+Metrics (readings of the required accuracy):
+  D: |D_gpu - D_ref| / max(D_ref, 1e-3 (G_x + G_a))   -- FP32 inputs cannot support a
+     relative accuracy finer than ~eps32 (G_x + G_a) / D on the cancelling form;
+  s: |s_gpu - s_ref| / M;
+  z: |z_gpu - z_ref| / max(|z_ref|, 1/lambda);
+  gradients: max_k |g_gpu - g_ref| / max_k |g_ref| per frame.
+Tolerances: FP64 mode 1e-9, FP32 1e-5, FP16 storage 1e-3 (gradients: FP64 1e-8,
+FP32 2e-4, FP16 2e-2; derived in the design doc).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+from paper_1801_02362_gb300 import synth
+
+TOL = {"fp64": 1e-9, "fp32": 1e-5, "fp16": 1e-3}
+GRAD_TOL = {"fp64": 1e-8, "fp32": 2e-4, "fp16": 2e-2}
+
+
+def problem(seed, n, m, f, noise=0.05, schedule="drift", precision="fp32", ou_rho=0.0, lnoise=0.02):
+    fdt = np.float64 if precision == "fp64" else np.float32
+    lm, fr = synth.make_problem(seed, n_atoms=n, n_landmarks=m, n_frames=f, frame_noise=noise,
+                                landmark_noise=lnoise, schedule=schedule, ou_rho=ou_rho, frame_dtype=fdt,
+                                landmark_dtype=fdt)
+    lam = 2.3 / oracle.mean_adjacent_msd(lm)
+    return lm, fr, lam
+
+
+def gsum(coords, w=None):
+    """G = sum_j w_j |c_j - centre|^2 for each structure of a (S, N, 3) stack."""
+    n = coords.shape[1]
+    w = np.full(n, 1.0 / n) if w is None else w / w.sum()
+    c = np.einsum("j,sjk->sk", w, coords)
+    d = coords - c[:, None, :]
+    return np.einsum("j,sjk,sjk->s", w, d, d)
+
+
+def d_err(D_gpu, D_ref, frames, landmarks, w=None):
+    gx = gsum(frames, w)[:, None]
+    ga = gsum(landmarks, w)[None, :]
+    return np.max(np.abs(D_gpu - D_ref) / np.maximum(D_ref, 1e-3 * (gx + ga)))
+
+
+def s_err(s_gpu, s_ref, m):
+    return np.max(np.abs(s_gpu - s_ref)) / m
+
+
+def z_err(z_gpu, z_ref, lam):
+    return np.max(np.abs(z_gpu - z_ref) / np.maximum(np.abs(z_ref), 1.0 / lam))
+
+
+def grad_err(g_gpu, g_ref):
+    num = np.max(np.abs(g_gpu - g_ref).reshape(g_gpu.shape[0], -1), axis=1)
+    den = np.max(np.abs(g_ref).reshape(g_ref.shape[0], -1), axis=1)
+    return float(np.max(num / den))

@@ -1,0 +1,57 @@
+"""Host-side checks of the C ABI: the library builds for sm_103a, loads, exports every
+entry point include/pcv.h declares, and rejects calls it can reject without a GPU."""
+import ctypes
+import re
+from pathlib import Path
+
+import pytest
+
+from paper_1801_02362_gb300 import build_lib, pcv
+
+ROOT = Path(__file__).resolve().parents[1]
+HEADER = ROOT / "include" / "pcv.h"
+
+
+def declared_symbols():
+    text = HEADER.read_text()
+    return sorted(set(re.findall(r"^PCV_API\s+[\w\s\*]+?\b(pcv_\w+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_lib.build()
+    return pcv.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for required in ("pcv_create", "pcv_destroy", "pcv_set_landmarks", "pcv_set_lambda", "pcv_set_close_threshold",
+                     "pcv_evaluate", "pcv_evaluate_host", "pcv_reset_close_state", "pcv_save_state",
+                     "pcv_load_state", "pcv_get_stats", "pcv_sync", "pcv_last_error", "pcv_combine_grad"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+    assert set(declared_symbols()) <= set(pcv.SIGNATURES)
+
+
+def test_binary_targets_sm_103a(lib):
+    data = build_lib.LIB.read_bytes()
+    assert b"sm_103a" in data or b"sm_103" in data
+
+
+def test_null_context_is_rejected_without_gpu(lib):
+    assert lib.pcv_set_lambda(None, 1.0) == pcv.PCV_EINVAL
+    assert lib.pcv_evaluate(None, 1, None, None, None, None, None, None, None) == pcv.PCV_EINVAL
+    assert lib.pcv_destroy(None) == pcv.PCV_OK
+    assert isinstance(lib.pcv_last_error(None), bytes)
+    st = pcv.pcv_stats()
+    assert ctypes.sizeof(st) == 8 * 8
+
+
+def test_create_reports_bad_precision(lib):
+    h = ctypes.c_void_p()
+    assert lib.pcv_create(ctypes.byref(h), 0, None, 7) == pcv.PCV_EINVAL
+    assert h.value is None
