@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark of the path-CV hot path on one GB300 (or N independent walkers on N GPUs).
+
+Workload (the configuration the headline metric is quoted on): N = 300 atoms, M = 200
+landmarks along a synthetic path, a batch of F = 100,000 FP32 frames drifting along the
+path with N(0, 0.05 nm) noise; floating close structure with eps = 0.05 nm^2 (Algorithm 2);
+one step evaluates s, z and their coordinate derivatives ds/dx, dz/dx for the whole batch
+(every step of the path: frame centring, close-structure decisions, exact alignments at
+reassignments, approximate MSDs, path CVs, adjoint).  The close-structure state is reset
+at the start of every step so each step does the same work.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on the box's
+host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "path-CV frames/s and aligned MSDs/s on 1 GB300; % of HBM/L2 roofline"
+N_ATOMS, N_LANDMARKS, N_FRAMES = 300, 200, 100_000
+SEED = 1
+
+# FP32 ALU peak of one GB300: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.070 GHz (max SM clock)
+SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.070
+FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
+
+# algorithmic FP32 flops per (frame, landmark, atom) of each pair kernel (FMA = 2 flops)
+FLOPS_PER_UNIT = {
+    "approx_pair": 9,    # d = x' - b (3 sub), |d|^2 (3 FMA)
+    "exact_pair": 45,    # pass 1: 9 FMA; pass 2: R a (9 FMA), 3 sub, 3 FMA
+    "adjoint_beta": 36,  # beta^s, beta^z += gamma R a (2 x 9 FMA)
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--eps", type=float, default=0.05)
+    ap.add_argument("--frames", type=int, default=N_FRAMES)
+    ap.add_argument("--no-details", action="store_true", help="skip the exact-mode / eps-sweep side measurements")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+def workload_config(args):
+    return {
+        "workload": f"close-structure path CV, N={N_ATOMS} atoms, M={N_LANDMARKS} landmarks, F={args.frames} "
+                    f"frames per step, FP32, eps={args.eps} nm^2, s/z + ds/dx, dz/dx",
+        "atoms": N_ATOMS, "landmarks": N_LANDMARKS, "frames_per_step": args.frames, "eps_nm2": args.eps,
+        "precision": "fp32 (compensated sums, FP32 eigen-solve + direct MSD; FP64 refresh re-checks)",
+        "l2": "inputs larger than L2: frames 360 MB per step vs 126 MB L2 (landmarks 0.72 MB stay L2-resident)",
+        "data": "synthetic: seeded self-avoiding chains, interpolated path, drift + N(0,0.05) noise",
+    }
+
+
+def make_inputs(frames: int):
+    from paper_1801_02362_gb300 import synth
+
+    lm, fr = synth.make_problem(SEED, n_atoms=N_ATOMS, n_landmarks=N_LANDMARKS, n_frames=frames, frame_noise=0.05)
+    return lm, np.ascontiguousarray(fr, dtype=np.float32)
+
+
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.dev), "-lms", "100"], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in Path(self.path).read_text().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        import torch
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def max_over_ranks(value: float, pg, device):
+    if pg is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+# ------------------------------------------------------------------------------------------
+def lambda_from_gpu(pcv, lm):
+    """lambda = 2.3 / mean D(a_k, a_{k+1}), the adjacent-landmark MSDs computed by the library."""
+    import torch
+
+    ctx = pcv.PathCV(lm, 1.0, eps=-1.0, precision="fp32")
+    out = ctx.evaluate(torch.tensor(lm, dtype=torch.float32, device="cuda"), msd=True)
+    d = out["msd"].cpu().numpy()
+    ctx.close()
+    return 2.3 / float(np.mean(np.diagonal(d, offset=1)))
+
+
+def cpu_baseline(lm, fr, lam, eps, seconds: float) -> dict:
+    import oracle
+
+    oracle.build()
+    probe = 50
+    t0 = time.perf_counter()
+    oracle.close(fr[:probe], lm, lam, eps, want_grad=True, want_D=False)
+    per = (time.perf_counter() - t0) / probe
+    n = int(max(probe, min(len(fr), seconds / max(per, 1e-9))))
+    t0 = time.perf_counter()
+    oracle.close(fr[:n], lm, lam, eps, want_grad=True, want_D=False)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {n} frames of the workload, close structure eps={eps} with gradients, "
+                      f"{dt:.1f} s (Algorithm 2 is sequential: one thread)"}
+
+
+def run_reference(args):
+    world, rank, local, pg = dist_setup(args)
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    lm, fr = make_inputs(min(args.frames, 20000))
+    lam = 2.3 / oracle.mean_adjacent_msd(lm)
+    # bounded sample per step: ~2 s of oracle time
+    probe = 40
+    t0 = time.perf_counter()
+    oracle.close(fr[:probe], lm, lam, args.eps, want_grad=True, want_D=False)
+    per = (time.perf_counter() - t0) / probe
+    n = int(max(probe, min(len(fr), 2.0 / max(per, 1e-9))))
+    for _ in range(args.warmup):
+        oracle.close(fr[:n], lm, lam, args.eps, want_grad=True, want_D=False)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.close(fr[:n], lm, lam, args.eps, want_grad=True, want_D=False)
+    dt = time.perf_counter() - t0
+    value = n * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args),
+        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {n} frames of the workload per step (Algorithm 2 is sequential)"},
+        "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1801_02362_gb300 import pcv
+
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pcv.load()
+    lm, fr = make_inputs(args.frames)
+    F = fr.shape[0]
+    lam = lambda_from_gpu(pcv, lm)
+    frames = torch.from_numpy(fr).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = pcv.PathCV(lm, lam, eps=args.eps, precision="fp32", device=local)
+    s = torch.empty(F, dtype=torch.float64, device=dev)
+    z = torch.empty(F, dtype=torch.float64, device=dev)
+    gs = torch.empty_like(frames)
+    gz = torch.empty_like(frames)
+    P = pcv._ptr
+
+    def step():
+        pcv.pcv_reset_close_state(ctx.ctx)
+        pcv.pcv_evaluate(ctx.ctx, F, P(frames), P(s), P(z), P(gs), P(gz), None, None)
+
+    pcv.pcv_set_stream(ctx.ctx, stream.cuda_stream)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    ctx.set_profiling(True)
+    ctx.profile()  # clear
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(pg)
+    torch.cuda.synchronize(dev)
+    launches0 = ctx.stats()["kernel_launches"]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(pg)
+    clk = clocks.stop()
+    ms_local = e0.elapsed_time(e1)
+    prof = ctx.profile()
+    ctx.set_profiling(False)
+    st = ctx.stats()
+    launches = st["kernel_launches"] - launches0
+    ms = max_over_ranks(ms_local, pg, dev)
+    frames_total = F * args.steps * world
+    value = frames_total / (ms / 1e3)
+    msds = F * N_LANDMARKS * args.steps * world / (ms / 1e3)
+    # per-step counts of exact and approximate MSDs (the stats reset with the state each step)
+    exact_msds_step = st["landmark_alignments"]
+    approx_msds_step = st["approx_msds"]
+
+    # roofline of the dominant kernel (by measured share of device time)
+    share = {k: v[0] for k, v in prof.items()}
+    total_ms = sum(share.values())
+    dom = max((k for k in prof if k in FLOPS_PER_UNIT), key=lambda k: prof[k][0])
+    dom_ms, dom_launches = prof[dom]
+    per_launch_ms = dom_ms / dom_launches
+    if dom == "approx_pair":
+        units = approx_msds_step / dom_launches * N_ATOMS
+    elif dom == "exact_pair":
+        units = exact_msds_step / dom_launches * N_ATOMS
+    else:
+        units = F * N_LANDMARKS * N_ATOMS
+    flops = FLOPS_PER_UNIT[dom] * units
+    achieved = flops / (per_launch_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz max clock (derived; FP32 FMA pipe)",
+                "per_launch_ms": per_launch_ms,
+                "flops_per_launch": flops,
+                "kernel_share": {k: round(v / total_ms, 4) for k, v in sorted(share.items(), key=lambda kv: -kv[1])}}
+
+    # end to end through the host entry point: H2D of the frames, evaluation, D2H of s, z, gradients
+    host_fr = torch.from_numpy(fr).pin_memory()
+    hs = torch.empty(F, dtype=torch.float64).pin_memory()
+    hz = torch.empty(F, dtype=torch.float64).pin_memory()
+    hgs = torch.empty_like(host_fr).pin_memory()
+    hgz = torch.empty_like(host_fr).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+    pcv.pcv_reset_close_state(ctx.ctx)
+    pcv.pcv_evaluate_host(ctx.ctx, F, P(host_fr), P(hs), P(hz), P(hgs), P(hgz), None, None)
+    barrier(pg)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        pcv.pcv_reset_close_state(ctx.ctx)
+        pcv.pcv_evaluate_host(ctx.ctx, F, P(host_fr), P(hs), P(hz), P(hgs), P(hgz), None, None)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, pg, dev)
+    e2e = {"value": F * e2e_steps * world / e2e_s, "unit": "frames/s", "h2d_bytes_per_step": int(fr.nbytes),
+           "d2h_bytes_per_step": int(2 * F * 8 + 2 * fr.nbytes), "api": "pcv_evaluate_host"}
+
+    details = {}
+    if not args.no_details and rank == 0:
+        for label, eps, grad in (("exact_fwd_grad", -1.0, True), ("close_eps0.01", 0.01, True),
+                                 ("close_eps0.1", 0.1, True), ("close_eps0.05_fwd_only", 0.05, False)):
+            pcv.pcv_set_close_threshold(ctx.ctx, eps)
+            for _ in range(2):
+                pcv.pcv_reset_close_state(ctx.ctx)
+                pcv.pcv_evaluate(ctx.ctx, F, P(frames), P(s), P(z), P(gs) if grad else None, P(gz) if grad else None,
+                                 None, None)
+            torch.cuda.synchronize(dev)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            n = 3
+            pcv.pcv_set_option(ctx.ctx, pcv.PCV_OPT_PROFILE, 1)
+            pcv.pcv_get_profile(ctx.ctx)
+            a.record(stream)
+            for _ in range(n):
+                pcv.pcv_reset_close_state(ctx.ctx)
+                pcv.pcv_evaluate(ctx.ctx, F, P(frames), P(s), P(z), P(gs) if grad else None, P(gz) if grad else None,
+                                 None, None)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            t = a.elapsed_time(b) / n
+            pr = pcv.pcv_get_profile(ctx.ctx)
+            pcv.pcv_set_option(ctx.ctx, pcv.PCV_OPT_PROFILE, 0)
+            st2 = ctx.stats()
+            details[label] = {"ms_per_step": t, "frames_per_s": F / (t / 1e3),
+                              "refreshes": st2["refreshes_threshold"], "exact_msds": st2["landmark_alignments"],
+                              "approx_msds": st2["approx_msds"],
+                              "kernel_ms": {k: round(v[0] / n, 4) for k, v in pr.items()}}
+        pcv.pcv_set_close_threshold(ctx.ctx, args.eps)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(lm, fr, lam, args.eps, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args),
+            "msds_per_s": msds, "exact_msds_per_step": exact_msds_step, "approx_msds_per_step": approx_msds_step,
+            "refreshes_per_step": st["refreshes_threshold"], "lambda": lam,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk, "details": details,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -73,6 +73,7 @@ typedef struct {
   int64_t refreshes_initial;   /* initial close-structure assignments                     */
   int64_t fp64_rechecks;       /* refresh decisions re-evaluated in full FP64             */
   int64_t host_syncs;          /* host round trips of the refresh search                  */
+  int64_t kernel_launches;     /* CUDA kernels this context launched                      */
 } pcv_stats;
 
 /* Create a context on CUDA device `device`, enqueueing on `cuda_stream` (a cudaStream_t;
@@ -142,7 +143,8 @@ PCV_API pcv_status pcv_evaluate_host(pcv_ctx* ctx, int F, const void* frames, do
 PCV_API pcv_status pcv_combine_grad(pcv_ctx* ctx, int F, const double* g_s, const double* g_z,
                             const void* dsdx, const void* dzdx, void* out);
 
-/* Forget the close structure: the next frame is an initial assignment. Clears counters. */
+/* Forget the close structure: the next frame is an initial assignment.  Clears the
+ * counters except host_syncs and kernel_launches, which count over the context's life. */
 PCV_API pcv_status pcv_reset_close_state(pcv_ctx* ctx);
 
 /* Serialise the close-structure state (y, R_{a_i y}, counters) into host memory.
@@ -167,9 +169,22 @@ enum {
                               ahead of the refresh search (1..6, default 2)           */
   PCV_OPT_CHUNK = 2,       /* minimum frames per speculative x-y alignment chunk       */
   PCV_OPT_EXACT_TILE = 3,  /* tile variant index of the exact pair kernel              */
-  PCV_OPT_APPROX_TILE = 4  /* tile variant index of the approximate pair kernel        */
+  PCV_OPT_APPROX_TILE = 4, /* tile variant index of the approximate pair kernel        */
+  PCV_OPT_PROFILE = 5      /* 1: time every kernel launch with CUDA events on the
+                              context's stream (see pcv_get_profile), 0: off (default)  */
 };
 PCV_API pcv_status pcv_set_option(pcv_ctx* ctx, int key, int64_t value);
+
+/* Kernel timings collected while PCV_OPT_PROFILE is on, per kernel family id
+ * 0..PCV_PROFILE_KERNELS-1 (names from pcv_profile_name): total milliseconds of device time
+ * between events recorded around each launch on the context's stream, and launch counts.
+ * ms and launches are host arrays of n entries (n <= PCV_PROFILE_KERNELS).  Synchronises
+ * the stream, then clears the collected timings. */
+#define PCV_PROFILE_KERNELS 16
+PCV_API pcv_status pcv_get_profile(pcv_ctx* ctx, int n, double* ms, int64_t* launches);
+
+/* Name of kernel family `id` ("" outside 0..PCV_PROFILE_KERNELS-1). */
+PCV_API const char* pcv_profile_name(int id);
 
 /* One-line description of the last error on ctx (never NULL). */
 PCV_API const char* pcv_last_error(const pcv_ctx* ctx);

@@ -954,7 +954,7 @@ void launch_frame_prep(Prec p, int F, const void* frames, const LandmarkDev& L, 
                                                             fi.c64, fi.G);
   else
     frame_prep_f32<<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(F, L.N, (const float*)frames, L.w, fi.c32, fi.c64,
-                                                            fi.G);
+                                                            fi.G); note_launch();
 }
 
 void launch_align_band(Prec p, int F, int W, const void* frames, const LandmarkDev& L, FrameInfo fi,
@@ -970,7 +970,7 @@ void launch_align_band(Prec p, int F, int W, const void* frames, const LandmarkD
   else
     align_kernel<false><<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(0, F, W, 0, 0, 0, L.N, frames, none, fi.c32,
                                                                  fi.c64, fi.G, L.w, L.w64, L.dscale, eps, out.D,
-                                                                 out.q, out.flag, recheck_list, recheck_count);
+                                                                 out.q, out.flag, recheck_list, recheck_count); note_launch();
 }
 
 void launch_align_chunk(Prec p, int t0, int t1, const void* frames, const LandmarkDev& L, FrameInfo fi,
@@ -987,7 +987,7 @@ void launch_align_chunk(Prec p, int t0, int t1, const void* frames, const Landma
     align_kernel<false><<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(1, 0, 1, t0, t1, ref_index, L.N, frames,
                                                                  view_of(prior), fi.c32, fi.c64, fi.G, L.w,
                                                                  L.w64, L.dscale, eps, out.D, out.q, out.flag,
-                                                                 recheck_list, recheck_count);
+                                                                 recheck_list, recheck_count); note_launch();
 }
 
 void launch_recheck(Prec p, int max_entries, const int* list, const int* count, int W, const void* frames,
@@ -997,35 +997,35 @@ void launch_recheck(Prec p, int max_entries, const int* list, const int* count, 
   const unsigned blocks = blocks_for((size_t)max_entries, WARPS_PER_BLOCK);
   recheck_kernel<<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(list, count, W, L.N, (const float*)frames,
                                                           view_of(prior), chunk_ref, L.w64, L.dscale, eps, band.D,
-                                                          band.flag, chunk.D, chunk.flag, n_rechecks);
+                                                          band.flag, chunk.D, chunk.flag, n_rechecks); note_launch();
 }
 
-void launch_set_int(int* p, int v, cudaStream_t st) { set_int_kernel<<<1, 1, 0, st>>>(p, v); }
+void launch_set_int(int* p, int v, cudaStream_t st) { set_int_kernel<<<1, 1, 0, st>>>(p, v); note_launch(); }
 
 void launch_first_exceed(int t0, int t1, const uint8_t* flag, int* first, cudaStream_t st) {
-  set_int_kernel<<<1, 1, 0, st>>>(first, t1);
+  set_int_kernel<<<1, 1, 0, st>>>(first, t1); note_launch();
   if (t1 <= t0) return;
-  first_exceed_kernel<<<blocks_for((size_t)(t1 - t0), 256), 256, 0, st>>>(t0, t1, flag, first);
+  first_exceed_kernel<<<blocks_for((size_t)(t1 - t0), 256), 256, 0, st>>>(t0, t1, flag, first); note_launch();
 }
 
 void launch_band_scan(int F, int W, int t0, int o_init, const AlignOut band, FrameRec rec, ScanResult* res,
                       cudaStream_t st) {
-  band_scan_kernel<<<1, SCAN_THREADS, 0, st>>>(F, W, t0, o_init, band.D, band.q, band.flag, rec, res);
+  band_scan_kernel<<<1, SCAN_THREADS, 0, st>>>(F, W, t0, o_init, band.D, band.q, band.flag, rec, res); note_launch();
 }
 
 void launch_chunk_records(int t0, int t_end, int t1, int ref, const AlignOut chunk, FrameRec rec,
                           cudaStream_t st) {
   const int n = (t_end < t1 ? t_end + 1 : t1) - t0;
   if (n <= 0) return;
-  chunk_records_kernel<<<blocks_for((size_t)n, 256), 256, 0, st>>>(t0, t_end, t1, ref, chunk.D, chunk.q, rec);
+  chunk_records_kernel<<<blocks_for((size_t)n, 256), 256, 0, st>>>(t0, t_end, t1, ref, chunk.D, chunk.q, rec); note_launch();
 }
 
-void launch_initial_record(FrameRec rec, cudaStream_t st) { initial_record_kernel<<<1, 1, 0, st>>>(rec); }
+void launch_initial_record(FrameRec rec, cudaStream_t st) { initial_record_kernel<<<1, 1, 0, st>>>(rec); note_launch(); }
 
 void launch_compact(int F, const FrameRec rec, int* refresh_list, int* refresh_count, int* seg_of_frame,
                     int* approx_list, int* approx_count, int* approx_seg, int prior_seg, cudaStream_t st) {
   compact_kernel<<<1, SCAN_THREADS, 0, st>>>(F, rec.flag, refresh_list, refresh_count, seg_of_frame, approx_list,
-                                             approx_count, approx_seg, prior_seg);
+                                             approx_count, approx_seg, prior_seg); note_launch();
 }
 
 void launch_finalize(Prec p, int F, int M, const void* D, const double* q, double lambda, double* s, double* z,
@@ -1036,7 +1036,7 @@ void launch_finalize(Prec p, int F, int M, const void* D, const double* q, doubl
     finalize_f64<<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(F, M, (const double*)D, q, lambda, s, z, mstat64,
                                                           msd_out);
   else
-    finalize_f32<<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(F, M, (const float*)D, q, lambda, s, z, mstat, msd_out);
+    finalize_f32<<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(F, M, (const float*)D, q, lambda, s, z, mstat, msd_out); note_launch();
 }
 
 void launch_adjoint_beta(Prec p, int F, const LandmarkDev& L, const void* D, const float* mstat, const double* s,
@@ -1048,17 +1048,17 @@ void launch_adjoint_beta(Prec p, int F, const LandmarkDev& L, const void* D, con
     case P_F64:
       adjoint_beta_kernel<double, double, double><<<grid, AB_THREADS, 0, st>>>(
           F, L.M, L.N, (const double*)L.coords, L.q, (const double*)D, (const double*)(const void*)mstat, s, lambda,
-          (const double*)Rpair, (const double*)Bseg, seg_of_frame, (double*)gs, (double*)gz);
+          (const double*)Rpair, (const double*)Bseg, seg_of_frame, (double*)gs, (double*)gz); note_launch();
       break;
     case P_F32:
       adjoint_beta_kernel<float, float, float><<<grid, AB_THREADS, 0, st>>>(
           F, L.M, L.N, (const float*)L.coords, L.q, (const float*)D, mstat, s, lambda, (const float*)Rpair,
-          (const float*)Bseg, seg_of_frame, (float*)gs, (float*)gz);
+          (const float*)Bseg, seg_of_frame, (float*)gs, (float*)gz); note_launch();
       break;
     case P_F16:
       adjoint_beta_kernel<float, __half, float><<<grid, AB_THREADS, 0, st>>>(
           F, L.M, L.N, (const __half*)L.coords, L.q, (const float*)D, mstat, s, lambda, (const float*)Rpair,
-          (const float*)Bseg, seg_of_frame, (float*)gs, (float*)gz);
+          (const float*)Bseg, seg_of_frame, (float*)gs, (float*)gz); note_launch();
       break;
   }
 }
@@ -1076,7 +1076,7 @@ void launch_adjoint_finish(Prec p, int F, const void* frames, const LandmarkDev&
   else
     adjoint_finish_kernel<float, float><<<F, 128, 0, st>>>(
         F, L.M, L.N, (const float*)frames, fi.c32, fi.c64, L.w, L.w64, L.A, L.q, L.dscale, (const float*)D, mstat,
-        nullptr, s, lambda, (const float*)Bseg, seg_of_frame, rec, view_of(prior), (float*)gs, (float*)gz, status);
+        nullptr, s, lambda, (const float*)Bseg, seg_of_frame, rec, view_of(prior), (float*)gs, (float*)gz, status); note_launch();
 }
 
 void launch_combine_grad(Prec p, int F, int N3, const double* g_s, const double* g_z, const void* gs,
@@ -1088,12 +1088,12 @@ void launch_combine_grad(Prec p, int F, int N3, const double* g_s, const double*
                                                                      (const double*)gz, (double*)out);
   else
     combine_grad_kernel<float><<<blocks_for(n, 256), 256, 0, st>>>(n, N3, g_s, g_z, (const float*)gs,
-                                                                    (const float*)gz, (float*)out);
+                                                                    (const float*)gz, (float*)out); note_launch();
 }
 
 void launch_fill_u8(uint8_t* p, uint8_t v, size_t n, cudaStream_t st) {
   if (n == 0) return;
-  fill_u8_kernel<<<blocks_for(n, 256), 256, 0, st>>>(p, v, n);
+  fill_u8_kernel<<<blocks_for(n, 256), 256, 0, st>>>(p, v, n); note_launch();
 }
 
 }  // namespace pcv

@@ -1,13 +1,12 @@
 // k_pair.cu -- frame x landmark pair kernels (the O(F M N) part of the path).
 //
-// exact_pair_kernel: Algorithm 1 (and the reassignment branch of Algorithm 2) for a tile
+// exact pair kernels: Algorithm 1 (and the reassignment branch of Algorithm 2) for a tile
 //   of TF frames x TM landmarks.  The 3x3 correlation H_fi[b][c] = sum_j wk_j a_ijb x_fjc
 //   is a dense (3 TM x N)(N x 3 TF) contraction; each thread owns 2 frames x 2 landmarks
-//   (36 sums), atoms are streamed through shared memory in chunks of KC.  FP32 products
-//   are summed per chunk and the chunk sums are added into an error-free (hi, lo) pair,
-//   so the correlation keeps ~FP64 accuracy with FP32 arithmetic.  Each pair then takes
-//   the FP64 quaternion eigen-solve (Section 3, Kearsley / Coutsias) and the FP64
-//   assembly D = G_x + G_a - 2 lambda_max of Eq. (dist).
+//   (36 sums), atoms are streamed through shared memory in chunks of KC.  The quaternion
+//   eigen-solve (Section 3, Kearsley / Coutsias) gives R per pair.  FP32 modes then
+//   evaluate Eq. (dist) directly in a second pass; FP64 mode assembles
+//   D = G_x + G_a - 2 lambda_max.
 // approx_pair_kernel: Eq. (close_dist) for frames of Algorithm 2's "else" branch.  With
 //   x' = R_{xy}^T x and b_i = R_{a_i y} a_i the approximate distance is
 //   D~ = sum_j w_j |x'_j - b_ij|^2, evaluated directly (positive terms, no cancellation);
@@ -29,27 +28,6 @@ template <>
 __device__ __forceinline__ float load_as<float, __half>(const __half* p) {
   return __half2float(*p);
 }
-
-// compensated accumulator: FP32 partial + error-free (hi, lo) total; plain in FP64
-template <typename ST>
-struct Acc;
-template <>
-struct Acc<float> {
-  float p, hi, lo;
-  __device__ __forceinline__ void zero() { p = hi = lo = 0.0f; }
-  __device__ __forceinline__ void flush() {
-    two_sum_acc(hi, lo, p);
-    p = 0.0f;
-  }
-  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
-};
-template <>
-struct Acc<double> {
-  double p;
-  __device__ __forceinline__ void zero() { p = 0.0; }
-  __device__ __forceinline__ void flush() {}
-  __device__ __forceinline__ double value() const { return p; }
-};
 
 template <typename ST>
 __device__ __forceinline__ void load2(const ST* p, ST& a, ST& b);
@@ -105,30 +83,63 @@ __device__ __forceinline__ void frame_centre<double>(const float4*, const double
 // ---------------------------------------------------------------------------------------
 constexpr int EX_TF = 16, EX_TM = 32, EX_THREADS = 128;
 
-template <typename FT, typename LT, typename ST>
-__global__ void __launch_bounds__(EX_THREADS, 3)
-exact_pair_kernel(int rows, const int* __restrict__ row_frame, const int* __restrict__ rows_dev,
-                  const FT* __restrict__ frames, const float4* __restrict__ c32,
-                  const double4* __restrict__ c64, const double* __restrict__ fG,
-                  const LT* __restrict__ lm, const double* __restrict__ lG,
-                  const float* __restrict__ wts, int M, int N, double dscale, ST* __restrict__ Dout,
-                  ST* __restrict__ Rout, unsigned* __restrict__ status) {
-  constexpr int TF = EX_TF, TM = EX_TM;
-  constexpr int KC = sizeof(ST) == 8 ? 16 : 32;
-  constexpr int PF = TF + 2, PM = TM + 2;
-  __shared__ __align__(16) ST Xs[KC * 3][PF];
-  __shared__ __align__(16) ST As[KC * 3][PM];
-  __shared__ int s_frame[TF];
-  __shared__ ST s_c[TF][3];
-
-  if (rows_dev) rows = *rows_dev;
-  const int row0 = blockIdx.y * TF;
-  if (row0 >= rows) return;
-  const int i0 = blockIdx.x * TM;
+// Stage one chunk of KC atoms of the tile: frames centred (weight mode 1: x w_j,
+// 2: x sqrt(w_j)), landmarks (mode 2: a sqrt(w_j)).  Layout [jj*3 + c][row].
+template <typename FT, typename LT, typename ST, int TF, int TM, int KC, int PF, int PM>
+__device__ __forceinline__ void stage_exact(int j0, int N, int M, int i0, const FT* __restrict__ frames,
+                                            const LT* __restrict__ lm, const float* __restrict__ wts,
+                                            int wmode, const int* s_frame, const ST (*s_c)[3],
+                                            ST (*Xs)[PF], ST (*As)[PM]) {
   const int tid = threadIdx.x;
-  const int tx = tid & 15;  // landmark pair: i0 + 2 tx + {0,1}
-  const int ty = tid >> 4;  // frame pair: rows 2 ty + {0,1}
-  if (tid < TF) {
+  for (int e = tid; e < TF * KC; e += EX_THREADS) {
+    const int ff = e / KC, jj = e - ff * KC;
+    const int j = j0 + jj;
+    const int f = s_frame[ff];
+    ST v0 = 0, v1 = 0, v2 = 0;
+    if (f >= 0 && j < N) {
+      const FT* src = frames + ((size_t)f * N + j) * 3;
+      v0 = (ST)src[0] - s_c[ff][0];
+      v1 = (ST)src[1] - s_c[ff][1];
+      v2 = (ST)src[2] - s_c[ff][2];
+      if (wts && wmode) {
+        const ST wj = wmode == 1 ? (ST)wts[j] : (ST)sqrt((double)wts[j]);
+        v0 *= wj;
+        v1 *= wj;
+        v2 *= wj;
+      }
+    }
+    Xs[jj * 3 + 0][ff] = v0;
+    Xs[jj * 3 + 1][ff] = v1;
+    Xs[jj * 3 + 2][ff] = v2;
+  }
+  for (int e = tid; e < TM * KC; e += EX_THREADS) {
+    const int ll = e / KC, jj = e - ll * KC;
+    const int j = j0 + jj, i = i0 + ll;
+    ST v0 = 0, v1 = 0, v2 = 0;
+    if (i < M && j < N) {
+      const LT* src = lm + ((size_t)i * N + j) * 3;
+      v0 = load_as<ST>(src);
+      v1 = load_as<ST>(src + 1);
+      v2 = load_as<ST>(src + 2);
+      if (wts && wmode == 2) {
+        const ST sw = (ST)sqrt((double)wts[j]);
+        v0 *= sw;
+        v1 *= sw;
+        v2 *= sw;
+      }
+    }
+    As[jj * 3 + 0][ll] = v0;
+    As[jj * 3 + 1][ll] = v1;
+    As[jj * 3 + 2][ll] = v2;
+  }
+}
+
+template <typename FT, typename ST>
+__device__ __forceinline__ void load_tile_frames(int rows, const int* __restrict__ row_frame, int row0,
+                                                 const float4* __restrict__ c32, const double4* __restrict__ c64,
+                                                 int* s_frame, ST (*s_c)[3]) {
+  const int tid = threadIdx.x;
+  if (tid < EX_TF) {
     const int r = row0 + tid;
     int f = -1;
     if (r < rows) f = row_frame ? row_frame[r] : r;
@@ -139,61 +150,54 @@ exact_pair_kernel(int rows, const int* __restrict__ row_frame, const int* __rest
     s_c[tid][1] = c[1];
     s_c[tid][2] = c[2];
   }
+}
+
+// FP32 modes: two passes over the atoms of a 16 x 32 tile.
+//  pass 1: H = sum_j w_j a_j x_j^T in FP32 (2 frames x 2 landmarks x 9 sums per thread);
+//          per pair, the top eigenvector of the quaternion matrix in FP32 -> R_{a x};
+//  pass 2: D = sum_j w_j |x_j - R a_j|^2 directly in FP32 (Eq. dist): positive terms, no
+//          cancellation, stationary in R -- so D is accurate to ~1e-7 relative although
+//          every operation is FP32.
+template <typename LT>
+__global__ void __launch_bounds__(EX_THREADS, 4)
+exact_pair_f32(int rows, const int* __restrict__ row_frame, const float* __restrict__ frames,
+               const float4* __restrict__ c32, const double* __restrict__ fG, const LT* __restrict__ lm,
+               const double* __restrict__ lG, const float* __restrict__ wts, int M, int N, double dscale,
+               float* __restrict__ Dout, float* __restrict__ Rout, unsigned* __restrict__ status) {
+  constexpr int TF = EX_TF, TM = EX_TM, KC = 32;
+  constexpr int PF = TF + 2, PM = TM + 2;
+  __shared__ __align__(16) float Xs[KC * 3][PF];
+  __shared__ __align__(16) float As[KC * 3][PM];
+  __shared__ int s_frame[TF];
+  __shared__ float s_c[TF][3];
+
+  const int row0 = blockIdx.y * TF;
+  if (row0 >= rows) return;
+  const int i0 = blockIdx.x * TM;
+  const int tid = threadIdx.x;
+  const int tx = tid & 15;  // landmark pair: i0 + 2 tx + {0,1}
+  const int ty = tid >> 4;  // frame pair: rows 2 ty + {0,1}
+  load_tile_frames<float, float>(rows, row_frame, row0, c32, nullptr, s_frame, s_c);
   __syncthreads();
 
-  Acc<ST> acc[2][2][9];
+  float h[2][2][9];
 #pragma unroll
   for (int u = 0; u < 2; ++u)
 #pragma unroll
     for (int v = 0; v < 2; ++v)
 #pragma unroll
-      for (int e = 0; e < 9; ++e) acc[u][v][e].zero();
+      for (int e = 0; e < 9; ++e) h[u][v][e] = 0.0f;
 
   for (int j0 = 0; j0 < N; j0 += KC) {
-    // frames: one atom (3 coordinates) per work item, centred (and weighted)
-    for (int e = tid; e < TF * KC; e += EX_THREADS) {
-      const int ff = e / KC, jj = e - ff * KC;
-      const int j = j0 + jj;
-      const int f = s_frame[ff];
-      ST v0 = 0, v1 = 0, v2 = 0;
-      if (f >= 0 && j < N) {
-        const FT* src = frames + ((size_t)f * N + j) * 3;
-        v0 = (ST)src[0] - s_c[ff][0];
-        v1 = (ST)src[1] - s_c[ff][1];
-        v2 = (ST)src[2] - s_c[ff][2];
-        if (wts) {
-          const ST wj = (ST)wts[j];
-          v0 *= wj;
-          v1 *= wj;
-          v2 *= wj;
-        }
-      }
-      Xs[jj * 3 + 0][ff] = v0;
-      Xs[jj * 3 + 1][ff] = v1;
-      Xs[jj * 3 + 2][ff] = v2;
-    }
-    for (int e = tid; e < TM * KC; e += EX_THREADS) {
-      const int ll = e / KC, jj = e - ll * KC;
-      const int j = j0 + jj, i = i0 + ll;
-      ST v0 = 0, v1 = 0, v2 = 0;
-      if (i < M && j < N) {
-        const LT* src = lm + ((size_t)i * N + j) * 3;
-        v0 = load_as<ST>(src);
-        v1 = load_as<ST>(src + 1);
-        v2 = load_as<ST>(src + 2);
-      }
-      As[jj * 3 + 0][ll] = v0;
-      As[jj * 3 + 1][ll] = v1;
-      As[jj * 3 + 2][ll] = v2;
-    }
+    stage_exact<float, LT, float, TF, TM, KC, PF, PM>(j0, N, M, i0, frames, lm, wts, 1, s_frame, s_c, Xs, As);
     __syncthreads();
 #pragma unroll 4
     for (int jj = 0; jj < KC; ++jj) {
-      ST x[2][3], a[2][3];
+      float x[2][3], a[2][3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        load2<ST>(&Xs[jj * 3 + c][ty * 2], x[0][c], x[1][c]);
-        load2<ST>(&As[jj * 3 + c][tx * 2], a[0][c], a[1][c]);
+        load2<float>(&Xs[jj * 3 + c][ty * 2], x[0][c], x[1][c]);
+        load2<float>(&As[jj * 3 + c][tx * 2], a[0][c], a[1][c]);
       }
 #pragma unroll
       for (int u = 0; u < 2; ++u)
@@ -202,52 +206,154 @@ exact_pair_kernel(int rows, const int* __restrict__ row_frame, const int* __rest
 #pragma unroll
           for (int b = 0; b < 3; ++b)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) acc[u][v][3 * b + c].p = fma(a[v][b], x[u][c], acc[u][v][3 * b + c].p);
+            for (int c = 0; c < 3; ++c) h[u][v][3 * b + c] = fmaf(a[v][b], x[u][c], h[u][v][3 * b + c]);
+    }
+    __syncthreads();
+  }
+
+  // rotations of the four pairs
+  float R[2][2][9];
+  bool all_ok = true;
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int f = s_frame[ty * 2 + u];
+      const int i = i0 + tx * 2 + v;
+      float q[4] = {1.0f, 0.0f, 0.0f, 0.0f};
+      if (f >= 0 && i < M) {
+        const float ub = (float)(0.5 * (fG[f] + lG[i])) * 1.00001f + 1e-30f;
+        all_ok &= top_quat_f32(h[u][v], ub, q);
+      }
+      quat_to_rot(q, R[u][v]);
+    }
+
+  // per-chunk FP32 partials, added into an error-free (hi, lo) total after each chunk
+  float acc[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+  float thi[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}}, tlo[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+  for (int j0 = 0; j0 < N; j0 += KC) {
+    stage_exact<float, LT, float, TF, TM, KC, PF, PM>(j0, N, M, i0, frames, lm, wts, 2, s_frame, s_c, Xs, As);
+    __syncthreads();
+#pragma unroll 4
+    for (int jj = 0; jj < KC; ++jj) {
+      float x[2][3], a[2][3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        load2<float>(&Xs[jj * 3 + c][ty * 2], x[0][c], x[1][c]);
+        load2<float>(&As[jj * 3 + c][tx * 2], a[0][c], a[1][c]);
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+          const float* Rr = R[u][v];
+          const float d0 = x[u][0] - fmaf(Rr[0], a[v][0], fmaf(Rr[1], a[v][1], Rr[2] * a[v][2]));
+          const float d1 = x[u][1] - fmaf(Rr[3], a[v][0], fmaf(Rr[4], a[v][1], Rr[5] * a[v][2]));
+          const float d2 = x[u][2] - fmaf(Rr[6], a[v][0], fmaf(Rr[7], a[v][1], Rr[8] * a[v][2]));
+          acc[u][v] = fmaf(d0, d0, fmaf(d1, d1, fmaf(d2, d2, acc[u][v])));
+        }
     }
 #pragma unroll
     for (int u = 0; u < 2; ++u)
 #pragma unroll
-      for (int v = 0; v < 2; ++v)
-#pragma unroll
-        for (int e = 0; e < 9; ++e) acc[u][v][e].flush();
+      for (int v = 0; v < 2; ++v) {
+        two_sum_acc(thi[u][v], tlo[u][v], acc[u][v]);
+        acc[u][v] = 0.0f;
+      }
     __syncthreads();
   }
 
-  // epilogue: FP64 eigen-solve and assembly per pair
 #pragma unroll
   for (int u = 0; u < 2; ++u)
 #pragma unroll
     for (int v = 0; v < 2; ++v) {
       const int r = row0 + ty * 2 + u;
-      const int f = (ty * 2 + u) < TF ? s_frame[ty * 2 + u] : -1;
+      const int f = s_frame[ty * 2 + u];
       const int i = i0 + tx * 2 + v;
       if (f < 0 || i >= M) continue;
-      double H[9];
+      Dout[(size_t)f * M + i] = (float)(pair_to_double(thi[u][v], tlo[u][v]) * dscale);
+      if (Rout) {
+        float* dst = Rout + ((size_t)r * M + i) * 9;
 #pragma unroll
-      for (int e = 0; e < 9; ++e) H[e] = acc[u][v][e].value();
+        for (int e = 0; e < 9; ++e) dst[e] = R[u][v][e];
+      }
+    }
+  if (!all_ok) atomicOr(status, STATUS_NOCONV);
+}
+
+// FP64 mode: one pass, FP64 correlation, FP64 eigenvalue and D = G_x + G_a - 2 lambda_max
+// (FP64 sums carry ~1e-16 relative error, far below the cancellation's needs).
+__global__ void __launch_bounds__(EX_THREADS, 3)
+exact_pair_f64(int rows, const int* __restrict__ row_frame, const double* __restrict__ frames,
+               const double4* __restrict__ c64, const double* __restrict__ fG, const double* __restrict__ lm,
+               const double* __restrict__ lG, const float* __restrict__ wts, int M, int N, double dscale,
+               double* __restrict__ Dout, double* __restrict__ Rout, unsigned* __restrict__ status) {
+  constexpr int TF = EX_TF, TM = EX_TM, KC = 16;
+  constexpr int PF = TF + 2, PM = TM + 2;
+  __shared__ __align__(16) double Xs[KC * 3][PF];
+  __shared__ __align__(16) double As[KC * 3][PM];
+  __shared__ int s_frame[TF];
+  __shared__ double s_c[TF][3];
+
+  const int row0 = blockIdx.y * TF;
+  if (row0 >= rows) return;
+  const int i0 = blockIdx.x * TM;
+  const int tid = threadIdx.x;
+  const int tx = tid & 15;
+  const int ty = tid >> 4;
+  load_tile_frames<double, double>(rows, row_frame, row0, nullptr, c64, s_frame, s_c);
+  __syncthreads();
+  double h[2][2][9];
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v)
+#pragma unroll
+      for (int e = 0; e < 9; ++e) h[u][v][e] = 0.0;
+  for (int j0 = 0; j0 < N; j0 += KC) {
+    stage_exact<double, double, double, TF, TM, KC, PF, PM>(j0, N, M, i0, frames, lm, wts, 1, s_frame, s_c, Xs, As);
+    __syncthreads();
+#pragma unroll 4
+    for (int jj = 0; jj < KC; ++jj) {
+      double x[2][3], a[2][3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        load2<double>(&Xs[jj * 3 + c][ty * 2], x[0][c], x[1][c]);
+        load2<double>(&As[jj * 3 + c][tx * 2], a[0][c], a[1][c]);
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v)
+#pragma unroll
+          for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) h[u][v][3 * b + c] = fma(a[v][b], x[u][c], h[u][v][3 * b + c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int r = row0 + ty * 2 + u;
+      const int f = s_frame[ty * 2 + u];
+      const int i = i0 + tx * 2 + v;
+      if (f < 0 || i >= M) continue;
       const double Gx = fG[f], Ga = lG[i];
       bool ok = true;
-      const double lam = lambda_max_newton(H, 0.5 * (Gx + Ga), &ok);
+      const double lam = lambda_max_newton(h[u][v], 0.5 * (Gx + Ga), &ok);
       double D = (Gx + Ga - 2.0 * lam) * dscale;
       if (D < 0.0) D = 0.0;
-      Dout[(size_t)f * M + i] = (ST)D;
+      Dout[(size_t)f * M + i] = D;
       if (Rout) {
-        double K[16];
-        quat_matrix(H, K);
-        ST* dst = Rout + ((size_t)r * M + i) * 9;
-        if (sizeof(ST) == 8) {
-          double q[4], R[9];
-          adj_eigvec_f64(K, lam, q);
-          quat_to_rot(q, R);
+        double K[16], q[4], Rm[9];
+        quat_matrix(h[u][v], K);
+        adj_eigvec_f64(K, lam, q);
+        quat_to_rot(q, Rm);
+        double* dst = Rout + ((size_t)r * M + i) * 9;
 #pragma unroll
-          for (int e = 0; e < 9; ++e) dst[e] = (ST)R[e];
-        } else {
-          float q[4], R[9];
-          adj_eigvec(K, lam, q);
-          quat_to_rot(q, R);
-#pragma unroll
-          for (int e = 0; e < 9; ++e) dst[e] = (ST)R[e];
-        }
+        for (int e = 0; e < 9; ++e) dst[e] = Rm[e];
       }
       if (!ok) atomicOr(status, STATUS_NOCONV);
     }
@@ -329,11 +435,11 @@ approx_pair_kernel(const int* __restrict__ alist, const int* __restrict__ aseg,
       const int i = i0 + ll;
       s_B[ll][c] = (i < M) ? Bseg[((size_t)seg * M + i) * 9 + c] : (ST)0;
     }
-    ST acc[4][4];
+    ST acc[4][4], thi[4][4], tlo[4][4];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) acc[u][v] = 0;
+      for (int v = 0; v < 4; ++v) acc[u][v] = thi[u][v] = tlo[u][v] = 0;
     __syncthreads();
 
     for (int j0 = 0; j0 < N; j0 += KC) {
@@ -405,6 +511,21 @@ approx_pair_kernel(const int* __restrict__ alist, const int* __restrict__ aseg,
             acc[u][v] = t;
           }
       }
+      // chunk partials into an error-free (hi, lo) total
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          if (sizeof(ST) == 4) {
+            float h = (float)thi[u][v], l = (float)tlo[u][v];
+            two_sum_acc(h, l, (float)acc[u][v]);
+            thi[u][v] = (ST)h;
+            tlo[u][v] = (ST)l;
+          } else {
+            thi[u][v] += acc[u][v];
+          }
+          acc[u][v] = 0;
+        }
       __syncthreads();
     }
 #pragma unroll
@@ -415,7 +536,7 @@ approx_pair_kernel(const int* __restrict__ alist, const int* __restrict__ aseg,
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         const int i = i0 + tx * 4 + v;
-        if (i < M) Dout[(size_t)f * M + i] = (ST)((double)acc[u][v] * dscale);
+        if (i < M) Dout[(size_t)f * M + i] = (ST)(((double)thi[u][v] + (double)tlo[u][v]) * dscale);
       }
     }
     k = kend;
@@ -429,23 +550,24 @@ approx_pair_kernel(const int* __restrict__ alist, const int* __restrict__ aseg,
 void launch_exact_pairs(Prec p, int rows, const int* row_frame, const int* rows_dev, const void* frames,
                         const LandmarkDev& L, FrameInfo fi, void* D, void* Rout, unsigned* status,
                         cudaStream_t st) {
+  (void)rows_dev;
   if (rows <= 0) return;
   dim3 grid((L.M + EX_TM - 1) / EX_TM, (rows + EX_TF - 1) / EX_TF);
   switch (p) {
     case P_F64:
-      exact_pair_kernel<double, double, double><<<grid, EX_THREADS, 0, st>>>(
-          rows, row_frame, rows_dev, (const double*)frames, fi.c32, fi.c64, fi.G, (const double*)L.coords,
-          L.G, L.w, L.M, L.N, L.dscale, (double*)D, (double*)Rout, status);
+      exact_pair_f64<<<grid, EX_THREADS, 0, st>>>(rows, row_frame, (const double*)frames, fi.c64, fi.G,
+                                                  (const double*)L.coords, L.G, L.w, L.M, L.N, L.dscale,
+                                                  (double*)D, (double*)Rout, status); note_launch();
       break;
     case P_F32:
-      exact_pair_kernel<float, float, float><<<grid, EX_THREADS, 0, st>>>(
-          rows, row_frame, rows_dev, (const float*)frames, fi.c32, fi.c64, fi.G, (const float*)L.coords, L.G,
-          L.w, L.M, L.N, L.dscale, (float*)D, (float*)Rout, status);
+      exact_pair_f32<float><<<grid, EX_THREADS, 0, st>>>(rows, row_frame, (const float*)frames, fi.c32, fi.G,
+                                                         (const float*)L.coords, L.G, L.w, L.M, L.N, L.dscale,
+                                                         (float*)D, (float*)Rout, status); note_launch();
       break;
     case P_F16:
-      exact_pair_kernel<float, __half, float><<<grid, EX_THREADS, 0, st>>>(
-          rows, row_frame, rows_dev, (const float*)frames, fi.c32, fi.c64, fi.G, (const __half*)L.coords, L.G,
-          L.w, L.M, L.N, L.dscale, (float*)D, (float*)Rout, status);
+      exact_pair_f32<__half><<<grid, EX_THREADS, 0, st>>>(rows, row_frame, (const float*)frames, fi.c32, fi.G,
+                                                          (const __half*)L.coords, L.G, L.w, L.M, L.N, L.dscale,
+                                                          (float*)D, (float*)Rout, status); note_launch();
       break;
   }
 }
@@ -459,17 +581,17 @@ void launch_approx_pairs(Prec p, int max_rows, const int* approx_list, const int
     case P_F64:
       approx_pair_kernel<double, double, double><<<grid, AP_THREADS, 0, st>>>(
           approx_list, approx_seg, count, (const double*)frames, fi.c32, fi.c64, qxy,
-          (const double*)L.coords, (const double*)Bseg, L.w, L.M, L.N, L.dscale, (double*)D);
+          (const double*)L.coords, (const double*)Bseg, L.w, L.M, L.N, L.dscale, (double*)D); note_launch();
       break;
     case P_F32:
       approx_pair_kernel<float, float, float><<<grid, AP_THREADS, 0, st>>>(
           approx_list, approx_seg, count, (const float*)frames, fi.c32, fi.c64, qxy, (const float*)L.coords,
-          (const float*)Bseg, L.w, L.M, L.N, L.dscale, (float*)D);
+          (const float*)Bseg, L.w, L.M, L.N, L.dscale, (float*)D); note_launch();
       break;
     case P_F16:
       approx_pair_kernel<float, __half, float><<<grid, AP_THREADS, 0, st>>>(
           approx_list, approx_seg, count, (const float*)frames, fi.c32, fi.c64, qxy, (const __half*)L.coords,
-          (const float*)Bseg, L.w, L.M, L.N, L.dscale, (float*)D);
+          (const float*)Bseg, L.w, L.M, L.N, L.dscale, (float*)D); note_launch();
       break;
   }
 }

@@ -50,7 +50,27 @@ __global__ void small_tail_kernel(Small* sm, const int* refresh_list, const floa
   }
 }
 
+thread_local int64_t t_launches = 0;
+
+// kernel families timed by the profiler
+enum KernelId {
+  K_PREP = 0, K_BAND, K_RECHECK, K_SCAN, K_CHUNK, K_FIRST, K_RECORDS, K_COMPACT, K_EXACT, K_APPROX,
+  K_FINAL, K_ADJ_BETA, K_ADJ_FINISH, K_COMBINE, K_MISC, K_COUNT
+};
+const char* const kKernelNames[PCV_PROFILE_KERNELS] = {
+    "frame_prep", "align_band", "recheck_fp64", "band_scan", "align_chunk", "first_exceed", "records",
+    "compact", "exact_pair", "approx_pair", "finalize", "adjoint_beta", "adjoint_finish", "combine_grad", "misc", ""};
+
+struct ProfEvent {
+  int id;
+  cudaEvent_t a, b;
+};
+
 }  // namespace
+
+namespace pcv {
+void note_launch(int n) { t_launches += n; }
+}  // namespace pcv
 
 struct pcv_ctx {
   int device = 0;
@@ -81,7 +101,48 @@ struct pcv_ctx {
   Small* small_host = nullptr;
   pcv_stats stats{};
   std::string err;
+  // profiler
+  bool prof_on = false;
+  std::vector<ProfEvent> prof_pending;
+  std::vector<cudaEvent_t> prof_pool;
+  double prof_ms[PCV_PROFILE_KERNELS] = {0};
+  int64_t prof_launches[PCV_PROFILE_KERNELS] = {0};
 };
+
+namespace {
+cudaEvent_t prof_event(pcv_ctx* c) {
+  if (!c->prof_pool.empty()) {
+    cudaEvent_t e = c->prof_pool.back();
+    c->prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// times the launches issued during its lifetime when the profiler is on
+struct ProfScope {
+  pcv_ctx* c;
+  ProfEvent ev;
+  ProfScope(pcv_ctx* ctx, int id) : c(ctx) {
+    ev.id = id;
+    ev.a = ev.b = nullptr;
+    if (c->prof_on) {
+      ev.a = prof_event(c);
+      ev.b = prof_event(c);
+      cudaEventRecord(ev.a, c->stream);
+    }
+  }
+  ~ProfScope() {
+    if (c->prof_on && ev.a) {
+      cudaEventRecord(ev.b, c->stream);
+      c->prof_pending.push_back(ev);
+    }
+  }
+};
+#define PROF(ctx, id) ProfScope prof_scope_##id(ctx, id)
+}  // namespace
 
 namespace {
 
@@ -210,6 +271,11 @@ pcv_status pcv_destroy(pcv_ctx* c) {
                     &c->Dbuf, &c->Rpair, &c->Bseg, &c->mstat, &c->status, &c->nrecheck, &c->small, &c->h_frames,
                     &c->h_s, &c->h_z, &c->h_gs, &c->h_gz, &c->h_msd, &c->h_ref};
   for (DevBuf* b : bufs) release(*b);
+  for (const ProfEvent& e : c->prof_pending) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   if (c->small_host) cudaFreeHost(c->small_host);
   delete c;
   return PCV_OK;
@@ -249,6 +315,9 @@ pcv_status pcv_set_option(pcv_ctx* c, int key, int64_t value) {
       if (value < 1 || value > (1 << 30)) return fail(c, PCV_EINVAL, "chunk must be in 1..2^30");
       c->min_chunk = (int)value;
       return PCV_OK;
+    case PCV_OPT_PROFILE:
+      c->prof_on = value != 0;
+      return PCV_OK;
     case PCV_OPT_EXACT_TILE:
     case PCV_OPT_APPROX_TILE:
       if (value != 0) return fail(c, PCV_EINVAL, "only tile variant 0 is built");
@@ -262,7 +331,10 @@ pcv_status pcv_reset_close_state(pcv_ctx* c) {
   if (!c) return fail(nullptr, PCV_EINVAL, "NULL context");
   c->has_y = false;
   c->gap_estimate = 0.0;
+  const int64_t syncs = c->stats.host_syncs, launches = c->stats.kernel_launches;
   c->stats = pcv_stats{};
+  c->stats.host_syncs = syncs;  // cumulative over the context's lifetime
+  c->stats.kernel_launches = launches;
   cudaSetDevice(c->device);
   CUDA_TRY(c, cudaMemsetAsync(c->nrecheck.p, 0, 16, c->stream));
   return PCV_OK;
@@ -431,10 +503,17 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
   int* rc = &sm->recheck_count;
   const bool had_prior = c->has_y;
 
-  launch_frame_prep(c->prec, F, frames, L, fi, st);
+  {
+    PROF(c, K_PREP);
+    launch_frame_prep(c->prec, F, frames, L, fi, st);
+  }
   launch_set_int(rc, 0, st);
   if (F > 1) {
-    launch_align_band(c->prec, F, W, frames, L, fi, c->eps, band, rl, rc, st);
+    {
+      PROF(c, K_BAND);
+      launch_align_band(c->prec, F, W, frames, L, fi, c->eps, band, rl, rc, st);
+    }
+    PROF(c, K_RECHECK);
     launch_recheck(c->prec, (F - 1) * W, rl, rc, W, frames, L, prior, -1, c->eps, band, chunk,
                    (unsigned long long*)c->nrecheck.p, st);
   }
@@ -452,7 +531,10 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
   while (t < F) {
     if (++guard > 4LL * F + 16) return fail(c, PCV_ESTATE, "refresh search did not terminate");
     if (band_mode) {
-      launch_band_scan(F, W, t, o, band, rec, &sm->scan, st);
+      {
+        PROF(c, K_SCAN);
+        launch_band_scan(F, W, t, o, band, rec, &sm->scan, st);
+      }
       pcv_status ps = sync_small(c);
       if (ps != PCV_OK) return ps;
       const int ts = c->small_host->scan.t_stop;
@@ -468,14 +550,26 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
     if (c->gap_estimate > 0.0) B = (int)std::fmin(std::fmax((double)B, 2.0 * c->gap_estimate), 1e9);
     const int t1 = (int)std::min<long long>((long long)F, (long long)t + B);
     launch_set_int(rc, 0, st);
-    launch_align_chunk(c->prec, t, t1, frames, L, fi, ref, prior, c->eps, chunk, rl, rc, st);
-    launch_recheck(c->prec, t1 - t, rl, rc, W, frames, L, prior, ref, c->eps, band, chunk,
-                   (unsigned long long*)c->nrecheck.p, st);
-    launch_first_exceed(t, t1, chunk.flag, &sm->first, st);
+    {
+      PROF(c, K_CHUNK);
+      launch_align_chunk(c->prec, t, t1, frames, L, fi, ref, prior, c->eps, chunk, rl, rc, st);
+    }
+    {
+      PROF(c, K_RECHECK);
+      launch_recheck(c->prec, t1 - t, rl, rc, W, frames, L, prior, ref, c->eps, band, chunk,
+                     (unsigned long long*)c->nrecheck.p, st);
+    }
+    {
+      PROF(c, K_FIRST);
+      launch_first_exceed(t, t1, chunk.flag, &sm->first, st);
+    }
     pcv_status ps = sync_small(c);
     if (ps != PCV_OK) return ps;
     const int first = c->small_host->first;
-    launch_chunk_records(t, first, t1, ref, chunk, rec, st);
+    {
+      PROF(c, K_RECORDS);
+      launch_chunk_records(t, first, t1, ref, chunk, rec, st);
+    }
     if (first < t1) {
       const double gap = (double)(first - (ref >= 0 ? ref : first - 1));
       c->gap_estimate = c->gap_estimate > 0.0 ? 0.5 * (c->gap_estimate + gap) : gap;
@@ -488,8 +582,11 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
     }
   }
   // compaction and per-segment work
-  launch_compact(F, rec, (int*)c->reflist.p, &sm->refresh_count, (int*)c->segof.p, (int*)c->alist.p,
-                 &sm->approx_count, (int*)c->aseg.p, 0, st);
+  {
+    PROF(c, K_COMPACT);
+    launch_compact(F, rec, (int*)c->reflist.p, &sm->refresh_count, (int*)c->segof.p, (int*)c->alist.p,
+                   &sm->approx_count, (int*)c->aseg.p, 0, st);
+  }
   small_tail_kernel<<<1, 1, 0, st>>>(sm, (const int*)c->reflist.p, fi.c32, fi.c64, fi.G);
   pcv_status ps = sync_small(c);
   if (ps != PCV_OK) return ps;
@@ -499,15 +596,29 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
   if ((ps = ensure(c, c->Bseg, seg_bytes * (size_t)(nref + 1))) != PCV_OK) return ps;
   if (had_prior) CUDA_TRY(c, cudaMemcpyAsync(c->Bseg.p, c->Bprior.p, seg_bytes, cudaMemcpyDeviceToDevice, st));
   void* Bseg1 = (char*)c->Bseg.p + seg_bytes;
-  launch_exact_pairs(c->prec, nref, (const int*)c->reflist.p, nullptr, frames, L, fi, c->Dbuf.p, Bseg1,
-                     (unsigned*)c->status.p, st);
-  launch_approx_pairs(c->prec, napp, (const int*)c->alist.p, (const int*)c->aseg.p, &sm->approx_count, frames, L,
-                      fi, rec.qxy, c->Bseg.p, c->Dbuf.p, st);
-  launch_finalize(c->prec, F, M, c->Dbuf.p, L.q, c->lambda, s, z, (float*)c->mstat.p, (double*)c->mstat.p, msd, st);
+  {
+    PROF(c, K_EXACT);
+    launch_exact_pairs(c->prec, nref, (const int*)c->reflist.p, nullptr, frames, L, fi, c->Dbuf.p, Bseg1,
+                       (unsigned*)c->status.p, st);
+  }
+  {
+    PROF(c, K_APPROX);
+    launch_approx_pairs(c->prec, napp, (const int*)c->alist.p, (const int*)c->aseg.p, &sm->approx_count, frames,
+                        L, fi, rec.qxy, c->Bseg.p, c->Dbuf.p, st);
+  }
+  {
+    PROF(c, K_FINAL);
+    launch_finalize(c->prec, F, M, c->Dbuf.p, L.q, c->lambda, s, z, (float*)c->mstat.p, (double*)c->mstat.p, msd,
+                    st);
+  }
   if (refreshed) CUDA_TRY(c, cudaMemcpyAsync(refreshed, rec.flag, F, cudaMemcpyDeviceToDevice, st));
   if (gs && gz) {
-    launch_adjoint_beta(c->prec, F, L, c->Dbuf.p, (const float*)c->mstat.p, s, c->lambda, nullptr, c->Bseg.p,
-                        (const int*)c->segof.p, gs, gz, st);
+    {
+      PROF(c, K_ADJ_BETA);
+      launch_adjoint_beta(c->prec, F, L, c->Dbuf.p, (const float*)c->mstat.p, s, c->lambda, nullptr, c->Bseg.p,
+                          (const int*)c->segof.p, gs, gz, st);
+    }
+    PROF(c, K_ADJ_FINISH);
     launch_adjoint_finish(c->prec, F, frames, L, fi, c->Dbuf.p, (const float*)c->mstat.p, s, c->lambda, c->Bseg.p,
                           (const int*)c->segof.p, rec, prior, gs, gz, (unsigned*)c->status.p, st);
   }
@@ -541,15 +652,28 @@ pcv_status evaluate_exact(pcv_ctx* c, int F, const void* frames, double* s, doub
   const LandmarkDev L = lm_view(c);
   const FrameInfo fi = frame_info(c);
   const bool grads = gs && gz;
-  launch_frame_prep(c->prec, F, frames, L, fi, st);
-  launch_exact_pairs(c->prec, F, nullptr, nullptr, frames, L, fi, c->Dbuf.p, grads ? c->Rpair.p : nullptr,
-                     (unsigned*)c->status.p, st);
-  launch_finalize(c->prec, F, c->M, c->Dbuf.p, L.q, c->lambda, s, z, (float*)c->mstat.p, (double*)c->mstat.p, msd,
-                  st);
+  {
+    PROF(c, K_PREP);
+    launch_frame_prep(c->prec, F, frames, L, fi, st);
+  }
+  {
+    PROF(c, K_EXACT);
+    launch_exact_pairs(c->prec, F, nullptr, nullptr, frames, L, fi, c->Dbuf.p, grads ? c->Rpair.p : nullptr,
+                       (unsigned*)c->status.p, st);
+  }
+  {
+    PROF(c, K_FINAL);
+    launch_finalize(c->prec, F, c->M, c->Dbuf.p, L.q, c->lambda, s, z, (float*)c->mstat.p, (double*)c->mstat.p,
+                    msd, st);
+  }
   if (refreshed) launch_fill_u8(refreshed, 1, (size_t)F, st);
   if (grads) {
-    launch_adjoint_beta(c->prec, F, L, c->Dbuf.p, (const float*)c->mstat.p, s, c->lambda, c->Rpair.p, nullptr, nullptr,
-                        gs, gz, st);
+    {
+      PROF(c, K_ADJ_BETA);
+      launch_adjoint_beta(c->prec, F, L, c->Dbuf.p, (const float*)c->mstat.p, s, c->lambda, c->Rpair.p, nullptr,
+                          nullptr, gs, gz, st);
+    }
+    PROF(c, K_ADJ_FINISH);
     FrameRec none;
     RefDesc nop;
     launch_adjoint_finish(c->prec, F, frames, L, fi, c->Dbuf.p, (const float*)c->mstat.p, s, c->lambda, nullptr,
@@ -576,8 +700,10 @@ pcv_status pcv_evaluate(pcv_ctx* c, int F, const void* frames, double* s, double
   const bool close = c->eps >= 0.0;
   pcv_status st = ensure_frame_workspace(c, F, close, dsdx != nullptr);
   if (st != PCV_OK) return st;
+  const int64_t launches0 = t_launches;
   st = close ? evaluate_close(c, F, frames, s, z, dsdx, dzdx, msd, refreshed)
              : evaluate_exact(c, F, frames, s, z, dsdx, dzdx, msd, refreshed);
+  c->stats.kernel_launches += t_launches - launches0;
   if (st != PCV_OK) return st;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(c, PCV_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
@@ -630,7 +756,12 @@ pcv_status pcv_combine_grad(pcv_ctx* c, int F, const double* g_s, const double* 
   if (F == 0) return PCV_OK;
   if (!dsdx || !dzdx || !out) return fail(c, PCV_EINVAL, "dsdx, dzdx and out are required");
   cudaSetDevice(c->device);
-  launch_combine_grad(c->prec, F, 3 * c->N, g_s, g_z, dsdx, dzdx, out, c->stream);
+  const int64_t launches0 = t_launches;
+  {
+    PROF(c, K_COMBINE);
+    launch_combine_grad(c->prec, F, 3 * c->N, g_s, g_z, dsdx, dzdx, out, c->stream);
+  }
+  c->stats.kernel_launches += t_launches - launches0;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(c, PCV_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
   return PCV_OK;
@@ -648,6 +779,34 @@ pcv_status pcv_sync(pcv_ctx* c) {
   }
   return PCV_OK;
 }
+
+pcv_status pcv_get_profile(pcv_ctx* c, int n, double* ms, int64_t* launches) {
+  if (!c) return fail(nullptr, PCV_EINVAL, "NULL context");
+  if (n < 0 || n > PCV_PROFILE_KERNELS || (n > 0 && (!ms || !launches))) return fail(c, PCV_EINVAL, "bad arrays");
+  cudaSetDevice(c->device);
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  for (const ProfEvent& e : c->prof_pending) {
+    float t = 0.0f;
+    if (cudaEventElapsedTime(&t, e.a, e.b) == cudaSuccess) {
+      c->prof_ms[e.id] += t;
+      c->prof_launches[e.id] += 1;
+    }
+    c->prof_pool.push_back(e.a);
+    c->prof_pool.push_back(e.b);
+  }
+  c->prof_pending.clear();
+  for (int k = 0; k < n; ++k) {
+    ms[k] = c->prof_ms[k];
+    launches[k] = c->prof_launches[k];
+  }
+  for (int k = 0; k < PCV_PROFILE_KERNELS; ++k) {
+    c->prof_ms[k] = 0.0;
+    c->prof_launches[k] = 0;
+  }
+  return PCV_OK;
+}
+
+const char* pcv_profile_name(int id) { return (id >= 0 && id < PCV_PROFILE_KERNELS) ? kKernelNames[id] : ""; }
 
 pcv_status pcv_get_stats(pcv_ctx* c, pcv_stats* out) {
   if (!c || !out) return fail(c, PCV_EINVAL, "NULL argument");

@@ -249,6 +249,139 @@ __device__ __forceinline__ void quat_to_rot(const T* q, T* R) {
   R[8] = (s * s - x * x - y * y + z * z) * inv;
 }
 
+// ---------------------------------------------------------------------------------------
+// FP32 top eigenvector of K(H) (the quaternion of the optimal rotation), for the direct
+// two-pass MSD: the rotation only needs FP32 accuracy because the directly evaluated
+// MSD sum_j w_j |x_j - R a_j|^2 is stationary in R.  H is normalised by an upper bound
+// ub >= lambda_max so that the iteration works on O(1) numbers.
+
+// cofactor-based eigenvector of the symmetric 4x4 A = K - lam I; returns the magnitude of
+// the adjugate diagonal entry used (small => lam is (nearly) a multiple eigenvalue)
+__device__ __forceinline__ float adj_eigvec_f32(const float* A, float* q) {
+  float cof[16];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float m[9];
+      int k = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (i == r) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (j == c) continue;
+          m[k++] = A[4 * i + j];
+        }
+      }
+      const float d = det3(m);
+      cof[4 * r + c] = ((r + c) & 1) ? -d : d;
+    }
+  int best = 0;
+  float bv = fabsf(cof[0]);
+#pragma unroll
+  for (int i = 1; i < 4; ++i)
+    if (fabsf(cof[5 * i]) > bv) {
+      bv = fabsf(cof[5 * i]);
+      best = i;
+    }
+  float n2 = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    q[i] = cof[4 * i + best];
+    n2 += q[i] * q[i];
+  }
+  if (n2 > 0.0f) {
+    const float inv = rsqrtf(n2) * (q[0] < 0.0f ? -1.0f : 1.0f);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) q[i] *= inv;
+  }
+  return bv;
+}
+
+// cyclic Jacobi fallback (FP32) for (nearly) degenerate top eigenvalues: top eigenvector
+static __device__ __noinline__ void jacobi_top_f32(const float* Kin, float* q) {
+  float A[16], V[16];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) {
+    A[e] = Kin[e];
+    V[e] = (e % 5 == 0) ? 1.0f : 0.0f;
+  }
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    float off = 0.0f;
+    for (int i = 0; i < 4; ++i)
+      for (int j = i + 1; j < 4; ++j) off += A[4 * i + j] * A[4 * i + j];
+    if (off < 1e-30f) break;
+    for (int p = 0; p < 3; ++p)
+      for (int r = p + 1; r < 4; ++r) {
+        const float apr = A[4 * p + r];
+        if (apr == 0.0f) continue;
+        const float th = (A[5 * r] - A[5 * p]) / (2.0f * apr);
+        const float t = copysignf(1.0f, th) / (fabsf(th) + sqrtf(th * th + 1.0f));
+        const float c = rsqrtf(t * t + 1.0f), sn = t * c;
+        for (int k = 0; k < 4; ++k) {
+          const float akp = A[4 * k + p], akr = A[4 * k + r];
+          A[4 * k + p] = c * akp - sn * akr;
+          A[4 * k + r] = sn * akp + c * akr;
+        }
+        for (int k = 0; k < 4; ++k) {
+          const float apk = A[4 * p + k], ark = A[4 * r + k];
+          A[4 * p + k] = c * apk - sn * ark;
+          A[4 * r + k] = sn * apk + c * ark;
+        }
+        for (int k = 0; k < 4; ++k) {
+          const float vkp = V[4 * k + p], vkr = V[4 * k + r];
+          V[4 * k + p] = c * vkp - sn * vkr;
+          V[4 * k + r] = sn * vkp + c * vkr;
+        }
+      }
+  }
+  int best = 0;
+  for (int i = 1; i < 4; ++i)
+    if (A[5 * i] > A[5 * best]) best = i;
+  const float sg = V[best] < 0.0f ? -1.0f : 1.0f;
+  for (int i = 0; i < 4; ++i) q[i] = sg * V[4 * i + best];
+}
+
+// Top eigenvector (unit quaternion, q[0] >= 0) of K(H) in FP32.  Returns false if the
+// Newton iteration hit its cap (the result is still usable).
+__device__ __forceinline__ bool top_quat_f32(const float* Hin, float ub, float* q) {
+  const float sc = 1.0f / ub;
+  float H[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) H[e] = Hin[e] * sc;
+  float K[16];
+  quat_matrix(H, K);
+  float c2, c1, c0;
+  char_poly(H, K, c2, c1, c0);
+  float l = 1.0f;
+  bool ok = false;
+  for (int it = 0; it < 60; ++it) {
+    const float p = fmaf(fmaf(fmaf(l, l, c2), l, c1), l, c0);
+    const float dp = fmaf(fmaf(4.0f * l, l, 2.0f * c2), l, c1);
+    if (!(dp > 0.0f)) {
+      ok = true;
+      break;
+    }
+    const float step = p / dp;
+    l -= step;
+    if (fabsf(step) <= 2e-7f) {
+      ok = true;
+      break;
+    }
+  }
+  float A[16];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) A[e] = K[e];
+  A[0] -= l;
+  A[5] -= l;
+  A[10] -= l;
+  A[15] -= l;
+  const float mag = adj_eigvec_f32(A, q);
+  if (!(mag > 1e-5f)) jacobi_top_f32(K, q);
+  return ok;
+}
+
 // Unit eigenvector of K for eigenvalue lam in FP64 (adjugate column, as adj_eigvec).
 __device__ __forceinline__ void adj_eigvec_f64(const double* K, double lam, double* q) {
   double A[16];

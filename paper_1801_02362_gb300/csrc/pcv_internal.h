@@ -8,6 +8,9 @@ namespace pcv {
 
 enum Prec { P_F64 = 0, P_F32 = 1, P_F16 = 2 };
 
+// counts kernel launches of the calling host thread (defined in pcv_api.cu)
+void note_launch(int n = 1);
+
 // status bits written to the context's device status word
 constexpr unsigned STATUS_NOCONV = 1u;
 

@@ -18,7 +18,8 @@ from . import build_lib
 
 PCV_OK, PCV_EINVAL, PCV_ECUDA, PCV_ENOMEM, PCV_ENOCONV, PCV_ESTATE = 0, -1, -2, -3, -4, -5
 PCV_FP64, PCV_FP32, PCV_FP16_STORAGE = 0, 1, 2
-PCV_OPT_BAND, PCV_OPT_CHUNK, PCV_OPT_EXACT_TILE, PCV_OPT_APPROX_TILE = 1, 2, 3, 4
+PCV_OPT_BAND, PCV_OPT_CHUNK, PCV_OPT_EXACT_TILE, PCV_OPT_APPROX_TILE, PCV_OPT_PROFILE = 1, 2, 3, 4, 5
+PCV_PROFILE_KERNELS = 16
 
 _STATUS_NAMES = {0: "PCV_OK", -1: "PCV_EINVAL", -2: "PCV_ECUDA", -3: "PCV_ENOMEM", -4: "PCV_ENOCONV",
                  -5: "PCV_ESTATE"}
@@ -33,7 +34,7 @@ class PcvError(RuntimeError):
 class pcv_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("frames", "xy_alignments", "landmark_alignments", "approx_msds",
                                               "refreshes_threshold", "refreshes_initial", "fp64_rechecks",
-                                              "host_syncs")]
+                                              "host_syncs", "kernel_launches")]
 
     def as_dict(self) -> dict:
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
@@ -58,6 +59,8 @@ SIGNATURES = {
     "pcv_sync": (_i, [_vp]),
     "pcv_set_option": (_i, [_vp, _i, ctypes.c_int64]),
     "pcv_last_error": (ctypes.c_char_p, [_vp]),
+    "pcv_get_profile": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
+    "pcv_profile_name": (ctypes.c_char_p, [_i]),
 }
 
 _lib = None
@@ -171,6 +174,20 @@ def pcv_sync(ctx):
     _check(ctx, load().pcv_sync(ctx))
 
 
+def pcv_get_profile(ctx) -> dict:
+    """{kernel family: (total ms, launches)} collected since the last call."""
+    n = PCV_PROFILE_KERNELS
+    ms = (ctypes.c_double * n)()
+    la = (ctypes.c_int64 * n)()
+    _check(ctx, load().pcv_get_profile(ctx, n, ms, la))
+    out = {}
+    for k in range(n):
+        name = load().pcv_profile_name(k).decode()
+        if name and la[k]:
+            out[name] = (float(ms[k]), int(la[k]))
+    return out
+
+
 def pcv_last_error(ctx) -> str:
     m = load().pcv_last_error(ctx)
     return m.decode() if m else ""
@@ -250,6 +267,12 @@ class PathCV:
 
     def stats(self) -> dict:
         return pcv_get_stats(self.ctx)
+
+    def set_profiling(self, on: bool):
+        pcv_set_option(self.ctx, PCV_OPT_PROFILE, 1 if on else 0)
+
+    def profile(self) -> dict:
+        return pcv_get_profile(self.ctx)
 
     def sync(self):
         pcv_sync(self.ctx)

@@ -48,7 +48,7 @@ def test_null_context_is_rejected_without_gpu(lib):
     assert lib.pcv_destroy(None) == pcv.PCV_OK
     assert isinstance(lib.pcv_last_error(None), bytes)
     st = pcv.pcv_stats()
-    assert ctypes.sizeof(st) == 8 * 8
+    assert ctypes.sizeof(st) == 9 * 8
 
 
 def test_create_reports_bad_precision(lib):
