@@ -157,21 +157,25 @@ __device__ __forceinline__ double lambda_max_newton(const double* H, double ub, 
   if (!(l <= ub) || !(l == l)) l = ub;
   const double tol = 1e-13 * fabs(ub) + 1e-300;
   *ok = false;
+  double prev = 1.0e300;
   for (int it = 0; it < 60; ++it) {
     const double l2 = l * l;
     const double p = fma(fma(l2 + c2, l, c1), l, c0);
     const double dp = fma(fma(4.0 * l, l, 2.0 * c2), l, c1);
     if (!(dp > 0.0)) {
-      *ok = (p == 0.0);
+      *ok = true;  // at (or numerically on) the root
       break;
     }
     // the step only needs relative accuracy: divide in FP32
     const double step = (double)__fdiv_rn((float)p, (float)dp);
     l -= step;
-    if (fabs(step) <= tol) {
+    const double a = fabs(step);
+    // converged, or at the rounding-noise floor of P (steps stop shrinking near the root)
+    if (a <= tol || (a < 1e-9 * fabs(ub) && a >= 0.5 * prev)) {
       *ok = true;
       break;
     }
+    prev = a;
   }
   return l;
 }
@@ -356,6 +360,7 @@ __device__ __forceinline__ bool top_quat_f32(const float* Hin, float ub, float* 
   char_poly(H, K, c2, c1, c0);
   float l = 1.0f;
   bool ok = false;
+  float prev = 3.0e38f;
   for (int it = 0; it < 60; ++it) {
     const float p = fmaf(fmaf(fmaf(l, l, c2), l, c1), l, c0);
     const float dp = fmaf(fmaf(4.0f * l, l, 2.0f * c2), l, c1);
@@ -365,10 +370,14 @@ __device__ __forceinline__ bool top_quat_f32(const float* Hin, float ub, float* 
     }
     const float step = p / dp;
     l -= step;
-    if (fabsf(step) <= 2e-7f) {
+    const float a = fabsf(step);
+    // converged: below FP32 resolution, or at the rounding-noise floor of P near the root
+    // (steps no longer shrink; happens when the top eigenvalue gap is small)
+    if (a <= 2e-7f || (a < 1e-4f && a >= 0.5f * prev)) {
       ok = true;
       break;
     }
+    prev = a;
   }
   float A[16];
 #pragma unroll
