@@ -186,6 +186,40 @@ PCV_API pcv_status pcv_get_profile(pcv_ctx* ctx, int n, double* ms, int64_t* lau
 /* Name of kernel family `id` ("" outside 0..PCV_PROFILE_KERNELS-1). */
 PCV_API const char* pcv_profile_name(int id);
 
+/* Exact-mode path CVs for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart; this is a deployment aid.  Some callers cannot call
+ * cudaMalloc: an MD engine that hands out all device memory from its own pool, or code
+ * where a device allocation would stall or break the caller's timing.  This call needs no
+ * context and allocates nothing.  Its intermediates live in one fixed device array of
+ * PCV_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the process
+ * exits.
+ *
+ * It computes the same s, z and MSDs as pcv_evaluate in exact mode with uniform weights
+ * and FP32 storage (Algorithm 1 for every frame; no close structure, no gradients):
+ *   frames     device, F*N*3 floats, uncentred;
+ *   landmarks  device, M*N*3 floats, uncentred (centred here, in FP64, then stored FP32);
+ *   q          device, M doubles, or NULL for q_i = i (1-based);
+ *   lambda     > 0, nm^-2;
+ *   s, z       device, F doubles each; msd device, F*M doubles, or NULL;
+ *   cuda_stream  the stream to run on (NULL = legacy default stream), on the current device;
+ *   err, err_len  optional host buffer that receives a one-line message on failure.
+ * Limits and behaviour:
+ *   - the problem must fit the fixed scratch: about 12*M*N + 4*F*M + 72*F + 16*M bytes
+ *     (plus alignment) <= PCV_NOALLOC_SCRATCH_BYTES; larger problems return PCV_EINVAL
+ *     with a message, before any GPU work;
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture;
+ *   - every call shares the one array, which keeps the previous call's contents: calls that
+ *     overlap on the GPU (different streams, threads or processes on the same device)
+ *     race and must be serialised by the caller;
+ *   - the call waits for its own stream and reports PCV_ENOCONV if an eigen-solve hit its
+ *     iteration cap; other errors: PCV_EINVAL, PCV_ECUDA. */
+#define PCV_NOALLOC_SCRATCH_BYTES (16u << 20)
+PCV_API pcv_status pcv_evaluate_exact_noalloc(int F, int M, int N, const float* frames, const float* landmarks,
+                                              const double* q, double lambda, double* s, double* z, double* msd,
+                                              void* cuda_stream, char* err, size_t err_len);
+
 /* One-line description of the last error on ctx (never NULL). */
 PCV_API const char* pcv_last_error(const pcv_ctx* ctx);
 

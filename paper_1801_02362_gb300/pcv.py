@@ -61,6 +61,8 @@ SIGNATURES = {
     "pcv_last_error": (ctypes.c_char_p, [_vp]),
     "pcv_get_profile": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
     "pcv_profile_name": (ctypes.c_char_p, [_i]),
+    "pcv_evaluate_exact_noalloc": (_i, [_i, _i, _i, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, ctypes.c_char_p,
+                                       ctypes.c_size_t]),
 }
 
 _lib = None
