@@ -39,9 +39,10 @@ FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
 
 # algorithmic FP32 flops per (frame, landmark, atom) of each pair kernel (FMA = 2 flops)
 FLOPS_PER_UNIT = {
-    "approx_pair": 9,    # d = x' - b (3 sub), |d|^2 (3 FMA)
-    "exact_pair": 45,    # pass 1: 9 FMA; pass 2: R a (9 FMA), 3 sub, 3 FMA
-    "adjoint_beta": 36,  # beta^s, beta^z += gamma R a (2 x 9 FMA)
+    "approx_pair": 9,         # d = x' - b (3 sub), |d|^2 (3 FMA)
+    "exact_pair": 45,         # pass 1: 9 FMA; pass 2: R a (9 FMA), 3 sub, 3 FMA
+    "adjoint_beta_pair": 36,  # beta^s, beta^z += gamma R_i a (2 x 9 FMA), per-pair rotations
+    "adjoint_beta_seg": 12,   # beta^s, beta^z += gamma b_i (2 x 3 FMA), b_i shared by a segment
 }
 
 

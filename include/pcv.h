@@ -205,7 +205,7 @@ PCV_API const char* pcv_profile_name(int id);
  *   cuda_stream  the stream to run on (NULL = legacy default stream), on the current device;
  *   err, err_len  optional host buffer that receives a one-line message on failure.
  * Limits and behaviour:
- *   - the problem must fit the fixed scratch: about 12*M*N + 4*F*M + 72*F + 16*M bytes
+ *   - the problem must fit the fixed scratch: about 12*M*N + 4*F*M + 72*F + 20*M bytes
  *     (plus alignment) <= PCV_NOALLOC_SCRATCH_BYTES; larger problems return PCV_EINVAL
  *     with a message, before any GPU work;
  *   - the first call on a device looks up the array's device address

@@ -1,0 +1,476 @@
+// k_adjoint.cu -- the adjoint of the path CVs: ds/dx and dz/dx of every frame.
+//
+// With gamma_i = dL/dD_i (gamma^z_i = p_i, gamma^s_i = -lambda p_i (q_i - s),
+// p_i = exp(-lambda (D_i - m)) / l), the direct part of Eq. (der_dist) summed over the
+// landmarks is 2 w_k ((sum_i gamma_i) x_k - beta_k) with beta_k = sum_i gamma_i Rot_i a_ik,
+// Rot_i = R_{a_i x} at exact / reassignment frames and R_{a_i y} at approximate frames
+// (R_xy is applied afterwards).  Two contraction kernels compute beta:
+//   adjoint_beta_pair: any per-(frame, landmark) rotation (exact mode, frequent
+//     reassignments): 18 FMA per (frame, landmark, atom) for s and z together;
+//   adjoint_beta_seg: frames that share a close structure share Rot_i, so b_i = Rot_i a_i
+//     is formed once per tile and beta = sum_i gamma_i b_i is a plain GEMM: 6 FMA.
+// adjoint_finish_warp (one warp per frame) turns beta into gradients and adds, at
+// approximate frames, the rotation term of Eq. (close_der_dist) (derivation in
+// pcv_device.cuh: adjoint_rotation_term).
+#include <cuda_fp16.h>
+
+#include "pcv_device.cuh"
+#include "pcv_internal.h"
+
+namespace pcv {
+namespace {
+
+template <typename ST, typename LT>
+__device__ __forceinline__ ST lm_at(const LT* p) {
+  return (ST)(*p);
+}
+template <>
+__device__ __forceinline__ float lm_at<float, __half>(const __half* p) {
+  return __half2float(*p);
+}
+
+// gamma^s, gamma^z of one (frame, landmark) pair from the softmax weight p
+template <typename ST>
+__device__ __forceinline__ void gammas(ST p, ST lambda, ST qi, ST sf, ST& gs, ST& gz) {
+  gz = p;
+  gs = -lambda * p * (qi - sf);
+}
+
+// ---------------------------------------------------------------------------------------
+constexpr int BP_TF = 32, BP_TJ = 64, BP_THREADS = 128;
+
+template <typename ST, typename LT>
+__global__ void __launch_bounds__(BP_THREADS)
+adjoint_beta_pair(int F, int M, int N, const LT* __restrict__ lm, const double* __restrict__ q,
+                  const float* __restrict__ q32, const ST* __restrict__ P, const double* __restrict__ s, double lambda,
+                  const ST* __restrict__ Rpair, const ST* __restrict__ Bseg, const int* __restrict__ seg_of_frame,
+                  ST* __restrict__ gs, ST* __restrict__ gz) {
+  constexpr int KL = sizeof(ST) == 8 ? 4 : 8;
+  __shared__ __align__(16) ST Ws[KL * 3][BP_TF * 3];  // gamma^s_fi Rot_fi[b][c] at [(i,c)][(f,b)]
+  __shared__ __align__(16) ST Wz[KL * 3][BP_TF * 3];
+  __shared__ __align__(16) ST As[KL * 3][BP_TJ];
+  const int f0 = blockIdx.y * BP_TF, j0 = blockIdx.x * BP_TJ;
+  const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+  ST bs[2][3][8], bz[2][3][8];
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) bs[u][b][k] = bz[u][b][k] = 0;
+  const ST lam = (ST)lambda;
+  for (int i0 = 0; i0 < M; i0 += KL) {
+    for (int e = tid; e < BP_TF * KL; e += BP_THREADS) {
+      const int ff = e / KL, ii = e - ff * KL;
+      const int f = f0 + ff, i = i0 + ii;
+      ST rot[9];
+      ST gsv = 0, gzv = 0;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) rot[c] = 0;
+      if (f < F && i < M) {
+        const ST qi = sizeof(ST) == 8 ? (ST)q[i] : (ST)q32[i];
+        gammas<ST>(P[(size_t)f * M + i], lam, qi, (ST)s[f], gsv, gzv);
+        const ST* R = Rpair ? Rpair + ((size_t)f * M + i) * 9 : Bseg + ((size_t)seg_of_frame[f] * M + i) * 9;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) rot[c] = R[c];
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          Ws[ii * 3 + c][ff * 3 + b] = gsv * rot[3 * b + c];
+          Wz[ii * 3 + c][ff * 3 + b] = gzv * rot[3 * b + c];
+        }
+    }
+    for (int e = tid; e < KL * BP_TJ; e += BP_THREADS) {
+      const int ii = e / BP_TJ, jj = e - ii * BP_TJ;
+      const int i = i0 + ii, j = j0 + jj;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) As[ii * 3 + c][jj] = (i < M && j < N) ? lm_at<ST>(lm + ((size_t)i * N + j) * 3 + c) : (ST)0;
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int kk = 0; kk < KL * 3; ++kk) {
+      ST a[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) a[k] = As[kk][tx * 8 + k];
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          const ST ws = Ws[kk][(ty * 2 + u) * 3 + b];
+          const ST wz = Wz[kk][(ty * 2 + u) * 3 + b];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            bs[u][b][k] = fma(ws, a[k], bs[u][b][k]);
+            bz[u][b][k] = fma(wz, a[k], bz[u][b][k]);
+          }
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int f = f0 + ty * 2 + u;
+    if (f >= F) continue;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int j = j0 + tx * 8 + k;
+      if (j >= N) continue;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        gs[((size_t)f * N + j) * 3 + b] = bs[u][b][k];
+        gz[((size_t)f * N + j) * 3 + b] = bz[u][b][k];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// beta for frames sharing close structures: tile of 64 consecutive frames x 64 atoms, 256
+// threads, each 4 frames x 4 atoms x 3 components x {s, z}.  Frames of the tile are grouped
+// into runs of equal segment; per run and landmark chunk the landmarks are rotated once by
+// R_{a_i y} into shared memory, and gamma is formed from p (coalesced rows of P).
+constexpr int BS_TF = 64, BS_TJ = 64, BS_KL = 16, BS_THREADS = 256;
+
+template <typename LT>
+__global__ void __launch_bounds__(BS_THREADS, 2)
+adjoint_beta_seg(int F, int M, int N, const LT* __restrict__ lm, const float* __restrict__ q32,
+                 const float* __restrict__ P, const double* __restrict__ s, float lambda,
+                 const float* __restrict__ Bseg, const int* __restrict__ seg_of_frame, float* __restrict__ gs,
+                 float* __restrict__ gz) {
+  __shared__ __align__(16) float Gs[BS_KL][BS_TF];  // gamma^s of (landmark, frame), 0 outside the run
+  __shared__ __align__(16) float Gz[BS_KL][BS_TF];
+  __shared__ __align__(16) float Bb[BS_KL][BS_TJ * 3];  // b_ij = R_{a_i y} a_ij, (atom, xyz) packed
+  __shared__ float s_B[BS_KL][9];
+  __shared__ int s_seg[BS_TF];
+  __shared__ float s_s[BS_TF];
+  const int f0 = blockIdx.y * BS_TF, j0 = blockIdx.x * BS_TJ;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;  // atoms j0 + 4 tx + {0..3}; frames 4 ty + {0..3}
+  if (tid < BS_TF) {
+    const int f = f0 + tid;
+    s_seg[tid] = f < F ? seg_of_frame[f] : -1;
+    s_s[tid] = f < F ? (float)s[f] : 0.0f;
+  }
+  float acs[4][12], acz[4][12];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acs[u][k] = acz[u][k] = 0.0f;
+  __syncthreads();
+  int k = 0;
+  while (k < BS_TF && s_seg[k] >= 0) {
+    const int seg = s_seg[k];
+    int kend = k;
+    while (kend < BS_TF && s_seg[kend] == seg) ++kend;
+    for (int i0 = 0; i0 < M; i0 += BS_KL) {
+      if (tid < BS_KL * 9) {
+        const int ii = tid / 9, c = tid - ii * 9;
+        const int i = i0 + ii;
+        s_B[ii][c] = i < M ? Bseg[((size_t)seg * M + i) * 9 + c] : 0.0f;
+      }
+      // gamma: consecutive threads walk a frame's row of P (coalesced)
+      for (int e = tid; e < BS_KL * BS_TF; e += BS_THREADS) {
+        const int ff = e / BS_KL, ii = e - ff * BS_KL;
+        const int f = f0 + ff, i = i0 + ii;
+        float gsv = 0.0f, gzv = 0.0f;
+        if (ff >= k && ff < kend && i < M) gammas<float>(P[(size_t)f * M + i], lambda, q32[i], s_s[ff], gsv, gzv);
+        Gs[ii][ff] = gsv;
+        Gz[ii][ff] = gzv;
+      }
+      __syncthreads();
+      for (int e = tid; e < BS_KL * BS_TJ; e += BS_THREADS) {
+        const int ii = e / BS_TJ, jj = e - ii * BS_TJ;
+        const int i = i0 + ii, j = j0 + jj;
+        float b0 = 0.0f, b1 = 0.0f, b2 = 0.0f;
+        if (i < M && j < N) {
+          const LT* src = lm + ((size_t)i * N + j) * 3;
+          const float a0 = lm_at<float>(src), a1 = lm_at<float>(src + 1), a2 = lm_at<float>(src + 2);
+          const float* B = s_B[ii];
+          b0 = B[0] * a0 + B[1] * a1 + B[2] * a2;
+          b1 = B[3] * a0 + B[4] * a1 + B[5] * a2;
+          b2 = B[6] * a0 + B[7] * a1 + B[8] * a2;
+        }
+        Bb[ii][jj * 3 + 0] = b0;
+        Bb[ii][jj * 3 + 1] = b1;
+        Bb[ii][jj * 3 + 2] = b2;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int ii = 0; ii < BS_KL; ++ii) {
+        const float4 g1 = *reinterpret_cast<const float4*>(&Gs[ii][ty * 4]);
+        const float4 g2 = *reinterpret_cast<const float4*>(&Gz[ii][ty * 4]);
+        const float gsv[4] = {g1.x, g1.y, g1.z, g1.w}, gzv[4] = {g2.x, g2.y, g2.z, g2.w};
+        float b[12];
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+          const float4 t = *reinterpret_cast<const float4*>(&Bb[ii][tx * 12 + 4 * v]);
+          b[4 * v] = t.x;
+          b[4 * v + 1] = t.y;
+          b[4 * v + 2] = t.z;
+          b[4 * v + 3] = t.w;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int c = 0; c < 12; ++c) {
+            acs[u][c] = fmaf(gsv[u], b[c], acs[u][c]);
+            acz[u][c] = fmaf(gzv[u], b[c], acz[u][c]);
+          }
+      }
+      __syncthreads();
+    }
+    k = kend;
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int f = f0 + ty * 4 + u;
+    if (f >= F) continue;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int j = j0 + tx * 4 + a;
+      if (j >= N) continue;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        gs[((size_t)f * N + j) * 3 + c] = acs[u][3 * a + c];
+        gz[((size_t)f * N + j) * 3 + c] = acz[u][3 * a + c];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// warp-wide FP32 / FP64 sums
+__device__ __forceinline__ float wsum(float v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+__device__ __forceinline__ double wsum(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// Per-frame finish, one warp per frame.  beta (in gs / gz) -> gradients; approximate
+// frames add w_k T^T y_k (see adjoint_rotation_term).
+template <typename ST, typename FT>
+__global__ void __launch_bounds__(128)
+adjoint_finish_warp(int F, int M, int N, const FT* __restrict__ frames, const float4* __restrict__ c32,
+                    const double4* __restrict__ c64, const float* __restrict__ wts, const double* __restrict__ w64,
+                    const float* __restrict__ A32, const double* __restrict__ A64, const double* __restrict__ q,
+                    const float* __restrict__ q32, double dscale, const ST* __restrict__ P,
+                    const double* __restrict__ s, double lambda, const ST* __restrict__ Bseg,
+                    const int* __restrict__ seg_of_frame, FrameRec rec, const FT* __restrict__ prior_coords,
+                    double4 prior_c, ST* __restrict__ gs, ST* __restrict__ gz) {
+  const int f = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  if (f >= F) return;
+  const int lane = threadIdx.x & 31;
+  const bool f64 = sizeof(ST) == 8;
+  ST cx[3];
+  if (f64) {
+    const double4 c = c64[f];
+    cx[0] = (ST)c.x; cx[1] = (ST)c.y; cx[2] = (ST)c.z;
+  } else {
+    const float4 c = c32[f];
+    cx[0] = (ST)c.x; cx[1] = (ST)c.y; cx[2] = (ST)c.z;
+  }
+  const FT* x = frames + (size_t)f * N * 3;
+  ST* bsp = gs + (size_t)f * N * 3;
+  ST* bzp = gz + (size_t)f * N * 3;
+  const ST wuni = (ST)dscale;  // uniform weight; converted once, not per atom
+  auto wt = [&](int j) -> ST {
+    if (f64) return w64 ? (ST)w64[j] : wuni;
+    return wts ? (ST)wts[j] : wuni;
+  };
+  const bool approx = rec.flag && rec.flag[f] == 0;
+  // Gamma = sum_i gamma_i from the same p the contraction used.  In exact arithmetic
+  // Gamma^s = 0 and Gamma^z = 1, but the FP32 value of s and the p-weighted sum of q differ
+  // by ~u s, which lambda ~ 1e3 amplifies: keeping the term makes the gradient exactly that
+  // of sum_i gamma_i D_i for the gammas used.
+  const ST sf = (ST)s[f], lamw = (ST)lambda;
+  ST Gs = 0, Gz = 0;
+  for (int i = lane; i < M; i += 32) {
+    ST gsv, gzv;
+    const ST qi = f64 ? (ST)q[i] : (ST)q32[i];
+    gammas<ST>(P[(size_t)f * M + i], lamw, qi, sf, gsv, gzv);
+    Gs += gsv;
+    Gz += gzv;
+  }
+  Gs = wsum(Gs);
+  Gz = wsum(Gz);
+  if (!approx) {
+    for (int j = lane; j < N; j += 32) {
+      const ST w = wt(j);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const ST v = (ST)x[3 * j + b] - cx[b];
+        bsp[3 * j + b] = (ST)2 * w * (Gs * v - bsp[3 * j + b]);
+        bzp[3 * j + b] = (ST)2 * w * (Gz * v - bzp[3 * j + b]);
+      }
+    }
+    return;
+  }
+  const int r = rec.ref[f];
+  const FT* y = r >= 0 ? frames + (size_t)r * N * 3 : prior_coords;
+  ST cy[3];
+  if (r >= 0) {
+    if (f64) { const double4 c = c64[r]; cy[0] = (ST)c.x; cy[1] = (ST)c.y; cy[2] = (ST)c.z; }
+    else { const float4 c = c32[r]; cy[0] = (ST)c.x; cy[1] = (ST)c.y; cy[2] = (ST)c.z; }
+  } else {
+    cy[0] = (ST)prior_c.x;
+    cy[1] = (ST)prior_c.y;
+    cy[2] = (ST)prior_c.z;
+  }
+  ST R[9];
+  {
+    const double4 qq = rec.qxy[f];
+    const ST qd[4] = {(ST)qq.x, (ST)qq.y, (ST)qq.z, (ST)qq.w};
+    quat_to_rot(qd, R);
+  }
+  // X = sum_j w x_j beta_j^T (s, z) and H_xy = sum_j w y_j x_j^T, centred, true weights
+  ST acc[27];
+#pragma unroll
+  for (int e = 0; e < 27; ++e) acc[e] = 0;
+  for (int j = lane; j < N; j += 32) {
+    const ST w = wt(j);
+    ST v[3], u[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      v[b] = (ST)x[3 * j + b] - cx[b];
+      u[b] = (ST)y[3 * j + b] - cy[b];
+    }
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const ST wv = w * v[b], wu = w * u[b];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        acc[3 * b + c] = fma(wv, bsp[3 * j + c], acc[3 * b + c]);
+        acc[9 + 3 * b + c] = fma(wv, bzp[3 * j + c], acc[9 + 3 * b + c]);
+        acc[18 + 3 * b + c] = fma(wu, v[c], acc[18 + 3 * b + c]);
+      }
+    }
+  }
+  // Phi = sum_i gamma_i R_{a_i y} A_i R_{a_i y}^T (s, z)
+  ST ph[12];
+#pragma unroll
+  for (int e = 0; e < 12; ++e) ph[e] = 0;
+  const int seg = seg_of_frame[f];
+  for (int i = lane; i < M; i += 32) {
+    ST gsv, gzv;
+    const ST qi = f64 ? (ST)q[i] : (ST)q32[i];
+    gammas<ST>(P[(size_t)f * M + i], lamw, qi, sf, gsv, gzv);
+    const ST* B = Bseg + ((size_t)seg * M + i) * 9;
+    ST A6[6];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) A6[e] = f64 ? (ST)A64[(size_t)i * 6 + e] : (ST)A32[(size_t)i * 6 + e];
+    const ST A[9] = {A6[0], A6[1], A6[2], A6[1], A6[3], A6[4], A6[2], A6[4], A6[5]};
+    ST BA[9];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) BA[3 * b + c] = B[3 * b] * A[c] + B[3 * b + 1] * A[3 + c] + B[3 * b + 2] * A[6 + c];
+    // symmetric S = BA B^T: xx xy xz yy yz zz
+    const int ib[6] = {0, 0, 0, 1, 1, 2}, ic[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      const int b = ib[e], c = ic[e];
+      const ST S = BA[3 * b] * B[3 * c] + BA[3 * b + 1] * B[3 * c + 1] + BA[3 * b + 2] * B[3 * c + 2];
+      ph[e] = fma(gsv, S, ph[e]);
+      ph[6 + e] = fma(gzv, S, ph[6 + e]);
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < 27; ++e) acc[e] = wsum(acc[e]);
+#pragma unroll
+  for (int e = 0; e < 12; ++e) ph[e] = wsum(ph[e]);
+  // every lane holds the totals; all lanes do the (tiny) 4x4 algebra
+  ST Ts[9], Tz[9];
+  {
+    const ST Ps[9] = {ph[0], ph[1], ph[2], ph[1], ph[3], ph[4], ph[2], ph[4], ph[5]};
+    const ST Pz[9] = {ph[6], ph[7], ph[8], ph[7], ph[9], ph[10], ph[8], ph[10], ph[11]};
+    adjoint_rotation_term<ST>(acc + 18, R, acc, Ps, Ts);
+    adjoint_rotation_term<ST>(acc + 18, R, acc + 9, Pz, Tz);
+  }
+  for (int j = lane; j < N; j += 32) {
+    const ST w = wt(j);
+    ST v[3], u[3], bsj[3], bzj[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      v[b] = (ST)x[3 * j + b] - cx[b];
+      u[b] = (ST)y[3 * j + b] - cy[b];
+      bsj[b] = bsp[3 * j + b];
+      bzj[b] = bzp[3 * j + b];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const ST Rbs = R[3 * c] * bsj[0] + R[3 * c + 1] * bsj[1] + R[3 * c + 2] * bsj[2];
+      const ST Rbz = R[3 * c] * bzj[0] + R[3 * c + 1] * bzj[1] + R[3 * c + 2] * bzj[2];
+      const ST ts = Ts[c] * u[0] + Ts[3 + c] * u[1] + Ts[6 + c] * u[2];
+      const ST tz = Tz[c] * u[0] + Tz[3 + c] * u[1] + Tz[6 + c] * u[2];
+      bsp[3 * j + c] = (ST)2 * w * (Gs * v[c] - Rbs) + w * ts;
+      bzp[3 * j + c] = (ST)2 * w * (Gz * v[c] - Rbz) + w * tz;
+    }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+void launch_adjoint_beta(Prec p, int F, const LandmarkDev& L, const void* P, const double* s, double lambda,
+                         const void* Rpair, const void* Bseg, const int* seg_of_frame, bool seg_form, void* gs,
+                         void* gz, cudaStream_t st) {
+  if (F <= 0) return;
+  if (seg_form && p != P_F64) {
+    dim3 grid((L.N + BS_TJ - 1) / BS_TJ, (F + BS_TF - 1) / BS_TF);
+    if (p == P_F32)
+      adjoint_beta_seg<float><<<grid, BS_THREADS, 0, st>>>(F, L.M, L.N, (const float*)L.coords, L.q32,
+                                                           (const float*)P, s, (float)lambda, (const float*)Bseg,
+                                                           seg_of_frame, (float*)gs, (float*)gz);
+    else
+      adjoint_beta_seg<__half><<<grid, BS_THREADS, 0, st>>>(F, L.M, L.N, (const __half*)L.coords, L.q32,
+                                                            (const float*)P, s, (float)lambda, (const float*)Bseg,
+                                                            seg_of_frame, (float*)gs, (float*)gz);
+    note_launch();
+    return;
+  }
+  dim3 grid((L.N + BP_TJ - 1) / BP_TJ, (F + BP_TF - 1) / BP_TF);
+  switch (p) {
+    case P_F64:
+      adjoint_beta_pair<double, double><<<grid, BP_THREADS, 0, st>>>(
+          F, L.M, L.N, (const double*)L.coords, L.q, L.q32, (const double*)P, s, lambda, (const double*)Rpair,
+          (const double*)Bseg, seg_of_frame, (double*)gs, (double*)gz);
+      break;
+    case P_F32:
+      adjoint_beta_pair<float, float><<<grid, BP_THREADS, 0, st>>>(
+          F, L.M, L.N, (const float*)L.coords, L.q, L.q32, (const float*)P, s, lambda, (const float*)Rpair,
+          (const float*)Bseg, seg_of_frame, (float*)gs, (float*)gz);
+      break;
+    case P_F16:
+      adjoint_beta_pair<float, __half><<<grid, BP_THREADS, 0, st>>>(
+          F, L.M, L.N, (const __half*)L.coords, L.q, L.q32, (const float*)P, s, lambda, (const float*)Rpair,
+          (const float*)Bseg, seg_of_frame, (float*)gs, (float*)gz);
+      break;
+  }
+  note_launch();
+}
+
+void launch_adjoint_finish(Prec p, int F, const void* frames, const LandmarkDev& L, FrameInfo fi, const void* P,
+                           const double* s, double lambda, const void* Bseg, const int* seg_of_frame,
+                           const FrameRec rec, const RefDesc& prior, void* gs, void* gz, cudaStream_t st) {
+  if (F <= 0) return;
+  const unsigned blocks = (unsigned)((F + 3) / 4);
+  if (p == P_F64)
+    adjoint_finish_warp<double, double><<<blocks, 128, 0, st>>>(
+        F, L.M, L.N, (const double*)frames, fi.c32, fi.c64, L.w, L.w64, L.A32, L.A, L.q, L.q32, L.dscale,
+        (const double*)P, s, lambda, (const double*)Bseg, seg_of_frame, rec, (const double*)prior.coords, prior.c64,
+        (double*)gs, (double*)gz);
+  else
+    adjoint_finish_warp<float, float><<<blocks, 128, 0, st>>>(
+        F, L.M, L.N, (const float*)frames, fi.c32, fi.c64, L.w, L.w64, L.A32, L.A, L.q, L.q32, L.dscale,
+        (const float*)P, s, lambda, (const float*)Bseg, seg_of_frame, rec, (const float*)prior.coords,
+        make_double4(prior.c32.x, prior.c32.y, prior.c32.z, 0.0), (float*)gs, (float*)gz);
+  note_launch();
+}
+
+}  // namespace pcv

@@ -2,8 +2,8 @@
 //   frame preparation (centres, sums of squares), frame-vs-structure alignments for the
 //   close-structure decision of Algorithm 2 (band of previous frames, speculative chunks,
 //   FP64 re-check of undecidable cases), the parallel refresh-search scan, compaction,
-//   path-CV finalisation (Eq. property_map_cv and z) and the adjoint of
-//   Eq. (der_dist) / Eq. (close_der_dist).
+//   path-CV finalisation (Eq. property_map_cv and z) and the chain-rule combination of
+//   the gradients.
 #include <cuda_fp16.h>
 
 #include "pcv_device.cuh"
@@ -45,14 +45,15 @@ __global__ void frame_prep_f32(int F, int N, const float* __restrict__ frames,
       }
     }
   }
-  double c[3];
+  // FP32 centre: any centre works as long as G is taken over the same staged values;
+  // FP64 per frame would cost ~16 SM cycles per warp instruction on this chip
+  float cf[3];
+  const float invn = 1.0f / (float)N;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     warp_sum_pair(hi[k], lo[k]);
-    c[k] = pair_to_double(hi[k], lo[k]);
-    if (!wts) c[k] /= (double)N;
+    cf[k] = wts ? hi[k] + lo[k] : (hi[k] + lo[k]) * invn;
   }
-  const float cf[3] = {(float)c[0], (float)c[1], (float)c[2]};
   float gh = 0.0f, gl = 0.0f;
   for (int j = lane; j < N; j += 32) {
 #pragma unroll
@@ -68,7 +69,6 @@ __global__ void frame_prep_f32(int F, int N, const float* __restrict__ frames,
   warp_sum_pair(gh, gl);
   if (lane == 0) {
     c32[f] = make_float4(cf[0], cf[1], cf[2], 0.0f);
-    c64[f] = make_double4(c[0], c[1], c[2], 0.0);
     G[f] = pair_to_double(gh, gl);
   }
 }
@@ -158,6 +158,46 @@ __device__ __forceinline__ void warp_corr_f32(int N, const float* __restrict__ x
   }
 }
 
+// as warp_corr_f32, returning the compensated sums rounded to FP32 (no FP64 instruction)
+__device__ __forceinline__ void warp_corr_pair_f32(int N, const float* __restrict__ x, float4 cx,
+                                                   const float* __restrict__ y, float4 cy,
+                                                   const float* __restrict__ wts, float* H) {
+  const int lane = threadIdx.x & 31;
+  float p[9], hi[9], lo[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) p[e] = hi[e] = lo[e] = 0.0f;
+  int cnt = 0;
+  for (int j = lane; j < N; j += 32) {
+    float u0 = y[3 * j] - cy.x, u1 = y[3 * j + 1] - cy.y, u2 = y[3 * j + 2] - cy.z;
+    const float v0 = x[3 * j] - cx.x, v1 = x[3 * j + 1] - cx.y, v2 = x[3 * j + 2] - cx.z;
+    if (wts) {
+      const float wj = wts[j];
+      u0 *= wj;
+      u1 *= wj;
+      u2 *= wj;
+    }
+    const float u[3] = {u0, u1, u2}, v[3] = {v0, v1, v2};
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) p[3 * b + c] = fmaf(u[b], v[c], p[3 * b + c]);
+    if (++cnt == 16) {
+      cnt = 0;
+#pragma unroll
+      for (int e = 0; e < 9; ++e) {
+        two_sum_acc(hi[e], lo[e], p[e]);
+        p[e] = 0.0f;
+      }
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    two_sum_acc(hi[e], lo[e], p[e]);
+    warp_sum_pair(hi[e], lo[e]);
+    H[e] = hi[e] + lo[e];
+  }
+}
+
 __device__ __forceinline__ void warp_corr_f64(int N, const double* __restrict__ x, double4 cx,
                                               const double* __restrict__ y, double4 cy,
                                               const double* __restrict__ w64, double* H) {
@@ -200,6 +240,55 @@ __device__ __forceinline__ void finish_alignment(const double* H, double Gx, dou
   *outFlag = (uint8_t)((D > eps ? 1 : 0) | (amb ? 2 : 0));
 }
 
+// FP32 decision alignment (one warp): pass 1 the correlation in FP32 and an FP32 eigen-
+// solve for R (fits y onto x); pass 2 D = sum_j w_j |x_j - R y_j|^2 directly.  Returns D in
+// true units on every lane together with a bound on |D - D_exact|:
+//   lane sums of ~N/32 positive terms and a 5-level tree: (N/32 + 8) u D;
+//   FP32 centring, rotation and residual rounding: <= 20 u sqrt(D (G_x + G_y));
+// times a safety factor of 4 (u = 2^-24).
+__device__ __forceinline__ double warp_direct_f32(int N, const float* __restrict__ x, float4 cx,
+                                                  const float* __restrict__ y, float4 cy, const float* __restrict__ wts,
+                                                  double Gx, double Gy, double dscale, double* bound) {
+  const int lane = threadIdx.x & 31;
+  float h[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) h[e] = 0.0f;
+  for (int j = lane; j < N; j += 32) {
+    float u[3] = {y[3 * j] - cy.x, y[3 * j + 1] - cy.y, y[3 * j + 2] - cy.z};
+    const float v[3] = {x[3 * j] - cx.x, x[3 * j + 1] - cx.y, x[3 * j + 2] - cx.z};
+    if (wts) {
+      const float wj = wts[j];
+      u[0] *= wj;
+      u[1] *= wj;
+      u[2] *= wj;
+    }
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) h[3 * b + c] = fmaf(u[b], v[c], h[3 * b + c]);
+  }
+#pragma unroll
+  for (int e = 0; e < 9; ++e) h[e] = warp_sum_float(h[e]);
+  float q[4], R[9];
+  top_quat_f32(h, (float)(0.5 * (Gx + Gy)) * 1.00001f + 1e-30f, q);
+  quat_to_rot(q, R);
+  float dsum = 0.0f;
+  for (int j = lane; j < N; j += 32) {
+    const float u0 = y[3 * j] - cy.x, u1 = y[3 * j + 1] - cy.y, u2 = y[3 * j + 2] - cy.z;
+    const float v0 = x[3 * j] - cx.x, v1 = x[3 * j + 1] - cx.y, v2 = x[3 * j + 2] - cx.z;
+    const float d0 = v0 - fmaf(R[0], u0, fmaf(R[1], u1, R[2] * u2));
+    const float d1 = v1 - fmaf(R[3], u0, fmaf(R[4], u1, R[5] * u2));
+    const float d2 = v2 - fmaf(R[6], u0, fmaf(R[7], u1, R[8] * u2));
+    const float t = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+    dsum = wts ? fmaf(wts[j], t, dsum) : dsum + t;
+  }
+  const double D = (double)warp_sum_float(dsum) * dscale;
+  const double u32 = 5.9604644775390625e-8;
+  const double G = (Gx + Gy) * dscale;
+  *bound = 4.0 * (((double)N / 32.0 + 8.0) * u32 * D + 20.0 * u32 * sqrt(fmax(D, 0.0) * G)) + 1e-30;
+  return D;
+}
+
 template <bool F64>
 __global__ void align_kernel(int mode, int F, int W, int t0, int t1, int ref_index, int N,
                              const void* __restrict__ frames_v, RefView prior,
@@ -212,10 +301,10 @@ __global__ void align_kernel(int mode, int F, int W, int t0, int t1, int ref_ind
   const int wid = warp_global();
   const int lane = threadIdx.x & 31;
   int t, ref, slot;
-  if (mode == 0) {  // band
-    t = 1 + wid / W;
+  if (mode == 0) {  // band rows t in [t0, t1)
+    t = t0 + wid / W;
     const int k = 1 + wid % W;
-    if (t >= F) return;
+    if (t >= t1) return;
     ref = t - k;
     slot = t * W + k - 1;
     if (ref < 0) {
@@ -231,27 +320,58 @@ __global__ void align_kernel(int mode, int F, int W, int t0, int t1, int ref_ind
     ref = ref_index;
     slot = t;
   }
-  double H[9];
   const double Gx = fG[t];
   const double Gy = ref >= 0 ? fG[ref] : prior.G;
   if (F64) {
+    double H[9];
     const double* frames = (const double*)frames_v;
     const double* y = ref >= 0 ? frames + (size_t)ref * N * 3 : (const double*)prior.coords;
     const double4 cy = ref >= 0 ? c64[ref] : prior.c64;
     warp_corr_f64(N, frames + (size_t)t * N * 3, c64[t], y, cy, w64, H);
+    if (lane == 0) {
+      bool amb = false;
+      finish_alignment(H, Gx, Gy, dscale, eps, false, outD + slot, outQ + slot, outFlag + slot, &amb);
+    }
   } else {
     const float* frames = (const float*)frames_v;
     const float* y = ref >= 0 ? frames + (size_t)ref * N * 3 : (const float*)prior.coords;
     const float4 cy = ref >= 0 ? c32[ref] : prior.c32;
-    warp_corr_f32(N, frames + (size_t)t * N * 3, c32[t], y, cy, wts, H);
-  }
-  if (lane == 0) {
-    bool amb = false;
-    finish_alignment(H, Gx, Gy, dscale, eps, !F64, outD + slot, outQ + slot, outFlag + slot, &amb);
-    if (amb) {
-      const int pos = atomicAdd(recheck_count, 1);
-      recheck_list[pos] = (slot << 1) | (mode == 0 ? 0 : 1);
+    double bound = 0.0;
+    const double D = warp_direct_f32(N, frames + (size_t)t * N * 3, c32[t], y, cy, wts, Gx, Gy, dscale, &bound);
+    if (lane == 0) {
+      const bool amb = fabs(D - eps) <= bound;
+      outD[slot] = D;
+      outFlag[slot] = (uint8_t)((D > eps ? 1 : 0) | (amb ? 2 : 0));
+      if (amb) {
+        const int pos = atomicAdd(recheck_count, 1);
+        recheck_list[pos] = (slot << 1) | (mode == 0 ? 0 : 1);
+      }
     }
+  }
+}
+
+// Accurate R_xy for the approximate frames (FP32 modes): compensated correlation, FP64
+// eigenvalue and FP64 eigenvector.  The approximate MSD of Eq. (close_dist) is not
+// stationary in R_xy, so R_xy must be accurate to FP32 rounding.  One warp per frame.
+__global__ void xy_refine_kernel(int F, int N, const float* __restrict__ frames, RefView prior,
+                                 const float4* __restrict__ c32, const double* __restrict__ fG,
+                                 const float* __restrict__ wts, double dscale, FrameRec rec) {
+  const int t = warp_global();
+  if (t >= F) return;
+  if (rec.flag[t] != 0) return;
+  const int lane = threadIdx.x & 31;
+  const int ref = rec.ref[t];
+  const float* y = ref >= 0 ? frames + (size_t)ref * N * 3 : (const float*)prior.coords;
+  const float4 cy = ref >= 0 ? c32[ref] : prior.c32;
+  float H[9];
+  warp_corr_pair_f32(N, frames + (size_t)t * N * 3, c32[t], y, cy, wts, H);
+  if (lane == 0) {
+    // H is accurate to ~1e-8 relative (compensated sums); the FP32 eigen-solve then gives
+    // q to ~u / (relative gap) ~ 1e-7 with no FP64 instruction
+    const float Gx = (float)fG[t], Gy = (float)(ref >= 0 ? fG[ref] : prior.G);
+    float q[4];
+    top_quat_f32(H, 0.5f * (Gx + Gy) * 1.00001f + 1e-30f, q);
+    rec.qxy[t] = make_double4(q[0], q[1], q[2], q[3]);
   }
 }
 
@@ -377,6 +497,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) band_scan_kernel(int F, int W, i
   __shared__ int s_stop;
   const int tid = threadIdx.x, lane = tid & 31, wrp = tid >> 5;
   unsigned s_in = (unsigned)o_init;
+  int nref = 0;
   for (int base = t0; base < F; base += SCAN_THREADS) {
     const int t = base + tid;
     unsigned m = (t < F) ? frame_map(bandFlag, t, W) : 0x76543210u;  // identity beyond F
@@ -421,11 +542,13 @@ __global__ void __launch_bounds__(SCAN_THREADS) band_scan_kernel(int F, int W, i
         rec.qxy[t] = bandQ[sl];
       }
     }
+    nref += __syncthreads_count(t < F && t < stop && after == 0);
     if (stop < F) {
       if (tid == 0) {
         // frame stop-1 had offset W from its close structure
         res->t_stop = stop;
         res->ref = stop - 1 - W;
+        res->nref = nref;
       }
       return;
     }
@@ -435,6 +558,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) band_scan_kernel(int F, int W, i
   if (tid == 0) {
     res->t_stop = F;
     res->ref = -2;
+    res->nref = nref;
   }
 }
 
@@ -532,42 +656,48 @@ __global__ void __launch_bounds__(SCAN_THREADS) compact_kernel(int F, const uint
 // Path CVs: m = min D, l = sum exp(-lambda (D - m)), s = sum q e / l, z = m - ln(l)/lambda.
 // FP32 modes: exponentials in FP32 (relative error ~1e-7, far inside the tolerance),
 // lane partials combined in FP64.  One warp per frame.
-__global__ void finalize_f32(int F, int M, const float* __restrict__ D, const double* __restrict__ q,
-                             double lambda, double* __restrict__ s, double* __restrict__ z,
-                             float* __restrict__ mstat, double* __restrict__ msd) {
+// With want_p the distances are overwritten by the softmax weights p_i = exp(-lambda (D_i -
+// m)) / l that the adjoint consumes (gamma^z_i = p_i, gamma^s_i = -lambda p_i (q_i - s)).
+__global__ void finalize_f32(int F, int M, float* __restrict__ D, const float* __restrict__ q, float lambda,
+                             double* __restrict__ s, double* __restrict__ z, float* __restrict__ mstat,
+                             double* __restrict__ msd, int want_p) {
   const int f = warp_global();
   if (f >= F) return;
   const int lane = threadIdx.x & 31;
-  const float* d = D + (size_t)f * M;
+  float* d = D + (size_t)f * M;
   float m = 3.4e38f;
   for (int i = lane; i < M; i += 32) m = fminf(m, d[i]);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, off));
-  const float lf = (float)lambda;
+  // l >= 1 and every term is in (0, 1]: FP32 sums are accurate to ~1e-7 relative
   float l = 0.0f, sq = 0.0f;
   for (int i = lane; i < M; i += 32) {
-    const float e = expf(-lf * (d[i] - m));
+    const float e = expf(-lambda * (d[i] - m));
     l += e;
-    sq = fmaf((float)q[i], e, sq);
+    sq = fmaf(q[i], e, sq);
     if (msd) msd[(size_t)f * M + i] = (double)d[i];
   }
-  const double L = warp_sum_double((double)l);
-  const double SQ = warp_sum_double((double)sq);
+  l = warp_sum_float(l);
+  sq = warp_sum_float(sq);
+  if (want_p) {
+    const float il = 1.0f / l;
+    for (int i = lane; i < M; i += 32) d[i] = expf(-lambda * (d[i] - m)) * il;
+  }
   if (lane == 0) {
-    s[f] = SQ / L;
-    z[f] = (double)m - log(L) / lambda;
+    s[f] = (double)(sq / l);
+    z[f] = (double)(m - __logf(l) / lambda);
     mstat[2 * f] = m;
-    mstat[2 * f + 1] = (float)L;
+    mstat[2 * f + 1] = l;
   }
 }
 
-__global__ void finalize_f64(int F, int M, const double* __restrict__ D, const double* __restrict__ q,
+__global__ void finalize_f64(int F, int M, double* __restrict__ D, const double* __restrict__ q,
                              double lambda, double* __restrict__ s, double* __restrict__ z,
-                             double* __restrict__ mstat64, double* __restrict__ msd) {
+                             double* __restrict__ mstat64, double* __restrict__ msd, int want_p) {
   const int f = warp_global();
   if (f >= F) return;
   const int lane = threadIdx.x & 31;
-  const double* d = D + (size_t)f * M;
+  double* d = D + (size_t)f * M;
   double m = 1.0e300;
   for (int i = lane; i < M; i += 32) m = fmin(m, d[i]);
 #pragma unroll
@@ -581,344 +711,13 @@ __global__ void finalize_f64(int F, int M, const double* __restrict__ D, const d
   }
   l = warp_sum_double(l);
   sq = warp_sum_double(sq);
+  if (want_p)
+    for (int i = lane; i < M; i += 32) d[i] = exp(-lambda * (d[i] - m)) / l;
   if (lane == 0) {
     s[f] = sq / l;
     z[f] = m - log(l) / lambda;
     mstat64[2 * f] = m;
     mstat64[2 * f + 1] = l;
-  }
-}
-
-// ---------------------------------------------------------------------------------------
-// Adjoint.  For L = s and L = z, dL/dD_i = gamma_i with p_i = exp(-lambda (D_i - m))/l:
-// gamma^z_i = p_i, gamma^s_i = -lambda p_i (q_i - s).  The direct part of Eq. (der_dist)
-// summed over landmarks is 2 w_k ((sum_i gamma_i) x_k - beta_k) with
-// beta_k = sum_i gamma_i Rot_i a_ik: a (3F x 3M)(3M x N) contraction computed here, with
-// Rot_i = R_{a_i x} (exact) or R_{a_i y} (close structure, R_{xy} applied afterwards).
-constexpr int AB_TF = 32, AB_TJ = 64, AB_KL = 8, AB_THREADS = 128;
-
-template <typename ST, typename LT>
-__device__ __forceinline__ ST lm_load(const LT* p) {
-  return (ST)(*p);
-}
-template <>
-__device__ __forceinline__ float lm_load<float, __half>(const __half* p) {
-  return __half2float(*p);
-}
-
-template <typename ST, typename LT, typename MT>
-__global__ void __launch_bounds__(AB_THREADS)
-adjoint_beta_kernel(int F, int M, int N, const LT* __restrict__ lm, const double* __restrict__ q,
-                    const ST* __restrict__ D, const MT* __restrict__ mstat, const double* __restrict__ s,
-                    double lambda, const ST* __restrict__ Rpair, const ST* __restrict__ Bseg,
-                    const int* __restrict__ seg_of_frame, ST* __restrict__ gs, ST* __restrict__ gz) {
-  // thread: 2 frames (ty) x 8 atoms (tx); CTA: 32 frames x 64 atoms
-  __shared__ __align__(16) ST Ws[AB_KL * 3][AB_TF * 3];  // W^s[(i,c)][(f,b)] = gamma^s_fi Rot_fi[b][c]
-  __shared__ __align__(16) ST Wz[AB_KL * 3][AB_TF * 3];
-  __shared__ __align__(16) ST As[AB_KL * 3][AB_TJ];      // a_ij[c]
-  const int f0 = blockIdx.y * AB_TF, j0 = blockIdx.x * AB_TJ;
-  const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
-  ST bs[2][3][8], bz[2][3][8];
-#pragma unroll
-  for (int u = 0; u < 2; ++u)
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-      for (int k = 0; k < 8; ++k) bs[u][b][k] = bz[u][b][k] = 0;
-
-  for (int i0 = 0; i0 < M; i0 += AB_KL) {
-    // weights W for (frame, landmark) pairs of this chunk
-    for (int e = tid; e < AB_TF * AB_KL; e += AB_THREADS) {
-      const int ff = e / AB_KL, ii = e - ff * AB_KL;
-      const int f = f0 + ff, i = i0 + ii;
-      ST rot[9];
-      ST gsv = 0, gzv = 0;
-#pragma unroll
-      for (int c = 0; c < 9; ++c) rot[c] = 0;
-      if (f < F && i < M) {
-        const double m = (double)mstat[2 * f], l = (double)mstat[2 * f + 1];
-        const double p = exp(-lambda * ((double)D[(size_t)f * M + i] - m)) / l;
-        gzv = (ST)p;
-        gsv = (ST)(-lambda * p * (q[i] - s[f]));
-        const ST* R = Rpair ? Rpair + ((size_t)f * M + i) * 9 : Bseg + ((size_t)seg_of_frame[f] * M + i) * 9;
-#pragma unroll
-        for (int c = 0; c < 9; ++c) rot[c] = R[c];
-      }
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          Ws[ii * 3 + c][ff * 3 + b] = gsv * rot[3 * b + c];
-          Wz[ii * 3 + c][ff * 3 + b] = gzv * rot[3 * b + c];
-        }
-    }
-    for (int e = tid; e < AB_KL * AB_TJ; e += AB_THREADS) {
-      const int ii = e / AB_TJ, jj = e - ii * AB_TJ;
-      const int i = i0 + ii, j = j0 + jj;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) As[ii * 3 + c][jj] = (i < M && j < N) ? lm_load<ST>(lm + ((size_t)i * N + j) * 3 + c) : (ST)0;
-    }
-    __syncthreads();
-#pragma unroll 2
-    for (int kk = 0; kk < AB_KL * 3; ++kk) {
-      ST a[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) a[k] = As[kk][tx * 8 + k];
-#pragma unroll
-      for (int u = 0; u < 2; ++u)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          const ST ws = Ws[kk][(ty * 2 + u) * 3 + b];
-          const ST wz = Wz[kk][(ty * 2 + u) * 3 + b];
-#pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            bs[u][b][k] = fma(ws, a[k], bs[u][b][k]);
-            bz[u][b][k] = fma(wz, a[k], bz[u][b][k]);
-          }
-        }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int u = 0; u < 2; ++u) {
-    const int f = f0 + ty * 2 + u;
-    if (f >= F) continue;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int j = j0 + tx * 8 + k;
-      if (j >= N) continue;
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        gs[((size_t)f * N + j) * 3 + b] = bs[u][b][k];
-        gz[((size_t)f * N + j) * 3 + b] = bz[u][b][k];
-      }
-    }
-  }
-}
-
-// block-wide FP64 sum of per-thread values (blockDim.x == 128)
-__device__ __forceinline__ double block_sum128(double v, double* scratch) {
-  v = warp_sum_double(v);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) scratch[w] = v;
-  __syncthreads();
-  return scratch[0] + scratch[1] + scratch[2] + scratch[3];
-}
-
-// Per-frame finish: from beta (in gs/gz) to ds/dx and dz/dx.
-//  exact / reassignment frames: ds/dx_k = -2 w_k beta^s_k, dz/dx_k = 2 w_k (x_k - beta^z_k);
-//  approximate frames (beta in the close-structure frame): the direct term uses R_xy beta,
-//  plus the rotation term sum_ab Ghat_ab dR_xy,ab/dx_k of Eq. (close_der_dist).  With
-//  Ghat = -2 (sum_j w_j x_j beta_j^T - R_xy Phi), Phi = sum_i gamma_i R_{a_i y} A_i
-//  R_{a_i y}^T (A_i = sum_j w_j a_ij a_ij^T), the rotation term is w_k T^T y_k with
-//  T_bc = p^T K(E_bc) q0, where q0 is the top eigenvector of K(H_xy) (eigenvalue l0) and
-//  p solves (l0 I - K + q0 q0^T) p = g - (q0.g) q0, g = 2 K(Ghat^T) q0 (first-order
-//  eigenvector perturbation).
-template <typename ST, typename FT>
-__global__ void __launch_bounds__(128)
-adjoint_finish_kernel(int F, int M, int N, const FT* __restrict__ frames, const float4* __restrict__ c32,
-                      const double4* __restrict__ c64, const float* __restrict__ wts,
-                      const double* __restrict__ w64, const double* __restrict__ LA,
-                      const double* __restrict__ q, double dscale, const ST* __restrict__ D,
-                      const float* __restrict__ mstat, const double* __restrict__ mstat64,
-                      const double* __restrict__ s, double lambda, const ST* __restrict__ Bseg,
-                      const int* __restrict__ seg_of_frame, FrameRec rec, RefView prior,
-                      ST* __restrict__ gs, ST* __restrict__ gz, unsigned* __restrict__ status) {
-  const int f = blockIdx.x;
-  if (f >= F) return;
-  const int tid = threadIdx.x;
-  __shared__ double scratch[4];
-  __shared__ double s_T[2][9];  // rotation-term matrices T^s, T^z
-  __shared__ double s_R[9];     // R_xy
-  __shared__ double s_yc[3];
-  const bool approx = rec.flag && rec.flag[f] == 0;
-  const bool f64 = sizeof(ST) == 8;
-  double cx[3];
-  if (f64) {
-    const double4 c = c64[f];
-    cx[0] = c.x; cx[1] = c.y; cx[2] = c.z;
-  } else {
-    const float4 c = c32[f];
-    cx[0] = c.x; cx[1] = c.y; cx[2] = c.z;
-  }
-  const FT* x = frames + (size_t)f * N * 3;
-  auto wt = [&](int j) -> double { return f64 ? (w64 ? w64[j] : dscale) : (wts ? (double)wts[j] : dscale); };
-
-  if (!approx) {
-    for (int j = tid; j < N; j += 128) {
-      const double w = wt(j);
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        const size_t idx = ((size_t)f * N + j) * 3 + b;
-        const ST v = (ST)x[3 * j + b] - (ST)cx[b];
-        gs[idx] = (ST)(-2.0 * w * (double)gs[idx]);
-        gz[idx] = (ST)(2.0 * w * (double)(v - gz[idx]));
-      }
-    }
-    return;
-  }
-
-  // ---- approximate frame ----
-  const int r = rec.ref[f];
-  const FT* y = r >= 0 ? frames + (size_t)r * N * 3 : (const FT*)prior.coords;
-  double cy[3];
-  if (r >= 0) {
-    if (f64) { const double4 c = c64[r]; cy[0] = c.x; cy[1] = c.y; cy[2] = c.z; }
-    else { const float4 c = c32[r]; cy[0] = c.x; cy[1] = c.y; cy[2] = c.z; }
-  } else {
-    if (f64) { cy[0] = prior.c64.x; cy[1] = prior.c64.y; cy[2] = prior.c64.z; }
-    else { cy[0] = prior.c32.x; cy[1] = prior.c32.y; cy[2] = prior.c32.z; }
-  }
-  if (tid == 0) {
-    const double4 qq = rec.qxy[f];
-    const double qd[4] = {qq.x, qq.y, qq.z, qq.w};
-    quat_to_rot(qd, s_R);
-  }
-  __syncthreads();
-  // X = sum_j w_j x_j beta_j^T (s and z) and H_xy = sum_j w_j y_j x_j^T, true weights
-  double Xs[9], Xz[9], Hy[9];
-#pragma unroll
-  for (int e = 0; e < 9; ++e) Xs[e] = Xz[e] = Hy[e] = 0.0;
-  for (int j = tid; j < N; j += 128) {
-    const double w = wt(j);
-    double v[3], u[3], bsj[3], bzj[3];
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      v[b] = (double)((ST)x[3 * j + b] - (ST)cx[b]);
-      u[b] = (double)((ST)y[3 * j + b] - (ST)cy[b]);
-      const size_t idx = ((size_t)f * N + j) * 3 + b;
-      bsj[b] = (double)gs[idx];
-      bzj[b] = (double)gz[idx];
-    }
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        Xs[3 * b + c] += w * v[b] * bsj[c];
-        Xz[3 * b + c] += w * v[b] * bzj[c];
-        Hy[3 * b + c] += w * u[b] * v[c];
-      }
-  }
-#pragma unroll
-  for (int e = 0; e < 9; ++e) {
-    Xs[e] = block_sum128(Xs[e], scratch);
-    Xz[e] = block_sum128(Xz[e], scratch);
-    Hy[e] = block_sum128(Hy[e], scratch);
-  }
-  // Phi = sum_i gamma_i B_i A_i B_i^T
-  double Ps[9], Pz[9];
-#pragma unroll
-  for (int e = 0; e < 9; ++e) Ps[e] = Pz[e] = 0.0;
-  const int seg = seg_of_frame[f];
-  const double mm = f64 ? mstat64[2 * f] : (double)mstat[2 * f];
-  const double ll = f64 ? mstat64[2 * f + 1] : (double)mstat[2 * f + 1];
-  for (int i = tid; i < M; i += 128) {
-    const double p = exp(-lambda * ((double)D[(size_t)f * M + i] - mm)) / ll;
-    const double gzv = p, gsv = -lambda * p * (q[i] - s[f]);
-    const ST* B = Bseg + ((size_t)seg * M + i) * 9;
-    const double* A6 = LA + (size_t)i * 6;
-    const double A[9] = {A6[0], A6[1], A6[2], A6[1], A6[3], A6[4], A6[2], A6[4], A6[5]};
-    double BA[9];
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        BA[3 * b + c] = (double)B[3 * b] * A[c] + (double)B[3 * b + 1] * A[3 + c] + (double)B[3 * b + 2] * A[6 + c];
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const double S = BA[3 * b] * (double)B[3 * c] + BA[3 * b + 1] * (double)B[3 * c + 1] + BA[3 * b + 2] * (double)B[3 * c + 2];
-        Ps[3 * b + c] += gsv * S;
-        Pz[3 * b + c] += gzv * S;
-      }
-  }
-#pragma unroll
-  for (int e = 0; e < 9; ++e) {
-    Ps[e] = block_sum128(Ps[e], scratch);
-    Pz[e] = block_sum128(Pz[e], scratch);
-  }
-  if (tid == 0) {
-    // eigen-decomposition data of K(H_xy) in true units
-    double K[16];
-    quat_matrix(Hy, K);
-    double Gx = 0.0, Gy = 0.0;  // upper bound from the trace-free structure: use |K| bound
-    // lambda_max via Newton from an upper bound: the largest absolute row sum of K
-    double ub = 0.0;
-    for (int a = 0; a < 4; ++a) {
-      double rs = 0.0;
-      for (int b = 0; b < 4; ++b) rs += fabs(K[4 * a + b]);
-      ub = fmax(ub, rs);
-    }
-    (void)Gx;
-    (void)Gy;
-    bool ok = true;
-    const double l0 = lambda_max_newton(Hy, ub, &ok);
-    if (!ok) atomicOr(status, STATUS_NOCONV);
-    double q0[4];
-    adj_eigvec_f64(K, l0, q0);
-    double Amat[16];
-    for (int a = 0; a < 4; ++a)
-      for (int b = 0; b < 4; ++b) Amat[4 * a + b] = (a == b ? l0 : 0.0) - K[4 * a + b] + q0[a] * q0[b];
-    for (int which = 0; which < 2; ++which) {
-      const double* X = which == 0 ? Xs : Xz;
-      const double* P = which == 0 ? Ps : Pz;
-      // Ghat = -2 (X - R_xy Phi)
-      double Gh[9];
-      for (int b = 0; b < 3; ++b)
-        for (int c = 0; c < 3; ++c)
-          Gh[3 * b + c] = -2.0 * (X[3 * b + c] - (s_R[3 * b] * P[c] + s_R[3 * b + 1] * P[3 + c] + s_R[3 * b + 2] * P[6 + c]));
-      double GhT[9];
-      for (int b = 0; b < 3; ++b)
-        for (int c = 0; c < 3; ++c) GhT[3 * b + c] = Gh[3 * c + b];
-      double KG[16];
-      quat_matrix(GhT, KG);
-      double g[4];
-      for (int a = 0; a < 4; ++a) {
-        g[a] = 0.0;
-        for (int b = 0; b < 4; ++b) g[a] += 2.0 * KG[4 * a + b] * q0[b];
-      }
-      const double gq = g[0] * q0[0] + g[1] * q0[1] + g[2] * q0[2] + g[3] * q0[3];
-      for (int a = 0; a < 4; ++a) g[a] -= gq * q0[a];
-      double pv[4] = {0, 0, 0, 0};
-      if (!spd_solve4(Amat, g, pv)) atomicOr(status, STATUS_NOCONV);
-      // T_bc = p^T K(E_bc) q0
-      for (int b = 0; b < 3; ++b)
-        for (int c = 0; c < 3; ++c) {
-          double E[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-          E[3 * b + c] = 1.0;
-          double KE[16];
-          quat_matrix(E, KE);
-          double t = 0.0;
-          for (int a = 0; a < 4; ++a)
-            for (int d = 0; d < 4; ++d) t += pv[a] * KE[4 * a + d] * q0[d];
-          s_T[which][3 * b + c] = t;
-        }
-    }
-  }
-  __syncthreads();
-  for (int j = tid; j < N; j += 128) {
-    const double w = wt(j);
-    double v[3], u[3], bsj[3], bzj[3];
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      v[b] = (double)((ST)x[3 * j + b] - (ST)cx[b]);
-      u[b] = (double)((ST)y[3 * j + b] - (ST)cy[b]);
-      const size_t idx = ((size_t)f * N + j) * 3 + b;
-      bsj[b] = (double)gs[idx];
-      bzj[b] = (double)gz[idx];
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const double Rbs = s_R[3 * c] * bsj[0] + s_R[3 * c + 1] * bsj[1] + s_R[3 * c + 2] * bsj[2];
-      const double Rbz = s_R[3 * c] * bzj[0] + s_R[3 * c + 1] * bzj[1] + s_R[3 * c + 2] * bzj[2];
-      const double Ts = s_T[0][c] * u[0] + s_T[0][3 + c] * u[1] + s_T[0][6 + c] * u[2];
-      const double Tz = s_T[1][c] * u[0] + s_T[1][3 + c] * u[1] + s_T[1][6 + c] * u[2];
-      const size_t idx = ((size_t)f * N + j) * 3 + c;
-      gs[idx] = (ST)(-2.0 * w * Rbs + w * Ts);
-      gz[idx] = (ST)(2.0 * w * (v[c] - Rbz) + w * Tz);
-    }
   }
 }
 
@@ -957,20 +756,24 @@ void launch_frame_prep(Prec p, int F, const void* frames, const LandmarkDev& L, 
                                                             fi.G); note_launch();
 }
 
-void launch_align_band(Prec p, int F, int W, const void* frames, const LandmarkDev& L, FrameInfo fi,
-                       double eps, AlignOut out, int* recheck_list, int* recheck_count, cudaStream_t st) {
-  if (F <= 1) return;
-  const size_t warps = (size_t)(F - 1) * W;
+void launch_align_band(Prec p, int F, int W, int t_lo, int t_hi, const void* frames, const LandmarkDev& L,
+                       FrameInfo fi, double eps, AlignOut out, int* recheck_list, int* recheck_count,
+                       cudaStream_t st) {
+  t_lo = t_lo < 1 ? 1 : t_lo;
+  if (t_hi > F) t_hi = F;
+  if (t_hi <= t_lo) return;
+  const size_t warps = (size_t)(t_hi - t_lo) * W;
   const unsigned blocks = blocks_for(warps, WARPS_PER_BLOCK);
   RefView none{nullptr, make_float4(0, 0, 0, 0), make_double4(0, 0, 0, 0), 0.0};
   if (p == P_F64)
-    align_kernel<true><<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(0, F, W, 0, 0, 0, L.N, frames, none, fi.c32, fi.c64,
-                                                                fi.G, L.w, L.w64, L.dscale, eps, out.D, out.q,
+    align_kernel<true><<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(0, F, W, t_lo, t_hi, 0, L.N, frames, none, fi.c32,
+                                                                fi.c64, fi.G, L.w, L.w64, L.dscale, eps, out.D, out.q,
                                                                 out.flag, recheck_list, recheck_count);
   else
-    align_kernel<false><<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(0, F, W, 0, 0, 0, L.N, frames, none, fi.c32,
-                                                                 fi.c64, fi.G, L.w, L.w64, L.dscale, eps, out.D,
-                                                                 out.q, out.flag, recheck_list, recheck_count); note_launch();
+    align_kernel<false><<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(0, F, W, t_lo, t_hi, 0, L.N, frames, none, fi.c32,
+                                                                 fi.c64, fi.G, L.w, L.w64, L.dscale, eps, out.D, out.q,
+                                                                 out.flag, recheck_list, recheck_count);
+  note_launch();
 }
 
 void launch_align_chunk(Prec p, int t0, int t1, const void* frames, const LandmarkDev& L, FrameInfo fi,
@@ -998,6 +801,14 @@ void launch_recheck(Prec p, int max_entries, const int* list, const int* count, 
   recheck_kernel<<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(list, count, W, L.N, (const float*)frames,
                                                           view_of(prior), chunk_ref, L.w64, L.dscale, eps, band.D,
                                                           band.flag, chunk.D, chunk.flag, n_rechecks); note_launch();
+}
+
+void launch_xy_refine(Prec p, int F, const void* frames, const LandmarkDev& L, FrameInfo fi, const RefDesc& prior,
+                      FrameRec rec, cudaStream_t st) {
+  if (p == P_F64 || F <= 0) return;
+  xy_refine_kernel<<<blocks_for((size_t)F, WARPS_PER_BLOCK), 32 * WARPS_PER_BLOCK, 0, st>>>(
+      F, L.N, (const float*)frames, view_of(prior), fi.c32, fi.G, L.w, L.dscale, rec);
+  note_launch();
 }
 
 void launch_set_int(int* p, int v, cudaStream_t st) { set_int_kernel<<<1, 1, 0, st>>>(p, v); note_launch(); }
@@ -1028,55 +839,17 @@ void launch_compact(int F, const FrameRec rec, int* refresh_list, int* refresh_c
                                              approx_count, approx_seg, prior_seg); note_launch();
 }
 
-void launch_finalize(Prec p, int F, int M, const void* D, const double* q, double lambda, double* s, double* z,
-                     float* mstat, double* mstat64, double* msd_out, cudaStream_t st) {
+void launch_finalize(Prec p, int F, int M, void* D, const double* q, const float* q32, double lambda, double* s,
+                     double* z, float* mstat, double* mstat64, double* msd_out, bool want_p, cudaStream_t st) {
   if (F <= 0) return;
   const unsigned blocks = blocks_for((size_t)F, WARPS_PER_BLOCK);
   if (p == P_F64)
-    finalize_f64<<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(F, M, (const double*)D, q, lambda, s, z, mstat64,
-                                                          msd_out);
+    finalize_f64<<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(F, M, (double*)D, q, lambda, s, z, mstat64, msd_out,
+                                                          want_p ? 1 : 0);
   else
-    finalize_f32<<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(F, M, (const float*)D, q, lambda, s, z, mstat, msd_out); note_launch();
-}
-
-void launch_adjoint_beta(Prec p, int F, const LandmarkDev& L, const void* D, const float* mstat, const double* s,
-                         double lambda, const void* Rpair, const void* Bseg, const int* seg_of_frame, void* gs,
-                         void* gz, cudaStream_t st) {
-  if (F <= 0) return;
-  dim3 grid((L.N + AB_TJ - 1) / AB_TJ, (F + AB_TF - 1) / AB_TF);
-  switch (p) {
-    case P_F64:
-      adjoint_beta_kernel<double, double, double><<<grid, AB_THREADS, 0, st>>>(
-          F, L.M, L.N, (const double*)L.coords, L.q, (const double*)D, (const double*)(const void*)mstat, s, lambda,
-          (const double*)Rpair, (const double*)Bseg, seg_of_frame, (double*)gs, (double*)gz); note_launch();
-      break;
-    case P_F32:
-      adjoint_beta_kernel<float, float, float><<<grid, AB_THREADS, 0, st>>>(
-          F, L.M, L.N, (const float*)L.coords, L.q, (const float*)D, mstat, s, lambda, (const float*)Rpair,
-          (const float*)Bseg, seg_of_frame, (float*)gs, (float*)gz); note_launch();
-      break;
-    case P_F16:
-      adjoint_beta_kernel<float, __half, float><<<grid, AB_THREADS, 0, st>>>(
-          F, L.M, L.N, (const __half*)L.coords, L.q, (const float*)D, mstat, s, lambda, (const float*)Rpair,
-          (const float*)Bseg, seg_of_frame, (float*)gs, (float*)gz); note_launch();
-      break;
-  }
-}
-
-void launch_adjoint_finish(Prec p, int F, const void* frames, const LandmarkDev& L, FrameInfo fi, const void* D,
-                           const float* mstat, const double* s, double lambda, const void* Bseg,
-                           const int* seg_of_frame, const FrameRec rec, const RefDesc& prior, void* gs, void* gz,
-                           unsigned* status, cudaStream_t st) {
-  if (F <= 0) return;
-  if (p == P_F64)
-    adjoint_finish_kernel<double, double><<<F, 128, 0, st>>>(
-        F, L.M, L.N, (const double*)frames, fi.c32, fi.c64, L.w, L.w64, L.A, L.q, L.dscale, (const double*)D,
-        nullptr, (const double*)(const void*)mstat, s, lambda, (const double*)Bseg, seg_of_frame, rec,
-        view_of(prior), (double*)gs, (double*)gz, status);
-  else
-    adjoint_finish_kernel<float, float><<<F, 128, 0, st>>>(
-        F, L.M, L.N, (const float*)frames, fi.c32, fi.c64, L.w, L.w64, L.A, L.q, L.dscale, (const float*)D, mstat,
-        nullptr, s, lambda, (const float*)Bseg, seg_of_frame, rec, view_of(prior), (float*)gs, (float*)gz, status); note_launch();
+    finalize_f32<<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(F, M, (float*)D, q32, (float)lambda, s, z, mstat, msd_out,
+                                                          want_p ? 1 : 0);
+  note_launch();
 }
 
 void launch_combine_grad(Prec p, int F, int N3, const double* g_s, const double* g_z, const void* gs,

@@ -49,7 +49,7 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 // given.  One warp per landmark.
 __global__ void prep_landmarks_noalloc(int M, int N, const float* __restrict__ in, float* __restrict__ out,
                                        double* __restrict__ G, const double* __restrict__ q_in,
-                                       double* __restrict__ q_out) {
+                                       double* __restrict__ q_out, float* __restrict__ q_out32) {
   const int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   if (i >= M) return;
   const int lane = threadIdx.x & 31;
@@ -73,6 +73,7 @@ __global__ void prep_landmarks_noalloc(int M, int N, const float* __restrict__ i
   if (lane == 0) {
     G[i] = g;
     q_out[i] = q_in ? q_in[i] : (double)(i + 1);
+    q_out32[i] = (float)q_out[i];
   }
 }
 
@@ -96,13 +97,14 @@ extern "C" PCV_API pcv_status pcv_evaluate_exact_noalloc(int F, int M, int N, co
   const size_t b_lm = align256((size_t)M * N * 3 * sizeof(float));
   const size_t b_G = align256((size_t)M * sizeof(double));
   const size_t b_q = align256((size_t)M * sizeof(double));
+  const size_t b_q32 = align256((size_t)M * sizeof(float));
   const size_t b_c32 = align256((size_t)F * sizeof(float4));
   const size_t b_c64 = align256((size_t)F * sizeof(double4));
   const size_t b_fG = align256((size_t)F * sizeof(double));
   const size_t b_D = align256((size_t)F * M * sizeof(float));
   const size_t b_ms = align256((size_t)F * 2 * sizeof(double));
   const size_t b_st = 256;
-  const size_t need = b_lm + b_G + b_q + b_c32 + b_c64 + b_fG + b_D + b_ms + b_st;
+  const size_t need = b_lm + b_G + b_q + b_q32 + b_c32 + b_c64 + b_fG + b_D + b_ms + b_st;
   if (need > kScratchBytes) {
     char msg[160];
     snprintf(msg, sizeof(msg), "problem needs %zu bytes of scratch, more than the fixed %zu (reduce F or M)", need,
@@ -121,6 +123,8 @@ extern "C" PCV_API pcv_status pcv_evaluate_exact_noalloc(int F, int M, int N, co
   p += b_G;
   double* qs = (double*)p;
   p += b_q;
+  float* qs32 = (float*)p;
+  p += b_q32;
   pcv::FrameInfo fi;
   fi.c32 = (float4*)p;
   p += b_c32;
@@ -137,17 +141,18 @@ extern "C" PCV_API pcv_status pcv_evaluate_exact_noalloc(int F, int M, int N, co
   cudaStream_t st = (cudaStream_t)cuda_stream;
   // the status word must start at zero: the scratch keeps the previous call's contents
   if ((e = cudaMemsetAsync(status, 0, sizeof(unsigned), st)) != cudaSuccess) return fail(PCV_ECUDA, cudaGetErrorString(e));
-  prep_landmarks_noalloc<<<(unsigned)((M + 3) / 4), 128, 0, st>>>(M, N, landmarks, lm, G, q, qs);
+  prep_landmarks_noalloc<<<(unsigned)((M + 3) / 4), 128, 0, st>>>(M, N, landmarks, lm, G, q, qs, qs32);
   pcv::LandmarkDev L;
   L.M = M;
   L.N = N;
   L.coords = lm;
   L.G = G;
   L.q = qs;
+  L.q32 = qs32;
   L.dscale = 1.0 / N;
   pcv::launch_frame_prep(pcv::P_F32, F, frames, L, fi, st);
   pcv::launch_exact_pairs(pcv::P_F32, F, nullptr, nullptr, frames, L, fi, D, nullptr, status, st);
-  pcv::launch_finalize(pcv::P_F32, F, M, D, qs, lambda, s, z, mstat, nullptr, msd, st);
+  pcv::launch_finalize(pcv::P_F32, F, M, D, qs, qs32, lambda, s, z, mstat, nullptr, msd, false, st);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail(PCV_ECUDA, cudaGetErrorString(e));
   unsigned h_status = 0;
   if ((e = cudaMemcpyAsync(&h_status, status, sizeof(unsigned), cudaMemcpyDeviceToHost, st)) != cudaSuccess)

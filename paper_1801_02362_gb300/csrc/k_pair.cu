@@ -229,6 +229,7 @@ exact_pair_f32(int rows, const int* __restrict__ row_frame, const float* __restr
     }
 
   // per-chunk FP32 partials, added into an error-free (hi, lo) total after each chunk
+  const float dsf = (float)dscale;
   float acc[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
   float thi[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}}, tlo[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
   for (int j0 = 0; j0 < N; j0 += KC) {
@@ -271,7 +272,7 @@ exact_pair_f32(int rows, const int* __restrict__ row_frame, const float* __restr
       const int f = s_frame[ty * 2 + u];
       const int i = i0 + tx * 2 + v;
       if (f < 0 || i >= M) continue;
-      Dout[(size_t)f * M + i] = (float)(pair_to_double(thi[u][v], tlo[u][v]) * dscale);
+      Dout[(size_t)f * M + i] = (thi[u][v] + tlo[u][v]) * dsf;
       if (Rout) {
         float* dst = Rout + ((size_t)r * M + i) * 9;
 #pragma unroll
@@ -384,6 +385,7 @@ approx_pair_kernel(const int* __restrict__ alist, const int* __restrict__ aseg,
   const int count = *acount;
   const int row0 = blockIdx.y * TF;
   if (row0 >= count) return;
+  const ST dsc = (ST)dscale;
   const int i0 = blockIdx.x * TM;
   const int tid = threadIdx.x;
   const int tx = tid & 7;   // landmarks i0 + 4 tx + {0..3}
@@ -536,7 +538,7 @@ approx_pair_kernel(const int* __restrict__ alist, const int* __restrict__ aseg,
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         const int i = i0 + tx * 4 + v;
-        if (i < M) Dout[(size_t)f * M + i] = (ST)(((double)thi[u][v] + (double)tlo[u][v]) * dscale);
+        if (i < M) Dout[(size_t)f * M + i] = (thi[u][v] + tlo[u][v]) * dsc;
       }
     }
     k = kend;

@@ -55,11 +55,12 @@ thread_local int64_t t_launches = 0;
 // kernel families timed by the profiler
 enum KernelId {
   K_PREP = 0, K_BAND, K_RECHECK, K_SCAN, K_CHUNK, K_FIRST, K_RECORDS, K_COMPACT, K_EXACT, K_APPROX,
-  K_FINAL, K_ADJ_BETA, K_ADJ_FINISH, K_COMBINE, K_MISC, K_COUNT
+  K_FINAL, K_ADJ_BETA, K_ADJ_FINISH, K_COMBINE, K_XY_REFINE, K_ADJ_BETA_SEG, K_COUNT
 };
 const char* const kKernelNames[PCV_PROFILE_KERNELS] = {
     "frame_prep", "align_band", "recheck_fp64", "band_scan", "align_chunk", "first_exceed", "records",
-    "compact", "exact_pair", "approx_pair", "finalize", "adjoint_beta", "adjoint_finish", "combine_grad", "misc", ""};
+    "compact", "exact_pair", "approx_pair", "finalize", "adjoint_beta_pair", "adjoint_finish", "combine_grad", "xy_refine",
+    "adjoint_beta_seg"};
 
 struct ProfEvent {
   int id;
@@ -81,7 +82,7 @@ struct pcv_ctx {
   bool have_lm = false;
   bool uniform = true;
   double dscale = 1.0;
-  DevBuf lm, lmG, lmA, lmq, w32, w64;
+  DevBuf lm, lmG, lmA, lmA32, lmq, lmq32, w32, w64;
   double lambda = 0.0;
   bool have_lambda = false;
   double eps = -1.0;
@@ -200,7 +201,9 @@ LandmarkDev lm_view(const pcv_ctx* c) {
   L.coords = c->lm.p;
   L.G = (const double*)c->lmG.p;
   L.A = (const double*)c->lmA.p;
+  L.A32 = (const float*)c->lmA32.p;
   L.q = (const double*)c->lmq.p;
+  L.q32 = (const float*)c->lmq32.p;
   L.w = c->uniform ? nullptr : (const float*)c->w32.p;
   L.w64 = c->uniform ? nullptr : (const double*)c->w64.p;
   L.dscale = c->dscale;
@@ -265,7 +268,7 @@ pcv_status pcv_destroy(pcv_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
-  DevBuf* bufs[] = {&c->lm, &c->lmG, &c->lmA, &c->lmq, &c->w32, &c->w64, &c->y, &c->Bprior, &c->c32, &c->c64,
+  DevBuf* bufs[] = {&c->lm, &c->lmG, &c->lmA, &c->lmA32, &c->lmq, &c->lmq32, &c->w32, &c->w64, &c->y, &c->Bprior, &c->c32, &c->c64,
                     &c->fG, &c->bandD, &c->bandQ, &c->bandF, &c->chD, &c->chQ, &c->chF, &c->rlist, &c->rcount,
                     &c->recF, &c->recRef, &c->recD, &c->recQ, &c->reflist, &c->segof, &c->alist, &c->aseg,
                     &c->Dbuf, &c->Rpair, &c->Bseg, &c->mstat, &c->status, &c->nrecheck, &c->small, &c->h_frames,
@@ -329,8 +332,7 @@ pcv_status pcv_set_option(pcv_ctx* c, int key, int64_t value) {
 
 pcv_status pcv_reset_close_state(pcv_ctx* c) {
   if (!c) return fail(nullptr, PCV_EINVAL, "NULL context");
-  c->has_y = false;
-  c->gap_estimate = 0.0;
+  c->has_y = false;  // the gap estimate is a tuning statistic and survives the reset
   const int64_t syncs = c->stats.host_syncs, launches = c->stats.kernel_launches;
   c->stats = pcv_stats{};
   c->stats.host_syncs = syncs;  // cumulative over the context's lifetime
@@ -413,14 +415,20 @@ pcv_status pcv_set_landmarks(pcv_ctx* c, int M, int N, const double* coords, con
   if ((st = ensure(c, c->lm, store.size())) != PCV_OK) return st;
   if ((st = ensure(c, c->lmG, sizeof(double) * M)) != PCV_OK) return st;
   if ((st = ensure(c, c->lmA, sizeof(double) * 6 * M)) != PCV_OK) return st;
+  if ((st = ensure(c, c->lmA32, sizeof(float) * 6 * M)) != PCV_OK) return st;
   if ((st = ensure(c, c->lmq, sizeof(double) * M)) != PCV_OK) return st;
+  if ((st = ensure(c, c->lmq32, sizeof(float) * M)) != PCV_OK) return st;
   if ((st = ensure(c, c->w32, sizeof(float) * N)) != PCV_OK) return st;
   if ((st = ensure(c, c->w64, sizeof(double) * N)) != PCV_OK) return st;
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   CUDA_TRY(c, cudaMemcpy(c->lm.p, store.data(), store.size(), cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(c->lmG.p, G.data(), sizeof(double) * M, cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(c->lmA.p, A.data(), sizeof(double) * 6 * M, cudaMemcpyHostToDevice));
+  std::vector<float> A32(A.begin(), A.end());
+  CUDA_TRY(c, cudaMemcpy(c->lmA32.p, A32.data(), sizeof(float) * 6 * M, cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(c->lmq.p, qv.data(), sizeof(double) * M, cudaMemcpyHostToDevice));
+  std::vector<float> q32(qv.begin(), qv.end());
+  CUDA_TRY(c, cudaMemcpy(c->lmq32.p, q32.data(), sizeof(float) * M, cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(c->w32.p, w32.data(), sizeof(float) * N, cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(c->w64.p, wn.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
   c->M = M;
@@ -507,16 +515,24 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
     PROF(c, K_PREP);
     launch_frame_prep(c->prec, F, frames, L, fi, st);
   }
-  launch_set_int(rc, 0, st);
-  if (F > 1) {
+  // The band pays off when reassignments come every few frames; with long observed gaps the
+  // search uses speculative chunks only.  Band rows are computed lazily from the first frame
+  // that needs them (band_from: rows [band_from, F) are ready).
+  int band_from = F;
+  auto want_band = [&]() { return F > 1 && !(c->gap_estimate > 8.0 * W); };
+  auto ensure_band = [&](int from) {
+    from = from < 1 ? 1 : from;
+    if (from >= band_from) return;
+    launch_set_int(rc, 0, st);
     {
       PROF(c, K_BAND);
-      launch_align_band(c->prec, F, W, frames, L, fi, c->eps, band, rl, rc, st);
+      launch_align_band(c->prec, F, W, from, band_from, frames, L, fi, c->eps, band, rl, rc, st);
     }
     PROF(c, K_RECHECK);
-    launch_recheck(c->prec, (F - 1) * W, rl, rc, W, frames, L, prior, -1, c->eps, band, chunk,
+    launch_recheck(c->prec, (band_from - from) * W, rl, rc, W, frames, L, prior, -1, c->eps, band, chunk,
                    (unsigned long long*)c->nrecheck.p, st);
-  }
+    band_from = from;
+  };
   // host-driven refresh search
   int t = 0, ref = -1, o = 0;
   bool band_mode = false;
@@ -525,12 +541,13 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
     t = 1;
     ref = 0;
     o = 0;
-    band_mode = true;
+    band_mode = want_band();
   }
   long long guard = 0;
   while (t < F) {
     if (++guard > 4LL * F + 16) return fail(c, PCV_ESTATE, "refresh search did not terminate");
     if (band_mode) {
+      ensure_band(t);
       {
         PROF(c, K_SCAN);
         launch_band_scan(F, W, t, o, band, rec, &sm->scan, st);
@@ -538,6 +555,11 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
       pcv_status ps = sync_small(c);
       if (ps != PCV_OK) return ps;
       const int ts = c->small_host->scan.t_stop;
+      const int nr = c->small_host->scan.nref;
+      if (nr > 0) {
+        const double gap = (double)((ts < F ? ts : F) - t) / nr;
+        c->gap_estimate = c->gap_estimate > 0.0 ? 0.5 * (c->gap_estimate + gap) : gap;
+      }
       if (ts >= F) break;
       if (ts < t) return fail(c, PCV_ESTATE, "band scan went backwards");
       t = ts;
@@ -576,10 +598,14 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
       t = first + 1;
       ref = first;
       o = 0;
-      band_mode = (W >= 1 && F > 1);
+      band_mode = want_band();
     } else {
       t = t1;
     }
+  }
+  {
+    PROF(c, K_XY_REFINE);
+    launch_xy_refine(c->prec, F, frames, L, fi, prior, rec, st);
   }
   // compaction and per-segment work
   {
@@ -608,19 +634,21 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
   }
   {
     PROF(c, K_FINAL);
-    launch_finalize(c->prec, F, M, c->Dbuf.p, L.q, c->lambda, s, z, (float*)c->mstat.p, (double*)c->mstat.p, msd,
-                    st);
+    launch_finalize(c->prec, F, M, c->Dbuf.p, L.q, L.q32, c->lambda, s, z, (float*)c->mstat.p, (double*)c->mstat.p, msd,
+                    gs != nullptr, st);
   }
   if (refreshed) CUDA_TRY(c, cudaMemcpyAsync(refreshed, rec.flag, F, cudaMemcpyDeviceToDevice, st));
   if (gs && gz) {
+    // frames sharing close structures: the segment GEMM; frequent reassignments: per pair
+    const bool seg_form = (int64_t)(nref + 1) * 16 <= (int64_t)F;
     {
-      PROF(c, K_ADJ_BETA);
-      launch_adjoint_beta(c->prec, F, L, c->Dbuf.p, (const float*)c->mstat.p, s, c->lambda, nullptr, c->Bseg.p,
-                          (const int*)c->segof.p, gs, gz, st);
+      ProfScope ps(c, seg_form && c->prec != P_F64 ? K_ADJ_BETA_SEG : K_ADJ_BETA);
+      launch_adjoint_beta(c->prec, F, L, c->Dbuf.p, s, c->lambda, nullptr, c->Bseg.p, (const int*)c->segof.p,
+                          seg_form, gs, gz, st);
     }
     PROF(c, K_ADJ_FINISH);
-    launch_adjoint_finish(c->prec, F, frames, L, fi, c->Dbuf.p, (const float*)c->mstat.p, s, c->lambda, c->Bseg.p,
-                          (const int*)c->segof.p, rec, prior, gs, gz, (unsigned*)c->status.p, st);
+    launch_adjoint_finish(c->prec, F, frames, L, fi, c->Dbuf.p, s, c->lambda, c->Bseg.p, (const int*)c->segof.p, rec,
+                          prior, gs, gz, st);
   }
   // carry the close structure over to the next call
   const int last = c->small_host->last_refresh;
@@ -663,21 +691,19 @@ pcv_status evaluate_exact(pcv_ctx* c, int F, const void* frames, double* s, doub
   }
   {
     PROF(c, K_FINAL);
-    launch_finalize(c->prec, F, c->M, c->Dbuf.p, L.q, c->lambda, s, z, (float*)c->mstat.p, (double*)c->mstat.p,
-                    msd, st);
+    launch_finalize(c->prec, F, c->M, c->Dbuf.p, L.q, L.q32, c->lambda, s, z, (float*)c->mstat.p, (double*)c->mstat.p,
+                    msd, grads, st);
   }
   if (refreshed) launch_fill_u8(refreshed, 1, (size_t)F, st);
   if (grads) {
     {
       PROF(c, K_ADJ_BETA);
-      launch_adjoint_beta(c->prec, F, L, c->Dbuf.p, (const float*)c->mstat.p, s, c->lambda, c->Rpair.p, nullptr,
-                          nullptr, gs, gz, st);
+      launch_adjoint_beta(c->prec, F, L, c->Dbuf.p, s, c->lambda, c->Rpair.p, nullptr, nullptr, false, gs, gz, st);
     }
     PROF(c, K_ADJ_FINISH);
     FrameRec none;
     RefDesc nop;
-    launch_adjoint_finish(c->prec, F, frames, L, fi, c->Dbuf.p, (const float*)c->mstat.p, s, c->lambda, nullptr,
-                          nullptr, none, nop, gs, gz, (unsigned*)c->status.p, st);
+    launch_adjoint_finish(c->prec, F, frames, L, fi, c->Dbuf.p, s, c->lambda, nullptr, nullptr, none, nop, gs, gz, st);
   }
   c->stats.frames += F;
   c->stats.landmark_alignments += (int64_t)c->M * F;

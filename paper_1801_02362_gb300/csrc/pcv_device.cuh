@@ -443,36 +443,137 @@ __device__ __forceinline__ void adj_eigvec_f64(const double* K, double lam, doub
   for (int i = 0; i < 4; ++i) q[i] *= inv;
 }
 
-// Solve the 4x4 symmetric positive definite system A p = g by Cholesky (FP64).
+// Solve the 4x4 symmetric positive definite system A p = g by Cholesky.
 // Returns false if A is not numerically positive definite.
-__device__ __forceinline__ bool spd_solve4(const double* A, const double* g, double* p) {
-  double L[16];
+template <typename T>
+__device__ __forceinline__ bool spd_solve4(const T* A, const T* g, T* p) {
+  T L[16];
 #pragma unroll
-  for (int e = 0; e < 16; ++e) L[e] = 0.0;
+  for (int e = 0; e < 16; ++e) L[e] = 0;
+#pragma unroll
   for (int i = 0; i < 4; ++i) {
+#pragma unroll
     for (int j = 0; j <= i; ++j) {
-      double sum = A[4 * i + j];
+      T sum = A[4 * i + j];
+#pragma unroll
       for (int k = 0; k < j; ++k) sum -= L[4 * i + k] * L[4 * j + k];
       if (i == j) {
-        if (!(sum > 0.0)) return false;
+        if (!(sum > T(0))) return false;
         L[4 * i + i] = sqrt(sum);
       } else {
         L[4 * i + j] = sum / L[4 * j + j];
       }
     }
   }
-  double y[4];
+  T y[4];
+#pragma unroll
   for (int i = 0; i < 4; ++i) {
-    double sum = g[i];
+    T sum = g[i];
+#pragma unroll
     for (int k = 0; k < i; ++k) sum -= L[4 * i + k] * y[k];
     y[i] = sum / L[4 * i + i];
   }
+#pragma unroll
   for (int i = 3; i >= 0; --i) {
-    double sum = y[i];
+    T sum = y[i];
+#pragma unroll
     for (int k = i + 1; k < 4; ++k) sum -= L[4 * k + i] * p[k];
     p[i] = sum / L[4 * i + i];
   }
   return true;
+}
+
+// top eigenpair (lambda0, unit q0) of K(H) in the working precision
+__device__ __forceinline__ void top_eig(const float* H, const float* K, float* l0, float* q0) {
+  float ub = 0.0f;  // Gershgorin bound >= lambda_max
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    float rs = 0.0f;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) rs += fabsf(K[4 * a + b]);
+    ub = fmaxf(ub, rs);
+  }
+  top_quat_f32(H, ub + 1e-30f, q0);
+  float t = 0.0f;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) t += q0[a] * K[4 * a + b] * q0[b];
+  *l0 = t;
+}
+__device__ __forceinline__ void top_eig(const double* H, const double* K, double* l0, double* q0) {
+  double ub = 0.0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    double rs = 0.0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) rs += fabs(K[4 * a + b]);
+    ub = fmax(ub, rs);
+  }
+  bool ok = true;
+  *l0 = lambda_max_newton(H, ub + 1e-300, &ok);
+  adj_eigvec_f64(K, *l0, q0);
+}
+
+// Rotation term of Eq. (close_der_dist) summed over the landmarks with weights gamma_i:
+// sum_ab Ghat_ab dR_xy,ab / dx_kc = w_k (T^T y_k)_c, where
+//   Ghat = -2 (X - R_xy Phi),  X = sum_j w_j x_j beta_j^T,  Phi = sum_i gamma_i B_i A_i B_i^T,
+//   q0, l0: top eigenpair of K(H_xy), H_xy = sum_j w_j y_j x_j^T,
+//   g = 2 K(Ghat^T) q0 (gradient of sum_ab Ghat_ab R(q)_ab at q0),
+//   p solves (l0 I - K + q0 q0^T) p = g - (q0.g) q0 (first-order eigenvector perturbation
+//   dq0 = (l0 I - K)^+ dK q0, with dK = K(w_k y_k e_c^T)),
+//   T_bc = p^T K(E_bc) q0.
+template <typename T>
+__device__ __forceinline__ void adjoint_rotation_term(const T* H, const T* R, const T* X, const T* Phi, T* Tout) {
+  T K[16];
+  quat_matrix(H, K);
+  T l0, q0[4];
+  top_eig(H, K, &l0, q0);
+  T Gh[9];
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      Gh[3 * b + c] = T(-2) * (X[3 * b + c] - (R[3 * b] * Phi[c] + R[3 * b + 1] * Phi[3 + c] + R[3 * b + 2] * Phi[6 + c]));
+  T GhT[9];
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) GhT[3 * b + c] = Gh[3 * c + b];
+  T KG[16];
+  quat_matrix(GhT, KG);
+  T g[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    g[a] = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) g[a] += T(2) * KG[4 * a + b] * q0[b];
+  }
+  const T gq = g[0] * q0[0] + g[1] * q0[1] + g[2] * q0[2] + g[3] * q0[3];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) g[a] -= gq * q0[a];
+  T Am[16];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) Am[4 * a + b] = (a == b ? l0 : T(0)) - K[4 * a + b] + q0[a] * q0[b];
+  T pv[4] = {0, 0, 0, 0};
+  spd_solve4(Am, g, pv);
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T E[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+      E[3 * b + c] = 1;
+      T KE[16];
+      quat_matrix(E, KE);
+      T t = 0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int d = 0; d < 4; ++d) t += pv[a] * KE[4 * a + d] * q0[d];
+      Tout[3 * b + c] = t;
+    }
 }
 
 }  // namespace pcv

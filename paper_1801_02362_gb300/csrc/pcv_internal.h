@@ -20,7 +20,9 @@ struct LandmarkDev {
   const void* coords = nullptr;  // M*N*3, centred, storage type of the mode
   const double* G = nullptr;     // M: sum_j wk_j |a_j|^2 in kernel units (see below)
   const double* A = nullptr;     // M*6: sum_j w_j a_j a_j^T (true weights, xx xy xz yy yz zz)
+  const float* A32 = nullptr;    // the same in FP32
   const double* q = nullptr;     // M: property q_i
+  const float* q32 = nullptr;    // M: the same in FP32
   const float* w = nullptr;      // N: true weights (normalised), or nullptr when uniform
   const double* w64 = nullptr;   // N: the same weights in FP64, or nullptr when uniform
   double dscale = 1.0;           // kernel units -> true: 1/N for uniform weights, else 1
@@ -56,10 +58,10 @@ struct AlignOut {
 // ---- k_aux.cu ----
 void launch_frame_prep(Prec p, int F, const void* frames, const LandmarkDev& L, FrameInfo fi,
                        cudaStream_t st);
-// band: for t in [1, F) and k = 1..W with t-k >= 0: D(x_t, x_{t-k}) -> out[t*W + k-1]
-void launch_align_band(Prec p, int F, int W, const void* frames, const LandmarkDev& L,
-                       FrameInfo fi, double eps, AlignOut out, int* recheck_list,
-                       int* recheck_count, cudaStream_t st);
+// band: for t in [max(t_lo,1), t_hi) and k = 1..W with t-k >= 0: D(x_t, x_{t-k}) -> out[t*W + k-1]
+void launch_align_band(Prec p, int F, int W, int t_lo, int t_hi, const void* frames, const LandmarkDev& L,
+                       FrameInfo fi, double eps, AlignOut out, int* recheck_list, int* recheck_count,
+                       cudaStream_t st);
 // chunk: for t in [t0, t1): D(x_t, ref) -> out[t]; ref_index >= 0 is a frame of the batch
 void launch_align_chunk(Prec p, int t0, int t1, const void* frames, const LandmarkDev& L,
                         FrameInfo fi, int ref_index, const RefDesc& prior, double eps,
@@ -70,6 +72,11 @@ void launch_recheck(Prec p, int max_entries, const int* list, const int* count, 
                     double eps, AlignOut band, AlignOut chunk, unsigned long long* n_rechecks,
                     cudaStream_t st);
 // recheck list entries: (slot << 1) | kind, kind 0 = band slot t*W + k-1, 1 = chunk slot t
+// accurate quaternions of R_xy for the approximate frames (FP32 modes; FP64 mode keeps the
+// FP64 band / chunk quaternions)
+struct FrameRec;
+void launch_xy_refine(Prec p, int F, const void* frames, const LandmarkDev& L, FrameInfo fi, const RefDesc& prior,
+                      FrameRec rec, cudaStream_t st);
 // first t in [t0, t1) with chunk flag bit0 set -> *first (initialised to t1 by the kernel)
 void launch_first_exceed(int t0, int t1, const uint8_t* flag, int* first, cudaStream_t st);
 
@@ -83,6 +90,8 @@ struct FrameRec {
 struct ScanResult {
   int t_stop;  // first frame the band could not decide (F if none)
   int ref;     // close-structure frame index in force at t_stop
+  int nref;    // reassignments among the decided frames
+  int pad;
 };
 // decide frames [t0, F) from the band with the state `o_init` (offset of frame t0-1 from
 // its close structure, 0..W); writes records and *res (device)
@@ -101,22 +110,22 @@ void launch_compact(int F, const FrameRec rec, int* refresh_list, int* refresh_c
 
 // softmax finalisation: s, z per frame from the F x M distances (float in FP32 modes,
 // double in FP64 mode); mstat[f] = (m, l) with m = min_i D_i, l = sum_i exp(-lambda(D_i-m));
-// msd_out (optional) receives the distances as doubles
-void launch_finalize(Prec p, int F, int M, const void* D, const double* q, double lambda,
-                     double* s, double* z, float* mstat, double* mstat64, double* msd_out,
-                     cudaStream_t st);
+// msd_out (optional) receives the distances as doubles; want_p overwrites D with the
+// weights p_i = exp(-lambda (D_i - m)) / l used by the adjoint
+void launch_finalize(Prec p, int F, int M, void* D, const double* q, const float* q32, double lambda, double* s,
+                     double* z, float* mstat, double* mstat64, double* msd_out, bool want_p, cudaStream_t st);
 
-// adjoint: beta = sum_i gamma_i Rot_fi a_i (written into gs/gz), then per-frame finish.
-// Rpair (exact mode): F*M*9 rotations; otherwise Bseg[seg_of_frame[f]*M + i] (close mode).
-void launch_adjoint_beta(Prec p, int F, const LandmarkDev& L, const void* D, const float* mstat,
-                         const double* s, double lambda, const void* Rpair, const void* Bseg,
-                         const int* seg_of_frame, void* gs, void* gz, cudaStream_t st);
+// adjoint (k_adjoint.cu): beta = sum_i gamma_i Rot_fi a_i written into gs/gz, then the
+// per-frame finish.  P holds the softmax weights p (launch_finalize with want_p).  Rpair
+// (exact mode): F*M*9 rotations; otherwise Bseg[seg_of_frame[f]*M + i].  seg_form: frames
+// share their segment's rotations (close structure, few segments).
+void launch_adjoint_beta(Prec p, int F, const LandmarkDev& L, const void* P, const double* s, double lambda,
+                         const void* Rpair, const void* Bseg, const int* seg_of_frame, bool seg_form, void* gs,
+                         void* gz, cudaStream_t st);
 // rec.flag == nullptr: exact mode (no rotation term)
-void launch_adjoint_finish(Prec p, int F, const void* frames, const LandmarkDev& L, FrameInfo fi,
-                           const void* D, const float* mstat, const double* s, double lambda,
-                           const void* Bseg, const int* seg_of_frame, const FrameRec rec,
-                           const RefDesc& prior, void* gs, void* gz, unsigned* status,
-                           cudaStream_t st);
+void launch_adjoint_finish(Prec p, int F, const void* frames, const LandmarkDev& L, FrameInfo fi, const void* P,
+                           const double* s, double lambda, const void* Bseg, const int* seg_of_frame,
+                           const FrameRec rec, const RefDesc& prior, void* gs, void* gz, cudaStream_t st);
 void launch_combine_grad(Prec p, int F, int N3, const double* g_s, const double* g_z,
                          const void* gs, const void* gz, void* out, cudaStream_t st);
 void launch_fill_u8(uint8_t* p, uint8_t v, size_t n, cudaStream_t st);

@@ -138,6 +138,21 @@ def test_close_eps_sweep_refresh_flags_exact(pcv, eps, min_chunk):
     assert st["xy_alignments"] == oc["xy_alignments"]
 
 
+def test_close_same_context_across_regimes(pcv):
+    """One context, reset between batches: long gaps (the band is skipped once the gap
+    estimate is large), then every frame reassigning (the band comes back lazily)."""
+    lm, fr, lam = problem(7, 300, 200, 1500)
+    ctx = pcv.PathCV(lm, lam, eps=0.05, precision="fp32")
+    for eps in (0.05, 0.05, 0.01, 0.1, 0.01):
+        pcv.pcv_set_close_threshold(ctx.ctx, eps)
+        pcv.pcv_reset_close_state(ctx.ctx)
+        r = oracle.close(fr, lm, lam, eps)
+        g = run(pcv, lm, fr, lam, ctx=ctx)
+        np.testing.assert_array_equal(g["refreshed"], r["refreshed"])
+        check_values(g, r, fr, lm, lam, "fp32")
+    ctx.close()
+
+
 @pytest.mark.parametrize("band", [1, 2, 6])
 def test_close_correlated_noise_all_band_states(pcv, band):
     """Ornstein-Uhlenbeck frame noise: gaps of a few frames, exercising every band state."""
