@@ -283,12 +283,13 @@ def run_ours(args):
     dom = max((k for k in prof if k in FLOPS_PER_UNIT), key=lambda k: prof[k][0])
     dom_ms, dom_launches = prof[dom]
     per_launch_ms = dom_ms / dom_launches
+    launches_per_step = dom_launches / args.steps
     if dom == "approx_pair":
-        units = approx_msds_step / dom_launches * N_ATOMS
+        units = approx_msds_step / launches_per_step * N_ATOMS
     elif dom == "exact_pair":
-        units = exact_msds_step / dom_launches * N_ATOMS
+        units = exact_msds_step / launches_per_step * N_ATOMS
     else:
-        units = F * N_LANDMARKS * N_ATOMS
+        units = F * N_LANDMARKS * N_ATOMS / launches_per_step
     flops = FLOPS_PER_UNIT[dom] * units
     achieved = flops / (per_launch_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",

@@ -127,36 +127,37 @@ adjoint_beta_pair(int F, int M, int N, const LT* __restrict__ lm, const double* 
 }
 
 // ---------------------------------------------------------------------------------------
-// beta for frames sharing close structures: tile of 64 consecutive frames x 64 atoms, 256
-// threads, each 4 frames x 4 atoms x 3 components x {s, z}.  Frames of the tile are grouped
-// into runs of equal segment; per run and landmark chunk the landmarks are rotated once by
-// R_{a_i y} into shared memory, and gamma is formed from p (coalesced rows of P).
-constexpr int BS_TF = 64, BS_TJ = 64, BS_KL = 16, BS_THREADS = 256;
+// beta for frames sharing close structures: tile of 64 consecutive frames x 32 atoms, 256
+// threads, each 4 frames x 2 atoms x 3 components x {s, z} (48 FP32 sums): per landmark
+// two LDS.128 of gamma and 6 landmark values feed 48 FMAs.  Frames of the tile are grouped
+// into runs of equal segment; per run, landmark chunks are rotated by R_{a_i y} into shared
+// memory and gamma is formed from p (coalesced rows of P).
+constexpr int BS_TF = 64, BS_TJ = 32, BS_KL = 16, BS_THREADS = 256;
 
 template <typename LT>
-__global__ void __launch_bounds__(BS_THREADS, 2)
+__global__ void __launch_bounds__(BS_THREADS, 3)
 adjoint_beta_seg(int F, int M, int N, const LT* __restrict__ lm, const float* __restrict__ q32,
                  const float* __restrict__ P, const double* __restrict__ s, float lambda,
                  const float* __restrict__ Bseg, const int* __restrict__ seg_of_frame, float* __restrict__ gs,
                  float* __restrict__ gz) {
-  __shared__ __align__(16) float Gs[BS_KL][BS_TF];  // gamma^s of (landmark, frame), 0 outside the run
-  __shared__ __align__(16) float Gz[BS_KL][BS_TF];
-  __shared__ __align__(16) float Bb[BS_KL][BS_TJ * 3];  // b_ij = R_{a_i y} a_ij, (atom, xyz) packed
+  __shared__ __align__(16) float Gs[BS_KL][BS_TF + 4];  // gamma^s of (landmark, frame), 0 outside the run
+  __shared__ __align__(16) float Gz[BS_KL][BS_TF + 4];
+  __shared__ __align__(16) float Bb[BS_KL][BS_TJ * 3 + 4];  // b_ij = R_{a_i y} a_ij, (atom, xyz) packed
   __shared__ float s_B[BS_KL][9];
   __shared__ int s_seg[BS_TF];
   __shared__ float s_s[BS_TF];
   const int f0 = blockIdx.y * BS_TF, j0 = blockIdx.x * BS_TJ;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;  // atoms j0 + 4 tx + {0..3}; frames 4 ty + {0..3}
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;  // atoms j0 + 2 tx + {0,1}; frames 4 ty + {0..3}
   if (tid < BS_TF) {
     const int f = f0 + tid;
     s_seg[tid] = f < F ? seg_of_frame[f] : -1;
     s_s[tid] = f < F ? (float)s[f] : 0.0f;
   }
-  float acs[4][12], acz[4][12];
+  float acs[4][6], acz[4][6];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int k = 0; k < 12; ++k) acs[u][k] = acz[u][k] = 0.0f;
+    for (int k = 0; k < 6; ++k) acs[u][k] = acz[u][k] = 0.0f;
   __syncthreads();
   int k = 0;
   while (k < BS_TF && s_seg[k] >= 0) {
@@ -169,7 +170,6 @@ adjoint_beta_seg(int F, int M, int N, const LT* __restrict__ lm, const float* __
         const int i = i0 + ii;
         s_B[ii][c] = i < M ? Bseg[((size_t)seg * M + i) * 9 + c] : 0.0f;
       }
-      // gamma: consecutive threads walk a frame's row of P (coalesced)
       for (int e = tid; e < BS_KL * BS_TF; e += BS_THREADS) {
         const int ff = e / BS_KL, ii = e - ff * BS_KL;
         const int f = f0 + ff, i = i0 + ii;
@@ -201,19 +201,15 @@ adjoint_beta_seg(int F, int M, int N, const LT* __restrict__ lm, const float* __
         const float4 g1 = *reinterpret_cast<const float4*>(&Gs[ii][ty * 4]);
         const float4 g2 = *reinterpret_cast<const float4*>(&Gz[ii][ty * 4]);
         const float gsv[4] = {g1.x, g1.y, g1.z, g1.w}, gzv[4] = {g2.x, g2.y, g2.z, g2.w};
-        float b[12];
-#pragma unroll
-        for (int v = 0; v < 3; ++v) {
-          const float4 t = *reinterpret_cast<const float4*>(&Bb[ii][tx * 12 + 4 * v]);
-          b[4 * v] = t.x;
-          b[4 * v + 1] = t.y;
-          b[4 * v + 2] = t.z;
-          b[4 * v + 3] = t.w;
-        }
+        // 6 floats at byte offset 24 tx: three 8-byte aligned float2 loads
+        const float2 ba = *reinterpret_cast<const float2*>(&Bb[ii][tx * 6]);
+        const float2 bb = *reinterpret_cast<const float2*>(&Bb[ii][tx * 6 + 2]);
+        const float2 bc = *reinterpret_cast<const float2*>(&Bb[ii][tx * 6 + 4]);
+        const float b[6] = {ba.x, ba.y, bb.x, bb.y, bc.x, bc.y};
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
-          for (int c = 0; c < 12; ++c) {
+          for (int c = 0; c < 6; ++c) {
             acs[u][c] = fmaf(gsv[u], b[c], acs[u][c]);
             acz[u][c] = fmaf(gzv[u], b[c], acz[u][c]);
           }
@@ -227,8 +223,8 @@ adjoint_beta_seg(int F, int M, int N, const LT* __restrict__ lm, const float* __
     const int f = f0 + ty * 4 + u;
     if (f >= F) continue;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int j = j0 + tx * 4 + a;
+    for (int a = 0; a < 2; ++a) {
+      const int j = j0 + tx * 2 + a;
       if (j >= N) continue;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {

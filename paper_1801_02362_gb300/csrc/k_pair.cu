@@ -361,25 +361,30 @@ exact_pair_f64(int rows, const int* __restrict__ row_frame, const double* __rest
 }
 
 // ---------------------------------------------------------------------------------------
-constexpr int AP_TF = 64, AP_TM = 32, AP_THREADS = 128;
+// Approximate pairs.  Tile: 64 frames x (8 RM) landmarks, 128 threads, each 4 frames x RM
+// landmarks.  Atoms in chunks of 16, software-pipelined: raw coordinates of chunk c+1 are
+// loaded into registers while chunk c is computed from one of two shared buffers, then
+// rotated (frames by R_xy^T after centring, landmarks by R_{a_i y}) into the other buffer.
+constexpr int AP_TF = 64, AP_THREADS = 128, AP_KC = 16;
 
-template <typename FT, typename LT, typename ST>
-__global__ void __launch_bounds__(AP_THREADS)
+template <typename FT, typename LT, typename ST, int RM>
+__global__ void __launch_bounds__(AP_THREADS, 3)
 approx_pair_kernel(const int* __restrict__ alist, const int* __restrict__ aseg,
                    const int* __restrict__ acount, const FT* __restrict__ frames,
                    const float4* __restrict__ c32, const double4* __restrict__ c64,
                    const double4* __restrict__ qxy, const LT* __restrict__ lm,
                    const ST* __restrict__ Bseg, const float* __restrict__ wts, int M, int N,
                    double dscale, ST* __restrict__ Dout) {
-  constexpr int TF = AP_TF, TM = AP_TM;
-  constexpr int KC = sizeof(ST) == 8 ? 16 : 32;
+  constexpr int TF = AP_TF, TM = 8 * RM, KC = sizeof(ST) == 8 ? AP_KC / 2 : AP_KC;
   constexpr int PF = TF + 4, PM = TM + 4;
-  __shared__ __align__(16) ST Xs[KC * 3][PF];
-  __shared__ __align__(16) ST Bs[KC * 3][PM];
+  constexpr int NF = TF * KC / AP_THREADS;  // frame-atom items per thread per chunk
+  constexpr int NL = (TM * KC + AP_THREADS - 1) / AP_THREADS;
+  __shared__ __align__(16) ST Xs[2][KC * 3][PF];
+  __shared__ __align__(16) ST Bs[2][KC * 3][PM];
   __shared__ ST s_R[TF][9];
   __shared__ ST s_B[TM][9];
   __shared__ ST s_c[TF][3];
-  __shared__ ST s_sw[KC];
+  __shared__ ST s_sw[2][KC];
   __shared__ int s_frame[TF], s_seg[TF];
 
   const int count = *acount;
@@ -388,7 +393,7 @@ approx_pair_kernel(const int* __restrict__ alist, const int* __restrict__ aseg,
   const ST dsc = (ST)dscale;
   const int i0 = blockIdx.x * TM;
   const int tid = threadIdx.x;
-  const int tx = tid & 7;   // landmarks i0 + 4 tx + {0..3}
+  const int tx = tid & 7;   // landmarks i0 + RM tx + {0..RM-1}
   const int ty = tid >> 3;  // rows 4 ty + {0..3}
 
   if (tid < TF) {
@@ -405,14 +410,14 @@ approx_pair_kernel(const int* __restrict__ alist, const int* __restrict__ aseg,
     if (f >= 0) {
       frame_centre<ST>(c32, c64, f, c);
       const double4 qq = qxy[f];
-      const double qd[4] = {qq.x, qq.y, qq.z, qq.w};
       if (sizeof(ST) == 8) {
+        const double qd[4] = {qq.x, qq.y, qq.z, qq.w};
         double Rd[9];
         quat_to_rot(qd, Rd);
 #pragma unroll
         for (int e = 0; e < 9; ++e) R[e] = (ST)Rd[e];
       } else {
-        const float qf[4] = {(float)qd[0], (float)qd[1], (float)qd[2], (float)qd[3]};
+        const float qf[4] = {(float)qq.x, (float)qq.y, (float)qq.z, (float)qq.w};
         float Rf[9];
         quat_to_rot(qf, Rf);
 #pragma unroll
@@ -427,6 +432,7 @@ approx_pair_kernel(const int* __restrict__ alist, const int* __restrict__ aseg,
   }
   __syncthreads();
 
+  const int nchunk = (N + KC - 1) / KC;
   int k = 0;
   while (k < TF && s_frame[k] >= 0) {
     const int seg = s_seg[k];
@@ -437,72 +443,106 @@ approx_pair_kernel(const int* __restrict__ alist, const int* __restrict__ aseg,
       const int i = i0 + ll;
       s_B[ll][c] = (i < M) ? Bseg[((size_t)seg * M + i) * 9 + c] : (ST)0;
     }
-    ST acc[4][4], thi[4][4], tlo[4][4];
+    ST acc[4][RM], thi[4][RM], tlo[4][RM];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) acc[u][v] = thi[u][v] = tlo[u][v] = 0;
-    __syncthreads();
+      for (int v = 0; v < RM; ++v) acc[u][v] = thi[u][v] = tlo[u][v] = 0;
 
-    for (int j0 = 0; j0 < N; j0 += KC) {
-      if (tid < KC) {
-        const int j = j0 + tid;
-        ST sw = 1;
-        if (wts) sw = (j < N) ? (ST)sqrt((double)wts[j]) : (ST)0;
-        s_sw[tid] = sw;
-      }
-      __syncthreads();
-      // frames: x' = R_xy^T (x - c), rows outside [k, kend) staged as zero
-      for (int e = tid; e < TF * KC; e += AP_THREADS) {
+    ST rf[NF][3], rl[NL][3], rsw = 1;
+    auto load_chunk = [&](int c) {
+      const int j0 = c * KC;
+#pragma unroll
+      for (int r = 0; r < NF; ++r) {
+        const int e = tid + r * AP_THREADS;
         const int ff = e / KC, jj = e - ff * KC;
         const int j = j0 + jj;
-        ST o0 = 0, o1 = 0, o2 = 0;
         if (ff >= k && ff < kend && j < N) {
           const FT* src = frames + ((size_t)s_frame[ff] * N + j) * 3;
-          const ST v0 = (ST)src[0] - s_c[ff][0];
-          const ST v1 = (ST)src[1] - s_c[ff][1];
-          const ST v2 = (ST)src[2] - s_c[ff][2];
+          rf[r][0] = (ST)src[0];
+          rf[r][1] = (ST)src[1];
+          rf[r][2] = (ST)src[2];
+        } else {
+          rf[r][0] = rf[r][1] = rf[r][2] = 0;
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < NL; ++r) {
+        const int e = tid + r * AP_THREADS;
+        const int ll = e / KC, jj = e - ll * KC;
+        const int j = j0 + jj, i = i0 + ll;
+        if (e < TM * KC && i < M && j < N) {
+          const LT* src = lm + ((size_t)i * N + j) * 3;
+          rl[r][0] = load_as<ST>(src);
+          rl[r][1] = load_as<ST>(src + 1);
+          rl[r][2] = load_as<ST>(src + 2);
+        } else {
+          rl[r][0] = rl[r][1] = rl[r][2] = 0;
+        }
+      }
+      if (tid < KC) {
+        const int j = j0 + tid;
+        rsw = 1;
+        if (wts) rsw = (j < N) ? (ST)sqrt(wts[j]) : (ST)0;
+      }
+    };
+    auto store_chunk = [&](int c, int buf) {
+      const int j0 = c * KC;
+      if (tid < KC) s_sw[buf][tid] = rsw;
+#pragma unroll
+      for (int r = 0; r < NF; ++r) {
+        const int e = tid + r * AP_THREADS;
+        const int ff = e / KC, jj = e - ff * KC;
+        ST o0 = 0, o1 = 0, o2 = 0;
+        if (ff >= k && ff < kend && j0 + jj < N) {
+          const ST v0 = rf[r][0] - s_c[ff][0];
+          const ST v1 = rf[r][1] - s_c[ff][1];
+          const ST v2 = rf[r][2] - s_c[ff][2];
           const ST* R = s_R[ff];
-          const ST sw = s_sw[jj];
+          ST sw = 1;
+          if (wts) sw = (ST)sqrt(wts[j0 + jj]);
           o0 = (R[0] * v0 + R[3] * v1 + R[6] * v2) * sw;
           o1 = (R[1] * v0 + R[4] * v1 + R[7] * v2) * sw;
           o2 = (R[2] * v0 + R[5] * v1 + R[8] * v2) * sw;
         }
-        Xs[jj * 3 + 0][ff] = o0;
-        Xs[jj * 3 + 1][ff] = o1;
-        Xs[jj * 3 + 2][ff] = o2;
+        Xs[buf][jj * 3 + 0][ff] = o0;
+        Xs[buf][jj * 3 + 1][ff] = o1;
+        Xs[buf][jj * 3 + 2][ff] = o2;
       }
-      // landmarks: b = R_{a_i y} a
-      for (int e = tid; e < TM * KC; e += AP_THREADS) {
+#pragma unroll
+      for (int r = 0; r < NL; ++r) {
+        const int e = tid + r * AP_THREADS;
+        if (e >= TM * KC) continue;
         const int ll = e / KC, jj = e - ll * KC;
-        const int j = j0 + jj, i = i0 + ll;
-        ST o0 = 0, o1 = 0, o2 = 0;
-        if (i < M && j < N) {
-          const LT* src = lm + ((size_t)i * N + j) * 3;
-          const ST a0 = load_as<ST>(src), a1 = load_as<ST>(src + 1), a2 = load_as<ST>(src + 2);
-          const ST* B = s_B[ll];
-          const ST sw = s_sw[jj];
-          o0 = (B[0] * a0 + B[1] * a1 + B[2] * a2) * sw;
-          o1 = (B[3] * a0 + B[4] * a1 + B[5] * a2) * sw;
-          o2 = (B[6] * a0 + B[7] * a1 + B[8] * a2) * sw;
-        }
-        Bs[jj * 3 + 0][ll] = o0;
-        Bs[jj * 3 + 1][ll] = o1;
-        Bs[jj * 3 + 2][ll] = o2;
+        const ST* B = s_B[ll];
+        ST sw = 1;
+        if (wts && j0 + jj < N) sw = (ST)sqrt(wts[j0 + jj]);
+        Bs[buf][jj * 3 + 0][ll] = (B[0] * rl[r][0] + B[1] * rl[r][1] + B[2] * rl[r][2]) * sw;
+        Bs[buf][jj * 3 + 1][ll] = (B[3] * rl[r][0] + B[4] * rl[r][1] + B[5] * rl[r][2]) * sw;
+        Bs[buf][jj * 3 + 2][ll] = (B[6] * rl[r][0] + B[7] * rl[r][1] + B[8] * rl[r][2]) * sw;
       }
-      __syncthreads();
+    };
+    __syncthreads();  // s_B ready
+    load_chunk(0);
+    store_chunk(0, 0);
+    __syncthreads();
+    for (int c = 0; c < nchunk; ++c) {
+      const int buf = c & 1;
+      const bool more = c + 1 < nchunk;
+      if (more) load_chunk(c + 1);
 #pragma unroll 4
       for (int jj = 0; jj < KC; ++jj) {
-        ST x[3][4], b[3][4];
+        ST x[3][4], b[3][RM];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          load4<ST>(&Xs[jj * 3 + c][ty * 4], x[c]);
-          load4<ST>(&Bs[jj * 3 + c][tx * 4], b[c]);
+        for (int cc = 0; cc < 3; ++cc) {
+          load4<ST>(&Xs[buf][jj * 3 + cc][ty * 4], x[cc]);
+#pragma unroll
+          for (int v = 0; v < RM; ++v) b[cc][v] = Bs[buf][jj * 3 + cc][tx * RM + v];
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
-          for (int v = 0; v < 4; ++v) {
+          for (int v = 0; v < RM; ++v) {
             const ST d0 = x[0][u] - b[0][v];
             const ST d1 = x[1][u] - b[1][v];
             const ST d2 = x[2][u] - b[2][v];
@@ -513,21 +553,24 @@ approx_pair_kernel(const int* __restrict__ alist, const int* __restrict__ aseg,
             acc[u][v] = t;
           }
       }
-      // chunk partials into an error-free (hi, lo) total
+      // every 2 chunks: chunk partials into the error-free (hi, lo) totals
+      if ((c & 1) || !more) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          if (sizeof(ST) == 4) {
-            float h = (float)thi[u][v], l = (float)tlo[u][v];
-            two_sum_acc(h, l, (float)acc[u][v]);
-            thi[u][v] = (ST)h;
-            tlo[u][v] = (ST)l;
-          } else {
-            thi[u][v] += acc[u][v];
+          for (int v = 0; v < RM; ++v) {
+            if (sizeof(ST) == 4) {
+              float h = (float)thi[u][v], l = (float)tlo[u][v];
+              two_sum_acc(h, l, (float)acc[u][v]);
+              thi[u][v] = (ST)h;
+              tlo[u][v] = (ST)l;
+            } else {
+              thi[u][v] += acc[u][v];
+            }
+            acc[u][v] = 0;
           }
-          acc[u][v] = 0;
-        }
+      }
+      if (more) store_chunk(c + 1, buf ^ 1);
       __syncthreads();
     }
 #pragma unroll
@@ -536,9 +579,165 @@ approx_pair_kernel(const int* __restrict__ alist, const int* __restrict__ aseg,
       if (ff < k || ff >= kend) continue;
       const int f = s_frame[ff];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const int i = i0 + tx * 4 + v;
+      for (int v = 0; v < RM; ++v) {
+        const int i = i0 + tx * RM + v;
         if (i < M) Dout[(size_t)f * M + i] = (thi[u][v] + tlo[u][v]) * dsc;
+      }
+    }
+    k = kend;
+    __syncthreads();
+  }
+}
+
+// FP32 modes.  Tile: 128 frames x (8 RM) landmarks, 128 threads, each 8 frames x RM
+// landmarks (40 pairs for RM = 5): per atom 8 x 3 frame values (6 LDS.128) and RM x 3
+// landmark values feed 6 RM x 8 FP32 operations.  Atoms come in chunks of 8; the chunk
+// sums of each pair go into an FP32 total every 32 atoms (relative rounding ~u sqrt(N/32),
+// 7.5e-7 at N = 5000).  Frames are centred and rotated by R_xy^T while staged, landmarks
+// rotated by R_{a_i y}.
+constexpr int AQ_TF = 128, AQ_THREADS = 128, AQ_KC = 8;
+
+template <typename LT, int RM>
+__global__ void __launch_bounds__(AQ_THREADS, 3)
+approx_pair_f32t(const int* __restrict__ alist, const int* __restrict__ aseg, const int* __restrict__ acount,
+                 const float* __restrict__ frames, const float4* __restrict__ c32, const double4* __restrict__ qxy,
+                 const LT* __restrict__ lm, const float* __restrict__ Bseg, const float* __restrict__ wts, int M,
+                 int N, float dscale, float* __restrict__ Dout) {
+  constexpr int TF = AQ_TF, TM = 8 * RM, KC = AQ_KC;
+  __shared__ __align__(16) float Xs[KC * 3][TF + 4];
+  __shared__ __align__(16) float Bs[KC * 3][TM + 4];
+  __shared__ float s_R[TF][9];
+  __shared__ float s_B[TM][9];
+  __shared__ float s_c[TF][3];
+  __shared__ int s_frame[TF], s_seg[TF];
+
+  const int count = *acount;
+  const int row0 = blockIdx.y * TF;
+  if (row0 >= count) return;
+  const int i0 = blockIdx.x * TM;
+  const int tid = threadIdx.x;
+  const int tx = tid & 7;   // landmarks i0 + RM tx + {0..RM-1}
+  const int ty = tid >> 3;  // rows 8 ty + {0..7}
+
+  if (tid < TF) {
+    const int r = row0 + tid;
+    int f = -1, sg = -1;
+    if (r < count) {
+      f = alist[r];
+      sg = aseg[r];
+    }
+    s_frame[tid] = f;
+    s_seg[tid] = sg;
+    float R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (f >= 0) {
+      c = c32[f];
+      const double4 qq = qxy[f];
+      const float qf[4] = {(float)qq.x, (float)qq.y, (float)qq.z, (float)qq.w};
+      quat_to_rot(qf, R);
+    }
+#pragma unroll
+    for (int e = 0; e < 9; ++e) s_R[tid][e] = R[e];
+    s_c[tid][0] = c.x;
+    s_c[tid][1] = c.y;
+    s_c[tid][2] = c.z;
+  }
+  __syncthreads();
+
+  int k = 0;
+  while (k < TF && s_frame[k] >= 0) {
+    const int seg = s_seg[k];
+    int kend = k;
+    while (kend < TF && s_frame[kend] >= 0 && s_seg[kend] == seg) ++kend;
+    for (int e = tid; e < TM * 9; e += AQ_THREADS) {
+      const int ll = e / 9, c = e - ll * 9;
+      const int i = i0 + ll;
+      s_B[ll][c] = (i < M) ? Bseg[((size_t)seg * M + i) * 9 + c] : 0.0f;
+    }
+    float acc[8][RM], tot[8][RM];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int v = 0; v < RM; ++v) acc[u][v] = tot[u][v] = 0.0f;
+    __syncthreads();
+    for (int j0 = 0, c = 0; j0 < N; j0 += KC, ++c) {
+      for (int e = tid; e < TF * KC; e += AQ_THREADS) {
+        const int ff = e / KC, jj = e - ff * KC;
+        const int j = j0 + jj;
+        float o0 = 0.0f, o1 = 0.0f, o2 = 0.0f;
+        if (ff >= k && ff < kend && j < N) {
+          const float* src = frames + ((size_t)s_frame[ff] * N + j) * 3;
+          const float v0 = src[0] - s_c[ff][0], v1 = src[1] - s_c[ff][1], v2 = src[2] - s_c[ff][2];
+          const float* R = s_R[ff];
+          const float sw = wts ? sqrtf(wts[j]) : 1.0f;
+          o0 = (R[0] * v0 + R[3] * v1 + R[6] * v2) * sw;
+          o1 = (R[1] * v0 + R[4] * v1 + R[7] * v2) * sw;
+          o2 = (R[2] * v0 + R[5] * v1 + R[8] * v2) * sw;
+        }
+        Xs[jj * 3 + 0][ff] = o0;
+        Xs[jj * 3 + 1][ff] = o1;
+        Xs[jj * 3 + 2][ff] = o2;
+      }
+      for (int e = tid; e < TM * KC; e += AQ_THREADS) {
+        const int ll = e / KC, jj = e - ll * KC;
+        const int j = j0 + jj, i = i0 + ll;
+        float b0 = 0.0f, b1 = 0.0f, b2 = 0.0f;
+        if (i < M && j < N) {
+          const LT* src = lm + ((size_t)i * N + j) * 3;
+          const float a0 = load_as<float>(src), a1 = load_as<float>(src + 1), a2 = load_as<float>(src + 2);
+          const float* B = s_B[ll];
+          const float sw = wts ? sqrtf(wts[j]) : 1.0f;
+          b0 = (B[0] * a0 + B[1] * a1 + B[2] * a2) * sw;
+          b1 = (B[3] * a0 + B[4] * a1 + B[5] * a2) * sw;
+          b2 = (B[6] * a0 + B[7] * a1 + B[8] * a2) * sw;
+        }
+        Bs[jj * 3 + 0][ll] = b0;
+        Bs[jj * 3 + 1][ll] = b1;
+        Bs[jj * 3 + 2][ll] = b2;
+      }
+      __syncthreads();
+#pragma unroll 2
+      for (int jj = 0; jj < KC; ++jj) {
+        float x[3][8], b[3][RM];
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+          const float4 xa = *reinterpret_cast<const float4*>(&Xs[jj * 3 + cc][ty * 8]);
+          const float4 xb = *reinterpret_cast<const float4*>(&Xs[jj * 3 + cc][ty * 8 + 4]);
+          x[cc][0] = xa.x; x[cc][1] = xa.y; x[cc][2] = xa.z; x[cc][3] = xa.w;
+          x[cc][4] = xb.x; x[cc][5] = xb.y; x[cc][6] = xb.z; x[cc][7] = xb.w;
+#pragma unroll
+          for (int v = 0; v < RM; ++v) b[cc][v] = Bs[jj * 3 + cc][tx * RM + v];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int v = 0; v < RM; ++v) {
+            const float d0 = x[0][u] - b[0][v];
+            const float d1 = x[1][u] - b[1][v];
+            const float d2 = x[2][u] - b[2][v];
+            acc[u][v] = fmaf(d0, d0, fmaf(d1, d1, fmaf(d2, d2, acc[u][v])));
+          }
+      }
+      if ((c & 3) == 3 || j0 + KC >= N) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int v = 0; v < RM; ++v) {
+            tot[u][v] += acc[u][v];
+            acc[u][v] = 0.0f;
+          }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int ff = ty * 8 + u;
+      if (ff < k || ff >= kend) continue;
+      const int f = s_frame[ff];
+#pragma unroll
+      for (int v = 0; v < RM; ++v) {
+        const int i = i0 + tx * RM + v;
+        if (i < M) Dout[(size_t)f * M + i] = tot[u][v] * dscale;
       }
     }
     k = kend;
@@ -574,28 +773,58 @@ void launch_exact_pairs(Prec p, int rows, const int* row_frame, const int* rows_
   }
 }
 
-void launch_approx_pairs(Prec p, int max_rows, const int* approx_list, const int* approx_seg,
-                           const int* count, const void* frames, const LandmarkDev& L, FrameInfo fi,
-                           const double4* qxy, const void* Bseg, void* D, cudaStream_t st) {
-  if (max_rows <= 0) return;
-  dim3 grid((L.M + AP_TM - 1) / AP_TM, (max_rows + AP_TF - 1) / AP_TF);
+// landmark tile of 32 or 40 (whichever wastes fewer rows of the last tile)
+static int approx_rm(int M) {
+  const int w4 = (M + 31) / 32 * 32 - M, w5 = (M + 39) / 40 * 40 - M;
+  return w5 < w4 ? 5 : 4;
+}
+
+template <int RM>
+static void approx_launch(Prec p, int max_rows, const int* approx_list, const int* approx_seg, const int* count,
+                          const void* frames, const LandmarkDev& L, FrameInfo fi, const double4* qxy,
+                          const void* Bseg, void* D, cudaStream_t st) {
+  dim3 grid((L.M + 8 * RM - 1) / (8 * RM), (max_rows + AP_TF - 1) / AP_TF);
+  if (p == P_F32 || p == P_F16) {
+    dim3 gq((L.M + 8 * RM - 1) / (8 * RM), (max_rows + AQ_TF - 1) / AQ_TF);
+    if (p == P_F32)
+      approx_pair_f32t<float, RM><<<gq, AQ_THREADS, 0, st>>>(approx_list, approx_seg, count, (const float*)frames,
+                                                             fi.c32, qxy, (const float*)L.coords, (const float*)Bseg,
+                                                             L.w, L.M, L.N, (float)L.dscale, (float*)D);
+    else
+      approx_pair_f32t<__half, RM><<<gq, AQ_THREADS, 0, st>>>(approx_list, approx_seg, count, (const float*)frames,
+                                                              fi.c32, qxy, (const __half*)L.coords, (const float*)Bseg,
+                                                              L.w, L.M, L.N, (float)L.dscale, (float*)D);
+    note_launch();
+    return;
+  }
   switch (p) {
     case P_F64:
-      approx_pair_kernel<double, double, double><<<grid, AP_THREADS, 0, st>>>(
-          approx_list, approx_seg, count, (const double*)frames, fi.c32, fi.c64, qxy,
-          (const double*)L.coords, (const double*)Bseg, L.w, L.M, L.N, L.dscale, (double*)D); note_launch();
+      approx_pair_kernel<double, double, double, RM><<<grid, AP_THREADS, 0, st>>>(
+          approx_list, approx_seg, count, (const double*)frames, fi.c32, fi.c64, qxy, (const double*)L.coords,
+          (const double*)Bseg, L.w, L.M, L.N, L.dscale, (double*)D);
       break;
     case P_F32:
-      approx_pair_kernel<float, float, float><<<grid, AP_THREADS, 0, st>>>(
+      approx_pair_kernel<float, float, float, RM><<<grid, AP_THREADS, 0, st>>>(
           approx_list, approx_seg, count, (const float*)frames, fi.c32, fi.c64, qxy, (const float*)L.coords,
-          (const float*)Bseg, L.w, L.M, L.N, L.dscale, (float*)D); note_launch();
+          (const float*)Bseg, L.w, L.M, L.N, L.dscale, (float*)D);
       break;
     case P_F16:
-      approx_pair_kernel<float, __half, float><<<grid, AP_THREADS, 0, st>>>(
+      approx_pair_kernel<float, __half, float, RM><<<grid, AP_THREADS, 0, st>>>(
           approx_list, approx_seg, count, (const float*)frames, fi.c32, fi.c64, qxy, (const __half*)L.coords,
-          (const float*)Bseg, L.w, L.M, L.N, L.dscale, (float*)D); note_launch();
+          (const float*)Bseg, L.w, L.M, L.N, L.dscale, (float*)D);
       break;
   }
+  note_launch();
+}
+
+void launch_approx_pairs(Prec p, int max_rows, const int* approx_list, const int* approx_seg, const int* count,
+                         const void* frames, const LandmarkDev& L, FrameInfo fi, const double4* qxy, const void* Bseg,
+                         void* D, cudaStream_t st) {
+  if (max_rows <= 0) return;
+  if (approx_rm(L.M) == 5)
+    approx_launch<5>(p, max_rows, approx_list, approx_seg, count, frames, L, fi, qxy, Bseg, D, st);
+  else
+    approx_launch<4>(p, max_rows, approx_list, approx_seg, count, frames, L, fi, qxy, Bseg, D, st);
 }
 
 }  // namespace pcv

@@ -59,6 +59,43 @@ __device__ __forceinline__ float warp_sum_float(float v) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Packed FP32 pairs (Blackwell f32x2 instructions): one instruction performs two IEEE FP32
+// operations with round-to-nearest, bit-identical to two scalar ones, at half the issue
+// cost.  A pair lives in a 64-bit register pair: low half = first element.
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(f2 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+  f2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+  f2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+  f2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+// (hi, lo) += v element-wise without losing the rounding error of the addition (TwoSum)
+__device__ __forceinline__ void f2_two_sum_acc(f2& hi, f2& lo, f2 v) {
+  const f2 s = f2_add(hi, v);
+  const f2 bp = f2_sub(s, hi);
+  const f2 err = f2_add(f2_sub(hi, f2_sub(s, bp)), f2_sub(v, bp));
+  hi = s;
+  lo = f2_add(lo, err);
+}
+
+// ---------------------------------------------------------------------------------------
 // storage conversions
 __device__ __forceinline__ float to_f32(float v) { return v; }
 __device__ __forceinline__ float to_f32(__half v) { return __half2float(v); }
