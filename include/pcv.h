@@ -170,8 +170,16 @@ enum {
   PCV_OPT_CHUNK = 2,       /* minimum frames per speculative x-y alignment chunk       */
   PCV_OPT_EXACT_TILE = 3,  /* tile variant index of the exact pair kernel              */
   PCV_OPT_APPROX_TILE = 4, /* tile variant index of the approximate pair kernel        */
-  PCV_OPT_PROFILE = 5      /* 1: time every kernel launch with CUDA events on the
+  PCV_OPT_PROFILE = 5,     /* 1: time every kernel launch with CUDA events on the
                               context's stream (see pcv_get_profile), 0: off (default)  */
+  PCV_OPT_MATERIALIZE = 6  /* byte cap (default 2^31) on the device buffers of the
+                              materialised close-structure operands: rotated frames
+                              x' = R_xy^T (x - c), rotated landmarks b = R_{a_i y} a per
+                              segment, and the gamma rows of the adjoint.  Used in the
+                              FP32 and FP16-storage modes with uniform weights when
+                              segments average 16 frames or more; 0 turns them off (the
+                              kernels then rotate while staging).  Results agree within
+                              the mode's tolerance either way.                          */
 };
 PCV_API pcv_status pcv_set_option(pcv_ctx* ctx, int key, int64_t value);
 
@@ -180,7 +188,7 @@ PCV_API pcv_status pcv_set_option(pcv_ctx* ctx, int key, int64_t value);
  * between events recorded around each launch on the context's stream, and launch counts.
  * ms and launches are host arrays of n entries (n <= PCV_PROFILE_KERNELS).  Synchronises
  * the stream, then clears the collected timings. */
-#define PCV_PROFILE_KERNELS 16
+#define PCV_PROFILE_KERNELS 20
 PCV_API pcv_status pcv_get_profile(pcv_ctx* ctx, int n, double* ms, int64_t* launches);
 
 /* Name of kernel family `id` ("" outside 0..PCV_PROFILE_KERNELS-1). */

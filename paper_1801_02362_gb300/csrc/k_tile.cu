@@ -1,0 +1,461 @@
+// k_tile.cu -- close-structure kernels on materialised, rotated operands (FP32 modes,
+// uniform weights).
+//
+// With the close structure every approximate frame x enters only as x' = R_xy^T (x - c),
+// and every landmark of segment s (frames sharing the close structure y(s)) only as
+// b = R_{a_i y} a (Eq. close_dist).  Writing x' once per frame and b once per segment turns
+// the two heavy loops into plain tiles over contiguous rows:
+//   approx_pair_tile:   D~_fi = sum_j |x'_fj - b_ij|^2 / N;
+//   adjoint_beta_tile:  beta_fj = sum_i gamma_fi b_ij, for gamma^s and gamma^z at once.
+// Rows are padded to N16 (a multiple of 16 atoms, zeros), so each chunk is a run of
+// 16-byte pieces moved global -> shared with cp.async in a 3-stage pipeline: copies of chunk
+// c+2 are in flight while chunk c is used, and no register holds staged data.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "pcv_device.cuh"
+#include "pcv_internal.h"
+
+namespace pcv {
+namespace {
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool pred) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = pred ? 16 : 0;  // 0 source bytes: the 16 shared bytes are zero-filled
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory");
+}
+
+template <typename LT>
+__device__ __forceinline__ float lm_f(const LT* p) {
+  return (float)(*p);
+}
+template <>
+__device__ __forceinline__ float lm_f<__half>(const __half* p) {
+  return __half2float(*p);
+}
+
+// ---------------------------------------------------------------------------------------
+// x'_k = R_xy^T (x_f - c_f), f = alist[k], one row of N16 atoms per approximate frame.
+__global__ void materialize_frames_kernel(int napp_max, const int* __restrict__ acount, const int* __restrict__ alist,
+                                          int N, int N16, const float* __restrict__ frames,
+                                          const float4* __restrict__ c32, const double4* __restrict__ qxy,
+                                          float* __restrict__ Xr) {
+  const int k = blockIdx.x;
+  if (k >= napp_max || k >= *acount) return;
+  const int f = alist[k];
+  const float4 c = c32[f];
+  const double4 qq = qxy[f];
+  const float qf[4] = {(float)qq.x, (float)qq.y, (float)qq.z, (float)qq.w};
+  float R[9];
+  quat_to_rot(qf, R);
+  const float* x = frames + (size_t)f * N * 3;
+  float* out = Xr + (size_t)k * N16 * 3;
+  for (int j = threadIdx.x; j < N16; j += blockDim.x) {
+    float o0 = 0.0f, o1 = 0.0f, o2 = 0.0f;
+    if (j < N) {
+      const float v0 = x[3 * j] - c.x, v1 = x[3 * j + 1] - c.y, v2 = x[3 * j + 2] - c.z;
+      o0 = R[0] * v0 + R[3] * v1 + R[6] * v2;
+      o1 = R[1] * v0 + R[4] * v1 + R[7] * v2;
+      o2 = R[2] * v0 + R[5] * v1 + R[8] * v2;
+    }
+    out[3 * j] = o0;
+    out[3 * j + 1] = o1;
+    out[3 * j + 2] = o2;
+  }
+}
+
+// b_{s,i} = R_{a_i y(s)} a_i for segments s in [s0, s0 + gridDim.y), rows of N16 atoms.
+template <typename LT>
+__global__ void materialize_landmarks_kernel(int s0, int M, int N, int N16, const LT* __restrict__ lm,
+                                             const float* __restrict__ Bseg, float* __restrict__ Bm) {
+  const int i = blockIdx.x, s = s0 + blockIdx.y;
+  const float* B = Bseg + ((size_t)s * M + i) * 9;
+  float R[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) R[e] = B[e];
+  const LT* a = lm + (size_t)i * N * 3;
+  float* out = Bm + ((size_t)blockIdx.y * M + i) * N16 * 3;
+  for (int j = threadIdx.x; j < N16; j += blockDim.x) {
+    float o0 = 0.0f, o1 = 0.0f, o2 = 0.0f;
+    if (j < N) {
+      const float a0 = lm_f(a + 3 * j), a1 = lm_f(a + 3 * j + 1), a2 = lm_f(a + 3 * j + 2);
+      o0 = R[0] * a0 + R[1] * a1 + R[2] * a2;
+      o1 = R[3] * a0 + R[4] * a1 + R[5] * a2;
+      o2 = R[6] * a0 + R[7] * a1 + R[8] * a2;
+    }
+    out[3 * j] = o0;
+    out[3 * j + 1] = o1;
+    out[3 * j + 2] = o2;
+  }
+}
+
+// gamma^s_fi = -lambda p_fi (q_i - s_f), gamma^z_fi = p_fi (Eqs. 5-6 differentiated), rows of
+// Mp >= M entries, zero beyond M.
+__global__ void gamma_kernel(int F, int M, int Mp, const float* __restrict__ P, const float* __restrict__ q32,
+                             const double* __restrict__ s, float lambda, float* __restrict__ GS, float* __restrict__ GZ) {
+  const size_t total = (size_t)F * Mp;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int f = (int)(e / Mp), i = (int)(e - (size_t)f * Mp);
+    float gs = 0.0f, gz = 0.0f;
+    if (i < M) {
+      const float p = P[(size_t)f * M + i];
+      gz = p;
+      gs = -lambda * p * (q32[i] - (float)s[f]);
+    }
+    GS[e] = gs;
+    GZ[e] = gz;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// approximate MSDs.  Tile: 64 approximate frames x 8 RM landmarks, 128 threads; thread
+// (tx, ty) holds frames u*16 + ty (u < 4) and landmarks v*8 + tx (v < RM).  Chunks of 16
+// atoms (192 bytes per row); shared rows of 52 floats, so the 4 frame rows and the 8 landmark
+// rows a warp reads at one step fall in distinct banks.  Two atoms per step: 3 LDS.64 per row.
+constexpr int AT_TF = 64, AT_THREADS = 128, AT_KC = 16, AT_STAGES = 3;
+constexpr int AT_ROWF = AT_KC * 3 + 4;
+
+template <int RM>
+__global__ void __launch_bounds__(AT_THREADS, 3)
+approx_pair_tile(const int* __restrict__ alist, const int* __restrict__ aseg, const int* __restrict__ acount,
+                 int seg_base, int M, int N16, const float* __restrict__ Xr, const float* __restrict__ Bm,
+                 float dscale, float* __restrict__ Dout) {
+  constexpr int TF = AT_TF, TM = 8 * RM;
+  extern __shared__ __align__(16) float smem[];
+  float* Xs = smem;                            // [stage][TF][ROWF]
+  float* Ls = smem + AT_STAGES * TF * AT_ROWF;  // [stage][TM][ROWF]
+  __shared__ int s_seg[TF];
+  __shared__ int s_frame[TF];
+  const int count = *acount;
+  const int i0 = blockIdx.x * TM;
+  const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+  const int nchunk = N16 / AT_KC;
+  const size_t rowlen = (size_t)N16 * 3;
+  for (int row0 = blockIdx.y * TF; row0 < count; row0 += gridDim.y * TF) {
+    __syncthreads();  // the previous tile's reads of s_seg / s_frame are done
+    if (tid < TF) {
+      const int r = row0 + tid;
+      s_seg[tid] = r < count ? aseg[r] : -1;
+      s_frame[tid] = r < count ? alist[r] : -1;
+    }
+    __syncthreads();
+    int k = 0;
+    while (k < TF && s_seg[k] >= 0) {
+      const int seg = s_seg[k];
+      int kend = k;
+      while (kend < TF && s_seg[kend] == seg) ++kend;
+      const float* Bsrc = Bm + (size_t)(seg - seg_base) * M * rowlen;
+      auto issue = [&](int c) {
+        const int st = c % AT_STAGES;
+        float* xs = Xs + st * TF * AT_ROWF;
+        float* ls = Ls + st * TM * AT_ROWF;
+        const size_t col = (size_t)c * AT_KC * 3;
+        for (int e = tid; e < (TF + TM) * 12; e += AT_THREADS) {  // 12 pieces of 16 bytes per row
+          const int row = e / 12, piece = e - row * 12;
+          if (row < TF) {
+            const bool ok = row >= k && row < kend;
+            const float* src = ok ? Xr + (size_t)(row0 + row) * rowlen + col + piece * 4 : Xr;
+            cp_async16(xs + row * AT_ROWF + piece * 4, src, ok);
+          } else {
+            const int ll = row - TF, i = i0 + ll;
+            const bool ok = i < M;
+            const float* src = ok ? Bsrc + (size_t)i * rowlen + col + piece * 4 : Bm;
+            cp_async16(ls + ll * AT_ROWF + piece * 4, src, ok);
+          }
+        }
+      };
+      float acc[4][RM], thi[4][RM], tlo[4][RM];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < RM; ++v) acc[u][v] = thi[u][v] = tlo[u][v] = 0.0f;
+#pragma unroll
+      for (int st = 0; st < AT_STAGES - 1; ++st) {
+        if (st < nchunk) issue(st);
+        cp_async_commit();
+      }
+      for (int c = 0; c < nchunk; ++c) {
+        cp_async_wait<AT_STAGES - 2>();
+        __syncthreads();
+        if (c + AT_STAGES - 1 < nchunk) issue(c + AT_STAGES - 1);
+        cp_async_commit();
+        const int st = c % AT_STAGES;
+        const float* xs = Xs + st * TF * AT_ROWF;
+        const float* ls = Ls + st * TM * AT_ROWF;
+#pragma unroll 2
+        for (int a = 0; a < AT_KC; a += 2) {
+          float x[4][6], b[RM][6];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int h = 0; h < 3; ++h) {
+              const float2 t = *reinterpret_cast<const float2*>(xs + (u * 16 + ty) * AT_ROWF + a * 3 + 2 * h);
+              x[u][2 * h] = t.x;
+              x[u][2 * h + 1] = t.y;
+            }
+#pragma unroll
+          for (int v = 0; v < RM; ++v)
+#pragma unroll
+            for (int h = 0; h < 3; ++h) {
+              const float2 t = *reinterpret_cast<const float2*>(ls + (v * 8 + tx) * AT_ROWF + a * 3 + 2 * h);
+              b[v][2 * h] = t.x;
+              b[v][2 * h + 1] = t.y;
+            }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < RM; ++v) {
+              float t = acc[u][v];
+#pragma unroll
+              for (int e = 0; e < 6; ++e) {
+                const float d = x[u][e] - b[v][e];
+                t = fmaf(d, d, t);
+              }
+              acc[u][v] = t;
+            }
+        }
+        if ((c & 1) || c + 1 == nchunk) {  // every 32 atoms into the compensated totals
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < RM; ++v) {
+              two_sum_acc(thi[u][v], tlo[u][v], acc[u][v]);
+              acc[u][v] = 0.0f;
+            }
+        }
+      }
+      cp_async_wait<0>();
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int ff = u * 16 + ty;
+        if (ff < k || ff >= kend) continue;
+        const int f = s_frame[ff];
+#pragma unroll
+        for (int v = 0; v < RM; ++v) {
+          const int i = i0 + v * 8 + tx;
+          if (i < M) Dout[(size_t)f * M + i] = (thi[u][v] + tlo[u][v]) * dscale;
+        }
+      }
+      k = kend;
+      __syncthreads();  // the next run's first copies overwrite stages still being read
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// beta for frames grouped by segment.  Tile: 64 consecutive frames x 32 atoms, 256 threads,
+// each 4 frames x 2 atoms x 3 components x {s, z}.  Landmark chunks of 16: per frame a row
+// of 16 gamma^s and 16 gamma^z, per landmark 32 atoms of b (384 bytes, 24 pieces).  Per
+// four landmarks: one LDS.128 of each gamma per frame, 3 LDS.64 of b per landmark.
+constexpr int BT_TF = 64, BT_TJ = 32, BT_KL = 16, BT_THREADS = 256, BT_STAGES = 3;
+constexpr int BT_GROW = BT_KL + 4;
+constexpr int BT_BROW = BT_TJ * 3 + 4;
+
+__global__ void __launch_bounds__(BT_THREADS, 2)
+adjoint_beta_tile(int F, int M, int Mp, int N, int N16, int seg_base, const float* __restrict__ GS,
+                  const float* __restrict__ GZ, const float* __restrict__ Bm, const int* __restrict__ seg_of_frame,
+                  float* __restrict__ gs, float* __restrict__ gz) {
+  extern __shared__ __align__(16) float smem[];
+  float* Gss = smem;                               // [stage][TF][GROW]
+  float* Gzs = Gss + BT_STAGES * BT_TF * BT_GROW;  // [stage][TF][GROW]
+  float* Bbs = Gzs + BT_STAGES * BT_TF * BT_GROW;  // [stage][KL][BROW]
+  __shared__ int s_seg[BT_TF];
+  const int j0 = blockIdx.x * BT_TJ;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int nchunk = Mp / BT_KL;
+  const size_t rowlen = (size_t)N16 * 3;
+  const int colend = N16 * 3 - j0 * 3;  // floats of the row left from this tile's first atom
+  for (int f0 = blockIdx.y * BT_TF; f0 < F; f0 += gridDim.y * BT_TF) {
+    __syncthreads();  // the previous tile's reads of s_seg are done
+    if (tid < BT_TF) s_seg[tid] = f0 + tid < F ? seg_of_frame[f0 + tid] : -1;
+    float acs[4][6], acz[4][6];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int e = 0; e < 6; ++e) acs[u][e] = acz[u][e] = 0.0f;
+    __syncthreads();
+    int k = 0;
+    while (k < BT_TF && s_seg[k] >= 0) {
+      const int seg = s_seg[k];
+      int kend = k;
+      while (kend < BT_TF && s_seg[kend] == seg) ++kend;
+      const float* Bsrc = Bm + (size_t)(seg - seg_base) * M * rowlen + (size_t)j0 * 3;
+      auto issue = [&](int c) {
+        const int st = c % BT_STAGES;
+        float* gss = Gss + st * BT_TF * BT_GROW;
+        float* gzs = Gzs + st * BT_TF * BT_GROW;
+        float* bbs = Bbs + st * BT_KL * BT_BROW;
+        const int i0 = c * BT_KL;
+        for (int e = tid; e < BT_TF * 8 + BT_KL * 24; e += BT_THREADS) {
+          if (e < BT_TF * 8) {  // per frame 4 pieces of gamma^s, then 4 of gamma^z
+            const int row = e >> 3, pc = e & 7, piece = pc & 3;
+            const bool ok = row >= k && row < kend;
+            const float* base = pc < 4 ? GS : GZ;
+            const float* src = ok ? base + (size_t)(f0 + row) * Mp + i0 + piece * 4 : GS;
+            cp_async16((pc < 4 ? gss : gzs) + row * BT_GROW + piece * 4, src, ok);
+          } else {
+            const int e2 = e - BT_TF * 8;
+            const int ll = e2 / 24, piece = e2 - ll * 24;
+            const int i = i0 + ll;
+            const bool ok = i < M && piece * 4 < colend;
+            const float* src = ok ? Bsrc + (size_t)i * rowlen + piece * 4 : Bm;
+            cp_async16(bbs + ll * BT_BROW + piece * 4, src, ok);
+          }
+        }
+      };
+#pragma unroll
+      for (int st = 0; st < BT_STAGES - 1; ++st) {
+        if (st < nchunk) issue(st);
+        cp_async_commit();
+      }
+      for (int c = 0; c < nchunk; ++c) {
+        cp_async_wait<BT_STAGES - 2>();
+        __syncthreads();
+        if (c + BT_STAGES - 1 < nchunk) issue(c + BT_STAGES - 1);
+        cp_async_commit();
+        const int st = c % BT_STAGES;
+        const float* gss = Gss + st * BT_TF * BT_GROW;
+        const float* gzs = Gzs + st * BT_TF * BT_GROW;
+        const float* bbs = Bbs + st * BT_KL * BT_BROW;
+#pragma unroll
+        for (int i4 = 0; i4 < BT_KL; i4 += 4) {
+          float g1[4][4], g2[4][4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4 a = *reinterpret_cast<const float4*>(gss + (ty * 4 + u) * BT_GROW + i4);
+            const float4 b = *reinterpret_cast<const float4*>(gzs + (ty * 4 + u) * BT_GROW + i4);
+            g1[u][0] = a.x;
+            g1[u][1] = a.y;
+            g1[u][2] = a.z;
+            g1[u][3] = a.w;
+            g2[u][0] = b.x;
+            g2[u][1] = b.y;
+            g2[u][2] = b.z;
+            g2[u][3] = b.w;
+          }
+#pragma unroll
+          for (int l = 0; l < 4; ++l) {
+            float bv[6];
+#pragma unroll
+            for (int h = 0; h < 3; ++h) {
+              const float2 t = *reinterpret_cast<const float2*>(bbs + (i4 + l) * BT_BROW + tx * 6 + 2 * h);
+              bv[2 * h] = t.x;
+              bv[2 * h + 1] = t.y;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int e = 0; e < 6; ++e) {
+                acs[u][e] = fmaf(g1[u][l], bv[e], acs[u][e]);
+                acz[u][e] = fmaf(g2[u][l], bv[e], acz[u][e]);
+              }
+          }
+        }
+      }
+      cp_async_wait<0>();
+      __syncthreads();  // the next run's first copies overwrite stages still being read
+      k = kend;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int f = f0 + ty * 4 + u;
+      if (f >= F) continue;
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const int j = j0 + tx * 2 + a;
+        if (j >= N) continue;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          gs[((size_t)f * N + j) * 3 + c] = acs[u][3 * a + c];
+          gz[((size_t)f * N + j) * 3 + c] = acz[u][3 * a + c];
+        }
+      }
+    }
+  }
+}
+
+template <typename K>
+void set_smem(K kernel, size_t bytes) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+int tile_rm(int M) {
+  const int w4 = (M + 31) / 32 * 32 - M, w5 = (M + 39) / 40 * 40 - M;
+  return w5 < w4 ? 5 : 4;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+size_t tile_bytes_frames(int napp, int N) { return (size_t)napp * round_up16(N) * 3 * sizeof(float); }
+size_t tile_bytes_landmarks(int nseg, int M, int N) {
+  return (size_t)nseg * M * round_up16(N) * 3 * sizeof(float);
+}
+size_t tile_bytes_gamma(int F, int M) { return (size_t)2 * F * round_up16(M) * sizeof(float); }
+
+void launch_materialize_frames(int napp, const int* acount, const int* alist, const LandmarkDev& L,
+                               const void* frames, FrameInfo fi, const double4* qxy, float* Xr, cudaStream_t st) {
+  if (napp <= 0) return;
+  materialize_frames_kernel<<<napp, 128, 0, st>>>(napp, acount, alist, L.N, round_up16(L.N), (const float*)frames,
+                                                  fi.c32, qxy, Xr);
+  note_launch();
+}
+
+void launch_materialize_landmarks(Prec p, int s0, int ns, const LandmarkDev& L, const float* Bseg, float* Bm,
+                                  cudaStream_t st) {
+  if (ns <= 0 || L.M <= 0) return;
+  const dim3 grid(L.M, ns);
+  const int N16 = round_up16(L.N);
+  if (p == P_F16)
+    materialize_landmarks_kernel<__half><<<grid, 128, 0, st>>>(s0, L.M, L.N, N16, (const __half*)L.coords, Bseg, Bm);
+  else
+    materialize_landmarks_kernel<float><<<grid, 128, 0, st>>>(s0, L.M, L.N, N16, (const float*)L.coords, Bseg, Bm);
+  note_launch();
+}
+
+void launch_gamma(int F, const LandmarkDev& L, const float* P, const double* s, double lambda, float* GS, float* GZ,
+                  cudaStream_t st) {
+  if (F <= 0) return;
+  const int Mp = round_up16(L.M);
+  const size_t total = (size_t)F * Mp;
+  const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, (size_t)152 * 16);
+  gamma_kernel<<<blocks, 256, 0, st>>>(F, L.M, Mp, P, L.q32, s, (float)lambda, GS, GZ);
+  note_launch();
+}
+
+void launch_approx_pairs_tile(int napp, const int* alist, const int* aseg, const int* acount, int seg_base,
+                              const LandmarkDev& L, const float* Xr, const float* Bm, float* D, cudaStream_t st) {
+  if (napp <= 0 || L.M <= 0) return;
+  const int rm = tile_rm(L.M), tm = 8 * rm, N16 = round_up16(L.N);
+  const size_t smem = (size_t)AT_STAGES * (AT_TF + tm) * AT_ROWF * sizeof(float);
+  const dim3 grid((L.M + tm - 1) / tm, std::min((napp + AT_TF - 1) / AT_TF, 65535));
+  if (rm == 5) {
+    set_smem(approx_pair_tile<5>, smem);
+    approx_pair_tile<5><<<grid, AT_THREADS, smem, st>>>(alist, aseg, acount, seg_base, L.M, N16, Xr, Bm,
+                                                         (float)L.dscale, D);
+  } else {
+    set_smem(approx_pair_tile<4>, smem);
+    approx_pair_tile<4><<<grid, AT_THREADS, smem, st>>>(alist, aseg, acount, seg_base, L.M, N16, Xr, Bm,
+                                                         (float)L.dscale, D);
+  }
+  note_launch();
+}
+
+void launch_adjoint_beta_tile(int F, const LandmarkDev& L, int seg_base, const float* GS, const float* GZ,
+                              const float* Bm, const int* seg_of_frame, float* gs, float* gz, cudaStream_t st) {
+  if (F <= 0) return;
+  const size_t smem = (size_t)BT_STAGES * (2 * BT_TF * BT_GROW + BT_KL * BT_BROW) * sizeof(float);
+  const dim3 grid((L.N + BT_TJ - 1) / BT_TJ, std::min((F + BT_TF - 1) / BT_TF, 65535));
+  set_smem(adjoint_beta_tile, smem);
+  adjoint_beta_tile<<<grid, BT_THREADS, smem, st>>>(F, L.M, round_up16(L.M), L.N, round_up16(L.N), seg_base, GS, GZ,
+                                                    Bm, seg_of_frame, gs, gz);
+  note_launch();
+}
+
+}  // namespace pcv

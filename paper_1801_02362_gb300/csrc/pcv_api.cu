@@ -55,12 +55,12 @@ thread_local int64_t t_launches = 0;
 // kernel families timed by the profiler
 enum KernelId {
   K_PREP = 0, K_BAND, K_RECHECK, K_SCAN, K_CHUNK, K_FIRST, K_RECORDS, K_COMPACT, K_EXACT, K_APPROX,
-  K_FINAL, K_ADJ_BETA, K_ADJ_FINISH, K_COMBINE, K_XY_REFINE, K_ADJ_BETA_SEG, K_COUNT
+  K_FINAL, K_ADJ_BETA, K_ADJ_FINISH, K_COMBINE, K_XY_REFINE, K_ADJ_BETA_SEG, K_MATERIALIZE, K_GAMMA, K_COUNT
 };
 const char* const kKernelNames[PCV_PROFILE_KERNELS] = {
     "frame_prep", "align_band", "recheck_fp64", "band_scan", "align_chunk", "first_exceed", "records",
     "compact", "exact_pair", "approx_pair", "finalize", "adjoint_beta_pair", "adjoint_finish", "combine_grad", "xy_refine",
-    "adjoint_beta_seg"};
+    "adjoint_beta_seg", "materialize", "gamma", "", ""};
 
 struct ProfEvent {
   int id;
@@ -88,6 +88,7 @@ struct pcv_ctx {
   double eps = -1.0;
   int band_W = 2;
   int min_chunk = 4096;
+  int64_t mat_cap = int64_t(2) << 30;  // bytes of materialised operands allowed (PCV_OPT_MATERIALIZE)
   double gap_estimate = 0.0;
   // close state
   bool has_y = false;
@@ -98,6 +99,7 @@ struct pcv_ctx {
   // workspace
   DevBuf c32, c64, fG, bandD, bandQ, bandF, chD, chQ, chF, rlist, rcount, recF, recRef, recD, recQ, reflist,
       segof, alist, aseg, Dbuf, Rpair, Bseg, mstat, status, nrecheck, small;
+  DevBuf Xr, Bm, GSb, GZb;  // materialised x', b and the gamma rows
   DevBuf h_frames, h_s, h_z, h_gs, h_gz, h_msd, h_ref;  // device staging for pcv_evaluate_host
   Small* small_host = nullptr;
   pcv_stats stats{};
@@ -271,7 +273,7 @@ pcv_status pcv_destroy(pcv_ctx* c) {
   DevBuf* bufs[] = {&c->lm, &c->lmG, &c->lmA, &c->lmA32, &c->lmq, &c->lmq32, &c->w32, &c->w64, &c->y, &c->Bprior, &c->c32, &c->c64,
                     &c->fG, &c->bandD, &c->bandQ, &c->bandF, &c->chD, &c->chQ, &c->chF, &c->rlist, &c->rcount,
                     &c->recF, &c->recRef, &c->recD, &c->recQ, &c->reflist, &c->segof, &c->alist, &c->aseg,
-                    &c->Dbuf, &c->Rpair, &c->Bseg, &c->mstat, &c->status, &c->nrecheck, &c->small, &c->h_frames,
+                    &c->Dbuf, &c->Rpair, &c->Bseg, &c->Xr, &c->Bm, &c->GSb, &c->GZb, &c->mstat, &c->status, &c->nrecheck, &c->small, &c->h_frames,
                     &c->h_s, &c->h_z, &c->h_gs, &c->h_gz, &c->h_msd, &c->h_ref};
   for (DevBuf* b : bufs) release(*b);
   for (const ProfEvent& e : c->prof_pending) {
@@ -320,6 +322,10 @@ pcv_status pcv_set_option(pcv_ctx* c, int key, int64_t value) {
       return PCV_OK;
     case PCV_OPT_PROFILE:
       c->prof_on = value != 0;
+      return PCV_OK;
+    case PCV_OPT_MATERIALIZE:
+      if (value < 0) return fail(c, PCV_EINVAL, "materialise cap must be >= 0");
+      c->mat_cap = value;
       return PCV_OK;
     case PCV_OPT_EXACT_TILE:
     case PCV_OPT_APPROX_TILE:
@@ -622,15 +628,44 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
   if ((ps = ensure(c, c->Bseg, seg_bytes * (size_t)(nref + 1))) != PCV_OK) return ps;
   if (had_prior) CUDA_TRY(c, cudaMemcpyAsync(c->Bseg.p, c->Bprior.p, seg_bytes, cudaMemcpyDeviceToDevice, st));
   void* Bseg1 = (char*)c->Bseg.p + seg_bytes;
+  // Frames sharing close structures (segments of 16 frames or more on average): the
+  // segment GEMM form of the adjoint, and with FP32 arithmetic and uniform weights the
+  // materialised operands x' and b when they fit the cap.
+  const bool grads = gs && gz;
+  const bool seg_form = (int64_t)(nref + 1) * 16 <= (int64_t)F;
+  const int seg_base = had_prior ? 0 : 1;  // without a prior structure segment 0 is empty
+  const int nseg = nref + 1 - seg_base;
+  bool tiled = false;
+  if (c->prec != P_F64 && c->uniform && seg_form && nseg > 0) {
+    const size_t xb = tile_bytes_frames(napp, c->N), bb = tile_bytes_landmarks(nseg, M, c->N);
+    const size_t gb = grads ? tile_bytes_gamma(F, M) / 2 : 0;
+    if ((int64_t)(xb + bb + 2 * gb) <= c->mat_cap) {
+      if ((ps = ensure(c, c->Xr, xb)) != PCV_OK) return ps;
+      if ((ps = ensure(c, c->Bm, bb)) != PCV_OK) return ps;
+      if (grads && (ps = ensure(c, c->GSb, gb)) != PCV_OK) return ps;
+      if (grads && (ps = ensure(c, c->GZb, gb)) != PCV_OK) return ps;
+      tiled = true;
+    }
+  }
   {
     PROF(c, K_EXACT);
     launch_exact_pairs(c->prec, nref, (const int*)c->reflist.p, nullptr, frames, L, fi, c->Dbuf.p, Bseg1,
                        (unsigned*)c->status.p, st);
   }
+  if (tiled) {
+    PROF(c, K_MATERIALIZE);
+    launch_materialize_landmarks(c->prec, seg_base, nseg, L, (const float*)c->Bseg.p, (float*)c->Bm.p, st);
+    launch_materialize_frames(napp, &sm->approx_count, (const int*)c->alist.p, L, frames, fi, rec.qxy,
+                              (float*)c->Xr.p, st);
+  }
   {
     PROF(c, K_APPROX);
-    launch_approx_pairs(c->prec, napp, (const int*)c->alist.p, (const int*)c->aseg.p, &sm->approx_count, frames,
-                        L, fi, rec.qxy, c->Bseg.p, c->Dbuf.p, st);
+    if (tiled)
+      launch_approx_pairs_tile(napp, (const int*)c->alist.p, (const int*)c->aseg.p, &sm->approx_count, seg_base, L,
+                               (const float*)c->Xr.p, (const float*)c->Bm.p, (float*)c->Dbuf.p, st);
+    else
+      launch_approx_pairs(c->prec, napp, (const int*)c->alist.p, (const int*)c->aseg.p, &sm->approx_count, frames,
+                          L, fi, rec.qxy, c->Bseg.p, c->Dbuf.p, st);
   }
   {
     PROF(c, K_FINAL);
@@ -638,10 +673,16 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
                     gs != nullptr, st);
   }
   if (refreshed) CUDA_TRY(c, cudaMemcpyAsync(refreshed, rec.flag, F, cudaMemcpyDeviceToDevice, st));
-  if (gs && gz) {
-    // frames sharing close structures: the segment GEMM; frequent reassignments: per pair
-    const bool seg_form = (int64_t)(nref + 1) * 16 <= (int64_t)F;
-    {
+  if (grads) {
+    if (tiled) {
+      {
+        PROF(c, K_GAMMA);
+        launch_gamma(F, L, (const float*)c->Dbuf.p, s, c->lambda, (float*)c->GSb.p, (float*)c->GZb.p, st);
+      }
+      PROF(c, K_ADJ_BETA_SEG);
+      launch_adjoint_beta_tile(F, L, seg_base, (const float*)c->GSb.p, (const float*)c->GZb.p, (const float*)c->Bm.p,
+                               (const int*)c->segof.p, (float*)gs, (float*)gz, st);
+    } else {
       ProfScope ps(c, seg_form && c->prec != P_F64 ? K_ADJ_BETA_SEG : K_ADJ_BETA);
       launch_adjoint_beta(c->prec, F, L, c->Dbuf.p, s, c->lambda, nullptr, c->Bseg.p, (const int*)c->segof.p,
                           seg_form, gs, gz, st);

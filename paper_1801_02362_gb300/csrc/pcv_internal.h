@@ -143,4 +143,25 @@ void launch_approx_pairs(Prec p, int max_rows, const int* approx_list, const int
                          const int* count, const void* frames, const LandmarkDev& L, FrameInfo fi,
                          const double4* qxy, const void* Bseg, void* D, cudaStream_t st);
 
+// ---------------------------------------------------------------------------------------
+// materialised-operand path (k_tile.cu; FP32 and FP16-storage modes, uniform weights).
+// Rows padded to round_up16(N) atoms; Bm holds segments [seg_base, seg_base + ns).
+inline int round_up16(int n) { return (n + 15) & ~15; }
+size_t tile_bytes_frames(int napp, int N);
+size_t tile_bytes_landmarks(int nseg, int M, int N);
+size_t tile_bytes_gamma(int F, int M);
+// x'_k = R_xy^T (x - c) for approximate frames k < *acount (f = alist[k])
+void launch_materialize_frames(int napp, const int* acount, const int* alist, const LandmarkDev& L,
+                               const void* frames, FrameInfo fi, const double4* qxy, float* Xr, cudaStream_t st);
+// b = R_{a_i y} a_i for segments [s0, s0 + ns), rotations Bseg (9 floats each)
+void launch_materialize_landmarks(Prec p, int s0, int ns, const LandmarkDev& L, const float* Bseg, float* Bm,
+                                  cudaStream_t st);
+// gamma^s, gamma^z rows (round_up16(M) entries each) from the softmax weights P
+void launch_gamma(int F, const LandmarkDev& L, const float* P, const double* s, double lambda, float* GS, float* GZ,
+                  cudaStream_t st);
+void launch_approx_pairs_tile(int napp, const int* alist, const int* aseg, const int* acount, int seg_base,
+                              const LandmarkDev& L, const float* Xr, const float* Bm, float* D, cudaStream_t st);
+void launch_adjoint_beta_tile(int F, const LandmarkDev& L, int seg_base, const float* GS, const float* GZ,
+                              const float* Bm, const int* seg_of_frame, float* gs, float* gz, cudaStream_t st);
+
 }  // namespace pcv

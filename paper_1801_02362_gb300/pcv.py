@@ -19,7 +19,8 @@ from . import build_lib
 PCV_OK, PCV_EINVAL, PCV_ECUDA, PCV_ENOMEM, PCV_ENOCONV, PCV_ESTATE = 0, -1, -2, -3, -4, -5
 PCV_FP64, PCV_FP32, PCV_FP16_STORAGE = 0, 1, 2
 PCV_OPT_BAND, PCV_OPT_CHUNK, PCV_OPT_EXACT_TILE, PCV_OPT_APPROX_TILE, PCV_OPT_PROFILE = 1, 2, 3, 4, 5
-PCV_PROFILE_KERNELS = 16
+PCV_OPT_MATERIALIZE = 6
+PCV_PROFILE_KERNELS = 20
 
 _STATUS_NAMES = {0: "PCV_OK", -1: "PCV_EINVAL", -2: "PCV_ECUDA", -3: "PCV_ENOMEM", -4: "PCV_ENOCONV",
                  -5: "PCV_ESTATE"}
@@ -211,7 +212,7 @@ class PathCV:
 
     def __init__(self, landmarks: np.ndarray, lam: float, eps: float = -1.0, precision: str = "fp32",
                  weights: np.ndarray | None = None, props: np.ndarray | None = None, device: int = 0,
-                 band: int | None = None, min_chunk: int | None = None):
+                 band: int | None = None, min_chunk: int | None = None, materialize: int | None = None):
         import torch
 
         self.torch = torch
@@ -227,6 +228,8 @@ class PathCV:
             pcv_set_option(self.ctx, PCV_OPT_BAND, band)
         if min_chunk is not None:
             pcv_set_option(self.ctx, PCV_OPT_CHUNK, min_chunk)
+        if materialize is not None:
+            pcv_set_option(self.ctx, PCV_OPT_MATERIALIZE, materialize)
 
     @property
     def frame_dtype(self):
