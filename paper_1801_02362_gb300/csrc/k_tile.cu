@@ -10,6 +10,11 @@
 // Rows are padded to N16 (a multiple of 16 atoms, zeros), so each chunk is a run of
 // 16-byte pieces moved global -> shared with cp.async in a 3-stage pipeline: copies of chunk
 // c+2 are in flight while chunk c is used, and no register holds staged data.
+//
+// The approximate-MSD loop uses packed FP32 pairs (f32x2) over adjacent coordinates of x'
+// and b: each instruction performs two IEEE FP32 operations, which frees issue slots for the
+// shared-memory loads (the packed operations run on one of the two FP32 sub-pipes, so the
+// FP32 rate itself is unchanged).
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -117,7 +122,8 @@ __global__ void gamma_kernel(int F, int M, int Mp, const float* __restrict__ P, 
 // approximate MSDs.  Tile: 64 approximate frames x 8 RM landmarks, 128 threads; thread
 // (tx, ty) holds frames u*16 + ty (u < 4) and landmarks v*8 + tx (v < RM).  Chunks of 16
 // atoms (192 bytes per row); shared rows of 52 floats, so the 4 frame rows and the 8 landmark
-// rows a warp reads at one step fall in distinct banks.  Two atoms per step: 3 LDS.64 per row.
+// rows a warp reads at one step fall in distinct banks.  Two atoms per step: 3 LDS.64 per
+// row, each an adjacent coordinate pair; per (frame, landmark) 3 SUB2 + 3 FMA2.
 constexpr int AT_TF = 64, AT_THREADS = 128, AT_KC = 16, AT_STAGES = 3;
 constexpr int AT_ROWF = AT_KC * 3 + 4;
 
@@ -170,11 +176,15 @@ approx_pair_tile(const int* __restrict__ alist, const int* __restrict__ aseg, co
           }
         }
       };
-      float acc[4][RM], thi[4][RM], tlo[4][RM];
+      f2 acc[4][RM];
+      float thi[4][RM], tlo[4][RM];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < RM; ++v) acc[u][v] = thi[u][v] = tlo[u][v] = 0.0f;
+        for (int v = 0; v < RM; ++v) {
+          acc[u][v] = 0ull;  // the bit pattern of (+0, +0)
+          thi[u][v] = tlo[u][v] = 0.0f;
+        }
 #pragma unroll
       for (int st = 0; st < AT_STAGES - 1; ++st) {
         if (st < nchunk) issue(st);
@@ -190,43 +200,39 @@ approx_pair_tile(const int* __restrict__ alist, const int* __restrict__ aseg, co
         const float* ls = Ls + st * TM * AT_ROWF;
 #pragma unroll 2
         for (int a = 0; a < AT_KC; a += 2) {
-          float x[4][6], b[RM][6];
+          f2 x[4][3], b[RM][3];
 #pragma unroll
           for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int h = 0; h < 3; ++h) {
-              const float2 t = *reinterpret_cast<const float2*>(xs + (u * 16 + ty) * AT_ROWF + a * 3 + 2 * h);
-              x[u][2 * h] = t.x;
-              x[u][2 * h + 1] = t.y;
-            }
+            for (int h = 0; h < 3; ++h)
+              x[u][h] = *reinterpret_cast<const f2*>(xs + (u * 16 + ty) * AT_ROWF + a * 3 + 2 * h);
 #pragma unroll
           for (int v = 0; v < RM; ++v)
 #pragma unroll
-            for (int h = 0; h < 3; ++h) {
-              const float2 t = *reinterpret_cast<const float2*>(ls + (v * 8 + tx) * AT_ROWF + a * 3 + 2 * h);
-              b[v][2 * h] = t.x;
-              b[v][2 * h + 1] = t.y;
-            }
+            for (int h = 0; h < 3; ++h)
+              b[v][h] = *reinterpret_cast<const f2*>(ls + (v * 8 + tx) * AT_ROWF + a * 3 + 2 * h);
 #pragma unroll
           for (int u = 0; u < 4; ++u)
 #pragma unroll
             for (int v = 0; v < RM; ++v) {
-              float t = acc[u][v];
+              f2 t = acc[u][v];
 #pragma unroll
-              for (int e = 0; e < 6; ++e) {
-                const float d = x[u][e] - b[v][e];
-                t = fmaf(d, d, t);
+              for (int h = 0; h < 3; ++h) {
+                const f2 d = f2_sub(x[u][h], b[v][h]);
+                t = f2_fma(d, d, t);
               }
               acc[u][v] = t;
             }
         }
-        if ((c & 1) || c + 1 == nchunk) {  // every 32 atoms into the compensated totals
+        if ((c & 3) == 3 || c + 1 == nchunk) {  // every 64 atoms into the compensated totals
 #pragma unroll
           for (int u = 0; u < 4; ++u)
 #pragma unroll
             for (int v = 0; v < RM; ++v) {
-              two_sum_acc(thi[u][v], tlo[u][v], acc[u][v]);
-              acc[u][v] = 0.0f;
+              float lo, hi;
+              f2_unpack(acc[u][v], lo, hi);
+              two_sum_acc(thi[u][v], tlo[u][v], lo + hi);
+              acc[u][v] = 0ull;
             }
         }
       }
@@ -397,7 +403,7 @@ size_t tile_bytes_frames(int napp, int N) { return (size_t)napp * round_up16(N) 
 size_t tile_bytes_landmarks(int nseg, int M, int N) {
   return (size_t)nseg * M * round_up16(N) * 3 * sizeof(float);
 }
-size_t tile_bytes_gamma(int F, int M) { return (size_t)2 * F * round_up16(M) * sizeof(float); }
+size_t tile_bytes_gamma(int F, int M) { return (size_t)F * round_up16(M) * sizeof(float); }
 
 void launch_materialize_frames(int napp, const int* acount, const int* alist, const LandmarkDev& L,
                                const void* frames, FrameInfo fi, const double4* qxy, float* Xr, cudaStream_t st) {

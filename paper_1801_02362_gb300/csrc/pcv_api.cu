@@ -638,7 +638,7 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
   bool tiled = false;
   if (c->prec != P_F64 && c->uniform && seg_form && nseg > 0) {
     const size_t xb = tile_bytes_frames(napp, c->N), bb = tile_bytes_landmarks(nseg, M, c->N);
-    const size_t gb = grads ? tile_bytes_gamma(F, M) / 2 : 0;
+    const size_t gb = grads ? tile_bytes_gamma(F, M) : 0;  // per gamma kind
     if ((int64_t)(xb + bb + 2 * gb) <= c->mat_cap) {
       if ((ps = ensure(c, c->Xr, xb)) != PCV_OK) return ps;
       if ((ps = ensure(c, c->Bm, bb)) != PCV_OK) return ps;

@@ -156,7 +156,8 @@ void launch_materialize_frames(int napp, const int* acount, const int* alist, co
 // b = R_{a_i y} a_i for segments [s0, s0 + ns), rotations Bseg (9 floats each)
 void launch_materialize_landmarks(Prec p, int s0, int ns, const LandmarkDev& L, const float* Bseg, float* Bm,
                                   cudaStream_t st);
-// gamma^s, gamma^z rows (round_up16(M) entries each) from the softmax weights P
+// gamma^s, gamma^z rows (round_up16(M) entries each, tile_bytes_gamma bytes per kind) from
+// the softmax weights P
 void launch_gamma(int F, const LandmarkDev& L, const float* P, const double* s, double lambda, float* GS, float* GZ,
                   cudaStream_t st);
 void launch_approx_pairs_tile(int napp, const int* alist, const int* aseg, const int* acount, int seg_base,
