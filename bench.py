@@ -43,7 +43,20 @@ FLOPS_PER_UNIT = {
     "exact_pair": 45,         # pass 1: 9 FMA; pass 2: R a (9 FMA), 3 sub, 3 FMA
     "adjoint_beta_pair": 36,  # beta^s, beta^z += gamma R_i a (2 x 9 FMA), per-pair rotations
     "adjoint_beta_seg": 12,   # beta^s, beta^z += gamma b_i (2 x 3 FMA), b_i shared by a segment
+    "adjoint_beta_mma": 12,   # the same product on the tensor cores (3 TF32 MMAs per product)
 }
+TENSOR_KERNELS = {"adjoint_beta_mma"}
+# TF32 tensor peak: measured bf16 cuBLAS rate x the nominal TF32/bf16 ratio (1.1 / 2.25 PFLOP/s)
+TF32_PER_BF16 = 1.1 / 2.25
+
+
+def measured_peaks() -> dict:
+    """Peaks measured on this GPU pool (HBM copy bandwidth, bf16 cuBLAS burst and sustained)."""
+    path = ROOT / "MEASURED_PEAKS.json"
+    try:
+        return json.loads(path.read_text())
+    except (OSError, ValueError):
+        return {}
 
 
 def parse():
@@ -292,9 +305,17 @@ def run_ours(args):
         units = F * N_LANDMARKS * N_ATOMS / launches_per_step
     flops = FLOPS_PER_UNIT[dom] * units
     achieved = flops / (per_launch_ms / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz max clock (derived; FP32 FMA pipe)",
+    if dom in TENSOR_KERNELS:
+        peaks = measured_peaks()
+        peak = peaks.get("bf16_tflops_sustained", 1700.0) * TF32_PER_BF16
+        bound, peak_source = "tensor", ("TF32 dense: measured sustained bf16 cuBLAS rate x 1.1/2.25 (nominal TF32/bf16); "
+                                        "3xTF32 issues 3 MMAs per algorithmic product, so frac <= 1/3")
+    else:
+        peak, bound = FP32_PEAK_TFLOPS, "alu"
+        peak_source = "152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz max clock (derived; FP32 FMA pipe)"
+    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": peak_source,
                 "per_launch_ms": per_launch_ms,
                 "flops_per_launch": flops,
                 "kernel_share": {k: round(v / total_ms, 4) for k, v in sorted(share.items(), key=lambda kv: -kv[1])}}

@@ -55,7 +55,9 @@ typedef enum {
   PCV_ECUDA = -2,   /* a CUDA runtime call failed; see pcv_last_error()                */
   PCV_ENOMEM = -3,  /* device or host allocation failed                                 */
   PCV_ENOCONV = -4, /* an eigen-solve hit its iteration cap (reported at pcv_sync)      */
-  PCV_ESTATE = -5   /* call out of order (no landmarks, bad saved state, ...)           */
+  PCV_ESTATE = -5,  /* call out of order (no landmarks, bad saved state, ...)           */
+  PCV_ETIMEOUT = -6 /* a bounded device-side wait expired (reported at pcv_sync); the
+                       results of the batches since the previous pcv_sync are invalid */
 } pcv_status;
 
 typedef enum { PCV_FP64 = 0, PCV_FP32 = 1, PCV_FP16_STORAGE = 2 } pcv_precision;
@@ -159,8 +161,9 @@ PCV_API pcv_status pcv_load_state(pcv_ctx* ctx, const void* buf, size_t len);
 /* Copy the counters.  Synchronises the context's stream. */
 PCV_API pcv_status pcv_get_stats(pcv_ctx* ctx, pcv_stats* out);
 
-/* Wait for the context's work and report deferred device errors (PCV_ENOCONV when an
- * eigen-solve hit its iteration cap since the last pcv_sync). */
+/* Wait for the context's work and report deferred device errors since the last pcv_sync:
+ * PCV_ETIMEOUT when a kernel's bounded wait expired, PCV_ENOCONV when an eigen-solve hit
+ * its iteration cap. */
 PCV_API pcv_status pcv_sync(pcv_ctx* ctx);
 
 /* Tuning knobs (pcv_set_option keys). */
@@ -172,7 +175,7 @@ enum {
   PCV_OPT_APPROX_TILE = 4, /* tile variant index of the approximate pair kernel        */
   PCV_OPT_PROFILE = 5,     /* 1: time every kernel launch with CUDA events on the
                               context's stream (see pcv_get_profile), 0: off (default)  */
-  PCV_OPT_MATERIALIZE = 6  /* byte cap (default 2^31) on the device buffers of the
+  PCV_OPT_MATERIALIZE = 6, /* byte cap (default 2^31) on the device buffers of the
                               materialised close-structure operands: rotated frames
                               x' = R_xy^T (x - c), rotated landmarks b = R_{a_i y} a per
                               segment, and the gamma rows of the adjoint.  Used in the
@@ -180,6 +183,10 @@ enum {
                               segments average 16 frames or more; 0 turns them off (the
                               kernels then rotate while staging).  Results agree within
                               the mode's tolerance either way.                          */
+  PCV_OPT_TENSOR_CORES = 7 /* 1 (default): with materialised operands, the segment adjoint
+                              beta = sum_i gamma_i (R_{a_i y} a_i) runs on the tensor cores
+                              (TF32 operands split hi + lo, three products per term, on
+                              deviations from the close structure); 0: FP32 CUDA cores.   */
 };
 PCV_API pcv_status pcv_set_option(pcv_ctx* ctx, int key, int64_t value);
 

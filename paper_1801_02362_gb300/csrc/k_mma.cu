@@ -1,0 +1,470 @@
+// k_mma.cu -- the segment adjoint as a tensor-core GEMM (tcgen05, TF32 inputs split 3 ways).
+//
+// For frames sharing the close structure y of a segment, the adjoint needs
+//   beta_f = sum_i gamma_fi b_i,   b_i = R_{a_i y} a_i  (3N values per landmark)
+// for gamma^s and gamma^z (the derivatives of Eqs. 5-6 with respect to the MSDs).  Per
+// segment this is a dense product: rows (frame, s|z) x K = landmarks x columns 3N.  It runs
+// on the 5th-generation tensor cores (tcgen05.mma, kind::tf32, accumulator in tensor
+// memory) with two measures for FP32 accuracy:
+//   * deviations: the product uses delta_i = b_i - y' (y' = the centred close structure),
+//     and the epilogue adds Gamma_f y' (Gamma_f = sum_i gamma_fi).  The weights gamma are
+//     concentrated on landmarks near the frame, hence near y, so the accumulated terms are
+//     small compared with beta itself;
+//   * 3xTF32: every operand is split v = hi + lo, hi = v truncated to TF32 (10 mantissa bits),
+//     lo = v - hi truncated likewise, and the product is hi*hi + hi*lo + lo*hi (relative
+//     error about 2^-21 per product instead of 2^-11).
+//
+// The producers write both operands pre-tiled in the canonical K-major shared-memory layout
+// without swizzling: core matrices of 8 rows x 16 bytes (4 TF32 values) stored as 128
+// contiguous bytes, the 4 core matrices of a 16-value K chunk 128 bytes apart (LBO) and the
+// 8-row groups 512 bytes apart (SBO).  So one stage of operands is four contiguous blocks
+// moved by cp.async.bulk (one producer thread, completion counted in bytes on an mbarrier);
+// one thread issues the MMAs and tcgen05.commit releases each stage when its MMAs are done.
+// Every wait is bounded by a clock budget: on expiry the kernel records STATUS_TIMEOUT,
+// waits for its copies and MMAs within a second budget, frees its tensor memory and returns.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "pcv_device.cuh"
+#include "pcv_internal.h"
+
+namespace pcv {
+namespace {
+
+constexpr int MM_ROWS = 128;  // MMA M: 64 frames x {gamma^s, gamma^z}
+constexpr int MM_FRAMES = 64;
+constexpr int MM_KC = 16;       // K values (landmarks) per stage
+constexpr int MM_BN_MAX = 256;  // columns per CTA (MMA N), multiple of 16
+constexpr int MM_THREADS = 128;
+constexpr int MM_STAGES = 4;
+constexpr int MM_TMEM_COLS = 256;
+constexpr int MM_A_BYTES = MM_ROWS * MM_KC * 4;  // one operand part (hi or lo) of one K chunk
+constexpr long long MM_WAIT_CYCLES = 4000000000LL;  // about 2 s at the maximum SM clock
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
+
+// byte offset of (row r, K value kk < 16) inside one canonical K-major block
+__host__ __device__ __forceinline__ uint32_t canon_off(int r, int kk) {
+  return (uint32_t)((r >> 3) * 512 + (kk >> 2) * 128 + (r & 7) * 16 + (kk & 3) * 4);
+}
+
+// shared-memory matrix descriptor: K-major, no swizzling
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for this architecture
+  return d;                // base offset 0, absolute LBO mode, layout type 0 (no swizzle)
+}
+
+// instruction descriptor: kind::tf32, FP32 accumulator, A and B TF32 and K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4)                      // D format: F32
+         | (2u << 7)                    // A format: TF32
+         | (2u << 10)                   // B format: TF32
+         | ((uint32_t)(N >> 3) << 17)   // N / 8
+         | ((uint32_t)(M >> 4) << 24);  // M / 16
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(mbar)
+      : "memory");
+}
+
+// bounded wait for the phase with the given parity; false after the clock budget
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > MM_WAIT_CYCLES) return false;
+  }
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
+}
+
+// ---------------------------------------------------------------------------------------
+// gamma operand: for frame tile t (64 frames) and K chunk c, blocks hi | lo of 128 rows x 16
+// values (rows 0..63 gamma^s of frames 64t + r, rows 64..127 gamma^z), zero for landmarks
+// >= M and frames >= F; and Gamma^s_f, Gamma^z_f.  One warp per frame (Fp = frames rounded
+// up to 64).
+__global__ void gamma_split_kernel(int F, int Fp, int M, int Kp, const float* __restrict__ P,
+                                   const float* __restrict__ q32, const double* __restrict__ s, float lambda,
+                                   float* __restrict__ A, float* __restrict__ Gsum) {
+  const int lane = threadIdx.x & 31;
+  const int f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (f >= Fp) return;
+  const bool live = f < F;
+  const float sf = live ? (float)s[f] : 0.0f;
+  const int nck = Kp / MM_KC;
+  const int t = f / MM_FRAMES, r = f % MM_FRAMES;
+  float ss = 0.0f, sz = 0.0f;
+  for (int i = lane; i < Kp; i += 32) {
+    float gs = 0.0f, gz = 0.0f;
+    if (live && i < M) {
+      const float p = P[(size_t)f * M + i];
+      gz = p;
+      gs = -lambda * p * (q32[i] - sf);
+    }
+    ss += gs;
+    sz += gz;
+    const int c = i / MM_KC, kk = i % MM_KC;
+    uint8_t* blk = reinterpret_cast<uint8_t*>(A) + ((size_t)t * nck + c) * 2 * MM_A_BYTES;
+    const float hs = tf32_hi(gs), hz = tf32_hi(gz);
+    *reinterpret_cast<float*>(blk + canon_off(r, kk)) = hs;
+    *reinterpret_cast<float*>(blk + canon_off(r + MM_FRAMES, kk)) = hz;
+    *reinterpret_cast<float*>(blk + MM_A_BYTES + canon_off(r, kk)) = tf32_hi(gs - hs);
+    *reinterpret_cast<float*>(blk + MM_A_BYTES + canon_off(r + MM_FRAMES, kk)) = tf32_hi(gz - hz);
+  }
+  ss = warp_sum_float(ss);
+  sz = warp_sum_float(sz);
+  if (lane == 0 && live) {
+    Gsum[2 * f] = ss;
+    Gsum[2 * f + 1] = sz;
+  }
+}
+
+// deviation operand: for segment slot s (segment seg_base + s), column tile nt (BN values of
+// n = 3j + c) and K chunk c, blocks hi | lo of BN rows x 16 values holding
+// delta_i[n] = b_i[n] - y'[n].  The buffer is zeroed beforehand (rows n >= 3N, landmarks
+// >= M).  Block (i, s) also writes y'[s][n] when i == 0.  y is the prior structure for
+// segment 0, else the frame refresh_list[seg - 1].
+template <typename LT>
+__global__ void delta_split_kernel(int seg_base, int M, int N, int Kp, int BN, int NT, const LT* __restrict__ lm,
+                                   const float* __restrict__ Bseg, const float* __restrict__ frames,
+                                   const float4* __restrict__ c32, const int* __restrict__ refresh_list,
+                                   const float* __restrict__ prior, float4 prior_c, float* __restrict__ B,
+                                   float* __restrict__ Yc) {
+  const int i = blockIdx.x, slot = blockIdx.y, seg = seg_base + slot;
+  const int NB = 3 * N;
+  const int nck = Kp / MM_KC;
+  const float* y;
+  float4 c;
+  if (seg == 0) {
+    y = prior;
+    c = prior_c;
+  } else {
+    const int f = refresh_list[seg - 1];
+    y = frames + (size_t)f * NB;
+    c = c32[f];
+  }
+  float R[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) R[e] = Bseg[((size_t)seg * M + i) * 9 + e];
+  const size_t bblk = (size_t)BN * MM_KC * 4;  // bytes of one part of one block
+  const int ck = i / MM_KC, kk = i % MM_KC;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const float yv[3] = {y[3 * j] - c.x, y[3 * j + 1] - c.y, y[3 * j + 2] - c.z};
+    const LT* a = lm + ((size_t)i * N + j) * 3;
+    const float a0 = (float)a[0], a1 = (float)a[1], a2 = (float)a[2];
+    const float d[3] = {(R[0] * a0 + R[1] * a1 + R[2] * a2) - yv[0], (R[3] * a0 + R[4] * a1 + R[5] * a2) - yv[1],
+                        (R[6] * a0 + R[7] * a1 + R[8] * a2) - yv[2]};
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+      const int n = 3 * j + cc;
+      const int nt = n / BN, r = n % BN;
+      uint8_t* blk = reinterpret_cast<uint8_t*>(B) + (((size_t)slot * NT + nt) * nck + ck) * 2 * bblk;
+      const float h = tf32_hi(d[cc]);
+      *reinterpret_cast<float*>(blk + canon_off(r, kk)) = h;
+      *reinterpret_cast<float*>(blk + bblk + canon_off(r, kk)) = tf32_hi(d[cc] - h);
+      if (i == 0) Yc[(size_t)slot * NB + n] = yv[cc];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// beta tile: rows 64 frames x {s, z}, columns [n0, n0 + BN) of 3N.  The tile's frames are
+// taken in runs of equal segment; each run accumulates from zero over all K chunks with its
+// segment's deviations and writes the rows of its own frames.
+struct MmaArgs {
+  int F, M, N, Kp, BN, NT, seg_base, tile0;
+  const float *A, *Gsum, *B, *Yc;
+  const int* seg_of_frame;
+  float *gs, *gz;
+  unsigned* status;
+};
+
+__global__ void __launch_bounds__(MM_THREADS, 1) adjoint_beta_mma(MmaArgs p) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t full[MM_STAGES], empty[MM_STAGES], done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_seg[MM_FRAMES];
+  __shared__ int s_run[MM_FRAMES + 1];
+  __shared__ int s_nrun;
+  __shared__ int s_fail;
+  __shared__ int s_fail_run;
+  __shared__ int s_issued;  // chunks whose copies the producer started (global counter)
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tile = p.tile0 + blockIdx.y;
+  const int f0 = tile * MM_FRAMES;
+  const int n0 = blockIdx.x * p.BN;
+  const int NB = 3 * p.N;
+  const int nck = p.Kp / MM_KC;
+  const uint32_t idesc = idesc_tf32(MM_ROWS, p.BN);
+  const uint32_t a_bytes = MM_A_BYTES, b_bytes = (uint32_t)p.BN * MM_KC * 4;
+  const uint32_t stage_bytes = 2 * a_bytes + 2 * (uint32_t)MM_BN_MAX * MM_KC * 4;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(MM_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < MM_STAGES; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(&done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_fail = 0;
+    s_issued = 0;
+  }
+  if (tid < MM_FRAMES) s_seg[tid] = f0 + tid < p.F ? p.seg_of_frame[f0 + tid] : -1;
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  if (tid == 0) {  // runs of equal segment among the tile's frames
+    int n = 0, k = 0;
+    while (k < MM_FRAMES && s_seg[k] >= 0) {
+      s_run[n++] = k;
+      int e = k;
+      while (e < MM_FRAMES && s_seg[e] == s_seg[k]) ++e;
+      k = e;
+    }
+    s_run[n] = k;
+    s_nrun = n;
+  }
+  __syncthreads();
+  const int nrun = s_nrun;
+  const uint32_t sbase = smem_u32(smem);
+  const uint8_t* Ab = reinterpret_cast<const uint8_t*>(p.A) + (size_t)tile * nck * 2 * a_bytes;
+
+  for (int run = 0; run < nrun; ++run) {
+    const int k = s_run[run], kend = s_run[run + 1];
+    const int slot = s_seg[k] - p.seg_base;
+    const uint8_t* Bb =
+        reinterpret_cast<const uint8_t*>(p.B) + (((size_t)slot * p.NT + blockIdx.x) * nck) * 2 * b_bytes;
+    const int g0 = run * nck;  // global chunk counter: stage and phase bookkeeping across runs
+    if (warp == 1) {
+      if (lane == 0) {  // producer
+        for (int c = 0; c < nck; ++c) {
+          const int g = g0 + c, st = g % MM_STAGES;
+          if (g >= MM_STAGES && !mbar_wait(smem_u32(&empty[st]), (uint32_t)((g / MM_STAGES - 1) & 1))) {
+            s_fail = 1;
+            break;
+          }
+          const uint32_t dst = sbase + st * stage_bytes;
+          mbar_expect_tx(smem_u32(&full[st]), 2 * a_bytes + 2 * b_bytes);
+          bulk_g2s(dst, Ab + (size_t)c * 2 * a_bytes, 2 * a_bytes, smem_u32(&full[st]));
+          bulk_g2s(dst + 2 * a_bytes, Bb + (size_t)c * 2 * b_bytes, 2 * b_bytes, smem_u32(&full[st]));
+          s_issued = g + 1;
+        }
+      }
+      __syncwarp();
+    } else if (warp == 0) {
+      if (lane == 0) {  // MMA issuer
+        for (int c = 0; c < nck; ++c) {
+          const int g = g0 + c, st = g % MM_STAGES;
+          if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((g / MM_STAGES) & 1))) {
+            s_fail = 1;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t ah = sbase + st * stage_bytes, al = ah + a_bytes;
+          const uint32_t bh = ah + 2 * a_bytes, bl = bh + b_bytes;
+#pragma unroll
+          for (int ks = 0; ks < MM_KC / 8; ++ks) {  // 8 TF32 values per MMA: 2 core matrices, 256 bytes
+            const uint32_t off = ks * 256;
+            const uint64_t dah = smem_desc(ah + off, 128, 512), dal = smem_desc(al + off, 128, 512);
+            const uint64_t dbh = smem_desc(bh + off, 128, 512), dbl = smem_desc(bl + off, 128, 512);
+            mma_tf32(tmem, dah, dbh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+            mma_tf32(tmem, dah, dbl, idesc, 1u);
+            mma_tf32(tmem, dal, dbh, idesc, 1u);
+          }
+          mma_commit(smem_u32(&empty[st]));
+        }
+        mma_commit(smem_u32(&done));
+      }
+      __syncwarp();
+    }
+    // all warps: wait for the run's MMAs, then the epilogue beta = D + Gamma_f y'
+    const bool ok = mbar_wait(smem_u32(&done), (uint32_t)(run & 1));
+    if (!ok) s_fail = 1;
+    __syncthreads();
+    if (s_fail) {
+      s_fail_run = run;  // every thread writes the same value
+      break;
+    }
+    tc_fence_after();
+    const int r = warp * 32 + lane;
+    const bool zrow = r >= MM_FRAMES;
+    const int ff = r & (MM_FRAMES - 1);
+    const int f = f0 + ff;
+    const bool mine = ff >= k && ff < kend && f < p.F;
+    const float Gam = mine ? p.Gsum[2 * f + (zrow ? 1 : 0)] : 0.0f;
+    const float* yrow = p.Yc + (size_t)slot * NB;
+    float* out = (zrow ? p.gz : p.gs) + (size_t)f * NB;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int cb = 0; cb < p.BN; cb += 16) {
+      float v[16];
+      tmem_ld16(trow + cb, v);
+      if (mine) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int n = n0 + cb + e;
+          if (n < NB) out[n] = fmaf(Gam, yrow[n], v[e]);
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();  // the accumulator is read before the next run overwrites it
+  }
+  if (s_fail) {
+    // Copies and MMAs already issued still land in this CTA's memory: wait for them, within
+    // the same budget, before the tensor memory is released.  The extra commit arrives once
+    // every MMA issued so far is done; the producer waits for the last copy of each stage.
+    if (tid == 0) {
+      atomicOr(p.status, STATUS_TIMEOUT);
+      mma_commit(smem_u32(&done));
+    }
+    if (tid == 32) {
+      const int last = s_issued;
+      for (int g = std::max(0, last - MM_STAGES); g < last; ++g)
+        mbar_wait(smem_u32(&full[g % MM_STAGES]), (uint32_t)((g / MM_STAGES) & 1));
+    }
+    mbar_wait(smem_u32(&done), (uint32_t)(s_fail_run & 1));
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(MM_TMEM_COLS) : "memory");
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+MmaShape mma_shape(int F, int M, int N) {
+  MmaShape s;
+  s.Kp = (M + MM_KC - 1) / MM_KC * MM_KC;
+  s.Fp = (F + MM_FRAMES - 1) / MM_FRAMES * MM_FRAMES;
+  const int NB = 3 * N;
+  const int nt = (NB + MM_BN_MAX - 1) / MM_BN_MAX;
+  s.BN = ((NB + nt - 1) / nt + 15) / 16 * 16;
+  s.NT = (NB + s.BN - 1) / s.BN;
+  s.a_bytes = (size_t)s.Fp * 2 * s.Kp * 2 * sizeof(float);
+  s.b_bytes_per_seg = (size_t)s.NT * s.BN * s.Kp * 2 * sizeof(float);
+  s.y_bytes_per_seg = (size_t)NB * sizeof(float);
+  return s;
+}
+
+void launch_gamma_split(int F, const LandmarkDev& L, const MmaShape& sh, const float* P, const double* s,
+                        double lambda, float* A, float* Gsum, cudaStream_t st) {
+  if (F <= 0) return;
+  gamma_split_kernel<<<sh.Fp / 8, 256, 0, st>>>(F, sh.Fp, L.M, sh.Kp, P, L.q32, s, (float)lambda, A, Gsum);
+  note_launch();
+}
+
+void launch_delta_split(Prec p, int seg_base, int nseg, const LandmarkDev& L, const MmaShape& sh, const float* Bseg,
+                        const void* frames, FrameInfo fi, const int* refresh_list, const RefDesc& prior, float* B,
+                        float* Yc, cudaStream_t st) {
+  if (nseg <= 0 || L.M <= 0) return;
+  cudaMemsetAsync(B, 0, sh.b_bytes_per_seg * nseg, st);
+  const dim3 grid(L.M, nseg);
+  if (p == P_F16)
+    delta_split_kernel<__half><<<grid, 128, 0, st>>>(seg_base, L.M, L.N, sh.Kp, sh.BN, sh.NT, (const __half*)L.coords,
+                                                     Bseg, (const float*)frames, fi.c32, refresh_list,
+                                                     (const float*)prior.coords, prior.c32, B, Yc);
+  else
+    delta_split_kernel<float><<<grid, 128, 0, st>>>(seg_base, L.M, L.N, sh.Kp, sh.BN, sh.NT, (const float*)L.coords,
+                                                    Bseg, (const float*)frames, fi.c32, refresh_list,
+                                                    (const float*)prior.coords, prior.c32, B, Yc);
+  note_launch();
+}
+
+void launch_adjoint_beta_mma(int F, const LandmarkDev& L, const MmaShape& sh, int seg_base, const float* A,
+                             const float* Gsum, const float* B, const float* Yc, const int* seg_of_frame, float* gs,
+                             float* gz, unsigned* status, cudaStream_t st) {
+  if (F <= 0) return;
+  MmaArgs a;
+  a.F = F;
+  a.M = L.M;
+  a.N = L.N;
+  a.Kp = sh.Kp;
+  a.BN = sh.BN;
+  a.NT = sh.NT;
+  a.seg_base = seg_base;
+  a.A = A;
+  a.Gsum = Gsum;
+  a.B = B;
+  a.Yc = Yc;
+  a.seg_of_frame = seg_of_frame;
+  a.gs = gs;
+  a.gz = gz;
+  a.status = status;
+  const size_t smem = (size_t)MM_STAGES * (2 * MM_A_BYTES + 2 * MM_BN_MAX * MM_KC * 4);
+  cudaFuncSetAttribute(adjoint_beta_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int tiles = sh.Fp / MM_FRAMES;
+  for (int t0 = 0; t0 < tiles; t0 += 65535) {
+    a.tile0 = t0;
+    const dim3 grid(sh.NT, std::min(tiles - t0, 65535));
+    adjoint_beta_mma<<<grid, MM_THREADS, smem, st>>>(a);
+    note_launch();
+  }
+}
+
+}  // namespace pcv

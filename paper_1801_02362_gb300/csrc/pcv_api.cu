@@ -55,12 +55,12 @@ thread_local int64_t t_launches = 0;
 // kernel families timed by the profiler
 enum KernelId {
   K_PREP = 0, K_BAND, K_RECHECK, K_SCAN, K_CHUNK, K_FIRST, K_RECORDS, K_COMPACT, K_EXACT, K_APPROX,
-  K_FINAL, K_ADJ_BETA, K_ADJ_FINISH, K_COMBINE, K_XY_REFINE, K_ADJ_BETA_SEG, K_MATERIALIZE, K_GAMMA, K_COUNT
+  K_FINAL, K_ADJ_BETA, K_ADJ_FINISH, K_COMBINE, K_XY_REFINE, K_ADJ_BETA_SEG, K_MATERIALIZE, K_GAMMA, K_ADJ_MMA, K_COUNT
 };
 const char* const kKernelNames[PCV_PROFILE_KERNELS] = {
     "frame_prep", "align_band", "recheck_fp64", "band_scan", "align_chunk", "first_exceed", "records",
     "compact", "exact_pair", "approx_pair", "finalize", "adjoint_beta_pair", "adjoint_finish", "combine_grad", "xy_refine",
-    "adjoint_beta_seg", "materialize", "gamma", "", ""};
+    "adjoint_beta_seg", "materialize", "gamma", "adjoint_beta_mma", ""};
 
 struct ProfEvent {
   int id;
@@ -89,6 +89,7 @@ struct pcv_ctx {
   int band_W = 2;
   int min_chunk = 4096;
   int64_t mat_cap = int64_t(2) << 30;  // bytes of materialised operands allowed (PCV_OPT_MATERIALIZE)
+  bool tensor_cores = true;             // segment adjoint on the tensor cores (PCV_OPT_TENSOR_CORES)
   double gap_estimate = 0.0;
   // close state
   bool has_y = false;
@@ -100,6 +101,7 @@ struct pcv_ctx {
   DevBuf c32, c64, fG, bandD, bandQ, bandF, chD, chQ, chF, rlist, rcount, recF, recRef, recD, recQ, reflist,
       segof, alist, aseg, Dbuf, Rpair, Bseg, mstat, status, nrecheck, small;
   DevBuf Xr, Bm, GSb, GZb;  // materialised x', b and the gamma rows
+  DevBuf Amma, Gsum, Bmma, Ymma;  // tensor-core adjoint operands
   DevBuf h_frames, h_s, h_z, h_gs, h_gz, h_msd, h_ref;  // device staging for pcv_evaluate_host
   Small* small_host = nullptr;
   pcv_stats stats{};
@@ -273,7 +275,7 @@ pcv_status pcv_destroy(pcv_ctx* c) {
   DevBuf* bufs[] = {&c->lm, &c->lmG, &c->lmA, &c->lmA32, &c->lmq, &c->lmq32, &c->w32, &c->w64, &c->y, &c->Bprior, &c->c32, &c->c64,
                     &c->fG, &c->bandD, &c->bandQ, &c->bandF, &c->chD, &c->chQ, &c->chF, &c->rlist, &c->rcount,
                     &c->recF, &c->recRef, &c->recD, &c->recQ, &c->reflist, &c->segof, &c->alist, &c->aseg,
-                    &c->Dbuf, &c->Rpair, &c->Bseg, &c->Xr, &c->Bm, &c->GSb, &c->GZb, &c->mstat, &c->status, &c->nrecheck, &c->small, &c->h_frames,
+                    &c->Dbuf, &c->Rpair, &c->Bseg, &c->Xr, &c->Bm, &c->GSb, &c->GZb, &c->Amma, &c->Gsum, &c->Bmma, &c->Ymma, &c->mstat, &c->status, &c->nrecheck, &c->small, &c->h_frames,
                     &c->h_s, &c->h_z, &c->h_gs, &c->h_gz, &c->h_msd, &c->h_ref};
   for (DevBuf* b : bufs) release(*b);
   for (const ProfEvent& e : c->prof_pending) {
@@ -326,6 +328,9 @@ pcv_status pcv_set_option(pcv_ctx* c, int key, int64_t value) {
     case PCV_OPT_MATERIALIZE:
       if (value < 0) return fail(c, PCV_EINVAL, "materialise cap must be >= 0");
       c->mat_cap = value;
+      return PCV_OK;
+    case PCV_OPT_TENSOR_CORES:
+      c->tensor_cores = value != 0;
       return PCV_OK;
     case PCV_OPT_EXACT_TILE:
     case PCV_OPT_APPROX_TILE:
@@ -635,16 +640,28 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
   const bool seg_form = (int64_t)(nref + 1) * 16 <= (int64_t)F;
   const int seg_base = had_prior ? 0 : 1;  // without a prior structure segment 0 is empty
   const int nseg = nref + 1 - seg_base;
-  bool tiled = false;
+  bool tiled = false, mma = false;
+  const MmaShape msh = mma_shape(F, M, c->N);
   if (c->prec != P_F64 && c->uniform && seg_form && nseg > 0) {
     const size_t xb = tile_bytes_frames(napp, c->N), bb = tile_bytes_landmarks(nseg, M, c->N);
     const size_t gb = grads ? tile_bytes_gamma(F, M) : 0;  // per gamma kind
-    if ((int64_t)(xb + bb + 2 * gb) <= c->mat_cap) {
+    const size_t mb = msh.a_bytes + 2 * sizeof(float) * (size_t)F + (msh.b_bytes_per_seg + msh.y_bytes_per_seg) * nseg;
+    mma = grads && c->tensor_cores;
+    if ((int64_t)(xb + bb + (mma ? mb : 2 * gb)) <= c->mat_cap) {
       if ((ps = ensure(c, c->Xr, xb)) != PCV_OK) return ps;
       if ((ps = ensure(c, c->Bm, bb)) != PCV_OK) return ps;
-      if (grads && (ps = ensure(c, c->GSb, gb)) != PCV_OK) return ps;
-      if (grads && (ps = ensure(c, c->GZb, gb)) != PCV_OK) return ps;
+      if (mma) {
+        if ((ps = ensure(c, c->Amma, msh.a_bytes)) != PCV_OK) return ps;
+        if ((ps = ensure(c, c->Gsum, 2 * sizeof(float) * (size_t)F)) != PCV_OK) return ps;
+        if ((ps = ensure(c, c->Bmma, msh.b_bytes_per_seg * nseg)) != PCV_OK) return ps;
+        if ((ps = ensure(c, c->Ymma, msh.y_bytes_per_seg * nseg)) != PCV_OK) return ps;
+      } else if (grads) {
+        if ((ps = ensure(c, c->GSb, gb)) != PCV_OK) return ps;
+        if ((ps = ensure(c, c->GZb, gb)) != PCV_OK) return ps;
+      }
       tiled = true;
+    } else {
+      mma = false;
     }
   }
   {
@@ -655,6 +672,9 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
   if (tiled) {
     PROF(c, K_MATERIALIZE);
     launch_materialize_landmarks(c->prec, seg_base, nseg, L, (const float*)c->Bseg.p, (float*)c->Bm.p, st);
+    if (mma)
+      launch_delta_split(c->prec, seg_base, nseg, L, msh, (const float*)c->Bseg.p, frames, fi,
+                         (const int*)c->reflist.p, prior, (float*)c->Bmma.p, (float*)c->Ymma.p, st);
     launch_materialize_frames(napp, &sm->approx_count, (const int*)c->alist.p, L, frames, fi, rec.qxy,
                               (float*)c->Xr.p, st);
   }
@@ -674,7 +694,16 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
   }
   if (refreshed) CUDA_TRY(c, cudaMemcpyAsync(refreshed, rec.flag, F, cudaMemcpyDeviceToDevice, st));
   if (grads) {
-    if (tiled) {
+    if (mma) {
+      {
+        PROF(c, K_GAMMA);
+        launch_gamma_split(F, L, msh, (const float*)c->Dbuf.p, s, c->lambda, (float*)c->Amma.p, (float*)c->Gsum.p, st);
+      }
+      PROF(c, K_ADJ_MMA);
+      launch_adjoint_beta_mma(F, L, msh, seg_base, (const float*)c->Amma.p, (const float*)c->Gsum.p,
+                              (const float*)c->Bmma.p, (const float*)c->Ymma.p, (const int*)c->segof.p, (float*)gs,
+                              (float*)gz, (unsigned*)c->status.p, st);
+    } else if (tiled) {
       {
         PROF(c, K_GAMMA);
         launch_gamma(F, L, (const float*)c->Dbuf.p, s, c->lambda, (float*)c->GSb.p, (float*)c->GZb.p, st);
@@ -842,6 +871,8 @@ pcv_status pcv_sync(pcv_ctx* c) {
   CUDA_TRY(c, cudaMemcpy(&status, c->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost));
   if (status) {
     CUDA_TRY(c, cudaMemset(c->status.p, 0, sizeof(unsigned)));
+    if (status & STATUS_TIMEOUT)
+      return fail(c, PCV_ETIMEOUT, "a device-side wait exceeded its time limit; the batch's results are invalid");
     if (status & STATUS_NOCONV) return fail(c, PCV_ENOCONV, "an eigen-solve reached its iteration cap");
   }
   return PCV_OK;

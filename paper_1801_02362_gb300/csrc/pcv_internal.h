@@ -12,7 +12,7 @@ enum Prec { P_F64 = 0, P_F32 = 1, P_F16 = 2 };
 void note_launch(int n = 1);
 
 // status bits written to the context's device status word
-constexpr unsigned STATUS_NOCONV = 1u;
+constexpr unsigned STATUS_NOCONV = 1, STATUS_TIMEOUT = 2u;
 
 // Landmark set resident on the device (written by pcv_set_landmarks).
 struct LandmarkDev {
@@ -164,5 +164,27 @@ void launch_approx_pairs_tile(int napp, const int* alist, const int* aseg, const
                               const LandmarkDev& L, const float* Xr, const float* Bm, float* D, cudaStream_t st);
 void launch_adjoint_beta_tile(int F, const LandmarkDev& L, int seg_base, const float* GS, const float* GZ,
                               const float* Bm, const int* seg_of_frame, float* gs, float* gz, cudaStream_t st);
+
+
+// ---------------------------------------------------------------------------------------
+// tensor-core segment adjoint (k_mma.cu; FP32 and FP16-storage modes, uniform weights)
+struct MmaShape {
+  int Kp = 0, Fp = 0, BN = 0, NT = 0;  // landmarks / frames padded, column tile, column tiles
+  size_t a_bytes = 0;                  // gamma operand (hi and lo, s and z) for Fp frames
+  size_t b_bytes_per_seg = 0;          // deviation operand per segment
+  size_t y_bytes_per_seg = 0;          // centred close structure per segment
+};
+MmaShape mma_shape(int F, int M, int N);
+// gamma operand pre-tiled for the MMA, and Gamma^s_f, Gamma^z_f (Gsum, 2F floats)
+void launch_gamma_split(int F, const LandmarkDev& L, const MmaShape& sh, const float* P, const double* s,
+                        double lambda, float* A, float* Gsum, cudaStream_t st);
+// deviation operand delta_i = R_{a_i y} a_i - y' of segments [seg_base, seg_base + nseg), and y'
+void launch_delta_split(Prec p, int seg_base, int nseg, const LandmarkDev& L, const MmaShape& sh, const float* Bseg,
+                        const void* frames, FrameInfo fi, const int* refresh_list, const RefDesc& prior, float* B,
+                        float* Yc, cudaStream_t st);
+// beta^s, beta^z for all F frames into gs, gz (STATUS_TIMEOUT in *status if a wait expired)
+void launch_adjoint_beta_mma(int F, const LandmarkDev& L, const MmaShape& sh, int seg_base, const float* A,
+                             const float* Gsum, const float* B, const float* Yc, const int* seg_of_frame, float* gs,
+                             float* gz, unsigned* status, cudaStream_t st);
 
 }  // namespace pcv

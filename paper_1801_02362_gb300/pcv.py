@@ -16,14 +16,15 @@ import numpy as np
 
 from . import build_lib
 
-PCV_OK, PCV_EINVAL, PCV_ECUDA, PCV_ENOMEM, PCV_ENOCONV, PCV_ESTATE = 0, -1, -2, -3, -4, -5
+PCV_OK, PCV_EINVAL, PCV_ECUDA, PCV_ENOMEM, PCV_ENOCONV, PCV_ESTATE, PCV_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 PCV_FP64, PCV_FP32, PCV_FP16_STORAGE = 0, 1, 2
 PCV_OPT_BAND, PCV_OPT_CHUNK, PCV_OPT_EXACT_TILE, PCV_OPT_APPROX_TILE, PCV_OPT_PROFILE = 1, 2, 3, 4, 5
 PCV_OPT_MATERIALIZE = 6
+PCV_OPT_TENSOR_CORES = 7
 PCV_PROFILE_KERNELS = 20
 
 _STATUS_NAMES = {0: "PCV_OK", -1: "PCV_EINVAL", -2: "PCV_ECUDA", -3: "PCV_ENOMEM", -4: "PCV_ENOCONV",
-                 -5: "PCV_ESTATE"}
+                 -5: "PCV_ESTATE", -6: "PCV_ETIMEOUT"}
 
 
 class PcvError(RuntimeError):
@@ -212,7 +213,8 @@ class PathCV:
 
     def __init__(self, landmarks: np.ndarray, lam: float, eps: float = -1.0, precision: str = "fp32",
                  weights: np.ndarray | None = None, props: np.ndarray | None = None, device: int = 0,
-                 band: int | None = None, min_chunk: int | None = None, materialize: int | None = None):
+                 band: int | None = None, min_chunk: int | None = None, materialize: int | None = None,
+                 tensor_cores: bool | None = None):
         import torch
 
         self.torch = torch
@@ -230,6 +232,8 @@ class PathCV:
             pcv_set_option(self.ctx, PCV_OPT_CHUNK, min_chunk)
         if materialize is not None:
             pcv_set_option(self.ctx, PCV_OPT_MATERIALIZE, materialize)
+        if tensor_cores is not None:
+            pcv_set_option(self.ctx, PCV_OPT_TENSOR_CORES, 1 if tensor_cores else 0)
 
     @property
     def frame_dtype(self):

@@ -204,28 +204,34 @@ def test_close_split_calls_and_saved_state(pcv):
 
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])
 @pytest.mark.parametrize("n,m", [(140, 45), (61, 200)])
-def test_close_materialized_operands(pcv, precision, n, m):
+@pytest.mark.parametrize("variant", ["tensor_cores", "cuda_cores", "not_materialized"])
+def test_close_materialized_operands(pcv, precision, n, m, variant):
     """Long segments (20 refreshes in 700 frames): the rotated frames x' and the rotated
-    landmarks b of each segment are materialised and both heavy loops run as plain tiles.
-    N = 140 pads to 144 atoms (a half tile of 32 at the end), N = 61 to 64; M = 45 and 200
-    take the two landmark tile widths; 700 frames end in a ragged tile of 64.  The second
-    call starts from the first call's close structure (the prior segment in use).  A cap of
-    0 turns materialisation off: both must match the oracle."""
+    landmarks b of each segment are materialised and both heavy loops run as plain tiles;
+    the segment adjoint runs on the tensor cores (3xTF32 on deviations from the close
+    structure) or on the CUDA cores.  N = 140 pads to 144 atoms (a half tile of 32 at the
+    end) and 420 adjoint columns (two column tiles of 224); N = 61 to 64 atoms and 183
+    columns (one tile of 192); M = 45 and 200 take the two landmark tile widths and pad the
+    tensor-core K to 48 and 208; 700 frames end in a ragged tile of 64.  The second call
+    starts from the first call's close structure (the prior segment in use).  A cap of 0
+    turns materialisation off.  All must match the oracle."""
     lm, fr, lam = problem(12, n, m, 700, noise=0.02, schedule="walk", precision=precision, ou_rho=0.9)
     eps = 0.0025
     r = oracle.close(fr, lm, lam, eps, want_grad=True)
-    for cap in (None, 0):
-        ctx = pcv.PathCV(lm, lam, eps=eps, precision=precision, materialize=cap)
-        ctx.set_profiling(True)
-        parts = [run(pcv, lm, fr[a:b], lam, ctx=ctx, grad=True) for a, b in ((0, 430), (430, 700))]
-        prof = ctx.profile()
-        ctx.close()
-        assert ("materialize" in prof) == (cap is None), prof
-        np.testing.assert_array_equal(np.concatenate([p["refreshed"] for p in parts]), r["refreshed"])
-        g = {k: np.concatenate([p[k] for p in parts]) for k in ("s", "z", "msd", "dsdx", "dzdx")}
-        check_values(g, r, fr, lm, lam, precision)
-        assert grad_err(g["dsdx"], r["dsdx"]) < GRAD_TOL[precision]
-        assert grad_err(g["dzdx"], r["dzdx"]) < GRAD_TOL[precision]
+    cap = 0 if variant == "not_materialized" else None
+    ctx = pcv.PathCV(lm, lam, eps=eps, precision=precision, materialize=cap,
+                     tensor_cores=variant == "tensor_cores")
+    ctx.set_profiling(True)
+    parts = [run(pcv, lm, fr[a:b], lam, ctx=ctx, grad=True) for a, b in ((0, 430), (430, 700))]
+    prof = ctx.profile()
+    ctx.close()
+    assert ("materialize" in prof) == (cap is None), prof
+    assert ("adjoint_beta_mma" in prof) == (variant == "tensor_cores"), prof
+    np.testing.assert_array_equal(np.concatenate([p["refreshed"] for p in parts]), r["refreshed"])
+    g = {k: np.concatenate([p[k] for p in parts]) for k in ("s", "z", "msd", "dsdx", "dzdx")}
+    check_values(g, r, fr, lm, lam, precision)
+    assert grad_err(g["dsdx"], r["dsdx"]) < GRAD_TOL[precision]
+    assert grad_err(g["dzdx"], r["dzdx"]) < GRAD_TOL[precision]
 
 
 def test_close_fp64_workload_c1(pcv):
