@@ -38,7 +38,7 @@ constexpr int MM_FRAMES = 64;
 constexpr int MM_KC = 16;       // K values (landmarks) per stage
 constexpr int MM_BN_MAX = 256;  // columns per CTA (MMA N), multiple of 16
 constexpr int MM_THREADS = 128;
-constexpr int MM_STAGES = 4;
+constexpr int MM_STAGES = 2;   // two CTAs per SM: one's epilogue overlaps the other's MMAs
 constexpr int MM_TMEM_COLS = 256;
 constexpr int MM_A_BYTES = MM_ROWS * MM_KC * 4;  // one operand part (hi or lo) of one K chunk
 constexpr long long MM_WAIT_CYCLES = 4000000000LL;  // about 2 s at the maximum SM clock
@@ -234,7 +234,7 @@ struct MmaArgs {
   unsigned* status;
 };
 
-__global__ void __launch_bounds__(MM_THREADS, 1) adjoint_beta_mma(MmaArgs p) {
+__global__ void __launch_bounds__(MM_THREADS, 2) adjoint_beta_mma(MmaArgs p) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t full[MM_STAGES], empty[MM_STAGES], done;
   __shared__ uint32_t tmem_slot;
@@ -349,25 +349,49 @@ __global__ void __launch_bounds__(MM_THREADS, 1) adjoint_beta_mma(MmaArgs p) {
       break;
     }
     tc_fence_after();
+    // Each warp holds rows 32 warp + lane of the accumulator.  Columns are moved in halves
+    // through shared memory (the operand stages are idle now) so that the global stores
+    // run along rows: a warp writes 32 consecutive columns of one frame per instruction.
     const int r = warp * 32 + lane;
-    const bool zrow = r >= MM_FRAMES;
+    const bool zrow = warp >= 2;  // rows 64..127: gamma^z
     const int ff = r & (MM_FRAMES - 1);
     const int f = f0 + ff;
-    const bool mine = ff >= k && ff < kend && f < p.F;
+    const int mine = (ff >= k && ff < kend && f < p.F) ? 1 : 0;
     const float Gam = mine ? p.Gsum[2 * f + (zrow ? 1 : 0)] : 0.0f;
     const float* yrow = p.Yc + (size_t)slot * NB;
-    float* out = (zrow ? p.gz : p.gs) + (size_t)f * NB;
+    float* outb = zrow ? p.gz : p.gs;
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int cb = 0; cb < p.BN; cb += 16) {
-      float v[16];
-      tmem_ld16(trow + cb, v);
-      if (mine) {
+    const int half = (p.BN / 2 + 15) / 16 * 16;  // columns per pass, multiple of 16
+    const int ld = half + 1;                      // odd row stride: conflict-free scalar writes
+    float* stg = reinterpret_cast<float*>(smem) + warp * 32 * ld;
+    for (int c0 = 0; c0 < p.BN; c0 += half) {
+      const int cn = min(half, p.BN - c0);
+      for (int cb = 0; cb < cn; cb += 16) {
+        float v[16];
+        tmem_ld16(trow + c0 + cb, v);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const int n = n0 + cb + e;
-          if (n < NB) out[n] = fmaf(Gam, yrow[n], v[e]);
+        for (int e = 0; e < 16; ++e) stg[lane * ld + cb + e] = v[e];
+      }
+      __syncwarp();
+      float yv[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int n = n0 + c0 + lane + 32 * q;
+        yv[q] = (lane + 32 * q < cn && n < NB) ? yrow[n] : 0.0f;
+      }
+      for (int rr = 0; rr < 32; ++rr) {
+        const int mr = __shfl_sync(0xffffffffu, mine, rr);
+        const float G = __shfl_sync(0xffffffffu, Gam, rr);
+        const int fr = __shfl_sync(0xffffffffu, f, rr);
+        if (!mr) continue;
+        float* orow = outb + (size_t)fr * NB;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int col = lane + 32 * q, n = n0 + c0 + col;
+          if (col < cn && n < NB) orow[n] = fmaf(G, yv[q], stg[rr * ld + col]);
         }
       }
+      __syncwarp();
     }
     tc_fence_before();
     __syncthreads();  // the accumulator is read before the next run overwrites it
