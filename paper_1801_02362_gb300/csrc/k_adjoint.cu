@@ -410,6 +410,199 @@ adjoint_finish_warp(int F, int M, int N, const FT* __restrict__ frames, const fl
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// S_i = R_{a_i y} A_i R_{a_i y}^T (xx xy xz yy yz zz) for every landmark of the segments
+// [seg_base, seg_base + nseg): the per-landmark part of Phi, shared by a segment's frames.
+__global__ void seg_moments_kernel(int seg_base, int nseg, int M, const float* __restrict__ Bseg,
+                                   const float* __restrict__ A32, float* __restrict__ S6) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nseg * M) return;
+  const int slot = idx / M, i = idx - slot * M;
+  const float* B = Bseg + ((size_t)(seg_base + slot) * M + i) * 9;
+  const float* a = A32 + (size_t)i * 6;
+  const float A[9] = {a[0], a[1], a[2], a[1], a[3], a[4], a[2], a[4], a[5]};
+  float Bv[9], BA[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) Bv[e] = B[e];
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) BA[3 * b + c] = Bv[3 * b] * A[c] + Bv[3 * b + 1] * A[3 + c] + Bv[3 * b + 2] * A[6 + c];
+  const int ib[6] = {0, 0, 0, 1, 1, 2}, ic[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+  for (int e = 0; e < 6; ++e) {
+    const int b = ib[e], c = ic[e];
+    S6[(size_t)idx * 6 + e] = BA[3 * b] * Bv[3 * c] + BA[3 * b + 1] * Bv[3 * c + 1] + BA[3 * b + 2] * Bv[3 * c + 2];
+  }
+}
+
+// Per-frame finish for the FP32 modes, one warp per frame, the frame staged in shared
+// memory: x - c, y - c_y, beta^s and beta^z are read from global memory once (coalesced)
+// and both passes over the atoms run from shared memory.  Gamma comes from Gsum when the
+// gamma kernel produced it (else from P), and Phi from the segment moments S6 when given
+// (else from Bseg and A32), with the arithmetic of adjoint_finish_warp except that the top
+// eigenvector of K(H_xy) is the stored alignment quaternion q_xy (adjoint_rotation_terms2).
+__global__ void __launch_bounds__(128)
+adjoint_finish_staged(int F, int M, int N, const float* __restrict__ frames, const float4* __restrict__ c32,
+                      const float* __restrict__ wts, float wuni, const float* __restrict__ A32,
+                      const float* __restrict__ q32, const float* __restrict__ P, const double* __restrict__ s,
+                      float lambda, const float* __restrict__ Gsum, const float* __restrict__ S6, int seg_base,
+                      const float* __restrict__ Bseg, const int* __restrict__ seg_of_frame, FrameRec rec,
+                      const float* __restrict__ prior_coords, float4 prior_c, float* __restrict__ gs,
+                      float* __restrict__ gz) {
+  extern __shared__ float fsm[];
+  const int wpb = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int f = blockIdx.x * wpb + w;
+  if (f >= F) return;  // the whole warp leaves; only warp-level synchronisation below
+  const int N3 = 3 * N;
+  float* xv = fsm + (size_t)w * 4 * N3;  // x - c
+  float* uv = xv + N3;                   // y - c_y (approximate frames)
+  float* bs = uv + N3;                   // beta^s
+  float* bz = bs + N3;                   // beta^z
+  const float4 c = c32[f];
+  const float cx[3] = {c.x, c.y, c.z};
+  const float* x = frames + (size_t)f * N3;
+  float* gsp = gs + (size_t)f * N3;
+  float* gzp = gz + (size_t)f * N3;
+  for (int e = lane; e < N3; e += 32) {
+    const int b = e - 3 * (e / 3);
+    xv[e] = x[e] - cx[b];
+    bs[e] = gsp[e];
+    bz[e] = gzp[e];
+  }
+  const float sf = (float)s[f];
+  float Gs, Gz;
+  if (Gsum) {
+    Gs = Gsum[2 * f];
+    Gz = Gsum[2 * f + 1];
+  } else {
+    Gs = 0.0f;
+    Gz = 0.0f;
+    for (int i = lane; i < M; i += 32) {
+      float gsv, gzv;
+      gammas<float>(P[(size_t)f * M + i], lambda, q32[i], sf, gsv, gzv);
+      Gs += gsv;
+      Gz += gzv;
+    }
+    Gs = wsum(Gs);
+    Gz = wsum(Gz);
+  }
+  const bool approx = rec.flag && rec.flag[f] == 0;
+  if (!approx) {
+    __syncwarp();
+    for (int e = lane; e < N3; e += 32) {
+      const float wj = wts ? wts[e / 3] : wuni;
+      gsp[e] = 2.0f * wj * (Gs * xv[e] - bs[e]);
+      gzp[e] = 2.0f * wj * (Gz * xv[e] - bz[e]);
+    }
+    return;
+  }
+  const int r = rec.ref[f];
+  const float* y = r >= 0 ? frames + (size_t)r * N3 : prior_coords;
+  float4 cyv = prior_c;
+  if (r >= 0) cyv = c32[r];
+  const float cy[3] = {cyv.x, cyv.y, cyv.z};
+  for (int e = lane; e < N3; e += 32) uv[e] = y[e] - cy[e - 3 * (e / 3)];
+  __syncwarp();
+  float R[9], qxy[4];
+  {
+    const double4 qq = rec.qxy[f];
+    qxy[0] = (float)qq.x;
+    qxy[1] = (float)qq.y;
+    qxy[2] = (float)qq.z;
+    qxy[3] = (float)qq.w;
+    quat_to_rot(qxy, R);
+  }
+  // X = sum_j w x_j beta_j^T (s, z) and H_xy = sum_j w y_j x_j^T, centred, true weights
+  float acc[27];
+#pragma unroll
+  for (int e = 0; e < 27; ++e) acc[e] = 0.0f;
+  for (int j = lane; j < N; j += 32) {
+    const float wj = wts ? wts[j] : wuni;
+    float v[3], u[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      v[b] = xv[3 * j + b];
+      u[b] = uv[3 * j + b];
+    }
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const float wv = wj * v[b], wu = wj * u[b];
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) {
+        acc[3 * b + cc] = fmaf(wv, bs[3 * j + cc], acc[3 * b + cc]);
+        acc[9 + 3 * b + cc] = fmaf(wv, bz[3 * j + cc], acc[9 + 3 * b + cc]);
+        acc[18 + 3 * b + cc] = fmaf(wu, v[cc], acc[18 + 3 * b + cc]);
+      }
+    }
+  }
+  // Phi = sum_i gamma_i S_i (s, z)
+  float ph[12];
+#pragma unroll
+  for (int e = 0; e < 12; ++e) ph[e] = 0.0f;
+  const int seg = seg_of_frame[f];
+  for (int i = lane; i < M; i += 32) {
+    float gsv, gzv;
+    gammas<float>(P[(size_t)f * M + i], lambda, q32[i], sf, gsv, gzv);
+    float S[6];
+    if (S6) {
+      const float* sp = S6 + ((size_t)(seg - seg_base) * M + i) * 6;
+#pragma unroll
+      for (int e = 0; e < 6; ++e) S[e] = sp[e];
+    } else {
+      const float* B = Bseg + ((size_t)seg * M + i) * 9;
+      const float* a = A32 + (size_t)i * 6;
+      const float A[9] = {a[0], a[1], a[2], a[1], a[3], a[4], a[2], a[4], a[5]};
+      float BA[9];
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) BA[3 * b + cc] = B[3 * b] * A[cc] + B[3 * b + 1] * A[3 + cc] + B[3 * b + 2] * A[6 + cc];
+      const int ib[6] = {0, 0, 0, 1, 1, 2}, ic[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+      for (int e = 0; e < 6; ++e) {
+        const int b = ib[e], cc = ic[e];
+        S[e] = BA[3 * b] * B[3 * cc] + BA[3 * b + 1] * B[3 * cc + 1] + BA[3 * b + 2] * B[3 * cc + 2];
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      ph[e] = fmaf(gsv, S[e], ph[e]);
+      ph[6 + e] = fmaf(gzv, S[e], ph[6 + e]);
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < 27; ++e) acc[e] = wsum(acc[e]);
+#pragma unroll
+  for (int e = 0; e < 12; ++e) ph[e] = wsum(ph[e]);
+  float Ts[9], Tz[9];
+  {
+    const float Ps[9] = {ph[0], ph[1], ph[2], ph[1], ph[3], ph[4], ph[2], ph[4], ph[5]};
+    const float Pz[9] = {ph[6], ph[7], ph[8], ph[7], ph[9], ph[10], ph[8], ph[10], ph[11]};
+    adjoint_rotation_terms2<float>(acc + 18, R, qxy, acc, acc + 9, Ps, Pz, Ts, Tz);
+  }
+  for (int j = lane; j < N; j += 32) {
+    const float wj = wts ? wts[j] : wuni;
+    float v[3], u[3], bsj[3], bzj[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      v[b] = xv[3 * j + b];
+      u[b] = uv[3 * j + b];
+      bsj[b] = bs[3 * j + b];
+      bzj[b] = bz[3 * j + b];
+    }
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+      const float Rbs = R[3 * cc] * bsj[0] + R[3 * cc + 1] * bsj[1] + R[3 * cc + 2] * bsj[2];
+      const float Rbz = R[3 * cc] * bzj[0] + R[3 * cc + 1] * bzj[1] + R[3 * cc + 2] * bzj[2];
+      const float ts = Ts[cc] * u[0] + Ts[3 + cc] * u[1] + Ts[6 + cc] * u[2];
+      const float tz = Tz[cc] * u[0] + Tz[3 + cc] * u[1] + Tz[6 + cc] * u[2];
+      gsp[3 * j + cc] = 2.0f * wj * (Gs * v[cc] - Rbs) + wj * ts;
+      gzp[3 * j + cc] = 2.0f * wj * (Gz * v[cc] - Rbz) + wj * tz;
+    }
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------------
@@ -451,10 +644,32 @@ void launch_adjoint_beta(Prec p, int F, const LandmarkDev& L, const void* P, con
   note_launch();
 }
 
+void launch_seg_moments(int seg_base, int nseg, const LandmarkDev& L, const float* Bseg, float* S6, cudaStream_t st) {
+  if (nseg <= 0 || L.M <= 0) return;
+  const int n = nseg * L.M;
+  seg_moments_kernel<<<(n + 255) / 256, 256, 0, st>>>(seg_base, nseg, L.M, Bseg, L.A32, S6);
+  note_launch();
+}
+
 void launch_adjoint_finish(Prec p, int F, const void* frames, const LandmarkDev& L, FrameInfo fi, const void* P,
                            const double* s, double lambda, const void* Bseg, const int* seg_of_frame,
-                           const FrameRec rec, const RefDesc& prior, void* gs, void* gz, cudaStream_t st) {
+                           const FrameRec rec, const RefDesc& prior, void* gs, void* gz, cudaStream_t st,
+                           const float* Gsum, const float* S6, int seg_base) {
   if (F <= 0) return;
+  // FP32 modes: frames staged in shared memory (4 arrays of 3N floats per warp)
+  const size_t per_warp = (size_t)12 * L.N * sizeof(float);
+  if (p != P_F64 && per_warp <= 200 * 1024) {
+    const int wpb = per_warp * 4 <= 96 * 1024 ? 4 : (per_warp * 2 <= 160 * 1024 ? 2 : 1);
+    const size_t smem = per_warp * wpb;
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(adjoint_finish_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    adjoint_finish_staged<<<(unsigned)((F + wpb - 1) / wpb), 32 * wpb, smem, st>>>(
+        F, L.M, L.N, (const float*)frames, fi.c32, L.w, (float)L.dscale, L.A32, L.q32, (const float*)P, s,
+        (float)lambda, Gsum, S6, seg_base, (const float*)Bseg, seg_of_frame, rec, (const float*)prior.coords,
+        prior.c32, (float*)gs, (float*)gz);
+    note_launch();
+    return;
+  }
   const unsigned blocks = (unsigned)((F + 3) / 4);
   if (p == P_F64)
     adjoint_finish_warp<double, double><<<blocks, 128, 0, st>>>(

@@ -55,12 +55,12 @@ thread_local int64_t t_launches = 0;
 // kernel families timed by the profiler
 enum KernelId {
   K_PREP = 0, K_BAND, K_RECHECK, K_SCAN, K_CHUNK, K_FIRST, K_RECORDS, K_COMPACT, K_EXACT, K_APPROX,
-  K_FINAL, K_ADJ_BETA, K_ADJ_FINISH, K_COMBINE, K_XY_REFINE, K_ADJ_BETA_SEG, K_MATERIALIZE, K_GAMMA, K_ADJ_MMA, K_COUNT
+  K_FINAL, K_ADJ_BETA, K_ADJ_FINISH, K_COMBINE, K_XY_REFINE, K_ADJ_BETA_SEG, K_MATERIALIZE, K_GAMMA, K_ADJ_MMA, K_SEG_MOMENTS, K_COUNT
 };
 const char* const kKernelNames[PCV_PROFILE_KERNELS] = {
     "frame_prep", "align_band", "recheck_fp64", "band_scan", "align_chunk", "first_exceed", "records",
     "compact", "exact_pair", "approx_pair", "finalize", "adjoint_beta_pair", "adjoint_finish", "combine_grad", "xy_refine",
-    "adjoint_beta_seg", "materialize", "gamma", "adjoint_beta_mma", ""};
+    "adjoint_beta_seg", "materialize", "gamma", "adjoint_beta_mma", "seg_moments"};
 
 struct ProfEvent {
   int id;
@@ -102,6 +102,7 @@ struct pcv_ctx {
       segof, alist, aseg, Dbuf, Rpair, Bseg, mstat, status, nrecheck, small;
   DevBuf Xr, Bm, GSb, GZb;  // materialised x', b and the gamma rows
   DevBuf Amma, Gsum, Bmma, Ymma;  // tensor-core adjoint operands
+  DevBuf S6;                      // per-segment landmark moments R A R^T of the finish
   DevBuf h_frames, h_s, h_z, h_gs, h_gz, h_msd, h_ref;  // device staging for pcv_evaluate_host
   Small* small_host = nullptr;
   pcv_stats stats{};
@@ -275,7 +276,7 @@ pcv_status pcv_destroy(pcv_ctx* c) {
   DevBuf* bufs[] = {&c->lm, &c->lmG, &c->lmA, &c->lmA32, &c->lmq, &c->lmq32, &c->w32, &c->w64, &c->y, &c->Bprior, &c->c32, &c->c64,
                     &c->fG, &c->bandD, &c->bandQ, &c->bandF, &c->chD, &c->chQ, &c->chF, &c->rlist, &c->rcount,
                     &c->recF, &c->recRef, &c->recD, &c->recQ, &c->reflist, &c->segof, &c->alist, &c->aseg,
-                    &c->Dbuf, &c->Rpair, &c->Bseg, &c->Xr, &c->Bm, &c->GSb, &c->GZb, &c->Amma, &c->Gsum, &c->Bmma, &c->Ymma, &c->mstat, &c->status, &c->nrecheck, &c->small, &c->h_frames,
+                    &c->Dbuf, &c->Rpair, &c->Bseg, &c->Xr, &c->Bm, &c->GSb, &c->GZb, &c->Amma, &c->Gsum, &c->Bmma, &c->Ymma, &c->S6, &c->mstat, &c->status, &c->nrecheck, &c->small, &c->h_frames,
                     &c->h_s, &c->h_z, &c->h_gs, &c->h_gz, &c->h_msd, &c->h_ref};
   for (DevBuf* b : bufs) release(*b);
   for (const ProfEvent& e : c->prof_pending) {
@@ -716,9 +717,17 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
       launch_adjoint_beta(c->prec, F, L, c->Dbuf.p, s, c->lambda, nullptr, c->Bseg.p, (const int*)c->segof.p,
                           seg_form, gs, gz, st);
     }
+    // segment moments for Phi when frames share close structures (FP32 modes)
+    const bool moments = c->prec != P_F64 && seg_form && nseg > 0;
+    if (moments) {
+      if ((ps = ensure(c, c->S6, sizeof(float) * 6 * (size_t)nseg * M)) != PCV_OK) return ps;
+      PROF(c, K_SEG_MOMENTS);
+      launch_seg_moments(seg_base, nseg, L, (const float*)c->Bseg.p, (float*)c->S6.p, st);
+    }
     PROF(c, K_ADJ_FINISH);
     launch_adjoint_finish(c->prec, F, frames, L, fi, c->Dbuf.p, s, c->lambda, c->Bseg.p, (const int*)c->segof.p, rec,
-                          prior, gs, gz, st);
+                          prior, gs, gz, st, mma ? (const float*)c->Gsum.p : nullptr,
+                          moments ? (const float*)c->S6.p : nullptr, seg_base);
   }
   // carry the close structure over to the next call
   const int last = c->small_host->last_refresh;

@@ -613,4 +613,106 @@ __device__ __forceinline__ void adjoint_rotation_term(const T* H, const T* R, co
     }
 }
 
+
+// The rotation terms of gamma^s and gamma^z together (as adjoint_rotation_term), given the
+// top eigenvector q0 of K(H) -- the alignment quaternion of x onto y, known from the
+// refresh search -- so the eigen-solve and the factorisation of (l0 I - K + q0 q0^T) are
+// done once for both.  q0 may have either sign: T is quadratic in q0.
+template <typename T>
+__device__ __forceinline__ void adjoint_rotation_terms2(const T* H, const T* R, const T* q0in, const T* Xs,
+                                                        const T* Xz, const T* Ps, const T* Pz, T* Ts, T* Tz) {
+  T K[16];
+  quat_matrix(H, K);
+  T q0[4];
+  {
+    const T n = sqrt(q0in[0] * q0in[0] + q0in[1] * q0in[1] + q0in[2] * q0in[2] + q0in[3] * q0in[3]);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) q0[a] = q0in[a] / n;
+  }
+  T l0 = 0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) l0 += q0[a] * K[4 * a + b] * q0[b];
+  T g2[2][4];
+#pragma unroll
+  for (int which = 0; which < 2; ++which) {
+    const T* X = which ? Xz : Xs;
+    const T* Phi = which ? Pz : Ps;
+    T GhT[9];  // Ghat^T, Ghat = -2 (X - R Phi)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        GhT[3 * c + b] = T(-2) * (X[3 * b + c] - (R[3 * b] * Phi[c] + R[3 * b + 1] * Phi[3 + c] + R[3 * b + 2] * Phi[6 + c]));
+    T KG[16];
+    quat_matrix(GhT, KG);
+    T* g = g2[which];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      g[a] = 0;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) g[a] += T(2) * KG[4 * a + b] * q0[b];
+    }
+    const T gq = g[0] * q0[0] + g[1] * q0[1] + g[2] * q0[2] + g[3] * q0[3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) g[a] -= gq * q0[a];
+  }
+  // Cholesky factor of l0 I - K + q0 q0^T, then two solves
+  T L[16];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) L[e] = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      T sum = (i == j ? l0 : T(0)) - K[4 * i + j] + q0[i] * q0[j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) sum -= L[4 * i + k] * L[4 * j + k];
+      if (i == j)
+        L[4 * i + i] = sqrt(sum > T(0) ? sum : T(1e-30));
+      else
+        L[4 * i + j] = sum / L[4 * j + j];
+    }
+  }
+  T pv[2][4];
+#pragma unroll
+  for (int which = 0; which < 2; ++which) {
+    T y[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      T sum = g2[which][i];
+#pragma unroll
+      for (int k = 0; k < i; ++k) sum -= L[4 * i + k] * y[k];
+      y[i] = sum / L[4 * i + i];
+    }
+#pragma unroll
+    for (int i = 3; i >= 0; --i) {
+      T sum = y[i];
+#pragma unroll
+      for (int k = i + 1; k < 4; ++k) sum -= L[4 * k + i] * pv[which][k];
+      pv[which][i] = sum / L[4 * i + i];
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T E[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+      E[3 * b + c] = 1;
+      T KE[16];
+      quat_matrix(E, KE);
+      T ts = 0, tz = 0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+          ts += pv[0][a] * KE[4 * a + d] * q0[d];
+          tz += pv[1][a] * KE[4 * a + d] * q0[d];
+        }
+      Ts[3 * b + c] = ts;
+      Tz[3 * b + c] = tz;
+    }
+}
+
 }  // namespace pcv

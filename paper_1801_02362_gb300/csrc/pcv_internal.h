@@ -123,9 +123,14 @@ void launch_adjoint_beta(Prec p, int F, const LandmarkDev& L, const void* P, con
                          const void* Rpair, const void* Bseg, const int* seg_of_frame, bool seg_form, void* gs,
                          void* gz, cudaStream_t st);
 // rec.flag == nullptr: exact mode (no rotation term)
+// Gsum (Gamma^s_f, Gamma^z_f) and S6 (segment moments of segments from seg_base) are
+// optional inputs of the FP32 finish; null: computed from P and from Bseg, A32
 void launch_adjoint_finish(Prec p, int F, const void* frames, const LandmarkDev& L, FrameInfo fi, const void* P,
                            const double* s, double lambda, const void* Bseg, const int* seg_of_frame,
-                           const FrameRec rec, const RefDesc& prior, void* gs, void* gz, cudaStream_t st);
+                           const FrameRec rec, const RefDesc& prior, void* gs, void* gz, cudaStream_t st,
+                           const float* Gsum = nullptr, const float* S6 = nullptr, int seg_base = 0);
+// S_i = R_{a_i y} A_i R_{a_i y}^T (6 floats) of segments [seg_base, seg_base + nseg)
+void launch_seg_moments(int seg_base, int nseg, const LandmarkDev& L, const float* Bseg, float* S6, cudaStream_t st);
 void launch_combine_grad(Prec p, int F, int N3, const double* g_s, const double* g_z,
                          const void* gs, const void* gz, void* out, cudaStream_t st);
 void launch_fill_u8(uint8_t* p, uint8_t v, size_t n, cudaStream_t st);
