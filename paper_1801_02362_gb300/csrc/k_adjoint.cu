@@ -442,6 +442,7 @@ __global__ void seg_moments_kernel(int seg_base, int nseg, int M, const float* _
 // gamma kernel produced it (else from P), and Phi from the segment moments S6 when given
 // (else from Bseg and A32), with the arithmetic of adjoint_finish_warp except that the top
 // eigenvector of K(H_xy) is the stored alignment quaternion q_xy (adjoint_rotation_terms2).
+template <bool ASYNC>
 __global__ void __launch_bounds__(128)
 adjoint_finish_staged(int F, int M, int N, const float* __restrict__ frames, const float4* __restrict__ c32,
                       const float* __restrict__ wts, float wuni, const float* __restrict__ A32,
@@ -455,8 +456,8 @@ adjoint_finish_staged(int F, int M, int N, const float* __restrict__ frames, con
   const int f = blockIdx.x * wpb + w;
   if (f >= F) return;  // the whole warp leaves; only warp-level synchronisation below
   const int N3 = 3 * N;
-  float* xv = fsm + (size_t)w * 4 * N3;  // x - c
-  float* uv = xv + N3;                   // y - c_y (approximate frames)
+  float* xv = fsm + (size_t)w * 4 * N3;  // x (minus c below)
+  float* uv = xv + N3;                   // y (minus c_y below; approximate frames)
   float* bs = uv + N3;                   // beta^s
   float* bz = bs + N3;                   // beta^z
   const float4 c = c32[f];
@@ -464,11 +465,36 @@ adjoint_finish_staged(int F, int M, int N, const float* __restrict__ frames, con
   const float* x = frames + (size_t)f * N3;
   float* gsp = gs + (size_t)f * N3;
   float* gzp = gz + (size_t)f * N3;
-  for (int e = lane; e < N3; e += 32) {
-    const int b = e - 3 * (e / 3);
-    xv[e] = x[e] - cx[b];
-    bs[e] = gsp[e];
-    bz[e] = gzp[e];
+  const bool approx = rec.flag && rec.flag[f] == 0;
+  const int r = approx ? rec.ref[f] : 0;
+  const float* y = r >= 0 ? frames + (size_t)r * N3 : prior_coords;
+  if (ASYNC) {
+    // rows are 16-byte aligned (3N % 4 == 0): every 16-byte piece of x, beta^s, beta^z and
+    // y is in flight at once
+    const int n4 = N3 / 4;
+    for (int e = lane; e < n4; e += 32) {
+      const unsigned o = 16u * e;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(xv) + o),
+                   "l"(x + 4 * e) : "memory");
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(bs) + o),
+                   "l"(gsp + 4 * e) : "memory");
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(bz) + o),
+                   "l"(gzp + 4 * e) : "memory");
+      if (approx)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(uv) + o),
+                     "l"(y + 4 * e) : "memory");
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncwarp();
+    for (int e = lane; e < N3; e += 32) xv[e] -= cx[e - 3 * (e / 3)];
+  } else {
+    for (int e = lane; e < N3; e += 32) {
+      const int b = e - 3 * (e / 3);
+      xv[e] = x[e] - cx[b];
+      bs[e] = gsp[e];
+      bz[e] = gzp[e];
+      if (approx) uv[e] = y[e];
+    }
   }
   const float sf = (float)s[f];
   float Gs, Gz;
@@ -487,7 +513,6 @@ adjoint_finish_staged(int F, int M, int N, const float* __restrict__ frames, con
     Gs = wsum(Gs);
     Gz = wsum(Gz);
   }
-  const bool approx = rec.flag && rec.flag[f] == 0;
   if (!approx) {
     __syncwarp();
     for (int e = lane; e < N3; e += 32) {
@@ -497,12 +522,10 @@ adjoint_finish_staged(int F, int M, int N, const float* __restrict__ frames, con
     }
     return;
   }
-  const int r = rec.ref[f];
-  const float* y = r >= 0 ? frames + (size_t)r * N3 : prior_coords;
   float4 cyv = prior_c;
   if (r >= 0) cyv = c32[r];
   const float cy[3] = {cyv.x, cyv.y, cyv.z};
-  for (int e = lane; e < N3; e += 32) uv[e] = y[e] - cy[e - 3 * (e / 3)];
+  for (int e = lane; e < N3; e += 32) uv[e] -= cy[e - 3 * (e / 3)];
   __syncwarp();
   float R[9], qxy[4];
   {
@@ -661,12 +684,24 @@ void launch_adjoint_finish(Prec p, int F, const void* frames, const LandmarkDev&
   if (p != P_F64 && per_warp <= 200 * 1024) {
     const int wpb = per_warp * 4 <= 96 * 1024 ? 4 : (per_warp * 2 <= 160 * 1024 ? 2 : 1);
     const size_t smem = per_warp * wpb;
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(adjoint_finish_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    adjoint_finish_staged<<<(unsigned)((F + wpb - 1) / wpb), 32 * wpb, smem, st>>>(
-        F, L.M, L.N, (const float*)frames, fi.c32, L.w, (float)L.dscale, L.A32, L.q32, (const float*)P, s,
-        (float)lambda, Gsum, S6, seg_base, (const float*)Bseg, seg_of_frame, rec, (const float*)prior.coords,
-        prior.c32, (float*)gs, (float*)gz);
+    const bool async = (3 * L.N) % 4 == 0 && ((uintptr_t)frames % 16) == 0 && ((uintptr_t)gs % 16) == 0 &&
+                       ((uintptr_t)gz % 16) == 0 && ((uintptr_t)prior.coords % 16) == 0;
+    const unsigned blocks = (unsigned)((F + wpb - 1) / wpb);
+    if (async) {
+      if (smem > 48 * 1024)
+        cudaFuncSetAttribute(adjoint_finish_staged<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      adjoint_finish_staged<true><<<blocks, 32 * wpb, smem, st>>>(
+          F, L.M, L.N, (const float*)frames, fi.c32, L.w, (float)L.dscale, L.A32, L.q32, (const float*)P, s,
+          (float)lambda, Gsum, S6, seg_base, (const float*)Bseg, seg_of_frame, rec, (const float*)prior.coords,
+          prior.c32, (float*)gs, (float*)gz);
+    } else {
+      if (smem > 48 * 1024)
+        cudaFuncSetAttribute(adjoint_finish_staged<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      adjoint_finish_staged<false><<<blocks, 32 * wpb, smem, st>>>(
+          F, L.M, L.N, (const float*)frames, fi.c32, L.w, (float)L.dscale, L.A32, L.q32, (const float*)P, s,
+          (float)lambda, Gsum, S6, seg_base, (const float*)Bseg, seg_of_frame, rec, (const float*)prior.coords,
+          prior.c32, (float*)gs, (float*)gz);
+    }
     note_launch();
     return;
   }
