@@ -3,16 +3,21 @@
 //
 // With the close structure every approximate frame x enters only as x' = R_xy^T (x - c),
 // and every landmark of segment s (frames sharing the close structure y(s)) only as
-// b = R_{a_i y} a (Eq. close_dist).  Writing x' once per frame and b once per segment turns
-// the two heavy loops into plain tiles over contiguous rows:
-//   approx_pair_tile:   D~_fi = sum_j |x'_fj - b_ij|^2 / N;
-//   adjoint_beta_tile:  beta_fj = sum_i gamma_fi b_ij, for gamma^s and gamma^z at once.
+// b = R_{a_i y} a (Eq. close_dist).  Both are written once, as deviations from the centred
+// close structure y' of their segment: dx = x' - y' and d_i = b_i - y', with their squared
+// norms.  Then
+//   approx_pair_tile:   D~_fi = (|dx_f|^2 + |d_i|^2 - 2 dx_f . d_i) / N,
+//   adjoint_beta_tile:  beta_f = Gamma_f y' + sum_i gamma_fi d_i  (gamma^s and gamma^z).
+// The identity |x' - b|^2 = |dx - d|^2 is exact; the cancelling form costs one FMA per
+// coordinate instead of a subtraction and an FMA, and stays accurate in FP32 because the
+// deviations are small: frames are within the close threshold of y, and the landmarks that
+// matter (large softmax weight) are near the frame, hence near y.
 // Rows are padded to N16 (a multiple of 16 atoms, zeros), so each chunk is a run of
 // 16-byte pieces moved global -> shared with cp.async in a 3-stage pipeline: copies of chunk
 // c+2 are in flight while chunk c is used, and no register holds staged data.
 //
-// The approximate-MSD loop uses packed FP32 pairs (f32x2) over adjacent coordinates of x'
-// and b: each instruction performs two IEEE FP32 operations, which frees issue slots for the
+// The approximate-MSD loop uses packed FP32 pairs (f32x2) over adjacent coordinates of dx
+// and d: each instruction performs two IEEE FP32 operations, which frees issue slots for the
 // shared-memory loads (the packed operations run on one of the two FP32 sub-pipes, so the
 // FP32 rate itself is unchanged).
 #include <cuda_fp16.h>
@@ -46,13 +51,85 @@ __device__ __forceinline__ float lm_f<__half>(const __half* p) {
 }
 
 // ---------------------------------------------------------------------------------------
-// x'_k = R_xy^T (x_f - c_f), f = alist[k], one row of N16 atoms per approximate frame.
+// block sum of one value per thread (blockDim.x a multiple of 32, at most 1024)
+__device__ __forceinline__ float block_sum(float v, float* red) {
+  v = warp_sum_float(v);
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[w] = v;
+  __syncthreads();
+  float t = 0.0f;
+  for (int k = 0; k < nw; ++k) t += red[k];
+  return t;
+}
+
+// y' (centred close structure) of segment slot s: the prior structure for segment 0, else
+// the frame refresh_list[seg - 1]
+__device__ __forceinline__ const float* seg_structure(int seg, const float* frames, int N3, const float4* c32,
+                                                      const int* refresh_list, const float* prior, float4 prior_c,
+                                                      float4& c) {
+  if (seg == 0) {
+    c = prior_c;
+    return prior;
+  }
+  const int f = refresh_list[seg - 1];
+  c = c32[f];
+  return frames + (size_t)f * N3;
+}
+
+// d_{s,i} = R_{a_i y(s)} a_i - y'(s) for segments s in [s0, s0 + gridDim.y): rows of N16
+// atoms in Bm, |d_{s,i}|^2 in Nb[s * M + i]; block i == 0 also writes y'(s) to Yc[s].
+template <typename LT>
+__global__ void materialize_landmarks_kernel(int s0, int M, int N, int N16, const LT* __restrict__ lm,
+                                             const float* __restrict__ Bseg, const float* __restrict__ frames,
+                                             const float4* __restrict__ c32, const int* __restrict__ refresh_list,
+                                             const float* __restrict__ prior, float4 prior_c, float* __restrict__ Bm,
+                                             float* __restrict__ Nb, float* __restrict__ Yc) {
+  __shared__ float red[32];
+  const int i = blockIdx.x, slot = blockIdx.y, seg = s0 + slot;
+  float4 c;
+  const float* y = seg_structure(seg, frames, 3 * N, c32, refresh_list, prior, prior_c, c);
+  const float* B = Bseg + ((size_t)seg * M + i) * 9;
+  float R[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) R[e] = B[e];
+  const LT* a = lm + (size_t)i * N * 3;
+  const size_t row = (size_t)slot * M + i;
+  float* out = Bm + row * N16 * 3;
+  float nrm = 0.0f;
+  for (int j = threadIdx.x; j < N16; j += blockDim.x) {
+    float o0 = 0.0f, o1 = 0.0f, o2 = 0.0f;
+    if (j < N) {
+      const float a0 = lm_f(a + 3 * j), a1 = lm_f(a + 3 * j + 1), a2 = lm_f(a + 3 * j + 2);
+      const float y0 = y[3 * j] - c.x, y1 = y[3 * j + 1] - c.y, y2 = y[3 * j + 2] - c.z;
+      o0 = (R[0] * a0 + R[1] * a1 + R[2] * a2) - y0;
+      o1 = (R[3] * a0 + R[4] * a1 + R[5] * a2) - y1;
+      o2 = (R[6] * a0 + R[7] * a1 + R[8] * a2) - y2;
+      if (i == 0) {
+        Yc[(size_t)slot * 3 * N + 3 * j] = y0;
+        Yc[(size_t)slot * 3 * N + 3 * j + 1] = y1;
+        Yc[(size_t)slot * 3 * N + 3 * j + 2] = y2;
+      }
+    }
+    out[3 * j] = o0;
+    out[3 * j + 1] = o1;
+    out[3 * j + 2] = o2;
+    nrm = fmaf(o0, o0, fmaf(o1, o1, fmaf(o2, o2, nrm)));
+  }
+  nrm = block_sum(nrm, red);
+  if (threadIdx.x == 0) Nb[row] = nrm;
+}
+
+// dx_k = R_xy^T (x_f - c_f) - y'(seg), f = alist[k], one row of N16 atoms per approximate
+// frame, and |dx_k|^2 in Nx[k].  Runs after materialize_landmarks (y' from Yc).
 __global__ void materialize_frames_kernel(int napp_max, const int* __restrict__ acount, const int* __restrict__ alist,
-                                          int N, int N16, const float* __restrict__ frames,
-                                          const float4* __restrict__ c32, const double4* __restrict__ qxy,
-                                          float* __restrict__ Xr) {
+                                          const int* __restrict__ aseg, int seg_base, int N, int N16,
+                                          const float* __restrict__ frames, const float4* __restrict__ c32,
+                                          const double4* __restrict__ qxy, const float* __restrict__ Yc,
+                                          float* __restrict__ Xr, float* __restrict__ Nx) {
+  __shared__ float red[32];
   const int k = blockIdx.x;
-  if (k >= napp_max || k >= *acount) return;
+  if (k >= napp_max || k >= *acount) return;  // uniform over the block
   const int f = alist[k];
   const float4 c = c32[f];
   const double4 qq = qxy[f];
@@ -60,61 +137,53 @@ __global__ void materialize_frames_kernel(int napp_max, const int* __restrict__ 
   float R[9];
   quat_to_rot(qf, R);
   const float* x = frames + (size_t)f * N * 3;
+  const float* yc = Yc + (size_t)(aseg[k] - seg_base) * 3 * N;
   float* out = Xr + (size_t)k * N16 * 3;
+  float nrm = 0.0f;
   for (int j = threadIdx.x; j < N16; j += blockDim.x) {
     float o0 = 0.0f, o1 = 0.0f, o2 = 0.0f;
     if (j < N) {
       const float v0 = x[3 * j] - c.x, v1 = x[3 * j + 1] - c.y, v2 = x[3 * j + 2] - c.z;
-      o0 = R[0] * v0 + R[3] * v1 + R[6] * v2;
-      o1 = R[1] * v0 + R[4] * v1 + R[7] * v2;
-      o2 = R[2] * v0 + R[5] * v1 + R[8] * v2;
+      o0 = (R[0] * v0 + R[3] * v1 + R[6] * v2) - yc[3 * j];
+      o1 = (R[1] * v0 + R[4] * v1 + R[7] * v2) - yc[3 * j + 1];
+      o2 = (R[2] * v0 + R[5] * v1 + R[8] * v2) - yc[3 * j + 2];
     }
     out[3 * j] = o0;
     out[3 * j + 1] = o1;
     out[3 * j + 2] = o2;
+    nrm = fmaf(o0, o0, fmaf(o1, o1, fmaf(o2, o2, nrm)));
   }
-}
-
-// b_{s,i} = R_{a_i y(s)} a_i for segments s in [s0, s0 + gridDim.y), rows of N16 atoms.
-template <typename LT>
-__global__ void materialize_landmarks_kernel(int s0, int M, int N, int N16, const LT* __restrict__ lm,
-                                             const float* __restrict__ Bseg, float* __restrict__ Bm) {
-  const int i = blockIdx.x, s = s0 + blockIdx.y;
-  const float* B = Bseg + ((size_t)s * M + i) * 9;
-  float R[9];
-#pragma unroll
-  for (int e = 0; e < 9; ++e) R[e] = B[e];
-  const LT* a = lm + (size_t)i * N * 3;
-  float* out = Bm + ((size_t)blockIdx.y * M + i) * N16 * 3;
-  for (int j = threadIdx.x; j < N16; j += blockDim.x) {
-    float o0 = 0.0f, o1 = 0.0f, o2 = 0.0f;
-    if (j < N) {
-      const float a0 = lm_f(a + 3 * j), a1 = lm_f(a + 3 * j + 1), a2 = lm_f(a + 3 * j + 2);
-      o0 = R[0] * a0 + R[1] * a1 + R[2] * a2;
-      o1 = R[3] * a0 + R[4] * a1 + R[5] * a2;
-      o2 = R[6] * a0 + R[7] * a1 + R[8] * a2;
-    }
-    out[3 * j] = o0;
-    out[3 * j + 1] = o1;
-    out[3 * j + 2] = o2;
-  }
+  nrm = block_sum(nrm, red);
+  if (threadIdx.x == 0) Nx[k] = nrm;
 }
 
 // gamma^s_fi = -lambda p_fi (q_i - s_f), gamma^z_fi = p_fi (Eqs. 5-6 differentiated), rows of
-// Mp >= M entries, zero beyond M.
+// Mp >= M entries (zero beyond M), and Gamma^s_f, Gamma^z_f in Gsum.  One warp per frame.
 __global__ void gamma_kernel(int F, int M, int Mp, const float* __restrict__ P, const float* __restrict__ q32,
-                             const double* __restrict__ s, float lambda, float* __restrict__ GS, float* __restrict__ GZ) {
-  const size_t total = (size_t)F * Mp;
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const int f = (int)(e / Mp), i = (int)(e - (size_t)f * Mp);
+                             const double* __restrict__ s, float lambda, float* __restrict__ GS, float* __restrict__ GZ,
+                             float* __restrict__ Gsum) {
+  const int lane = threadIdx.x & 31;
+  const int f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (f >= F) return;
+  const float sf = (float)s[f];
+  float ss = 0.0f, sz = 0.0f;
+  for (int i = lane; i < Mp; i += 32) {
     float gs = 0.0f, gz = 0.0f;
     if (i < M) {
       const float p = P[(size_t)f * M + i];
       gz = p;
-      gs = -lambda * p * (q32[i] - (float)s[f]);
+      gs = -lambda * p * (q32[i] - sf);
     }
-    GS[e] = gs;
-    GZ[e] = gz;
+    GS[(size_t)f * Mp + i] = gs;
+    GZ[(size_t)f * Mp + i] = gz;
+    ss += gs;
+    sz += gz;
+  }
+  ss = warp_sum_float(ss);
+  sz = warp_sum_float(sz);
+  if (lane == 0) {
+    Gsum[2 * f] = ss;
+    Gsum[2 * f + 1] = sz;
   }
 }
 
@@ -123,7 +192,7 @@ __global__ void gamma_kernel(int F, int M, int Mp, const float* __restrict__ P, 
 // (tx, ty) holds frames u*16 + ty (u < 4) and landmarks v*8 + tx (v < RM).  Chunks of 16
 // atoms (192 bytes per row); shared rows of 52 floats, so the 4 frame rows and the 8 landmark
 // rows a warp reads at one step fall in distinct banks.  Two atoms per step: 3 LDS.64 per
-// row, each an adjacent coordinate pair; per (frame, landmark) 3 SUB2 + 3 FMA2.
+// row, each an adjacent coordinate pair; per (frame, landmark) 3 FMA2 of dx . d.
 constexpr int AT_TF = 64, AT_THREADS = 128, AT_KC = 16, AT_STAGES = 3;
 constexpr int AT_ROWF = AT_KC * 3 + 4;
 
@@ -131,7 +200,7 @@ template <int RM>
 __global__ void __launch_bounds__(AT_THREADS, 3)
 approx_pair_tile(const int* __restrict__ alist, const int* __restrict__ aseg, const int* __restrict__ acount,
                  int seg_base, int M, int N16, const float* __restrict__ Xr, const float* __restrict__ Bm,
-                 float dscale, float* __restrict__ Dout) {
+                 const float* __restrict__ Nx, const float* __restrict__ Nb, float dscale, float* __restrict__ Dout) {
   constexpr int TF = AT_TF, TM = 8 * RM;
   extern __shared__ __align__(16) float smem[];
   float* Xs = smem;                            // [stage][TF][ROWF]
@@ -218,8 +287,7 @@ approx_pair_tile(const int* __restrict__ alist, const int* __restrict__ aseg, co
               f2 t = acc[u][v];
 #pragma unroll
               for (int h = 0; h < 3; ++h) {
-                const f2 d = f2_sub(x[u][h], b[v][h]);
-                t = f2_fma(d, d, t);
+                t = f2_fma(x[u][h], b[v][h], t);
               }
               acc[u][v] = t;
             }
@@ -242,10 +310,17 @@ approx_pair_tile(const int* __restrict__ alist, const int* __restrict__ aseg, co
         const int ff = u * 16 + ty;
         if (ff < k || ff >= kend) continue;
         const int f = s_frame[ff];
+        const float nx = Nx[row0 + ff];
+        const float* nb = Nb + (size_t)(seg - seg_base) * M;
 #pragma unroll
         for (int v = 0; v < RM; ++v) {
           const int i = i0 + v * 8 + tx;
-          if (i < M) Dout[(size_t)f * M + i] = (thi[u][v] + tlo[u][v]) * dscale;
+          if (i < M) {
+            // |dx|^2 + |d|^2 - 2 dx.d with the compensated cross term
+            const float two_c = 2.0f * thi[u][v];
+            const float base = nx + nb[i];
+            Dout[(size_t)f * M + i] = ((base - two_c) - 2.0f * tlo[u][v]) * dscale;
+          }
         }
       }
       k = kend;
@@ -265,8 +340,9 @@ constexpr int BT_BROW = BT_TJ * 3 + 4;
 
 __global__ void __launch_bounds__(BT_THREADS, 2)
 adjoint_beta_tile(int F, int M, int Mp, int N, int N16, int seg_base, const float* __restrict__ GS,
-                  const float* __restrict__ GZ, const float* __restrict__ Bm, const int* __restrict__ seg_of_frame,
-                  float* __restrict__ gs, float* __restrict__ gz) {
+                  const float* __restrict__ GZ, const float* __restrict__ Bm, const float* __restrict__ Gsum,
+                  const float* __restrict__ Yc, const int* __restrict__ seg_of_frame, float* __restrict__ gs,
+                  float* __restrict__ gz) {
   extern __shared__ __align__(16) float smem[];
   float* Gss = smem;                               // [stage][TF][GROW]
   float* Gzs = Gss + BT_STAGES * BT_TF * BT_GROW;  // [stage][TF][GROW]
@@ -368,18 +444,22 @@ adjoint_beta_tile(int F, int M, int Mp, int N, int N16, int seg_base, const floa
       __syncthreads();  // the next run's first copies overwrite stages still being read
       k = kend;
     }
+    // beta = Gamma_f y' + sum_i gamma_fi d_i
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int f = f0 + ty * 4 + u;
       if (f >= F) continue;
+      const float Gs = Gsum[2 * f], Gz = Gsum[2 * f + 1];
+      const float* yc = Yc + (size_t)(s_seg[ty * 4 + u] - seg_base) * 3 * N;
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
         const int j = j0 + tx * 2 + a;
         if (j >= N) continue;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          gs[((size_t)f * N + j) * 3 + c] = acs[u][3 * a + c];
-          gz[((size_t)f * N + j) * 3 + c] = acz[u][3 * a + c];
+          const float yv = yc[3 * j + c];
+          gs[((size_t)f * N + j) * 3 + c] = fmaf(Gs, yv, acs[u][3 * a + c]);
+          gz[((size_t)f * N + j) * 3 + c] = fmaf(Gz, yv, acz[u][3 * a + c]);
         }
       }
     }
@@ -405,62 +485,67 @@ size_t tile_bytes_landmarks(int nseg, int M, int N) {
 }
 size_t tile_bytes_gamma(int F, int M) { return (size_t)F * round_up16(M) * sizeof(float); }
 
-void launch_materialize_frames(int napp, const int* acount, const int* alist, const LandmarkDev& L,
-                               const void* frames, FrameInfo fi, const double4* qxy, float* Xr, cudaStream_t st) {
-  if (napp <= 0) return;
-  materialize_frames_kernel<<<napp, 128, 0, st>>>(napp, acount, alist, L.N, round_up16(L.N), (const float*)frames,
-                                                  fi.c32, qxy, Xr);
-  note_launch();
-}
-
-void launch_materialize_landmarks(Prec p, int s0, int ns, const LandmarkDev& L, const float* Bseg, float* Bm,
-                                  cudaStream_t st) {
+void launch_materialize_landmarks(Prec p, int s0, int ns, const LandmarkDev& L, const float* Bseg, const void* frames,
+                                  FrameInfo fi, const int* refresh_list, const RefDesc& prior, float* Bm, float* Nb,
+                                  float* Yc, cudaStream_t st) {
   if (ns <= 0 || L.M <= 0) return;
   const dim3 grid(L.M, ns);
   const int N16 = round_up16(L.N);
   if (p == P_F16)
-    materialize_landmarks_kernel<__half><<<grid, 128, 0, st>>>(s0, L.M, L.N, N16, (const __half*)L.coords, Bseg, Bm);
+    materialize_landmarks_kernel<__half><<<grid, 128, 0, st>>>(s0, L.M, L.N, N16, (const __half*)L.coords, Bseg,
+                                                               (const float*)frames, fi.c32, refresh_list,
+                                                               (const float*)prior.coords, prior.c32, Bm, Nb, Yc);
   else
-    materialize_landmarks_kernel<float><<<grid, 128, 0, st>>>(s0, L.M, L.N, N16, (const float*)L.coords, Bseg, Bm);
+    materialize_landmarks_kernel<float><<<grid, 128, 0, st>>>(s0, L.M, L.N, N16, (const float*)L.coords, Bseg,
+                                                              (const float*)frames, fi.c32, refresh_list,
+                                                              (const float*)prior.coords, prior.c32, Bm, Nb, Yc);
+  note_launch();
+}
+
+void launch_materialize_frames(int napp, const int* acount, const int* alist, const int* aseg, int seg_base,
+                               const LandmarkDev& L, const void* frames, FrameInfo fi, const double4* qxy,
+                               const float* Yc, float* Xr, float* Nx, cudaStream_t st) {
+  if (napp <= 0) return;
+  materialize_frames_kernel<<<napp, 128, 0, st>>>(napp, acount, alist, aseg, seg_base, L.N, round_up16(L.N),
+                                                  (const float*)frames, fi.c32, qxy, Yc, Xr, Nx);
   note_launch();
 }
 
 void launch_gamma(int F, const LandmarkDev& L, const float* P, const double* s, double lambda, float* GS, float* GZ,
-                  cudaStream_t st) {
+                  float* Gsum, cudaStream_t st) {
   if (F <= 0) return;
-  const int Mp = round_up16(L.M);
-  const size_t total = (size_t)F * Mp;
-  const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, (size_t)152 * 16);
-  gamma_kernel<<<blocks, 256, 0, st>>>(F, L.M, Mp, P, L.q32, s, (float)lambda, GS, GZ);
+  gamma_kernel<<<(F + 7) / 8, 256, 0, st>>>(F, L.M, round_up16(L.M), P, L.q32, s, (float)lambda, GS, GZ, Gsum);
   note_launch();
 }
 
 void launch_approx_pairs_tile(int napp, const int* alist, const int* aseg, const int* acount, int seg_base,
-                              const LandmarkDev& L, const float* Xr, const float* Bm, float* D, cudaStream_t st) {
+                              const LandmarkDev& L, const float* Xr, const float* Bm, const float* Nx, const float* Nb,
+                              float* D, cudaStream_t st) {
   if (napp <= 0 || L.M <= 0) return;
   const int rm = tile_rm(L.M), tm = 8 * rm, N16 = round_up16(L.N);
   const size_t smem = (size_t)AT_STAGES * (AT_TF + tm) * AT_ROWF * sizeof(float);
   const dim3 grid((L.M + tm - 1) / tm, std::min((napp + AT_TF - 1) / AT_TF, 65535));
   if (rm == 5) {
     set_smem(approx_pair_tile<5>, smem);
-    approx_pair_tile<5><<<grid, AT_THREADS, smem, st>>>(alist, aseg, acount, seg_base, L.M, N16, Xr, Bm,
+    approx_pair_tile<5><<<grid, AT_THREADS, smem, st>>>(alist, aseg, acount, seg_base, L.M, N16, Xr, Bm, Nx, Nb,
                                                          (float)L.dscale, D);
   } else {
     set_smem(approx_pair_tile<4>, smem);
-    approx_pair_tile<4><<<grid, AT_THREADS, smem, st>>>(alist, aseg, acount, seg_base, L.M, N16, Xr, Bm,
+    approx_pair_tile<4><<<grid, AT_THREADS, smem, st>>>(alist, aseg, acount, seg_base, L.M, N16, Xr, Bm, Nx, Nb,
                                                          (float)L.dscale, D);
   }
   note_launch();
 }
 
 void launch_adjoint_beta_tile(int F, const LandmarkDev& L, int seg_base, const float* GS, const float* GZ,
-                              const float* Bm, const int* seg_of_frame, float* gs, float* gz, cudaStream_t st) {
+                              const float* Bm, const float* Gsum, const float* Yc, const int* seg_of_frame, float* gs,
+                              float* gz, cudaStream_t st) {
   if (F <= 0) return;
   const size_t smem = (size_t)BT_STAGES * (2 * BT_TF * BT_GROW + BT_KL * BT_BROW) * sizeof(float);
   const dim3 grid((L.N + BT_TJ - 1) / BT_TJ, std::min((F + BT_TF - 1) / BT_TF, 65535));
   set_smem(adjoint_beta_tile, smem);
   adjoint_beta_tile<<<grid, BT_THREADS, smem, st>>>(F, L.M, round_up16(L.M), L.N, round_up16(L.N), seg_base, GS, GZ,
-                                                    Bm, seg_of_frame, gs, gz);
+                                                    Bm, Gsum, Yc, seg_of_frame, gs, gz);
   note_launch();
 }
 

@@ -101,7 +101,8 @@ struct pcv_ctx {
   DevBuf c32, c64, fG, bandD, bandQ, bandF, chD, chQ, chF, rlist, rcount, recF, recRef, recD, recQ, reflist,
       segof, alist, aseg, Dbuf, Rpair, Bseg, mstat, status, nrecheck, small;
   DevBuf Xr, Bm, GSb, GZb;  // materialised x', b and the gamma rows
-  DevBuf Amma, Gsum, Bmma, Ymma;  // tensor-core adjoint operands
+  DevBuf Nx, Nb, Yc, Gsum;       // |dx|^2, |d|^2, centred close structures, Gamma sums
+  DevBuf Amma, Bmma;              // tensor-core adjoint operands
   DevBuf S6;                      // per-segment landmark moments R A R^T of the finish
   DevBuf h_frames, h_s, h_z, h_gs, h_gz, h_msd, h_ref;  // device staging for pcv_evaluate_host
   Small* small_host = nullptr;
@@ -276,7 +277,7 @@ pcv_status pcv_destroy(pcv_ctx* c) {
   DevBuf* bufs[] = {&c->lm, &c->lmG, &c->lmA, &c->lmA32, &c->lmq, &c->lmq32, &c->w32, &c->w64, &c->y, &c->Bprior, &c->c32, &c->c64,
                     &c->fG, &c->bandD, &c->bandQ, &c->bandF, &c->chD, &c->chQ, &c->chF, &c->rlist, &c->rcount,
                     &c->recF, &c->recRef, &c->recD, &c->recQ, &c->reflist, &c->segof, &c->alist, &c->aseg,
-                    &c->Dbuf, &c->Rpair, &c->Bseg, &c->Xr, &c->Bm, &c->GSb, &c->GZb, &c->Amma, &c->Gsum, &c->Bmma, &c->Ymma, &c->S6, &c->mstat, &c->status, &c->nrecheck, &c->small, &c->h_frames,
+                    &c->Dbuf, &c->Rpair, &c->Bseg, &c->Xr, &c->Bm, &c->GSb, &c->GZb, &c->Nx, &c->Nb, &c->Yc, &c->Gsum, &c->Amma, &c->Bmma, &c->S6, &c->mstat, &c->status, &c->nrecheck, &c->small, &c->h_frames,
                     &c->h_s, &c->h_z, &c->h_gs, &c->h_gz, &c->h_msd, &c->h_ref};
   for (DevBuf* b : bufs) release(*b);
   for (const ProfEvent& e : c->prof_pending) {
@@ -645,17 +646,20 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
   const MmaShape msh = mma_shape(F, M, c->N);
   if (c->prec != P_F64 && c->uniform && seg_form && nseg > 0) {
     const size_t xb = tile_bytes_frames(napp, c->N), bb = tile_bytes_landmarks(nseg, M, c->N);
+    const size_t nb = sizeof(float) * ((size_t)napp + (size_t)nseg * M + (size_t)nseg * 3 * c->N + 2 * (size_t)F);
     const size_t gb = grads ? tile_bytes_gamma(F, M) : 0;  // per gamma kind
-    const size_t mb = msh.a_bytes + 2 * sizeof(float) * (size_t)F + (msh.b_bytes_per_seg + msh.y_bytes_per_seg) * nseg;
+    const size_t mb = msh.a_bytes + msh.b_bytes_per_seg * nseg;
     mma = grads && c->tensor_cores;
-    if ((int64_t)(xb + bb + (mma ? mb : 2 * gb)) <= c->mat_cap) {
+    if ((int64_t)(xb + bb + nb + (mma ? mb : 2 * gb)) <= c->mat_cap) {
       if ((ps = ensure(c, c->Xr, xb)) != PCV_OK) return ps;
       if ((ps = ensure(c, c->Bm, bb)) != PCV_OK) return ps;
+      if ((ps = ensure(c, c->Nx, sizeof(float) * (size_t)napp)) != PCV_OK) return ps;
+      if ((ps = ensure(c, c->Nb, sizeof(float) * (size_t)nseg * M)) != PCV_OK) return ps;
+      if ((ps = ensure(c, c->Yc, sizeof(float) * 3 * (size_t)c->N * nseg)) != PCV_OK) return ps;
+      if (grads && (ps = ensure(c, c->Gsum, 2 * sizeof(float) * (size_t)F)) != PCV_OK) return ps;
       if (mma) {
         if ((ps = ensure(c, c->Amma, msh.a_bytes)) != PCV_OK) return ps;
-        if ((ps = ensure(c, c->Gsum, 2 * sizeof(float) * (size_t)F)) != PCV_OK) return ps;
         if ((ps = ensure(c, c->Bmma, msh.b_bytes_per_seg * nseg)) != PCV_OK) return ps;
-        if ((ps = ensure(c, c->Ymma, msh.y_bytes_per_seg * nseg)) != PCV_OK) return ps;
       } else if (grads) {
         if ((ps = ensure(c, c->GSb, gb)) != PCV_OK) return ps;
         if ((ps = ensure(c, c->GZb, gb)) != PCV_OK) return ps;
@@ -672,18 +676,20 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
   }
   if (tiled) {
     PROF(c, K_MATERIALIZE);
-    launch_materialize_landmarks(c->prec, seg_base, nseg, L, (const float*)c->Bseg.p, (float*)c->Bm.p, st);
+    launch_materialize_landmarks(c->prec, seg_base, nseg, L, (const float*)c->Bseg.p, frames, fi,
+                                 (const int*)c->reflist.p, prior, (float*)c->Bm.p, (float*)c->Nb.p, (float*)c->Yc.p, st);
     if (mma)
       launch_delta_split(c->prec, seg_base, nseg, L, msh, (const float*)c->Bseg.p, frames, fi,
-                         (const int*)c->reflist.p, prior, (float*)c->Bmma.p, (float*)c->Ymma.p, st);
-    launch_materialize_frames(napp, &sm->approx_count, (const int*)c->alist.p, L, frames, fi, rec.qxy,
-                              (float*)c->Xr.p, st);
+                         (const int*)c->reflist.p, prior, (float*)c->Bmma.p, (float*)c->Yc.p, st);
+    launch_materialize_frames(napp, &sm->approx_count, (const int*)c->alist.p, (const int*)c->aseg.p, seg_base, L,
+                              frames, fi, rec.qxy, (const float*)c->Yc.p, (float*)c->Xr.p, (float*)c->Nx.p, st);
   }
   {
     PROF(c, K_APPROX);
     if (tiled)
       launch_approx_pairs_tile(napp, (const int*)c->alist.p, (const int*)c->aseg.p, &sm->approx_count, seg_base, L,
-                               (const float*)c->Xr.p, (const float*)c->Bm.p, (float*)c->Dbuf.p, st);
+                               (const float*)c->Xr.p, (const float*)c->Bm.p, (const float*)c->Nx.p,
+                               (const float*)c->Nb.p, (float*)c->Dbuf.p, st);
     else
       launch_approx_pairs(c->prec, napp, (const int*)c->alist.p, (const int*)c->aseg.p, &sm->approx_count, frames,
                           L, fi, rec.qxy, c->Bseg.p, c->Dbuf.p, st);
@@ -702,16 +708,18 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
       }
       PROF(c, K_ADJ_MMA);
       launch_adjoint_beta_mma(F, L, msh, seg_base, (const float*)c->Amma.p, (const float*)c->Gsum.p,
-                              (const float*)c->Bmma.p, (const float*)c->Ymma.p, (const int*)c->segof.p, (float*)gs,
+                              (const float*)c->Bmma.p, (const float*)c->Yc.p, (const int*)c->segof.p, (float*)gs,
                               (float*)gz, (unsigned*)c->status.p, st);
     } else if (tiled) {
       {
         PROF(c, K_GAMMA);
-        launch_gamma(F, L, (const float*)c->Dbuf.p, s, c->lambda, (float*)c->GSb.p, (float*)c->GZb.p, st);
+        launch_gamma(F, L, (const float*)c->Dbuf.p, s, c->lambda, (float*)c->GSb.p, (float*)c->GZb.p,
+                     (float*)c->Gsum.p, st);
       }
       PROF(c, K_ADJ_BETA_SEG);
       launch_adjoint_beta_tile(F, L, seg_base, (const float*)c->GSb.p, (const float*)c->GZb.p, (const float*)c->Bm.p,
-                               (const int*)c->segof.p, (float*)gs, (float*)gz, st);
+                               (const float*)c->Gsum.p, (const float*)c->Yc.p, (const int*)c->segof.p, (float*)gs,
+                               (float*)gz, st);
     } else {
       ProfScope ps(c, seg_form && c->prec != P_F64 ? K_ADJ_BETA_SEG : K_ADJ_BETA);
       launch_adjoint_beta(c->prec, F, L, c->Dbuf.p, s, c->lambda, nullptr, c->Bseg.p, (const int*)c->segof.p,
@@ -726,7 +734,7 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
     }
     PROF(c, K_ADJ_FINISH);
     launch_adjoint_finish(c->prec, F, frames, L, fi, c->Dbuf.p, s, c->lambda, c->Bseg.p, (const int*)c->segof.p, rec,
-                          prior, gs, gz, st, mma ? (const float*)c->Gsum.p : nullptr,
+                          prior, gs, gz, st, tiled ? (const float*)c->Gsum.p : nullptr,
                           moments ? (const float*)c->S6.p : nullptr, seg_base);
   }
   // carry the close structure over to the next call

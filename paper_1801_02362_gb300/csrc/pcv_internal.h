@@ -150,26 +150,31 @@ void launch_approx_pairs(Prec p, int max_rows, const int* approx_list, const int
 
 // ---------------------------------------------------------------------------------------
 // materialised-operand path (k_tile.cu; FP32 and FP16-storage modes, uniform weights).
-// Rows padded to round_up16(N) atoms; Bm holds segments [seg_base, seg_base + ns).
+// Rows padded to round_up16(N) atoms; segment slots s = seg - seg_base in [0, ns).
 inline int round_up16(int n) { return (n + 15) & ~15; }
 size_t tile_bytes_frames(int napp, int N);
 size_t tile_bytes_landmarks(int nseg, int M, int N);
 size_t tile_bytes_gamma(int F, int M);
-// x'_k = R_xy^T (x - c) for approximate frames k < *acount (f = alist[k])
-void launch_materialize_frames(int napp, const int* acount, const int* alist, const LandmarkDev& L,
-                               const void* frames, FrameInfo fi, const double4* qxy, float* Xr, cudaStream_t st);
-// b = R_{a_i y} a_i for segments [s0, s0 + ns), rotations Bseg (9 floats each)
-void launch_materialize_landmarks(Prec p, int s0, int ns, const LandmarkDev& L, const float* Bseg, float* Bm,
-                                  cudaStream_t st);
+// d_i = R_{a_i y} a_i - y' per segment (Bm), |d_i|^2 (Nb, ns*M floats), y' (Yc, ns*3N floats);
+// y is the prior structure for segment 0, else frame refresh_list[seg - 1]
+void launch_materialize_landmarks(Prec p, int s0, int ns, const LandmarkDev& L, const float* Bseg, const void* frames,
+                                  FrameInfo fi, const int* refresh_list, const RefDesc& prior, float* Bm, float* Nb,
+                                  float* Yc, cudaStream_t st);
+// dx_k = R_xy^T (x - c) - y' for approximate frames k < *acount (Xr), |dx_k|^2 (Nx); after
+// launch_materialize_landmarks
+void launch_materialize_frames(int napp, const int* acount, const int* alist, const int* aseg, int seg_base,
+                               const LandmarkDev& L, const void* frames, FrameInfo fi, const double4* qxy,
+                               const float* Yc, float* Xr, float* Nx, cudaStream_t st);
 // gamma^s, gamma^z rows (round_up16(M) entries each, tile_bytes_gamma bytes per kind) from
-// the softmax weights P
+// the softmax weights P, and Gamma^s_f, Gamma^z_f (Gsum, 2F floats)
 void launch_gamma(int F, const LandmarkDev& L, const float* P, const double* s, double lambda, float* GS, float* GZ,
-                  cudaStream_t st);
+                  float* Gsum, cudaStream_t st);
 void launch_approx_pairs_tile(int napp, const int* alist, const int* aseg, const int* acount, int seg_base,
-                              const LandmarkDev& L, const float* Xr, const float* Bm, float* D, cudaStream_t st);
+                              const LandmarkDev& L, const float* Xr, const float* Bm, const float* Nx, const float* Nb,
+                              float* D, cudaStream_t st);
 void launch_adjoint_beta_tile(int F, const LandmarkDev& L, int seg_base, const float* GS, const float* GZ,
-                              const float* Bm, const int* seg_of_frame, float* gs, float* gz, cudaStream_t st);
-
+                              const float* Bm, const float* Gsum, const float* Yc, const int* seg_of_frame, float* gs,
+                              float* gz, cudaStream_t st);
 
 // ---------------------------------------------------------------------------------------
 // tensor-core segment adjoint (k_mma.cu; FP32 and FP16-storage modes, uniform weights)
