@@ -181,6 +181,45 @@ def lambda_from_gpu(pcv, lm):
     return 2.3 / float(np.mean(np.diagonal(d, offset=1)))
 
 
+def time_config(pcv, label: str, seed: int, n: int, m: int, f: int, eps: float, grad: bool, precision: str,
+                noise: float = 0.05, steps: int = 3, schedule: str = "drift") -> dict:
+    """One side measurement: a fresh context on seeded synthetic inputs of the given sizes,
+    2 untimed evaluations, then `steps` timed ones (CUDA events on the context's stream)."""
+    import torch
+    from paper_1801_02362_gb300 import synth
+
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    sdt = np.float64 if precision == "fp64" else np.float32
+    lm, fr = synth.make_problem(seed, n_atoms=n, n_landmarks=m, n_frames=f, frame_noise=noise, schedule=schedule,
+                                frame_dtype=sdt, landmark_dtype=sdt)
+    lam = lambda_from_gpu(pcv, lm)
+    ctx = pcv.PathCV(lm, lam, eps=eps, precision=precision)
+    frames = torch.tensor(np.ascontiguousarray(fr), dtype=dt, device="cuda")
+    for _ in range(2):
+        pcv.pcv_reset_close_state(ctx.ctx)
+        ctx.evaluate(frames, grad=grad)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    ctx.set_profiling(True)
+    ctx.profile()
+    a.record(stream)
+    for _ in range(steps):
+        pcv.pcv_reset_close_state(ctx.ctx)
+        ctx.evaluate(frames, grad=grad)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t = a.elapsed_time(b) / steps
+    pr = ctx.profile()
+    st = ctx.stats()
+    ctx.close()
+    return {"workload": label, "atoms": n, "landmarks": m, "frames": f, "eps_nm2": eps, "precision": precision,
+            "gradients": grad, "ms_per_step": t, "frames_per_s": f / (t / 1e3),
+            "msds_per_s": f * m / (t / 1e3), "exact_msds": st["landmark_alignments"], "approx_msds": st["approx_msds"],
+            "kernel_ms": {k: round(v[0] / steps, 4) for k, v in pr.items()}}
+
+
 def cpu_baseline(lm, fr, lam, eps, seconds: float) -> dict:
     import oracle
 
@@ -369,6 +408,11 @@ def run_ours(args):
                               "approx_msds": st2["approx_msds"],
                               "kernel_ms": {k: round(v[0] / n, 4) for k, v in pr.items()}}
         pcv.pcv_set_close_threshold(ctx.ctx, args.eps)
+        details["c1_exact_fp64"] = time_config(pcv, "exact path CV, FP64, N=22, M=20, F=1000 (reflecting walk)", 1,
+                                               22, 20, 1000, -1.0, False, "fp64", noise=0.02, steps=10,
+                                               schedule="walk")
+        details["c4_exact_grad"] = time_config(pcv, "exact path CV with gradients, FP32, N=1000, M=500, F=4096", 4,
+                                               1000, 500, 4096, -1.0, True, "fp32")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -201,6 +201,41 @@ PCV_API pcv_status pcv_get_profile(pcv_ctx* ctx, int n, double* ms, int64_t* lau
 /* Name of kernel family `id` ("" outside 0..PCV_PROFILE_KERNELS-1). */
 PCV_API const char* pcv_profile_name(int id);
 
+/* Landmark shards (one GPU per shard, or several contexts on one GPU).
+ *
+ * Eqs. 5-6 are a log-sum-exp over the landmarks, so path CVs computed by contexts that
+ * each hold a subset of the landmarks (with the landmarks' global properties q_i) combine
+ * exactly into the whole-path values: with w_r = exp(-lambda (z_r - z)) over shards r,
+ *   z = -(1/lambda) ln sum_r exp(-lambda z_r),  s = sum_r w_r s_r,  dz = sum_r w_r dz_r,
+ *   ds = sum_r w_r (ds_r - lambda (s_r - s) dz_r).
+ * The combine is one MIN reduction of z_r over the shards (zmin, F values) and one SUM
+ * reduction of packed terms:
+ *   pcv_shard_pack:   shard values -> scalars (F x 2 doubles) and, when gradients are
+ *                     given, elements (F x N x 3 x 3 doubles);
+ *   (sum scalars and elements over the shards: an all-reduce, or a host/device sum)
+ *   pcv_shard_unpack: summed terms -> s, z (F doubles) and dsdx, dzdx (F x N x 3).
+ * precision selects the gradient type: double for PCV_FP64, float otherwise.  dsdx and
+ * dzdx are both given or both NULL (then elements may be NULL).  zmin[f] must be <= z_r[f]
+ * for every shard (the MIN over shards is exact and keeps every exp <= 1).
+ * Device versions: all pointers are device memory, work is enqueued on `stream` (a
+ * cudaStream_t, NULL = default stream), and the output of pack may alias nothing of its
+ * input.  Host versions: all pointers are host memory; no GPU is needed.
+ * Returns PCV_EINVAL on F < 0, N < 1, lambda <= 0 or missing arrays, PCV_ECUDA when the
+ * launch fails.  The paper shards landmarks over MPI ranks in its implementation; this is
+ * the same reduction written for exact reassembly. */
+PCV_API pcv_status pcv_shard_pack(int precision, int F, int N, double lambda, const double* zmin, const double* s,
+                                  const double* z, const void* dsdx, const void* dzdx, double* scalars,
+                                  double* elements, void* stream);
+PCV_API pcv_status pcv_shard_unpack(int precision, int F, int N, double lambda, const double* zmin,
+                                    const double* scalars, const double* elements, double* s, double* z, void* dsdx,
+                                    void* dzdx, void* stream);
+PCV_API pcv_status pcv_shard_pack_host(int precision, int F, int N, double lambda, const double* zmin,
+                                       const double* s, const double* z, const void* dsdx, const void* dzdx,
+                                       double* scalars, double* elements);
+PCV_API pcv_status pcv_shard_unpack_host(int precision, int F, int N, double lambda, const double* zmin,
+                                         const double* scalars, const double* elements, double* s, double* z,
+                                         void* dsdx, void* dzdx);
+
 /* Exact-mode path CVs for callers that cannot allocate device memory.
  *
  * The paper has no counterpart; this is a deployment aid.  Some callers cannot call

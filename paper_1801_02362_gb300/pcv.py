@@ -65,6 +65,10 @@ SIGNATURES = {
     "pcv_profile_name": (ctypes.c_char_p, [_i]),
     "pcv_evaluate_exact_noalloc": (_i, [_i, _i, _i, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, ctypes.c_char_p,
                                        ctypes.c_size_t]),
+    "pcv_shard_pack": (_i, [_i, _i, _i, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "pcv_shard_unpack": (_i, [_i, _i, _i, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "pcv_shard_pack_host": (_i, [_i, _i, _i, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "pcv_shard_unpack_host": (_i, [_i, _i, _i, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -190,6 +194,54 @@ def pcv_get_profile(ctx) -> dict:
         if name and la[k]:
             out[name] = (float(ms[k]), int(la[k]))
     return out
+
+
+def pcv_shard_pack(precision: int, F: int, N: int, lam: float, zmin_ptr, s_ptr, z_ptr, dsdx_ptr, dzdx_ptr,
+                   scalars_ptr, elements_ptr, stream=None):
+    """Device pointers: shard values -> summable terms (see include/pcv.h)."""
+    _check(None, load().pcv_shard_pack(precision, F, N, float(lam), zmin_ptr, s_ptr, z_ptr, dsdx_ptr, dzdx_ptr,
+                                       scalars_ptr, elements_ptr, stream))
+
+
+def pcv_shard_unpack(precision: int, F: int, N: int, lam: float, zmin_ptr, scalars_ptr, elements_ptr, s_ptr,
+                     z_ptr, dsdx_ptr, dzdx_ptr, stream=None):
+    """Device pointers: summed terms -> whole-path s, z and gradients."""
+    _check(None, load().pcv_shard_unpack(precision, F, N, float(lam), zmin_ptr, scalars_ptr, elements_ptr, s_ptr,
+                                         z_ptr, dsdx_ptr, dzdx_ptr, stream))
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def pcv_shard_pack_host(lam: float, zmin: np.ndarray, s: np.ndarray, z: np.ndarray, dsdx=None, dzdx=None):
+    """Host arrays (FP64 gradients): returns (scalars F x 2, elements F x N x 3 x 3 or None)."""
+    F = s.shape[0]
+    N = dsdx.shape[1] if dsdx is not None else 1
+    zmin, s, z = (np.ascontiguousarray(a, dtype=np.float64) for a in (zmin, s, z))
+    g = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in (dsdx, dzdx)]
+    scal = np.zeros((F, 2))
+    elem = np.zeros((F, N, 3, 3)) if g[0] is not None else None
+    _check(None, load().pcv_shard_pack_host(PCV_FP64, F, N, float(lam), _np_ptr(zmin), _np_ptr(s), _np_ptr(z),
+                                            _np_ptr(g[0]), _np_ptr(g[1]), _np_ptr(scal), _np_ptr(elem)))
+    return scal, elem
+
+
+def pcv_shard_unpack_host(lam: float, zmin: np.ndarray, scalars: np.ndarray, elements=None):
+    """Host arrays: summed terms -> (s, z, dsdx, dzdx) with FP64 gradients (None without elements)."""
+    F = scalars.shape[0]
+    zmin = np.ascontiguousarray(zmin, dtype=np.float64)
+    scalars = np.ascontiguousarray(scalars, dtype=np.float64)
+    s, z = np.zeros(F), np.zeros(F)
+    gs = gz = None
+    N = 1
+    if elements is not None:
+        elements = np.ascontiguousarray(elements, dtype=np.float64)
+        N = elements.shape[1]
+        gs, gz = np.zeros((F, N, 3)), np.zeros((F, N, 3))
+    _check(None, load().pcv_shard_unpack_host(PCV_FP64, F, N, float(lam), _np_ptr(zmin), _np_ptr(scalars),
+                                              _np_ptr(elements), _np_ptr(s), _np_ptr(z), _np_ptr(gs), _np_ptr(gz)))
+    return s, z, gs, gz
 
 
 def pcv_last_error(ctx) -> str:

@@ -1,0 +1,109 @@
+"""Full-size GPU parity in the launch configuration the benchmark times.
+
+The oracle cannot replay 100k frames of Algorithm 2 with gradients in seconds, so the
+full-size runs are checked through properties and samples it can compute one by one:
+  * every refresh decision: D(x_t, y) > eps with the exact alignment of each frame onto the
+    close structure y in force (y tracked through the GPU's own flags, so one wrong flag
+    makes the check fail at that frame);
+  * sampled frames in full (MSD row, s, z, both gradients): an approximate frame t with close
+    structure y is exactly the second frame of the two-frame sequence [y, x_t], a refreshed
+    frame is Algorithm 1 on x_t.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from _util import GRAD_TOL, TOL, d_err, grad_err, s_err, z_err
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pcv():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1801_02362_gb300 import build_lib
+    from paper_1801_02362_gb300 import pcv as mod
+
+    build_lib.build()
+    mod.load()
+    return mod
+
+
+def _check_frame_samples(res, fr, lm, lam, eps, ts, precision="fp32"):
+    flags = res["refreshed"]
+    for t in ts:
+        if flags[t]:
+            r = oracle.exact(fr[t:t + 1], lm, lam, want_grad=True)
+            row = 0
+        else:
+            y_idx = int(np.nonzero(flags[:t + 1])[0][-1])
+            r = oracle.close(np.stack([fr[y_idx], fr[t]]), lm, lam, eps, want_grad=True)
+            assert r["refreshed"][1] == 0
+            row = 1
+        sl = slice(t, t + 1)
+        assert d_err(res["msd"][sl], r["D"][row:row + 1], fr[sl], lm) < TOL[precision]
+        assert s_err(res["s"][sl], r["s"][row:row + 1], lm.shape[0]) < TOL[precision]
+        assert z_err(res["z"][sl], r["z"][row:row + 1], lam) < TOL[precision]
+        assert grad_err(res["dsdx"][sl], r["dsdx"][row:row + 1]) < GRAD_TOL[precision]
+        assert grad_err(res["dzdx"][sl], r["dzdx"][row:row + 1]) < GRAD_TOL[precision]
+
+
+def _check_refresh_sequence(flags, fr, eps):
+    """Each frame refreshes iff its exact MSD to the close structure in force exceeds eps."""
+    assert flags[0] == 2  # the initial assignment
+    y = fr[0]
+    for t in range(1, fr.shape[0]):
+        d = oracle.align(fr[t], y)["D"]
+        if bool(flags[t]) != (d > eps):
+            raise AssertionError(f"frame {t}: flag {flags[t]}, exact D(x_t, y) = {d!r} vs eps {eps}")
+        if flags[t]:
+            y = fr[t]
+
+
+def test_c2_full_size_close_with_gradients(pcv):
+    """N=300, M=200, F=100000 FP32, eps=0.05 nm^2, s/z with gradients: the benchmark's step."""
+    from paper_1801_02362_gb300 import synth
+
+    lm, fr = synth.make_problem(1, n_atoms=300, n_landmarks=200, n_frames=100_000, frame_noise=0.05)
+    fr = np.ascontiguousarray(fr, dtype=np.float32)
+    lam = 2.3 / oracle.mean_adjacent_msd(lm)
+    eps = 0.05
+    ctx = pcv.PathCV(lm, lam, eps=eps, precision="fp32")
+    out = ctx.evaluate(torch.from_numpy(fr).cuda(), grad=True, msd=True, refreshed=True)
+    ctx.sync()
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    ctx.close()
+    flags = res["refreshed"]
+    assert 2 <= int((flags > 0).sum()) < 1000  # long segments: the materialised tensor-core path
+    _check_refresh_sequence(flags, fr.astype(np.float64), eps)
+    rng = np.random.default_rng(5)
+    refreshed = np.nonzero(flags)[0]
+    ts = sorted(set(rng.integers(1, fr.shape[0], 10).tolist()) | {int(refreshed[-1]), fr.shape[0] - 1})
+    _check_frame_samples(res, fr, lm, lam, eps, ts)
+
+
+def test_c4_full_size_exact_gradients_sampled(pcv):
+    """N=1000, M=500, F=4096 FP32 exact mode with gradients; 6 frames checked in full."""
+    from paper_1801_02362_gb300 import synth
+
+    lm, fr = synth.make_problem(4, n_atoms=1000, n_landmarks=500, n_frames=4096, frame_noise=0.05)
+    fr = np.ascontiguousarray(fr, dtype=np.float32)
+    lam = 2.3 / oracle.mean_adjacent_msd(lm)
+    ctx = pcv.PathCV(lm, lam, eps=-1.0, precision="fp32")
+    out = ctx.evaluate(torch.from_numpy(fr).cuda(), grad=True, msd=True, refreshed=True)
+    ctx.sync()
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    ctx.close()
+    assert np.all(res["refreshed"] == 1)
+    ts = [0, 1, 1777, 2048, 3000, 4095]
+    for t in ts:
+        r = oracle.exact(fr[t:t + 1], lm, lam, want_grad=True)
+        sl = slice(t, t + 1)
+        assert d_err(res["msd"][sl], r["D"], fr[sl], lm) < TOL["fp32"]
+        assert s_err(res["s"][sl], r["s"], 500) < TOL["fp32"]
+        assert z_err(res["z"][sl], r["z"], lam) < TOL["fp32"]
+        assert grad_err(res["dsdx"][sl], r["dsdx"]) < GRAD_TOL["fp32"]
+        assert grad_err(res["dzdx"][sl], r["dzdx"]) < GRAD_TOL["fp32"]
