@@ -190,8 +190,9 @@ def time_config(pcv, label: str, seed: int, n: int, m: int, f: int, eps: float, 
 
     dt = torch.float64 if precision == "fp64" else torch.float32
     sdt = np.float64 if precision == "fp64" else np.float32
+    ldt = np.float16 if precision == "fp16" else sdt
     lm, fr = synth.make_problem(seed, n_atoms=n, n_landmarks=m, n_frames=f, frame_noise=noise, schedule=schedule,
-                                frame_dtype=sdt, landmark_dtype=sdt)
+                                frame_dtype=sdt, landmark_dtype=ldt)
     lam = lambda_from_gpu(pcv, lm)
     ctx = pcv.PathCV(lm, lam, eps=eps, precision=precision)
     frames = torch.tensor(np.ascontiguousarray(fr), dtype=dt, device="cuda")
@@ -218,6 +219,59 @@ def time_config(pcv, label: str, seed: int, n: int, m: int, f: int, eps: float, 
             "gradients": grad, "ms_per_step": t, "frames_per_s": f / (t / 1e3),
             "msds_per_s": f * m / (t / 1e3), "exact_msds": st["landmark_alignments"], "approx_msds": st["approx_msds"],
             "kernel_ms": {k: round(v[0] / steps, 4) for k, v in pr.items()}}
+
+
+def time_stream(pcv, precision: str, n: int = 5000, m: int = 2000, calls: int = 200, eps: float = 0.05,
+                seed: int = 5) -> dict:
+    """Per-MD-step use: close-structure evaluation fed one frame per call (no gradients).
+    Reports the time per call and, for the landmark-streaming kernels, bytes of landmarks
+    read per launch / the kernel's average launch time against the measured HBM peak."""
+    import torch
+    from paper_1801_02362_gb300 import synth
+
+    ldt = np.float16 if precision == "fp16" else np.float32
+    lm, fr = synth.make_problem(seed, n_atoms=n, n_landmarks=m, n_frames=10_000, frame_noise=0.05,
+                                landmark_dtype=ldt)
+    fr = torch.tensor(np.ascontiguousarray(fr[:calls + 8]), dtype=torch.float32, device="cuda")
+    lam = lambda_from_gpu(pcv, lm)
+    ctx = pcv.PathCV(lm, lam, eps=eps, precision=precision)
+    s = torch.empty(1, dtype=torch.float64, device="cuda")
+    z = torch.empty_like(s)
+    P = lambda t: t.data_ptr()
+    for t in range(8):  # warm-up calls
+        pcv.pcv_evaluate(ctx.ctx, 1, P(fr[t]), P(s), P(z), None, None, None, None)
+    torch.cuda.synchronize()
+    ctx.set_profiling(True)
+    ctx.profile()
+    st0 = ctx.stats()
+    stream = torch.cuda.current_stream()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for t in range(8, 8 + calls):
+        pcv.pcv_evaluate(ctx.ctx, 1, P(fr[t]), P(s), P(z), None, None, None, None)
+    b.record(stream)
+    torch.cuda.synchronize()
+    per_call_ms = a.elapsed_time(b) / calls
+    pr = ctx.profile()
+    st = ctx.stats()
+    ctx.close()
+    elem = 2 if precision == "fp16" else 4
+    set_bytes = m * n * 3 * elem
+    hbm = measured_peaks().get("hbm_gbs", 6793.8)
+    kern = {}
+    for name in ("exact_pair", "approx_pair"):
+        if name in pr and pr[name][1]:
+            ms, k = pr[name]
+            gbs = set_bytes / (ms / k / 1e3) / 1e9
+            kern[name] = {"launches": k, "ms_per_launch": ms / k, "landmark_GB_per_s": gbs,
+                          "frac_of_hbm_peak": gbs / hbm}
+    return {"workload": f"close-structure path CV one frame per call, N={n}, M={m}, {precision} landmark storage",
+            "landmark_set_MB": set_bytes / 1e6, "l2_resident": set_bytes < 126e6, "calls": calls,
+            "ms_per_call": per_call_ms, "frames_per_s": 1e3 / per_call_ms,
+            "refreshes": st["refreshes_threshold"] - st0["refreshes_threshold"],
+            "kernels": kern, "hbm_peak_GB_per_s": hbm,
+            "kernel_ms": {k: round(v[0] / calls, 4) for k, v in pr.items()}}
 
 
 def cpu_baseline(lm, fr, lam, eps, seconds: float) -> dict:
@@ -413,6 +467,16 @@ def run_ours(args):
                                                schedule="walk")
         details["c4_exact_grad"] = time_config(pcv, "exact path CV with gradients, FP32, N=1000, M=500, F=4096", 4,
                                                1000, 500, 4096, -1.0, True, "fp32")
+        for prec in ("fp32", "fp16"):
+            details[f"c5_stream_{prec}"] = time_stream(pcv, prec)
+        for prec in ("fp32", "fp16"):
+            details[f"c5_batched_{prec}"] = time_config(
+                pcv, f"close-structure path CV, N=5000, M=2000, F=10000, {prec} landmark storage", 5, 5000, 2000,
+                10_000, 0.05, False, prec, steps=1)
+        if "c5_stream_fp32" in details and "c5_stream_fp16" in details:
+            details["c5_fp16_vs_fp32_speedup"] = {
+                "stream_per_call": details["c5_stream_fp32"]["ms_per_call"] / details["c5_stream_fp16"]["ms_per_call"],
+                "batched_per_step": details["c5_batched_fp32"]["ms_per_step"] / details["c5_batched_fp16"]["ms_per_step"]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -753,6 +753,10 @@ void launch_exact_pairs(Prec p, int rows, const int* row_frame, const int* rows_
                         cudaStream_t st) {
   (void)rows_dev;
   if (rows <= 0) return;
+  if (p != P_F64 && rows <= STREAM_FRAMES && stream_fits(p, L.N)) {  // a few frames: one CTA per landmark
+    launch_exact_stream(p, rows, row_frame, frames, L, fi, D, Rout, status, st);
+    return;
+  }
   dim3 grid((L.M + EX_TM - 1) / EX_TM, (rows + EX_TF - 1) / EX_TF);
   switch (p) {
     case P_F64:
@@ -821,6 +825,10 @@ void launch_approx_pairs(Prec p, int max_rows, const int* approx_list, const int
                          const void* frames, const LandmarkDev& L, FrameInfo fi, const double4* qxy, const void* Bseg,
                          void* D, cudaStream_t st) {
   if (max_rows <= 0) return;
+  if (p != P_F64 && max_rows <= STREAM_FRAMES && stream_fits(p, L.N)) {  // a few frames: one CTA per landmark
+    launch_approx_stream(p, approx_list, approx_seg, count, frames, L, fi, qxy, Bseg, D, st);
+    return;
+  }
   if (approx_rm(L.M) == 5)
     approx_launch<5>(p, max_rows, approx_list, approx_seg, count, frames, L, fi, qxy, Bseg, D, st);
   else

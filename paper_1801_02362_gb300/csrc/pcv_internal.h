@@ -149,6 +149,17 @@ void launch_approx_pairs(Prec p, int max_rows, const int* approx_list, const int
                          const double4* qxy, const void* Bseg, void* D, cudaStream_t st);
 
 // ---------------------------------------------------------------------------------------
+// landmark-parallel kernels for up to STREAM_FRAMES frames per call (k_stream.cu; FP32
+// and FP16-storage modes; one CTA per landmark, the landmark staged in shared memory)
+constexpr int STREAM_FRAMES = 4;
+bool stream_fits(Prec p, int N);  // the staged landmark fits in shared memory
+void launch_exact_stream(Prec p, int rows, const int* row_frame, const void* frames, const LandmarkDev& L,
+                         FrameInfo fi, void* D, void* Rout, unsigned* status, cudaStream_t st);
+void launch_approx_stream(Prec p, const int* approx_list, const int* approx_seg, const int* count,
+                          const void* frames, const LandmarkDev& L, FrameInfo fi, const double4* qxy, const void* Bseg,
+                          void* D, cudaStream_t st);
+
+// ---------------------------------------------------------------------------------------
 // materialised-operand path (k_tile.cu; FP32 and FP16-storage modes, uniform weights).
 // Rows padded to round_up16(N) atoms; segment slots s = seg - seg_base in [0, ns).
 inline int round_up16(int n) { return (n + 15) & ~15; }
