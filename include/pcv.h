@@ -22,10 +22,18 @@
  *  - Precision modes fix the element types:
  *      PCV_FP64          frames double, landmarks double, all arithmetic FP64,
  *                        gradients double;
- *      PCV_FP32          frames float, landmarks float (centred), per-atom sums in
- *                        compensated FP32, 4x4 eigen-solve and MSD assembly in FP64,
+ *      PCV_FP32          frames float, landmarks float (centred); correlation sums in
+ *                        FP32, the 4x4 eigen-solve in FP32 for the rotation only, and the
+ *                        MSD summed directly as sum_j w_j |x_j - R a_j|^2 in compensated
+ *                        FP32 (it is stationary in R, so a rotation accurate to FP32 gives
+ *                        an MSD accurate to FP32); close-structure decisions within the
+ *                        FP32 rounding window of the threshold are re-checked in FP64;
  *                        gradients float;
- *      PCV_FP16_STORAGE  as PCV_FP32 but landmarks stored as centred FP16.
+ *      PCV_FP16_STORAGE  as PCV_FP32 but landmarks stored as FP16 residuals about an
+ *                        FP32 offset per landmark and block of 16 consecutive atoms (the
+ *                        block mean of the centred coordinates): 6 bytes per atom plus
+ *                        12 bytes per block, with the rounding error of a block's extent
+ *                        rather than of the whole structure's.
  *  - The library allocates its own device workspace (cudaMalloc, grow-only) on first
  *    use of a size; it is freed by pcv_destroy.
  */

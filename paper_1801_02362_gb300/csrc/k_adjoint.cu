@@ -41,7 +41,8 @@ constexpr int BP_TF = 32, BP_TJ = 64, BP_THREADS = 128;
 
 template <typename ST, typename LT>
 __global__ void __launch_bounds__(BP_THREADS)
-adjoint_beta_pair(int F, int M, int N, const LT* __restrict__ lm, const double* __restrict__ q,
+adjoint_beta_pair(int F, int M, int N, const LT* __restrict__ lm, const float* __restrict__ lmoff,
+                  const double* __restrict__ q,
                   const float* __restrict__ q32, const ST* __restrict__ P, const double* __restrict__ s, double lambda,
                   const ST* __restrict__ Rpair, const ST* __restrict__ Bseg, const int* __restrict__ seg_of_frame,
                   ST* __restrict__ gs, ST* __restrict__ gz) {
@@ -86,7 +87,7 @@ adjoint_beta_pair(int F, int M, int N, const LT* __restrict__ lm, const double* 
       const int ii = e / BP_TJ, jj = e - ii * BP_TJ;
       const int i = i0 + ii, j = j0 + jj;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) As[ii * 3 + c][jj] = (i < M && j < N) ? lm_at<ST>(lm + ((size_t)i * N + j) * 3 + c) : (ST)0;
+      for (int c = 0; c < 3; ++c) As[ii * 3 + c][jj] = (i < M && j < N) ? lm_coord<ST, LT>(lm, lmoff, N, i, j, c) : (ST)0;
     }
     __syncthreads();
 #pragma unroll 2
@@ -136,7 +137,8 @@ constexpr int BS_TF = 64, BS_TJ = 32, BS_KL = 16, BS_THREADS = 256;
 
 template <typename LT>
 __global__ void __launch_bounds__(BS_THREADS, 3)
-adjoint_beta_seg(int F, int M, int N, const LT* __restrict__ lm, const float* __restrict__ q32,
+adjoint_beta_seg(int F, int M, int N, const LT* __restrict__ lm, const float* __restrict__ lmoff,
+                 const float* __restrict__ q32,
                  const float* __restrict__ P, const double* __restrict__ s, float lambda,
                  const float* __restrict__ Bseg, const int* __restrict__ seg_of_frame, float* __restrict__ gs,
                  float* __restrict__ gz) {
@@ -184,8 +186,9 @@ adjoint_beta_seg(int F, int M, int N, const LT* __restrict__ lm, const float* __
         const int i = i0 + ii, j = j0 + jj;
         float b0 = 0.0f, b1 = 0.0f, b2 = 0.0f;
         if (i < M && j < N) {
-          const LT* src = lm + ((size_t)i * N + j) * 3;
-          const float a0 = lm_at<float>(src), a1 = lm_at<float>(src + 1), a2 = lm_at<float>(src + 2);
+          const float a0 = lm_coord<float, LT>(lm, lmoff, N, i, j, 0);
+          const float a1 = lm_coord<float, LT>(lm, lmoff, N, i, j, 1);
+          const float a2 = lm_coord<float, LT>(lm, lmoff, N, i, j, 2);
           const float* B = s_B[ii];
           b0 = B[0] * a0 + B[1] * a1 + B[2] * a2;
           b1 = B[3] * a0 + B[4] * a1 + B[5] * a2;
@@ -636,11 +639,11 @@ void launch_adjoint_beta(Prec p, int F, const LandmarkDev& L, const void* P, con
   if (seg_form && p != P_F64) {
     dim3 grid((L.N + BS_TJ - 1) / BS_TJ, (F + BS_TF - 1) / BS_TF);
     if (p == P_F32)
-      adjoint_beta_seg<float><<<grid, BS_THREADS, 0, st>>>(F, L.M, L.N, (const float*)L.coords, L.q32,
+      adjoint_beta_seg<float><<<grid, BS_THREADS, 0, st>>>(F, L.M, L.N, (const float*)L.coords, L.off, L.q32,
                                                            (const float*)P, s, (float)lambda, (const float*)Bseg,
                                                            seg_of_frame, (float*)gs, (float*)gz);
     else
-      adjoint_beta_seg<__half><<<grid, BS_THREADS, 0, st>>>(F, L.M, L.N, (const __half*)L.coords, L.q32,
+      adjoint_beta_seg<__half><<<grid, BS_THREADS, 0, st>>>(F, L.M, L.N, (const __half*)L.coords, L.off, L.q32,
                                                             (const float*)P, s, (float)lambda, (const float*)Bseg,
                                                             seg_of_frame, (float*)gs, (float*)gz);
     note_launch();
@@ -650,17 +653,17 @@ void launch_adjoint_beta(Prec p, int F, const LandmarkDev& L, const void* P, con
   switch (p) {
     case P_F64:
       adjoint_beta_pair<double, double><<<grid, BP_THREADS, 0, st>>>(
-          F, L.M, L.N, (const double*)L.coords, L.q, L.q32, (const double*)P, s, lambda, (const double*)Rpair,
+          F, L.M, L.N, (const double*)L.coords, nullptr, L.q, L.q32, (const double*)P, s, lambda, (const double*)Rpair,
           (const double*)Bseg, seg_of_frame, (double*)gs, (double*)gz);
       break;
     case P_F32:
       adjoint_beta_pair<float, float><<<grid, BP_THREADS, 0, st>>>(
-          F, L.M, L.N, (const float*)L.coords, L.q, L.q32, (const float*)P, s, lambda, (const float*)Rpair,
+          F, L.M, L.N, (const float*)L.coords, L.off, L.q, L.q32, (const float*)P, s, lambda, (const float*)Rpair,
           (const float*)Bseg, seg_of_frame, (float*)gs, (float*)gz);
       break;
     case P_F16:
       adjoint_beta_pair<float, __half><<<grid, BP_THREADS, 0, st>>>(
-          F, L.M, L.N, (const __half*)L.coords, L.q, L.q32, (const float*)P, s, lambda, (const float*)Rpair,
+          F, L.M, L.N, (const __half*)L.coords, L.off, L.q, L.q32, (const float*)P, s, lambda, (const float*)Rpair,
           (const float*)Bseg, seg_of_frame, (float*)gs, (float*)gz);
       break;
   }

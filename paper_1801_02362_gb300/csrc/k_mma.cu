@@ -181,7 +181,7 @@ __global__ void gamma_split_kernel(int F, int Fp, int M, int Kp, const float* __
 // segment 0, else the frame refresh_list[seg - 1].
 template <typename LT>
 __global__ void delta_split_kernel(int seg_base, int M, int N, int Kp, int BN, int NT, const LT* __restrict__ lm,
-                                   const float* __restrict__ Bseg, const float* __restrict__ frames,
+                                   const float* __restrict__ lmoff, const float* __restrict__ Bseg, const float* __restrict__ frames,
                                    const float4* __restrict__ c32, const int* __restrict__ refresh_list,
                                    const float* __restrict__ prior, float4 prior_c, float* __restrict__ B,
                                    float* __restrict__ Yc) {
@@ -205,8 +205,9 @@ __global__ void delta_split_kernel(int seg_base, int M, int N, int Kp, int BN, i
   const int ck = i / MM_KC, kk = i % MM_KC;
   for (int j = threadIdx.x; j < N; j += blockDim.x) {
     const float yv[3] = {y[3 * j] - c.x, y[3 * j + 1] - c.y, y[3 * j + 2] - c.z};
-    const LT* a = lm + ((size_t)i * N + j) * 3;
-    const float a0 = (float)a[0], a1 = (float)a[1], a2 = (float)a[2];
+    const float a0 = lm_coord<float, LT>(lm, lmoff, N, i, j, 0);
+    const float a1 = lm_coord<float, LT>(lm, lmoff, N, i, j, 1);
+    const float a2 = lm_coord<float, LT>(lm, lmoff, N, i, j, 2);
     const float d[3] = {(R[0] * a0 + R[1] * a1 + R[2] * a2) - yv[0], (R[3] * a0 + R[4] * a1 + R[5] * a2) - yv[1],
                         (R[6] * a0 + R[7] * a1 + R[8] * a2) - yv[2]};
 #pragma unroll
@@ -451,11 +452,11 @@ void launch_delta_split(Prec p, int seg_base, int nseg, const LandmarkDev& L, co
   const dim3 grid(L.M, nseg);
   if (p == P_F16)
     delta_split_kernel<__half><<<grid, 128, 0, st>>>(seg_base, L.M, L.N, sh.Kp, sh.BN, sh.NT, (const __half*)L.coords,
-                                                     Bseg, (const float*)frames, fi.c32, refresh_list,
+                                                     L.off, Bseg, (const float*)frames, fi.c32, refresh_list,
                                                      (const float*)prior.coords, prior.c32, B, Yc);
   else
     delta_split_kernel<float><<<grid, 128, 0, st>>>(seg_base, L.M, L.N, sh.Kp, sh.BN, sh.NT, (const float*)L.coords,
-                                                    Bseg, (const float*)frames, fi.c32, refresh_list,
+                                                    L.off, Bseg, (const float*)frames, fi.c32, refresh_list,
                                                     (const float*)prior.coords, prior.c32, B, Yc);
   note_launch();
 }

@@ -87,8 +87,9 @@ constexpr int EX_TF = 16, EX_TM = 32, EX_THREADS = 128;
 // 2: x sqrt(w_j)), landmarks (mode 2: a sqrt(w_j)).  Layout [jj*3 + c][row].
 template <typename FT, typename LT, typename ST, int TF, int TM, int KC, int PF, int PM>
 __device__ __forceinline__ void stage_exact(int j0, int N, int M, int i0, const FT* __restrict__ frames,
-                                            const LT* __restrict__ lm, const float* __restrict__ wts,
-                                            int wmode, const int* s_frame, const ST (*s_c)[3],
+                                            const LT* __restrict__ lm, const float* __restrict__ lmoff,
+                                            const float* __restrict__ wts, int wmode, const int* s_frame,
+                                            const ST (*s_c)[3],
                                             ST (*Xs)[PF], ST (*As)[PM]) {
   const int tid = threadIdx.x;
   for (int e = tid; e < TF * KC; e += EX_THREADS) {
@@ -117,10 +118,9 @@ __device__ __forceinline__ void stage_exact(int j0, int N, int M, int i0, const 
     const int j = j0 + jj, i = i0 + ll;
     ST v0 = 0, v1 = 0, v2 = 0;
     if (i < M && j < N) {
-      const LT* src = lm + ((size_t)i * N + j) * 3;
-      v0 = load_as<ST>(src);
-      v1 = load_as<ST>(src + 1);
-      v2 = load_as<ST>(src + 2);
+      v0 = lm_coord<ST, LT>(lm, lmoff, N, i, j, 0);
+      v1 = lm_coord<ST, LT>(lm, lmoff, N, i, j, 1);
+      v2 = lm_coord<ST, LT>(lm, lmoff, N, i, j, 2);
       if (wts && wmode == 2) {
         const ST sw = (ST)sqrt((double)wts[j]);
         v0 *= sw;
@@ -162,8 +162,9 @@ template <typename LT>
 __global__ void __launch_bounds__(EX_THREADS, 4)
 exact_pair_f32(int rows, const int* __restrict__ row_frame, const float* __restrict__ frames,
                const float4* __restrict__ c32, const double* __restrict__ fG, const LT* __restrict__ lm,
-               const double* __restrict__ lG, const float* __restrict__ wts, int M, int N, double dscale,
-               float* __restrict__ Dout, float* __restrict__ Rout, unsigned* __restrict__ status) {
+               const float* __restrict__ lmoff, const double* __restrict__ lG, const float* __restrict__ wts, int M,
+               int N, double dscale, float* __restrict__ Dout, float* __restrict__ Rout,
+               unsigned* __restrict__ status) {
   constexpr int TF = EX_TF, TM = EX_TM, KC = 32;
   constexpr int PF = TF + 2, PM = TM + 2;
   __shared__ __align__(16) float Xs[KC * 3][PF];
@@ -189,7 +190,7 @@ exact_pair_f32(int rows, const int* __restrict__ row_frame, const float* __restr
       for (int e = 0; e < 9; ++e) h[u][v][e] = 0.0f;
 
   for (int j0 = 0; j0 < N; j0 += KC) {
-    stage_exact<float, LT, float, TF, TM, KC, PF, PM>(j0, N, M, i0, frames, lm, wts, 1, s_frame, s_c, Xs, As);
+    stage_exact<float, LT, float, TF, TM, KC, PF, PM>(j0, N, M, i0, frames, lm, lmoff, wts, 1, s_frame, s_c, Xs, As);
     __syncthreads();
 #pragma unroll 4
     for (int jj = 0; jj < KC; ++jj) {
@@ -233,7 +234,7 @@ exact_pair_f32(int rows, const int* __restrict__ row_frame, const float* __restr
   float acc[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
   float thi[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}}, tlo[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
   for (int j0 = 0; j0 < N; j0 += KC) {
-    stage_exact<float, LT, float, TF, TM, KC, PF, PM>(j0, N, M, i0, frames, lm, wts, 2, s_frame, s_c, Xs, As);
+    stage_exact<float, LT, float, TF, TM, KC, PF, PM>(j0, N, M, i0, frames, lm, lmoff, wts, 2, s_frame, s_c, Xs, As);
     __syncthreads();
 #pragma unroll 4
     for (int jj = 0; jj < KC; ++jj) {
@@ -289,6 +290,7 @@ exact_pair_f64(int rows, const int* __restrict__ row_frame, const double* __rest
                const double4* __restrict__ c64, const double* __restrict__ fG, const double* __restrict__ lm,
                const double* __restrict__ lG, const float* __restrict__ wts, int M, int N, double dscale,
                double* __restrict__ Dout, double* __restrict__ Rout, unsigned* __restrict__ status) {
+  const float* lmoff = nullptr;  // FP64 storage has no block offsets
   constexpr int TF = EX_TF, TM = EX_TM, KC = 16;
   constexpr int PF = TF + 2, PM = TM + 2;
   __shared__ __align__(16) double Xs[KC * 3][PF];
@@ -312,7 +314,7 @@ exact_pair_f64(int rows, const int* __restrict__ row_frame, const double* __rest
 #pragma unroll
       for (int e = 0; e < 9; ++e) h[u][v][e] = 0.0;
   for (int j0 = 0; j0 < N; j0 += KC) {
-    stage_exact<double, double, double, TF, TM, KC, PF, PM>(j0, N, M, i0, frames, lm, wts, 1, s_frame, s_c, Xs, As);
+    stage_exact<double, double, double, TF, TM, KC, PF, PM>(j0, N, M, i0, frames, lm, lmoff, wts, 1, s_frame, s_c, Xs, As);
     __syncthreads();
 #pragma unroll 4
     for (int jj = 0; jj < KC; ++jj) {
@@ -372,7 +374,7 @@ __global__ void __launch_bounds__(AP_THREADS, 3)
 approx_pair_kernel(const int* __restrict__ alist, const int* __restrict__ aseg,
                    const int* __restrict__ acount, const FT* __restrict__ frames,
                    const float4* __restrict__ c32, const double4* __restrict__ c64,
-                   const double4* __restrict__ qxy, const LT* __restrict__ lm,
+                   const double4* __restrict__ qxy, const LT* __restrict__ lm, const float* __restrict__ lmoff,
                    const ST* __restrict__ Bseg, const float* __restrict__ wts, int M, int N,
                    double dscale, ST* __restrict__ Dout) {
   constexpr int TF = AP_TF, TM = 8 * RM, KC = sizeof(ST) == 8 ? AP_KC / 2 : AP_KC;
@@ -472,10 +474,9 @@ approx_pair_kernel(const int* __restrict__ alist, const int* __restrict__ aseg,
         const int ll = e / KC, jj = e - ll * KC;
         const int j = j0 + jj, i = i0 + ll;
         if (e < TM * KC && i < M && j < N) {
-          const LT* src = lm + ((size_t)i * N + j) * 3;
-          rl[r][0] = load_as<ST>(src);
-          rl[r][1] = load_as<ST>(src + 1);
-          rl[r][2] = load_as<ST>(src + 2);
+          rl[r][0] = lm_coord<ST, LT>(lm, lmoff, N, i, j, 0);
+          rl[r][1] = lm_coord<ST, LT>(lm, lmoff, N, i, j, 1);
+          rl[r][2] = lm_coord<ST, LT>(lm, lmoff, N, i, j, 2);
         } else {
           rl[r][0] = rl[r][1] = rl[r][2] = 0;
         }
@@ -601,8 +602,8 @@ template <typename LT, int RM>
 __global__ void __launch_bounds__(AQ_THREADS, 3)
 approx_pair_f32t(const int* __restrict__ alist, const int* __restrict__ aseg, const int* __restrict__ acount,
                  const float* __restrict__ frames, const float4* __restrict__ c32, const double4* __restrict__ qxy,
-                 const LT* __restrict__ lm, const float* __restrict__ Bseg, const float* __restrict__ wts, int M,
-                 int N, float dscale, float* __restrict__ Dout) {
+                 const LT* __restrict__ lm, const float* __restrict__ lmoff, const float* __restrict__ Bseg,
+                 const float* __restrict__ wts, int M, int N, float dscale, float* __restrict__ Dout) {
   constexpr int TF = AQ_TF, TM = 8 * RM, KC = AQ_KC;
   __shared__ __align__(16) float Xs[KC * 3][TF + 4];
   __shared__ __align__(16) float Bs[KC * 3][TM + 4];
@@ -683,8 +684,9 @@ approx_pair_f32t(const int* __restrict__ alist, const int* __restrict__ aseg, co
         const int j = j0 + jj, i = i0 + ll;
         float b0 = 0.0f, b1 = 0.0f, b2 = 0.0f;
         if (i < M && j < N) {
-          const LT* src = lm + ((size_t)i * N + j) * 3;
-          const float a0 = load_as<float>(src), a1 = load_as<float>(src + 1), a2 = load_as<float>(src + 2);
+          const float a0 = lm_coord<float, LT>(lm, lmoff, N, i, j, 0);
+          const float a1 = lm_coord<float, LT>(lm, lmoff, N, i, j, 1);
+          const float a2 = lm_coord<float, LT>(lm, lmoff, N, i, j, 2);
           const float* B = s_B[ll];
           const float sw = wts ? sqrtf(wts[j]) : 1.0f;
           b0 = (B[0] * a0 + B[1] * a1 + B[2] * a2) * sw;
@@ -766,12 +768,14 @@ void launch_exact_pairs(Prec p, int rows, const int* row_frame, const int* rows_
       break;
     case P_F32:
       exact_pair_f32<float><<<grid, EX_THREADS, 0, st>>>(rows, row_frame, (const float*)frames, fi.c32, fi.G,
-                                                         (const float*)L.coords, L.G, L.w, L.M, L.N, L.dscale,
+                                                         (const float*)L.coords, L.off, L.G, L.w, L.M, L.N,
+                                                         L.dscale,
                                                          (float*)D, (float*)Rout, status); note_launch();
       break;
     case P_F16:
       exact_pair_f32<__half><<<grid, EX_THREADS, 0, st>>>(rows, row_frame, (const float*)frames, fi.c32, fi.G,
-                                                          (const __half*)L.coords, L.G, L.w, L.M, L.N, L.dscale,
+                                                          (const __half*)L.coords, L.off, L.G, L.w, L.M, L.N,
+                                                          L.dscale,
                                                           (float*)D, (float*)Rout, status); note_launch();
       break;
   }
@@ -792,11 +796,13 @@ static void approx_launch(Prec p, int max_rows, const int* approx_list, const in
     dim3 gq((L.M + 8 * RM - 1) / (8 * RM), (max_rows + AQ_TF - 1) / AQ_TF);
     if (p == P_F32)
       approx_pair_f32t<float, RM><<<gq, AQ_THREADS, 0, st>>>(approx_list, approx_seg, count, (const float*)frames,
-                                                             fi.c32, qxy, (const float*)L.coords, (const float*)Bseg,
+                                                             fi.c32, qxy, (const float*)L.coords, L.off,
+                                                             (const float*)Bseg,
                                                              L.w, L.M, L.N, (float)L.dscale, (float*)D);
     else
       approx_pair_f32t<__half, RM><<<gq, AQ_THREADS, 0, st>>>(approx_list, approx_seg, count, (const float*)frames,
-                                                              fi.c32, qxy, (const __half*)L.coords, (const float*)Bseg,
+                                                              fi.c32, qxy, (const __half*)L.coords, L.off,
+                                                              (const float*)Bseg,
                                                               L.w, L.M, L.N, (float)L.dscale, (float*)D);
     note_launch();
     return;
@@ -805,17 +811,17 @@ static void approx_launch(Prec p, int max_rows, const int* approx_list, const in
     case P_F64:
       approx_pair_kernel<double, double, double, RM><<<grid, AP_THREADS, 0, st>>>(
           approx_list, approx_seg, count, (const double*)frames, fi.c32, fi.c64, qxy, (const double*)L.coords,
-          (const double*)Bseg, L.w, L.M, L.N, L.dscale, (double*)D);
+          nullptr, (const double*)Bseg, L.w, L.M, L.N, L.dscale, (double*)D);
       break;
     case P_F32:
       approx_pair_kernel<float, float, float, RM><<<grid, AP_THREADS, 0, st>>>(
           approx_list, approx_seg, count, (const float*)frames, fi.c32, fi.c64, qxy, (const float*)L.coords,
-          (const float*)Bseg, L.w, L.M, L.N, L.dscale, (float*)D);
+          L.off, (const float*)Bseg, L.w, L.M, L.N, L.dscale, (float*)D);
       break;
     case P_F16:
       approx_pair_kernel<float, __half, float, RM><<<grid, AP_THREADS, 0, st>>>(
           approx_list, approx_seg, count, (const float*)frames, fi.c32, fi.c64, qxy, (const __half*)L.coords,
-          (const float*)Bseg, L.w, L.M, L.N, L.dscale, (float*)D);
+          L.off, (const float*)Bseg, L.w, L.M, L.N, L.dscale, (float*)D);
       break;
   }
   note_launch();

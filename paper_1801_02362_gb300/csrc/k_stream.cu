@@ -74,7 +74,7 @@ template <typename LT>
 __global__ void __launch_bounds__(ST_THREADS)
 exact_stream_f32(int rows, const int* __restrict__ row_frame, const float* __restrict__ frames,
                  const float4* __restrict__ c32, const double* __restrict__ fG, const LT* __restrict__ lm,
-                 const double* __restrict__ lG, const float* __restrict__ wts, int M, int N, double dscale,
+                 const float* __restrict__ lmoff, const double* __restrict__ lG, const float* __restrict__ wts, int M, int N, double dscale,
                  bool aligned, float* __restrict__ Dout, float* __restrict__ Rout, unsigned* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char stream_sm[];
   LT* As = reinterpret_cast<LT*>(stream_sm);
@@ -99,7 +99,9 @@ exact_stream_f32(int rows, const int* __restrict__ row_frame, const float* __res
 #pragma unroll
   for (int e = 0; e < K; ++e) h[e] = 0.0f;
   for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    const float a[3] = {ldf(As + 3 * j), ldf(As + 3 * j + 1), ldf(As + 3 * j + 2)};
+    const float a[3] = {lm_plus_off<LT>(ldf(As + 3 * j), lmoff, N, i, j, 0),
+                        lm_plus_off<LT>(ldf(As + 3 * j + 1), lmoff, N, i, j, 1),
+                        lm_plus_off<LT>(ldf(As + 3 * j + 2), lmoff, N, i, j, 2)};
     const float wj = wts ? wts[j] : 1.0f;
 #pragma unroll
     for (int r = 0; r < STREAM_FRAMES; ++r) {
@@ -131,7 +133,9 @@ exact_stream_f32(int rows, const int* __restrict__ row_frame, const float* __res
   for (int r = 0; r < STREAM_FRAMES; ++r) acc[r] = thi[r] = tlo[r] = 0.0f;
   int cnt = 0;
   for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    const float a[3] = {ldf(As + 3 * j), ldf(As + 3 * j + 1), ldf(As + 3 * j + 2)};
+    const float a[3] = {lm_plus_off<LT>(ldf(As + 3 * j), lmoff, N, i, j, 0),
+                        lm_plus_off<LT>(ldf(As + 3 * j + 1), lmoff, N, i, j, 1),
+                        lm_plus_off<LT>(ldf(As + 3 * j + 2), lmoff, N, i, j, 2)};
     const float wj = wts ? wts[j] : 1.0f;
 #pragma unroll
     for (int r = 0; r < STREAM_FRAMES; ++r) {
@@ -175,7 +179,8 @@ template <typename LT>
 __global__ void __launch_bounds__(ST_THREADS)
 approx_stream_f32(const int* __restrict__ alist, const int* __restrict__ aseg, const int* __restrict__ acount,
                   const float* __restrict__ frames, const float4* __restrict__ c32, const double4* __restrict__ qxy,
-                  const LT* __restrict__ lm, const float* __restrict__ Bseg, const float* __restrict__ wts, int M,
+                  const LT* __restrict__ lm, const float* __restrict__ lmoff, const float* __restrict__ Bseg,
+                  const float* __restrict__ wts, int M,
                   int N, double dscale, bool aligned, float* __restrict__ Dout) {
   extern __shared__ __align__(16) unsigned char stream_sm[];
   LT* As = reinterpret_cast<LT*>(stream_sm);
@@ -218,7 +223,9 @@ approx_stream_f32(const int* __restrict__ alist, const int* __restrict__ aseg, c
   for (int r = 0; r < STREAM_FRAMES; ++r) acc[r] = thi[r] = tlo[r] = 0.0f;
   int cnt = 0;
   for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    const float a[3] = {ldf(As + 3 * j), ldf(As + 3 * j + 1), ldf(As + 3 * j + 2)};
+    const float a[3] = {lm_plus_off<LT>(ldf(As + 3 * j), lmoff, N, i, j, 0),
+                        lm_plus_off<LT>(ldf(As + 3 * j + 1), lmoff, N, i, j, 1),
+                        lm_plus_off<LT>(ldf(As + 3 * j + 2), lmoff, N, i, j, 2)};
     const float wj = wts ? wts[j] : 1.0f;
 #pragma unroll
     for (int r = 0; r < STREAM_FRAMES; ++r) {
@@ -277,12 +284,12 @@ void launch_exact_stream(Prec p, int rows, const int* row_frame, const void* fra
   if (p == P_F16) {
     allow_smem(exact_stream_f32<__half>, smem);
     exact_stream_f32<__half><<<L.M, ST_THREADS, smem, st>>>(rows, row_frame, (const float*)frames, fi.c32, fi.G,
-                                                            (const __half*)L.coords, L.G, L.w, L.M, L.N, L.dscale,
+                                                            (const __half*)L.coords, L.off, L.G, L.w, L.M, L.N, L.dscale,
                                                             aligned, (float*)D, (float*)Rout, status);
   } else {
     allow_smem(exact_stream_f32<float>, smem);
     exact_stream_f32<float><<<L.M, ST_THREADS, smem, st>>>(rows, row_frame, (const float*)frames, fi.c32, fi.G,
-                                                           (const float*)L.coords, L.G, L.w, L.M, L.N, L.dscale,
+                                                           (const float*)L.coords, L.off, L.G, L.w, L.M, L.N, L.dscale,
                                                            aligned, (float*)D, (float*)Rout, status);
   }
   note_launch();
@@ -298,13 +305,13 @@ void launch_approx_stream(Prec p, const int* approx_list, const int* approx_seg,
   if (p == P_F16) {
     allow_smem(approx_stream_f32<__half>, smem);
     approx_stream_f32<__half><<<L.M, ST_THREADS, smem, st>>>(approx_list, approx_seg, count, (const float*)frames,
-                                                             fi.c32, qxy, (const __half*)L.coords,
+                                                             fi.c32, qxy, (const __half*)L.coords, L.off,
                                                              (const float*)Bseg, L.w, L.M, L.N, L.dscale, aligned,
                                                              (float*)D);
   } else {
     allow_smem(approx_stream_f32<float>, smem);
     approx_stream_f32<float><<<L.M, ST_THREADS, smem, st>>>(approx_list, approx_seg, count, (const float*)frames,
-                                                            fi.c32, qxy, (const float*)L.coords, (const float*)Bseg,
+                                                            fi.c32, qxy, (const float*)L.coords, L.off, (const float*)Bseg,
                                                             L.w, L.M, L.N, L.dscale, aligned, (float*)D);
   }
   note_launch();

@@ -81,7 +81,7 @@ __device__ __forceinline__ const float* seg_structure(int seg, const float* fram
 // atoms in Bm, |d_{s,i}|^2 in Nb[s * M + i]; block i == 0 also writes y'(s) to Yc[s].
 template <typename LT>
 __global__ void materialize_landmarks_kernel(int s0, int M, int N, int N16, const LT* __restrict__ lm,
-                                             const float* __restrict__ Bseg, const float* __restrict__ frames,
+                                             const float* __restrict__ lmoff, const float* __restrict__ Bseg, const float* __restrict__ frames,
                                              const float4* __restrict__ c32, const int* __restrict__ refresh_list,
                                              const float* __restrict__ prior, float4 prior_c, float* __restrict__ Bm,
                                              float* __restrict__ Nb, float* __restrict__ Yc) {
@@ -100,7 +100,9 @@ __global__ void materialize_landmarks_kernel(int s0, int M, int N, int N16, cons
   for (int j = threadIdx.x; j < N16; j += blockDim.x) {
     float o0 = 0.0f, o1 = 0.0f, o2 = 0.0f;
     if (j < N) {
-      const float a0 = lm_f(a + 3 * j), a1 = lm_f(a + 3 * j + 1), a2 = lm_f(a + 3 * j + 2);
+      const float a0 = lm_coord<float, LT>(lm, lmoff, N, i, j, 0);
+      const float a1 = lm_coord<float, LT>(lm, lmoff, N, i, j, 1);
+      const float a2 = lm_coord<float, LT>(lm, lmoff, N, i, j, 2);
       const float y0 = y[3 * j] - c.x, y1 = y[3 * j + 1] - c.y, y2 = y[3 * j + 2] - c.z;
       o0 = (R[0] * a0 + R[1] * a1 + R[2] * a2) - y0;
       o1 = (R[3] * a0 + R[4] * a1 + R[5] * a2) - y1;
@@ -492,11 +494,11 @@ void launch_materialize_landmarks(Prec p, int s0, int ns, const LandmarkDev& L, 
   const dim3 grid(L.M, ns);
   const int N16 = round_up16(L.N);
   if (p == P_F16)
-    materialize_landmarks_kernel<__half><<<grid, 128, 0, st>>>(s0, L.M, L.N, N16, (const __half*)L.coords, Bseg,
+    materialize_landmarks_kernel<__half><<<grid, 128, 0, st>>>(s0, L.M, L.N, N16, (const __half*)L.coords, L.off, Bseg,
                                                                (const float*)frames, fi.c32, refresh_list,
                                                                (const float*)prior.coords, prior.c32, Bm, Nb, Yc);
   else
-    materialize_landmarks_kernel<float><<<grid, 128, 0, st>>>(s0, L.M, L.N, N16, (const float*)L.coords, Bseg,
+    materialize_landmarks_kernel<float><<<grid, 128, 0, st>>>(s0, L.M, L.N, N16, (const float*)L.coords, L.off, Bseg,
                                                               (const float*)frames, fi.c32, refresh_list,
                                                               (const float*)prior.coords, prior.c32, Bm, Nb, Yc);
   note_launch();

@@ -82,7 +82,7 @@ struct pcv_ctx {
   bool have_lm = false;
   bool uniform = true;
   double dscale = 1.0;
-  DevBuf lm, lmG, lmA, lmA32, lmq, lmq32, w32, w64;
+  DevBuf lm, lmoff, lmG, lmA, lmA32, lmq, lmq32, w32, w64;
   double lambda = 0.0;
   bool have_lambda = false;
   double eps = -1.0;
@@ -213,6 +213,7 @@ LandmarkDev lm_view(const pcv_ctx* c) {
   L.w = c->uniform ? nullptr : (const float*)c->w32.p;
   L.w64 = c->uniform ? nullptr : (const double*)c->w64.p;
   L.dscale = c->dscale;
+  L.off = c->prec == P_F16 ? (const float*)c->lmoff.p : nullptr;
   return L;
 }
 
@@ -274,7 +275,7 @@ pcv_status pcv_destroy(pcv_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
-  DevBuf* bufs[] = {&c->lm, &c->lmG, &c->lmA, &c->lmA32, &c->lmq, &c->lmq32, &c->w32, &c->w64, &c->y, &c->Bprior, &c->c32, &c->c64,
+  DevBuf* bufs[] = {&c->lm, &c->lmoff, &c->lmG, &c->lmA, &c->lmA32, &c->lmq, &c->lmq32, &c->w32, &c->w64, &c->y, &c->Bprior, &c->c32, &c->c64,
                     &c->fG, &c->bandD, &c->bandQ, &c->bandF, &c->chD, &c->chQ, &c->chF, &c->rlist, &c->rcount,
                     &c->recF, &c->recRef, &c->recD, &c->recQ, &c->reflist, &c->segof, &c->alist, &c->aseg,
                     &c->Dbuf, &c->Rpair, &c->Bseg, &c->Xr, &c->Bm, &c->GSb, &c->GZb, &c->Nx, &c->Nb, &c->Yc, &c->Gsum, &c->Amma, &c->Bmma, &c->S6, &c->mstat, &c->status, &c->nrecheck, &c->small, &c->h_frames,
@@ -385,6 +386,10 @@ pcv_status pcv_set_landmarks(pcv_ctx* c, int M, int N, const double* coords, con
   const Prec p = c->prec;
   std::vector<double> G(M), A((size_t)M * 6);
   std::vector<unsigned char> store((size_t)M * n3 * store_elem(p));
+  // FP16 storage: per block of 16 atoms an FP32 offset (the block mean of the centred
+  // coordinates) and FP16 residuals; the device reads offset + residual in FP32
+  const int NB = (N + 15) / 16;
+  std::vector<float> off(p == P_F16 ? (size_t)M * NB * 3 : 0);
   std::vector<float> w32(N);
   for (int j = 0; j < N; ++j) w32[j] = (float)wn[j];
   for (int i = 0; i < M; ++i) {
@@ -393,6 +398,15 @@ pcv_status pcv_set_landmarks(pcv_ctx* c, int M, int N, const double* coords, con
     for (int j = 0; j < N; ++j)
       for (int k = 0; k < 3; ++k) cen[k] += wn[j] * a[3 * j + k];
     double g = 0.0, Ai[6] = {0, 0, 0, 0, 0, 0};
+    if (p == P_F16) {
+      for (int b = 0; b < NB; ++b) {
+        double m3[3] = {0, 0, 0};
+        const int j1 = std::min(N, 16 * b + 16);
+        for (int j = 16 * b; j < j1; ++j)
+          for (int k = 0; k < 3; ++k) m3[k] += a[3 * j + k] - cen[k];
+        for (int k = 0; k < 3; ++k) off[((size_t)i * NB + b) * 3 + k] = (float)(m3[k] / (j1 - 16 * b));
+      }
+    }
     for (int j = 0; j < N; ++j) {
       double v[3];
       for (int k = 0; k < 3; ++k) {
@@ -406,9 +420,10 @@ pcv_status pcv_set_landmarks(pcv_ctx* c, int M, int N, const double* coords, con
           ((float*)store.data())[idx] = f;
           v[k] = f;
         } else {
-          const __half h = __float2half_rn((float)cv);
+          const float o = off[((size_t)i * NB + j / 16) * 3 + k];
+          const __half h = __float2half_rn((float)(cv - (double)o));
           ((__half*)store.data())[idx] = h;
-          v[k] = (double)__half2float(h);
+          v[k] = (double)(__half2float(h) + o);  // the device's FP32 reconstruction
         }
       }
       const double wk = uniform ? 1.0 : (p == P_F64 ? wn[j] : (double)w32[j]);
@@ -426,6 +441,7 @@ pcv_status pcv_set_landmarks(pcv_ctx* c, int M, int N, const double* coords, con
   cudaSetDevice(c->device);
   pcv_status st;
   if ((st = ensure(c, c->lm, store.size())) != PCV_OK) return st;
+  if (p == P_F16 && (st = ensure(c, c->lmoff, sizeof(float) * off.size())) != PCV_OK) return st;
   if ((st = ensure(c, c->lmG, sizeof(double) * M)) != PCV_OK) return st;
   if ((st = ensure(c, c->lmA, sizeof(double) * 6 * M)) != PCV_OK) return st;
   if ((st = ensure(c, c->lmA32, sizeof(float) * 6 * M)) != PCV_OK) return st;
@@ -435,6 +451,8 @@ pcv_status pcv_set_landmarks(pcv_ctx* c, int M, int N, const double* coords, con
   if ((st = ensure(c, c->w64, sizeof(double) * N)) != PCV_OK) return st;
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   CUDA_TRY(c, cudaMemcpy(c->lm.p, store.data(), store.size(), cudaMemcpyHostToDevice));
+  if (p == P_F16)
+    CUDA_TRY(c, cudaMemcpy(c->lmoff.p, off.data(), sizeof(float) * off.size(), cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(c->lmG.p, G.data(), sizeof(double) * M, cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(c->lmA.p, A.data(), sizeof(double) * 6 * M, cudaMemcpyHostToDevice));
   std::vector<float> A32(A.begin(), A.end());

@@ -59,6 +59,34 @@ __device__ __forceinline__ float warp_sum_float(float v) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Landmark coordinate (i, j, c) in the working type: the stored value, plus the FP32 block
+// offset in FP16 storage (blocks of 16 atoms; off holds M*ceil(N/16)*3 floats).
+template <typename ST, typename LT>
+__device__ __forceinline__ ST lm_coord(const LT* lm, const float* off, int N, size_t i, int j, int c) {
+  (void)off;
+  return (ST)lm[(i * N + j) * 3 + c];
+}
+template <>
+__device__ __forceinline__ float lm_coord<float, __half>(const __half* lm, const float* off, int N, size_t i, int j,
+                                                        int c) {
+  return __half2float(lm[(i * N + j) * 3 + c]) + off[(i * ((N + 15) >> 4) + (j >> 4)) * 3 + c];
+}
+// the same for a value already read (e.g. from a shared-memory copy of the landmark)
+template <typename LT>
+__device__ __forceinline__ float lm_plus_off(float v, const float* off, int N, size_t i, int j, int c) {
+  (void)off;
+  (void)N;
+  (void)i;
+  (void)j;
+  (void)c;
+  return v;
+}
+template <>
+__device__ __forceinline__ float lm_plus_off<__half>(float v, const float* off, int N, size_t i, int j, int c) {
+  return v + off[(i * ((N + 15) >> 4) + (j >> 4)) * 3 + c];
+}
+
+// ---------------------------------------------------------------------------------------
 // Packed FP32 pairs (Blackwell f32x2 instructions): one instruction performs two IEEE FP32
 // operations with round-to-nearest, bit-identical to two scalar ones, at half the issue
 // cost.  A pair lives in a 64-bit register pair: low half = first element.

@@ -26,7 +26,12 @@ struct LandmarkDev {
   const float* w = nullptr;      // N: true weights (normalised), or nullptr when uniform
   const double* w64 = nullptr;   // N: the same weights in FP64, or nullptr when uniform
   double dscale = 1.0;           // kernel units -> true: 1/N for uniform weights, else 1
+  const float* off = nullptr;    // FP16 storage: M*ceil(N/16)*3 block offsets (else nullptr)
 };
+// FP16 storage keeps, per landmark and block of 16 consecutive atoms, an FP32 offset (the
+// block's mean centred coordinate) and the FP16 residuals: coordinate = offset + residual
+// (see lm_coord).  Residuals span a block (~1 nm), not the structure, so the rounding error
+// stays far below what a single centroid shift would give for large structures.
 // "Kernel units": with uniform weights the kernels sum unweighted products and the
 // results are scaled by dscale = 1/N in FP64 at the end; with explicit weights the
 // weights are applied inside the sums and dscale = 1.
