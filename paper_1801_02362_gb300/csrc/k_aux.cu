@@ -73,6 +73,65 @@ __global__ void frame_prep_f32(int F, int N, const float* __restrict__ frames,
   }
 }
 
+// The same per frame with one 256-thread block per frame, for a few large frames (the
+// per-step case): warp sums, then the 8 warps' compensated pairs combined in shared memory.
+__device__ __forceinline__ void block_sum_pair(float& hi, float& lo, float (*sh)[2]) {
+  warp_sum_pair(hi, lo);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    sh[w][0] = hi;
+    sh[w][1] = lo;
+  }
+  __syncthreads();
+  hi = 0.0f;
+  lo = 0.0f;
+  for (int k = 0; k < nw; ++k) two_sum_pair(hi, lo, sh[k][0], sh[k][1]);
+}
+
+__global__ void frame_prep_f32_block(int F, int N, const float* __restrict__ frames, const float* __restrict__ wts,
+                                     float4* __restrict__ c32, double* __restrict__ G) {
+  __shared__ float sh[32][2];
+  const int f = blockIdx.x;
+  const float* x = frames + (size_t)f * N * 3;
+  float cf[3];
+  const float invn = 1.0f / (float)N;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float hi = 0.0f, lo = 0.0f;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+      const float v = x[3 * j + k];
+      if (wts) {
+        const float p = wts[j] * v;
+        const float e = fmaf(wts[j], v, -p);
+        two_sum_acc(hi, lo, p);
+        lo += e;
+      } else {
+        two_sum_acc(hi, lo, v);
+      }
+    }
+    block_sum_pair(hi, lo, sh);
+    cf[k] = wts ? hi + lo : (hi + lo) * invn;
+  }
+  float gh = 0.0f, gl = 0.0f;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float v = x[3 * j + k] - cf[k];
+      const float vw = wts ? v * wts[j] : v;
+      const float p = vw * v;
+      const float e = fmaf(vw, v, -p);
+      two_sum_acc(gh, gl, p);
+      gl += e;
+    }
+  }
+  block_sum_pair(gh, gl, sh);
+  if (threadIdx.x == 0) {
+    c32[f] = make_float4(cf[0], cf[1], cf[2], 0.0f);
+    G[f] = pair_to_double(gh, gl);
+  }
+}
+
 __global__ void frame_prep_f64(int F, int N, const double* __restrict__ frames,
                                const double* __restrict__ w64, float4* __restrict__ c32,
                                double4* __restrict__ c64, double* __restrict__ G) {
@@ -751,9 +810,12 @@ void launch_frame_prep(Prec p, int F, const void* frames, const LandmarkDev& L, 
   if (p == P_F64)
     frame_prep_f64<<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(F, L.N, (const double*)frames, L.w64, fi.c32,
                                                             fi.c64, fi.G);
+  else if (F <= 1216 && L.N >= 256)  // few large frames: one block per frame
+    frame_prep_f32_block<<<F, 256, 0, st>>>(F, L.N, (const float*)frames, L.w, fi.c32, fi.G);
   else
     frame_prep_f32<<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(F, L.N, (const float*)frames, L.w, fi.c32, fi.c64,
-                                                            fi.G); note_launch();
+                                                            fi.G);
+  note_launch();
 }
 
 void launch_align_band(Prec p, int F, int W, int t_lo, int t_hi, const void* frames, const LandmarkDev& L,

@@ -832,7 +832,7 @@ void launch_approx_pairs(Prec p, int max_rows, const int* approx_list, const int
                          void* D, cudaStream_t st) {
   if (max_rows <= 0) return;
   if (p != P_F64 && max_rows <= STREAM_FRAMES && stream_fits(p, L.N)) {  // a few frames: one CTA per landmark
-    launch_approx_stream(p, approx_list, approx_seg, count, frames, L, fi, qxy, Bseg, D, st);
+    launch_approx_stream(p, max_rows, approx_list, approx_seg, count, frames, L, fi, qxy, Bseg, D, st);
     return;
   }
   if (approx_rm(L.M) == 5)

@@ -262,6 +262,121 @@ approx_stream_f32(const int* __restrict__ alist, const int* __restrict__ aseg, c
   }
 }
 
+// One frame (the per-step case): LPB landmarks per CTA, atoms in groups of APG (4 in FP32,
+// 8 in FP16 storage) read as three 16-byte vectors of each landmark and of the frame; the
+// frame is rotated once per group and serves the CTA's LPB landmarks.  No shared-memory
+// staging, so many CTAs per SM keep enough loads in flight to stream the landmark set at
+// the memory's rate.  Requires 16-byte aligned rows (N a multiple of APG).
+template <typename LT, int LPB>
+__global__ void __launch_bounds__(ST_THREADS)
+approx_stream_vec(const int* __restrict__ alist, const int* __restrict__ aseg, const int* __restrict__ acount,
+                  const float* __restrict__ frames, const float4* __restrict__ c32, const double4* __restrict__ qxy,
+                  const LT* __restrict__ lm, const float* __restrict__ lmoff, const float* __restrict__ Bseg,
+                  const float* __restrict__ wts, int M, int N, double dscale, float* __restrict__ Dout) {
+  constexpr int APG = sizeof(LT) == 2 ? 8 : 4;
+  __shared__ float red[ST_THREADS / 32][LPB];
+  if (*acount < 1) return;  // uniform over the grid
+  const int f = alist[0], seg = aseg[0];
+  const int i0 = blockIdx.x * LPB;
+  float R[9];
+  {
+    const double4 qq = qxy[f];
+    const float q[4] = {(float)qq.x, (float)qq.y, (float)qq.z, (float)qq.w};
+    quat_to_rot(q, R);
+  }
+  const float4 c = c32[f];
+  float B[LPB][9];
+#pragma unroll
+  for (int l = 0; l < LPB; ++l)
+#pragma unroll
+    for (int e = 0; e < 9; ++e) B[l][e] = i0 + l < M ? Bseg[((size_t)seg * M + i0 + l) * 9 + e] : 0.0f;
+  float acc[LPB];
+#pragma unroll
+  for (int l = 0; l < LPB; ++l) acc[l] = 0.0f;
+  const int ngroups = N / APG;
+  const float* xf = frames + (size_t)f * N * 3;
+  for (int g = threadIdx.x; g < ngroups; g += blockDim.x) {
+    const int j0 = g * APG;
+    float xr[APG][3];
+    {
+      const float4* xv = reinterpret_cast<const float4*>(xf + (size_t)j0 * 3);
+      float xs[APG * 3];
+#pragma unroll
+      for (int q = 0; q < APG * 3 / 4; ++q) {
+        const float4 t = xv[q];
+        xs[4 * q] = t.x;
+        xs[4 * q + 1] = t.y;
+        xs[4 * q + 2] = t.z;
+        xs[4 * q + 3] = t.w;
+      }
+#pragma unroll
+      for (int a = 0; a < APG; ++a) {
+        const float v0 = xs[3 * a] - c.x, v1 = xs[3 * a + 1] - c.y, v2 = xs[3 * a + 2] - c.z;
+        xr[a][0] = R[0] * v0 + R[3] * v1 + R[6] * v2;
+        xr[a][1] = R[1] * v0 + R[4] * v1 + R[7] * v2;
+        xr[a][2] = R[2] * v0 + R[5] * v1 + R[8] * v2;
+      }
+    }
+    float wv[APG];
+#pragma unroll
+    for (int a = 0; a < APG; ++a) wv[a] = wts ? wts[j0 + a] : 1.0f;
+#pragma unroll
+    for (int l = 0; l < LPB; ++l) {
+      const int i = i0 + l;
+      if (i >= M) break;
+      float av[APG * 3];
+      const uint4* src = reinterpret_cast<const uint4*>(lm + ((size_t)i * N + j0) * 3);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const uint4 t = src[q];
+        const unsigned u[4] = {t.x, t.y, t.z, t.w};
+        if (sizeof(LT) == 2) {
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const __half2 hh = *reinterpret_cast<const __half2*>(&u[h]);
+            const float2 ff = __half22float2(hh);
+            av[8 * q + 2 * h] = ff.x;
+            av[8 * q + 2 * h + 1] = ff.y;
+          }
+        } else {
+#pragma unroll
+          for (int h = 0; h < 4; ++h) av[4 * q + h] = __uint_as_float(u[h]);
+        }
+      }
+      float o[3] = {0.0f, 0.0f, 0.0f};
+      if (sizeof(LT) == 2) {  // one 16-atom block offset serves the group of 8
+        const float* op = lmoff + ((size_t)i * ((N + 15) >> 4) + (j0 >> 4)) * 3;
+        o[0] = op[0];
+        o[1] = op[1];
+        o[2] = op[2];
+      }
+      const float* Bl = B[l];
+      float t = acc[l];
+#pragma unroll
+      for (int a = 0; a < APG; ++a) {
+        const float a0 = av[3 * a] + o[0], a1 = av[3 * a + 1] + o[1], a2 = av[3 * a + 2] + o[2];
+        const float d0 = xr[a][0] - (Bl[0] * a0 + Bl[1] * a1 + Bl[2] * a2);
+        const float d1 = xr[a][1] - (Bl[3] * a0 + Bl[4] * a1 + Bl[5] * a2);
+        const float d2 = xr[a][2] - (Bl[6] * a0 + Bl[7] * a1 + Bl[8] * a2);
+        t = fmaf(wv[a] * d0, d0, fmaf(wv[a] * d1, d1, fmaf(wv[a] * d2, d2, t)));
+      }
+      acc[l] = t;
+    }
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int l = 0; l < LPB; ++l) {
+    const float t = warp_sum_float(acc[l]);
+    if (lane == 0) red[w][l] = t;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < LPB && i0 + (int)threadIdx.x < M) {
+    float t = 0.0f;
+    for (int k = 0; k < ST_THREADS / 32; ++k) t += red[k][threadIdx.x];
+    Dout[(size_t)f * M + i0 + threadIdx.x] = t * (float)dscale;
+  }
+}
+
 template <typename K>
 void allow_smem(K kernel, size_t bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -295,10 +410,25 @@ void launch_exact_stream(Prec p, int rows, const int* row_frame, const void* fra
   note_launch();
 }
 
-void launch_approx_stream(Prec p, const int* approx_list, const int* approx_seg, const int* count,
+void launch_approx_stream(Prec p, int max_rows, const int* approx_list, const int* approx_seg, const int* count,
                           const void* frames, const LandmarkDev& L, FrameInfo fi, const double4* qxy, const void* Bseg,
                           void* D, cudaStream_t st) {
   if (L.M <= 0) return;
+  const int apg = p == P_F16 ? 8 : 4;
+  if (max_rows == 1 && L.N % apg == 0 && (uintptr_t)L.coords % 16 == 0 && (uintptr_t)frames % 16 == 0) {
+    constexpr int LPB = 4;
+    const unsigned blocks = (unsigned)((L.M + LPB - 1) / LPB);
+    if (p == P_F16)
+      approx_stream_vec<__half, LPB><<<blocks, ST_THREADS, 0, st>>>(
+          approx_list, approx_seg, count, (const float*)frames, fi.c32, qxy, (const __half*)L.coords, L.off,
+          (const float*)Bseg, L.w, L.M, L.N, L.dscale, (float*)D);
+    else
+      approx_stream_vec<float, LPB><<<blocks, ST_THREADS, 0, st>>>(
+          approx_list, approx_seg, count, (const float*)frames, fi.c32, qxy, (const float*)L.coords, L.off,
+          (const float*)Bseg, L.w, L.M, L.N, L.dscale, (float*)D);
+    note_launch();
+    return;
+  }
   const size_t es = p == P_F16 ? sizeof(__half) : sizeof(float);
   const size_t smem = (size_t)3 * L.N * es;
   const bool aligned = ((3 * (size_t)L.N * es) % 16 == 0) && ((uintptr_t)L.coords % 16 == 0);

@@ -160,7 +160,7 @@ constexpr int STREAM_FRAMES = 4;
 bool stream_fits(Prec p, int N);  // the staged landmark fits in shared memory
 void launch_exact_stream(Prec p, int rows, const int* row_frame, const void* frames, const LandmarkDev& L,
                          FrameInfo fi, void* D, void* Rout, unsigned* status, cudaStream_t st);
-void launch_approx_stream(Prec p, const int* approx_list, const int* approx_seg, const int* count,
+void launch_approx_stream(Prec p, int max_rows, const int* approx_list, const int* approx_seg, const int* count,
                           const void* frames, const LandmarkDev& L, FrameInfo fi, const double4* qxy, const void* Bseg,
                           void* D, cudaStream_t st);
 
