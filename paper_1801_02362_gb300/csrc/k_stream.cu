@@ -268,13 +268,13 @@ approx_stream_f32(const int* __restrict__ alist, const int* __restrict__ aseg, c
 // staging, so many CTAs per SM keep enough loads in flight to stream the landmark set at
 // the memory's rate.  Requires 16-byte aligned rows (N a multiple of APG).
 template <typename LT, int LPB>
-__global__ void __launch_bounds__(ST_THREADS)
+__global__ void __launch_bounds__(128)
 approx_stream_vec(const int* __restrict__ alist, const int* __restrict__ aseg, const int* __restrict__ acount,
                   const float* __restrict__ frames, const float4* __restrict__ c32, const double4* __restrict__ qxy,
                   const LT* __restrict__ lm, const float* __restrict__ lmoff, const float* __restrict__ Bseg,
                   const float* __restrict__ wts, int M, int N, double dscale, float* __restrict__ Dout) {
   constexpr int APG = sizeof(LT) == 2 ? 8 : 4;
-  __shared__ float red[ST_THREADS / 32][LPB];
+  __shared__ float red[32][LPB];
   if (*acount < 1) return;  // uniform over the grid
   const int f = alist[0], seg = aseg[0];
   const int i0 = blockIdx.x * LPB;
@@ -320,16 +320,22 @@ approx_stream_vec(const int* __restrict__ alist, const int* __restrict__ aseg, c
     float wv[APG];
 #pragma unroll
     for (int a = 0; a < APG; ++a) wv[a] = wts ? wts[j0 + a] : 1.0f;
+    // every landmark vector of the group is requested before any is used
+    uint4 raw[LPB][3];
 #pragma unroll
     for (int l = 0; l < LPB; ++l) {
-      const int i = i0 + l;
-      if (i >= M) break;
-      float av[APG * 3];
+      const int i = min(i0 + l, M - 1);  // rows beyond M repeat the last landmark; not written
       const uint4* src = reinterpret_cast<const uint4*>(lm + ((size_t)i * N + j0) * 3);
 #pragma unroll
+      for (int q = 0; q < 3; ++q) raw[l][q] = src[q];
+    }
+#pragma unroll
+    for (int l = 0; l < LPB; ++l) {
+      const int i = min(i0 + l, M - 1);
+      float av[APG * 3];
+#pragma unroll
       for (int q = 0; q < 3; ++q) {
-        const uint4 t = src[q];
-        const unsigned u[4] = {t.x, t.y, t.z, t.w};
+        const unsigned u[4] = {raw[l][q].x, raw[l][q].y, raw[l][q].z, raw[l][q].w};
         if (sizeof(LT) == 2) {
 #pragma unroll
           for (int h = 0; h < 4; ++h) {
@@ -372,7 +378,7 @@ approx_stream_vec(const int* __restrict__ alist, const int* __restrict__ aseg, c
   __syncthreads();
   if ((int)threadIdx.x < LPB && i0 + (int)threadIdx.x < M) {
     float t = 0.0f;
-    for (int k = 0; k < ST_THREADS / 32; ++k) t += red[k][threadIdx.x];
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k][threadIdx.x];
     Dout[(size_t)f * M + i0 + threadIdx.x] = t * (float)dscale;
   }
 }
@@ -419,11 +425,11 @@ void launch_approx_stream(Prec p, int max_rows, const int* approx_list, const in
     constexpr int LPB = 4;
     const unsigned blocks = (unsigned)((L.M + LPB - 1) / LPB);
     if (p == P_F16)
-      approx_stream_vec<__half, LPB><<<blocks, ST_THREADS, 0, st>>>(
+      approx_stream_vec<__half, LPB><<<blocks, 128, 0, st>>>(
           approx_list, approx_seg, count, (const float*)frames, fi.c32, qxy, (const __half*)L.coords, L.off,
           (const float*)Bseg, L.w, L.M, L.N, L.dscale, (float*)D);
     else
-      approx_stream_vec<float, LPB><<<blocks, ST_THREADS, 0, st>>>(
+      approx_stream_vec<float, LPB><<<blocks, 128, 0, st>>>(
           approx_list, approx_seg, count, (const float*)frames, fi.c32, qxy, (const float*)L.coords, L.off,
           (const float*)Bseg, L.w, L.M, L.N, L.dscale, (float*)D);
     note_launch();
