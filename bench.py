@@ -59,6 +59,31 @@ def measured_peaks() -> dict:
         return {}
 
 
+# side measurements: name -> (function, keyword arguments); see run_ours
+DETAILS = {
+    "c1_exact_fp64": ("config", dict(label="exact path CV, FP64, N=22, M=20, F=1000 (reflecting walk)", seed=1, n=22,
+                                     m=20, f=1000, eps=-1.0, grad=False, precision="fp64", noise=0.02, steps=10,
+                                     schedule="walk")),
+    "c4_exact_grad": ("config", dict(label="exact path CV with gradients, FP32, N=1000, M=500, F=4096", seed=4,
+                                     n=1000, m=500, f=4096, eps=-1.0, grad=True, precision="fp32")),
+    "c5_stream_fp32": ("stream", dict(precision="fp32")),
+    "c5_stream_fp16": ("stream", dict(precision="fp16")),
+    "c5_batched_fp32": ("config", dict(label="close-structure path CV, N=5000, M=2000, F=10000, fp32 landmark storage",
+                                       seed=5, n=5000, m=2000, f=10_000, eps=0.05, grad=False, precision="fp32",
+                                       steps=1)),
+    "c5_batched_fp16": ("config", dict(label="close-structure path CV, N=5000, M=2000, F=10000, fp16 landmark storage",
+                                       seed=5, n=5000, m=2000, f=10_000, eps=0.05, grad=False, precision="fp16",
+                                       steps=1)),
+}
+
+
+def run_detail(pcv, name: str, calls: int = 200) -> dict:
+    kind, kw = DETAILS[name]
+    if kind == "stream":
+        return time_stream(pcv, calls=calls, **kw)
+    return time_config(pcv, **kw)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -70,6 +95,9 @@ def parse():
     ap.add_argument("--no-details", action="store_true", help="skip the exact-mode / eps-sweep side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--detail", default=None, choices=sorted(DETAILS),
+                    help="run one side measurement alone and print it (for profiling)")
+    ap.add_argument("--calls", type=int, default=200, help="frames fed one per call in the streaming measurements")
     return ap.parse_args()
 
 
@@ -335,6 +363,10 @@ def run_ours(args):
 
     from paper_1801_02362_gb300 import pcv
 
+    if args.detail:
+        pcv.load()
+        print(json.dumps({"detail": args.detail, **run_detail(pcv, args.detail, args.calls)}), flush=True)
+        return
     world, rank, local, pg = dist_setup(args)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -467,17 +499,8 @@ def run_ours(args):
                               "approx_msds": st2["approx_msds"],
                               "kernel_ms": {k: round(v[0] / n, 4) for k, v in pr.items()}}
         pcv.pcv_set_close_threshold(ctx.ctx, args.eps)
-        details["c1_exact_fp64"] = time_config(pcv, "exact path CV, FP64, N=22, M=20, F=1000 (reflecting walk)", 1,
-                                               22, 20, 1000, -1.0, False, "fp64", noise=0.02, steps=10,
-                                               schedule="walk")
-        details["c4_exact_grad"] = time_config(pcv, "exact path CV with gradients, FP32, N=1000, M=500, F=4096", 4,
-                                               1000, 500, 4096, -1.0, True, "fp32")
-        for prec in ("fp32", "fp16"):
-            details[f"c5_stream_{prec}"] = time_stream(pcv, prec)
-        for prec in ("fp32", "fp16"):
-            details[f"c5_batched_{prec}"] = time_config(
-                pcv, f"close-structure path CV, N=5000, M=2000, F=10000, {prec} landmark storage", 5, 5000, 2000,
-                10_000, 0.05, False, prec, steps=1)
+        for name in DETAILS:
+            details[name] = run_detail(pcv, name, args.calls)
         if "c5_stream_fp32" in details and "c5_stream_fp16" in details:
             details["c5_fp16_vs_fp32_speedup"] = {
                 "stream_per_call": details["c5_stream_fp32"]["ms_per_call"] / details["c5_stream_fp16"]["ms_per_call"],

@@ -422,14 +422,15 @@ void launch_approx_stream(Prec p, int max_rows, const int* approx_list, const in
   if (L.M <= 0) return;
   const int apg = p == P_F16 ? 8 : 4;
   if (max_rows == 1 && L.N % apg == 0 && (uintptr_t)L.coords % 16 == 0 && (uintptr_t)frames % 16 == 0) {
-    constexpr int LPB = 4;
-    const unsigned blocks = (unsigned)((L.M + LPB - 1) / LPB);
+    // landmarks per 128-thread CTA (measured on the 5000-atom, 2000-landmark set): FP32 4 (the
+    // frame is re-read and rotated once per CTA), FP16 2 (half the bytes per landmark: more
+    // CTAs in flight cover the load latency better)
     if (p == P_F16)
-      approx_stream_vec<__half, LPB><<<blocks, 128, 0, st>>>(
+      approx_stream_vec<__half, 2><<<(unsigned)((L.M + 1) / 2), 128, 0, st>>>(
           approx_list, approx_seg, count, (const float*)frames, fi.c32, qxy, (const __half*)L.coords, L.off,
           (const float*)Bseg, L.w, L.M, L.N, L.dscale, (float*)D);
     else
-      approx_stream_vec<float, LPB><<<blocks, 128, 0, st>>>(
+      approx_stream_vec<float, 4><<<(unsigned)((L.M + 3) / 4), 128, 0, st>>>(
           approx_list, approx_seg, count, (const float*)frames, fi.c32, qxy, (const float*)L.coords, L.off,
           (const float*)Bseg, L.w, L.M, L.N, L.dscale, (float*)D);
     note_launch();
