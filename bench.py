@@ -39,13 +39,18 @@ FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
 
 # algorithmic FP32 flops per (frame, landmark, atom) of each pair kernel (FMA = 2 flops)
 FLOPS_PER_UNIT = {
-    "approx_pair": 9,         # d = x' - b (3 sub), |d|^2 (3 FMA)
+    "approx_pair": 6,         # deviation form: dx . d (3 FMA); the norms are O(N) per frame / landmark
     "exact_pair": 45,         # pass 1: 9 FMA; pass 2: R a (9 FMA), 3 sub, 3 FMA
     "adjoint_beta_pair": 36,  # beta^s, beta^z += gamma R_i a (2 x 9 FMA), per-pair rotations
     "adjoint_beta_seg": 12,   # beta^s, beta^z += gamma b_i (2 x 3 FMA), b_i shared by a segment
     "adjoint_beta_mma": 12,   # the same product on the tensor cores (3 TF32 MMAs per product)
 }
 TENSOR_KERNELS = {"adjoint_beta_mma"}
+# DRAM bytes per unit of work from ncu captures of the current kernels (profiles/
+# c2_close_kernels_f50k.md, F=50000, scaled here by the units one launch processes):
+# approx_pair per approximate MSD, adjoint_beta_mma per frame
+DRAM_BYTES_PER_UNIT = {"approx_pair": (191.970816e6 + 30.303232e6) / 9_997_600,
+                       "adjoint_beta_mma": (186.908672e6 + 305.802752e6) / 50_000}
 # TF32 tensor peak: measured bf16 cuBLAS rate x the nominal TF32/bf16 ratio (1.1 / 2.25 PFLOP/s)
 TF32_PER_BF16 = 1.1 / 2.25
 
@@ -443,8 +448,13 @@ def run_ours(args):
     else:
         peak, bound = FP32_PEAK_TFLOPS, "alu"
         peak_source = "152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz max clock (derived; FP32 FMA pipe)"
+    traffic = None
+    if dom == "approx_pair":
+        traffic = DRAM_BYTES_PER_UNIT[dom] * approx_msds_step / launches_per_step
+    elif dom == "adjoint_beta_mma":
+        traffic = DRAM_BYTES_PER_UNIT[dom] * F / launches_per_step
     roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
                 "peak_source": peak_source,
                 "per_launch_ms": per_launch_ms,
                 "flops_per_launch": flops,
