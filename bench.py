@@ -71,6 +71,7 @@ DETAILS = {
                                      schedule="walk")),
     "c4_exact_grad": ("config", dict(label="exact path CV with gradients, FP32, N=1000, M=500, F=4096", seed=4,
                                      n=1000, m=500, f=4096, eps=-1.0, grad=True, precision="fp32")),
+    "c3_group": ("group", dict()),
     "c5_stream_fp32": ("stream", dict(precision="fp32")),
     "c5_stream_fp16": ("stream", dict(precision="fp16")),
     "c5_batched_fp32": ("config", dict(label="close-structure path CV, N=5000, M=2000, F=10000, fp32 landmark storage",
@@ -86,6 +87,8 @@ def run_detail(pcv, name: str, calls: int = 200) -> dict:
     kind, kw = DETAILS[name]
     if kind == "stream":
         return time_stream(pcv, calls=calls, **kw)
+    if kind == "group":
+        return time_group(pcv, **kw)
     return time_config(pcv, **kw)
 
 
@@ -310,6 +313,65 @@ def time_stream(pcv, precision: str, n: int = 5000, m: int = 2000, calls: int = 
             "refreshes": st["refreshes_threshold"] - st0["refreshes_threshold"],
             "kernels": kern, "hbm_peak_GB_per_s": hbm,
             "kernel_ms": {k: round(v[0] / calls, 4) for k, v in pr.items()}}
+
+
+def time_group(pcv, n_inst: int = 256, f: int = 512, seed: int = 7, steps: int = 5) -> dict:
+    """Batched multiple walkers: n_inst independent instances, N ~ U[50, 2000] atoms,
+    M ~ U[50, 1000] landmarks, f frames each, FP32 exact mode.  One group call (three
+    persistent launches, replayed from a captured graph after the first call) against one
+    pcv_evaluate per instance, on the same contexts and buffers."""
+    import torch
+    from paper_1801_02362_gb300 import synth
+
+    rng = np.random.default_rng(seed)
+    ctxs, bufs, pairs = [], [], 0
+    for k in range(n_inst):
+        n = int(rng.integers(50, 2001))
+        m = int(rng.integers(50, 1001))
+        lm, fr = synth.make_problem(1000 + k, n_atoms=n, n_landmarks=m, n_frames=f, frame_noise=0.05)
+        lam = lambda_from_gpu(pcv, lm)
+        ctx = pcv.PathCV(lm, lam, eps=-1.0, precision="fp32")
+        x = torch.tensor(np.ascontiguousarray(fr), dtype=torch.float32, device="cuda")
+        bufs.append({"x": x, "s": torch.empty(f, dtype=torch.float64, device="cuda"),
+                     "z": torch.empty(f, dtype=torch.float64, device="cuda")})
+        ctxs.append(ctx)
+        pairs += f * m * n
+    P = lambda t: t.data_ptr()
+    ios = [{"F": f, "frames": P(b["x"]), "s": P(b["s"]), "z": P(b["z"])} for b in bufs]
+    handles = [c.ctx for c in ctxs]
+    stream = torch.cuda.current_stream()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+
+    def per_instance():
+        for c, io in zip(ctxs, ios):
+            pcv.pcv_evaluate(c.ctx, f, io["frames"], io["s"], io["z"], None, None, None, None)
+
+    def group():
+        pcv.pcv_evaluate_group(handles, ios)
+
+    out = {}
+    for name, fn in (("per_instance_launches", per_instance), ("group_persistent_graph", group)):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[name] = a.elapsed_time(b) / steps
+    for c in ctxs:
+        c.close()
+    t = out["group_persistent_graph"]
+    flops = 45.0 * pairs  # exact tiles: 9 FMA (pass 1) + 9 FMA + 3 sub + 3 FMA (pass 2) per atom pair
+    return {"workload": f"{n_inst} independent instances, N~U[50,2000], M~U[50,1000], {f} frames each, "
+                        "FP32 exact mode",
+            "instances": n_inst, "frames_per_step": n_inst * f, "atom_landmark_frame_triples": pairs,
+            "ms_per_step_group": t, "ms_per_step_per_instance": out["per_instance_launches"],
+            "group_speedup": out["per_instance_launches"] / t, "frames_per_s": n_inst * f / (t / 1e3),
+            "achieved_TFLOP_s": flops / (t / 1e3) / 1e12, "fp32_peak_TFLOP_s": FP32_PEAK_TFLOPS,
+            "frac_of_fp32_peak": flops / (t / 1e3) / 1e12 / FP32_PEAK_TFLOPS}
 
 
 def cpu_baseline(lm, fr, lam, eps, seconds: float) -> dict:

@@ -209,6 +209,39 @@ PCV_API pcv_status pcv_get_profile(pcv_ctx* ctx, int n, double* ms, int64_t* lau
 /* Name of kernel family `id` ("" outside 0..PCV_PROFILE_KERNELS-1). */
 PCV_API const char* pcv_profile_name(int id);
 
+/* Many walkers or instances in one call (multiple-walker metadynamics: each walker has its
+ * own landmark path, sizes N and M, lambda and frames).
+ *
+ * io[k] is the batch of context ctxs[k] with the meaning of pcv_evaluate's arguments
+ * (frames, s, z, dsdx, dzdx, msd, refreshed; device pointers; F may differ per entry and may
+ * be 0).  The contexts must be distinct and on one device.  Work is ordered after the work
+ * already enqueued on `stream` (a cudaStream_t; NULL = the default stream) and later work on
+ * `stream` waits for it.
+ *
+ * When every context is in exact mode (threshold < 0) with FP32 or FP16 storage (all the
+ * same), and no entry asks for gradients, the step runs as three launches over all
+ * instances: frame preparation (one warp per frame), the exact pair tiles of every instance
+ * in one persistent kernel, and the path CVs (one warp per frame).  The first call with a
+ * given set of contexts, sizes and buffers times persistent grids of 1, 2, 3, 4 and 8 CTAs
+ * per SM (and one CTA per tile), keeps the fastest, and captures the three launches in a
+ * CUDA graph on a stream the first context owns; later calls with the same contexts, sizes,
+ * buffers and lambdas replay the graph.  Otherwise the batches are evaluated one after
+ * another with pcv_evaluate.  Errors: PCV_EINVAL / PCV_ESTATE as pcv_evaluate, reported on
+ * ctxs[0] (pcv_last_error(ctxs[0])); device-side failures are reported by pcv_sync of the
+ * context concerned.  The paper evaluates one structure per call; this is the batched
+ * form of its per-step evaluation. */
+typedef struct pcv_batch_io {
+  int F;
+  const void* frames;
+  double* s;
+  double* z;
+  void* dsdx;
+  void* dzdx;
+  double* msd;
+  uint8_t* refreshed;
+} pcv_batch_io;
+PCV_API pcv_status pcv_evaluate_group(pcv_ctx* const* ctxs, int n, const pcv_batch_io* io, void* stream);
+
 /* Landmark shards (one GPU per shard, or several contexts on one GPU).
  *
  * Eqs. 5-6 are a log-sum-exp over the landmarks, so path CVs computed by contexts that

@@ -23,11 +23,10 @@ __device__ __forceinline__ int warp_global() {
 //   FP32 frames: centre c = sum_j w_j x_j with compensated FP32 sums, c32 = fl(c);
 //   G = sum_j wk_j |fl(x_j - c32)|^2 over exactly the values the pair kernels stage
 //   (error-free squares, compensated sums).  FP64 frames: plain FP64.
-__global__ void frame_prep_f32(int F, int N, const float* __restrict__ frames,
-                               const float* __restrict__ wts, float4* __restrict__ c32,
-                               double4* __restrict__ c64, double* __restrict__ G) {
-  const int f = warp_global();
-  if (f >= F) return;
+// centre and G of frame f, one warp
+__device__ __forceinline__ void frame_prep_warp_f32(int f, int N, const float* __restrict__ frames,
+                                                    const float* __restrict__ wts, float4* __restrict__ c32,
+                                                    double* __restrict__ G) {
   const int lane = threadIdx.x & 31;
   const float* x = frames + (size_t)f * N * 3;
   float hi[3] = {0, 0, 0}, lo[3] = {0, 0, 0};
@@ -71,6 +70,13 @@ __global__ void frame_prep_f32(int F, int N, const float* __restrict__ frames,
     c32[f] = make_float4(cf[0], cf[1], cf[2], 0.0f);
     G[f] = pair_to_double(gh, gl);
   }
+}
+
+__global__ void frame_prep_f32(int F, int N, const float* __restrict__ frames, const float* __restrict__ wts,
+                               float4* __restrict__ c32, double4* __restrict__ c64, double* __restrict__ G) {
+  const int f = warp_global();
+  if (f >= F) return;
+  frame_prep_warp_f32(f, N, frames, wts, c32, G);
 }
 
 // The same per frame with one 256-thread block per frame, for a few large frames (the
@@ -717,11 +723,10 @@ __global__ void __launch_bounds__(SCAN_THREADS) compact_kernel(int F, const uint
 // lane partials combined in FP64.  One warp per frame.
 // With want_p the distances are overwritten by the softmax weights p_i = exp(-lambda (D_i -
 // m)) / l that the adjoint consumes (gamma^z_i = p_i, gamma^s_i = -lambda p_i (q_i - s)).
-__global__ void finalize_f32(int F, int M, float* __restrict__ D, const float* __restrict__ q, float lambda,
-                             double* __restrict__ s, double* __restrict__ z, float* __restrict__ mstat,
-                             double* __restrict__ msd, int want_p) {
-  const int f = warp_global();
-  if (f >= F) return;
+// s, z of frame f from its MSD row (Eqs. 5-6, shifted log-sum-exp), one warp
+__device__ __forceinline__ void finalize_warp_f32(int f, int M, float* __restrict__ D, const float* __restrict__ q,
+                                                  float lambda, double* __restrict__ s, double* __restrict__ z,
+                                                  float* __restrict__ mstat, double* __restrict__ msd, int want_p) {
   const int lane = threadIdx.x & 31;
   float* d = D + (size_t)f * M;
   float m = 3.4e38f;
@@ -748,6 +753,40 @@ __global__ void finalize_f32(int F, int M, float* __restrict__ D, const float* _
     mstat[2 * f] = m;
     mstat[2 * f + 1] = l;
   }
+}
+
+__global__ void finalize_f32(int F, int M, float* __restrict__ D, const float* __restrict__ q, float lambda,
+                             double* __restrict__ s, double* __restrict__ z, float* __restrict__ mstat,
+                             double* __restrict__ msd, int want_p) {
+  const int f = warp_global();
+  if (f >= F) return;
+  finalize_warp_f32(f, M, D, q, lambda, s, z, mstat, msd, want_p);
+}
+
+// ---- group forms: frames of many instances, one warp per frame, instance found by
+// binary search over the instances' first global frame index
+__device__ __forceinline__ int group_instance(const GroupInst* __restrict__ I, int n, int g) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (I[mid].fbase <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void frame_prep_group_f32(const GroupInst* __restrict__ I, int n, int Ftot) {
+  const int g = warp_global();
+  if (g >= Ftot) return;
+  const GroupInst& t = I[group_instance(I, n, g)];
+  frame_prep_warp_f32(g - t.fbase, t.N, t.frames, t.w, t.c32, t.fG);
+}
+
+__global__ void finalize_group_f32(const GroupInst* __restrict__ I, int n, int Ftot) {
+  const int g = warp_global();
+  if (g >= Ftot) return;
+  const GroupInst& t = I[group_instance(I, n, g)];
+  finalize_warp_f32(g - t.fbase, t.M, t.D, t.q32, t.lambda, t.s, t.z, t.mstat, t.msd, 0);
 }
 
 __global__ void finalize_f64(int F, int M, double* __restrict__ D, const double* __restrict__ q,
@@ -911,6 +950,18 @@ void launch_finalize(Prec p, int F, int M, void* D, const double* q, const float
   else
     finalize_f32<<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(F, M, (float*)D, q32, (float)lambda, s, z, mstat, msd_out,
                                                           want_p ? 1 : 0);
+  note_launch();
+}
+
+void launch_frame_prep_group(const GroupInst* I, int n, int Ftot, cudaStream_t st) {
+  if (Ftot <= 0) return;
+  frame_prep_group_f32<<<blocks_for((size_t)Ftot, WARPS_PER_BLOCK), 32 * WARPS_PER_BLOCK, 0, st>>>(I, n, Ftot);
+  note_launch();
+}
+
+void launch_finalize_group(const GroupInst* I, int n, int Ftot, cudaStream_t st) {
+  if (Ftot <= 0) return;
+  finalize_group_f32<<<blocks_for((size_t)Ftot, WARPS_PER_BLOCK), 32 * WARPS_PER_BLOCK, 0, st>>>(I, n, Ftot);
   note_launch();
 }
 

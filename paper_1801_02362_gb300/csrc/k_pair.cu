@@ -158,13 +158,16 @@ __device__ __forceinline__ void load_tile_frames(int rows, const int* __restrict
 //  pass 2: D = sum_j w_j |x_j - R a_j|^2 directly in FP32 (Eq. dist): positive terms, no
 //          cancellation, stationary in R -- so D is accurate to ~1e-7 relative although
 //          every operation is FP32.
+// one 16-frame x 32-landmark tile with origin (row0, i0); the per-call kernel and the
+// persistent group kernel both run it
 template <typename LT>
-__global__ void __launch_bounds__(EX_THREADS, 4)
-exact_pair_f32(int rows, const int* __restrict__ row_frame, const float* __restrict__ frames,
-               const float4* __restrict__ c32, const double* __restrict__ fG, const LT* __restrict__ lm,
-               const float* __restrict__ lmoff, const double* __restrict__ lG, const float* __restrict__ wts, int M,
-               int N, double dscale, float* __restrict__ Dout, float* __restrict__ Rout,
-               unsigned* __restrict__ status) {
+__device__ __forceinline__ void exact_tile_f32(int rows, const int* __restrict__ row_frame,
+                                               const float* __restrict__ frames, const float4* __restrict__ c32,
+                                               const double* __restrict__ fG, const LT* __restrict__ lm,
+                                               const float* __restrict__ lmoff, const double* __restrict__ lG,
+                                               const float* __restrict__ wts, int M, int N, double dscale,
+                                               float* __restrict__ Dout, float* __restrict__ Rout,
+                                               unsigned* __restrict__ status, int row0, int i0) {
   constexpr int TF = EX_TF, TM = EX_TM, KC = 32;
   constexpr int PF = TF + 2, PM = TM + 2;
   __shared__ __align__(16) float Xs[KC * 3][PF];
@@ -172,9 +175,7 @@ exact_pair_f32(int rows, const int* __restrict__ row_frame, const float* __restr
   __shared__ int s_frame[TF];
   __shared__ float s_c[TF][3];
 
-  const int row0 = blockIdx.y * TF;
   if (row0 >= rows) return;
-  const int i0 = blockIdx.x * TM;
   const int tid = threadIdx.x;
   const int tx = tid & 15;  // landmark pair: i0 + 2 tx + {0,1}
   const int ty = tid >> 4;  // frame pair: rows 2 ty + {0,1}
@@ -281,6 +282,30 @@ exact_pair_f32(int rows, const int* __restrict__ row_frame, const float* __restr
       }
     }
   if (!all_ok) atomicOr(status, STATUS_NOCONV);
+}
+
+template <typename LT>
+__global__ void __launch_bounds__(EX_THREADS, 4)
+exact_pair_f32(int rows, const int* __restrict__ row_frame, const float* __restrict__ frames,
+               const float4* __restrict__ c32, const double* __restrict__ fG, const LT* __restrict__ lm,
+               const float* __restrict__ lmoff, const double* __restrict__ lG, const float* __restrict__ wts, int M,
+               int N, double dscale, float* __restrict__ Dout, float* __restrict__ Rout,
+               unsigned* __restrict__ status) {
+  exact_tile_f32<LT>(rows, row_frame, frames, c32, fG, lm, lmoff, lG, wts, M, N, dscale, Dout, Rout, status,
+                     blockIdx.y * EX_TF, blockIdx.x * EX_TM);
+}
+
+// Many instances in one persistent launch: CTA b takes tiles b, b + grid, ...
+template <typename LT>
+__global__ void __launch_bounds__(EX_THREADS, 4)
+exact_group_f32(const GroupInst* __restrict__ I, const GroupTile* __restrict__ tiles, int ntiles) {
+  for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
+    const GroupTile w = tiles[k];
+    const GroupInst& t = I[w.inst];
+    exact_tile_f32<LT>(t.F, nullptr, t.frames, t.c32, t.fG, (const LT*)t.lm, t.lmoff, t.lG, t.w, t.M, t.N, t.dscale,
+                       t.D, nullptr, t.status, w.row0, w.i0);
+    __syncthreads();  // the tile's shared staging is reused by the next tile
+  }
 }
 
 // FP64 mode: one pass, FP64 correlation, FP64 eigenvalue and D = G_x + G_a - 2 lambda_max
@@ -779,6 +804,17 @@ void launch_exact_pairs(Prec p, int rows, const int* row_frame, const int* rows_
                                                           (float*)D, (float*)Rout, status); note_launch();
       break;
   }
+}
+
+void launch_exact_group(bool fp16, const GroupInst* I, const GroupTile* tiles, int ntiles, int blocks,
+                        cudaStream_t st) {
+  if (ntiles <= 0) return;
+  static_assert(GROUP_TILE_F == EX_TF && GROUP_TILE_M == EX_TM, "group tiles are the exact tiles");
+  if (fp16)
+    exact_group_f32<__half><<<blocks, EX_THREADS, 0, st>>>(I, tiles, ntiles);
+  else
+    exact_group_f32<float><<<blocks, EX_THREADS, 0, st>>>(I, tiles, ntiles);
+  note_launch();
 }
 
 // landmark tile of 32 or 40 (whichever wastes fewer rows of the last tile)

@@ -106,6 +106,13 @@ struct pcv_ctx {
   DevBuf S6;                      // per-segment landmark moments R A R^T of the finish
   DevBuf h_frames, h_s, h_z, h_gs, h_gz, h_msd, h_ref;  // device staging for pcv_evaluate_host
   Small* small_host = nullptr;
+  // state of group evaluations led by this context (pcv_evaluate_group with it first)
+  DevBuf grp_inst, grp_tiles;
+  std::vector<uint64_t> grp_sig;       // what the captured graph was built for
+  cudaGraphExec_t grp_exec = nullptr;
+  cudaStream_t grp_stream = nullptr;   // the library's own stream: graphs cannot be captured on stream 0
+  cudaEvent_t grp_ev[2] = {nullptr, nullptr};
+  int grp_blocks = 0;                  // persistent grid chosen by the autotuner
   pcv_stats stats{};
   std::string err;
   // profiler
@@ -279,8 +286,13 @@ pcv_status pcv_destroy(pcv_ctx* c) {
                     &c->fG, &c->bandD, &c->bandQ, &c->bandF, &c->chD, &c->chQ, &c->chF, &c->rlist, &c->rcount,
                     &c->recF, &c->recRef, &c->recD, &c->recQ, &c->reflist, &c->segof, &c->alist, &c->aseg,
                     &c->Dbuf, &c->Rpair, &c->Bseg, &c->Xr, &c->Bm, &c->GSb, &c->GZb, &c->Nx, &c->Nb, &c->Yc, &c->Gsum, &c->Amma, &c->Bmma, &c->S6, &c->mstat, &c->status, &c->nrecheck, &c->small, &c->h_frames,
-                    &c->h_s, &c->h_z, &c->h_gs, &c->h_gz, &c->h_msd, &c->h_ref};
+                    &c->h_s, &c->h_z, &c->h_gs, &c->h_gz, &c->h_msd, &c->h_ref, &c->grp_inst, &c->grp_tiles};
+  if (c->grp_stream) cudaStreamSynchronize(c->grp_stream);
   for (DevBuf* b : bufs) release(*b);
+  if (c->grp_exec) cudaGraphExecDestroy(c->grp_exec);
+  for (cudaEvent_t e : c->grp_ev)
+    if (e) cudaEventDestroy(e);
+  if (c->grp_stream) cudaStreamDestroy(c->grp_stream);
   for (const ProfEvent& e : c->prof_pending) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
@@ -838,6 +850,169 @@ pcv_status pcv_evaluate(pcv_ctx* c, int F, const void* frames, double* s, double
   if (st != PCV_OK) return st;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(c, PCV_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
+  return PCV_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Group evaluation (multiple walkers / ragged instances): one persistent launch per step of
+// the exact path over every instance, replayed from a captured CUDA graph.
+pcv_status pcv_evaluate_group(pcv_ctx* const* ctxs, int n, const pcv_batch_io* io, void* stream) {
+  if (n < 1 || !ctxs || !io) return fail(nullptr, PCV_EINVAL, "need n >= 1 contexts and as many io entries");
+  pcv_ctx* lead = ctxs[0];
+  if (!lead) return fail(nullptr, PCV_EINVAL, "NULL context 0");
+  bool persistent = true;
+  for (int k = 0; k < n; ++k) {
+    pcv_ctx* c = ctxs[k];
+    if (!c) return fail(lead, PCV_EINVAL, "NULL context %d", k);
+    for (int j = 0; j < k; ++j)
+      if (ctxs[j] == c) return fail(lead, PCV_EINVAL, "context %d appears twice (entries %d and %d)", k, j, k);
+    if (!c->have_lm || !c->have_lambda) return fail(lead, PCV_ESTATE, "context %d: landmarks or lambda not set", k);
+    if (c->device != lead->device) return fail(lead, PCV_EINVAL, "context %d is on another device", k);
+    const pcv_batch_io& b = io[k];
+    if (b.F < 0) return fail(lead, PCV_EINVAL, "entry %d: F < 0", k);
+    if (b.F > 0 && (!b.frames || !b.s || !b.z)) return fail(lead, PCV_EINVAL, "entry %d: frames, s, z required", k);
+    if ((b.dsdx == nullptr) != (b.dzdx == nullptr)) return fail(lead, PCV_EINVAL, "entry %d: dsdx and dzdx", k);
+    if ((size_t)b.F * c->M > ((size_t)1 << 40)) return fail(lead, PCV_EINVAL, "entry %d: F*M too large", k);
+    // the persistent path covers exact mode without gradients in the FP32 modes, one storage type
+    if (c->eps >= 0.0 || b.dsdx || c->prec == P_F64 || c->prec != lead->prec) persistent = false;
+  }
+  cudaSetDevice(lead->device);
+  const cudaStream_t user = (cudaStream_t)stream;
+  if (!persistent) {  // one evaluation per instance, in order, on the caller's stream
+    for (int k = 0; k < n; ++k) {
+      pcv_ctx* c = ctxs[k];
+      const cudaStream_t old = c->stream;
+      c->stream = user;
+      const pcv_batch_io& b = io[k];
+      const pcv_status r = pcv_evaluate(c, b.F, b.frames, b.s, b.z, b.dsdx, b.dzdx, b.msd, b.refreshed);
+      c->stream = old;
+      if (r != PCV_OK) {
+        if (c != lead) fail(lead, r, "entry %d: %s", k, c->err.c_str());
+        return r;
+      }
+    }
+    return PCV_OK;
+  }
+  // workspaces and descriptors
+  std::vector<GroupInst> inst(n);
+  std::vector<GroupTile> tiles;
+  int Ftot = 0;
+  std::vector<uint64_t> sig = {(uint64_t)n};
+  for (int k = 0; k < n; ++k) {
+    pcv_ctx* c = ctxs[k];
+    const pcv_batch_io& b = io[k];
+    pcv_status r = ensure_frame_workspace(c, b.F > 0 ? b.F : 1, false, false);
+    if (r != PCV_OK) return r;
+    const LandmarkDev L = lm_view(c);
+    GroupInst& t = inst[k];
+    t.frames = (const float*)b.frames;
+    t.lm = L.coords;
+    t.lmoff = L.off;
+    t.lG = L.G;
+    t.w = L.w;
+    t.dscale = L.dscale;
+    t.q32 = L.q32;
+    t.lambda = (float)c->lambda;
+    t.M = c->M;
+    t.N = c->N;
+    t.F = b.F;
+    t.fbase = Ftot;
+    t.c32 = (float4*)c->c32.p;
+    t.fG = (double*)c->fG.p;
+    t.D = (float*)c->Dbuf.p;
+    t.mstat = (float*)c->mstat.p;
+    t.s = b.s;
+    t.z = b.z;
+    t.msd = b.msd;
+    t.status = (unsigned*)c->status.p;
+    for (int r0 = 0; r0 < b.F; r0 += GROUP_TILE_F)
+      for (int i0 = 0; i0 < c->M; i0 += GROUP_TILE_M) tiles.push_back(GroupTile{k, r0, i0, 0});
+    Ftot += b.F;
+    const uint64_t lam_bits = *reinterpret_cast<const uint64_t*>(&c->lambda);
+    for (uint64_t v : {(uint64_t)(uintptr_t)c, (uint64_t)b.F, (uint64_t)(uintptr_t)b.frames, (uint64_t)(uintptr_t)b.s,
+                       (uint64_t)(uintptr_t)b.z, (uint64_t)(uintptr_t)b.msd, (uint64_t)(uintptr_t)L.coords,
+                       (uint64_t)(uintptr_t)c->Dbuf.p, (uint64_t)(uintptr_t)c->c32.p, lam_bits,
+                       (uint64_t)c->M, (uint64_t)c->N})
+      sig.push_back(v);
+  }
+  if (!lead->grp_stream) {
+    CUDA_TRY(lead, cudaStreamCreateWithFlags(&lead->grp_stream, cudaStreamNonBlocking));
+    CUDA_TRY(lead, cudaEventCreateWithFlags(&lead->grp_ev[0], cudaEventDisableTiming));
+    CUDA_TRY(lead, cudaEventCreateWithFlags(&lead->grp_ev[1], cudaEventDisableTiming));
+  }
+  const cudaStream_t gs = lead->grp_stream;
+  const int ntiles = (int)tiles.size();
+  const bool fp16 = lead->prec == P_F16;
+  // order the group's work after the caller's earlier work
+  CUDA_TRY(lead, cudaEventRecord(lead->grp_ev[0], user));
+  CUDA_TRY(lead, cudaStreamWaitEvent(gs, lead->grp_ev[0], 0));
+  if (sig != lead->grp_sig) {
+    pcv_status r;
+    if ((r = ensure(lead, lead->grp_inst, sizeof(GroupInst) * n)) != PCV_OK) return r;
+    if ((r = ensure(lead, lead->grp_tiles, sizeof(GroupTile) * (ntiles > 0 ? ntiles : 1))) != PCV_OK) return r;
+    CUDA_TRY(lead, cudaMemcpyAsync(lead->grp_inst.p, inst.data(), sizeof(GroupInst) * n, cudaMemcpyHostToDevice, gs));
+    if (ntiles > 0)
+      CUDA_TRY(lead, cudaMemcpyAsync(lead->grp_tiles.p, tiles.data(), sizeof(GroupTile) * ntiles,
+                                     cudaMemcpyHostToDevice, gs));
+    CUDA_TRY(lead, cudaStreamSynchronize(gs));  // the host vectors are released on return
+    const GroupInst* I = (const GroupInst*)lead->grp_inst.p;
+    const GroupTile* T = (const GroupTile*)lead->grp_tiles.p;
+    launch_frame_prep_group(I, n, Ftot, gs);
+    // autotuner: persistent grids of 1..8 CTAs per SM (and one CTA per tile), each timed once
+    // after the first run has warmed the caches; the fastest is kept for this group
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, lead->device);
+    const int cands[] = {sms, 2 * sms, 3 * sms, 4 * sms, 8 * sms, ntiles};
+    cudaEvent_t t0, t1;
+    CUDA_TRY(lead, cudaEventCreate(&t0));
+    CUDA_TRY(lead, cudaEventCreate(&t1));
+    launch_exact_group(fp16, I, T, ntiles, 4 * sms, gs);
+    float best = 3.4e38f;
+    int best_blocks = 4 * sms;
+    for (int cand : cands) {
+      const int blocks = cand < 1 ? 1 : (cand > ntiles && ntiles > 0 ? ntiles : cand);
+      cudaEventRecord(t0, gs);
+      launch_exact_group(fp16, I, T, ntiles, blocks, gs);
+      cudaEventRecord(t1, gs);
+      cudaEventSynchronize(t1);
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, t0, t1);
+      if (ms < best) {
+        best = ms;
+        best_blocks = blocks;
+      }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    lead->grp_blocks = best_blocks;
+    // capture the step: frame preparation, exact tiles, path CVs
+    if (lead->grp_exec) {
+      cudaGraphExecDestroy(lead->grp_exec);
+      lead->grp_exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    CUDA_TRY(lead, cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
+    launch_frame_prep_group(I, n, Ftot, gs);
+    launch_exact_group(fp16, I, T, ntiles, lead->grp_blocks, gs);
+    launch_finalize_group(I, n, Ftot, gs);
+    CUDA_TRY(lead, cudaStreamEndCapture(gs, &graph));
+    const cudaError_t ie = cudaGraphInstantiate(&lead->grp_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return fail(lead, PCV_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ie));
+    lead->grp_sig = sig;
+  }
+  CUDA_TRY(lead, cudaGraphLaunch(lead->grp_exec, gs));
+  CUDA_TRY(lead, cudaEventRecord(lead->grp_ev[1], gs));
+  CUDA_TRY(lead, cudaStreamWaitEvent(user, lead->grp_ev[1], 0));
+  for (int k = 0; k < n; ++k) {
+    pcv_ctx* c = ctxs[k];
+    c->stats.frames += io[k].F;
+    c->stats.landmark_alignments += (int64_t)c->M * io[k].F;
+    if (io[k].refreshed) launch_fill_u8(io[k].refreshed, 1, (size_t)io[k].F, user);
+  }
+  lead->stats.kernel_launches += 3;
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(lead, PCV_ECUDA, "group launch: %s", cudaGetErrorString(e));
   return PCV_OK;
 }
 

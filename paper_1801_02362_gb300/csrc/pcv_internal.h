@@ -154,6 +154,38 @@ void launch_approx_pairs(Prec p, int max_rows, const int* approx_list, const int
                          const double4* qxy, const void* Bseg, void* D, cudaStream_t st);
 
 // ---------------------------------------------------------------------------------------
+// group evaluation (many instances, exact mode, FP32 / FP16 storage): one descriptor per
+// instance in device memory; work items are global frames or (instance, frame tile,
+// landmark tile) triples
+struct GroupInst {
+  const float* frames;  // F x N x 3
+  const void* lm;       // landmarks (float or __half storage), lmoff the FP16 block offsets
+  const float* lmoff;
+  const double* lG;
+  const float* w;       // weights or nullptr (uniform)
+  double dscale;
+  const float* q32;
+  float lambda;
+  int M, N, F, fbase;   // fbase: global index of the instance's first frame
+  float4* c32;          // workspace of the instance's context
+  double* fG;
+  float* D;
+  float* mstat;
+  double* s;            // outputs
+  double* z;
+  double* msd;          // optional
+  unsigned* status;
+};
+struct GroupTile {
+  int inst, row0, i0, pad;
+};
+constexpr int GROUP_TILE_F = 16, GROUP_TILE_M = 32;  // the exact tile (k_pair.cu)
+void launch_frame_prep_group(const GroupInst* I, int n, int Ftot, cudaStream_t st);
+void launch_finalize_group(const GroupInst* I, int n, int Ftot, cudaStream_t st);
+// persistent grid of `blocks` CTAs over the tiles; fp16: landmarks in FP16 storage
+void launch_exact_group(bool fp16, const GroupInst* I, const GroupTile* tiles, int ntiles, int blocks, cudaStream_t st);
+
+// ---------------------------------------------------------------------------------------
 // landmark-parallel kernels for up to STREAM_FRAMES frames per call (k_stream.cu; FP32
 // and FP16-storage modes; one CTA per landmark, the landmark staged in shared memory)
 constexpr int STREAM_FRAMES = 4;

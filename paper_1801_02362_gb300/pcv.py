@@ -33,6 +33,12 @@ class PcvError(RuntimeError):
         self.status = status
 
 
+class pcv_batch_io(ctypes.Structure):
+    _fields_ = [("F", ctypes.c_int), ("frames", ctypes.c_void_p), ("s", ctypes.c_void_p), ("z", ctypes.c_void_p),
+                ("dsdx", ctypes.c_void_p), ("dzdx", ctypes.c_void_p), ("msd", ctypes.c_void_p),
+                ("refreshed", ctypes.c_void_p)]
+
+
 class pcv_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("frames", "xy_alignments", "landmark_alignments", "approx_msds",
                                               "refreshes_threshold", "refreshes_initial", "fp64_rechecks",
@@ -65,6 +71,7 @@ SIGNATURES = {
     "pcv_profile_name": (ctypes.c_char_p, [_i]),
     "pcv_evaluate_exact_noalloc": (_i, [_i, _i, _i, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, ctypes.c_char_p,
                                        ctypes.c_size_t]),
+    "pcv_evaluate_group": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(pcv_batch_io), _vp]),
     "pcv_shard_pack": (_i, [_i, _i, _i, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "pcv_shard_unpack": (_i, [_i, _i, _i, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "pcv_shard_pack_host": (_i, [_i, _i, _i, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -194,6 +201,20 @@ def pcv_get_profile(ctx) -> dict:
         if name and la[k]:
             out[name] = (float(ms[k]), int(la[k]))
     return out
+
+
+def pcv_evaluate_group(ctxs, ios, stream=None):
+    """ctxs: context handles; ios: dicts with keys F, frames, s, z and optionally dsdx, dzdx,
+    msd, refreshed (device pointers as ints)."""
+    n = len(ctxs)
+    handles = (_vp * n)(*[c.value if hasattr(c, "value") else c for c in ctxs])
+    arr = (pcv_batch_io * n)()
+    for k, d in enumerate(ios):
+        arr[k].F = int(d["F"])
+        for key in ("frames", "s", "z", "dsdx", "dzdx", "msd", "refreshed"):
+            setattr(arr[k], key, d.get(key))
+    st = load().pcv_evaluate_group(handles, n, arr, stream)
+    _check(ctxs[0], st)
 
 
 def pcv_shard_pack(precision: int, F: int, N: int, lam: float, zmin_ptr, s_ptr, z_ptr, dsdx_ptr, dzdx_ptr,
