@@ -52,8 +52,12 @@ def lib():
         L.orc_quat_to_rot.argtypes = [dp, dp]
         L.orc_path_cv.argtypes = [c_int, dp, dp, c_double, dp, dp, dp]
         L.orc_exact.argtypes = [c_int, c_int, c_int, dp, dp, dp, dp, c_double, dp, dp, dp, dp, dp]
+        i32p = ctypes.POINTER(ctypes.c_int32)
         L.orc_close.argtypes = [c_int, c_int, c_int, dp, dp, dp, dp, c_double, c_double, dp, dp,
-                                i64p, dp, dp, dp, u8p, dp, dp, dp]
+                                c_int, c_int, i32p, i64p, dp, dp, dp, u8p, dp, dp, dp]
+        L.orc_exact_nl.argtypes = [c_int, c_int, c_int, dp, dp, dp, dp, c_double, c_int, c_int, i32p, i64p,
+                                   dp, dp, dp, dp, dp]
+        L.orc_nl_select.argtypes = [c_int, dp, c_int, i32p]
         L.orc_close_distance.argtypes = [c_int, dp, dp, dp, dp, dp]
         L.orc_close_distance.restype = c_double
         for name in ("orc_cost_original", "orc_cost_close", "orc_amdahl"):
@@ -120,8 +124,12 @@ def path_cv(D, lam, q=None):
     return s[0], z[0], p
 
 
-def exact(frames, landmarks, lam, w=None, q=None, want_D=True, want_grad=False):
-    """Exact path CVs (Algorithm 1) for F frames."""
+def exact(frames, landmarks, lam, w=None, q=None, want_D=True, want_grad=False, nl=None, state=None):
+    """Exact path CVs (Algorithm 1) for F frames.
+
+    nl = (M_nl, L): neighbour list of the original method (distances to all landmarks
+    every L steps, to the M_nl closest of the last such step otherwise; frames in time
+    order, state carried in ``state``, a CloseState).  D of unlisted landmarks is +inf."""
     fr, lm = _f64(frames), _f64(landmarks)
     f, n = fr.shape[0], fr.shape[1]
     m = lm.shape[0]
@@ -130,44 +138,65 @@ def exact(frames, landmarks, lam, w=None, q=None, want_D=True, want_grad=False):
     D = np.zeros((f, m)) if want_D else None
     gs = np.zeros((f, n, 3)) if want_grad else None
     gz = np.zeros((f, n, 3)) if want_grad else None
-    st = lib().orc_exact(f, m, n, _p(_f64(w)), _p(fr), _p(lm), _p(_f64(q)), float(lam), _p(s), _p(z),
-                         _p(D), _p(gs), _p(gz))
+    if nl is None:
+        st = lib().orc_exact(f, m, n, _p(_f64(w)), _p(fr), _p(lm), _p(_f64(q)), float(lam), _p(s), _p(z),
+                             _p(D), _p(gs), _p(gz))
+    else:
+        if state is None:
+            state = CloseState(n, m)
+        st = lib().orc_exact_nl(f, m, n, _p(_f64(w)), _p(fr), _p(lm), _p(_f64(q)), float(lam), int(nl[0]),
+                                int(nl[1]), _p(state.nl, ctypes.c_int32), _p(state.ctr, ctypes.c_int64), _p(s),
+                                _p(z), _p(D), _p(gs), _p(gz))
     if st != 0:
         raise RuntimeError(f"oracle exact: status {st}")
-    return dict(s=s, z=z, D=D, dsdx=gs, dzdx=gz)
+    return dict(s=s, z=z, D=D, dsdx=gs, dzdx=gz, state=state)
+
+
+def nl_select(D, m_nl):
+    """The m_nl landmarks with the smallest D (ties to the lower index), in index order."""
+    D = _f64(D)
+    out = np.zeros(m_nl, dtype=np.int32)
+    lib().orc_nl_select(D.shape[0], _p(D), int(m_nl), _p(out, ctypes.c_int32))
+    return out
 
 
 class CloseState:
-    """Close-structure state (Algorithm 2) carried across calls."""
+    """Close-structure state (Algorithm 2) and neighbour list carried across calls."""
 
     def __init__(self, n_atoms: int, n_landmarks: int):
         self.y = np.zeros((n_atoms, 3))
         self.B = np.zeros((n_landmarks, 3, 3))
         self.ctr = np.zeros(8, dtype=np.int64)
+        self.nl = np.zeros(n_landmarks, dtype=np.int32)
 
     @property
     def counters(self) -> dict:
         c = self.ctr
         return dict(has_y=int(c[0]), frames=int(c[1]), xy_alignments=int(c[2]),
                     landmark_alignments=int(c[3]), approx_msds=int(c[4]),
-                    refreshes_threshold=int(c[5]), refreshes_initial=int(c[6]))
+                    refreshes_threshold=int(c[5]), refreshes_initial=int(c[6]), has_nl=int(c[7]))
 
     def copy(self) -> "CloseState":
         o = CloseState(self.y.shape[0], self.B.shape[0])
         o.y[:] = self.y
         o.B[:] = self.B
         o.ctr[:] = self.ctr
+        o.nl[:] = self.nl
         return o
 
 
 def close(frames, landmarks, lam, eps, state: CloseState | None = None, w=None, q=None,
-          want_D=True, want_grad=False):
-    """Floating close structure (Algorithm 2) over F time-ordered frames."""
+          want_D=True, want_grad=False, nl=None):
+    """Floating close structure (Algorithm 2) over F time-ordered frames.
+
+    nl = (M_nl, L): neighbour list chosen at reassignments (exact distances) and every L
+    steps (approximate distances), used in between.  D of unlisted landmarks is +inf."""
     fr, lm = _f64(frames), _f64(landmarks)
     f, n = fr.shape[0], fr.shape[1]
     m = lm.shape[0]
     if state is None:
         state = CloseState(n, m)
+    m_nl, stride = (0, 1) if nl is None else (int(nl[0]), int(nl[1]))
     s = np.zeros(f)
     z = np.zeros(f)
     D = np.zeros((f, m)) if want_D else None
@@ -176,8 +205,9 @@ def close(frames, landmarks, lam, eps, state: CloseState | None = None, w=None, 
     gs = np.zeros((f, n, 3)) if want_grad else None
     gz = np.zeros((f, n, 3)) if want_grad else None
     st = lib().orc_close(f, m, n, _p(_f64(w)), _p(fr), _p(lm), _p(_f64(q)), float(lam), float(eps),
-                         _p(state.y), _p(state.B), _p(state.ctr, ctypes.c_int64), _p(s), _p(z), _p(D),
-                         _p(ref, ctypes.c_uint8), _p(dxy), _p(gs), _p(gz))
+                         _p(state.y), _p(state.B), m_nl, stride, _p(state.nl, ctypes.c_int32),
+                         _p(state.ctr, ctypes.c_int64), _p(s), _p(z), _p(D), _p(ref, ctypes.c_uint8), _p(dxy),
+                         _p(gs), _p(gz))
     if st != 0:
         raise RuntimeError(f"oracle close: status {st}")
     return dict(s=s, z=z, D=D, refreshed=ref, dxy=dxy, dsdx=gs, dzdx=gz, state=state)

@@ -17,6 +17,11 @@
  *     cited in Section 2;
  *   - floating close structure, Algorithm 2 with Eq. (close_dist) and
  *     Eq. (close_der_dist); refresh when D(x, y) > eps (strictly), y <- x (Section 3.2);
+ *   - the neighbour list (Section 2, Section 3.1 after Eq. der_dist, the end of Section
+ *     3.2, Section 6.2): every L steps the distances to all landmarks are computed and
+ *     the M_nl closest kept; the other steps use only those.  With the close structure
+ *     the list is chosen from the approximate distances, and a reassignment (which
+ *     computes every distance exactly) also chooses it;
  *   - cost model of Section 6.2 ("Theoretical Speedup") and Amdahl's law, Eq. (ahmdal).
  *
  * Everything is double precision, plain loops, one frame / one landmark at a time.
@@ -317,29 +322,51 @@ static void rot_derivative_wrt_x(int n, const double* w, const double* yc, const
   rot_differential(q0, dq, dR);
 }
 
-/* Exact evaluation of one frame (Algorithm 1 over all landmarks).
+/* The landmarks a frame is evaluated against: all M (sel == NULL) or the msel entries of
+ * the neighbour list sel.  Path CVs over the members only (the sums of Eq.
+ * property_map_cv run over the list); D of a landmark outside the list is +infinity. */
+static int member(const int* sel, int k) { return sel ? sel[k] : k; }
+
+static void members_cv(int msel, const int* sel, const double* D, const double* qprop, double lambda,
+                       double* s, double* z, double* p) {
+  double* Dm = (double*)malloc(sizeof(double) * msel);
+  double* qm = (double*)malloc(sizeof(double) * msel);
+  for (int k = 0; k < msel; ++k) {
+    Dm[k] = D[member(sel, k)];
+    qm[k] = qprop[member(sel, k)];
+  }
+  orc_path_cv(msel, Dm, qm, lambda, s, z, p);
+  free(qm);
+  free(Dm);
+}
+
+/* Exact evaluation of one frame (Algorithm 1 over the landmarks of sel, or all).
  * xc: centred frame; lmc: centred landmarks (M x N x 3).  Outputs D (M), R (M x 9,
  * optional), s, z, and gradients ds/dx, dz/dx (N x 3, optional), Eq. (der_dist). */
 int orc_frame_exact(int m, int n, const double* w, const double* xc, const double* lmc,
-                    const double* qprop, double lambda, double* s, double* z, double* D,
-                    double* Rout, double* dsdx, double* dzdx) {
+                    const double* qprop, double lambda, const int* sel, int msel, double* s, double* z,
+                    double* D, double* Rout, double* dsdx, double* dzdx) {
   int st = ORC_OK;
-  double* R = (double*)malloc(sizeof(double) * 9 * m);
-  for (int i = 0; i < m; ++i) {
+  if (!sel) msel = m;
+  double* R = (double*)calloc((size_t)9 * m, sizeof(double));
+  for (int i = 0; i < m; ++i) D[i] = INFINITY;
+  for (int k = 0; k < msel; ++k) {
+    const int i = member(sel, k);
     orc_align_t al;
     if (orc_align_centered(n, w, xc, lmc + (size_t)i * n * 3, &al) != ORC_OK) st = ORC_ENOCONV;
     D[i] = al.D;
     memcpy(R + 9 * i, al.R, sizeof(al.R));
   }
-  double* p = (double*)malloc(sizeof(double) * m);
-  orc_path_cv(m, D, qprop, lambda, s, z, p);
+  double* p = (double*)malloc(sizeof(double) * msel);
+  members_cv(msel, sel, D, qprop, lambda, s, z, p);
   if (dsdx || dzdx) {
     /* Eq. (der_dist): dD_i/dx_k = 2 w_k d_k + w'_k sum_j (-2 w_j d_j) + (rotation term).
      * With R optimal the rotation term vanishes (stationarity of D in R). */
     if (dsdx) memset(dsdx, 0, sizeof(double) * 3 * n);
     if (dzdx) memset(dzdx, 0, sizeof(double) * 3 * n);
     double* d = (double*)malloc(sizeof(double) * 3 * n);
-    for (int i = 0; i < m; ++i) {
+    for (int k0 = 0; k0 < msel; ++k0) {
+      const int i = member(sel, k0);
       const double* a = lmc + (size_t)i * n * 3;
       const double* Ri = R + 9 * i;
       double dsum[3] = {0, 0, 0};
@@ -348,8 +375,8 @@ int orc_frame_exact(int m, int n, const double* w, const double* xc, const doubl
           d[3 * j + b] = xc[3 * j + b] - (Ri[3 * b] * a[3 * j] + Ri[3 * b + 1] * a[3 * j + 1] + Ri[3 * b + 2] * a[3 * j + 2]);
           dsum[b] += -2.0 * w[j] * d[3 * j + b];
         }
-      const double gs = -lambda * p[i] * (qprop[i] - *s); /* ds/dD_i */
-      const double gz = p[i];                           /* dz/dD_i */
+      const double gs = -lambda * p[k0] * (qprop[i] - *s); /* ds/dD_i */
+      const double gz = p[k0];                           /* dz/dD_i */
       for (int k = 0; k < n; ++k)
         for (int b = 0; b < 3; ++b) {
           const double dDi = 2.0 * w[k] * d[3 * k + b] + w[k] * dsum[b];
@@ -370,11 +397,14 @@ int orc_frame_exact(int m, int n, const double* w, const double* xc, const doubl
  * derivative, Eq. (close_der_dist).  al: the alignment of yc onto xc (R_{x y}). */
 int orc_frame_approx(int m, int n, const double* w, const double* xc, const double* yc,
                      const double* B, const double* lmc, const double* qprop, double lambda,
-                     const orc_align_t* al, double* s, double* z, double* D, double* dsdx,
-                     double* dzdx) {
+                     const orc_align_t* al, const int* sel, int msel, double* s, double* z, double* D,
+                     double* dsdx, double* dzdx) {
   const double* Rxy = al->R;
-  double* Q = (double*)malloc(sizeof(double) * 9 * m);
-  for (int i = 0; i < m; ++i) {
+  if (!sel) msel = m;
+  double* Q = (double*)calloc((size_t)9 * m, sizeof(double));
+  for (int i = 0; i < m; ++i) D[i] = INFINITY;
+  for (int k0 = 0; k0 < msel; ++k0) {
+    const int i = member(sel, k0);
     const double* Bi = B + 9 * i;
     double* Qi = Q + 9 * i;
     for (int b = 0; b < 3; ++b)
@@ -389,14 +419,15 @@ int orc_frame_approx(int m, int n, const double* w, const double* xc, const doub
       }
     D[i] = dd;
   }
-  double* p = (double*)malloc(sizeof(double) * m);
-  orc_path_cv(m, D, qprop, lambda, s, z, p);
+  double* p = (double*)malloc(sizeof(double) * msel);
+  members_cv(msel, sel, D, qprop, lambda, s, z, p);
   if (dsdx || dzdx) {
     if (dsdx) memset(dsdx, 0, sizeof(double) * 3 * n);
     if (dzdx) memset(dzdx, 0, sizeof(double) * 3 * n);
     double* dt = (double*)malloc(sizeof(double) * 3 * n);
     double Gs[9] = {0}, Gz[9] = {0}; /* sum_i (dL/dD_i) G_i for L = s and L = z */
-    for (int i = 0; i < m; ++i) {
+    for (int k0 = 0; k0 < msel; ++k0) {
+      const int i = member(sel, k0);
       const double* a = lmc + (size_t)i * n * 3;
       const double* Qi = Q + 9 * i;
       const double* Bi = B + 9 * i;
@@ -412,8 +443,8 @@ int orc_frame_approx(int m, int n, const double* w, const double* xc, const doub
         for (int b = 0; b < 3; ++b)
           for (int c = 0; c < 3; ++c) G[3 * b + c] += -2.0 * w[j] * dt[3 * j + b] * bj[c];
       }
-      const double gs = -lambda * p[i] * (qprop[i] - *s);
-      const double gz = p[i];
+      const double gs = -lambda * p[k0] * (qprop[i] - *s);
+      const double gz = p[k0];
       for (int k = 0; k < n; ++k)
         for (int b = 0; b < 3; ++b) {
           const double dDi = 2.0 * w[k] * dt[3 * k + b] + w[k] * dsum[b];
@@ -476,7 +507,7 @@ int orc_exact(int f, int m, int n, const double* w_in, const double* frames, con
     double* xc = (double*)malloc(sizeof(double) * 3 * n);
     double* Dt = (double*)malloc(sizeof(double) * m);
     orc_center(n, w, frames + (size_t)t * n * 3, xc);
-    int st_t = orc_frame_exact(m, n, w, xc, lmc, q, lambda, s + t, z + t, Dt, NULL,
+    int st_t = orc_frame_exact(m, n, w, xc, lmc, q, lambda, NULL, 0, s + t, z + t, Dt, NULL,
                                dsdx ? dsdx + (size_t)t * n * 3 : NULL, dzdx ? dzdx + (size_t)t * n * 3 : NULL);
     if (D) memcpy(D + (size_t)t * m, Dt, sizeof(double) * m);
     if (st_t != ORC_OK) {
@@ -492,20 +523,89 @@ int orc_exact(int f, int m, int n, const double* w_in, const double* frames, con
   return st;
 }
 
-/* Close-structure state carried between calls.  ctr: [0] has_y, [1] frames,
- * [2] x-y alignments, [3] landmark alignments (exact MSDs), [4] approximate MSDs,
- * [5] threshold refreshes, [6] initial assignments, [7] unused. */
-enum { C_HAS_Y = 0, C_FRAMES, C_XY, C_LMALIGN, C_APPROX, C_REF_THR, C_REF_INIT };
+/* State carried between calls.  ctr: [0] has_y, [1] frames (the step index of the next
+ * frame), [2] x-y alignments, [3] landmark alignments (exact MSDs), [4] approximate MSDs,
+ * [5] threshold refreshes, [6] initial assignments, [7] a neighbour list is held. */
+enum { C_HAS_Y = 0, C_FRAMES, C_XY, C_LMALIGN, C_APPROX, C_REF_THR, C_REF_INIT, C_HAS_NL };
+
+/* Neighbour list: the m_nl landmarks with the smallest distances D_i (ties to the lower
+ * index), written to out in increasing landmark index. */
+void orc_nl_select(int m, const double* D, int m_nl, int* out) {
+  unsigned char* taken = (unsigned char*)calloc((size_t)m, 1);
+  for (int k = 0; k < m_nl; ++k) {
+    int best = -1;
+    for (int i = 0; i < m; ++i)
+      if (!taken[i] && (best < 0 || D[i] < D[best])) best = i;
+    taken[best] = 1;
+  }
+  int c = 0;
+  for (int i = 0; i < m; ++i)
+    if (taken[i]) out[c++] = i;
+  free(taken);
+}
+
+/* Is step `step` a neighbour-list update of the original method: every l_stride steps
+ * from the first, or whenever no list is held yet. */
+static int nl_update_step(int64_t step, int l_stride, const int64_t* ctr) {
+  return !ctr[C_HAS_NL] || step % l_stride == 0;
+}
+
+/* Exact path CVs with a neighbour list (the original method of Section 6.2: distances to
+ * all M landmarks every L steps, to the M_nl listed ones otherwise), frames in time order.
+ * nl_state: m_nl landmark indices carried between calls; ctr as for orc_close (frames,
+ * landmark alignments, has-list).  m_nl <= 0 or >= M: no list. */
+int orc_exact_nl(int f, int m, int n, const double* w_in, const double* frames, const double* lm,
+                 const double* q_in, double lambda, int m_nl, int l_stride, int* nl_state, int64_t* ctr,
+                 double* s, double* z, double* D, double* dsdx, double* dzdx) {
+  if (f < 0 || m < 1 || n < 1 || !(lambda > 0.0) || l_stride < 1) return ORC_EINVAL;
+  const int use_nl = m_nl > 0 && m_nl < m;
+  double* w = (double*)malloc(sizeof(double) * n);
+  double* q = (double*)malloc(sizeof(double) * m);
+  normalise_weights(n, w_in, w);
+  default_props(m, q_in, q);
+  double* lmc = centred_copy(m, n, w, lm);
+  double* xc = (double*)malloc(sizeof(double) * 3 * n);
+  double* Dt = (double*)malloc(sizeof(double) * m);
+  int st = ORC_OK;
+  for (int t = 0; t < f; ++t) {
+    orc_center(n, w, frames + (size_t)t * n * 3, xc);
+    const int update = !use_nl || nl_update_step(ctr[C_FRAMES], l_stride, ctr);
+    const int* sel = update ? NULL : nl_state;
+    const int msel = update ? m : m_nl;
+    if (orc_frame_exact(m, n, w, xc, lmc, q, lambda, sel, msel, s + t, z + t, Dt, NULL,
+                        dsdx ? dsdx + (size_t)t * n * 3 : NULL, dzdx ? dzdx + (size_t)t * n * 3 : NULL) != ORC_OK)
+      st = ORC_ENOCONV;
+    if (use_nl && update) {
+      orc_nl_select(m, Dt, m_nl, nl_state);
+      ctr[C_HAS_NL] = 1;
+    }
+    ctr[C_LMALIGN] += msel;
+    ctr[C_FRAMES] += 1;
+    if (D) memcpy(D + (size_t)t * m, Dt, sizeof(double) * m);
+  }
+  free(Dt);
+  free(xc);
+  free(lmc);
+  free(q);
+  free(w);
+  return st;
+}
 
 /* Floating close structure, Algorithm 2, frames in time order.
  * y_state: N x 3 centred close structure; B_state: M x 9 rotations R_{a_i y}.
  * refreshed[t]: 0 approximate, 1 refresh (D(x,y) > eps), 2 initial assignment.
- * dxy[t]: D(x_t, y) that decided frame t (-1 at an initial assignment). */
+ * dxy[t]: D(x_t, y) that decided frame t (-1 at an initial assignment).
+ * Neighbour list (m_nl in 1..M-1, else none): at a reassignment every distance is exact
+ * and the list is chosen from them; at the other update steps (every l_stride steps) the
+ * distances to all landmarks are the approximate ones of Eq. (close_dist) and the list is
+ * chosen from those (end of Section 3.2); in between only the listed landmarks are
+ * evaluated.  nl_state: m_nl indices carried between calls. */
 int orc_close(int f, int m, int n, const double* w_in, const double* frames, const double* lm,
               const double* q_in, double lambda, double eps, double* y_state, double* B_state,
-              int64_t* ctr, double* s, double* z, double* D, uint8_t* refreshed, double* dxy,
-              double* dsdx, double* dzdx) {
-  if (f < 0 || m < 1 || n < 1 || !(lambda > 0.0) || !(eps >= 0.0)) return ORC_EINVAL;
+              int m_nl, int l_stride, int* nl_state, int64_t* ctr, double* s, double* z, double* D,
+              uint8_t* refreshed, double* dxy, double* dsdx, double* dzdx) {
+  if (f < 0 || m < 1 || n < 1 || !(lambda > 0.0) || !(eps >= 0.0) || l_stride < 1) return ORC_EINVAL;
+  const int use_nl = m_nl > 0 && m_nl < m;
   double* w = (double*)malloc(sizeof(double) * n);
   double* q = (double*)malloc(sizeof(double) * m);
   normalise_weights(n, w_in, w);
@@ -531,17 +631,25 @@ int orc_close(int f, int m, int n, const double* w_in, const double* frames, con
       if (dxy) dxy[t] = al.D;
       if (al.D > eps) refresh = 1;
     }
+    const int update = !use_nl || refresh || nl_update_step(ctr[C_FRAMES], l_stride, ctr);
     if (refresh) {
       /* reassign: exact distances to all landmarks, save R_{a_i x}, y <- x */
-      if (orc_frame_exact(m, n, w, xc, lmc, q, lambda, s + t, z + t, Dt, Rt, gs, gz) != ORC_OK) st = ORC_ENOCONV;
+      if (orc_frame_exact(m, n, w, xc, lmc, q, lambda, NULL, m, s + t, z + t, Dt, Rt, gs, gz) != ORC_OK)
+        st = ORC_ENOCONV;
       memcpy(B_state, Rt, sizeof(double) * 9 * m);
       memcpy(y_state, xc, sizeof(double) * 3 * n);
       ctr[C_HAS_Y] = 1;
       ctr[C_LMALIGN] += m;
       ctr[refresh == 1 ? C_REF_THR : C_REF_INIT] += 1;
     } else {
-      orc_frame_approx(m, n, w, xc, y_state, B_state, lmc, q, lambda, &al, s + t, z + t, Dt, gs, gz);
-      ctr[C_APPROX] += m;
+      const int* sel = update ? NULL : nl_state;
+      const int msel = update ? m : m_nl;
+      orc_frame_approx(m, n, w, xc, y_state, B_state, lmc, q, lambda, &al, sel, msel, s + t, z + t, Dt, gs, gz);
+      ctr[C_APPROX] += msel;
+    }
+    if (use_nl && update) {
+      orc_nl_select(m, Dt, m_nl, nl_state);
+      ctr[C_HAS_NL] = 1;
     }
     if (refreshed) refreshed[t] = (uint8_t)refresh;
     if (D) memcpy(D + (size_t)t * m, Dt, sizeof(double) * m);
