@@ -80,6 +80,21 @@ DETAILS = {
     "c5_batched_fp16": ("config", dict(label="close-structure path CV, N=5000, M=2000, F=10000, fp16 landmark storage",
                                        seed=5, n=5000, m=2000, f=10_000, eps=0.05, grad=False, precision="fp16",
                                        steps=1)),
+    # the paper's second data set in size (304 atoms, 2120 landmarks, a neighbour list of 50
+    # updated every 50 steps): the original method with and without the list, and the
+    # close structure with the list
+    "nl_exact_m2120": ("config", dict(label="exact path CV with gradients, N=304, M=2120, F=10000, FP32, "
+                                            "neighbour list 50 every 50 steps", seed=8, n=304, m=2120, f=10_000,
+                                      eps=-1.0, grad=True, precision="fp32", nl=(50, 50))),
+    "nl_exact_m2120_nolist": ("config", dict(label="exact path CV with gradients, N=304, M=2120, F=10000, FP32, "
+                                                   "no neighbour list", seed=8, n=304, m=2120, f=10_000, eps=-1.0,
+                                             grad=True, precision="fp32")),
+    "nl_close_m2120": ("config", dict(label="close-structure path CV with gradients, N=304, M=2120, F=10000, FP32, "
+                                            "eps=0.05, neighbour list 50 every 50 steps", seed=8, n=304, m=2120,
+                                      f=10_000, eps=0.05, grad=True, precision="fp32", nl=(50, 50))),
+    "nl_close_m2120_nolist": ("config", dict(label="close-structure path CV with gradients, N=304, M=2120, F=10000, "
+                                                   "FP32, eps=0.05, no neighbour list", seed=8, n=304, m=2120,
+                                             f=10_000, eps=0.05, grad=True, precision="fp32")),
 }
 
 
@@ -218,9 +233,10 @@ def lambda_from_gpu(pcv, lm):
 
 
 def time_config(pcv, label: str, seed: int, n: int, m: int, f: int, eps: float, grad: bool, precision: str,
-                noise: float = 0.05, steps: int = 3, schedule: str = "drift") -> dict:
+                noise: float = 0.05, steps: int = 3, schedule: str = "drift", nl=None) -> dict:
     """One side measurement: a fresh context on seeded synthetic inputs of the given sizes,
-    2 untimed evaluations, then `steps` timed ones (CUDA events on the context's stream)."""
+    2 untimed evaluations, then `steps` timed ones (CUDA events on the context's stream).
+    nl = (M_nl, L): neighbour list of M_nl landmarks updated every L steps."""
     import torch
     from paper_1801_02362_gb300 import synth
 
@@ -230,7 +246,7 @@ def time_config(pcv, label: str, seed: int, n: int, m: int, f: int, eps: float, 
     lm, fr = synth.make_problem(seed, n_atoms=n, n_landmarks=m, n_frames=f, frame_noise=noise, schedule=schedule,
                                 frame_dtype=sdt, landmark_dtype=ldt)
     lam = lambda_from_gpu(pcv, lm)
-    ctx = pcv.PathCV(lm, lam, eps=eps, precision=precision)
+    ctx = pcv.PathCV(lm, lam, eps=eps, precision=precision, neighbor_list=nl)
     frames = torch.tensor(np.ascontiguousarray(fr), dtype=dt, device="cuda")
     for _ in range(2):
         pcv.pcv_reset_close_state(ctx.ctx)
@@ -251,10 +267,16 @@ def time_config(pcv, label: str, seed: int, n: int, m: int, f: int, eps: float, 
     pr = ctx.profile()
     st = ctx.stats()
     ctx.close()
-    return {"workload": label, "atoms": n, "landmarks": m, "frames": f, "eps_nm2": eps, "precision": precision,
-            "gradients": grad, "ms_per_step": t, "frames_per_s": f / (t / 1e3),
-            "msds_per_s": f * m / (t / 1e3), "exact_msds": st["landmark_alignments"], "approx_msds": st["approx_msds"],
-            "kernel_ms": {k: round(v[0] / steps, 4) for k, v in pr.items()}}
+    out = {"workload": label, "atoms": n, "landmarks": m, "frames": f, "eps_nm2": eps, "precision": precision,
+           "gradients": grad, "ms_per_step": t, "frames_per_s": f / (t / 1e3),
+           "msds_per_s": (st["landmark_alignments"] + st["approx_msds"]) / (t / 1e3),
+           "exact_msds": st["landmark_alignments"], "approx_msds": st["approx_msds"],
+           "kernel_ms": {k: round(v[0] / steps, 4) for k, v in pr.items()}}
+    if nl is not None:
+        out["neighbor_list"] = {"size": nl[0], "stride": nl[1]}
+    # expensive distance computations per step (the cost model of the paper's Section 6.2)
+    out["expensive_per_step"] = (st["xy_alignments"] + st["landmark_alignments"]) / f
+    return out
 
 
 def time_stream(pcv, precision: str, n: int = 5000, m: int = 2000, calls: int = 200, eps: float = 0.05,

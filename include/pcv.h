@@ -121,6 +121,24 @@ PCV_API pcv_status pcv_set_lambda(pcv_ctx* ctx, double lambda);
  * (Algorithm 1 for every frame).  Changing eps keeps the current close structure. */
 PCV_API pcv_status pcv_set_close_threshold(pcv_ctx* ctx, double eps);
 
+/* Neighbour list (Section 2; Section 3.1 after Eq. der_dist; end of Section 3.2; the cost
+ * model of Section 6.2).  size = M_nl landmarks kept, stride = L steps between updates.
+ * Steps are counted from the last pcv_reset_close_state / pcv_set_landmarks (the
+ * `frames` counter of pcv_stats).  A step is an update step when its index is a multiple
+ * of L, when no list is held yet, and, in close mode, at every close-structure
+ * reassignment.  At an update step the distances to all M landmarks are computed (exact
+ * mode and reassignments: exactly; other close-mode steps: the approximate distances of
+ * Eq. close_dist), s and z use all of them, and the list becomes the M_nl landmarks with
+ * the smallest distances (ties to the lower index).  Between updates only the listed
+ * landmarks are evaluated and the sums of Eq. (property_map_cv), z and the derivatives run
+ * over them; the other entries of msd are +infinity.  size = 0 or size >= M evaluates
+ * every landmark at every step (the default).  Setting the list drops the list held (the
+ * next step is an update).  In FP32 / FP16 storage the choice is made on the FP32
+ * distances, so a landmark whose distance ties the M_nl-th smallest within FP32 rounding
+ * may be chosen differently from an FP64 evaluation.
+ * Errors: PCV_EINVAL (size < 0, stride < 1). */
+PCV_API pcv_status pcv_set_neighbor_list(pcv_ctx* ctx, int size, int stride);
+
 /* Evaluate F frames (time-ordered consecutive MD steps in close mode).
  *   frames     device, F*N*3 (double in PCV_FP64, else float), uncentred;
  *   s, z       device, F doubles each, required: the path CV s of Eq. (property_map_cv)
@@ -130,7 +148,8 @@ PCV_API pcv_status pcv_set_close_threshold(pcv_ctx* ctx, double eps);
  *              from Eq. (der_dist) (exact and reassignment frames) and
  *              Eq. (close_der_dist) (approximate frames);
  *   msd        device, F*M doubles, or NULL: D(x_t, a_i) (Eq. dist) or its close-structure
- *              approximation (Eq. close_dist);
+ *              approximation (Eq. close_dist); +infinity for landmarks outside the
+ *              neighbour list between list updates (pcv_set_neighbor_list);
  *   refreshed  device, F bytes, or NULL: 0 approximate frame, 1 close structure reassigned
  *              because D(x, y) > eps, 2 initial assignment (exact mode: all 1).
  * In close mode the close structure y and the rotations R_{a_i y} carry over between
@@ -153,17 +172,19 @@ PCV_API pcv_status pcv_evaluate_host(pcv_ctx* ctx, int F, const void* frames, do
 PCV_API pcv_status pcv_combine_grad(pcv_ctx* ctx, int F, const double* g_s, const double* g_z,
                             const void* dsdx, const void* dzdx, void* out);
 
-/* Forget the close structure: the next frame is an initial assignment.  Clears the
- * counters except host_syncs and kernel_launches, which count over the context's life. */
+/* Forget the close structure and the neighbour list: the next frame is an initial
+ * assignment and a list update, and the step count restarts at 0.  Clears the counters
+ * except host_syncs and kernel_launches, which count over the context's life. */
 PCV_API pcv_status pcv_reset_close_state(pcv_ctx* ctx);
 
-/* Serialise the close-structure state (y, R_{a_i y}, counters) into host memory.
+/* Serialise the close-structure state (y, R_{a_i y}, counters including the step count,
+ * the neighbour list held) into host memory.
  * If buf is NULL, *len receives the size needed.  Errors: PCV_EINVAL if *len is too
  * small. */
 PCV_API pcv_status pcv_save_state(pcv_ctx* ctx, void* buf, size_t* len);
 
-/* Restore a state written by pcv_save_state for the same landmarks, N, M and precision.
- * Errors: PCV_ESTATE if the blob does not match. */
+/* Restore a state written by pcv_save_state for the same landmarks, N, M, precision and
+ * neighbour-list size.  Errors: PCV_ESTATE if the blob does not match. */
 PCV_API pcv_status pcv_load_state(pcv_ctx* ctx, const void* buf, size_t len);
 
 /* Copy the counters.  Synchronises the context's stream. */
@@ -203,7 +224,7 @@ PCV_API pcv_status pcv_set_option(pcv_ctx* ctx, int key, int64_t value);
  * between events recorded around each launch on the context's stream, and launch counts.
  * ms and launches are host arrays of n entries (n <= PCV_PROFILE_KERNELS).  Synchronises
  * the stream, then clears the collected timings. */
-#define PCV_PROFILE_KERNELS 20
+#define PCV_PROFILE_KERNELS 24
 PCV_API pcv_status pcv_get_profile(pcv_ctx* ctx, int n, double* ms, int64_t* launches);
 
 /* Name of kernel family `id` ("" outside 0..PCV_PROFILE_KERNELS-1). */

@@ -31,6 +31,7 @@ struct Small {
   int recheck_count;
   int last_refresh;
   int pad;
+  int nl_counts[4];  // neighbour list: updates, approximate updates, frames between updates
   float4 last_c32;
   double4 last_c64;
   double last_G;
@@ -55,12 +56,15 @@ thread_local int64_t t_launches = 0;
 // kernel families timed by the profiler
 enum KernelId {
   K_PREP = 0, K_BAND, K_RECHECK, K_SCAN, K_CHUNK, K_FIRST, K_RECORDS, K_COMPACT, K_EXACT, K_APPROX,
-  K_FINAL, K_ADJ_BETA, K_ADJ_FINISH, K_COMBINE, K_XY_REFINE, K_ADJ_BETA_SEG, K_MATERIALIZE, K_GAMMA, K_ADJ_MMA, K_SEG_MOMENTS, K_COUNT
+  K_FINAL, K_ADJ_BETA, K_ADJ_FINISH, K_COMBINE, K_XY_REFINE, K_ADJ_BETA_SEG, K_MATERIALIZE, K_GAMMA, K_ADJ_MMA, K_SEG_MOMENTS,
+  K_NL_SCHEDULE, K_NL_SELECT, K_NL_PAIR, K_NL_BETA, K_COUNT
 };
 const char* const kKernelNames[PCV_PROFILE_KERNELS] = {
     "frame_prep", "align_band", "recheck_fp64", "band_scan", "align_chunk", "first_exceed", "records",
     "compact", "exact_pair", "approx_pair", "finalize", "adjoint_beta_pair", "adjoint_finish", "combine_grad", "xy_refine",
-    "adjoint_beta_seg", "materialize", "gamma", "adjoint_beta_mma", "seg_moments"};
+    "adjoint_beta_seg", "materialize", "gamma", "adjoint_beta_mma", "seg_moments", "nl_schedule", "nl_select",
+    "nl_pair", "nl_beta"};
+static_assert(K_COUNT <= PCV_PROFILE_KERNELS, "profiler table");
 
 struct ProfEvent {
   int id;
@@ -91,6 +95,11 @@ struct pcv_ctx {
   int64_t mat_cap = int64_t(2) << 30;  // bytes of materialised operands allowed (PCV_OPT_MATERIALIZE)
   bool tensor_cores = true;             // segment adjoint on the tensor cores (PCV_OPT_TENSOR_CORES)
   double gap_estimate = 0.0;
+  // neighbour list: size M_nl (0 = none) and update stride L; the list held between calls
+  int nl_size = 0, nl_stride = 1;
+  bool has_nl = false;
+  DevBuf nl_keep;
+  DevBuf nlSlot, nlUpd, nlU, nlUA, nlUAseg, nlN, NLtab, Rupd, Rnl;
   // close state
   bool has_y = false;
   DevBuf y, Bprior;
@@ -286,7 +295,9 @@ pcv_status pcv_destroy(pcv_ctx* c) {
                     &c->fG, &c->bandD, &c->bandQ, &c->bandF, &c->chD, &c->chQ, &c->chF, &c->rlist, &c->rcount,
                     &c->recF, &c->recRef, &c->recD, &c->recQ, &c->reflist, &c->segof, &c->alist, &c->aseg,
                     &c->Dbuf, &c->Rpair, &c->Bseg, &c->Xr, &c->Bm, &c->GSb, &c->GZb, &c->Nx, &c->Nb, &c->Yc, &c->Gsum, &c->Amma, &c->Bmma, &c->S6, &c->mstat, &c->status, &c->nrecheck, &c->small, &c->h_frames,
-                    &c->h_s, &c->h_z, &c->h_gs, &c->h_gz, &c->h_msd, &c->h_ref, &c->grp_inst, &c->grp_tiles};
+                    &c->h_s, &c->h_z, &c->h_gs, &c->h_gz, &c->h_msd, &c->h_ref, &c->grp_inst, &c->grp_tiles,
+                    &c->nl_keep, &c->nlSlot, &c->nlUpd, &c->nlU, &c->nlUA, &c->nlUAseg, &c->nlN, &c->NLtab,
+                    &c->Rupd, &c->Rnl};
   if (c->grp_stream) cudaStreamSynchronize(c->grp_stream);
   for (DevBuf* b : bufs) release(*b);
   if (c->grp_exec) cudaGraphExecDestroy(c->grp_exec);
@@ -356,9 +367,20 @@ pcv_status pcv_set_option(pcv_ctx* c, int key, int64_t value) {
   }
 }
 
+pcv_status pcv_set_neighbor_list(pcv_ctx* c, int size, int stride) {
+  if (!c) return fail(nullptr, PCV_EINVAL, "NULL context");
+  if (size < 0) return fail(c, PCV_EINVAL, "neighbour-list size must be >= 0");
+  if (stride < 1) return fail(c, PCV_EINVAL, "neighbour-list stride must be >= 1");
+  c->nl_size = size;
+  c->nl_stride = stride;
+  c->has_nl = false;
+  return PCV_OK;
+}
+
 pcv_status pcv_reset_close_state(pcv_ctx* c) {
   if (!c) return fail(nullptr, PCV_EINVAL, "NULL context");
   c->has_y = false;  // the gap estimate is a tuning statistic and survives the reset
+  c->has_nl = false;
   const int64_t syncs = c->stats.host_syncs, launches = c->stats.kernel_launches;
   c->stats = pcv_stats{};
   c->stats.host_syncs = syncs;  // cumulative over the context's lifetime
@@ -536,6 +558,44 @@ FrameRec frame_rec(pcv_ctx* c) {
   return r;
 }
 
+// Neighbour list in force: a size strictly between 0 and M (otherwise every landmark is
+// evaluated at every step).
+bool nl_active(const pcv_ctx* c) { return c->nl_size > 0 && c->nl_size < c->M; }
+
+pcv_status ensure_nl_workspace(pcv_ctx* c, int F, bool exact_grads) {
+  const size_t Mnl = c->nl_size;
+  pcv_status st;
+  if ((st = ensure(c, c->nl_keep, sizeof(int) * Mnl)) != PCV_OK) return st;
+  if ((st = ensure(c, c->nlSlot, sizeof(int) * F)) != PCV_OK) return st;
+  if ((st = ensure(c, c->nlUpd, F)) != PCV_OK) return st;
+  if ((st = ensure(c, c->nlU, sizeof(int) * F)) != PCV_OK) return st;
+  if ((st = ensure(c, c->nlUA, sizeof(int) * F)) != PCV_OK) return st;
+  if ((st = ensure(c, c->nlUAseg, sizeof(int) * F)) != PCV_OK) return st;
+  if ((st = ensure(c, c->nlN, sizeof(int) * F)) != PCV_OK) return st;
+  if ((st = ensure(c, c->NLtab, sizeof(int) * Mnl * ((size_t)F + 1))) != PCV_OK) return st;
+  if (exact_grads && (st = ensure(c, c->Rnl, work_elem(c->prec) * 9 * Mnl * (size_t)F)) != PCV_OK) return st;
+  return PCV_OK;
+}
+
+NlLists nl_lists(pcv_ctx* c) {
+  NlLists nl;
+  nl.slot = (int*)c->nlSlot.p;
+  nl.upd = (uint8_t*)c->nlUpd.p;
+  nl.ulist = (int*)c->nlU.p;
+  nl.uapp_list = (int*)c->nlUA.p;
+  nl.uapp_seg = (int*)c->nlUAseg.p;
+  nl.nlist = (int*)c->nlN.p;
+  nl.counts = ((Small*)c->small.p)->nl_counts;
+  return nl;
+}
+
+// the carried-over list is slot 0 of the table
+pcv_status nl_stage_carried(pcv_ctx* c) {
+  if (!c->has_nl) return PCV_OK;
+  CUDA_TRY(c, cudaMemcpyAsync(c->NLtab.p, c->nl_keep.p, sizeof(int) * c->nl_size, cudaMemcpyDeviceToDevice, c->stream));
+  return PCV_OK;
+}
+
 // Algorithm 2 over F frames: decide every frame (reassignment / approximate and its close
 // structure), then evaluate reassignment frames exactly and the rest approximately.
 pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, double* z, void* gs, void* gz,
@@ -657,10 +717,24 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
                    &sm->approx_count, (int*)c->aseg.p, 0, st);
   }
   small_tail_kernel<<<1, 1, 0, st>>>(sm, (const int*)c->reflist.p, fi.c32, fi.c64, fi.G);
-  pcv_status ps = sync_small(c);
+  // neighbour list: update frames are the reassignments and every L-th step
+  const bool nl = nl_active(c);
+  const int Mnl = c->nl_size;
+  pcv_status ps;
+  if (nl && (ps = ensure_nl_workspace(c, F, false)) != PCV_OK) return ps;
+  const NlLists nll = nl ? nl_lists(c) : NlLists{};  // after the workspace exists
+  if (nl) {
+    PROF(c, K_NL_SCHEDULE);
+    launch_nl_schedule(F, (long long)c->stats.frames, c->nl_stride, c->has_nl, rec.flag, (const int*)c->segof.p, nll,
+                       st);
+  }
+  ps = sync_small(c);
   if (ps != PCV_OK) return ps;
   const int nref = c->small_host->refresh_count;
   const int napp = c->small_host->approx_count;
+  const int nl_upd = nl ? c->small_host->nl_counts[0] : 0;
+  const int nl_uapp = nl ? c->small_host->nl_counts[1] : 0;
+  const int nl_between = nl ? c->small_host->nl_counts[2] : 0;
   const size_t seg_bytes = work_elem(c->prec) * 9 * (size_t)M;
   if ((ps = ensure(c, c->Bseg, seg_bytes * (size_t)(nref + 1))) != PCV_OK) return ps;
   if (had_prior) CUDA_TRY(c, cudaMemcpyAsync(c->Bseg.p, c->Bprior.p, seg_bytes, cudaMemcpyDeviceToDevice, st));
@@ -669,7 +743,7 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
   // segment GEMM form of the adjoint, and with FP32 arithmetic and uniform weights the
   // materialised operands x' and b when they fit the cap.
   const bool grads = gs && gz;
-  const bool seg_form = (int64_t)(nref + 1) * 16 <= (int64_t)F;
+  const bool seg_form = (int64_t)(nref + 1) * 16 <= (int64_t)F && !nl;
   const int seg_base = had_prior ? 0 : 1;  // without a prior structure segment 0 is empty
   const int nseg = nref + 1 - seg_base;
   bool tiled = false, mma = false;
@@ -714,7 +788,21 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
     launch_materialize_frames(napp, &sm->approx_count, (const int*)c->alist.p, (const int*)c->aseg.p, seg_base, L,
                               frames, fi, rec.qxy, (const float*)c->Yc.p, (float*)c->Xr.p, (float*)c->Nx.p, st);
   }
-  {
+  if (nl) {
+    {  // all-landmark approximate distances of the update frames that are not reassignments
+      PROF(c, K_APPROX);
+      launch_approx_pairs(c->prec, nl_uapp, nll.uapp_list, nll.uapp_seg, &nll.counts[1], frames, L, fi, rec.qxy,
+                          c->Bseg.p, c->Dbuf.p, st);
+    }
+    {
+      PROF(c, K_NL_SELECT);
+      launch_nl_select(c->prec, nl_upd, nll, M, Mnl, c->Dbuf.p, (int*)c->NLtab.p, st);
+    }
+    if ((ps = nl_stage_carried(c)) != PCV_OK) return ps;
+    PROF(c, K_NL_PAIR);
+    launch_nl_approx(c->prec, nl_between, nll, (const int*)c->NLtab.p, Mnl, frames, L, fi, rec.qxy, c->Bseg.p,
+                     (const int*)c->segof.p, c->Dbuf.p, st);
+  } else {
     PROF(c, K_APPROX);
     if (tiled)
       launch_approx_pairs_tile(napp, (const int*)c->alist.p, (const int*)c->aseg.p, &sm->approx_count, seg_base, L,
@@ -730,7 +818,16 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
                     gs != nullptr, st);
   }
   if (refreshed) CUDA_TRY(c, cudaMemcpyAsync(refreshed, rec.flag, F, cudaMemcpyDeviceToDevice, st));
-  if (grads) {
+  if (grads && nl) {
+    {
+      PROF(c, K_NL_BETA);
+      launch_nl_beta(c->prec, F, nll, (const int*)c->NLtab.p, Mnl, L, c->Dbuf.p, s, c->lambda, nullptr, nullptr,
+                     c->Bseg.p, (const int*)c->segof.p, gs, gz, st);
+    }
+    PROF(c, K_ADJ_FINISH);
+    launch_adjoint_finish(c->prec, F, frames, L, fi, c->Dbuf.p, s, c->lambda, c->Bseg.p, (const int*)c->segof.p, rec,
+                          prior, gs, gz, st);
+  } else if (grads) {
     if (mma) {
       {
         PROF(c, K_GAMMA);
@@ -782,12 +879,81 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
     c->y_G = c->small_host->last_G;
     c->has_y = true;
   }
+  if (nl) {
+    launch_nl_carry(nll, (const int*)c->NLtab.p, Mnl, (int*)c->nl_keep.p, st);
+    c->has_nl = true;
+  }
   c->stats.frames += F;
   c->stats.xy_alignments += had_prior ? F : F - 1;
   c->stats.landmark_alignments += (int64_t)M * nref;
-  c->stats.approx_msds += (int64_t)M * napp;
+  c->stats.approx_msds += nl ? (int64_t)M * nl_uapp + (int64_t)Mnl * nl_between : (int64_t)M * napp;
   c->stats.refreshes_initial += had_prior ? 0 : 1;
   c->stats.refreshes_threshold += nref - (had_prior ? 0 : 1);
+  return PCV_OK;
+}
+
+// Original method with a neighbour list (Section 6.2): all M landmarks at every L-th step,
+// the M_nl listed ones in between.  The update frames follow from the step counter alone,
+// so the host knows their number without a device round trip.
+pcv_status evaluate_exact_nl(pcv_ctx* c, int F, const void* frames, double* s, double* z, void* gs, void* gz,
+                             double* msd, uint8_t* refreshed) {
+  const cudaStream_t st = c->stream;
+  const LandmarkDev L = lm_view(c);
+  const FrameInfo fi = frame_info(c);
+  const bool grads = gs && gz;
+  const int M = c->M, Mnl = c->nl_size, Ls = c->nl_stride;
+  const long long step0 = (long long)c->stats.frames;
+  int nupd = 0;
+  for (int t = 0; t < F; ++t)
+    if ((step0 + t) % Ls == 0 || (t == 0 && !c->has_nl)) ++nupd;
+  pcv_status ps = ensure_nl_workspace(c, F, grads);
+  if (ps != PCV_OK) return ps;
+  if (grads && (ps = ensure(c, c->Rupd, work_elem(c->prec) * 9 * (size_t)M * nupd)) != PCV_OK) return ps;
+  const NlLists nll = nl_lists(c);
+  {
+    PROF(c, K_PREP);
+    launch_frame_prep(c->prec, F, frames, L, fi, st);
+  }
+  {
+    PROF(c, K_NL_SCHEDULE);
+    launch_nl_schedule(F, step0, Ls, c->has_nl, nullptr, nullptr, nll, st);
+  }
+  {
+    PROF(c, K_EXACT);
+    launch_exact_pairs(c->prec, nupd, nll.ulist, nullptr, frames, L, fi, c->Dbuf.p, grads ? c->Rupd.p : nullptr,
+                       (unsigned*)c->status.p, st);
+  }
+  {
+    PROF(c, K_NL_SELECT);
+    launch_nl_select(c->prec, nupd, nll, M, Mnl, c->Dbuf.p, (int*)c->NLtab.p, st);
+  }
+  if ((ps = nl_stage_carried(c)) != PCV_OK) return ps;
+  {
+    PROF(c, K_NL_PAIR);
+    launch_nl_exact(c->prec, F - nupd, nll, (const int*)c->NLtab.p, Mnl, frames, L, fi, c->Dbuf.p,
+                    grads ? c->Rnl.p : nullptr, (unsigned*)c->status.p, st);
+  }
+  {
+    PROF(c, K_FINAL);
+    launch_finalize(c->prec, F, M, c->Dbuf.p, L.q, L.q32, c->lambda, s, z, (float*)c->mstat.p, (double*)c->mstat.p,
+                    msd, grads, st);
+  }
+  if (refreshed) launch_fill_u8(refreshed, 1, (size_t)F, st);
+  if (grads) {
+    {
+      PROF(c, K_NL_BETA);
+      launch_nl_beta(c->prec, F, nll, (const int*)c->NLtab.p, Mnl, L, c->Dbuf.p, s, c->lambda, c->Rupd.p, c->Rnl.p,
+                     nullptr, nullptr, gs, gz, st);
+    }
+    PROF(c, K_ADJ_FINISH);
+    FrameRec none;
+    RefDesc nop;
+    launch_adjoint_finish(c->prec, F, frames, L, fi, c->Dbuf.p, s, c->lambda, nullptr, nullptr, none, nop, gs, gz, st);
+  }
+  launch_nl_carry(nll, (const int*)c->NLtab.p, Mnl, (int*)c->nl_keep.p, st);
+  c->has_nl = true;
+  c->stats.frames += F;
+  c->stats.landmark_alignments += (int64_t)M * nupd + (int64_t)Mnl * (F - nupd);
   return PCV_OK;
 }
 
@@ -841,11 +1007,12 @@ pcv_status pcv_evaluate(pcv_ctx* c, int F, const void* frames, double* s, double
   if ((size_t)F * c->M > ((size_t)1 << 40)) return fail(c, PCV_EINVAL, "F*M too large");
   cudaSetDevice(c->device);
   const bool close = c->eps >= 0.0;
-  pcv_status st = ensure_frame_workspace(c, F, close, dsdx != nullptr);
+  pcv_status st = ensure_frame_workspace(c, F, close, dsdx != nullptr && !nl_active(c));
   if (st != PCV_OK) return st;
   const int64_t launches0 = t_launches;
   st = close ? evaluate_close(c, F, frames, s, z, dsdx, dzdx, msd, refreshed)
-             : evaluate_exact(c, F, frames, s, z, dsdx, dzdx, msd, refreshed);
+             : (nl_active(c) ? evaluate_exact_nl(c, F, frames, s, z, dsdx, dzdx, msd, refreshed)
+                             : evaluate_exact(c, F, frames, s, z, dsdx, dzdx, msd, refreshed));
   c->stats.kernel_launches += t_launches - launches0;
   if (st != PCV_OK) return st;
   cudaError_t e = cudaGetLastError();
@@ -874,7 +1041,7 @@ pcv_status pcv_evaluate_group(pcv_ctx* const* ctxs, int n, const pcv_batch_io* i
     if ((b.dsdx == nullptr) != (b.dzdx == nullptr)) return fail(lead, PCV_EINVAL, "entry %d: dsdx and dzdx", k);
     if ((size_t)b.F * c->M > ((size_t)1 << 40)) return fail(lead, PCV_EINVAL, "entry %d: F*M too large", k);
     // the persistent path covers exact mode without gradients in the FP32 modes, one storage type
-    if (c->eps >= 0.0 || b.dsdx || c->prec == P_F64 || c->prec != lead->prec) persistent = false;
+    if (c->eps >= 0.0 || b.dsdx || c->prec == P_F64 || c->prec != lead->prec || nl_active(c)) persistent = false;
   }
   cudaSetDevice(lead->device);
   const cudaStream_t user = (cudaStream_t)stream;
@@ -1127,11 +1294,13 @@ pcv_status pcv_get_stats(pcv_ctx* c, pcv_stats* out) {
   return PCV_OK;
 }
 
-// state blob: header, then y (N*3 frame type), B (M*9 work type)
+// state blob: header, then y (N*3 frame type), B (M*9 work type), the neighbour list
+// (nl_size ints)
 namespace {
 struct StateHeader {
   char magic[8];
   int32_t version, prec, M, N, has_y, pad;
+  int32_t nl_size, has_nl;
   float4 y_c32;
   double4 y_c64;
   double y_G;
@@ -1145,7 +1314,8 @@ pcv_status pcv_save_state(pcv_ctx* c, void* buf, size_t* len) {
   if (!c->have_lm) return fail(c, PCV_ESTATE, "landmarks not set");
   const size_t ybytes = frame_elem(c->prec) * 3 * (size_t)c->N;
   const size_t bbytes = work_elem(c->prec) * 9 * (size_t)c->M;
-  const size_t need = sizeof(StateHeader) + ybytes + bbytes;
+  const size_t lbytes = sizeof(int) * (size_t)c->nl_size;
+  const size_t need = sizeof(StateHeader) + ybytes + bbytes + lbytes;
   if (!buf) {
     *len = need;
     return PCV_OK;
@@ -1156,8 +1326,10 @@ pcv_status pcv_save_state(pcv_ctx* c, void* buf, size_t* len) {
   if (st != PCV_OK) return st;
   StateHeader h{};
   memcpy(h.magic, "PCVSTAT", 8);
-  h.version = 1;
+  h.version = 2;
   h.prec = (int)c->prec;
+  h.nl_size = c->nl_size;
+  h.has_nl = c->has_nl ? 1 : 0;
   h.M = c->M;
   h.N = c->N;
   h.has_y = c->has_y ? 1 : 0;
@@ -1174,6 +1346,10 @@ pcv_status pcv_save_state(pcv_ctx* c, void* buf, size_t* len) {
   } else {
     memset(out + sizeof(h), 0, ybytes + bbytes);
   }
+  if (c->has_nl)
+    CUDA_TRY(c, cudaMemcpy(out + sizeof(h) + ybytes + bbytes, c->nl_keep.p, lbytes, cudaMemcpyDeviceToHost));
+  else
+    memset(out + sizeof(h) + ybytes + bbytes, 0, lbytes);
   *len = need;
   return PCV_OK;
 }
@@ -1186,8 +1362,16 @@ pcv_status pcv_load_state(pcv_ctx* c, const void* buf, size_t len) {
   if (len < sizeof(StateHeader) + ybytes + bbytes) return fail(c, PCV_ESTATE, "state blob too short");
   StateHeader h;
   memcpy(&h, buf, sizeof(h));
-  if (memcmp(h.magic, "PCVSTAT", 8) != 0 || h.version != 1) return fail(c, PCV_ESTATE, "not a state blob");
+  if (memcmp(h.magic, "PCVSTAT", 8) != 0 || h.version != 2) return fail(c, PCV_ESTATE, "not a state blob");
   if (h.prec != (int)c->prec || h.M != c->M || h.N != c->N) return fail(c, PCV_ESTATE, "state blob does not match");
+  if (h.nl_size != c->nl_size) return fail(c, PCV_ESTATE, "state blob has another neighbour-list size");
+  const size_t lbytes = sizeof(int) * (size_t)h.nl_size;
+  if (len < sizeof(StateHeader) + ybytes + bbytes + lbytes) return fail(c, PCV_ESTATE, "state blob too short");
+  if (h.has_nl && h.nl_size > 0) {
+    const int* lst = (const int*)((const char*)buf + sizeof(h) + ybytes + bbytes);
+    for (int r = 0; r < h.nl_size; ++r)
+      if (lst[r] < 0 || lst[r] >= c->M) return fail(c, PCV_ESTATE, "state blob holds a bad neighbour list");
+  }
   cudaSetDevice(c->device);
   pcv_status st;
   if ((st = ensure(c, c->y, ybytes)) != PCV_OK) return st;
@@ -1196,6 +1380,12 @@ pcv_status pcv_load_state(pcv_ctx* c, const void* buf, size_t len) {
   const char* in = (const char*)buf;
   CUDA_TRY(c, cudaMemcpy(c->y.p, in + sizeof(h), ybytes, cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(c->Bprior.p, in + sizeof(h) + ybytes, bbytes, cudaMemcpyHostToDevice));
+  c->has_nl = false;
+  if (h.has_nl && h.nl_size > 0) {
+    if ((st = ensure(c, c->nl_keep, lbytes)) != PCV_OK) return st;
+    CUDA_TRY(c, cudaMemcpy(c->nl_keep.p, in + sizeof(h) + ybytes + bbytes, lbytes, cudaMemcpyHostToDevice));
+    c->has_nl = true;
+  }
   c->has_y = h.has_y != 0;
   c->y_c32 = h.y_c32;
   c->y_c64 = h.y_c64;

@@ -245,4 +245,38 @@ void launch_adjoint_beta_mma(int F, const LandmarkDev& L, const MmaShape& sh, in
                              const float* Gsum, const float* B, const float* Yc, const int* seg_of_frame, float* gs,
                              float* gz, unsigned* status, cudaStream_t st);
 
+// ---------------------------------------------------------------------------------------
+// neighbour list (k_nl.cu): frame schedule of one call, list table NLtab (slot 0: the list
+// carried over from the previous call; slot k+1: the list chosen at the k-th update frame)
+struct NlLists {
+  int* slot = nullptr;       // F: list slot used by each frame (its own at update frames)
+  uint8_t* upd = nullptr;    // F: 1 at update frames
+  int* ulist = nullptr;      // update frames in time order
+  int* uapp_list = nullptr;  // update frames evaluated approximately (close mode) and
+  int* uapp_seg = nullptr;   //   their close-structure segment
+  int* nlist = nullptr;      // frames between updates
+  int* counts = nullptr;     // device ints: [0] updates, [1] approximate updates, [2] between
+};
+// update frames: (step0 + t) % L == 0, t == 0 without a carried list, flag[t] != 0 (close
+// mode reassignments; flag may be null)
+void launch_nl_schedule(int F, long long step0, int L, bool have_list, const uint8_t* flag, const int* segof,
+                        const NlLists& nl, cudaStream_t st);
+// list of every update frame from its row of D (all M distances), into NLtab slots 1..
+void launch_nl_select(Prec p, int max_upd, const NlLists& nl, int M, int Mnl, const void* D, int* NLtab,
+                      cudaStream_t st);
+// distances of the frames between updates to their listed landmarks (+inf elsewhere in the
+// row): exact (rotations -> Rnl[(f*Mnl + r)*9] when Rnl is given) or approximate
+void launch_nl_exact(Prec p, int max_rows, const NlLists& nl, const int* NLtab, int Mnl, const void* frames,
+                     const LandmarkDev& L, FrameInfo fi, void* D, void* Rnl, unsigned* status, cudaStream_t st);
+void launch_nl_approx(Prec p, int max_rows, const NlLists& nl, const int* NLtab, int Mnl, const void* frames,
+                      const LandmarkDev& L, FrameInfo fi, const double4* qxy, const void* Bseg, const int* segof,
+                      void* D, cudaStream_t st);
+// beta of the adjoint over each frame's landmarks; rotations from Bseg[segof[f]] (close
+// mode) or Rupd rows (update frames) and Rnl (between updates) in exact mode
+void launch_nl_beta(Prec p, int F, const NlLists& nl, const int* NLtab, int Mnl, const LandmarkDev& L, const void* P,
+                    const double* s, double lambda, const void* Rupd, const void* Rnl, const void* Bseg,
+                    const int* segof, void* gs, void* gz, cudaStream_t st);
+// the list of this call's last update frame -> keep (unchanged without an update)
+void launch_nl_carry(const NlLists& nl, const int* NLtab, int Mnl, int* keep, cudaStream_t st);
+
 }  // namespace pcv

@@ -21,7 +21,7 @@ PCV_FP64, PCV_FP32, PCV_FP16_STORAGE = 0, 1, 2
 PCV_OPT_BAND, PCV_OPT_CHUNK, PCV_OPT_EXACT_TILE, PCV_OPT_APPROX_TILE, PCV_OPT_PROFILE = 1, 2, 3, 4, 5
 PCV_OPT_MATERIALIZE = 6
 PCV_OPT_TENSOR_CORES = 7
-PCV_PROFILE_KERNELS = 20
+PCV_PROFILE_KERNELS = 24
 
 _STATUS_NAMES = {0: "PCV_OK", -1: "PCV_EINVAL", -2: "PCV_ECUDA", -3: "PCV_ENOMEM", -4: "PCV_ENOCONV",
                  -5: "PCV_ESTATE", -6: "PCV_ETIMEOUT"}
@@ -57,6 +57,7 @@ SIGNATURES = {
     "pcv_set_landmarks": (_i, [_vp, _i, _i, _vp, _vp, _vp]),
     "pcv_set_lambda": (_i, [_vp, _d]),
     "pcv_set_close_threshold": (_i, [_vp, _d]),
+    "pcv_set_neighbor_list": (_i, [_vp, _i, _i]),
     "pcv_evaluate": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "pcv_evaluate_host": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "pcv_combine_grad": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp]),
@@ -141,6 +142,10 @@ def pcv_set_lambda(ctx, lam: float):
 
 def pcv_set_close_threshold(ctx, eps: float):
     _check(ctx, load().pcv_set_close_threshold(ctx, float(eps)))
+
+
+def pcv_set_neighbor_list(ctx, size: int, stride: int):
+    _check(ctx, load().pcv_set_neighbor_list(ctx, int(size), int(stride)))
 
 
 def pcv_set_option(ctx, key: int, value: int):
@@ -287,7 +292,7 @@ class PathCV:
     def __init__(self, landmarks: np.ndarray, lam: float, eps: float = -1.0, precision: str = "fp32",
                  weights: np.ndarray | None = None, props: np.ndarray | None = None, device: int = 0,
                  band: int | None = None, min_chunk: int | None = None, materialize: int | None = None,
-                 tensor_cores: bool | None = None):
+                 tensor_cores: bool | None = None, neighbor_list: tuple[int, int] | None = None):
         import torch
 
         self.torch = torch
@@ -307,6 +312,8 @@ class PathCV:
             pcv_set_option(self.ctx, PCV_OPT_MATERIALIZE, materialize)
         if tensor_cores is not None:
             pcv_set_option(self.ctx, PCV_OPT_TENSOR_CORES, 1 if tensor_cores else 0)
+        if neighbor_list is not None:
+            pcv_set_neighbor_list(self.ctx, *neighbor_list)
 
     @property
     def frame_dtype(self):
@@ -361,6 +368,10 @@ class PathCV:
 
     def reset(self):
         pcv_reset_close_state(self.ctx)
+
+    def set_neighbor_list(self, size: int, stride: int):
+        """Keep the `size` closest landmarks, updated every `stride` steps (0: all landmarks)."""
+        pcv_set_neighbor_list(self.ctx, size, stride)
 
     def save_state(self) -> bytes:
         return pcv_save_state(self.ctx)
