@@ -204,13 +204,14 @@ enum {
   PCV_OPT_APPROX_TILE = 4, /* tile variant index of the approximate pair kernel        */
   PCV_OPT_PROFILE = 5,     /* 1: time every kernel launch with CUDA events on the
                               context's stream (see pcv_get_profile), 0: off (default)  */
-  PCV_OPT_MATERIALIZE = 6, /* byte cap (default 2^31) on the device buffers of the
+  PCV_OPT_MATERIALIZE = 6, /* byte cap (default 2^34) on the device buffers of the
                               materialised close-structure operands: rotated frames
                               x' = R_xy^T (x - c), rotated landmarks b = R_{a_i y} a per
                               segment, and the gamma rows of the adjoint.  Used in the
                               FP32 and FP16-storage modes with uniform weights when
                               segments average 16 frames or more; 0 turns them off (the
-                              kernels then rotate while staging).  Results agree within
+                              kernels then rotate while staging; so they also do when the
+                              device cannot allocate the operands).  Results agree within
                               the mode's tolerance either way.                          */
   PCV_OPT_TENSOR_CORES = 7 /* 1 (default): with materialised operands, the segment adjoint
                               beta = sum_i gamma_i (R_{a_i y} a_i) runs on the tensor cores

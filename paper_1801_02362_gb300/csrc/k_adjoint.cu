@@ -128,6 +128,158 @@ adjoint_beta_pair(int F, int M, int N, const LT* __restrict__ lm, const float* _
 }
 
 // ---------------------------------------------------------------------------------------
+// Exact-mode beta with a neighbour list (FP32 / FP16 storage): tile of up to 16 frames of a
+// frame list x 64 atoms, 128 threads, each 1 frame x 8 atoms x 3 components x {s, z}.
+// mode 0: entries [16 y, 16 y + 16) of the update-frame list, every landmark, rotations
+//         Rupd[(row * M + i) * 9] (row = position in the list); the landmarks are split
+//         into gridDim.z ranges (the update frames are few and the landmarks many), each
+//         CTA writing its partial sums to part[z][row][atom][6], summed by beta_part_sum;
+// mode 1: tile y of the between-update tiles, the landmarks of the tile's list, rotations
+//         Rnl[(f * Mnl + column) * 9].
+// Per chunk of 8 landmarks the weights gamma R (3 x 3 per frame and landmark) and the
+// landmark coordinates are staged in shared memory, as in adjoint_beta_pair.
+constexpr int BL_TF = NL_TILE_F, BL_TJ = 64, BL_THREADS = 128, BL_KL = 8;
+
+template <typename LT>
+__global__ void __launch_bounds__(BL_THREADS)
+adjoint_beta_list(int mode, const NlTile* __restrict__ tiles, const int* __restrict__ counts,
+                  const int* __restrict__ ulist, const int* __restrict__ nlist, const int* __restrict__ NLtab,
+                  int Mnl, int M, int N, const LT* __restrict__ lm, const float* __restrict__ lmoff,
+                  const float* __restrict__ q32, const float* __restrict__ P, const double* __restrict__ s,
+                  float lambda, const float* __restrict__ Rupd, const float* __restrict__ Rnl,
+                  float* __restrict__ gs, float* __restrict__ gz, float* __restrict__ part) {
+  __shared__ __align__(16) float Ws[BL_KL * 3][BL_TF * 3];
+  __shared__ __align__(16) float Wz[BL_KL * 3][BL_TF * 3];
+  __shared__ __align__(16) float As[BL_KL * 3][BL_TJ];
+  __shared__ int s_frame[BL_TF];
+  __shared__ float s_s[BL_TF];
+  int p0, rows, ncol;
+  const int* fl;
+  const int* cols;
+  if (mode == 0) {
+    p0 = blockIdx.y * BL_TF;
+    const int n = counts[0];
+    if (p0 >= n) return;  // uniform over the block
+    rows = min(BL_TF, n - p0);
+    fl = ulist;
+    cols = nullptr;
+    ncol = M;
+  } else {
+    if ((int)blockIdx.y >= counts[3]) return;
+    const NlTile w = tiles[blockIdx.y];
+    p0 = w.p0;
+    rows = w.rows;
+    fl = nlist;
+    cols = NLtab + (size_t)w.slot * Mnl;
+    ncol = Mnl;
+  }
+  // landmark range of this CTA (split of the update frames' landmarks over gridDim.z)
+  const int per = ((ncol + gridDim.z - 1) / gridDim.z + BL_KL - 1) / BL_KL * BL_KL;
+  const int cbeg = blockIdx.z * per, cend = min(ncol, cbeg + per);
+  const int j0 = blockIdx.x * BL_TJ;
+  const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+  if (tid < BL_TF) {
+    const int f = tid < rows ? fl[p0 + tid] : -1;
+    s_frame[tid] = f;
+    s_s[tid] = f >= 0 ? (float)s[f] : 0.0f;
+  }
+  __syncthreads();
+  float bs[3][8], bz[3][8];
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) bs[b][k] = bz[b][k] = 0.0f;
+  for (int c0 = cbeg; c0 < cend; c0 += BL_KL) {
+    for (int e = tid; e < BL_TF * BL_KL; e += BL_THREADS) {
+      const int ff = e / BL_KL, cc = e - ff * BL_KL;
+      const int f = s_frame[ff], c = c0 + cc;
+      float rot[9];
+      float gsv = 0.0f, gzv = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) rot[k] = 0.0f;
+      if (f >= 0 && c < cend) {
+        const int i = cols ? cols[c] : c;
+        gammas<float>(P[(size_t)f * M + i], lambda, q32[i], s_s[ff], gsv, gzv);
+        const float* R = mode == 0 ? Rupd + ((size_t)(p0 + ff) * M + i) * 9 : Rnl + ((size_t)f * Mnl + c) * 9;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) rot[k] = R[k];
+      }
+#pragma unroll
+      for (int cx = 0; cx < 3; ++cx)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          Ws[cc * 3 + cx][ff * 3 + b] = gsv * rot[3 * b + cx];
+          Wz[cc * 3 + cx][ff * 3 + b] = gzv * rot[3 * b + cx];
+        }
+    }
+    for (int e = tid; e < BL_KL * BL_TJ; e += BL_THREADS) {
+      const int cc = e / BL_TJ, jj = e - cc * BL_TJ;
+      const int c = c0 + cc, j = j0 + jj;
+      const bool ok = c < cend && j < N;
+      const int i = ok ? (cols ? cols[c] : c) : 0;
+#pragma unroll
+      for (int cx = 0; cx < 3; ++cx) As[cc * 3 + cx][jj] = ok ? lm_coord<float, LT>(lm, lmoff, N, i, j, cx) : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < BL_KL * 3; ++kk) {
+      float a[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) a[k] = As[kk][tx * 8 + k];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const float ws = Ws[kk][ty * 3 + b], wz = Wz[kk][ty * 3 + b];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          bs[b][k] = fmaf(ws, a[k], bs[b][k]);
+          bz[b][k] = fmaf(wz, a[k], bz[b][k]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const int f = s_frame[ty];
+  if (f < 0) return;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int j = j0 + tx * 8 + k;
+    if (j >= N) continue;
+    if (part) {
+      float* dst = part + (((size_t)blockIdx.z * counts[0] + p0 + ty) * N + j) * 6;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        dst[b] = bs[b][k];
+        dst[3 + b] = bz[b][k];
+      }
+    } else {
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        gs[((size_t)f * N + j) * 3 + b] = bs[b][k];
+        gz[((size_t)f * N + j) * 3 + b] = bz[b][k];
+      }
+    }
+  }
+}
+
+// beta of the update frames: the sum of the landmark ranges' partial sums, in range order
+__global__ void beta_part_sum(const int* __restrict__ counts, const int* __restrict__ ulist, int N, int nsplit,
+                              const float* __restrict__ part, float* __restrict__ gs, float* __restrict__ gz) {
+  const int n = counts[0];
+  const size_t total = (size_t)n * N * 6;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    float v = 0.0f;
+    for (int k = 0; k < nsplit; ++k) v += part[(size_t)k * total + e];
+    const size_t rj = e / 6;
+    const int comp = (int)(e - rj * 6), row = (int)(rj / N), j = (int)(rj - (size_t)row * N);
+    const size_t o = ((size_t)ulist[row] * N + j) * 3 + (comp % 3);
+    if (comp < 3)
+      gs[o] = v;
+    else
+      gz[o] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // beta for frames sharing close structures: tile of 64 consecutive frames x 32 atoms, 256
 // threads, each 4 frames x 2 atoms x 3 components x {s, z} (48 FP32 sums): per landmark
 // two LDS.128 of gamma and 6 landmark values feed 48 FMAs.  Frames of the tile are grouped
@@ -668,6 +820,41 @@ void launch_adjoint_beta(Prec p, int F, const LandmarkDev& L, const void* P, con
       break;
   }
   note_launch();
+}
+
+int nl_beta_split(int max_upd, int M, int N) {
+  const int ctas = ((max_upd + BL_TF - 1) / BL_TF) * ((N + BL_TJ - 1) / BL_TJ);
+  if (ctas <= 0) return 1;
+  const int want = (2 * 152 * 4 + ctas - 1) / ctas;  // about two waves of 4 CTAs per SM
+  const int most = (M + 8 * BL_KL - 1) / (8 * BL_KL);  // at least 64 landmarks per range
+  return want < 1 ? 1 : (want > most ? (most < 1 ? 1 : most) : want);
+}
+
+void launch_nl_beta_tiles(Prec p, int max_upd, int max_tiles, const NlLists& nl, const NlTile* tiles, const int* NLtab,
+                          int Mnl, const LandmarkDev& L, const void* P, const double* s, double lambda,
+                          const void* Rupd, const void* Rnl, void* gs, void* gz, float* part, cudaStream_t st) {
+  if (p == P_F64) return;
+  const unsigned gx = (unsigned)((L.N + BL_TJ - 1) / BL_TJ);
+  const int nsplit = nl_beta_split(max_upd, L.M, L.N);
+  for (int mode = 0; mode < 2; ++mode) {
+    const int ny = mode == 0 ? (max_upd + BL_TF - 1) / BL_TF : max_tiles;
+    if (ny <= 0) continue;
+    dim3 grid(gx, ny, mode == 0 ? nsplit : 1);
+    float* pt = mode == 0 ? part : nullptr;
+    if (p == P_F32)
+      adjoint_beta_list<float><<<grid, BL_THREADS, 0, st>>>(
+          mode, tiles, nl.counts, nl.ulist, nl.nlist, NLtab, Mnl, L.M, L.N, (const float*)L.coords, L.off, L.q32,
+          (const float*)P, s, (float)lambda, (const float*)Rupd, (const float*)Rnl, (float*)gs, (float*)gz, pt);
+    else
+      adjoint_beta_list<__half><<<grid, BL_THREADS, 0, st>>>(
+          mode, tiles, nl.counts, nl.ulist, nl.nlist, NLtab, Mnl, L.M, L.N, (const __half*)L.coords, L.off, L.q32,
+          (const float*)P, s, (float)lambda, (const float*)Rupd, (const float*)Rnl, (float*)gs, (float*)gz, pt);
+    note_launch();
+    if (mode == 0) {
+      beta_part_sum<<<4 * 152, 256, 0, st>>>(nl.counts, nl.ulist, L.N, nsplit, part, (float*)gs, (float*)gz);
+      note_launch();
+    }
+  }
 }
 
 void launch_seg_moments(int seg_base, int nseg, const LandmarkDev& L, const float* Bseg, float* S6, cudaStream_t st) {

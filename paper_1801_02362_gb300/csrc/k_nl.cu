@@ -504,6 +504,45 @@ nl_beta_kernel(int F, int M, int N, int Mnl, const uint8_t* __restrict__ upd, co
   }
 }
 
+// Tiles of the frames between updates: the frames of list slot s are the consecutive
+// frames strictly between update frames ulist[s-1] and ulist[s] (-1 and F at the ends), so
+// a tile starts at every NL_TILE_F-th frame of its run
+__global__ void __launch_bounds__(NL_SCAN_THREADS)
+nl_tiles_kernel(int F, int* __restrict__ counts, const int* __restrict__ nlist, const int* __restrict__ slot,
+                const int* __restrict__ ulist, NlTile* __restrict__ tiles) {
+  __shared__ int wsum[3 * 32 + 3];
+  const int nb = counts[2], nu = counts[0];
+  int base = 0;
+  for (int p0 = 0; p0 < nb; p0 += NL_SCAN_THREADS) {
+    const int p = p0 + threadIdx.x;
+    bool v[3] = {false, false, false};
+    int rows = 0, sl = 0;
+    if (p < nb) {
+      const int t = nlist[p];
+      sl = slot[t];
+      const int u = sl > 0 ? ulist[sl - 1] : -1;
+      const int nxt = sl < nu ? ulist[sl] : F;
+      const int off = t - u - 1;
+      v[0] = off % NL_TILE_F == 0;
+      rows = min(NL_TILE_F, nxt - u - 1 - off);
+    }
+    int ex[3], tot[3];
+    block_scan3(v, ex, tot, wsum);
+    if (v[0]) tiles[base + ex[0]] = NlTile{p, rows, sl, 0};
+    base += tot[0];
+  }
+  if (threadIdx.x == 0) counts[3] = base;
+}
+
+template <typename DT>
+__global__ void nl_fill_inf_kernel(const int* __restrict__ counts, const int* __restrict__ nlist, int M,
+                                   DT* __restrict__ D) {
+  const int p = blockIdx.x;
+  if (p >= counts[2]) return;
+  DT* row = D + (size_t)nlist[p] * M;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) row[i] = (DT)INFINITY;
+}
+
 // the list of the last update frame of this call becomes the carried-over list
 __global__ void nl_carry_kernel(const int* __restrict__ counts, const int* __restrict__ NLtab, int Mnl,
                                 int* __restrict__ keep) {
@@ -603,6 +642,21 @@ void launch_nl_beta(Prec p, int F, const NlLists& nl, const int* NLtab, int Mnl,
           (const float*)Rupd, (const float*)Rnl, (const float*)Bseg, segof, (float*)gs, (float*)gz);
       break;
   }
+  note_launch();
+}
+
+void launch_nl_tiles(int F, const NlLists& nl, NlTile* tiles, cudaStream_t st) {
+  if (F <= 0) return;
+  nl_tiles_kernel<<<1, NL_SCAN_THREADS, 0, st>>>(F, nl.counts, nl.nlist, nl.slot, nl.ulist, tiles);
+  note_launch();
+}
+
+void launch_nl_fill_inf(Prec p, int max_between, const NlLists& nl, int M, void* D, cudaStream_t st) {
+  if (max_between <= 0) return;
+  if (p == P_F64)
+    nl_fill_inf_kernel<double><<<max_between, 128, 0, st>>>(nl.counts, nl.nlist, M, (double*)D);
+  else
+    nl_fill_inf_kernel<float><<<max_between, 128, 0, st>>>(nl.counts, nl.nlist, M, (float*)D);
   note_launch();
 }
 

@@ -84,13 +84,16 @@ __device__ __forceinline__ void frame_centre<double>(const float4*, const double
 constexpr int EX_TF = 16, EX_TM = 32, EX_THREADS = 128;
 
 // Stage one chunk of KC atoms of the tile: frames centred (weight mode 1: x w_j,
-// 2: x sqrt(w_j)), landmarks (mode 2: a sqrt(w_j)).  Layout [jj*3 + c][row].
+// 2: x sqrt(w_j)), landmarks (mode 2: a sqrt(w_j)).  Layout [jj*3 + c][row].  Landmark
+// column c of the tile is landmark i0 + c, or with a column list cols (a neighbour list of
+// ncol entries) landmark cols[i0 + c].
 template <typename FT, typename LT, typename ST, int TF, int TM, int KC, int PF, int PM>
 __device__ __forceinline__ void stage_exact(int j0, int N, int M, int i0, const FT* __restrict__ frames,
                                             const LT* __restrict__ lm, const float* __restrict__ lmoff,
                                             const float* __restrict__ wts, int wmode, const int* s_frame,
                                             const ST (*s_c)[3],
-                                            ST (*Xs)[PF], ST (*As)[PM]) {
+                                            ST (*Xs)[PF], ST (*As)[PM], const int* __restrict__ cols = nullptr,
+                                            int ncol = 0) {
   const int tid = threadIdx.x;
   for (int e = tid; e < TF * KC; e += EX_THREADS) {
     const int ff = e / KC, jj = e - ff * KC;
@@ -115,9 +118,10 @@ __device__ __forceinline__ void stage_exact(int j0, int N, int M, int i0, const 
   }
   for (int e = tid; e < TM * KC; e += EX_THREADS) {
     const int ll = e / KC, jj = e - ll * KC;
-    const int j = j0 + jj, i = i0 + ll;
+    const int j = j0 + jj, ci = i0 + ll;
     ST v0 = 0, v1 = 0, v2 = 0;
-    if (i < M && j < N) {
+    if ((cols ? ci < ncol : ci < M) && j < N) {
+      const int i = cols ? cols[ci] : ci;
       v0 = lm_coord<ST, LT>(lm, lmoff, N, i, j, 0);
       v1 = lm_coord<ST, LT>(lm, lmoff, N, i, j, 1);
       v2 = lm_coord<ST, LT>(lm, lmoff, N, i, j, 2);
@@ -158,8 +162,9 @@ __device__ __forceinline__ void load_tile_frames(int rows, const int* __restrict
 //  pass 2: D = sum_j w_j |x_j - R a_j|^2 directly in FP32 (Eq. dist): positive terms, no
 //          cancellation, stationary in R -- so D is accurate to ~1e-7 relative although
 //          every operation is FP32.
-// one 16-frame x 32-landmark tile with origin (row0, i0); the per-call kernel and the
-// persistent group kernel both run it
+// one 16-frame x 32-landmark tile with origin (row0, i0); the per-call kernel, the
+// persistent group kernel and the neighbour-list kernel (column list cols of ncol
+// landmarks; rotations then go to Rout[(f * ncol + column) * 9]) run it
 template <typename LT>
 __device__ __forceinline__ void exact_tile_f32(int rows, const int* __restrict__ row_frame,
                                                const float* __restrict__ frames, const float4* __restrict__ c32,
@@ -167,7 +172,8 @@ __device__ __forceinline__ void exact_tile_f32(int rows, const int* __restrict__
                                                const float* __restrict__ lmoff, const double* __restrict__ lG,
                                                const float* __restrict__ wts, int M, int N, double dscale,
                                                float* __restrict__ Dout, float* __restrict__ Rout,
-                                               unsigned* __restrict__ status, int row0, int i0) {
+                                               unsigned* __restrict__ status, int row0, int i0,
+                                               const int* __restrict__ cols = nullptr, int ncol = 0) {
   constexpr int TF = EX_TF, TM = EX_TM, KC = 32;
   constexpr int PF = TF + 2, PM = TM + 2;
   __shared__ __align__(16) float Xs[KC * 3][PF];
@@ -191,7 +197,8 @@ __device__ __forceinline__ void exact_tile_f32(int rows, const int* __restrict__
       for (int e = 0; e < 9; ++e) h[u][v][e] = 0.0f;
 
   for (int j0 = 0; j0 < N; j0 += KC) {
-    stage_exact<float, LT, float, TF, TM, KC, PF, PM>(j0, N, M, i0, frames, lm, lmoff, wts, 1, s_frame, s_c, Xs, As);
+    stage_exact<float, LT, float, TF, TM, KC, PF, PM>(j0, N, M, i0, frames, lm, lmoff, wts, 1, s_frame, s_c, Xs, As,
+                                                      cols, ncol);
     __syncthreads();
 #pragma unroll 4
     for (int jj = 0; jj < KC; ++jj) {
@@ -221,9 +228,10 @@ __device__ __forceinline__ void exact_tile_f32(int rows, const int* __restrict__
 #pragma unroll
     for (int v = 0; v < 2; ++v) {
       const int f = s_frame[ty * 2 + u];
-      const int i = i0 + tx * 2 + v;
+      const int ci = i0 + tx * 2 + v;
       float q[4] = {1.0f, 0.0f, 0.0f, 0.0f};
-      if (f >= 0 && i < M) {
+      if (f >= 0 && (cols ? ci < ncol : ci < M)) {
+        const int i = cols ? cols[ci] : ci;
         const float ub = (float)(0.5 * (fG[f] + lG[i])) * 1.00001f + 1e-30f;
         all_ok &= top_quat_f32(h[u][v], ub, q);
       }
@@ -235,7 +243,8 @@ __device__ __forceinline__ void exact_tile_f32(int rows, const int* __restrict__
   float acc[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
   float thi[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}}, tlo[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
   for (int j0 = 0; j0 < N; j0 += KC) {
-    stage_exact<float, LT, float, TF, TM, KC, PF, PM>(j0, N, M, i0, frames, lm, lmoff, wts, 2, s_frame, s_c, Xs, As);
+    stage_exact<float, LT, float, TF, TM, KC, PF, PM>(j0, N, M, i0, frames, lm, lmoff, wts, 2, s_frame, s_c, Xs, As,
+                                                      cols, ncol);
     __syncthreads();
 #pragma unroll 4
     for (int jj = 0; jj < KC; ++jj) {
@@ -272,11 +281,12 @@ __device__ __forceinline__ void exact_tile_f32(int rows, const int* __restrict__
     for (int v = 0; v < 2; ++v) {
       const int r = row0 + ty * 2 + u;
       const int f = s_frame[ty * 2 + u];
-      const int i = i0 + tx * 2 + v;
-      if (f < 0 || i >= M) continue;
+      const int ci = i0 + tx * 2 + v;
+      if (f < 0 || !(cols ? ci < ncol : ci < M)) continue;
+      const int i = cols ? cols[ci] : ci;
       Dout[(size_t)f * M + i] = (thi[u][v] + tlo[u][v]) * dsf;
       if (Rout) {
-        float* dst = Rout + ((size_t)r * M + i) * 9;
+        float* dst = cols ? Rout + ((size_t)f * ncol + ci) * 9 : Rout + ((size_t)r * M + i) * 9;
 #pragma unroll
         for (int e = 0; e < 9; ++e) dst[e] = R[u][v][e];
       }
@@ -306,6 +316,23 @@ exact_group_f32(const GroupInst* __restrict__ I, const GroupTile* __restrict__ t
                        t.D, nullptr, t.status, w.row0, w.i0);
     __syncthreads();  // the tile's shared staging is reused by the next tile
   }
+}
+
+// Neighbour list: tile k = blockIdx.y covers `rows` consecutive entries of the list of
+// frames between list updates (all sharing the list `slot`), blockIdx.x the listed
+// landmarks in columns of 32
+template <typename LT>
+__global__ void __launch_bounds__(EX_THREADS, 4)
+exact_list_f32(const NlTile* __restrict__ tiles, const int* __restrict__ ntiles, const int* __restrict__ nlist,
+               const int* __restrict__ NLtab, int Mnl, const float* __restrict__ frames,
+               const float4* __restrict__ c32, const double* __restrict__ fG, const LT* __restrict__ lm,
+               const float* __restrict__ lmoff, const double* __restrict__ lG, const float* __restrict__ wts, int M,
+               int N, double dscale, float* __restrict__ Dout, float* __restrict__ Rnl,
+               unsigned* __restrict__ status) {
+  if ((int)blockIdx.y >= *ntiles) return;  // uniform over the block
+  const NlTile w = tiles[blockIdx.y];
+  exact_tile_f32<LT>(w.rows, nlist + w.p0, frames, c32, fG, lm, lmoff, lG, wts, M, N, dscale, Dout, Rnl, status, 0,
+                     blockIdx.x * EX_TM, NLtab + (size_t)w.slot * Mnl, Mnl);
 }
 
 // FP64 mode: one pass, FP64 correlation, FP64 eigenvalue and D = G_x + G_a - 2 lambda_max
@@ -860,6 +887,23 @@ static void approx_launch(Prec p, int max_rows, const int* approx_list, const in
           L.off, (const float*)Bseg, L.w, L.M, L.N, L.dscale, (float*)D);
       break;
   }
+  note_launch();
+}
+
+void launch_nl_exact_tiles(Prec p, int max_tiles, const NlLists& nl, const NlTile* tiles, const int* NLtab, int Mnl,
+                           const void* frames, const LandmarkDev& L, FrameInfo fi, void* D, void* Rnl,
+                           unsigned* status, cudaStream_t st) {
+  if (max_tiles <= 0 || p == P_F64) return;
+  dim3 grid((Mnl + EX_TM - 1) / EX_TM, max_tiles);
+  if (p == P_F32)
+    exact_list_f32<float><<<grid, EX_THREADS, 0, st>>>(tiles, nl.counts + 3, nl.nlist, NLtab, Mnl, (const float*)frames,
+                                                       fi.c32, fi.G, (const float*)L.coords, L.off, L.G, L.w, L.M,
+                                                       L.N, L.dscale, (float*)D, (float*)Rnl, status);
+  else
+    exact_list_f32<__half><<<grid, EX_THREADS, 0, st>>>(tiles, nl.counts + 3, nl.nlist, NLtab, Mnl,
+                                                        (const float*)frames, fi.c32, fi.G, (const __half*)L.coords,
+                                                        L.off, L.G, L.w, L.M, L.N, L.dscale, (float*)D, (float*)Rnl,
+                                                        status);
   note_launch();
 }
 

@@ -92,14 +92,14 @@ struct pcv_ctx {
   double eps = -1.0;
   int band_W = 2;
   int min_chunk = 4096;
-  int64_t mat_cap = int64_t(2) << 30;  // bytes of materialised operands allowed (PCV_OPT_MATERIALIZE)
+  int64_t mat_cap = int64_t(16) << 30;  // bytes of materialised operands allowed (PCV_OPT_MATERIALIZE)
   bool tensor_cores = true;             // segment adjoint on the tensor cores (PCV_OPT_TENSOR_CORES)
   double gap_estimate = 0.0;
   // neighbour list: size M_nl (0 = none) and update stride L; the list held between calls
   int nl_size = 0, nl_stride = 1;
   bool has_nl = false;
   DevBuf nl_keep;
-  DevBuf nlSlot, nlUpd, nlU, nlUA, nlUAseg, nlN, NLtab, Rupd, Rnl;
+  DevBuf nlSlot, nlUpd, nlU, nlUA, nlUAseg, nlN, NLtab, Rupd, Rnl, nlTiles, nlPart;
   // close state
   bool has_y = false;
   DevBuf y, Bprior;
@@ -297,7 +297,7 @@ pcv_status pcv_destroy(pcv_ctx* c) {
                     &c->Dbuf, &c->Rpair, &c->Bseg, &c->Xr, &c->Bm, &c->GSb, &c->GZb, &c->Nx, &c->Nb, &c->Yc, &c->Gsum, &c->Amma, &c->Bmma, &c->S6, &c->mstat, &c->status, &c->nrecheck, &c->small, &c->h_frames,
                     &c->h_s, &c->h_z, &c->h_gs, &c->h_gz, &c->h_msd, &c->h_ref, &c->grp_inst, &c->grp_tiles,
                     &c->nl_keep, &c->nlSlot, &c->nlUpd, &c->nlU, &c->nlUA, &c->nlUAseg, &c->nlN, &c->NLtab,
-                    &c->Rupd, &c->Rnl};
+                    &c->Rupd, &c->Rnl, &c->nlTiles, &c->nlPart};
   if (c->grp_stream) cudaStreamSynchronize(c->grp_stream);
   for (DevBuf* b : bufs) release(*b);
   if (c->grp_exec) cudaGraphExecDestroy(c->grp_exec);
@@ -573,6 +573,7 @@ pcv_status ensure_nl_workspace(pcv_ctx* c, int F, bool exact_grads) {
   if ((st = ensure(c, c->nlUAseg, sizeof(int) * F)) != PCV_OK) return st;
   if ((st = ensure(c, c->nlN, sizeof(int) * F)) != PCV_OK) return st;
   if ((st = ensure(c, c->NLtab, sizeof(int) * Mnl * ((size_t)F + 1))) != PCV_OK) return st;
+  if ((st = ensure(c, c->nlTiles, sizeof(NlTile) * ((size_t)F + F / NL_TILE_F + 4))) != PCV_OK) return st;
   if (exact_grads && (st = ensure(c, c->Rnl, work_elem(c->prec) * 9 * Mnl * (size_t)F)) != PCV_OK) return st;
   return PCV_OK;
 }
@@ -755,20 +756,24 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
     const size_t mb = msh.a_bytes + msh.b_bytes_per_seg * nseg;
     mma = grads && c->tensor_cores;
     if ((int64_t)(xb + bb + nb + (mma ? mb : 2 * gb)) <= c->mat_cap) {
-      if ((ps = ensure(c, c->Xr, xb)) != PCV_OK) return ps;
-      if ((ps = ensure(c, c->Bm, bb)) != PCV_OK) return ps;
-      if ((ps = ensure(c, c->Nx, sizeof(float) * (size_t)napp)) != PCV_OK) return ps;
-      if ((ps = ensure(c, c->Nb, sizeof(float) * (size_t)nseg * M)) != PCV_OK) return ps;
-      if ((ps = ensure(c, c->Yc, sizeof(float) * 3 * (size_t)c->N * nseg)) != PCV_OK) return ps;
-      if (grads && (ps = ensure(c, c->Gsum, 2 * sizeof(float) * (size_t)F)) != PCV_OK) return ps;
-      if (mma) {
-        if ((ps = ensure(c, c->Amma, msh.a_bytes)) != PCV_OK) return ps;
-        if ((ps = ensure(c, c->Bmma, msh.b_bytes_per_seg * nseg)) != PCV_OK) return ps;
-      } else if (grads) {
-        if ((ps = ensure(c, c->GSb, gb)) != PCV_OK) return ps;
-        if ((ps = ensure(c, c->GZb, gb)) != PCV_OK) return ps;
+      // the materialised operands are an optimisation: when the device cannot hold them the
+      // kernels that rotate while staging take over
+      bool ok = ensure(c, c->Xr, xb) == PCV_OK && ensure(c, c->Bm, bb) == PCV_OK &&
+                ensure(c, c->Nx, sizeof(float) * (size_t)napp) == PCV_OK &&
+                ensure(c, c->Nb, sizeof(float) * (size_t)nseg * M) == PCV_OK &&
+                ensure(c, c->Yc, sizeof(float) * 3 * (size_t)c->N * nseg) == PCV_OK &&
+                (!grads || ensure(c, c->Gsum, 2 * sizeof(float) * (size_t)F) == PCV_OK);
+      if (ok && mma)
+        ok = ensure(c, c->Amma, msh.a_bytes) == PCV_OK && ensure(c, c->Bmma, msh.b_bytes_per_seg * nseg) == PCV_OK;
+      else if (ok && grads)
+        ok = ensure(c, c->GSb, gb) == PCV_OK && ensure(c, c->GZb, gb) == PCV_OK;
+      if (ok) {
+        tiled = true;
+      } else {
+        for (DevBuf* b : {&c->Xr, &c->Bm, &c->Amma, &c->Bmma, &c->GSb, &c->GZb}) release(*b);
+        c->err = "no error";
+        mma = false;
       }
-      tiled = true;
     } else {
       mma = false;
     }
@@ -909,6 +914,9 @@ pcv_status evaluate_exact_nl(pcv_ctx* c, int F, const void* frames, double* s, d
   pcv_status ps = ensure_nl_workspace(c, F, grads);
   if (ps != PCV_OK) return ps;
   if (grads && (ps = ensure(c, c->Rupd, work_elem(c->prec) * 9 * (size_t)M * nupd)) != PCV_OK) return ps;
+  if (grads && c->prec != P_F64 &&
+      (ps = ensure(c, c->nlPart, sizeof(float) * 6 * (size_t)nl_beta_split(nupd, M, c->N) * nupd * c->N)) != PCV_OK)
+    return ps;
   const NlLists nll = nl_lists(c);
   {
     PROF(c, K_PREP);
@@ -928,10 +936,21 @@ pcv_status evaluate_exact_nl(pcv_ctx* c, int F, const void* frames, double* s, d
     launch_nl_select(c->prec, nupd, nll, M, Mnl, c->Dbuf.p, (int*)c->NLtab.p, st);
   }
   if ((ps = nl_stage_carried(c)) != PCV_OK) return ps;
+  // FP32 / FP16 storage: tiles of up to 16 frames sharing a list x 32 listed landmarks
+  const bool tiles = c->prec != P_F64;
+  const int max_tiles = (F - nupd + NL_TILE_F - 1) / NL_TILE_F + nupd + 1;
+  NlTile* tl = (NlTile*)c->nlTiles.p;
   {
     PROF(c, K_NL_PAIR);
-    launch_nl_exact(c->prec, F - nupd, nll, (const int*)c->NLtab.p, Mnl, frames, L, fi, c->Dbuf.p,
-                    grads ? c->Rnl.p : nullptr, (unsigned*)c->status.p, st);
+    if (tiles) {
+      launch_nl_tiles(F, nll, tl, st);
+      launch_nl_fill_inf(c->prec, F - nupd, nll, M, c->Dbuf.p, st);
+      launch_nl_exact_tiles(c->prec, max_tiles, nll, tl, (const int*)c->NLtab.p, Mnl, frames, L, fi, c->Dbuf.p,
+                            grads ? c->Rnl.p : nullptr, (unsigned*)c->status.p, st);
+    } else {
+      launch_nl_exact(c->prec, F - nupd, nll, (const int*)c->NLtab.p, Mnl, frames, L, fi, c->Dbuf.p,
+                      grads ? c->Rnl.p : nullptr, (unsigned*)c->status.p, st);
+    }
   }
   {
     PROF(c, K_FINAL);
@@ -942,8 +961,12 @@ pcv_status evaluate_exact_nl(pcv_ctx* c, int F, const void* frames, double* s, d
   if (grads) {
     {
       PROF(c, K_NL_BETA);
-      launch_nl_beta(c->prec, F, nll, (const int*)c->NLtab.p, Mnl, L, c->Dbuf.p, s, c->lambda, c->Rupd.p, c->Rnl.p,
-                     nullptr, nullptr, gs, gz, st);
+      if (tiles)
+        launch_nl_beta_tiles(c->prec, nupd, max_tiles, nll, tl, (const int*)c->NLtab.p, Mnl, L, c->Dbuf.p, s,
+                             c->lambda, c->Rupd.p, c->Rnl.p, gs, gz, (float*)c->nlPart.p, st);
+      else
+        launch_nl_beta(c->prec, F, nll, (const int*)c->NLtab.p, Mnl, L, c->Dbuf.p, s, c->lambda, c->Rupd.p,
+                       c->Rnl.p, nullptr, nullptr, gs, gz, st);
     }
     PROF(c, K_ADJ_FINISH);
     FrameRec none;

@@ -279,4 +279,28 @@ void launch_nl_beta(Prec p, int F, const NlLists& nl, const int* NLtab, int Mnl,
 // the list of this call's last update frame -> keep (unchanged without an update)
 void launch_nl_carry(const NlLists& nl, const int* NLtab, int Mnl, int* keep, cudaStream_t st);
 
+// Tiles of frames between updates for the tiled FP32 / FP16 kernels: `rows` (<= NL_TILE_F)
+// consecutive entries of nlist from position p0, all on the list `slot`.  nl_tiles writes
+// them and their number to counts[3]; at most (frames between) / NL_TILE_F + updates + 2.
+struct NlTile {
+  int p0, rows, slot, pad;
+};
+constexpr int NL_TILE_F = 16;
+void launch_nl_tiles(int F, const NlLists& nl, NlTile* tiles, cudaStream_t st);
+// +inf over the MSD rows of the frames between updates (before their listed entries are written)
+void launch_nl_fill_inf(Prec p, int max_between, const NlLists& nl, int M, void* D, cudaStream_t st);
+// exact MSDs of the frames between updates to their listed landmarks, tiled (FP32 / FP16
+// storage; rotations -> Rnl[(f*Mnl + column)*9] when Rnl is given) (k_pair.cu)
+void launch_nl_exact_tiles(Prec p, int max_tiles, const NlLists& nl, const NlTile* tiles, const int* NLtab, int Mnl,
+                           const void* frames, const LandmarkDev& L, FrameInfo fi, void* D, void* Rnl,
+                           unsigned* status, cudaStream_t st);
+// exact-mode beta of the adjoint, tiled (FP32 / FP16 storage) (k_adjoint.cu): the update
+// frames over every landmark (rotations Rupd, row = position in ulist; the landmarks split
+// into nl_beta_split ranges whose partial sums go to part, nl_beta_split * max_upd * N * 6
+// floats), then the frames in between over their lists (rotations Rnl)
+int nl_beta_split(int max_upd, int M, int N);
+void launch_nl_beta_tiles(Prec p, int max_upd, int max_tiles, const NlLists& nl, const NlTile* tiles, const int* NLtab,
+                          int Mnl, const LandmarkDev& L, const void* P, const double* s, double lambda,
+                          const void* Rupd, const void* Rnl, void* gs, void* gz, float* part, cudaStream_t st);
+
 }  // namespace pcv

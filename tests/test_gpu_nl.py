@@ -4,9 +4,9 @@ Section 6.2) and with the close structure (end of Section 3.2).
 
 The list is an integer decision taken on floating-point distances.  The tests compare the
 list membership exactly (the +inf pattern of the MSD rows) on data whose M_nl-th and
-(M_nl+1)-th smallest distances at every update step are separated by far more than the
-mode's tolerance (checked on the oracle's distances); under such a gap the choice is
-unique in any precision."""
+(M_nl+1)-th smallest distances at every update step differ by more than the sum of their
+tolerances (checked on the oracle's distances): distances within tolerance cannot order
+the two differently, so the choice is the same in any precision."""
 import numpy as np
 import pytest
 
@@ -76,9 +76,11 @@ def check(g, r, fr, lm, lam, precision, m_nl, grad=True):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16"])
-def test_nl_exact_mode(pcv, precision):
-    """Original method: N=40, M=70 (ragged landmark tile), F=300, list of 12 every 7 steps."""
-    m_nl, L = 12, 7
+@pytest.mark.parametrize("m_nl,L", [(12, 7), (34, 40)])
+def test_nl_exact_mode(pcv, precision, m_nl, L):
+    """Original method: N=40, M=70 (ragged landmark tile), F=300; a list of 12 every 7 steps,
+    and of 34 (two landmark columns of the tiled kernels, the second ragged) every 40 steps
+    (full 16-frame tiles and a ragged last tile per run)."""
     lm, fr, lam = problem(67, 40, 70, 300, noise=0.03, schedule="walk", precision=precision)
     r = oracle.exact(fr, lm, lam, want_grad=True, nl=(m_nl, L))
     assert_clear_gaps(r, m_nl, fr, lm, TOL[precision])
