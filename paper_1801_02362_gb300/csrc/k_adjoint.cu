@@ -136,6 +136,8 @@ adjoint_beta_pair(int F, int M, int N, const LT* __restrict__ lm, const float* _
 //         CTA writing its partial sums to part[z][row][atom][6], summed by beta_part_sum;
 // mode 1: tile y of the between-update tiles, the landmarks of the tile's list, rotations
 //         Rnl[(f * Mnl + column) * 9].
+// With Bseg (close structure) the rotations are the stored R_{a_i y} of each frame's segment,
+// Bseg[(segof[f] * M + i) * 9], in both modes.
 // Per chunk of 8 landmarks the weights gamma R (3 x 3 per frame and landmark) and the
 // landmark coordinates are staged in shared memory, as in adjoint_beta_pair.
 constexpr int BL_TF = NL_TILE_F, BL_TJ = 64, BL_THREADS = 128, BL_KL = 8;
@@ -147,7 +149,8 @@ adjoint_beta_list(int mode, const NlTile* __restrict__ tiles, const int* __restr
                   int Mnl, int M, int N, const LT* __restrict__ lm, const float* __restrict__ lmoff,
                   const float* __restrict__ q32, const float* __restrict__ P, const double* __restrict__ s,
                   float lambda, const float* __restrict__ Rupd, const float* __restrict__ Rnl,
-                  float* __restrict__ gs, float* __restrict__ gz, float* __restrict__ part) {
+                  const float* __restrict__ Bseg, const int* __restrict__ segof, float* __restrict__ gs,
+                  float* __restrict__ gz, float* __restrict__ part) {
   __shared__ __align__(16) float Ws[BL_KL * 3][BL_TF * 3];
   __shared__ __align__(16) float Wz[BL_KL * 3][BL_TF * 3];
   __shared__ __align__(16) float As[BL_KL * 3][BL_TJ];
@@ -200,7 +203,8 @@ adjoint_beta_list(int mode, const NlTile* __restrict__ tiles, const int* __restr
       if (f >= 0 && c < cend) {
         const int i = cols ? cols[c] : c;
         gammas<float>(P[(size_t)f * M + i], lambda, q32[i], s_s[ff], gsv, gzv);
-        const float* R = mode == 0 ? Rupd + ((size_t)(p0 + ff) * M + i) * 9 : Rnl + ((size_t)f * Mnl + c) * 9;
+        const float* R = Bseg ? Bseg + ((size_t)segof[f] * M + i) * 9
+                              : (mode == 0 ? Rupd + ((size_t)(p0 + ff) * M + i) * 9 : Rnl + ((size_t)f * Mnl + c) * 9);
 #pragma unroll
         for (int k = 0; k < 9; ++k) rot[k] = R[k];
       }
@@ -832,7 +836,8 @@ int nl_beta_split(int max_upd, int M, int N) {
 
 void launch_nl_beta_tiles(Prec p, int max_upd, int max_tiles, const NlLists& nl, const NlTile* tiles, const int* NLtab,
                           int Mnl, const LandmarkDev& L, const void* P, const double* s, double lambda,
-                          const void* Rupd, const void* Rnl, void* gs, void* gz, float* part, cudaStream_t st) {
+                          const void* Rupd, const void* Rnl, const void* Bseg, const int* segof, void* gs, void* gz,
+                          float* part, cudaStream_t st) {
   if (p == P_F64) return;
   const unsigned gx = (unsigned)((L.N + BL_TJ - 1) / BL_TJ);
   const int nsplit = nl_beta_split(max_upd, L.M, L.N);
@@ -844,11 +849,13 @@ void launch_nl_beta_tiles(Prec p, int max_upd, int max_tiles, const NlLists& nl,
     if (p == P_F32)
       adjoint_beta_list<float><<<grid, BL_THREADS, 0, st>>>(
           mode, tiles, nl.counts, nl.ulist, nl.nlist, NLtab, Mnl, L.M, L.N, (const float*)L.coords, L.off, L.q32,
-          (const float*)P, s, (float)lambda, (const float*)Rupd, (const float*)Rnl, (float*)gs, (float*)gz, pt);
+          (const float*)P, s, (float)lambda, (const float*)Rupd, (const float*)Rnl, (const float*)Bseg, segof,
+          (float*)gs, (float*)gz, pt);
     else
       adjoint_beta_list<__half><<<grid, BL_THREADS, 0, st>>>(
           mode, tiles, nl.counts, nl.ulist, nl.nlist, NLtab, Mnl, L.M, L.N, (const __half*)L.coords, L.off, L.q32,
-          (const float*)P, s, (float)lambda, (const float*)Rupd, (const float*)Rnl, (float*)gs, (float*)gz, pt);
+          (const float*)P, s, (float)lambda, (const float*)Rupd, (const float*)Rnl, (const float*)Bseg, segof,
+          (float*)gs, (float*)gz, pt);
     note_launch();
     if (mode == 0) {
       beta_part_sum<<<4 * 152, 256, 0, st>>>(nl.counts, nl.ulist, L.N, nsplit, part, (float*)gs, (float*)gz);

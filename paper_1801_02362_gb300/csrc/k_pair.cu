@@ -163,9 +163,12 @@ __device__ __forceinline__ void load_tile_frames(int rows, const int* __restrict
 //          cancellation, stationary in R -- so D is accurate to ~1e-7 relative although
 //          every operation is FP32.
 // one 16-frame x 32-landmark tile with origin (row0, i0); the per-call kernel, the
-// persistent group kernel and the neighbour-list kernel (column list cols of ncol
-// landmarks; rotations then go to Rout[(f * ncol + column) * 9]) run it
-template <typename LT>
+// persistent group kernel and the neighbour-list kernels (column list cols of ncol
+// landmarks; rotations then go to Rout[(f * ncol + column) * 9]) run it.
+// APPROX: the approximate MSD of Eq. (close_dist) instead: no pass 1, the rotation of each
+// pair is R_xy R_{a_i y} from the frame's alignment quaternion qxy[f] and the stored
+// rotations Bseg[segof[f] * M + i], then the direct pass 2.
+template <typename LT, bool APPROX = false>
 __device__ __forceinline__ void exact_tile_f32(int rows, const int* __restrict__ row_frame,
                                                const float* __restrict__ frames, const float4* __restrict__ c32,
                                                const double* __restrict__ fG, const LT* __restrict__ lm,
@@ -173,7 +176,10 @@ __device__ __forceinline__ void exact_tile_f32(int rows, const int* __restrict__
                                                const float* __restrict__ wts, int M, int N, double dscale,
                                                float* __restrict__ Dout, float* __restrict__ Rout,
                                                unsigned* __restrict__ status, int row0, int i0,
-                                               const int* __restrict__ cols = nullptr, int ncol = 0) {
+                                               const int* __restrict__ cols = nullptr, int ncol = 0,
+                                               const double4* __restrict__ qxy = nullptr,
+                                               const float* __restrict__ Bseg = nullptr,
+                                               const int* __restrict__ segof = nullptr) {
   constexpr int TF = EX_TF, TM = EX_TM, KC = 32;
   constexpr int PF = TF + 2, PM = TM + 2;
   __shared__ __align__(16) float Xs[KC * 3][PF];
@@ -196,7 +202,7 @@ __device__ __forceinline__ void exact_tile_f32(int rows, const int* __restrict__
 #pragma unroll
       for (int e = 0; e < 9; ++e) h[u][v][e] = 0.0f;
 
-  for (int j0 = 0; j0 < N; j0 += KC) {
+  for (int j0 = 0; j0 < (APPROX ? 0 : N); j0 += KC) {
     stage_exact<float, LT, float, TF, TM, KC, PF, PM>(j0, N, M, i0, frames, lm, lmoff, wts, 1, s_frame, s_c, Xs, As,
                                                       cols, ncol);
     __syncthreads();
@@ -230,6 +236,24 @@ __device__ __forceinline__ void exact_tile_f32(int rows, const int* __restrict__
       const int f = s_frame[ty * 2 + u];
       const int ci = i0 + tx * 2 + v;
       float q[4] = {1.0f, 0.0f, 0.0f, 0.0f};
+      if (APPROX) {
+        float Rxy[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, B[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+        if (f >= 0 && (cols ? ci < ncol : ci < M)) {
+          const int i = cols ? cols[ci] : ci;
+          const double4 qq = qxy[f];
+          const float qf[4] = {(float)qq.x, (float)qq.y, (float)qq.z, (float)qq.w};
+          quat_to_rot(qf, Rxy);
+          const float* Bi = Bseg + ((size_t)segof[f] * M + i) * 9;
+#pragma unroll
+          for (int e = 0; e < 9; ++e) B[e] = Bi[e];
+        }
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+          for (int cc = 0; cc < 3; ++cc)
+            R[u][v][3 * b + cc] = fmaf(Rxy[3 * b], B[cc], fmaf(Rxy[3 * b + 1], B[3 + cc], Rxy[3 * b + 2] * B[6 + cc]));
+        continue;
+      }
       if (f >= 0 && (cols ? ci < ncol : ci < M)) {
         const int i = cols ? cols[ci] : ci;
         const float ub = (float)(0.5 * (fG[f] + lG[i])) * 1.00001f + 1e-30f;
@@ -285,7 +309,7 @@ __device__ __forceinline__ void exact_tile_f32(int rows, const int* __restrict__
       if (f < 0 || !(cols ? ci < ncol : ci < M)) continue;
       const int i = cols ? cols[ci] : ci;
       Dout[(size_t)f * M + i] = (thi[u][v] + tlo[u][v]) * dsf;
-      if (Rout) {
+      if (Rout && !APPROX) {
         float* dst = cols ? Rout + ((size_t)f * ncol + ci) * 9 : Rout + ((size_t)r * M + i) * 9;
 #pragma unroll
         for (int e = 0; e < 9; ++e) dst[e] = R[u][v][e];
@@ -320,19 +344,32 @@ exact_group_f32(const GroupInst* __restrict__ I, const GroupTile* __restrict__ t
 
 // Neighbour list: tile k = blockIdx.y covers `rows` consecutive entries of the list of
 // frames between list updates (all sharing the list `slot`), blockIdx.x the listed
-// landmarks in columns of 32
-template <typename LT>
+// landmarks in columns of 32.  APPROX: Eq. (close_dist) with the frames' close structures.
+template <typename LT, bool APPROX>
 __global__ void __launch_bounds__(EX_THREADS, 4)
-exact_list_f32(const NlTile* __restrict__ tiles, const int* __restrict__ ntiles, const int* __restrict__ nlist,
-               const int* __restrict__ NLtab, int Mnl, const float* __restrict__ frames,
-               const float4* __restrict__ c32, const double* __restrict__ fG, const LT* __restrict__ lm,
-               const float* __restrict__ lmoff, const double* __restrict__ lG, const float* __restrict__ wts, int M,
-               int N, double dscale, float* __restrict__ Dout, float* __restrict__ Rnl,
-               unsigned* __restrict__ status) {
+nl_list_f32(const NlTile* __restrict__ tiles, const int* __restrict__ ntiles, const int* __restrict__ nlist,
+            const int* __restrict__ NLtab, int Mnl, const float* __restrict__ frames, const float4* __restrict__ c32,
+            const double* __restrict__ fG, const LT* __restrict__ lm, const float* __restrict__ lmoff,
+            const double* __restrict__ lG, const float* __restrict__ wts, int M, int N, double dscale,
+            float* __restrict__ Dout, float* __restrict__ Rnl, unsigned* __restrict__ status,
+            const double4* __restrict__ qxy, const float* __restrict__ Bseg, const int* __restrict__ segof) {
   if ((int)blockIdx.y >= *ntiles) return;  // uniform over the block
   const NlTile w = tiles[blockIdx.y];
-  exact_tile_f32<LT>(w.rows, nlist + w.p0, frames, c32, fG, lm, lmoff, lG, wts, M, N, dscale, Dout, Rnl, status, 0,
-                     blockIdx.x * EX_TM, NLtab + (size_t)w.slot * Mnl, Mnl);
+  exact_tile_f32<LT, APPROX>(w.rows, nlist + w.p0, frames, c32, fG, lm, lmoff, lG, wts, M, N, dscale, Dout, Rnl,
+                             status, 0, blockIdx.x * EX_TM, NLtab + (size_t)w.slot * Mnl, Mnl, qxy, Bseg, segof);
+}
+
+// Eq. (close_dist) for every landmark of the frames row_frame[0 .. *count) (frames of
+// different close structures may share a tile: the rotation is per pair)
+template <typename LT>
+__global__ void __launch_bounds__(EX_THREADS, 4)
+approx_rows_f32(const int* __restrict__ row_frame, const int* __restrict__ count, const float* __restrict__ frames,
+                const float4* __restrict__ c32, const LT* __restrict__ lm, const float* __restrict__ lmoff,
+                const float* __restrict__ wts, int M, int N, double dscale, float* __restrict__ Dout,
+                const double4* __restrict__ qxy, const float* __restrict__ Bseg, const int* __restrict__ segof) {
+  const int rows = *count;
+  exact_tile_f32<LT, true>(rows, row_frame, frames, c32, nullptr, lm, lmoff, nullptr, wts, M, N, dscale, Dout, nullptr,
+                           nullptr, blockIdx.y * EX_TF, blockIdx.x * EX_TM, nullptr, 0, qxy, Bseg, segof);
 }
 
 // FP64 mode: one pass, FP64 correlation, FP64 eigenvalue and D = G_x + G_a - 2 lambda_max
@@ -896,15 +933,44 @@ void launch_nl_exact_tiles(Prec p, int max_tiles, const NlLists& nl, const NlTil
   if (max_tiles <= 0 || p == P_F64) return;
   dim3 grid((Mnl + EX_TM - 1) / EX_TM, max_tiles);
   if (p == P_F32)
-    exact_list_f32<float><<<grid, EX_THREADS, 0, st>>>(tiles, nl.counts + 3, nl.nlist, NLtab, Mnl, (const float*)frames,
-                                                       fi.c32, fi.G, (const float*)L.coords, L.off, L.G, L.w, L.M,
-                                                       L.N, L.dscale, (float*)D, (float*)Rnl, status);
+    nl_list_f32<float, false><<<grid, EX_THREADS, 0, st>>>(
+        tiles, nl.counts + 3, nl.nlist, NLtab, Mnl, (const float*)frames, fi.c32, fi.G, (const float*)L.coords, L.off,
+        L.G, L.w, L.M, L.N, L.dscale, (float*)D, (float*)Rnl, status, nullptr, nullptr, nullptr);
   else
-    exact_list_f32<__half><<<grid, EX_THREADS, 0, st>>>(tiles, nl.counts + 3, nl.nlist, NLtab, Mnl,
-                                                        (const float*)frames, fi.c32, fi.G, (const __half*)L.coords,
-                                                        L.off, L.G, L.w, L.M, L.N, L.dscale, (float*)D, (float*)Rnl,
-                                                        status);
+    nl_list_f32<__half, false><<<grid, EX_THREADS, 0, st>>>(
+        tiles, nl.counts + 3, nl.nlist, NLtab, Mnl, (const float*)frames, fi.c32, fi.G, (const __half*)L.coords,
+        L.off, L.G, L.w, L.M, L.N, L.dscale, (float*)D, (float*)Rnl, status, nullptr, nullptr, nullptr);
   note_launch();
+}
+
+void launch_nl_approx_tiles(Prec p, int max_uapp, int max_tiles, const NlLists& nl, const NlTile* tiles,
+                            const int* NLtab, int Mnl, const void* frames, const LandmarkDev& L, FrameInfo fi,
+                            const double4* qxy, const void* Bseg, const int* segof, void* D, cudaStream_t st) {
+  if (p == P_F64) return;
+  if (max_uapp > 0) {  // update frames that are not reassignments: every landmark
+    dim3 grid((L.M + EX_TM - 1) / EX_TM, (max_uapp + EX_TF - 1) / EX_TF);
+    if (p == P_F32)
+      approx_rows_f32<float><<<grid, EX_THREADS, 0, st>>>(nl.uapp_list, nl.counts + 1, (const float*)frames, fi.c32,
+                                                          (const float*)L.coords, L.off, L.w, L.M, L.N, L.dscale,
+                                                          (float*)D, qxy, (const float*)Bseg, segof);
+    else
+      approx_rows_f32<__half><<<grid, EX_THREADS, 0, st>>>(nl.uapp_list, nl.counts + 1, (const float*)frames, fi.c32,
+                                                           (const __half*)L.coords, L.off, L.w, L.M, L.N, L.dscale,
+                                                           (float*)D, qxy, (const float*)Bseg, segof);
+    note_launch();
+  }
+  if (max_tiles > 0) {  // frames between updates: their lists
+    dim3 grid((Mnl + EX_TM - 1) / EX_TM, max_tiles);
+    if (p == P_F32)
+      nl_list_f32<float, true><<<grid, EX_THREADS, 0, st>>>(
+          tiles, nl.counts + 3, nl.nlist, NLtab, Mnl, (const float*)frames, fi.c32, nullptr, (const float*)L.coords,
+          L.off, nullptr, L.w, L.M, L.N, L.dscale, (float*)D, nullptr, nullptr, qxy, (const float*)Bseg, segof);
+    else
+      nl_list_f32<__half, true><<<grid, EX_THREADS, 0, st>>>(
+          tiles, nl.counts + 3, nl.nlist, NLtab, Mnl, (const float*)frames, fi.c32, nullptr, (const __half*)L.coords,
+          L.off, nullptr, L.w, L.M, L.N, L.dscale, (float*)D, nullptr, nullptr, qxy, (const float*)Bseg, segof);
+    note_launch();
+  }
 }
 
 void launch_approx_pairs(Prec p, int max_rows, const int* approx_list, const int* approx_seg, const int* count,

@@ -736,6 +736,10 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
   const int nl_upd = nl ? c->small_host->nl_counts[0] : 0;
   const int nl_uapp = nl ? c->small_host->nl_counts[1] : 0;
   const int nl_between = nl ? c->small_host->nl_counts[2] : 0;
+  if (nl && gs && gz && c->prec != P_F64 &&
+      (ps = ensure(c, c->nlPart, sizeof(float) * 6 * (size_t)nl_beta_split(nl_upd, M, c->N) * nl_upd * c->N)) !=
+          PCV_OK)
+    return ps;
   const size_t seg_bytes = work_elem(c->prec) * 9 * (size_t)M;
   if ((ps = ensure(c, c->Bseg, seg_bytes * (size_t)(nref + 1))) != PCV_OK) return ps;
   if (had_prior) CUDA_TRY(c, cudaMemcpyAsync(c->Bseg.p, c->Bprior.p, seg_bytes, cudaMemcpyDeviceToDevice, st));
@@ -793,7 +797,30 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
     launch_materialize_frames(napp, &sm->approx_count, (const int*)c->alist.p, (const int*)c->aseg.p, seg_base, L,
                               frames, fi, rec.qxy, (const float*)c->Yc.p, (float*)c->Xr.p, (float*)c->Nx.p, st);
   }
-  if (nl) {
+  // FP32 / FP16 storage: tiles of up to 16 frames sharing a list (and a close structure)
+  const bool nl_tiled = nl && c->prec != P_F64;
+  const int nl_max_tiles = (nl_between + NL_TILE_F - 1) / NL_TILE_F + nl_upd + 1;
+  NlTile* tl = (NlTile*)c->nlTiles.p;
+  if (nl_tiled) {
+    {
+      PROF(c, K_NL_SCHEDULE);
+      launch_nl_tiles(F, nll, tl, st);
+    }
+    {  // all-landmark approximate distances of the update frames that are not reassignments
+      PROF(c, K_APPROX);
+      launch_nl_approx_tiles(c->prec, nl_uapp, 0, nll, tl, (const int*)c->NLtab.p, Mnl, frames, L, fi, rec.qxy,
+                             c->Bseg.p, (const int*)c->segof.p, c->Dbuf.p, st);
+    }
+    {
+      PROF(c, K_NL_SELECT);
+      launch_nl_select(c->prec, nl_upd, nll, M, Mnl, c->Dbuf.p, (int*)c->NLtab.p, st);
+    }
+    if ((ps = nl_stage_carried(c)) != PCV_OK) return ps;
+    PROF(c, K_NL_PAIR);
+    launch_nl_fill_inf(c->prec, nl_between, nll, M, c->Dbuf.p, st);
+    launch_nl_approx_tiles(c->prec, 0, nl_max_tiles, nll, tl, (const int*)c->NLtab.p, Mnl, frames, L, fi, rec.qxy,
+                           c->Bseg.p, (const int*)c->segof.p, c->Dbuf.p, st);
+  } else if (nl) {
     {  // all-landmark approximate distances of the update frames that are not reassignments
       PROF(c, K_APPROX);
       launch_approx_pairs(c->prec, nl_uapp, nll.uapp_list, nll.uapp_seg, &nll.counts[1], frames, L, fi, rec.qxy,
@@ -826,8 +853,13 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
   if (grads && nl) {
     {
       PROF(c, K_NL_BETA);
-      launch_nl_beta(c->prec, F, nll, (const int*)c->NLtab.p, Mnl, L, c->Dbuf.p, s, c->lambda, nullptr, nullptr,
-                     c->Bseg.p, (const int*)c->segof.p, gs, gz, st);
+      if (nl_tiled)
+        launch_nl_beta_tiles(c->prec, nl_upd, nl_max_tiles, nll, tl, (const int*)c->NLtab.p, Mnl, L, c->Dbuf.p, s,
+                             c->lambda, nullptr, nullptr, c->Bseg.p, (const int*)c->segof.p, gs, gz,
+                             (float*)c->nlPart.p, st);
+      else
+        launch_nl_beta(c->prec, F, nll, (const int*)c->NLtab.p, Mnl, L, c->Dbuf.p, s, c->lambda, nullptr, nullptr,
+                       c->Bseg.p, (const int*)c->segof.p, gs, gz, st);
     }
     PROF(c, K_ADJ_FINISH);
     launch_adjoint_finish(c->prec, F, frames, L, fi, c->Dbuf.p, s, c->lambda, c->Bseg.p, (const int*)c->segof.p, rec,
@@ -963,7 +995,7 @@ pcv_status evaluate_exact_nl(pcv_ctx* c, int F, const void* frames, double* s, d
       PROF(c, K_NL_BETA);
       if (tiles)
         launch_nl_beta_tiles(c->prec, nupd, max_tiles, nll, tl, (const int*)c->NLtab.p, Mnl, L, c->Dbuf.p, s,
-                             c->lambda, c->Rupd.p, c->Rnl.p, gs, gz, (float*)c->nlPart.p, st);
+                             c->lambda, c->Rupd.p, c->Rnl.p, nullptr, nullptr, gs, gz, (float*)c->nlPart.p, st);
       else
         launch_nl_beta(c->prec, F, nll, (const int*)c->NLtab.p, Mnl, L, c->Dbuf.p, s, c->lambda, c->Rupd.p,
                        c->Rnl.p, nullptr, nullptr, gs, gz, st);

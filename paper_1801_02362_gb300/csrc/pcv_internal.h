@@ -299,8 +299,15 @@ void launch_nl_exact_tiles(Prec p, int max_tiles, const NlLists& nl, const NlTil
 // into nl_beta_split ranges whose partial sums go to part, nl_beta_split * max_upd * N * 6
 // floats), then the frames in between over their lists (rotations Rnl)
 int nl_beta_split(int max_upd, int M, int N);
+// (close mode: Bseg and segof given, rotations R_{a_i y} of each frame's segment)
 void launch_nl_beta_tiles(Prec p, int max_upd, int max_tiles, const NlLists& nl, const NlTile* tiles, const int* NLtab,
                           int Mnl, const LandmarkDev& L, const void* P, const double* s, double lambda,
-                          const void* Rupd, const void* Rnl, void* gs, void* gz, float* part, cudaStream_t st);
+                          const void* Rupd, const void* Rnl, const void* Bseg, const int* segof, void* gs, void* gz,
+                          float* part, cudaStream_t st);
+// close mode, FP32 / FP16 storage: Eq. (close_dist) for every landmark of the approximate
+// update frames (uapp_list) and for the listed landmarks of the tiles (k_pair.cu)
+void launch_nl_approx_tiles(Prec p, int max_uapp, int max_tiles, const NlLists& nl, const NlTile* tiles,
+                            const int* NLtab, int Mnl, const void* frames, const LandmarkDev& L, FrameInfo fi,
+                            const double4* qxy, const void* Bseg, const int* segof, void* D, cudaStream_t st);
 
 }  // namespace pcv
