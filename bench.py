@@ -274,6 +274,30 @@ def time_config(pcv, label: str, seed: int, n: int, m: int, f: int, eps: float, 
            "kernel_ms": {k: round(v[0] / steps, 4) for k, v in pr.items()}}
     if nl is not None:
         out["neighbor_list"] = {"size": nl[0], "stride": nl[1]}
+        # algorithmic FP32 work of the list kernels against the FP32 peak: frames between
+        # updates x listed landmarks x atoms (exact: 45 flop, approximate: 27 flop -- R a,
+        # 3 sub, 3 FMA -- per unit); the adjoint over every frame's own landmarks (36 flop:
+        # beta^s and beta^z, 2 x 9 FMA)
+        m_nl = nl[0]
+        if eps < 0:
+            n_upd = (st["landmark_alignments"] - m_nl * f) / (m - m_nl)
+            pair_flop = 45
+        else:
+            nref = st["landmark_alignments"] / m
+            n_uapp = (st["approx_msds"] - m_nl * (f - nref)) / (m - m_nl)
+            n_upd = nref + n_uapp
+            pair_flop = 27
+        n_between = f - n_upd
+        work = {"nl_pair": n_between * m_nl * n * pair_flop}
+        if grad:
+            work["nl_beta"] = (n_upd * m + n_between * m_nl) * n * 36
+        roof = {}
+        for name, flop in work.items():
+            if name in pr:
+                ms = pr[name][0] / steps
+                tf = flop / (ms / 1e3) / 1e12
+                roof[name] = {"ms": round(ms, 4), "TFLOP_s": round(tf, 2), "frac_fp32_peak": round(tf / FP32_PEAK_TFLOPS, 4)}
+        out["list_kernels"] = roof
     # expensive distance computations per step (the cost model of the paper's Section 6.2)
     out["expensive_per_step"] = (st["xy_alignments"] + st["landmark_alignments"]) / f
     return out
