@@ -58,6 +58,9 @@ def lib():
         L.orc_exact_nl.argtypes = [c_int, c_int, c_int, dp, dp, dp, dp, c_double, c_int, c_int, i32p, i64p,
                                    dp, dp, dp, dp, dp]
         L.orc_nl_select.argtypes = [c_int, dp, c_int, i32p]
+        L.orc_hills_value.argtypes = [c_int, dp, c_double, c_double, c_double, c_double, c_double, dp, dp, dp]
+        L.orc_metad.argtypes = [c_int, c_int, dp, dp, dp, dp, c_double, c_double, c_double, c_int, c_int, dp, i64p,
+                                dp, dp]
         L.orc_close_distance.argtypes = [c_int, dp, dp, dp, dp, dp]
         L.orc_close_distance.restype = c_double
         for name in ("orc_cost_original", "orc_cost_close", "orc_amdahl"):
@@ -211,6 +214,45 @@ def close(frames, landmarks, lam, eps, state: CloseState | None = None, w=None, 
     if st != 0:
         raise RuntimeError(f"oracle close: status {st}")
     return dict(s=s, z=z, D=D, refreshed=ref, dxy=dxy, dsdx=gs, dzdx=gz, state=state)
+
+
+def hills_value(hills, w, sigma_s, sigma_z, s, z):
+    """V, dV/ds, dV/dz of the Gaussian-hill bias (Eq. vbias) at (s, z)."""
+    h = np.ascontiguousarray(np.asarray(hills, dtype=np.float64).reshape(-1, 2))
+    out = np.zeros(3)
+    lib().orc_hills_value(h.shape[0], _p(h), float(w), float(sigma_s), float(sigma_z), float(s), float(z),
+                          _p(out[0:1]), _p(out[1:2]), _p(out[2:3]))
+    return out[0], out[1], out[2]
+
+
+class MetadState:
+    """Hills deposited so far and the step count of a metadynamics run (Eq. vbias)."""
+
+    def __init__(self, cap: int = 4096):
+        self.hills = np.zeros((cap, 2))
+        self.state = np.zeros(2, dtype=np.int64)
+
+    @property
+    def n_hills(self) -> int:
+        return int(self.state[0])
+
+
+def metad(s, z, w, sigma_s, sigma_z, stride, state: MetadState | None = None, dsdx=None, dzdx=None):
+    """Bias V of each frame (hills of earlier steps) and force -dV/dx; deposits hills every
+    `stride` steps at (s_t, z_t) after frame t is evaluated."""
+    s, z = _f64(s), _f64(z)
+    f = s.shape[0]
+    if state is None:
+        state = MetadState()
+    n = 0 if dsdx is None else dsdx.shape[1]
+    V = np.zeros(f)
+    force = np.zeros((f, n, 3)) if dsdx is not None else None
+    st = lib().orc_metad(f, n, _p(s), _p(z), _p(_f64(dsdx)), _p(_f64(dzdx)), float(w), float(sigma_s),
+                         float(sigma_z), int(stride), state.hills.shape[0], _p(state.hills),
+                         _p(state.state, ctypes.c_int64), _p(V), _p(force))
+    if st != 0:
+        raise RuntimeError(f"oracle metad: status {st}")
+    return dict(V=V, force=force, state=state)
 
 
 def close_distance(x, y, B, a, w=None):

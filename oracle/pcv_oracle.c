@@ -22,6 +22,8 @@
  *     the M_nl closest kept; the other steps use only those.  With the close structure
  *     the list is chosen from the approximate distances, and a reassignment (which
  *     computes every distance exactly) also chooses it;
+ *   - Gaussian-hill metadynamics bias on (s, z), Eq. (vbias), and its force through the
+ *     path-CV derivatives;
  *   - cost model of Section 6.2 ("Theoretical Speedup") and Amdahl's law, Eq. (ahmdal).
  *
  * Everything is double precision, plain loops, one frame / one landmark at a time.
@@ -693,6 +695,54 @@ double orc_close_distance(int n, const double* w_in, const double* x, const doub
   free(xc);
   free(w);
   return dd;
+}
+
+/* ------------------------------------------------------------------------------ */
+/* metadynamics bias on the path CVs, Eq. (vbias)                                   */
+
+/* Gaussian-hill bias V(s, z) = sum_k w exp(-(s - s_k)^2 / (2 sigma_s^2) - (z - z_k)^2 /
+ * (2 sigma_z^2)) over the hills deposited so far, and its derivatives dV/ds, dV/dz. */
+void orc_hills_value(int n_hills, const double* hills, double w, double sigma_s, double sigma_z, double s, double z,
+                     double* V, double* dVds, double* dVdz) {
+  double v = 0.0, gs = 0.0, gz = 0.0;
+  for (int k = 0; k < n_hills; ++k) {
+    const double ds = s - hills[2 * k], dz = z - hills[2 * k + 1];
+    const double e = w * exp(-ds * ds / (2.0 * sigma_s * sigma_s) - dz * dz / (2.0 * sigma_z * sigma_z));
+    v += e;
+    gs += -e * ds / (sigma_s * sigma_s);
+    gz += -e * dz / (sigma_z * sigma_z);
+  }
+  *V = v;
+  *dVds = gs;
+  *dVdz = gz;
+}
+
+/* Metadynamics over F time-ordered frames with path CVs s, z and their derivatives (N x 3
+ * per frame, optional).  Frame t sees the hills deposited at earlier steps; after it is
+ * evaluated, a hill is deposited at (s_t, z_t) when its step index (state[1]) is a multiple
+ * of the stride tau_G (Eq. vbias: hills every tau_G steps, the bias of a step summing the
+ * hills of the steps before it).  Outputs V (F), and force = -dV/dx = -(dV/ds ds/dx + dV/dz
+ * dz/dx) (F x N x 3, optional).  hills: capacity cap pairs (s_k, z_k); state[0] = hills
+ * held, state[1] = steps done.  Returns ORC_EINVAL when the capacity would be exceeded. */
+int orc_metad(int f, int n, const double* s, const double* z, const double* dsdx, const double* dzdx, double w,
+              double sigma_s, double sigma_z, int stride, int cap, double* hills, int64_t* state, double* V,
+              double* force) {
+  if (f < 0 || n < 0 || stride < 1 || !(sigma_s > 0.0) || !(sigma_z > 0.0)) return ORC_EINVAL;
+  for (int t = 0; t < f; ++t) {
+    double dVds, dVdz;
+    orc_hills_value((int)state[0], hills, w, sigma_s, sigma_z, s[t], z[t], V + t, &dVds, &dVdz);
+    if (force && dsdx && dzdx)
+      for (int e = 0; e < 3 * n; ++e)
+        force[(size_t)t * 3 * n + e] = -(dVds * dsdx[(size_t)t * 3 * n + e] + dVdz * dzdx[(size_t)t * 3 * n + e]);
+    if (state[1] % stride == 0) {
+      if (state[0] >= cap) return ORC_EINVAL;
+      hills[2 * state[0]] = s[t];
+      hills[2 * state[0] + 1] = z[t];
+      state[0] += 1;
+    }
+    state[1] += 1;
+  }
+  return ORC_OK;
 }
 
 /* ------------------------------------------------------------------------------ */
