@@ -92,6 +92,9 @@ DETAILS = {
     "nl_close_m2120": ("config", dict(label="close-structure path CV with gradients, N=304, M=2120, F=10000, FP32, "
                                             "eps=0.05, neighbour list 50 every 50 steps", seed=8, n=304, m=2120,
                                       f=10_000, eps=0.05, grad=True, precision="fp32", nl=(50, 50))),
+    # the consumer of s, z and their derivatives: Gaussian-hill bias and force on the frames of
+    # the headline workload's size
+    "metad_bias_f100k": ("metad", dict(f=100_000, n=300, hills=2000, stride=500)),
     "nl_close_m2120_nolist": ("config", dict(label="close-structure path CV with gradients, N=304, M=2120, F=10000, "
                                                    "FP32, eps=0.05, no neighbour list", seed=8, n=304, m=2120,
                                              f=10_000, eps=0.05, grad=True, precision="fp32")),
@@ -102,6 +105,8 @@ def run_detail(pcv, name: str, calls: int = 200) -> dict:
     kind, kw = DETAILS[name]
     if kind == "stream":
         return time_stream(pcv, calls=calls, **kw)
+    if kind == "metad":
+        return time_metad(pcv, **kw)
     if kind == "group":
         return time_group(pcv, **kw)
     return time_config(pcv, **kw)
@@ -359,6 +364,55 @@ def time_stream(pcv, precision: str, n: int = 5000, m: int = 2000, calls: int = 
             "refreshes": st["refreshes_threshold"] - st0["refreshes_threshold"],
             "kernels": kern, "hbm_peak_GB_per_s": hbm,
             "kernel_ms": {k: round(v[0] / calls, 4) for k, v in pr.items()}}
+
+
+def time_metad(pcv, f: int, n: int, hills: int, stride: int, seed: int = 9, steps: int = 10) -> dict:
+    """Metadynamics bias (Eq. vbias) on F steps: `hills` hills held before the call, a hill
+    every `stride` steps; s, z a seeded walk along a 200-landmark path, ds/dx, dz/dx seeded
+    FP32 arrays of N atoms.  Times the bias alone (hill sums) and with the force (the
+    chain-rule pass over F x N x 3 derivatives, HBM-bound)."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    s = torch.tensor(np.clip(1 + np.cumsum(rng.normal(scale=0.05, size=f)) % 199, 1, 200), device="cuda")
+    z = torch.tensor(rng.uniform(0.0, 0.02, size=f), device="cuda")
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    dsdx = torch.randn((f, n, 3), generator=g, device="cuda", dtype=torch.float32)
+    dzdx = torch.randn((f, n, 3), generator=g, device="cuda", dtype=torch.float32)
+    h0 = np.stack([rng.uniform(1, 200, hills), rng.uniform(0, 0.02, hills)], axis=1)
+    mt = pcv.Metad(1.0, 0.3, 0.002, stride, max_hills=hills + (steps + 4) * (f // stride + 1))
+    stream = torch.cuda.current_stream()
+    out = {}
+    for label, with_force in (("bias_only", False), ("bias_and_force", True)):
+        mt.set_hills(h0, 1)
+        for _ in range(2):
+            mt.apply(s, z, dsdx if with_force else None, dzdx if with_force else None)
+        mt.set_hills(h0, 1)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            mt.apply(s, z, dsdx if with_force else None, dzdx if with_force else None)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[label] = a.elapsed_time(b) / steps
+    n_end = mt.hills()[0].shape[0]
+    mt.close()
+    # hills seen per step, averaged over the timed calls (the hill set grows by f/stride per call)
+    avg_hills = (hills + n_end) / 2.0
+    evals = f * avg_hills
+    flops = evals * 14  # per hill: 2 sub, 2 mul + FMA (argument), exp (~4 flop), mul, add, 2 x (mul, FMA)
+    force_bytes = f * n * 3 * 4 * 3  # read ds/dx, dz/dx, write the force (FP32)
+    t_force = max(out["bias_and_force"] - out["bias_only"], 1e-9)
+    hbm = measured_peaks().get("hbm_gbs", 6793.8)
+    return {"workload": f"metadynamics bias on {f} steps, {hills}+ hills, a hill every {stride} steps, N={n} "
+                        "FP32 derivatives", "ms_bias_only": out["bias_only"], "ms_bias_and_force": out["bias_and_force"],
+            "steps_per_s": f / (out["bias_and_force"] / 1e3), "hill_evaluations_per_s": evals / (out["bias_only"] / 1e3),
+            "bias_TFLOP_s": flops / (out["bias_only"] / 1e3) / 1e12,
+            "bias_frac_fp32_peak": flops / (out["bias_only"] / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+            "force_GB_s": force_bytes / (t_force / 1e3) / 1e9,
+            "force_frac_hbm_peak": force_bytes / (t_force / 1e3) / 1e9 / hbm}
 
 
 def time_group(pcv, n_inst: int = 256, f: int = 512, seed: int = 7, steps: int = 5) -> dict:

@@ -333,6 +333,43 @@ PCV_API pcv_status pcv_evaluate_exact_noalloc(int F, int M, int N, const float* 
                                               const double* q, double lambda, double* s, double* z, double* msd,
                                               void* cuda_stream, char* err, size_t err_len);
 
+/* Gaussian-hill metadynamics on the path CVs (Eq. vbias, Section 2): the consumer of s, z
+ * and their derivatives that turns them into a bias potential and a bias force.
+ *
+ * A hill of height `height` and widths sigma_s, sigma_z (in s and z units) is deposited at
+ * (s_t, z_t) at every step t whose index is a multiple of `stride` (tau_G).  The bias of a
+ * step sums the hills of the steps before it:
+ *   V_t = sum_k height exp(-(s_t - s_k)^2 / (2 sigma_s^2) - (z_t - z_k)^2 / (2 sigma_z^2)),
+ * and its force is F_t = -dV_t/dx = -(dV/ds ds/dx + dV/dz dz/dx).  Steps are counted from
+ * creation (or pcv_metad_set_hills) across calls; each call evaluates F consecutive steps.
+ * The hills live in device memory of the object (capacity max_hills, fixed at creation).
+ * The Gaussians are evaluated in FP32 from FP64 differences (relative error ~1e-6).
+ *
+ * pcv_metad_create: device, stream (cudaStream_t, NULL = legacy default), height (finite;
+ *   negative gives a well), sigma_s, sigma_z > 0, stride >= 1, max_hills >= 1.  Errors:
+ *   PCV_EINVAL, PCV_ECUDA, PCV_ENOMEM.
+ * pcv_metad_apply: s, z device, F doubles (e.g. from pcv_evaluate); dsdx, dzdx device,
+ *   F*N*3 (double in PCV_FP64 `precision`, else float), may be NULL when force is NULL;
+ *   bias device, F doubles (out); force device, F*N*3 of the same type (out) or NULL.
+ *   Asynchronous on the object's stream.  Errors: PCV_EINVAL (sizes, NULL inputs, hill
+ *   capacity exceeded -- checked before any work), PCV_ECUDA.
+ * pcv_metad_get_hills: copies the n_hills hills (s_k, z_k) to host memory (hills may be
+ *   NULL to query the count) and the step count; synchronises the stream.
+ * pcv_metad_set_hills: replaces the hills (host memory, n_hills pairs) and the step count
+ *   (restart).  Synchronises the stream.
+ * The paper accumulates the hills on a grid to bound the cost of long runs; the GPU sums
+ * them directly (frames x hills, one warp per frame). */
+typedef struct pcv_metad pcv_metad;
+PCV_API pcv_status pcv_metad_create(pcv_metad** out, int device, void* cuda_stream, double height, double sigma_s,
+                                    double sigma_z, int stride, int max_hills);
+PCV_API pcv_status pcv_metad_destroy(pcv_metad* m);
+PCV_API pcv_status pcv_metad_set_stream(pcv_metad* m, void* cuda_stream);
+PCV_API pcv_status pcv_metad_apply(pcv_metad* m, int precision, int F, int N, const double* s, const double* z,
+                                   const void* dsdx, const void* dzdx, double* bias, void* force);
+PCV_API pcv_status pcv_metad_get_hills(pcv_metad* m, double* hills, int cap, int* n_hills, int64_t* steps);
+PCV_API pcv_status pcv_metad_set_hills(pcv_metad* m, const double* hills, int n_hills, int64_t steps);
+PCV_API const char* pcv_metad_last_error(const pcv_metad* m);
+
 /* One-line description of the last error on ctx (never NULL). */
 PCV_API const char* pcv_last_error(const pcv_ctx* ctx);
 

@@ -830,6 +830,29 @@ __global__ void combine_grad_kernel(size_t n, int N3, const double* __restrict__
   out[k] = (T)(a * (double)gs[k] + b * (double)gz[k]);
 }
 
+// FP32 rows: one block per frame row (grid-stride over rows), 16-byte vectors when the row
+// length 3N is a multiple of 4 and the buffers are 16-byte aligned; FP32 arithmetic (the
+// output is FP32)
+template <bool VEC>
+__global__ void combine_rows_f32(int F, int N3, const double* __restrict__ g_s, const double* __restrict__ g_z,
+                                 const float* __restrict__ gs, const float* __restrict__ gz, float* __restrict__ out) {
+  for (int f = blockIdx.x; f < F; f += gridDim.x) {
+    const float a = g_s ? (float)g_s[f] : 0.0f, b = g_z ? (float)g_z[f] : 0.0f;
+    const size_t base = (size_t)f * N3;
+    if (VEC) {
+      const float4* x = reinterpret_cast<const float4*>(gs + base);
+      const float4* y = reinterpret_cast<const float4*>(gz + base);
+      float4* o = reinterpret_cast<float4*>(out + base);
+      for (int e = threadIdx.x; e < N3 / 4; e += blockDim.x) {
+        const float4 u = x[e], v = y[e];
+        o[e] = make_float4(fmaf(a, u.x, b * v.x), fmaf(a, u.y, b * v.y), fmaf(a, u.z, b * v.z), fmaf(a, u.w, b * v.w));
+      }
+    } else {
+      for (int e = threadIdx.x; e < N3; e += blockDim.x) out[base + e] = fmaf(a, gs[base + e], b * gz[base + e]);
+    }
+  }
+}
+
 __global__ void fill_u8_kernel(uint8_t* p, uint8_t v, size_t n) {
   const size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (k < n) p[k] = v;
@@ -972,9 +995,18 @@ void launch_combine_grad(Prec p, int F, int N3, const double* g_s, const double*
   if (p == P_F64)
     combine_grad_kernel<double><<<blocks_for(n, 256), 256, 0, st>>>(n, N3, g_s, g_z, (const double*)gs,
                                                                      (const double*)gz, (double*)out);
-  else
-    combine_grad_kernel<float><<<blocks_for(n, 256), 256, 0, st>>>(n, N3, g_s, g_z, (const float*)gs,
-                                                                    (const float*)gz, (float*)out); note_launch();
+  else {
+    const bool vec = N3 % 4 == 0 && ((uintptr_t)gs % 16) == 0 && ((uintptr_t)gz % 16) == 0 && ((uintptr_t)out % 16) == 0;
+    const unsigned blocks = (unsigned)(F < 152 * 16 ? F : 152 * 16);
+    const unsigned threads = N3 >= 1024 ? 256 : 128;
+    if (vec)
+      combine_rows_f32<true><<<blocks, threads, 0, st>>>(F, N3, g_s, g_z, (const float*)gs, (const float*)gz,
+                                                          (float*)out);
+    else
+      combine_rows_f32<false><<<blocks, threads, 0, st>>>(F, N3, g_s, g_z, (const float*)gs, (const float*)gz,
+                                                           (float*)out);
+  }
+  note_launch();
 }
 
 void launch_fill_u8(uint8_t* p, uint8_t v, size_t n, cudaStream_t st) {

@@ -73,6 +73,13 @@ SIGNATURES = {
     "pcv_evaluate_exact_noalloc": (_i, [_i, _i, _i, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, ctypes.c_char_p,
                                        ctypes.c_size_t]),
     "pcv_evaluate_group": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(pcv_batch_io), _vp]),
+    "pcv_metad_create": (_i, [ctypes.POINTER(_vp), _i, _vp, _d, _d, _d, _i, _i]),
+    "pcv_metad_destroy": (_i, [_vp]),
+    "pcv_metad_set_stream": (_i, [_vp, _vp]),
+    "pcv_metad_apply": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "pcv_metad_get_hills": (_i, [_vp, _vp, _i, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_int64)]),
+    "pcv_metad_set_hills": (_i, [_vp, _vp, _i, ctypes.c_int64]),
+    "pcv_metad_last_error": (ctypes.c_char_p, [_vp]),
     "pcv_shard_pack": (_i, [_i, _i, _i, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "pcv_shard_unpack": (_i, [_i, _i, _i, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "pcv_shard_pack_host": (_i, [_i, _i, _i, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -270,6 +277,48 @@ def pcv_shard_unpack_host(lam: float, zmin: np.ndarray, scalars: np.ndarray, ele
     return s, z, gs, gz
 
 
+def _check_metad(m, st):
+    if st != PCV_OK:
+        msg = load().pcv_metad_last_error(m)
+        raise PcvError(st, msg.decode() if msg else "")
+
+
+def pcv_metad_create(device: int, stream, height: float, sigma_s: float, sigma_z: float, stride: int,
+                     max_hills: int):
+    h = ctypes.c_void_p()
+    _check_metad(None, load().pcv_metad_create(ctypes.byref(h), device, stream, float(height), float(sigma_s),
+                                               float(sigma_z), int(stride), int(max_hills)))
+    return h
+
+
+def pcv_metad_destroy(m):
+    load().pcv_metad_destroy(m)
+
+
+def pcv_metad_set_stream(m, stream):
+    _check_metad(m, load().pcv_metad_set_stream(m, stream))
+
+
+def pcv_metad_apply(m, precision: int, F: int, N: int, s_ptr, z_ptr, dsdx_ptr, dzdx_ptr, bias_ptr, force_ptr):
+    _check_metad(m, load().pcv_metad_apply(m, precision, F, N, s_ptr, z_ptr, dsdx_ptr, dzdx_ptr, bias_ptr,
+                                           force_ptr))
+
+
+def pcv_metad_get_hills(m):
+    """(hills as an (n, 2) array, step count)"""
+    n = ctypes.c_int(0)
+    steps = ctypes.c_int64(0)
+    _check_metad(m, load().pcv_metad_get_hills(m, None, 0, ctypes.byref(n), ctypes.byref(steps)))
+    out = np.zeros((max(n.value, 1), 2))
+    _check_metad(m, load().pcv_metad_get_hills(m, out.ctypes.data, n.value, ctypes.byref(n), ctypes.byref(steps)))
+    return out[:n.value], int(steps.value)
+
+
+def pcv_metad_set_hills(m, hills: np.ndarray, steps: int):
+    h = np.ascontiguousarray(np.asarray(hills, dtype=np.float64).reshape(-1, 2))
+    _check_metad(m, load().pcv_metad_set_hills(m, h.ctypes.data if h.size else None, h.shape[0], int(steps)))
+
+
 def pcv_last_error(ctx) -> str:
     m = load().pcv_last_error(ctx)
     return m.decode() if m else ""
@@ -378,6 +427,47 @@ class PathCV:
 
     def load_state(self, blob: bytes):
         pcv_load_state(self.ctx, blob)
+
+
+class Metad:
+    """Gaussian-hill metadynamics bias on (s, z) (pcv_metad_*) bound to a CUDA device and the
+    current torch stream."""
+
+    def __init__(self, height: float, sigma_s: float, sigma_z: float, stride: int, max_hills: int = 100_000,
+                 device: int = 0):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        self.m = pcv_metad_create(device, torch.cuda.current_stream(self.device).cuda_stream, height, sigma_s,
+                                  sigma_z, stride, max_hills)
+
+    def close(self):
+        if getattr(self, "m", None):
+            pcv_metad_destroy(self.m)
+            self.m = None
+
+    __del__ = close
+
+    def apply(self, s, z, dsdx=None, dzdx=None, precision: str = "fp32") -> dict:
+        """bias (F doubles) and, with dsdx / dzdx, the force -dV/dx (same shape and type)."""
+        torch = self.torch
+        F = s.shape[0]
+        out = {"bias": torch.empty(F, dtype=torch.float64, device=s.device)}
+        N = 0
+        if dsdx is not None:
+            out["force"] = torch.empty_like(dsdx)
+            N = dsdx.shape[1]
+        pcv_metad_set_stream(self.m, torch.cuda.current_stream(self.device).cuda_stream)
+        pcv_metad_apply(self.m, _PREC[precision], F, N, _ptr(s), _ptr(z), _ptr(dsdx), _ptr(dzdx), _ptr(out["bias"]),
+                        _ptr(out.get("force")))
+        return out
+
+    def hills(self):
+        return pcv_metad_get_hills(self.m)
+
+    def set_hills(self, hills, steps: int):
+        pcv_metad_set_hills(self.m, hills, steps)
 
 
 def _make_function():
