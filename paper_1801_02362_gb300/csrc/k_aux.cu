@@ -6,6 +6,8 @@
 //   the gradients.
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "pcv_device.cuh"
 #include "pcv_internal.h"
 
@@ -1006,6 +1008,29 @@ void launch_combine_grad(Prec p, int F, int N3, const double* g_s, const double*
       combine_rows_f32<false><<<blocks, threads, 0, st>>>(F, N3, g_s, g_z, (const float*)gs, (const float*)gz,
                                                            (float*)out);
   }
+  note_launch();
+}
+
+// device-to-device copy by the SMs (16-byte pieces when both ends are aligned): keeps the
+// copy engines free for host transfers running next to the evaluation
+__global__ void dev_copy_kernel(uint8_t* __restrict__ dst, const uint8_t* __restrict__ src, size_t n, int vec) {
+  const size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x, step = (size_t)gridDim.x * blockDim.x;
+  if (vec) {
+    const size_t n16 = n / 16;
+    for (size_t i = i0; i < n16; i += step)
+      reinterpret_cast<uint4*>(dst)[i] = reinterpret_cast<const uint4*>(src)[i];
+    for (size_t i = n16 * 16 + i0; i < n; i += step) dst[i] = src[i];
+  } else {
+    for (size_t i = i0; i < n; i += step) dst[i] = src[i];
+  }
+}
+
+void launch_dev_copy(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return;
+  const int vec = ((uintptr_t)dst % 16) == 0 && ((uintptr_t)src % 16) == 0;
+  const size_t units = vec ? bytes / 16 + 1 : bytes;
+  const unsigned blocks = (unsigned)std::min<size_t>((units + 255) / 256, 152 * 8);
+  dev_copy_kernel<<<blocks, 256, 0, st>>>((uint8_t*)dst, (const uint8_t*)src, bytes, vec);
   note_launch();
 }
 

@@ -3,6 +3,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -36,6 +37,16 @@ struct Small {
   double4 last_c64;
   double last_G;
 };
+
+// copy of the small struct into mapped host memory by the GPU's own stores: the host reads
+// it after a stream synchronisation, and no copy engine is involved (a device-to-host copy
+// here would queue behind large copies in flight on the same engine, e.g. the output copies
+// of pcv_evaluate_host, and stall the refresh search)
+__global__ void small_mirror_kernel(const Small* __restrict__ src, Small* __restrict__ dst) {
+  const unsigned* a = reinterpret_cast<const unsigned*>(src);
+  unsigned* b = reinterpret_cast<unsigned*>(dst);
+  for (unsigned k = threadIdx.x; k < sizeof(Small) / sizeof(unsigned); k += blockDim.x) b[k] = a[k];
+}
 
 __global__ void small_tail_kernel(Small* sm, const int* refresh_list, const float4* c32, const double4* c64,
                                   const double* G) {
@@ -114,7 +125,10 @@ struct pcv_ctx {
   DevBuf Amma, Bmma;              // tensor-core adjoint operands
   DevBuf S6;                      // per-segment landmark moments R A R^T of the finish
   DevBuf h_frames, h_s, h_z, h_gs, h_gz, h_msd, h_ref;  // device staging for pcv_evaluate_host
-  Small* small_host = nullptr;
+  cudaStream_t h2d_stream = nullptr, d2h_stream = nullptr;  // copy streams of pcv_evaluate_host
+  std::vector<cudaEvent_t> h_events;                        // its chunk events
+  Small* small_host = nullptr;      // mapped pinned host memory
+  Small* small_host_dev = nullptr;  // its device-side address
   // state of group evaluations led by this context (pcv_evaluate_group with it first)
   DevBuf grp_inst, grp_tiles;
   std::vector<uint64_t> grp_sig;       // what the captured graph was built for
@@ -243,7 +257,8 @@ RefDesc prior_view(const pcv_ctx* c) {
 }
 
 pcv_status sync_small(pcv_ctx* c) {
-  CUDA_TRY(c, cudaMemcpyAsync(c->small_host, c->small.p, sizeof(Small), cudaMemcpyDeviceToHost, c->stream));
+  small_mirror_kernel<<<1, 64, 0, c->stream>>>((const Small*)c->small.p, c->small_host_dev);
+  note_launch();
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->stats.host_syncs += 1;
   return PCV_OK;
@@ -272,8 +287,9 @@ pcv_status pcv_create(pcv_ctx** out, int device, void* cuda_stream, int precisio
   pcv_status st = ensure(c, c->small, sizeof(Small));
   if (st == PCV_OK) st = ensure(c, c->status, 16);
   if (st == PCV_OK) st = ensure(c, c->nrecheck, 16);
-  if (st == PCV_OK && cudaMallocHost((void**)&c->small_host, sizeof(Small)) != cudaSuccess)
-    st = fail(nullptr, PCV_ENOMEM, "cudaMallocHost failed");
+  if (st == PCV_OK && (cudaHostAlloc((void**)&c->small_host, sizeof(Small), cudaHostAllocMapped) != cudaSuccess ||
+                       cudaHostGetDevicePointer((void**)&c->small_host_dev, c->small_host, 0) != cudaSuccess))
+    st = fail(nullptr, PCV_ENOMEM, "cudaHostAlloc (mapped) failed");
   if (st == PCV_OK && (cudaMemset(c->status.p, 0, 16) != cudaSuccess || cudaMemset(c->nrecheck.p, 0, 16) != cudaSuccess))
     st = fail(nullptr, PCV_ECUDA, "cudaMemset failed");
   if (st != PCV_OK) {
@@ -304,6 +320,12 @@ pcv_status pcv_destroy(pcv_ctx* c) {
   for (cudaEvent_t e : c->grp_ev)
     if (e) cudaEventDestroy(e);
   if (c->grp_stream) cudaStreamDestroy(c->grp_stream);
+  for (cudaStream_t hs : {c->h2d_stream, c->d2h_stream})
+    if (hs) {
+      cudaStreamSynchronize(hs);
+      cudaStreamDestroy(hs);
+    }
+  for (cudaEvent_t e : c->h_events) cudaEventDestroy(e);
   for (const ProfEvent& e : c->prof_pending) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
@@ -593,7 +615,7 @@ NlLists nl_lists(pcv_ctx* c) {
 // the carried-over list is slot 0 of the table
 pcv_status nl_stage_carried(pcv_ctx* c) {
   if (!c->has_nl) return PCV_OK;
-  CUDA_TRY(c, cudaMemcpyAsync(c->NLtab.p, c->nl_keep.p, sizeof(int) * c->nl_size, cudaMemcpyDeviceToDevice, c->stream));
+  launch_dev_copy(c->NLtab.p, c->nl_keep.p, sizeof(int) * c->nl_size, c->stream);
   return PCV_OK;
 }
 
@@ -742,7 +764,7 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
     return ps;
   const size_t seg_bytes = work_elem(c->prec) * 9 * (size_t)M;
   if ((ps = ensure(c, c->Bseg, seg_bytes * (size_t)(nref + 1))) != PCV_OK) return ps;
-  if (had_prior) CUDA_TRY(c, cudaMemcpyAsync(c->Bseg.p, c->Bprior.p, seg_bytes, cudaMemcpyDeviceToDevice, st));
+  if (had_prior) launch_dev_copy(c->Bseg.p, c->Bprior.p, seg_bytes, st);
   void* Bseg1 = (char*)c->Bseg.p + seg_bytes;
   // Frames sharing close structures (segments of 16 frames or more on average): the
   // segment GEMM form of the adjoint, and with FP32 arithmetic and uniform weights the
@@ -849,7 +871,7 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
     launch_finalize(c->prec, F, M, c->Dbuf.p, L.q, L.q32, c->lambda, s, z, (float*)c->mstat.p, (double*)c->mstat.p, msd,
                     gs != nullptr, st);
   }
-  if (refreshed) CUDA_TRY(c, cudaMemcpyAsync(refreshed, rec.flag, F, cudaMemcpyDeviceToDevice, st));
+  if (refreshed) launch_dev_copy(refreshed, rec.flag, F, st);
   if (grads && nl) {
     {
       PROF(c, K_NL_BETA);
@@ -907,10 +929,8 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
     const size_t ybytes = frame_elem(c->prec) * 3 * (size_t)c->N;
     if ((ps = ensure(c, c->y, ybytes)) != PCV_OK) return ps;
     if ((ps = ensure(c, c->Bprior, seg_bytes)) != PCV_OK) return ps;
-    CUDA_TRY(c, cudaMemcpyAsync(c->y.p, (const char*)frames + ybytes * (size_t)last, ybytes,
-                                cudaMemcpyDeviceToDevice, st));
-    CUDA_TRY(c, cudaMemcpyAsync(c->Bprior.p, (char*)c->Bseg.p + seg_bytes * (size_t)nref, seg_bytes,
-                                cudaMemcpyDeviceToDevice, st));
+    launch_dev_copy(c->y.p, (const char*)frames + ybytes * (size_t)last, ybytes, st);
+    launch_dev_copy(c->Bprior.p, (char*)c->Bseg.p + seg_bytes * (size_t)nref, seg_bytes, st);
     c->y_c32 = c->small_host->last_c32;
     c->y_c64 = c->small_host->last_c64;
     c->y_G = c->small_host->last_G;
@@ -1258,20 +1278,63 @@ pcv_status pcv_evaluate_host(pcv_ctx* c, int F, const void* frames, double* s, d
   }
   if (msd && (st = ensure(c, c->h_msd, sizeof(double) * (size_t)F * c->M)) != PCV_OK) return st;
   if (refreshed && (st = ensure(c, c->h_ref, F)) != PCV_OK) return st;
-  CUDA_TRY(c, cudaMemcpyAsync(c->h_frames.p, frames, fbytes, cudaMemcpyHostToDevice, c->stream));
-  st = pcv_evaluate(c, F, c->h_frames.p, (double*)c->h_s.p, (double*)c->h_z.p, dsdx ? c->h_gs.p : nullptr,
-                    dsdx ? c->h_gz.p : nullptr, msd ? (double*)c->h_msd.p : nullptr,
-                    refreshed ? (uint8_t*)c->h_ref.p : nullptr);
-  if (st != PCV_OK) return st;
-  CUDA_TRY(c, cudaMemcpyAsync(s, c->h_s.p, sizeof(double) * F, cudaMemcpyDeviceToHost, c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(z, c->h_z.p, sizeof(double) * F, cudaMemcpyDeviceToHost, c->stream));
-  if (dsdx) {
-    CUDA_TRY(c, cudaMemcpyAsync(dsdx, c->h_gs.p, fbytes, cudaMemcpyDeviceToHost, c->stream));
-    CUDA_TRY(c, cudaMemcpyAsync(dzdx, c->h_gz.p, fbytes, cudaMemcpyDeviceToHost, c->stream));
+  // The batch is evaluated in chunks of consecutive frames (the close-structure state and
+  // the neighbour list carry over between chunks exactly as between calls): the frames of
+  // later chunks are copied in on one copy stream, and the outputs of earlier chunks copied
+  // out on another, while a chunk is evaluated on the context's stream.
+  const int chunk = F <= 16384 ? F : std::max(8192, (F + 5) / 6);
+  const int nchunk = (F + chunk - 1) / chunk;
+  for (cudaStream_t* hs : {&c->h2d_stream, &c->d2h_stream})
+    if (!*hs) CUDA_TRY(c, cudaStreamCreateWithFlags(hs, cudaStreamNonBlocking));
+  while ((int)c->h_events.size() < 2 * nchunk + 1) {
+    cudaEvent_t e;
+    CUDA_TRY(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    c->h_events.push_back(e);
   }
-  if (msd)
-    CUDA_TRY(c, cudaMemcpyAsync(msd, c->h_msd.p, sizeof(double) * (size_t)F * c->M, cudaMemcpyDeviceToHost, c->stream));
-  if (refreshed) CUDA_TRY(c, cudaMemcpyAsync(refreshed, c->h_ref.p, F, cudaMemcpyDeviceToHost, c->stream));
+  cudaEvent_t* ev_in = c->h_events.data();            // frames of chunk k are on the device
+  cudaEvent_t* ev_done = c->h_events.data() + nchunk;  // chunk k is evaluated
+  cudaEvent_t ev_start = c->h_events[2 * nchunk];
+  const size_t fstride = frame_elem(c->prec) * 3 * (size_t)c->N;  // bytes per frame
+  // the copies start after the context's earlier work (the staging buffers may be in use)
+  CUDA_TRY(c, cudaEventRecord(ev_start, c->stream));
+  CUDA_TRY(c, cudaStreamWaitEvent(c->h2d_stream, ev_start, 0));
+  CUDA_TRY(c, cudaStreamWaitEvent(c->d2h_stream, ev_start, 0));
+  for (int k = 0; k < nchunk; ++k) {
+    const size_t f0 = (size_t)k * chunk, nf = std::min<size_t>(chunk, F - f0);
+    CUDA_TRY(c, cudaMemcpyAsync((char*)c->h_frames.p + fstride * f0, (const char*)frames + fstride * f0, fstride * nf,
+                                cudaMemcpyHostToDevice, c->h2d_stream));
+    CUDA_TRY(c, cudaEventRecord(ev_in[k], c->h2d_stream));
+  }
+  for (int k = 0; k < nchunk; ++k) {
+    const size_t f0 = (size_t)k * chunk, nf = std::min<size_t>(chunk, F - f0);
+    CUDA_TRY(c, cudaStreamWaitEvent(c->stream, ev_in[k], 0));
+    st = pcv_evaluate(c, (int)nf, (char*)c->h_frames.p + fstride * f0, (double*)c->h_s.p + f0,
+                      (double*)c->h_z.p + f0, dsdx ? (char*)c->h_gs.p + fstride * f0 : nullptr,
+                      dsdx ? (char*)c->h_gz.p + fstride * f0 : nullptr,
+                      msd ? (double*)c->h_msd.p + f0 * c->M : nullptr, refreshed ? (uint8_t*)c->h_ref.p + f0 : nullptr);
+    if (st != PCV_OK) {
+      cudaStreamSynchronize(c->h2d_stream);
+      cudaStreamSynchronize(c->d2h_stream);
+      return st;
+    }
+    CUDA_TRY(c, cudaEventRecord(ev_done[k], c->stream));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->d2h_stream, ev_done[k], 0));
+    const cudaStream_t o = c->d2h_stream;
+    CUDA_TRY(c, cudaMemcpyAsync(s + f0, (double*)c->h_s.p + f0, sizeof(double) * nf, cudaMemcpyDeviceToHost, o));
+    CUDA_TRY(c, cudaMemcpyAsync(z + f0, (double*)c->h_z.p + f0, sizeof(double) * nf, cudaMemcpyDeviceToHost, o));
+    if (dsdx) {
+      CUDA_TRY(c, cudaMemcpyAsync((char*)dsdx + fstride * f0, (char*)c->h_gs.p + fstride * f0, fstride * nf,
+                                  cudaMemcpyDeviceToHost, o));
+      CUDA_TRY(c, cudaMemcpyAsync((char*)dzdx + fstride * f0, (char*)c->h_gz.p + fstride * f0, fstride * nf,
+                                  cudaMemcpyDeviceToHost, o));
+    }
+    if (msd)
+      CUDA_TRY(c, cudaMemcpyAsync(msd + f0 * c->M, (double*)c->h_msd.p + f0 * c->M, sizeof(double) * nf * c->M,
+                                  cudaMemcpyDeviceToHost, o));
+    if (refreshed)
+      CUDA_TRY(c, cudaMemcpyAsync(refreshed + f0, (uint8_t*)c->h_ref.p + f0, nf, cudaMemcpyDeviceToHost, o));
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->d2h_stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return PCV_OK;
 }

@@ -139,6 +139,8 @@ void launch_seg_moments(int seg_base, int nseg, const LandmarkDev& L, const floa
 void launch_combine_grad(Prec p, int F, int N3, const double* g_s, const double* g_z,
                          const void* gs, const void* gz, void* out, cudaStream_t st);
 void launch_fill_u8(uint8_t* p, uint8_t v, size_t n, cudaStream_t st);
+// device-to-device copy by a kernel (not a copy engine)
+void launch_dev_copy(void* dst, const void* src, size_t bytes, cudaStream_t st);
 void launch_set_int(int* p, int v, cudaStream_t st);
 
 // ---- k_pair.cu ----

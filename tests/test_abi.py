@@ -55,3 +55,13 @@ def test_create_reports_bad_precision(lib):
     h = ctypes.c_void_p()
     assert lib.pcv_create(ctypes.byref(h), 0, None, 7) == pcv.PCV_EINVAL
     assert h.value is None
+
+
+def test_new_entry_points_reject_null_without_gpu(lib):
+    assert lib.pcv_set_neighbor_list(None, 5, 5) == pcv.PCV_EINVAL
+    assert lib.pcv_metad_apply(None, 1, 1, 1, None, None, None, None, None, None) == pcv.PCV_EINVAL
+    assert lib.pcv_metad_destroy(None) == pcv.PCV_OK
+    assert isinstance(lib.pcv_metad_last_error(None), bytes)
+    h = ctypes.c_void_p()
+    assert lib.pcv_metad_create(ctypes.byref(h), 0, None, 1.0, 0.0, 1.0, 1, 10) == pcv.PCV_EINVAL
+    assert h.value is None

@@ -147,3 +147,33 @@ def test_c5_full_size_close_batched_sampled(pcv, precision):
         assert d_err(res["msd"][sl], r["D"][row:row + 1], fr[sl], lm) < TOL[precision]
         assert s_err(res["s"][sl], r["s"][row:row + 1], lm.shape[0]) < TOL[precision]
         assert z_err(res["z"][sl], r["z"][row:row + 1], lam) < TOL[precision]
+
+
+def test_c2_full_size_host_entry_point(pcv):
+    """The benchmark's end-to-end call: pcv_evaluate_host on the 100k frames from pinned host
+    memory (evaluated in chunks while the next frames are copied in and the previous
+    outputs copied out).  Every refresh decision and 8 frames in full against the oracle."""
+    from paper_1801_02362_gb300 import synth
+
+    lm, fr = synth.make_problem(1, n_atoms=300, n_landmarks=200, n_frames=100_000, frame_noise=0.05)
+    fr = np.ascontiguousarray(fr, dtype=np.float32)
+    lam = 2.3 / oracle.mean_adjacent_msd(lm)
+    eps = 0.05
+    ctx = pcv.PathCV(lm, lam, eps=eps, precision="fp32")
+    F = fr.shape[0]
+    host = {"frames": torch.from_numpy(fr).pin_memory(),
+            "s": torch.empty(F, dtype=torch.float64).pin_memory(), "z": torch.empty(F, dtype=torch.float64).pin_memory(),
+            "dsdx": torch.empty(fr.shape, dtype=torch.float32).pin_memory(),
+            "dzdx": torch.empty(fr.shape, dtype=torch.float32).pin_memory(),
+            "msd": torch.empty((F, 200), dtype=torch.float64).pin_memory(),
+            "refreshed": torch.empty(F, dtype=torch.uint8).pin_memory()}
+    P = lambda k: host[k].data_ptr()
+    pcv.pcv_evaluate_host(ctx.ctx, F, P("frames"), P("s"), P("z"), P("dsdx"), P("dzdx"), P("msd"), P("refreshed"))
+    ctx.close()
+    res = {k: v.numpy() for k, v in host.items() if k != "frames"}
+    flags = res["refreshed"]
+    _check_refresh_sequence(flags, fr.astype(np.float64), eps)
+    rng = np.random.default_rng(9)
+    # frames at and next to chunk boundaries of the pipelined call (chunks of 16667 frames)
+    ts = sorted({16666, 16667, 16668, 50001, 83334} | set(rng.integers(1, F, 3).tolist()))
+    _check_frame_samples(res, fr, lm, lam, eps, ts)
