@@ -51,17 +51,17 @@ def lib():
         L.orc_quat_matrix.argtypes = [dp, dp]
         L.orc_quat_to_rot.argtypes = [dp, dp]
         L.orc_path_cv.argtypes = [c_int, dp, dp, c_double, dp, dp, dp]
-        L.orc_exact.argtypes = [c_int, c_int, c_int, dp, dp, dp, dp, c_double, dp, dp, dp, dp, dp]
+        L.orc_exact.argtypes = [c_int, c_int, c_int, dp, dp, dp, dp, dp, c_double, dp, dp, dp, dp, dp]
         i32p = ctypes.POINTER(ctypes.c_int32)
-        L.orc_close.argtypes = [c_int, c_int, c_int, dp, dp, dp, dp, c_double, c_double, dp, dp,
+        L.orc_close.argtypes = [c_int, c_int, c_int, dp, dp, dp, dp, dp, c_double, c_double, dp, dp,
                                 c_int, c_int, i32p, i64p, dp, dp, dp, u8p, dp, dp, dp]
-        L.orc_exact_nl.argtypes = [c_int, c_int, c_int, dp, dp, dp, dp, c_double, c_int, c_int, i32p, i64p,
+        L.orc_exact_nl.argtypes = [c_int, c_int, c_int, dp, dp, dp, dp, dp, c_double, c_int, c_int, i32p, i64p,
                                    dp, dp, dp, dp, dp]
         L.orc_nl_select.argtypes = [c_int, dp, c_int, i32p]
         L.orc_hills_value.argtypes = [c_int, dp, c_double, c_double, c_double, c_double, c_double, dp, dp, dp]
         L.orc_metad.argtypes = [c_int, c_int, dp, dp, dp, dp, c_double, c_double, c_double, c_int, c_int, dp, i64p,
                                 dp, dp]
-        L.orc_close_distance.argtypes = [c_int, dp, dp, dp, dp, dp]
+        L.orc_close_distance.argtypes = [c_int, dp, dp, dp, dp, dp, dp]
         L.orc_close_distance.restype = c_double
         for name in ("orc_cost_original", "orc_cost_close", "orc_amdahl"):
             getattr(L, name).argtypes = [c_double] * (3 if name == "orc_cost_original" else 2)
@@ -127,8 +127,10 @@ def path_cv(D, lam, q=None):
     return s[0], z[0], p
 
 
-def exact(frames, landmarks, lam, w=None, q=None, want_D=True, want_grad=False, nl=None, state=None):
+def exact(frames, landmarks, lam, w=None, q=None, want_D=True, want_grad=False, nl=None, state=None, wa=None):
     """Exact path CVs (Algorithm 1) for F frames.
+
+    w: displacement weights, wa: alignment weights (centres; default w), Section 3.1.
 
     nl = (M_nl, L): neighbour list of the original method (distances to all landmarks
     every L steps, to the M_nl closest of the last such step otherwise; frames in time
@@ -142,12 +144,13 @@ def exact(frames, landmarks, lam, w=None, q=None, want_D=True, want_grad=False, 
     gs = np.zeros((f, n, 3)) if want_grad else None
     gz = np.zeros((f, n, 3)) if want_grad else None
     if nl is None:
-        st = lib().orc_exact(f, m, n, _p(_f64(w)), _p(fr), _p(lm), _p(_f64(q)), float(lam), _p(s), _p(z),
-                             _p(D), _p(gs), _p(gz))
+        st = lib().orc_exact(f, m, n, _p(_f64(w)), _p(_f64(wa)), _p(fr), _p(lm), _p(_f64(q)), float(lam), _p(s),
+                             _p(z), _p(D), _p(gs), _p(gz))
     else:
         if state is None:
             state = CloseState(n, m)
-        st = lib().orc_exact_nl(f, m, n, _p(_f64(w)), _p(fr), _p(lm), _p(_f64(q)), float(lam), int(nl[0]),
+        st = lib().orc_exact_nl(f, m, n, _p(_f64(w)), _p(_f64(wa)), _p(fr), _p(lm), _p(_f64(q)), float(lam),
+                                int(nl[0]),
                                 int(nl[1]), _p(state.nl, ctypes.c_int32), _p(state.ctr, ctypes.c_int64), _p(s),
                                 _p(z), _p(D), _p(gs), _p(gz))
     if st != 0:
@@ -189,7 +192,7 @@ class CloseState:
 
 
 def close(frames, landmarks, lam, eps, state: CloseState | None = None, w=None, q=None,
-          want_D=True, want_grad=False, nl=None):
+          want_D=True, want_grad=False, nl=None, wa=None):
     """Floating close structure (Algorithm 2) over F time-ordered frames.
 
     nl = (M_nl, L): neighbour list chosen at reassignments (exact distances) and every L
@@ -207,7 +210,7 @@ def close(frames, landmarks, lam, eps, state: CloseState | None = None, w=None, 
     dxy = np.zeros(f)
     gs = np.zeros((f, n, 3)) if want_grad else None
     gz = np.zeros((f, n, 3)) if want_grad else None
-    st = lib().orc_close(f, m, n, _p(_f64(w)), _p(fr), _p(lm), _p(_f64(q)), float(lam), float(eps),
+    st = lib().orc_close(f, m, n, _p(_f64(w)), _p(_f64(wa)), _p(fr), _p(lm), _p(_f64(q)), float(lam), float(eps),
                          _p(state.y), _p(state.B), m_nl, stride, _p(state.nl, ctypes.c_int32),
                          _p(state.ctr, ctypes.c_int64), _p(s), _p(z), _p(D), _p(ref, ctypes.c_uint8), _p(dxy),
                          _p(gs), _p(gz))
@@ -255,11 +258,11 @@ def metad(s, z, w, sigma_s, sigma_z, stride, state: MetadState | None = None, ds
     return dict(V=V, force=force, state=state)
 
 
-def close_distance(x, y, B, a, w=None):
+def close_distance(x, y, B, a, w=None, wa=None):
     x, y, a = _f64(x), _f64(y), _f64(a)
     B = _f64(B).reshape(9)
     n = x.shape[0]
-    return lib().orc_close_distance(n, _p(_f64(w)), _p(x), _p(y), _p(B), _p(a))
+    return lib().orc_close_distance(n, _p(_f64(w)), _p(_f64(wa)), _p(x), _p(y), _p(B), _p(a))
 
 
 def cost_original(m_nl, n_ref, l_stride):

@@ -28,9 +28,12 @@
  *
  * Everything is double precision, plain loops, one frame / one landmark at a time.
  * Conventions: coordinates are row-major (structure, atom, xyz).  R is row-major 3x3.
- * R_{a x} maps the centred landmark a onto the centred frame x: it minimises
- * sum_j w_j |x_j - R a_j|^2.  Weights are normalised to sum 1; one weight set serves
- * as both displacement weights w and alignment weights w' (w = w').
+ * Two weight sets (Section 3.1, after Eq. der_dist): displacement weights w, the
+ * contribution of each atom's displacement to the distance, and alignment weights w', the
+ * contribution to the centre of mass that sets the translation.  Structures are centred by
+ * their w'-weighted centres; R_{a x} maps the centred landmark a onto the centred frame x
+ * minimising the distance itself, sum_j w_j |x_j - R a_j|^2 (the fit minimises the
+ * distance, Section 3).  Both sets are normalised to sum 1; w' defaults to w.
  */
 #include <math.h>
 #include <stdint.h>
@@ -298,13 +301,14 @@ static void rot_differential(const double* q, const double* dq, double* dR) {
 
 /* dR_{y x}/dx_{kc} for the rotation R fitting the centred y onto the centred x, from
  * first-order eigenvector perturbation of K: dq0 = sum_{l=1..3} v_l (v_l^T dK q0)/(l0 - l_l),
- * with dK = K(dH) and dH = d/dx_{kc} sum_j w_j y_j (x_j - centre(x))^T. */
-static void rot_derivative_wrt_x(int n, const double* w, const double* yc, const orc_align_t* al,
+ * with dK = K(dH) and dH = d/dx_{kc} sum_j w_j y_j (x_j - centre(x))^T, the centre being
+ * the w'-weighted one: dH = (w_k y_k - w'_k sum_j w_j y_j) e_c^T. */
+static void rot_derivative_wrt_x(int n, const double* w, const double* wa, const double* yc, const orc_align_t* al,
                                  int k, int c, double* dR) {
   double ybar[3];
-  orc_centroid(n, w, yc, ybar);
+  orc_centroid(n, w, yc, ybar); /* sum_j w_j y_j */
   double dH[9] = {0};
-  for (int b = 0; b < 3; ++b) dH[3 * b + c] = w[k] * (yc[3 * k + b] - ybar[b]);
+  for (int b = 0; b < 3; ++b) dH[3 * b + c] = w[k] * yc[3 * k + b] - wa[k] * ybar[b];
   double dK[16];
   orc_quat_matrix(dH, dK);
   double q0[4];
@@ -345,7 +349,7 @@ static void members_cv(int msel, const int* sel, const double* D, const double* 
 /* Exact evaluation of one frame (Algorithm 1 over the landmarks of sel, or all).
  * xc: centred frame; lmc: centred landmarks (M x N x 3).  Outputs D (M), R (M x 9,
  * optional), s, z, and gradients ds/dx, dz/dx (N x 3, optional), Eq. (der_dist). */
-int orc_frame_exact(int m, int n, const double* w, const double* xc, const double* lmc,
+int orc_frame_exact(int m, int n, const double* w, const double* wa, const double* xc, const double* lmc,
                     const double* qprop, double lambda, const int* sel, int msel, double* s, double* z,
                     double* D, double* Rout, double* dsdx, double* dzdx) {
   int st = ORC_OK;
@@ -363,7 +367,8 @@ int orc_frame_exact(int m, int n, const double* w, const double* xc, const doubl
   members_cv(msel, sel, D, qprop, lambda, s, z, p);
   if (dsdx || dzdx) {
     /* Eq. (der_dist): dD_i/dx_k = 2 w_k d_k + w'_k sum_j (-2 w_j d_j) + (rotation term).
-     * With R optimal the rotation term vanishes (stationarity of D in R). */
+     * With R optimal for D the rotation term vanishes (stationarity of D in R); the centre
+     * term vanishes only when w' = w. */
     if (dsdx) memset(dsdx, 0, sizeof(double) * 3 * n);
     if (dzdx) memset(dzdx, 0, sizeof(double) * 3 * n);
     double* d = (double*)malloc(sizeof(double) * 3 * n);
@@ -381,7 +386,7 @@ int orc_frame_exact(int m, int n, const double* w, const double* xc, const doubl
       const double gz = p[k0];                           /* dz/dD_i */
       for (int k = 0; k < n; ++k)
         for (int b = 0; b < 3; ++b) {
-          const double dDi = 2.0 * w[k] * d[3 * k + b] + w[k] * dsum[b];
+          const double dDi = 2.0 * w[k] * d[3 * k + b] + wa[k] * dsum[b];
           if (dsdx) dsdx[3 * k + b] += gs * dDi;
           if (dzdx) dzdx[3 * k + b] += gz * dDi;
         }
@@ -397,7 +402,7 @@ int orc_frame_exact(int m, int n, const double* w, const double* xc, const doubl
 /* Approximate evaluation of one frame against close structure yc with stored rotations
  * B_i = R_{a_i y} (Algorithm 2, "else" branch): D~_i, Eq. (close_dist), and its
  * derivative, Eq. (close_der_dist).  al: the alignment of yc onto xc (R_{x y}). */
-int orc_frame_approx(int m, int n, const double* w, const double* xc, const double* yc,
+int orc_frame_approx(int m, int n, const double* w, const double* wa, const double* xc, const double* yc,
                      const double* B, const double* lmc, const double* qprop, double lambda,
                      const orc_align_t* al, const int* sel, int msel, double* s, double* z, double* D,
                      double* dsdx, double* dzdx) {
@@ -449,7 +454,7 @@ int orc_frame_approx(int m, int n, const double* w, const double* xc, const doub
       const double gz = p[k0];
       for (int k = 0; k < n; ++k)
         for (int b = 0; b < 3; ++b) {
-          const double dDi = 2.0 * w[k] * dt[3 * k + b] + w[k] * dsum[b];
+          const double dDi = 2.0 * w[k] * dt[3 * k + b] + wa[k] * dsum[b];
           if (dsdx) dsdx[3 * k + b] += gs * dDi;
           if (dzdx) dzdx[3 * k + b] += gz * dDi;
         }
@@ -462,7 +467,7 @@ int orc_frame_approx(int m, int n, const double* w, const double* xc, const doub
     for (int k = 0; k < n; ++k)
       for (int c = 0; c < 3; ++c) {
         double dR[9];
-        rot_derivative_wrt_x(n, w, yc, al, k, c, dR);
+        rot_derivative_wrt_x(n, w, wa, yc, al, k, c, dR);
         double ts = 0.0, tz = 0.0;
         for (int e = 0; e < 9; ++e) {
           ts += Gs[e] * dR[e];
@@ -494,22 +499,24 @@ static void default_props(int m, const double* q_in, double* q) {
 /* Exact path CVs for F frames (Algorithm 1, all landmarks, no neighbour list).
  * frames F x N x 3, landmarks M x N x 3 (uncentred), w (N) or NULL for uniform, q (M)
  * or NULL for q_i = i.  D (F x M), dsdx, dzdx (F x N x 3) optional. */
-int orc_exact(int f, int m, int n, const double* w_in, const double* frames, const double* lm,
+int orc_exact(int f, int m, int n, const double* w_in, const double* wa_in, const double* frames, const double* lm,
               const double* q_in, double lambda, double* s, double* z, double* D, double* dsdx,
               double* dzdx) {
   if (f < 0 || m < 1 || n < 1 || !(lambda > 0.0)) return ORC_EINVAL;
   double* w = (double*)malloc(sizeof(double) * n);
+  double* wa = (double*)malloc(sizeof(double) * n);
   double* q = (double*)malloc(sizeof(double) * m);
   normalise_weights(n, w_in, w);
+  normalise_weights(n, wa_in ? wa_in : w_in, wa);
   default_props(m, q_in, q);
-  double* lmc = centred_copy(m, n, w, lm);
+  double* lmc = centred_copy(m, n, wa, lm);
   int st = ORC_OK;
 #pragma omp parallel for schedule(dynamic, 1)
   for (int t = 0; t < f; ++t) {
     double* xc = (double*)malloc(sizeof(double) * 3 * n);
     double* Dt = (double*)malloc(sizeof(double) * m);
-    orc_center(n, w, frames + (size_t)t * n * 3, xc);
-    int st_t = orc_frame_exact(m, n, w, xc, lmc, q, lambda, NULL, 0, s + t, z + t, Dt, NULL,
+    orc_center(n, wa, frames + (size_t)t * n * 3, xc);
+    int st_t = orc_frame_exact(m, n, w, wa, xc, lmc, q, lambda, NULL, 0, s + t, z + t, Dt, NULL,
                                dsdx ? dsdx + (size_t)t * n * 3 : NULL, dzdx ? dzdx + (size_t)t * n * 3 : NULL);
     if (D) memcpy(D + (size_t)t * m, Dt, sizeof(double) * m);
     if (st_t != ORC_OK) {
@@ -521,6 +528,7 @@ int orc_exact(int f, int m, int n, const double* w_in, const double* frames, con
   }
   free(lmc);
   free(q);
+  free(wa);
   free(w);
   return st;
 }
@@ -556,25 +564,27 @@ static int nl_update_step(int64_t step, int l_stride, const int64_t* ctr) {
  * all M landmarks every L steps, to the M_nl listed ones otherwise), frames in time order.
  * nl_state: m_nl landmark indices carried between calls; ctr as for orc_close (frames,
  * landmark alignments, has-list).  m_nl <= 0 or >= M: no list. */
-int orc_exact_nl(int f, int m, int n, const double* w_in, const double* frames, const double* lm,
-                 const double* q_in, double lambda, int m_nl, int l_stride, int* nl_state, int64_t* ctr,
-                 double* s, double* z, double* D, double* dsdx, double* dzdx) {
+int orc_exact_nl(int f, int m, int n, const double* w_in, const double* wa_in, const double* frames,
+                 const double* lm, const double* q_in, double lambda, int m_nl, int l_stride, int* nl_state,
+                 int64_t* ctr, double* s, double* z, double* D, double* dsdx, double* dzdx) {
   if (f < 0 || m < 1 || n < 1 || !(lambda > 0.0) || l_stride < 1) return ORC_EINVAL;
   const int use_nl = m_nl > 0 && m_nl < m;
   double* w = (double*)malloc(sizeof(double) * n);
+  double* wa = (double*)malloc(sizeof(double) * n);
   double* q = (double*)malloc(sizeof(double) * m);
   normalise_weights(n, w_in, w);
+  normalise_weights(n, wa_in ? wa_in : w_in, wa);
   default_props(m, q_in, q);
-  double* lmc = centred_copy(m, n, w, lm);
+  double* lmc = centred_copy(m, n, wa, lm);
   double* xc = (double*)malloc(sizeof(double) * 3 * n);
   double* Dt = (double*)malloc(sizeof(double) * m);
   int st = ORC_OK;
   for (int t = 0; t < f; ++t) {
-    orc_center(n, w, frames + (size_t)t * n * 3, xc);
+    orc_center(n, wa, frames + (size_t)t * n * 3, xc);
     const int update = !use_nl || nl_update_step(ctr[C_FRAMES], l_stride, ctr);
     const int* sel = update ? NULL : nl_state;
     const int msel = update ? m : m_nl;
-    if (orc_frame_exact(m, n, w, xc, lmc, q, lambda, sel, msel, s + t, z + t, Dt, NULL,
+    if (orc_frame_exact(m, n, w, wa, xc, lmc, q, lambda, sel, msel, s + t, z + t, Dt, NULL,
                         dsdx ? dsdx + (size_t)t * n * 3 : NULL, dzdx ? dzdx + (size_t)t * n * 3 : NULL) != ORC_OK)
       st = ORC_ENOCONV;
     if (use_nl && update) {
@@ -589,6 +599,7 @@ int orc_exact_nl(int f, int m, int n, const double* w_in, const double* frames, 
   free(xc);
   free(lmc);
   free(q);
+  free(wa);
   free(w);
   return st;
 }
@@ -602,7 +613,7 @@ int orc_exact_nl(int f, int m, int n, const double* w_in, const double* frames, 
  * distances to all landmarks are the approximate ones of Eq. (close_dist) and the list is
  * chosen from those (end of Section 3.2); in between only the listed landmarks are
  * evaluated.  nl_state: m_nl indices carried between calls. */
-int orc_close(int f, int m, int n, const double* w_in, const double* frames, const double* lm,
+int orc_close(int f, int m, int n, const double* w_in, const double* wa_in, const double* frames, const double* lm,
               const double* q_in, double lambda, double eps, double* y_state, double* B_state,
               int m_nl, int l_stride, int* nl_state, int64_t* ctr, double* s, double* z, double* D,
               uint8_t* refreshed, double* dxy, double* dsdx, double* dzdx) {
@@ -610,15 +621,17 @@ int orc_close(int f, int m, int n, const double* w_in, const double* frames, con
   const int use_nl = m_nl > 0 && m_nl < m;
   double* w = (double*)malloc(sizeof(double) * n);
   double* q = (double*)malloc(sizeof(double) * m);
+  double* wa = (double*)malloc(sizeof(double) * n);
   normalise_weights(n, w_in, w);
+  normalise_weights(n, wa_in ? wa_in : w_in, wa);
   default_props(m, q_in, q);
-  double* lmc = centred_copy(m, n, w, lm);
+  double* lmc = centred_copy(m, n, wa, lm);
   double* xc = (double*)malloc(sizeof(double) * 3 * n);
   double* Dt = (double*)malloc(sizeof(double) * m);
   double* Rt = (double*)malloc(sizeof(double) * 9 * m);
   int st = ORC_OK;
   for (int t = 0; t < f; ++t) {
-    orc_center(n, w, frames + (size_t)t * n * 3, xc);
+    orc_center(n, wa, frames + (size_t)t * n * 3, xc);
     double* gs = dsdx ? dsdx + (size_t)t * n * 3 : NULL;
     double* gz = dzdx ? dzdx + (size_t)t * n * 3 : NULL;
     int refresh = 0;
@@ -636,7 +649,7 @@ int orc_close(int f, int m, int n, const double* w_in, const double* frames, con
     const int update = !use_nl || refresh || nl_update_step(ctr[C_FRAMES], l_stride, ctr);
     if (refresh) {
       /* reassign: exact distances to all landmarks, save R_{a_i x}, y <- x */
-      if (orc_frame_exact(m, n, w, xc, lmc, q, lambda, NULL, m, s + t, z + t, Dt, Rt, gs, gz) != ORC_OK)
+      if (orc_frame_exact(m, n, w, wa, xc, lmc, q, lambda, NULL, m, s + t, z + t, Dt, Rt, gs, gz) != ORC_OK)
         st = ORC_ENOCONV;
       memcpy(B_state, Rt, sizeof(double) * 9 * m);
       memcpy(y_state, xc, sizeof(double) * 3 * n);
@@ -646,7 +659,7 @@ int orc_close(int f, int m, int n, const double* w_in, const double* frames, con
     } else {
       const int* sel = update ? NULL : nl_state;
       const int msel = update ? m : m_nl;
-      orc_frame_approx(m, n, w, xc, y_state, B_state, lmc, q, lambda, &al, sel, msel, s + t, z + t, Dt, gs, gz);
+      orc_frame_approx(m, n, w, wa, xc, y_state, B_state, lmc, q, lambda, &al, sel, msel, s + t, z + t, Dt, gs, gz);
       ctr[C_APPROX] += msel;
     }
     if (use_nl && update) {
@@ -662,6 +675,7 @@ int orc_close(int f, int m, int n, const double* w_in, const double* frames, con
   free(xc);
   free(lmc);
   free(q);
+  free(wa);
   free(w);
   return st;
 }
@@ -669,16 +683,18 @@ int orc_close(int f, int m, int n, const double* w_in, const double* frames, con
 /* Approximate distance of one frame to one landmark through a close structure, for
  * finite-difference checks: D~ = sum_j w_j |x_j - R_{x y} B a_j|^2 with x, y, a
  * uncentred on input. */
-double orc_close_distance(int n, const double* w_in, const double* x, const double* y, const double* B,
-                          const double* a) {
+double orc_close_distance(int n, const double* w_in, const double* wa_in, const double* x, const double* y,
+                          const double* B, const double* a) {
   double* w = (double*)malloc(sizeof(double) * n);
+  double* wa = (double*)malloc(sizeof(double) * n);
   normalise_weights(n, w_in, w);
+  normalise_weights(n, wa_in ? wa_in : w_in, wa);
   double* xc = (double*)malloc(sizeof(double) * 3 * n);
   double* yc = (double*)malloc(sizeof(double) * 3 * n);
   double* ac = (double*)malloc(sizeof(double) * 3 * n);
-  orc_center(n, w, x, xc);
-  orc_center(n, w, y, yc);
-  orc_center(n, w, a, ac);
+  orc_center(n, wa, x, xc);
+  orc_center(n, wa, y, yc);
+  orc_center(n, wa, a, ac);
   orc_align_t al;
   orc_align_centered(n, w, xc, yc, &al);
   double Q[9];
@@ -693,6 +709,7 @@ double orc_close_distance(int n, const double* w_in, const double* x, const doub
   free(ac);
   free(yc);
   free(xc);
+  free(wa);
   free(w);
   return dd;
 }
