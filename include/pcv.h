@@ -104,13 +104,28 @@ PCV_API pcv_status pcv_set_stream(pcv_ctx* ctx, void* cuda_stream);
  *           storage type;
  *   w       host, N doubles > 0, or NULL for uniform weights; normalised to sum 1.  One
  *           weight set serves as displacement weights w and alignment weights w'
- *           (Eq. der_dist);
+ *           (Eq. der_dist; pcv_set_landmarks_weighted takes separate sets);
  *   q       host, M doubles, the property q_i of each landmark, or NULL for q_i = i
  *           (1-based index: the path CV s).
  * Resets the close-structure state.  Synchronous with respect to the host buffers.
  * Errors: PCV_EINVAL (M < 1, N < 3, NULL coords, non-finite values, w <= 0). */
 PCV_API pcv_status pcv_set_landmarks(pcv_ctx* ctx, int M, int N, const double* coords, const double* w,
                              const double* q);
+
+/* As pcv_set_landmarks, with separate alignment weights (Section 3.1 after Eq. der_dist):
+ *   w        displacement weights: each atom's contribution to the distance
+ *            D = sum_j w_j |x_j - R a_j|^2 (host, N doubles > 0, or NULL for uniform);
+ *   w_align  alignment weights: each atom's contribution to the centre of mass, which sets
+ *            the translation (host, N doubles > 0, or NULL for w_align = w).
+ * Frames, landmarks and close structures are centred by their w_align-weighted centres;
+ * the rotation minimises the w-weighted distance.  The derivatives of Eq. (der_dist) and
+ * Eq. (close_der_dist) then carry the centre term w'_k sum_j (-2 w_j d_j), and in close mode
+ * the rotation term's dependence of the fit on the centre of x.  With different sets the
+ * materialised-operand and tensor-core paths and the persistent group launch are not used
+ * (the kernels that rotate while staging are).  Both sets are normalised to sum 1.
+ * Errors: as pcv_set_landmarks, and PCV_EINVAL for w_align entries <= 0. */
+PCV_API pcv_status pcv_set_landmarks_weighted(pcv_ctx* ctx, int M, int N, const double* coords, const double* w,
+                                              const double* w_align, const double* q);
 
 /* Set lambda of Eq. (property_map_cv), in nm^-2.  Errors: PCV_EINVAL unless lambda > 0
  * and finite. */

@@ -409,10 +409,15 @@ __device__ __forceinline__ double wsum(double v) {
 
 // Per-frame finish, one warp per frame.  beta (in gs / gz) -> gradients; approximate
 // frames add w_k T^T y_k (see adjoint_rotation_term).
+// Alignment weights w' (wa / wa64, null when w' = w; Section 3.1): the centre of Eq.
+// (der_dist) adds -2 w'_k S with S = sum_i gamma_i sum_j w_j d_ij = Gamma X_w - (R) sum_j w_j
+// beta_j, X_w = sum_j w_j (x_j - c'), and the rotation term's dH/dx_k = (w_k y_k - w'_k Y_w) e_c^T
+// adds -w'_k T^T Y_w, Y_w = sum_j w_j (y_j - c'_y).
 template <typename ST, typename FT>
 __global__ void __launch_bounds__(128)
 adjoint_finish_warp(int F, int M, int N, const FT* __restrict__ frames, const float4* __restrict__ c32,
                     const double4* __restrict__ c64, const float* __restrict__ wts, const double* __restrict__ w64,
+                    const float* __restrict__ wa, const double* __restrict__ wa64,
                     const float* __restrict__ A32, const double* __restrict__ A64, const double* __restrict__ q,
                     const float* __restrict__ q32, double dscale, const ST* __restrict__ P,
                     const double* __restrict__ s, double lambda, const ST* __restrict__ Bseg,
@@ -438,6 +443,8 @@ adjoint_finish_warp(int F, int M, int N, const FT* __restrict__ frames, const fl
     if (f64) return w64 ? (ST)w64[j] : wuni;
     return wts ? (ST)wts[j] : wuni;
   };
+  const bool split = f64 ? wa64 != nullptr : wa != nullptr;
+  auto wat = [&](int j) -> ST { return f64 ? (ST)wa64[j] : (ST)wa[j]; };
   const bool approx = rec.flag && rec.flag[f] == 0;
   // Gamma = sum_i gamma_i from the same p the contraction used.  In exact arithmetic
   // Gamma^s = 0 and Gamma^z = 1, but the FP32 value of s and the p-weighted sum of q differ
@@ -455,13 +462,32 @@ adjoint_finish_warp(int F, int M, int N, const FT* __restrict__ frames, const fl
   Gs = wsum(Gs);
   Gz = wsum(Gz);
   if (!approx) {
+    ST Ss[3] = {0, 0, 0}, Sz[3] = {0, 0, 0};  // centre term (alignment weights)
+    if (split) {
+      ST xw[3] = {0, 0, 0}, bws[3] = {0, 0, 0}, bwz[3] = {0, 0, 0};
+      for (int j = lane; j < N; j += 32) {
+        const ST w = wt(j);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          xw[b] += w * ((ST)x[3 * j + b] - cx[b]);
+          bws[b] += w * bsp[3 * j + b];
+          bwz[b] += w * bzp[3 * j + b];
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        xw[b] = wsum(xw[b]);
+        Ss[b] = Gs * xw[b] - wsum(bws[b]);
+        Sz[b] = Gz * xw[b] - wsum(bwz[b]);
+      }
+    }
     for (int j = lane; j < N; j += 32) {
-      const ST w = wt(j);
+      const ST w = wt(j), w2 = split ? wat(j) : ST(0);
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
         const ST v = (ST)x[3 * j + b] - cx[b];
-        bsp[3 * j + b] = (ST)2 * w * (Gs * v - bsp[3 * j + b]);
-        bzp[3 * j + b] = (ST)2 * w * (Gz * v - bzp[3 * j + b]);
+        bsp[3 * j + b] = (ST)2 * w * (Gs * v - bsp[3 * j + b]) - (ST)2 * w2 * Ss[b];
+        bzp[3 * j + b] = (ST)2 * w * (Gz * v - bzp[3 * j + b]) - (ST)2 * w2 * Sz[b];
       }
     }
     return;
@@ -487,6 +513,7 @@ adjoint_finish_warp(int F, int M, int N, const FT* __restrict__ frames, const fl
   ST acc[27];
 #pragma unroll
   for (int e = 0; e < 27; ++e) acc[e] = 0;
+  ST xw[3] = {0, 0, 0}, yw[3] = {0, 0, 0}, bws[3] = {0, 0, 0}, bwz[3] = {0, 0, 0};  // alignment weights
   for (int j = lane; j < N; j += 32) {
     const ST w = wt(j);
     ST v[3], u[3];
@@ -494,6 +521,15 @@ adjoint_finish_warp(int F, int M, int N, const FT* __restrict__ frames, const fl
     for (int b = 0; b < 3; ++b) {
       v[b] = (ST)x[3 * j + b] - cx[b];
       u[b] = (ST)y[3 * j + b] - cy[b];
+    }
+    if (split) {
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        xw[b] += w * v[b];
+        yw[b] += w * u[b];
+        bws[b] += w * bsp[3 * j + b];
+        bwz[b] += w * bzp[3 * j + b];
+      }
     }
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
@@ -547,8 +583,26 @@ adjoint_finish_warp(int F, int M, int N, const FT* __restrict__ frames, const fl
     adjoint_rotation_term<ST>(acc + 18, R, acc, Ps, Ts);
     adjoint_rotation_term<ST>(acc + 18, R, acc + 9, Pz, Tz);
   }
+  // alignment weights: -w'_k (2 S + T^T Y_w), S = Gamma X_w - R sum_j w_j beta^y_j
+  ST Cs[3] = {0, 0, 0}, Cz[3] = {0, 0, 0};
+  if (split) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      xw[b] = wsum(xw[b]);
+      yw[b] = wsum(yw[b]);
+      bws[b] = wsum(bws[b]);
+      bwz[b] = wsum(bwz[b]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const ST Rbs = R[3 * c] * bws[0] + R[3 * c + 1] * bws[1] + R[3 * c + 2] * bws[2];
+      const ST Rbz = R[3 * c] * bwz[0] + R[3 * c + 1] * bwz[1] + R[3 * c + 2] * bwz[2];
+      Cs[c] = (ST)2 * (Gs * xw[c] - Rbs) + Ts[c] * yw[0] + Ts[3 + c] * yw[1] + Ts[6 + c] * yw[2];
+      Cz[c] = (ST)2 * (Gz * xw[c] - Rbz) + Tz[c] * yw[0] + Tz[3 + c] * yw[1] + Tz[6 + c] * yw[2];
+    }
+  }
   for (int j = lane; j < N; j += 32) {
-    const ST w = wt(j);
+    const ST w = wt(j), w2 = split ? wat(j) : ST(0);
     ST v[3], u[3], bsj[3], bzj[3];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
@@ -563,8 +617,8 @@ adjoint_finish_warp(int F, int M, int N, const FT* __restrict__ frames, const fl
       const ST Rbz = R[3 * c] * bzj[0] + R[3 * c + 1] * bzj[1] + R[3 * c + 2] * bzj[2];
       const ST ts = Ts[c] * u[0] + Ts[3 + c] * u[1] + Ts[6 + c] * u[2];
       const ST tz = Tz[c] * u[0] + Tz[3 + c] * u[1] + Tz[6 + c] * u[2];
-      bsp[3 * j + c] = (ST)2 * w * (Gs * v[c] - Rbs) + w * ts;
-      bzp[3 * j + c] = (ST)2 * w * (Gz * v[c] - Rbz) + w * tz;
+      bsp[3 * j + c] = (ST)2 * w * (Gs * v[c] - Rbs) + w * ts - w2 * Cs[c];
+      bzp[3 * j + c] = (ST)2 * w * (Gz * v[c] - Rbz) + w * tz - w2 * Cz[c];
     }
   }
 }
@@ -604,7 +658,8 @@ __global__ void seg_moments_kernel(int seg_base, int nseg, int M, const float* _
 template <bool ASYNC>
 __global__ void __launch_bounds__(128)
 adjoint_finish_staged(int F, int M, int N, const float* __restrict__ frames, const float4* __restrict__ c32,
-                      const float* __restrict__ wts, float wuni, const float* __restrict__ A32,
+                      const float* __restrict__ wts, const float* __restrict__ wa, float wuni,
+                      const float* __restrict__ A32,
                       const float* __restrict__ q32, const float* __restrict__ P, const double* __restrict__ s,
                       float lambda, const float* __restrict__ Gsum, const float* __restrict__ S6, int seg_base,
                       const float* __restrict__ Bseg, const int* __restrict__ seg_of_frame, FrameRec rec,
@@ -674,10 +729,30 @@ adjoint_finish_staged(int F, int M, int N, const float* __restrict__ frames, con
   }
   if (!approx) {
     __syncwarp();
+    float Ss[3] = {0.0f, 0.0f, 0.0f}, Sz[3] = {0.0f, 0.0f, 0.0f};  // centre term (alignment weights)
+    if (wa) {
+      float xw[3] = {0.0f, 0.0f, 0.0f}, bws[3] = {0.0f, 0.0f, 0.0f}, bwz[3] = {0.0f, 0.0f, 0.0f};
+      for (int j = lane; j < N; j += 32) {
+        const float wj = wts ? wts[j] : wuni;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          xw[b] = fmaf(wj, xv[3 * j + b], xw[b]);
+          bws[b] = fmaf(wj, bs[3 * j + b], bws[b]);
+          bwz[b] = fmaf(wj, bz[3 * j + b], bwz[b]);
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        xw[b] = wsum(xw[b]);
+        Ss[b] = Gs * xw[b] - wsum(bws[b]);
+        Sz[b] = Gz * xw[b] - wsum(bwz[b]);
+      }
+    }
     for (int e = lane; e < N3; e += 32) {
-      const float wj = wts ? wts[e / 3] : wuni;
-      gsp[e] = 2.0f * wj * (Gs * xv[e] - bs[e]);
-      gzp[e] = 2.0f * wj * (Gz * xv[e] - bz[e]);
+      const float wj = wts ? wts[e / 3] : wuni, w2 = wa ? wa[e / 3] : 0.0f;
+      const int b = e - 3 * (e / 3);
+      gsp[e] = 2.0f * wj * (Gs * xv[e] - bs[e]) - 2.0f * w2 * Ss[b];
+      gzp[e] = 2.0f * wj * (Gz * xv[e] - bz[e]) - 2.0f * w2 * Sz[b];
     }
     return;
   }
@@ -699,6 +774,8 @@ adjoint_finish_staged(int F, int M, int N, const float* __restrict__ frames, con
   float acc[27];
 #pragma unroll
   for (int e = 0; e < 27; ++e) acc[e] = 0.0f;
+  float xw[3] = {0.0f, 0.0f, 0.0f}, yw[3] = {0.0f, 0.0f, 0.0f}, bws[3] = {0.0f, 0.0f, 0.0f},
+        bwz[3] = {0.0f, 0.0f, 0.0f};  // alignment weights
   for (int j = lane; j < N; j += 32) {
     const float wj = wts ? wts[j] : wuni;
     float v[3], u[3];
@@ -706,6 +783,15 @@ adjoint_finish_staged(int F, int M, int N, const float* __restrict__ frames, con
     for (int b = 0; b < 3; ++b) {
       v[b] = xv[3 * j + b];
       u[b] = uv[3 * j + b];
+    }
+    if (wa) {
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        xw[b] = fmaf(wj, v[b], xw[b]);
+        yw[b] = fmaf(wj, u[b], yw[b]);
+        bws[b] = fmaf(wj, bs[3 * j + b], bws[b]);
+        bwz[b] = fmaf(wj, bz[3 * j + b], bwz[b]);
+      }
     }
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
@@ -763,8 +849,26 @@ adjoint_finish_staged(int F, int M, int N, const float* __restrict__ frames, con
     const float Pz[9] = {ph[6], ph[7], ph[8], ph[7], ph[9], ph[10], ph[8], ph[10], ph[11]};
     adjoint_rotation_terms2<float>(acc + 18, R, qxy, acc, acc + 9, Ps, Pz, Ts, Tz);
   }
+  // alignment weights: -w'_k (2 S + T^T Y_w), S = Gamma X_w - R sum_j w_j beta^y_j
+  float Cs[3] = {0.0f, 0.0f, 0.0f}, Cz[3] = {0.0f, 0.0f, 0.0f};
+  if (wa) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      xw[b] = wsum(xw[b]);
+      yw[b] = wsum(yw[b]);
+      bws[b] = wsum(bws[b]);
+      bwz[b] = wsum(bwz[b]);
+    }
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+      const float Rbs = R[3 * cc] * bws[0] + R[3 * cc + 1] * bws[1] + R[3 * cc + 2] * bws[2];
+      const float Rbz = R[3 * cc] * bwz[0] + R[3 * cc + 1] * bwz[1] + R[3 * cc + 2] * bwz[2];
+      Cs[cc] = 2.0f * (Gs * xw[cc] - Rbs) + Ts[cc] * yw[0] + Ts[3 + cc] * yw[1] + Ts[6 + cc] * yw[2];
+      Cz[cc] = 2.0f * (Gz * xw[cc] - Rbz) + Tz[cc] * yw[0] + Tz[3 + cc] * yw[1] + Tz[6 + cc] * yw[2];
+    }
+  }
   for (int j = lane; j < N; j += 32) {
-    const float wj = wts ? wts[j] : wuni;
+    const float wj = wts ? wts[j] : wuni, w2 = wa ? wa[j] : 0.0f;
     float v[3], u[3], bsj[3], bzj[3];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
@@ -779,8 +883,8 @@ adjoint_finish_staged(int F, int M, int N, const float* __restrict__ frames, con
       const float Rbz = R[3 * cc] * bzj[0] + R[3 * cc + 1] * bzj[1] + R[3 * cc + 2] * bzj[2];
       const float ts = Ts[cc] * u[0] + Ts[3 + cc] * u[1] + Ts[6 + cc] * u[2];
       const float tz = Tz[cc] * u[0] + Tz[3 + cc] * u[1] + Tz[6 + cc] * u[2];
-      gsp[3 * j + cc] = 2.0f * wj * (Gs * v[cc] - Rbs) + wj * ts;
-      gzp[3 * j + cc] = 2.0f * wj * (Gz * v[cc] - Rbz) + wj * tz;
+      gsp[3 * j + cc] = 2.0f * wj * (Gs * v[cc] - Rbs) + wj * ts - w2 * Cs[cc];
+      gzp[3 * j + cc] = 2.0f * wj * (Gz * v[cc] - Rbz) + wj * tz - w2 * Cz[cc];
     }
   }
 }
@@ -888,14 +992,14 @@ void launch_adjoint_finish(Prec p, int F, const void* frames, const LandmarkDev&
       if (smem > 48 * 1024)
         cudaFuncSetAttribute(adjoint_finish_staged<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       adjoint_finish_staged<true><<<blocks, 32 * wpb, smem, st>>>(
-          F, L.M, L.N, (const float*)frames, fi.c32, L.w, (float)L.dscale, L.A32, L.q32, (const float*)P, s,
+          F, L.M, L.N, (const float*)frames, fi.c32, L.w, L.wa, (float)L.dscale, L.A32, L.q32, (const float*)P, s,
           (float)lambda, Gsum, S6, seg_base, (const float*)Bseg, seg_of_frame, rec, (const float*)prior.coords,
           prior.c32, (float*)gs, (float*)gz);
     } else {
       if (smem > 48 * 1024)
         cudaFuncSetAttribute(adjoint_finish_staged<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       adjoint_finish_staged<false><<<blocks, 32 * wpb, smem, st>>>(
-          F, L.M, L.N, (const float*)frames, fi.c32, L.w, (float)L.dscale, L.A32, L.q32, (const float*)P, s,
+          F, L.M, L.N, (const float*)frames, fi.c32, L.w, L.wa, (float)L.dscale, L.A32, L.q32, (const float*)P, s,
           (float)lambda, Gsum, S6, seg_base, (const float*)Bseg, seg_of_frame, rec, (const float*)prior.coords,
           prior.c32, (float*)gs, (float*)gz);
     }
@@ -905,12 +1009,12 @@ void launch_adjoint_finish(Prec p, int F, const void* frames, const LandmarkDev&
   const unsigned blocks = (unsigned)((F + 3) / 4);
   if (p == P_F64)
     adjoint_finish_warp<double, double><<<blocks, 128, 0, st>>>(
-        F, L.M, L.N, (const double*)frames, fi.c32, fi.c64, L.w, L.w64, L.A32, L.A, L.q, L.q32, L.dscale,
+        F, L.M, L.N, (const double*)frames, fi.c32, fi.c64, L.w, L.w64, L.wa, L.wa64, L.A32, L.A, L.q, L.q32, L.dscale,
         (const double*)P, s, lambda, (const double*)Bseg, seg_of_frame, rec, (const double*)prior.coords, prior.c64,
         (double*)gs, (double*)gz);
   else
     adjoint_finish_warp<float, float><<<blocks, 128, 0, st>>>(
-        F, L.M, L.N, (const float*)frames, fi.c32, fi.c64, L.w, L.w64, L.A32, L.A, L.q, L.q32, L.dscale,
+        F, L.M, L.N, (const float*)frames, fi.c32, fi.c64, L.w, L.w64, L.wa, L.wa64, L.A32, L.A, L.q, L.q32, L.dscale,
         (const float*)P, s, lambda, (const float*)Bseg, seg_of_frame, rec, (const float*)prior.coords,
         make_double4(prior.c32.x, prior.c32.y, prior.c32.z, 0.0), (float*)gs, (float*)gz);
   note_launch();

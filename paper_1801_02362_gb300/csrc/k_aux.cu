@@ -25,20 +25,22 @@ __device__ __forceinline__ int warp_global() {
 //   FP32 frames: centre c = sum_j w_j x_j with compensated FP32 sums, c32 = fl(c);
 //   G = sum_j wk_j |fl(x_j - c32)|^2 over exactly the values the pair kernels stage
 //   (error-free squares, compensated sums).  FP64 frames: plain FP64.
-// centre and G of frame f, one warp
+// centre and G of frame f, one warp.  The centre is weighted by the alignment weights wc
+// when given (they set the translation, Section 3.1), else by wts; G by wts.
 __device__ __forceinline__ void frame_prep_warp_f32(int f, int N, const float* __restrict__ frames,
                                                     const float* __restrict__ wts, float4* __restrict__ c32,
-                                                    double* __restrict__ G) {
+                                                    double* __restrict__ G, const float* __restrict__ wc = nullptr) {
   const int lane = threadIdx.x & 31;
   const float* x = frames + (size_t)f * N * 3;
+  const float* cw = wc ? wc : wts;
   float hi[3] = {0, 0, 0}, lo[3] = {0, 0, 0};
   for (int j = lane; j < N; j += 32) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const float v = x[3 * j + c];
-      if (wts) {
-        const float p = wts[j] * v;
-        const float e = fmaf(wts[j], v, -p);
+      if (cw) {
+        const float p = cw[j] * v;
+        const float e = fmaf(cw[j], v, -p);
         two_sum_acc(hi[c], lo[c], p);
         lo[c] += e;
       } else {
@@ -53,7 +55,7 @@ __device__ __forceinline__ void frame_prep_warp_f32(int f, int N, const float* _
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     warp_sum_pair(hi[k], lo[k]);
-    cf[k] = wts ? hi[k] + lo[k] : (hi[k] + lo[k]) * invn;
+    cf[k] = cw ? hi[k] + lo[k] : (hi[k] + lo[k]) * invn;
   }
   float gh = 0.0f, gl = 0.0f;
   for (int j = lane; j < N; j += 32) {
@@ -75,10 +77,11 @@ __device__ __forceinline__ void frame_prep_warp_f32(int f, int N, const float* _
 }
 
 __global__ void frame_prep_f32(int F, int N, const float* __restrict__ frames, const float* __restrict__ wts,
-                               float4* __restrict__ c32, double4* __restrict__ c64, double* __restrict__ G) {
+                               float4* __restrict__ c32, double4* __restrict__ c64, double* __restrict__ G,
+                               const float* __restrict__ wc) {
   const int f = warp_global();
   if (f >= F) return;
-  frame_prep_warp_f32(f, N, frames, wts, c32, G);
+  frame_prep_warp_f32(f, N, frames, wts, c32, G, wc);
 }
 
 // The same per frame with one 256-thread block per frame, for a few large frames (the
@@ -98,10 +101,11 @@ __device__ __forceinline__ void block_sum_pair(float& hi, float& lo, float (*sh)
 }
 
 __global__ void frame_prep_f32_block(int F, int N, const float* __restrict__ frames, const float* __restrict__ wts,
-                                     float4* __restrict__ c32, double* __restrict__ G) {
+                                     float4* __restrict__ c32, double* __restrict__ G, const float* __restrict__ wc) {
   __shared__ float sh[32][2];
   const int f = blockIdx.x;
   const float* x = frames + (size_t)f * N * 3;
+  const float* cw = wc ? wc : wts;
   float cf[3];
   const float invn = 1.0f / (float)N;
 #pragma unroll
@@ -109,9 +113,9 @@ __global__ void frame_prep_f32_block(int F, int N, const float* __restrict__ fra
     float hi = 0.0f, lo = 0.0f;
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
       const float v = x[3 * j + k];
-      if (wts) {
-        const float p = wts[j] * v;
-        const float e = fmaf(wts[j], v, -p);
+      if (cw) {
+        const float p = cw[j] * v;
+        const float e = fmaf(cw[j], v, -p);
         two_sum_acc(hi, lo, p);
         lo += e;
       } else {
@@ -119,7 +123,7 @@ __global__ void frame_prep_f32_block(int F, int N, const float* __restrict__ fra
       }
     }
     block_sum_pair(hi, lo, sh);
-    cf[k] = wts ? hi + lo : (hi + lo) * invn;
+    cf[k] = cw ? hi + lo : (hi + lo) * invn;
   }
   float gh = 0.0f, gl = 0.0f;
   for (int j = threadIdx.x; j < N; j += blockDim.x) {
@@ -142,21 +146,22 @@ __global__ void frame_prep_f32_block(int F, int N, const float* __restrict__ fra
 
 __global__ void frame_prep_f64(int F, int N, const double* __restrict__ frames,
                                const double* __restrict__ w64, float4* __restrict__ c32,
-                               double4* __restrict__ c64, double* __restrict__ G) {
+                               double4* __restrict__ c64, double* __restrict__ G, const double* __restrict__ wc64) {
   const int f = warp_global();
   if (f >= F) return;
   const int lane = threadIdx.x & 31;
   const double* x = frames + (size_t)f * N * 3;
+  const double* cw = wc64 ? wc64 : w64;  // the centre: alignment weights when given
   double c[3] = {0, 0, 0};
   for (int j = lane; j < N; j += 32) {
-    const double wj = w64 ? w64[j] : 1.0;
+    const double wj = cw ? cw[j] : 1.0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) c[k] += wj * x[3 * j + k];
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     c[k] = warp_sum_double(c[k]);
-    if (!w64) c[k] /= (double)N;
+    if (!cw) c[k] /= (double)N;
   }
   double g = 0.0;
   for (int j = lane; j < N; j += 32) {
@@ -448,7 +453,7 @@ __global__ void recheck_kernel(const int* __restrict__ list, const int* __restri
                                int N, const float* __restrict__ frames, RefView prior, int chunk_ref,
                                const double* __restrict__ w64, double dscale, double eps,
                                double* bandD, uint8_t* bandFlag, double* chunkD, uint8_t* chunkFlag,
-                               unsigned long long* n_rechecks) {
+                               unsigned long long* n_rechecks, const double* __restrict__ wc64) {
   const int wid = warp_global();
   if (wid >= *count) return;
   const int lane = threadIdx.x & 31;
@@ -465,9 +470,10 @@ __global__ void recheck_kernel(const int* __restrict__ list, const int* __restri
   }
   const float* x = frames + (size_t)t * N * 3;
   const float* y = ref >= 0 ? frames + (size_t)ref * N * 3 : (const float*)prior.coords;
+  const double* cw = wc64 ? wc64 : w64;  // centres: alignment weights when given
   double cx[3] = {0, 0, 0}, cy[3] = {0, 0, 0};
   for (int j = lane; j < N; j += 32) {
-    const double wj = w64 ? w64[j] : 1.0;
+    const double wj = cw ? cw[j] : 1.0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       cx[c] += wj * (double)x[3 * j + c];
@@ -478,7 +484,7 @@ __global__ void recheck_kernel(const int* __restrict__ list, const int* __restri
   for (int c = 0; c < 3; ++c) {
     cx[c] = warp_sum_double(cx[c]);
     cy[c] = warp_sum_double(cy[c]);
-    if (!w64) {
+    if (!cw) {
       cx[c] /= (double)N;
       cy[c] /= (double)N;
     }
@@ -873,12 +879,12 @@ void launch_frame_prep(Prec p, int F, const void* frames, const LandmarkDev& L, 
   const unsigned blocks = blocks_for((size_t)F, WARPS_PER_BLOCK);
   if (p == P_F64)
     frame_prep_f64<<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(F, L.N, (const double*)frames, L.w64, fi.c32,
-                                                            fi.c64, fi.G);
+                                                            fi.c64, fi.G, L.wa64);
   else if (F <= 1216 && L.N >= 256)  // few large frames: one block per frame
-    frame_prep_f32_block<<<F, 256, 0, st>>>(F, L.N, (const float*)frames, L.w, fi.c32, fi.G);
+    frame_prep_f32_block<<<F, 256, 0, st>>>(F, L.N, (const float*)frames, L.w, fi.c32, fi.G, L.wa);
   else
     frame_prep_f32<<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(F, L.N, (const float*)frames, L.w, fi.c32, fi.c64,
-                                                            fi.G);
+                                                            fi.G, L.wa);
   note_launch();
 }
 
@@ -926,7 +932,8 @@ void launch_recheck(Prec p, int max_entries, const int* list, const int* count, 
   const unsigned blocks = blocks_for((size_t)max_entries, WARPS_PER_BLOCK);
   recheck_kernel<<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(list, count, W, L.N, (const float*)frames,
                                                           view_of(prior), chunk_ref, L.w64, L.dscale, eps, band.D,
-                                                          band.flag, chunk.D, chunk.flag, n_rechecks); note_launch();
+                                                          band.flag, chunk.D, chunk.flag, n_rechecks, L.wa64);
+  note_launch();
 }
 
 void launch_xy_refine(Prec p, int F, const void* frames, const LandmarkDev& L, FrameInfo fi, const RefDesc& prior,

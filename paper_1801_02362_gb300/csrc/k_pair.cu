@@ -90,7 +90,7 @@ constexpr int EX_TF = 16, EX_TM = 32, EX_THREADS = 128;
 template <typename FT, typename LT, typename ST, int TF, int TM, int KC, int PF, int PM>
 __device__ __forceinline__ void stage_exact(int j0, int N, int M, int i0, const FT* __restrict__ frames,
                                             const LT* __restrict__ lm, const float* __restrict__ lmoff,
-                                            const float* __restrict__ wts, int wmode, const int* s_frame,
+                                            const ST* __restrict__ wts, int wmode, const int* s_frame,
                                             const ST (*s_c)[3],
                                             ST (*Xs)[PF], ST (*As)[PM], const int* __restrict__ cols = nullptr,
                                             int ncol = 0) {
@@ -377,7 +377,7 @@ approx_rows_f32(const int* __restrict__ row_frame, const int* __restrict__ count
 __global__ void __launch_bounds__(EX_THREADS, 3)
 exact_pair_f64(int rows, const int* __restrict__ row_frame, const double* __restrict__ frames,
                const double4* __restrict__ c64, const double* __restrict__ fG, const double* __restrict__ lm,
-               const double* __restrict__ lG, const float* __restrict__ wts, int M, int N, double dscale,
+               const double* __restrict__ lG, const double* __restrict__ wts, int M, int N, double dscale,
                double* __restrict__ Dout, double* __restrict__ Rout, unsigned* __restrict__ status) {
   const float* lmoff = nullptr;  // FP64 storage has no block offsets
   constexpr int TF = EX_TF, TM = EX_TM, KC = 16;
@@ -464,7 +464,7 @@ approx_pair_kernel(const int* __restrict__ alist, const int* __restrict__ aseg,
                    const int* __restrict__ acount, const FT* __restrict__ frames,
                    const float4* __restrict__ c32, const double4* __restrict__ c64,
                    const double4* __restrict__ qxy, const LT* __restrict__ lm, const float* __restrict__ lmoff,
-                   const ST* __restrict__ Bseg, const float* __restrict__ wts, int M, int N,
+                   const ST* __restrict__ Bseg, const ST* __restrict__ wts, int M, int N,
                    double dscale, ST* __restrict__ Dout) {
   constexpr int TF = AP_TF, TM = 8 * RM, KC = sizeof(ST) == 8 ? AP_KC / 2 : AP_KC;
   constexpr int PF = TF + 4, PM = TM + 4;
@@ -852,7 +852,7 @@ void launch_exact_pairs(Prec p, int rows, const int* row_frame, const int* rows_
   switch (p) {
     case P_F64:
       exact_pair_f64<<<grid, EX_THREADS, 0, st>>>(rows, row_frame, (const double*)frames, fi.c64, fi.G,
-                                                  (const double*)L.coords, L.G, L.w, L.M, L.N, L.dscale,
+                                                  (const double*)L.coords, L.G, L.w64, L.M, L.N, L.dscale,
                                                   (double*)D, (double*)Rout, status); note_launch();
       break;
     case P_F32:
@@ -911,7 +911,7 @@ static void approx_launch(Prec p, int max_rows, const int* approx_list, const in
     case P_F64:
       approx_pair_kernel<double, double, double, RM><<<grid, AP_THREADS, 0, st>>>(
           approx_list, approx_seg, count, (const double*)frames, fi.c32, fi.c64, qxy, (const double*)L.coords,
-          nullptr, (const double*)Bseg, L.w, L.M, L.N, L.dscale, (double*)D);
+          nullptr, (const double*)Bseg, L.w64, L.M, L.N, L.dscale, (double*)D);
       break;
     case P_F32:
       approx_pair_kernel<float, float, float, RM><<<grid, AP_THREADS, 0, st>>>(

@@ -98,6 +98,8 @@ struct pcv_ctx {
   bool uniform = true;
   double dscale = 1.0;
   DevBuf lm, lmoff, lmG, lmA, lmA32, lmq, lmq32, w32, w64;
+  bool split_w = false;  // alignment weights w' differ from the displacement weights w
+  DevBuf wa32, wa64;
   double lambda = 0.0;
   bool have_lambda = false;
   double eps = -1.0;
@@ -244,6 +246,8 @@ LandmarkDev lm_view(const pcv_ctx* c) {
   L.w64 = c->uniform ? nullptr : (const double*)c->w64.p;
   L.dscale = c->dscale;
   L.off = c->prec == P_F16 ? (const float*)c->lmoff.p : nullptr;
+  L.wa = c->split_w ? (const float*)c->wa32.p : nullptr;
+  L.wa64 = c->split_w ? (const double*)c->wa64.p : nullptr;
   return L;
 }
 
@@ -307,7 +311,8 @@ pcv_status pcv_destroy(pcv_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
-  DevBuf* bufs[] = {&c->lm, &c->lmoff, &c->lmG, &c->lmA, &c->lmA32, &c->lmq, &c->lmq32, &c->w32, &c->w64, &c->y, &c->Bprior, &c->c32, &c->c64,
+  DevBuf* bufs[] = {&c->lm, &c->lmoff, &c->lmG, &c->lmA, &c->lmA32, &c->lmq, &c->lmq32, &c->w32, &c->w64, &c->wa32,
+                    &c->wa64, &c->y, &c->Bprior, &c->c32, &c->c64,
                     &c->fG, &c->bandD, &c->bandQ, &c->bandF, &c->chD, &c->chQ, &c->chF, &c->rlist, &c->rcount,
                     &c->recF, &c->recRef, &c->recD, &c->recQ, &c->reflist, &c->segof, &c->alist, &c->aseg,
                     &c->Dbuf, &c->Rpair, &c->Bseg, &c->Xr, &c->Bm, &c->GSb, &c->GZb, &c->Nx, &c->Nb, &c->Yc, &c->Gsum, &c->Amma, &c->Bmma, &c->S6, &c->mstat, &c->status, &c->nrecheck, &c->small, &c->h_frames,
@@ -416,6 +421,11 @@ pcv_status pcv_reset_close_state(pcv_ctx* c) {
 // Landmark preparation (row "a1"): FP64 centring by the weighted centre, rounding to the
 // storage type, then G_a, A_i = sum_j w_j a_j a_j^T from the stored (rounded) values.
 pcv_status pcv_set_landmarks(pcv_ctx* c, int M, int N, const double* coords, const double* w, const double* q) {
+  return pcv_set_landmarks_weighted(c, M, N, coords, w, nullptr, q);
+}
+
+pcv_status pcv_set_landmarks_weighted(pcv_ctx* c, int M, int N, const double* coords, const double* w,
+                                      const double* w_align, const double* q) {
   if (!c) return fail(nullptr, PCV_EINVAL, "NULL context");
   if (M < 1 || N < 3) return fail(c, PCV_EINVAL, "need M >= 1 and N >= 3 (got M=%d N=%d)", M, N);
   if (!coords) return fail(c, PCV_EINVAL, "coords is NULL");
@@ -431,6 +441,20 @@ pcv_status pcv_set_landmarks(pcv_ctx* c, int M, int N, const double* coords, con
     for (int j = 0; j < N; ++j) wn[j] = w[j] / sum;
     uniform = false;
   }
+  // alignment weights w' (Section 3.1): they set the centres; equal to w unless given and
+  // different
+  std::vector<double> wan(wn);
+  if (w_align) {
+    double sum = 0.0;
+    for (int j = 0; j < N; ++j) {
+      if (!(w_align[j] > 0.0) || !std::isfinite(w_align[j]))
+        return fail(c, PCV_EINVAL, "alignment weight %d not > 0", j);
+      sum += w_align[j];
+    }
+    for (int j = 0; j < N; ++j) wan[j] = w_align[j] / sum;
+  }
+  bool split = false;
+  for (int j = 0; j < N; ++j) split = split || wan[j] != wn[j];
   const size_t n3 = (size_t)N * 3;
   for (size_t k = 0; k < (size_t)M * n3; ++k)
     if (!std::isfinite(coords[k])) return fail(c, PCV_EINVAL, "non-finite landmark coordinate at %zu", k);
@@ -450,9 +474,9 @@ pcv_status pcv_set_landmarks(pcv_ctx* c, int M, int N, const double* coords, con
   for (int j = 0; j < N; ++j) w32[j] = (float)wn[j];
   for (int i = 0; i < M; ++i) {
     const double* a = coords + (size_t)i * n3;
-    double cen[3] = {0, 0, 0};
+    double cen[3] = {0, 0, 0};  // the alignment-weighted centre
     for (int j = 0; j < N; ++j)
-      for (int k = 0; k < 3; ++k) cen[k] += wn[j] * a[3 * j + k];
+      for (int k = 0; k < 3; ++k) cen[k] += wan[j] * a[3 * j + k];
     double g = 0.0, Ai[6] = {0, 0, 0, 0, 0, 0};
     if (p == P_F16) {
       for (int b = 0; b < NB; ++b) {
@@ -505,6 +529,8 @@ pcv_status pcv_set_landmarks(pcv_ctx* c, int M, int N, const double* coords, con
   if ((st = ensure(c, c->lmq32, sizeof(float) * M)) != PCV_OK) return st;
   if ((st = ensure(c, c->w32, sizeof(float) * N)) != PCV_OK) return st;
   if ((st = ensure(c, c->w64, sizeof(double) * N)) != PCV_OK) return st;
+  if (split && (st = ensure(c, c->wa32, sizeof(float) * N)) != PCV_OK) return st;
+  if (split && (st = ensure(c, c->wa64, sizeof(double) * N)) != PCV_OK) return st;
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   CUDA_TRY(c, cudaMemcpy(c->lm.p, store.data(), store.size(), cudaMemcpyHostToDevice));
   if (p == P_F16)
@@ -518,9 +544,15 @@ pcv_status pcv_set_landmarks(pcv_ctx* c, int M, int N, const double* coords, con
   CUDA_TRY(c, cudaMemcpy(c->lmq32.p, q32.data(), sizeof(float) * M, cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(c->w32.p, w32.data(), sizeof(float) * N, cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(c->w64.p, wn.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+  if (split) {
+    std::vector<float> wa32(wan.begin(), wan.end());
+    CUDA_TRY(c, cudaMemcpy(c->wa32.p, wa32.data(), sizeof(float) * N, cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(c->wa64.p, wan.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+  }
   c->M = M;
   c->N = N;
   c->uniform = uniform;
+  c->split_w = split;
   c->dscale = uniform ? 1.0 / N : 1.0;
   c->have_lm = true;
   return pcv_reset_close_state(c);
@@ -775,7 +807,7 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
   const int nseg = nref + 1 - seg_base;
   bool tiled = false, mma = false;
   const MmaShape msh = mma_shape(F, M, c->N);
-  if (c->prec != P_F64 && c->uniform && seg_form && nseg > 0) {
+  if (c->prec != P_F64 && c->uniform && !c->split_w && seg_form && nseg > 0) {
     const size_t xb = tile_bytes_frames(napp, c->N), bb = tile_bytes_landmarks(nseg, M, c->N);
     const size_t nb = sizeof(float) * ((size_t)napp + (size_t)nseg * M + (size_t)nseg * 3 * c->N + 2 * (size_t)F);
     const size_t gb = grads ? tile_bytes_gamma(F, M) : 0;  // per gamma kind
@@ -1116,7 +1148,8 @@ pcv_status pcv_evaluate_group(pcv_ctx* const* ctxs, int n, const pcv_batch_io* i
     if ((b.dsdx == nullptr) != (b.dzdx == nullptr)) return fail(lead, PCV_EINVAL, "entry %d: dsdx and dzdx", k);
     if ((size_t)b.F * c->M > ((size_t)1 << 40)) return fail(lead, PCV_EINVAL, "entry %d: F*M too large", k);
     // the persistent path covers exact mode without gradients in the FP32 modes, one storage type
-    if (c->eps >= 0.0 || b.dsdx || c->prec == P_F64 || c->prec != lead->prec || nl_active(c)) persistent = false;
+    if (c->eps >= 0.0 || b.dsdx || c->prec == P_F64 || c->prec != lead->prec || nl_active(c) || c->split_w)
+      persistent = false;
   }
   cudaSetDevice(lead->device);
   const cudaStream_t user = (cudaStream_t)stream;

@@ -27,6 +27,9 @@ struct LandmarkDev {
   const double* w64 = nullptr;   // N: the same weights in FP64, or nullptr when uniform
   double dscale = 1.0;           // kernel units -> true: 1/N for uniform weights, else 1
   const float* off = nullptr;    // FP16 storage: M*ceil(N/16)*3 block offsets (else nullptr)
+  // alignment weights w' (normalised; they set the centres), or nullptr when w' = w
+  const float* wa = nullptr;
+  const double* wa64 = nullptr;
 };
 // FP16 storage keeps, per landmark and block of 16 consecutive atoms, an FP32 offset (the
 // block's mean centred coordinate) and the FP16 residuals: coordinate = offset + residual

@@ -55,6 +55,7 @@ SIGNATURES = {
     "pcv_destroy": (_i, [_vp]),
     "pcv_set_stream": (_i, [_vp, _vp]),
     "pcv_set_landmarks": (_i, [_vp, _i, _i, _vp, _vp, _vp]),
+    "pcv_set_landmarks_weighted": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp]),
     "pcv_set_lambda": (_i, [_vp, _d]),
     "pcv_set_close_threshold": (_i, [_vp, _d]),
     "pcv_set_neighbor_list": (_i, [_vp, _i, _i]),
@@ -140,6 +141,16 @@ def pcv_set_landmarks(ctx, coords: np.ndarray, w: np.ndarray | None = None, q: n
     qp = None if q is None else np.ascontiguousarray(q, dtype=np.float64)
     st = load().pcv_set_landmarks(ctx, m, n, coords.ctypes.data, None if wp is None else wp.ctypes.data,
                                   None if qp is None else qp.ctypes.data)
+    _check(ctx, st)
+
+
+def pcv_set_landmarks_weighted(ctx, coords: np.ndarray, w: np.ndarray | None, w_align: np.ndarray | None,
+                               q: np.ndarray | None = None):
+    coords = np.ascontiguousarray(coords, dtype=np.float64)
+    m, n = coords.shape[0], coords.shape[1]
+    arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in (w, w_align, q)]
+    st = load().pcv_set_landmarks_weighted(ctx, m, n, coords.ctypes.data,
+                                           *[None if a is None else a.ctypes.data for a in arrs])
     _check(ctx, st)
 
 
@@ -341,7 +352,8 @@ class PathCV:
     def __init__(self, landmarks: np.ndarray, lam: float, eps: float = -1.0, precision: str = "fp32",
                  weights: np.ndarray | None = None, props: np.ndarray | None = None, device: int = 0,
                  band: int | None = None, min_chunk: int | None = None, materialize: int | None = None,
-                 tensor_cores: bool | None = None, neighbor_list: tuple[int, int] | None = None):
+                 tensor_cores: bool | None = None, neighbor_list: tuple[int, int] | None = None,
+                 align_weights: np.ndarray | None = None):
         import torch
 
         self.torch = torch
@@ -350,7 +362,10 @@ class PathCV:
         stream = torch.cuda.current_stream(self.device).cuda_stream
         self.ctx = pcv_create(device, stream, _PREC[precision])
         self.M, self.N = landmarks.shape[0], landmarks.shape[1]
-        pcv_set_landmarks(self.ctx, landmarks, weights, props)
+        if align_weights is None:
+            pcv_set_landmarks(self.ctx, landmarks, weights, props)
+        else:
+            pcv_set_landmarks_weighted(self.ctx, landmarks, weights, align_weights, props)
         pcv_set_lambda(self.ctx, lam)
         pcv_set_close_threshold(self.ctx, eps)
         if band is not None:
