@@ -256,7 +256,8 @@ PCV_API const char* pcv_profile_name(int id);
  * `stream` waits for it.
  *
  * When every context is in exact mode (threshold < 0) with FP32 or FP16 storage (all the
- * same), and no entry asks for gradients, the step runs as three launches over all
+ * same), without a neighbour list and with one weight set (w' = w), and no entry asks for
+ * gradients, the step runs as three launches over all
  * instances: frame preparation (one warp per frame), the exact pair tiles of every instance
  * in one persistent kernel, and the path CVs (one warp per frame).  The first call with a
  * given set of contexts, sizes and buffers times persistent grids of 1, 2, 3, 4 and 8 CTAs
