@@ -177,3 +177,79 @@ def test_c2_full_size_host_entry_point(pcv):
     # frames at and next to chunk boundaries of the pipelined call (chunks of 16667 frames)
     ts = sorted({16666, 16667, 16668, 50001, 83334} | set(rng.integers(1, F, 3).tolist()))
     _check_frame_samples(res, fr, lm, lam, eps, ts)
+
+
+def test_c3_full_size_group_sampled(pcv):
+    """256 independent instances (N ~ U[50, 2000], M ~ U[50, 1000], 512 frames each, FP32
+    exact mode) in one group call -- the persistent launch the benchmark times, after its
+    autotuner -- and 24 frames of 8 instances checked in full against the oracle."""
+    from paper_1801_02362_gb300 import synth
+
+    rng = np.random.default_rng(7)
+    insts = []
+    for k in range(256):
+        n = int(rng.integers(50, 2001))
+        m = int(rng.integers(50, 1001))
+        lm, fr = synth.make_problem(1000 + k, n_atoms=n, n_landmarks=m, n_frames=512, frame_noise=0.05)
+        insts.append((lm, np.ascontiguousarray(fr, dtype=np.float32)))
+    check = [0, 37, 99, 128, 170, 201, 233, 255]
+    lams = {k: 2.3 / oracle.mean_adjacent_msd(insts[k][0][:40]) for k in check}
+    ctxs, bufs = [], []
+    for k, (lm, fr) in enumerate(insts):
+        ctxs.append(pcv.PathCV(lm, lams.get(k, 500.0), eps=-1.0, precision="fp32"))
+        F, m = fr.shape[0], lm.shape[0]
+        bufs.append({"x": torch.from_numpy(fr).cuda(), "s": torch.zeros(F, dtype=torch.float64, device="cuda"),
+                     "z": torch.zeros(F, dtype=torch.float64, device="cuda"),
+                     "msd": torch.zeros((F, m), dtype=torch.float64, device="cuda")})
+    P = lambda t: t.data_ptr()
+    ios = [{"F": b["s"].shape[0], "frames": P(b["x"]), "s": P(b["s"]), "z": P(b["z"]), "msd": P(b["msd"])} for b in bufs]
+    handles = [c.ctx for c in ctxs]
+    pcv.pcv_evaluate_group(handles, ios)  # autotune and capture
+    pcv.pcv_evaluate_group(handles, ios)  # replay
+    torch.cuda.synchronize()
+    for c in ctxs:
+        c.sync()
+    for k in check:
+        lm, fr = insts[k]
+        ts = [0, 255, 511]
+        r = oracle.exact(fr[ts], lm, lams[k])
+        msd = bufs[k]["msd"].cpu().numpy()[ts]
+        assert d_err(msd, r["D"], fr[ts], lm) < TOL["fp32"], k
+        assert s_err(bufs[k]["s"].cpu().numpy()[ts], r["s"], lm.shape[0]) < TOL["fp32"], k
+        assert z_err(bufs[k]["z"].cpu().numpy()[ts], r["z"], lams[k]) < TOL["fp32"], k
+    for c in ctxs:
+        c.close()
+
+
+def test_nl_full_size_exact_sampled(pcv):
+    """The neighbour-list workload the benchmark times (304 atoms, 2120 landmarks, a list of
+    50 every 50 steps, 10k frames, FP32, gradients).  A frame t between updates depends only
+    on itself and its last update u, so the oracle evaluates [x_u, x_t] as a run whose first
+    step is an update: list membership, distances, s, z and gradients of both frames."""
+    from paper_1801_02362_gb300 import synth
+
+    lm, fr = synth.make_problem(8, n_atoms=304, n_landmarks=2120, n_frames=10_000, frame_noise=0.05)
+    fr = np.ascontiguousarray(fr, dtype=np.float32)
+    lam = 2.3 / oracle.mean_adjacent_msd(lm[:200])
+    ctx = pcv.PathCV(lm, lam, eps=-1.0, precision="fp32", neighbor_list=(50, 50))
+    out = ctx.evaluate(torch.from_numpy(fr).cuda(), grad=True, msd=True)
+    ctx.sync()
+    res = {k: v.double().cpu().numpy() for k, v in out.items()}
+    ctx.close()
+    for t in (1, 49, 2551, 5037, 9999):
+        u = t - t % 50
+        st = oracle.CloseState(304, 2120)
+        st.ctr[1] = u  # the run starts at step u (an update: u is a multiple of 50)
+        r = oracle.exact(fr[[u, t]], lm, lam, want_grad=True, nl=(50, 50), state=st)
+        d = np.sort(r["D"][0])
+        assert d[50] - d[49] > 2.5e-5 * max(d[49], 1e-3), "near-tie in the list at the update"  # precondition
+        for row, f in ((0, u), (1, t)):
+            fin = np.isfinite(r["D"][row])
+            np.testing.assert_array_equal(np.isfinite(res["msd"][f]), fin)
+            sl = slice(f, f + 1)
+            assert d_err(np.where(fin, res["msd"][sl], 1.0), np.where(fin, r["D"][row:row + 1], 1.0), fr[sl],
+                         lm) < TOL["fp32"]
+            assert s_err(res["s"][sl], r["s"][row:row + 1], 2120) < TOL["fp32"]
+            assert z_err(res["z"][sl], r["z"][row:row + 1], lam) < TOL["fp32"]
+            assert grad_err(res["dsdx"][sl], r["dsdx"][row:row + 1]) < GRAD_TOL["fp32"]
+            assert grad_err(res["dzdx"][sl], r["dzdx"][row:row + 1]) < GRAD_TOL["fp32"]
