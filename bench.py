@@ -74,6 +74,11 @@ DETAILS = {
     "c3_group": ("group", dict()),
     "c5_stream_fp32": ("stream", dict(precision="fp32")),
     "c5_stream_fp16": ("stream", dict(precision="fp16")),
+    # one frame per call at the size of the paper's first data set (24 atoms, 521 landmarks,
+    # no neighbour list, eps = 0.01 nm^2): the per-step latency of the call
+    "step_latency_n24_m521_fp64": ("stream", dict(precision="fp64", n=24, m=521, eps=0.01, seed=6)),
+    "step_latency_n24_m521_fp32": ("stream", dict(precision="fp32", n=24, m=521, eps=0.01, seed=6)),
+    "step_latency_n24_m521_fp32_grad": ("stream", dict(precision="fp32", n=24, m=521, eps=0.01, seed=6, grad=True)),
     "c5_batched_fp32": ("config", dict(label="close-structure path CV, N=5000, M=2000, F=10000, fp32 landmark storage",
                                        seed=5, n=5000, m=2000, f=10_000, eps=0.05, grad=False, precision="fp32",
                                        steps=1)),
@@ -309,24 +314,28 @@ def time_config(pcv, label: str, seed: int, n: int, m: int, f: int, eps: float, 
 
 
 def time_stream(pcv, precision: str, n: int = 5000, m: int = 2000, calls: int = 200, eps: float = 0.05,
-                seed: int = 5) -> dict:
+                seed: int = 5, grad: bool = False) -> dict:
     """Per-MD-step use: close-structure evaluation fed one frame per call (no gradients).
     Reports the time per call and, for the landmark-streaming kernels, bytes of landmarks
     read per launch / the kernel's average launch time against the measured HBM peak."""
     import torch
     from paper_1801_02362_gb300 import synth
 
-    ldt = np.float16 if precision == "fp16" else np.float32
+    ldt = np.float16 if precision == "fp16" else (np.float64 if precision == "fp64" else np.float32)
+    fdt = np.float64 if precision == "fp64" else np.float32
     lm, fr = synth.make_problem(seed, n_atoms=n, n_landmarks=m, n_frames=10_000, frame_noise=0.05,
-                                landmark_dtype=ldt)
-    fr = torch.tensor(np.ascontiguousarray(fr[:calls + 8]), dtype=torch.float32, device="cuda")
+                                landmark_dtype=ldt, frame_dtype=fdt)
+    fr = torch.tensor(np.ascontiguousarray(fr[:calls + 8]), dtype=torch.float64 if precision == "fp64" else torch.float32,
+                      device="cuda")
     lam = lambda_from_gpu(pcv, lm)
     ctx = pcv.PathCV(lm, lam, eps=eps, precision=precision)
     s = torch.empty(1, dtype=torch.float64, device="cuda")
     z = torch.empty_like(s)
-    P = lambda t: t.data_ptr()
+    gs = torch.empty_like(fr[0]) if grad else None
+    gz = torch.empty_like(fr[0]) if grad else None
+    P = lambda t: None if t is None else t.data_ptr()
     for t in range(8):  # warm-up calls
-        pcv.pcv_evaluate(ctx.ctx, 1, P(fr[t]), P(s), P(z), None, None, None, None)
+        pcv.pcv_evaluate(ctx.ctx, 1, P(fr[t]), P(s), P(z), P(gs), P(gz), None, None)
     torch.cuda.synchronize()
     ctx.set_profiling(True)
     ctx.profile()
@@ -336,14 +345,14 @@ def time_stream(pcv, precision: str, n: int = 5000, m: int = 2000, calls: int = 
     b = torch.cuda.Event(enable_timing=True)
     a.record(stream)
     for t in range(8, 8 + calls):
-        pcv.pcv_evaluate(ctx.ctx, 1, P(fr[t]), P(s), P(z), None, None, None, None)
+        pcv.pcv_evaluate(ctx.ctx, 1, P(fr[t]), P(s), P(z), P(gs), P(gz), None, None)
     b.record(stream)
     torch.cuda.synchronize()
     per_call_ms = a.elapsed_time(b) / calls
     pr = ctx.profile()
     st = ctx.stats()
     ctx.close()
-    elem = 2 if precision == "fp16" else 4
+    elem = {"fp16": 2, "fp32": 4, "fp64": 8}[precision]
     set_bytes = m * n * 3 * elem
     hbm = measured_peaks().get("hbm_gbs", 6793.8)
     # calls whose frame refreshed ran the exact kernel, the others the approximate one; each
@@ -358,7 +367,8 @@ def time_stream(pcv, precision: str, n: int = 5000, m: int = 2000, calls: int = 
             gbs = n_work * set_bytes / (ms / 1e3) / 1e9
             kern[name] = {"launches_with_work": n_work, "ms_per_launch": ms / n_work, "landmark_GB_per_s": gbs,
                           "frac_of_hbm_peak": gbs / hbm}
-    return {"workload": f"close-structure path CV one frame per call, N={n}, M={m}, {precision} landmark storage",
+    return {"workload": f"close-structure path CV one frame per call, N={n}, M={m}, eps={eps}, {precision} landmark "
+                        "storage",
             "landmark_set_MB": set_bytes / 1e6, "l2_resident": set_bytes < 126e6, "calls": calls,
             "ms_per_call": per_call_ms, "frames_per_s": 1e3 / per_call_ms,
             "refreshes": st["refreshes_threshold"] - st0["refreshes_threshold"],
