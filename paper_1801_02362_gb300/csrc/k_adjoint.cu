@@ -12,6 +12,8 @@
 // adjoint_finish_warp (one warp per frame) turns beta into gradients and adds, at
 // approximate frames, the rotation term of Eq. (close_der_dist) (derivation in
 // pcv_device.cuh: adjoint_rotation_term).
+#include <algorithm>
+
 #include <cuda_fp16.h>
 
 #include "pcv_device.cuh"
@@ -45,7 +47,7 @@ adjoint_beta_pair(int F, int M, int N, const LT* __restrict__ lm, const float* _
                   const double* __restrict__ q,
                   const float* __restrict__ q32, const ST* __restrict__ P, const double* __restrict__ s, double lambda,
                   const ST* __restrict__ Rpair, const ST* __restrict__ Bseg, const int* __restrict__ seg_of_frame,
-                  ST* __restrict__ gs, ST* __restrict__ gz) {
+                  ST* __restrict__ gs, ST* __restrict__ gz, ST* __restrict__ part) {
   constexpr int KL = sizeof(ST) == 8 ? 4 : 8;
   __shared__ __align__(16) ST Ws[KL * 3][BP_TF * 3];  // gamma^s_fi Rot_fi[b][c] at [(i,c)][(f,b)]
   __shared__ __align__(16) ST Wz[KL * 3][BP_TF * 3];
@@ -60,7 +62,12 @@ adjoint_beta_pair(int F, int M, int N, const LT* __restrict__ lm, const float* _
 #pragma unroll
       for (int k = 0; k < 8; ++k) bs[u][b][k] = bz[u][b][k] = 0;
   const ST lam = (ST)lambda;
-  for (int i0 = 0; i0 < M; i0 += KL) {
+  // landmark range of this CTA: a split over gridDim.z when the frames give less than a wave
+  const int per = ((M + gridDim.z - 1) / gridDim.z + KL - 1) / KL * KL;
+  const int ibeg = blockIdx.z * per, iend = min(M, ibeg + per);
+  // a warp holds the frames f0 + 8 w .. f0 + 8 w + 7: warps wholly past F skip the products
+  const bool live = f0 + (tid >> 5) * 8 < F;
+  for (int i0 = ibeg; i0 < iend; i0 += KL) {
     for (int e = tid; e < BP_TF * KL; e += BP_THREADS) {
       const int ff = e / KL, ii = e - ff * KL;
       const int f = f0 + ff, i = i0 + ii;
@@ -68,7 +75,7 @@ adjoint_beta_pair(int F, int M, int N, const LT* __restrict__ lm, const float* _
       ST gsv = 0, gzv = 0;
 #pragma unroll
       for (int c = 0; c < 9; ++c) rot[c] = 0;
-      if (f < F && i < M) {
+      if (f < F && i < iend) {
         const ST qi = sizeof(ST) == 8 ? (ST)q[i] : (ST)q32[i];
         gammas<ST>(P[(size_t)f * M + i], lam, qi, (ST)s[f], gsv, gzv);
         const ST* R = Rpair ? Rpair + ((size_t)f * M + i) * 9 : Bseg + ((size_t)seg_of_frame[f] * M + i) * 9;
@@ -87,11 +94,11 @@ adjoint_beta_pair(int F, int M, int N, const LT* __restrict__ lm, const float* _
       const int ii = e / BP_TJ, jj = e - ii * BP_TJ;
       const int i = i0 + ii, j = j0 + jj;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) As[ii * 3 + c][jj] = (i < M && j < N) ? lm_coord<ST, LT>(lm, lmoff, N, i, j, c) : (ST)0;
+      for (int c = 0; c < 3; ++c) As[ii * 3 + c][jj] = (i < iend && j < N) ? lm_coord<ST, LT>(lm, lmoff, N, i, j, c) : (ST)0;
     }
     __syncthreads();
 #pragma unroll 2
-    for (int kk = 0; kk < KL * 3; ++kk) {
+    for (int kk = 0; kk < (live ? KL * 3 : 0); ++kk) {
       ST a[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) a[k] = As[kk][tx * 8 + k];
@@ -118,12 +125,39 @@ adjoint_beta_pair(int F, int M, int N, const LT* __restrict__ lm, const float* _
     for (int k = 0; k < 8; ++k) {
       const int j = j0 + tx * 8 + k;
       if (j >= N) continue;
+      if (part) {
+        ST* dst = part + (((size_t)blockIdx.z * F + f) * N + j) * 6;
 #pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        gs[((size_t)f * N + j) * 3 + b] = bs[u][b][k];
-        gz[((size_t)f * N + j) * 3 + b] = bz[u][b][k];
+        for (int b = 0; b < 3; ++b) {
+          dst[b] = bs[u][b][k];
+          dst[3 + b] = bz[u][b][k];
+        }
+      } else {
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          gs[((size_t)f * N + j) * 3 + b] = bs[u][b][k];
+          gz[((size_t)f * N + j) * 3 + b] = bz[u][b][k];
+        }
       }
     }
+  }
+}
+
+// beta of every frame from the landmark ranges' partial sums part[z][f][atom][6], in range
+// order
+template <typename ST>
+__global__ void beta_pair_part_sum(int F, int N, int nsplit, const ST* __restrict__ part, ST* __restrict__ gs,
+                                   ST* __restrict__ gz) {
+  const size_t total = (size_t)F * N * 6;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    ST v = 0;
+    for (int k = 0; k < nsplit; ++k) v += part[(size_t)k * total + e];
+    const size_t fj = e / 6;
+    const int comp = (int)(e - fj * 6);
+    if (comp < 3)
+      gs[fj * 3 + comp] = v;
+    else
+      gz[fj * 3 + comp - 3] = v;
   }
 }
 
@@ -892,9 +926,18 @@ adjoint_finish_staged(int F, int M, int N, const float* __restrict__ frames, con
 }  // namespace
 
 // ---------------------------------------------------------------------------------------
+int beta_pair_split(Prec p, int F, int M, int N) {
+  const int ctas = ((N + BP_TJ - 1) / BP_TJ) * ((F + BP_TF - 1) / BP_TF);
+  if (ctas <= 0 || ctas >= 152) return 1;
+  const int kl = p == P_F64 ? 4 : 8;
+  const int want = (2 * 152 + ctas - 1) / ctas;     // about two CTAs per SM
+  const int most = (M + 2 * kl - 1) / (2 * kl);     // at least two landmark chunks per range
+  return want < 1 ? 1 : (want > most ? (most < 1 ? 1 : most) : want);
+}
+
 void launch_adjoint_beta(Prec p, int F, const LandmarkDev& L, const void* P, const double* s, double lambda,
                          const void* Rpair, const void* Bseg, const int* seg_of_frame, bool seg_form, void* gs,
-                         void* gz, cudaStream_t st) {
+                         void* gz, void* part, cudaStream_t st) {
   if (F <= 0) return;
   if (seg_form && p != P_F64) {
     dim3 grid((L.N + BS_TJ - 1) / BS_TJ, (F + BS_TF - 1) / BS_TF);
@@ -909,25 +952,36 @@ void launch_adjoint_beta(Prec p, int F, const LandmarkDev& L, const void* P, con
     note_launch();
     return;
   }
-  dim3 grid((L.N + BP_TJ - 1) / BP_TJ, (F + BP_TF - 1) / BP_TF);
+  const int nsplit = part ? beta_pair_split(p, F, L.M, L.N) : 1;
+  void* out = nsplit > 1 ? part : nullptr;
+  dim3 grid((L.N + BP_TJ - 1) / BP_TJ, (F + BP_TF - 1) / BP_TF, nsplit);
   switch (p) {
     case P_F64:
       adjoint_beta_pair<double, double><<<grid, BP_THREADS, 0, st>>>(
           F, L.M, L.N, (const double*)L.coords, nullptr, L.q, L.q32, (const double*)P, s, lambda, (const double*)Rpair,
-          (const double*)Bseg, seg_of_frame, (double*)gs, (double*)gz);
+          (const double*)Bseg, seg_of_frame, (double*)gs, (double*)gz, (double*)out);
       break;
     case P_F32:
       adjoint_beta_pair<float, float><<<grid, BP_THREADS, 0, st>>>(
           F, L.M, L.N, (const float*)L.coords, L.off, L.q, L.q32, (const float*)P, s, lambda, (const float*)Rpair,
-          (const float*)Bseg, seg_of_frame, (float*)gs, (float*)gz);
+          (const float*)Bseg, seg_of_frame, (float*)gs, (float*)gz, (float*)out);
       break;
     case P_F16:
       adjoint_beta_pair<float, __half><<<grid, BP_THREADS, 0, st>>>(
           F, L.M, L.N, (const __half*)L.coords, L.off, L.q, L.q32, (const float*)P, s, lambda, (const float*)Rpair,
-          (const float*)Bseg, seg_of_frame, (float*)gs, (float*)gz);
+          (const float*)Bseg, seg_of_frame, (float*)gs, (float*)gz, (float*)out);
       break;
   }
   note_launch();
+  if (nsplit > 1) {
+    const size_t total = (size_t)F * L.N * 6;
+    const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 4);
+    if (p == P_F64)
+      beta_pair_part_sum<double><<<blocks, 256, 0, st>>>(F, L.N, nsplit, (const double*)part, (double*)gs, (double*)gz);
+    else
+      beta_pair_part_sum<float><<<blocks, 256, 0, st>>>(F, L.N, nsplit, (const float*)part, (float*)gs, (float*)gz);
+    note_launch();
+  }
 }
 
 int nl_beta_split(int max_upd, int M, int N) {

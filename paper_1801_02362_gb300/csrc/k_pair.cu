@@ -193,6 +193,9 @@ __device__ __forceinline__ void exact_tile_f32(int rows, const int* __restrict__
   const int ty = tid >> 4;  // frame pair: rows 2 ty + {0,1}
   load_tile_frames<float, float>(rows, row_frame, row0, c32, nullptr, s_frame, s_c);
   __syncthreads();
+  // a warp holds the rows row0 + 4 w .. row0 + 4 w + 3: warps wholly past the rows skip the
+  // products (a tile of few frames, e.g. one MD step)
+  const int kc_live = row0 + (tid >> 5) * 4 < rows ? KC : 0;
 
   float h[2][2][9];
 #pragma unroll
@@ -207,7 +210,7 @@ __device__ __forceinline__ void exact_tile_f32(int rows, const int* __restrict__
                                                       cols, ncol);
     __syncthreads();
 #pragma unroll 4
-    for (int jj = 0; jj < KC; ++jj) {
+    for (int jj = 0; jj < kc_live; ++jj) {
       float x[2][3], a[2][3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -271,7 +274,7 @@ __device__ __forceinline__ void exact_tile_f32(int rows, const int* __restrict__
                                                       cols, ncol);
     __syncthreads();
 #pragma unroll 4
-    for (int jj = 0; jj < KC; ++jj) {
+    for (int jj = 0; jj < kc_live; ++jj) {
       float x[2][3], a[2][3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -402,11 +405,14 @@ exact_pair_f64(int rows, const int* __restrict__ row_frame, const double* __rest
     for (int v = 0; v < 2; ++v)
 #pragma unroll
       for (int e = 0; e < 9; ++e) h[u][v][e] = 0.0;
+  // a warp holds the rows row0 + 4 w .. row0 + 4 w + 3: warps wholly past the rows skip the
+  // products (FP64 issue slots are shared by the SM's warps)
+  const bool live = row0 + (tid >> 5) * 4 < rows;
   for (int j0 = 0; j0 < N; j0 += KC) {
     stage_exact<double, double, double, TF, TM, KC, PF, PM>(j0, N, M, i0, frames, lm, lmoff, wts, 1, s_frame, s_c, Xs, As);
     __syncthreads();
 #pragma unroll 4
-    for (int jj = 0; jj < KC; ++jj) {
+    for (int jj = 0; jj < (live ? KC : 0); ++jj) {
       double x[2][3], a[2][3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {

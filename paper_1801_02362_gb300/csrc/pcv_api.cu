@@ -113,6 +113,7 @@ struct pcv_ctx {
   bool has_nl = false;
   DevBuf nl_keep;
   DevBuf nlSlot, nlUpd, nlU, nlUA, nlUAseg, nlN, NLtab, Rupd, Rnl, nlTiles, nlPart;
+  DevBuf betaPart;  // landmark-range partial sums of the adjoint beta at small F
   // close state
   bool has_y = false;
   DevBuf y, Bprior;
@@ -318,7 +319,7 @@ pcv_status pcv_destroy(pcv_ctx* c) {
                     &c->Dbuf, &c->Rpair, &c->Bseg, &c->Xr, &c->Bm, &c->GSb, &c->GZb, &c->Nx, &c->Nb, &c->Yc, &c->Gsum, &c->Amma, &c->Bmma, &c->S6, &c->mstat, &c->status, &c->nrecheck, &c->small, &c->h_frames,
                     &c->h_s, &c->h_z, &c->h_gs, &c->h_gz, &c->h_msd, &c->h_ref, &c->grp_inst, &c->grp_tiles,
                     &c->nl_keep, &c->nlSlot, &c->nlUpd, &c->nlU, &c->nlUA, &c->nlUAseg, &c->nlN, &c->NLtab,
-                    &c->Rupd, &c->Rnl, &c->nlTiles, &c->nlPart};
+                    &c->Rupd, &c->Rnl, &c->nlTiles, &c->nlPart, &c->betaPart};
   if (c->grp_stream) cudaStreamSynchronize(c->grp_stream);
   for (DevBuf* b : bufs) release(*b);
   if (c->grp_exec) cudaGraphExecDestroy(c->grp_exec);
@@ -560,6 +561,16 @@ pcv_status pcv_set_landmarks_weighted(pcv_ctx* c, int M, int N, const double* co
 
 // ---------------------------------------------------------------------------------------
 namespace {
+
+// workspace of the adjoint beta's landmark-range split (few frames); *part null: no split
+pcv_status beta_part_workspace(pcv_ctx* c, int F, void** part) {
+  *part = nullptr;
+  const int k = beta_pair_split(c->prec, F, c->M, c->N);
+  if (k <= 1) return PCV_OK;
+  const pcv_status ps = ensure(c, c->betaPart, work_elem(c->prec) * 6 * (size_t)k * F * c->N);
+  if (ps == PCV_OK) *part = c->betaPart.p;
+  return ps;
+}
 
 pcv_status ensure_frame_workspace(pcv_ctx* c, int F, bool close, bool grads) {
   const size_t M = c->M, W = c->band_W;
@@ -939,9 +950,14 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
                                (const float*)c->Gsum.p, (const float*)c->Yc.p, (const int*)c->segof.p, (float*)gs,
                                (float*)gz, st);
     } else {
+      void* part = nullptr;
+      if (!(seg_form && c->prec != P_F64)) {
+        const pcv_status pw = beta_part_workspace(c, F, &part);
+        if (pw != PCV_OK) return pw;
+      }
       ProfScope ps(c, seg_form && c->prec != P_F64 ? K_ADJ_BETA_SEG : K_ADJ_BETA);
       launch_adjoint_beta(c->prec, F, L, c->Dbuf.p, s, c->lambda, nullptr, c->Bseg.p, (const int*)c->segof.p,
-                          seg_form, gs, gz, st);
+                          seg_form, gs, gz, part, st);
     }
     // segment moments for Phi when frames share close structures (FP32 modes)
     const bool moments = c->prec != P_F64 && seg_form && nseg > 0;
@@ -1087,8 +1103,12 @@ pcv_status evaluate_exact(pcv_ctx* c, int F, const void* frames, double* s, doub
   if (refreshed) launch_fill_u8(refreshed, 1, (size_t)F, st);
   if (grads) {
     {
+      void* part = nullptr;
+      const pcv_status pw = beta_part_workspace(c, F, &part);
+      if (pw != PCV_OK) return pw;
       PROF(c, K_ADJ_BETA);
-      launch_adjoint_beta(c->prec, F, L, c->Dbuf.p, s, c->lambda, c->Rpair.p, nullptr, nullptr, false, gs, gz, st);
+      launch_adjoint_beta(c->prec, F, L, c->Dbuf.p, s, c->lambda, c->Rpair.p, nullptr, nullptr, false, gs, gz, part,
+                          st);
     }
     PROF(c, K_ADJ_FINISH);
     FrameRec none;

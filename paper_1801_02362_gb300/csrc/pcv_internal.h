@@ -126,10 +126,15 @@ void launch_finalize(Prec p, int F, int M, void* D, const double* q, const float
 // adjoint (k_adjoint.cu): beta = sum_i gamma_i Rot_fi a_i written into gs/gz, then the
 // per-frame finish.  P holds the softmax weights p (launch_finalize with want_p).  Rpair
 // (exact mode): F*M*9 rotations; otherwise Bseg[seg_of_frame[f]*M + i].  seg_form: frames
-// share their segment's rotations (close structure, few segments).
+// share their segment's rotations (close structure, few segments).  part: workspace of
+// beta_pair_split(p, F, M, N) * F * N * 6 elements of the storage type (double in FP64
+// mode), used when the split is above 1 (the frames give less than a wave of CTAs and the
+// landmarks are divided into ranges whose partial sums are added by a second kernel); null:
+// no split.
+int beta_pair_split(Prec p, int F, int M, int N);
 void launch_adjoint_beta(Prec p, int F, const LandmarkDev& L, const void* P, const double* s, double lambda,
                          const void* Rpair, const void* Bseg, const int* seg_of_frame, bool seg_form, void* gs,
-                         void* gz, cudaStream_t st);
+                         void* gz, void* part, cudaStream_t st);
 // rec.flag == nullptr: exact mode (no rotation term)
 // Gsum (Gamma^s_f, Gamma^z_f) and S6 (segment moments of segments from seg_base) are
 // optional inputs of the FP32 finish; null: computed from P and from Bseg, A32

@@ -32,7 +32,7 @@ def _eval(ctx, fr, precision, grad=True):
     return {k: v.double().cpu().numpy() if v.dtype != torch.uint8 else v.cpu().numpy() for k, v in out.items()}
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16"])
 @pytest.mark.parametrize("n", [61, 140])  # 3N*4 bytes unaligned / aligned to 16
 @pytest.mark.parametrize("f", [1, 3, 4])
 def test_exact_few_frames(pcv, precision, n, f):
@@ -51,7 +51,7 @@ def test_exact_few_frames(pcv, precision, n, f):
     assert grad_err(g["dzdx"], r["dzdx"]) < GRAD_TOL[precision]
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16"])
 def test_close_one_frame_per_call(pcv, precision):
     """40 frames fed one per call: refresh decisions carried across calls, approximate and
     refreshed frames from the streaming kernels; identical to the oracle's single run."""
@@ -68,6 +68,29 @@ def test_close_one_frame_per_call(pcv, precision):
     tol = TOL[precision]
     assert d_err(g["msd"], r["D"], fr, lm) < tol
     assert s_err(g["s"], r["s"], 60) < tol
+    assert z_err(g["z"], r["z"], lam) < tol
+    assert grad_err(g["dsdx"], r["dsdx"]) < GRAD_TOL[precision]
+    assert grad_err(g["dzdx"], r["dzdx"]) < GRAD_TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("mode", ["exact", "close"])
+def test_one_frame_many_landmarks_gradients(pcv, precision, mode):
+    """One frame per call against 521 landmarks of 24 atoms (one MD step of a long path):
+    the adjoint's landmark sum is split into ranges (ragged last range) whose partial sums
+    are added by a second kernel; gradients against the oracle frame by frame."""
+    lm, fr, lam = problem(36, 24, 521, 12, noise=0.02, ou_rho=0.9)
+    eps = -1.0 if mode == "exact" else 0.01
+    r = oracle.exact(fr, lm, lam, want_grad=True) if mode == "exact" else oracle.close(fr, lm, lam, eps,
+                                                                                        want_grad=True)
+    ctx = pcv.PathCV(lm, lam, eps=eps, precision=precision)
+    parts = [_eval(ctx, fr[t:t + 1], precision) for t in range(fr.shape[0])]
+    ctx.close()
+    g = {k: np.concatenate([p[k] for p in parts]) for k in parts[0]}
+    if mode == "close":
+        np.testing.assert_array_equal(g["refreshed"], r["refreshed"])
+    tol = TOL[precision]
+    assert s_err(g["s"], r["s"], 521) < tol
     assert z_err(g["z"], r["z"], lam) < tol
     assert grad_err(g["dsdx"], r["dsdx"]) < GRAD_TOL[precision]
     assert grad_err(g["dzdx"], r["dzdx"]) < GRAD_TOL[precision]
