@@ -228,10 +228,17 @@ enum {
                               kernels then rotate while staging; so they also do when the
                               device cannot allocate the operands).  Results agree within
                               the mode's tolerance either way.                          */
-  PCV_OPT_TENSOR_CORES = 7 /* 1 (default): with materialised operands, the segment adjoint
+  PCV_OPT_TENSOR_CORES = 7, /* 1 (default): with materialised operands, the segment adjoint
                               beta = sum_i gamma_i (R_{a_i y} a_i) runs on the tensor cores
                               (TF32 operands split hi + lo, three products per term, on
                               deviations from the close structure); 0: FP32 CUDA cores.   */
+  PCV_OPT_HOST_CHUNKS = 8,  /* pcv_evaluate_host: number of chunks the batch is split into
+                              so that copies overlap evaluation (0 = automatic, default;
+                              1 = no overlap; at most 64)                               */
+  PCV_OPT_HOST_END_SHARE = 9 /* pcv_evaluate_host: size of the first and the last chunk in
+                              percent of a middle chunk (1..100; default 25): a small first
+                              chunk starts the evaluation early and a small last chunk
+                              shortens the copy-out that follows it                     */
 };
 PCV_API pcv_status pcv_set_option(pcv_ctx* ctx, int key, int64_t value);
 

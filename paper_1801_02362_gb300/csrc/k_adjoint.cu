@@ -713,12 +713,11 @@ adjoint_finish_staged(int F, int M, int N, const float* __restrict__ frames, con
   const float* x = frames + (size_t)f * N3;
   float* gsp = gs + (size_t)f * N3;
   float* gzp = gz + (size_t)f * N3;
-  const bool approx = rec.flag && rec.flag[f] == 0;
-  const int r = approx ? rec.ref[f] : 0;
-  const float* y = r >= 0 ? frames + (size_t)r * N3 : prior_coords;
+  // The frame and beta rows are copied first; the per-frame scalars are loaded next (the
+  // staging's asm statements are compiler barriers: loads written after them start after
+  // them), then the close structure's row once its index is known.
   if (ASYNC) {
-    // rows are 16-byte aligned (3N % 4 == 0): every 16-byte piece of x, beta^s, beta^z and
-    // y is in flight at once
+    // rows are 16-byte aligned (3N % 4 == 0): every 16-byte piece is in flight at once
     const int n4 = N3 / 4;
     for (int e = lane; e < n4; e += 32) {
       const unsigned o = 16u * e;
@@ -728,13 +727,31 @@ adjoint_finish_staged(int F, int M, int N, const float* __restrict__ frames, con
                    "l"(gsp + 4 * e) : "memory");
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(bz) + o),
                    "l"(gzp + 4 * e) : "memory");
-      if (approx)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(uv) + o),
+    }
+  }
+  const bool approx = rec.flag && rec.flag[f] == 0;
+  const int r = rec.flag ? rec.ref[f] : 0;
+  const float sf = (float)s[f];
+  float Gs = 0.0f, Gz = 0.0f;
+  if (Gsum) {
+    Gs = Gsum[2 * f];
+    Gz = Gsum[2 * f + 1];
+  }
+  double4 qq = make_double4(1.0, 0.0, 0.0, 0.0);
+  int seg = 0;
+  if (rec.flag) {
+    qq = rec.qxy[f];
+    seg = seg_of_frame[f];
+  }
+  const float* y = r >= 0 ? frames + (size_t)r * N3 : prior_coords;
+  if (ASYNC) {
+    if (approx) {
+      const int n4 = N3 / 4;
+      for (int e = lane; e < n4; e += 32)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                         (unsigned)__cvta_generic_to_shared(uv) + 16u * e),
                      "l"(y + 4 * e) : "memory");
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncwarp();
-    for (int e = lane; e < N3; e += 32) xv[e] -= cx[e - 3 * (e / 3)];
   } else {
     for (int e = lane; e < N3; e += 32) {
       const int b = e - 3 * (e / 3);
@@ -744,22 +761,72 @@ adjoint_finish_staged(int F, int M, int N, const float* __restrict__ frames, con
       if (approx) uv[e] = y[e];
     }
   }
-  const float sf = (float)s[f];
-  float Gs, Gz;
-  if (Gsum) {
-    Gs = Gsum[2 * f];
-    Gz = Gsum[2 * f + 1];
-  } else {
-    Gs = 0.0f;
-    Gz = 0.0f;
-    for (int i = lane; i < M; i += 32) {
-      float gsv, gzv;
-      gammas<float>(P[(size_t)f * M + i], lambda, q32[i], sf, gsv, gzv);
-      Gs += gsv;
-      Gz += gzv;
+  const float4 cyv = approx && r >= 0 ? c32[r] : prior_c;
+  // Over the landmarks while the copies are in flight (global loads only): Gamma when the
+  // gamma kernel did not produce it, and at approximate frames Phi = sum_i gamma_i S_i (s, z)
+  float ph[12];
+#pragma unroll
+  for (int e = 0; e < 12; ++e) ph[e] = 0.0f;
+  if (approx || !Gsum) {
+    constexpr int U = 4;  // landmarks per lane whose loads are in flight together
+    for (int i0 = lane; i0 < M; i0 += 32 * U) {
+      float pv[U], qv[U], S[U][6];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + 32 * u;
+        const bool ok = i < M;
+        pv[u] = ok ? P[(size_t)f * M + i] : 0.0f;
+        qv[u] = ok ? q32[i] : 0.0f;
+#pragma unroll
+        for (int e = 0; e < 6; ++e) S[u][e] = 0.0f;
+        if (ok && approx) {
+          if (S6) {
+            const float* sp = S6 + ((size_t)(seg - seg_base) * M + i) * 6;
+#pragma unroll
+            for (int e = 0; e < 6; ++e) S[u][e] = sp[e];
+          } else {
+            const float* B = Bseg + ((size_t)seg * M + i) * 9;
+            const float* a = A32 + (size_t)i * 6;
+            const float A[9] = {a[0], a[1], a[2], a[1], a[3], a[4], a[2], a[4], a[5]};
+            float BA[9];
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+#pragma unroll
+              for (int cc = 0; cc < 3; ++cc)
+                BA[3 * b + cc] = B[3 * b] * A[cc] + B[3 * b + 1] * A[3 + cc] + B[3 * b + 2] * A[6 + cc];
+            const int ib[6] = {0, 0, 0, 1, 1, 2}, ic[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+            for (int e = 0; e < 6; ++e) {
+              const int b = ib[e], cc = ic[e];
+              S[u][e] = BA[3 * b] * B[3 * cc] + BA[3 * b + 1] * B[3 * cc + 1] + BA[3 * b + 2] * B[3 * cc + 2];
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        float gsv, gzv;
+        gammas<float>(pv[u], lambda, qv[u], sf, gsv, gzv);  // zero for i >= M (p = 0)
+        if (!Gsum) {
+          Gs += gsv;
+          Gz += gzv;
+        }
+#pragma unroll
+        for (int e = 0; e < 6; ++e) {
+          ph[e] = fmaf(gsv, S[u][e], ph[e]);
+          ph[6 + e] = fmaf(gzv, S[u][e], ph[6 + e]);
+        }
+      }
     }
-    Gs = wsum(Gs);
-    Gz = wsum(Gz);
+    if (!Gsum) {
+      Gs = wsum(Gs);
+      Gz = wsum(Gz);
+    }
+  }
+  if (ASYNC) {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncwarp();
+    for (int e = lane; e < N3; e += 32) xv[e] -= cx[e - 3 * (e / 3)];
   }
   if (!approx) {
     __syncwarp();
@@ -790,26 +857,22 @@ adjoint_finish_staged(int F, int M, int N, const float* __restrict__ frames, con
     }
     return;
   }
-  float4 cyv = prior_c;
-  if (r >= 0) cyv = c32[r];
   const float cy[3] = {cyv.x, cyv.y, cyv.z};
   for (int e = lane; e < N3; e += 32) uv[e] -= cy[e - 3 * (e / 3)];
   __syncwarp();
   float R[9], qxy[4];
-  {
-    const double4 qq = rec.qxy[f];
-    qxy[0] = (float)qq.x;
-    qxy[1] = (float)qq.y;
-    qxy[2] = (float)qq.z;
-    qxy[3] = (float)qq.w;
-    quat_to_rot(qxy, R);
-  }
+  qxy[0] = (float)qq.x;
+  qxy[1] = (float)qq.y;
+  qxy[2] = (float)qq.z;
+  qxy[3] = (float)qq.w;
+  quat_to_rot(qxy, R);
   // X = sum_j w x_j beta_j^T (s, z) and H_xy = sum_j w y_j x_j^T, centred, true weights
   float acc[27];
 #pragma unroll
   for (int e = 0; e < 27; ++e) acc[e] = 0.0f;
   float xw[3] = {0.0f, 0.0f, 0.0f}, yw[3] = {0.0f, 0.0f, 0.0f}, bws[3] = {0.0f, 0.0f, 0.0f},
         bwz[3] = {0.0f, 0.0f, 0.0f};  // alignment weights
+#pragma unroll 2
   for (int j = lane; j < N; j += 32) {
     const float wj = wts ? wts[j] : wuni;
     float v[3], u[3];
@@ -836,41 +899,6 @@ adjoint_finish_staged(int F, int M, int N, const float* __restrict__ frames, con
         acc[9 + 3 * b + cc] = fmaf(wv, bz[3 * j + cc], acc[9 + 3 * b + cc]);
         acc[18 + 3 * b + cc] = fmaf(wu, v[cc], acc[18 + 3 * b + cc]);
       }
-    }
-  }
-  // Phi = sum_i gamma_i S_i (s, z)
-  float ph[12];
-#pragma unroll
-  for (int e = 0; e < 12; ++e) ph[e] = 0.0f;
-  const int seg = seg_of_frame[f];
-  for (int i = lane; i < M; i += 32) {
-    float gsv, gzv;
-    gammas<float>(P[(size_t)f * M + i], lambda, q32[i], sf, gsv, gzv);
-    float S[6];
-    if (S6) {
-      const float* sp = S6 + ((size_t)(seg - seg_base) * M + i) * 6;
-#pragma unroll
-      for (int e = 0; e < 6; ++e) S[e] = sp[e];
-    } else {
-      const float* B = Bseg + ((size_t)seg * M + i) * 9;
-      const float* a = A32 + (size_t)i * 6;
-      const float A[9] = {a[0], a[1], a[2], a[1], a[3], a[4], a[2], a[4], a[5]};
-      float BA[9];
-#pragma unroll
-      for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int cc = 0; cc < 3; ++cc) BA[3 * b + cc] = B[3 * b] * A[cc] + B[3 * b + 1] * A[3 + cc] + B[3 * b + 2] * A[6 + cc];
-      const int ib[6] = {0, 0, 0, 1, 1, 2}, ic[6] = {0, 1, 2, 1, 2, 2};
-#pragma unroll
-      for (int e = 0; e < 6; ++e) {
-        const int b = ib[e], cc = ic[e];
-        S[e] = BA[3 * b] * B[3 * cc] + BA[3 * b + 1] * B[3 * cc + 1] + BA[3 * b + 2] * B[3 * cc + 2];
-      }
-    }
-#pragma unroll
-    for (int e = 0; e < 6; ++e) {
-      ph[e] = fmaf(gsv, S[e], ph[e]);
-      ph[6 + e] = fmaf(gzv, S[e], ph[6 + e]);
     }
   }
 #pragma unroll
@@ -901,6 +929,7 @@ adjoint_finish_staged(int F, int M, int N, const float* __restrict__ frames, con
       Cz[cc] = 2.0f * (Gz * xw[cc] - Rbz) + Tz[cc] * yw[0] + Tz[3 + cc] * yw[1] + Tz[6 + cc] * yw[2];
     }
   }
+#pragma unroll 2
   for (int j = lane; j < N; j += 32) {
     const float wj = wts ? wts[j] : wuni, w2 = wa ? wa[j] : 0.0f;
     float v[3], u[3], bsj[3], bzj[3];
@@ -1037,21 +1066,47 @@ void launch_adjoint_finish(Prec p, int F, const void* frames, const LandmarkDev&
   // FP32 modes: frames staged in shared memory (4 arrays of 3N floats per warp)
   const size_t per_warp = (size_t)12 * L.N * sizeof(float);
   if (p != P_F64 && per_warp <= 200 * 1024) {
-    const int wpb = per_warp * 4 <= 96 * 1024 ? 4 : (per_warp * 2 <= 160 * 1024 ? 2 : 1);
-    const size_t smem = per_warp * wpb;
     const bool async = (3 * L.N) % 4 == 0 && ((uintptr_t)frames % 16) == 0 && ((uintptr_t)gs % 16) == 0 &&
                        ((uintptr_t)gz % 16) == 0 && ((uintptr_t)prior.coords % 16) == 0;
+    // warps per block: the most resident warps per SM (shared memory and registers both
+    // limit them), larger blocks on ties
+    thread_local size_t memo_bytes = 0;
+    thread_local bool memo_async = false;
+    thread_local int memo_wpb = 0;
+    int wpb = 1, best = -1;
+    if (memo_wpb > 0 && memo_bytes == per_warp && memo_async == async) {
+      wpb = memo_wpb;
+      best = 0;
+    }
+    for (int k = best < 0 ? 4 : 0; k >= 1; --k) {
+      const size_t sm_k = per_warp * k;
+      if (sm_k > 200 * 1024) continue;
+      int nb = 0;
+      if (async) {
+        cudaFuncSetAttribute(adjoint_finish_staged<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_k);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, adjoint_finish_staged<true>, 32 * k, sm_k);
+      } else {
+        cudaFuncSetAttribute(adjoint_finish_staged<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_k);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, adjoint_finish_staged<false>, 32 * k, sm_k);
+      }
+      if (nb * k > best) {
+        best = nb * k;
+        wpb = k;
+      }
+    }
+    memo_bytes = per_warp;
+    memo_async = async;
+    memo_wpb = wpb;
+    const size_t smem = per_warp * wpb;
     const unsigned blocks = (unsigned)((F + wpb - 1) / wpb);
-    if (async) {
-      if (smem > 48 * 1024)
-        cudaFuncSetAttribute(adjoint_finish_staged<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (async) {  // the attribute is set for every launch: the search above changed it
+      cudaFuncSetAttribute(adjoint_finish_staged<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       adjoint_finish_staged<true><<<blocks, 32 * wpb, smem, st>>>(
           F, L.M, L.N, (const float*)frames, fi.c32, L.w, L.wa, (float)L.dscale, L.A32, L.q32, (const float*)P, s,
           (float)lambda, Gsum, S6, seg_base, (const float*)Bseg, seg_of_frame, rec, (const float*)prior.coords,
           prior.c32, (float*)gs, (float*)gz);
     } else {
-      if (smem > 48 * 1024)
-        cudaFuncSetAttribute(adjoint_finish_staged<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(adjoint_finish_staged<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       adjoint_finish_staged<false><<<blocks, 32 * wpb, smem, st>>>(
           F, L.M, L.N, (const float*)frames, fi.c32, L.w, L.wa, (float)L.dscale, L.A32, L.q32, (const float*)P, s,
           (float)lambda, Gsum, S6, seg_base, (const float*)Bseg, seg_of_frame, rec, (const float*)prior.coords,

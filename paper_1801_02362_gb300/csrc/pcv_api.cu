@@ -129,6 +129,7 @@ struct pcv_ctx {
   DevBuf S6;                      // per-segment landmark moments R A R^T of the finish
   DevBuf h_frames, h_s, h_z, h_gs, h_gz, h_msd, h_ref;  // device staging for pcv_evaluate_host
   cudaStream_t h2d_stream = nullptr, d2h_stream = nullptr;  // copy streams of pcv_evaluate_host
+  int host_chunks = 0, host_end_share = 25;                  // its chunk plan (PCV_OPT_HOST_*)
   std::vector<cudaEvent_t> h_events;                        // its chunk events
   Small* small_host = nullptr;      // mapped pinned host memory
   Small* small_host_dev = nullptr;  // its device-side address
@@ -385,6 +386,14 @@ pcv_status pcv_set_option(pcv_ctx* c, int key, int64_t value) {
       return PCV_OK;
     case PCV_OPT_TENSOR_CORES:
       c->tensor_cores = value != 0;
+      return PCV_OK;
+    case PCV_OPT_HOST_CHUNKS:
+      if (value < 0 || value > 64) return fail(c, PCV_EINVAL, "host chunks must be in 0..64");
+      c->host_chunks = (int)value;
+      return PCV_OK;
+    case PCV_OPT_HOST_END_SHARE:
+      if (value < 1 || value > 100) return fail(c, PCV_EINVAL, "host end share must be in 1..100");
+      c->host_end_share = (int)value;
       return PCV_OK;
     case PCV_OPT_EXACT_TILE:
     case PCV_OPT_APPROX_TILE:
@@ -1311,6 +1320,27 @@ pcv_status pcv_evaluate_group(pcv_ctx* const* ctxs, int n, const pcv_batch_io* i
   return PCV_OK;
 }
 
+// Chunk sizes of pcv_evaluate_host: n chunks (0: about one per 16k frames, between 1 and 8)
+// whose first and last hold end_share percent of a middle one; at least 2048 frames each.
+std::vector<int> host_chunk_plan(int F, int n, int end_share) {
+  if (n <= 0) n = std::min(8, std::max(1, (F + 16383) / 16384));
+  n = std::min(n, std::max(1, F / 2048));
+  if (n <= 1) return {F};
+  const double we = end_share / 100.0;
+  const double unit = F / ((n - 2) + 2.0 * we);
+  const int e = std::max(2048, (int)(unit * we));
+  std::vector<int> plan(n, 0);
+  plan[0] = plan[n - 1] = e;
+  const int rest = F - 2 * e, mid = n - 2;
+  if (mid == 0) {
+    plan[0] = F / 2;
+    plan[1] = F - F / 2;
+    return plan;
+  }
+  for (int k = 0; k < mid; ++k) plan[1 + k] = rest / mid + (k < rest % mid ? 1 : 0);
+  return plan;
+}
+
 pcv_status pcv_evaluate_host(pcv_ctx* c, int F, const void* frames, double* s, double* z, void* dsdx, void* dzdx,
                              double* msd, uint8_t* refreshed) {
   if (!c) return fail(nullptr, PCV_EINVAL, "NULL context");
@@ -1334,9 +1364,13 @@ pcv_status pcv_evaluate_host(pcv_ctx* c, int F, const void* frames, double* s, d
   // The batch is evaluated in chunks of consecutive frames (the close-structure state and
   // the neighbour list carry over between chunks exactly as between calls): the frames of
   // later chunks are copied in on one copy stream, and the outputs of earlier chunks copied
-  // out on another, while a chunk is evaluated on the context's stream.
-  const int chunk = F <= 16384 ? F : std::max(8192, (F + 5) / 6);
-  const int nchunk = (F + chunk - 1) / chunk;
+  // out on another, while a chunk is evaluated on the context's stream.  The first and the
+  // last chunk are smaller than the others: nothing overlaps the first chunk's copy-in or
+  // the last chunk's copy-out.
+  const std::vector<int> plan = host_chunk_plan(F, c->host_chunks, c->host_end_share);
+  const int nchunk = (int)plan.size();
+  std::vector<size_t> first(nchunk + 1, 0);
+  for (int k = 0; k < nchunk; ++k) first[k + 1] = first[k] + (size_t)plan[k];
   for (cudaStream_t* hs : {&c->h2d_stream, &c->d2h_stream})
     if (!*hs) CUDA_TRY(c, cudaStreamCreateWithFlags(hs, cudaStreamNonBlocking));
   while ((int)c->h_events.size() < 2 * nchunk + 1) {
@@ -1353,13 +1387,13 @@ pcv_status pcv_evaluate_host(pcv_ctx* c, int F, const void* frames, double* s, d
   CUDA_TRY(c, cudaStreamWaitEvent(c->h2d_stream, ev_start, 0));
   CUDA_TRY(c, cudaStreamWaitEvent(c->d2h_stream, ev_start, 0));
   for (int k = 0; k < nchunk; ++k) {
-    const size_t f0 = (size_t)k * chunk, nf = std::min<size_t>(chunk, F - f0);
+    const size_t f0 = first[k], nf = (size_t)plan[k];
     CUDA_TRY(c, cudaMemcpyAsync((char*)c->h_frames.p + fstride * f0, (const char*)frames + fstride * f0, fstride * nf,
                                 cudaMemcpyHostToDevice, c->h2d_stream));
     CUDA_TRY(c, cudaEventRecord(ev_in[k], c->h2d_stream));
   }
   for (int k = 0; k < nchunk; ++k) {
-    const size_t f0 = (size_t)k * chunk, nf = std::min<size_t>(chunk, F - f0);
+    const size_t f0 = first[k], nf = (size_t)plan[k];
     CUDA_TRY(c, cudaStreamWaitEvent(c->stream, ev_in[k], 0));
     st = pcv_evaluate(c, (int)nf, (char*)c->h_frames.p + fstride * f0, (double*)c->h_s.p + f0,
                       (double*)c->h_z.p + f0, dsdx ? (char*)c->h_gs.p + fstride * f0 : nullptr,

@@ -21,6 +21,7 @@ PCV_FP64, PCV_FP32, PCV_FP16_STORAGE = 0, 1, 2
 PCV_OPT_BAND, PCV_OPT_CHUNK, PCV_OPT_EXACT_TILE, PCV_OPT_APPROX_TILE, PCV_OPT_PROFILE = 1, 2, 3, 4, 5
 PCV_OPT_MATERIALIZE = 6
 PCV_OPT_TENSOR_CORES = 7
+PCV_OPT_HOST_CHUNKS, PCV_OPT_HOST_END_SHARE = 8, 9
 PCV_PROFILE_KERNELS = 24
 
 _STATUS_NAMES = {0: "PCV_OK", -1: "PCV_EINVAL", -2: "PCV_ECUDA", -3: "PCV_ENOMEM", -4: "PCV_ENOCONV",

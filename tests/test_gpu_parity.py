@@ -281,6 +281,48 @@ def test_host_entry_point_matches_device(pcv):
     ctx.close()
 
 
+_CHUNK_CASE = {}
+
+
+def _chunk_case():
+    if not _CHUNK_CASE:
+        lm, fr, lam = problem(15, 40, 30, 9000, noise=0.03)
+        r = oracle.close(fr, lm, lam, 0.01, want_grad=True)
+        _CHUNK_CASE.update(lm=lm, fr=fr, lam=lam, r=r)
+    return _CHUNK_CASE
+
+
+@pytest.mark.parametrize("chunks,end_share", [(1, 25), (2, 25), (4, 1), (3, 100), (0, 25)])
+def test_host_entry_point_chunk_plans(pcv, chunks, end_share):
+    """9000 frames through pcv_evaluate_host split into 1..4 chunks (first and last chunk
+    smaller than the others, or all equal): the close-structure state carries over between
+    chunks, so refresh decisions and values match the oracle's single run."""
+    import ctypes
+
+    c = _chunk_case()
+    lm, fr, lam, r = c["lm"], c["fr"], c["lam"], c["r"]
+    nref = int((r["refreshed"] > 0).sum())
+    assert 3 < nref < fr.shape[0] // 4
+    ctx = pcv.PathCV(lm, lam, eps=0.01, precision="fp32")
+    pcv.pcv_set_option(ctx.ctx, pcv.PCV_OPT_HOST_CHUNKS, chunks)
+    pcv.pcv_set_option(ctx.ctx, pcv.PCV_OPT_HOST_END_SHARE, end_share)
+    f32 = np.ascontiguousarray(fr, dtype=np.float32)
+    F = fr.shape[0]
+    s, z = np.zeros(F), np.zeros(F)
+    gs, gz = np.zeros_like(f32), np.zeros_like(f32)
+    msd = np.zeros((F, lm.shape[0]))
+    ref = np.zeros(F, dtype=np.uint8)
+    p = lambda a: ctypes.c_void_p(a.ctypes.data)
+    pcv.pcv_evaluate_host(ctx.ctx, F, p(f32), p(s), p(z), p(gs), p(gz), p(msd), p(ref))
+    ctx.close()
+    np.testing.assert_array_equal(ref, r["refreshed"])
+    assert d_err(msd, r["D"], fr, lm) < TOL["fp32"]
+    assert s_err(s, r["s"], lm.shape[0]) < TOL["fp32"]
+    assert z_err(z, r["z"], lam) < TOL["fp32"]
+    assert grad_err(gs.astype(np.float64), r["dsdx"]) < GRAD_TOL["fp32"]
+    assert grad_err(gz.astype(np.float64), r["dzdx"]) < GRAD_TOL["fp32"]
+
+
 def test_invalid_arguments_are_rejected(pcv):
     lm, fr, lam = problem(14, 10, 4, 2)
     ctx = pcv.PathCV(lm, lam)
