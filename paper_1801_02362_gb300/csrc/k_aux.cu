@@ -361,37 +361,18 @@ __device__ __forceinline__ double warp_direct_f32(int N, const float* __restrict
   return D;
 }
 
+// One alignment of frame t onto the structure `ref` (-1: the stored prior y), written to
+// slot `slot` of the outputs.  Returns, on every lane, whether the frame definitely exceeds
+// eps (bit 0 of the flag set, outside the FP64 recheck band).
 template <bool F64>
-__global__ void align_kernel(int mode, int F, int W, int t0, int t1, int ref_index, int N,
-                             const void* __restrict__ frames_v, RefView prior,
-                             const float4* __restrict__ c32, const double4* __restrict__ c64,
-                             const double* __restrict__ fG, const float* __restrict__ wts,
-                             const double* __restrict__ w64, double dscale, double eps,
-                             double* __restrict__ outD, double4* __restrict__ outQ,
-                             uint8_t* __restrict__ outFlag, int* __restrict__ recheck_list,
-                             int* __restrict__ recheck_count) {
-  const int wid = warp_global();
+__device__ __forceinline__ bool align_frame(int mode, int t, int ref, int slot, int N, const void* __restrict__ frames_v,
+                                            const RefView& prior, const float4* __restrict__ c32,
+                                            const double4* __restrict__ c64, const double* __restrict__ fG,
+                                            const float* __restrict__ wts, const double* __restrict__ w64,
+                                            double dscale, double eps, double* __restrict__ outD,
+                                            double4* __restrict__ outQ, uint8_t* __restrict__ outFlag,
+                                            int* __restrict__ recheck_list, int* __restrict__ recheck_count) {
   const int lane = threadIdx.x & 31;
-  int t, ref, slot;
-  if (mode == 0) {  // band rows t in [t0, t1)
-    t = t0 + wid / W;
-    const int k = 1 + wid % W;
-    if (t >= t1) return;
-    ref = t - k;
-    slot = t * W + k - 1;
-    if (ref < 0) {
-      if (lane == 0) {
-        outD[slot] = -1.0;
-        outFlag[slot] = 0;
-      }
-      return;
-    }
-  } else {  // chunk
-    t = t0 + wid;
-    if (t >= t1) return;
-    ref = ref_index;
-    slot = t;
-  }
   const double Gx = fG[t];
   const double Gy = ref >= 0 ? fG[ref] : prior.G;
   if (F64) {
@@ -400,25 +381,75 @@ __global__ void align_kernel(int mode, int F, int W, int t0, int t1, int ref_ind
     const double* y = ref >= 0 ? frames + (size_t)ref * N * 3 : (const double*)prior.coords;
     const double4 cy = ref >= 0 ? c64[ref] : prior.c64;
     warp_corr_f64(N, frames + (size_t)t * N * 3, c64[t], y, cy, w64, H);
+    int ex = 0;
     if (lane == 0) {
       bool amb = false;
       finish_alignment(H, Gx, Gy, dscale, eps, false, outD + slot, outQ + slot, outFlag + slot, &amb);
+      ex = outFlag[slot] & 1;
     }
-  } else {
-    const float* frames = (const float*)frames_v;
-    const float* y = ref >= 0 ? frames + (size_t)ref * N * 3 : (const float*)prior.coords;
-    const float4 cy = ref >= 0 ? c32[ref] : prior.c32;
-    double bound = 0.0;
-    const double D = warp_direct_f32(N, frames + (size_t)t * N * 3, c32[t], y, cy, wts, Gx, Gy, dscale, &bound);
-    if (lane == 0) {
-      const bool amb = fabs(D - eps) <= bound;
-      outD[slot] = D;
-      outFlag[slot] = (uint8_t)((D > eps ? 1 : 0) | (amb ? 2 : 0));
-      if (amb) {
-        const int pos = atomicAdd(recheck_count, 1);
-        recheck_list[pos] = (slot << 1) | (mode == 0 ? 0 : 1);
+    return __shfl_sync(0xffffffffu, ex, 0) != 0;
+  }
+  const float* frames = (const float*)frames_v;
+  const float* y = ref >= 0 ? frames + (size_t)ref * N * 3 : (const float*)prior.coords;
+  const float4 cy = ref >= 0 ? c32[ref] : prior.c32;
+  double bound = 0.0;
+  const double D = warp_direct_f32(N, frames + (size_t)t * N * 3, c32[t], y, cy, wts, Gx, Gy, dscale, &bound);
+  const bool amb = fabs(D - eps) <= bound;  // the same on every lane (D and bound are)
+  if (lane == 0) {
+    outD[slot] = D;
+    outFlag[slot] = (uint8_t)((D > eps ? 1 : 0) | (amb ? 2 : 0));
+    if (amb) {
+      const int pos = atomicAdd(recheck_count, 1);
+      recheck_list[pos] = (slot << 1) | (mode == 0 ? 0 : 1);
+    }
+  }
+  return D > eps && !amb;
+}
+
+// mode 0: band rows, one warp per (frame t in [t0, t1), offset k in 1..W).
+// mode 1: chunk [t0, t1) against `ref_index`.  The warps take the frames in order with a
+// grid stride; a frame that definitely exceeds eps lowers *stop (set to t1 beforehand), and
+// frames past *stop are skipped: only the first exceeding frame matters to the search, and
+// every frame t <= the final *stop is aligned (a warp skips t only when t > *stop at its
+// check, and *stop never rises).  The frames aligned beyond the first exceed are bounded by
+// the warps in flight instead of the chunk length.
+template <bool F64>
+__global__ void align_kernel(int mode, int F, int W, int t0, int t1, int ref_index, int N,
+                             const void* __restrict__ frames_v, RefView prior,
+                             const float4* __restrict__ c32, const double4* __restrict__ c64,
+                             const double* __restrict__ fG, const float* __restrict__ wts,
+                             const double* __restrict__ w64, double dscale, double eps,
+                             double* __restrict__ outD, double4* __restrict__ outQ,
+                             uint8_t* __restrict__ outFlag, int* __restrict__ recheck_list,
+                             int* __restrict__ recheck_count, int* __restrict__ stop) {
+  const int wid = warp_global();
+  const int lane = threadIdx.x & 31;
+  if (mode == 0) {  // band rows t in [t0, t1)
+    const int t = t0 + wid / W;
+    const int k = 1 + wid % W;
+    if (t >= t1) return;
+    const int ref = t - k;
+    const int slot = t * W + k - 1;
+    if (ref < 0) {
+      if (lane == 0) {
+        outD[slot] = -1.0;
+        outFlag[slot] = 0;
       }
+      return;
     }
+    align_frame<F64>(0, t, ref, slot, N, frames_v, prior, c32, c64, fG, wts, w64, dscale, eps, outD, outQ, outFlag,
+                     recheck_list, recheck_count);
+    return;
+  }
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int t = t0 + wid; t < t1; t += nw) {
+    int lim = 0;
+    if (lane == 0) lim = *(volatile int*)stop;
+    lim = __shfl_sync(0xffffffffu, lim, 0);  // one value for the whole warp
+    if (t > lim) return;
+    const bool ex = align_frame<F64>(1, t, ref_index, t, N, frames_v, prior, c32, c64, fG, wts, w64, dscale, eps,
+                                     outD, outQ, outFlag, recheck_list, recheck_count);
+    if (ex && lane == 0) atomicMin(stop, t);
   }
 }
 
@@ -528,9 +559,12 @@ __global__ void recheck_kernel(const int* __restrict__ list, const int* __restri
 
 __global__ void set_int_kernel(int* p, int v) { *p = v; }
 
-__global__ void first_exceed_kernel(int t0, int t1, const uint8_t* __restrict__ flag, int* first) {
+// frames past *stop may not have been aligned by the chunk kernel: the scan ends at *stop
+__global__ void first_exceed_kernel(int t0, int t1, const uint8_t* __restrict__ flag, const int* __restrict__ stop,
+                                    int* first) {
   const int t = t0 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < t1 && (flag[t] & 1)) atomicMin(first, t);
+  const int hi = stop ? min(t1, *stop + 1) : t1;
+  if (t < hi && (flag[t] & 1)) atomicMin(first, t);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -900,29 +934,47 @@ void launch_align_band(Prec p, int F, int W, int t_lo, int t_hi, const void* fra
   if (p == P_F64)
     align_kernel<true><<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(0, F, W, t_lo, t_hi, 0, L.N, frames, none, fi.c32,
                                                                 fi.c64, fi.G, L.w, L.w64, L.dscale, eps, out.D, out.q,
-                                                                out.flag, recheck_list, recheck_count);
+                                                                out.flag, recheck_list, recheck_count, nullptr);
   else
     align_kernel<false><<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(0, F, W, t_lo, t_hi, 0, L.N, frames, none, fi.c32,
                                                                  fi.c64, fi.G, L.w, L.w64, L.dscale, eps, out.D, out.q,
-                                                                 out.flag, recheck_list, recheck_count);
+                                                                 out.flag, recheck_list, recheck_count, nullptr);
   note_launch();
+}
+
+// resident blocks of the chunk kernel on the whole device (the grid of its frame loop)
+template <bool F64>
+unsigned align_chunk_grid() {
+  thread_local int dev = -1;
+  thread_local unsigned grid = 0;
+  int d = 0;
+  cudaGetDevice(&d);
+  if (d != dev || grid == 0) {
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, align_kernel<F64>, 32 * WARPS_PER_BLOCK, 0);
+    grid = (unsigned)std::max(1, sms * std::max(per, 1));
+    dev = d;
+  }
+  return grid;
 }
 
 void launch_align_chunk(Prec p, int t0, int t1, const void* frames, const LandmarkDev& L, FrameInfo fi,
                         int ref_index, const RefDesc& prior, double eps, AlignOut out, int* recheck_list,
-                        int* recheck_count, cudaStream_t st) {
+                        int* recheck_count, int* stop, cudaStream_t st) {
+  set_int_kernel<<<1, 1, 0, st>>>(stop, t1);
+  note_launch();
   if (t1 <= t0) return;
-  const unsigned blocks = blocks_for((size_t)(t1 - t0), WARPS_PER_BLOCK);
+  const unsigned need = blocks_for((size_t)(t1 - t0), WARPS_PER_BLOCK);
   if (p == P_F64)
-    align_kernel<true><<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(1, 0, 1, t0, t1, ref_index, L.N, frames,
-                                                                view_of(prior), fi.c32, fi.c64, fi.G, L.w, L.w64,
-                                                                L.dscale, eps, out.D, out.q, out.flag,
-                                                                recheck_list, recheck_count);
+    align_kernel<true><<<std::min(need, align_chunk_grid<true>()), 32 * WARPS_PER_BLOCK, 0, st>>>(
+        1, 0, 1, t0, t1, ref_index, L.N, frames, view_of(prior), fi.c32, fi.c64, fi.G, L.w, L.w64, L.dscale, eps,
+        out.D, out.q, out.flag, recheck_list, recheck_count, stop);
   else
-    align_kernel<false><<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(1, 0, 1, t0, t1, ref_index, L.N, frames,
-                                                                 view_of(prior), fi.c32, fi.c64, fi.G, L.w,
-                                                                 L.w64, L.dscale, eps, out.D, out.q, out.flag,
-                                                                 recheck_list, recheck_count); note_launch();
+    align_kernel<false><<<std::min(need, align_chunk_grid<false>()), 32 * WARPS_PER_BLOCK, 0, st>>>(
+        1, 0, 1, t0, t1, ref_index, L.N, frames, view_of(prior), fi.c32, fi.c64, fi.G, L.w, L.w64, L.dscale, eps,
+        out.D, out.q, out.flag, recheck_list, recheck_count, stop);
+  note_launch();
 }
 
 void launch_recheck(Prec p, int max_entries, const int* list, const int* count, int W, const void* frames,
@@ -946,10 +998,10 @@ void launch_xy_refine(Prec p, int F, const void* frames, const LandmarkDev& L, F
 
 void launch_set_int(int* p, int v, cudaStream_t st) { set_int_kernel<<<1, 1, 0, st>>>(p, v); note_launch(); }
 
-void launch_first_exceed(int t0, int t1, const uint8_t* flag, int* first, cudaStream_t st) {
+void launch_first_exceed(int t0, int t1, const uint8_t* flag, const int* stop, int* first, cudaStream_t st) {
   set_int_kernel<<<1, 1, 0, st>>>(first, t1); note_launch();
   if (t1 <= t0) return;
-  first_exceed_kernel<<<blocks_for((size_t)(t1 - t0), 256), 256, 0, st>>>(t0, t1, flag, first); note_launch();
+  first_exceed_kernel<<<blocks_for((size_t)(t1 - t0), 256), 256, 0, st>>>(t0, t1, flag, stop, first); note_launch();
 }
 
 void launch_band_scan(int F, int W, int t0, int o_init, const AlignOut band, FrameRec rec, ScanResult* res,

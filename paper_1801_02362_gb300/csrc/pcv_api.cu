@@ -31,7 +31,7 @@ struct Small {
   int approx_count;
   int recheck_count;
   int last_refresh;
-  int pad;
+  int stop;  // first frame of the current chunk that definitely exceeds eps (launch_align_chunk)
   int nl_counts[4];  // neighbour list: updates, approximate updates, frames between updates
   float4 last_c32;
   double4 last_c64;
@@ -747,12 +747,14 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
     }
     // speculative chunk of frames aligned onto the close structure `ref`
     int B = c->min_chunk;
-    if (c->gap_estimate > 0.0) B = (int)std::fmin(std::fmax((double)B, 2.0 * c->gap_estimate), 1e9);
+    // the chunk kernel stops at its first definite exceed, so a long chunk costs only the
+    // frames in flight beyond it: four times the observed gap makes a second round rare
+    if (c->gap_estimate > 0.0) B = (int)std::fmin(std::fmax((double)B, 4.0 * c->gap_estimate), 1e9);
     const int t1 = (int)std::min<long long>((long long)F, (long long)t + B);
     launch_set_int(rc, 0, st);
     {
       PROF(c, K_CHUNK);
-      launch_align_chunk(c->prec, t, t1, frames, L, fi, ref, prior, c->eps, chunk, rl, rc, st);
+      launch_align_chunk(c->prec, t, t1, frames, L, fi, ref, prior, c->eps, chunk, rl, rc, &sm->stop, st);
     }
     {
       PROF(c, K_RECHECK);
@@ -761,7 +763,7 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
     }
     {
       PROF(c, K_FIRST);
-      launch_first_exceed(t, t1, chunk.flag, &sm->first, st);
+      launch_first_exceed(t, t1, chunk.flag, &sm->stop, &sm->first, st);
     }
     pcv_status ps = sync_small(c);
     if (ps != PCV_OK) return ps;

@@ -346,20 +346,21 @@ __device__ __forceinline__ float adj_eigvec_f32(const float* A, float* q) {
       const float d = det3(m);
       cof[4 * r + c] = ((r + c) & 1) ? -d : d;
     }
-  int best = 0;
+  // column of the largest diagonal cofactor, chosen by compares (a run-time index into the
+  // array would move it to local memory)
   float bv = fabsf(cof[0]);
 #pragma unroll
-  for (int i = 1; i < 4; ++i)
-    if (fabsf(cof[5 * i]) > bv) {
-      bv = fabsf(cof[5 * i]);
-      best = i;
-    }
+  for (int i = 0; i < 4; ++i) q[i] = cof[4 * i];
+#pragma unroll
+  for (int c = 1; c < 4; ++c) {
+    const bool take = fabsf(cof[5 * c]) > bv;
+    bv = take ? fabsf(cof[5 * c]) : bv;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) q[i] = take ? cof[4 * i + c] : q[i];
+  }
   float n2 = 0.0f;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    q[i] = cof[4 * i + best];
-    n2 += q[i] * q[i];
-  }
+  for (int i = 0; i < 4; ++i) n2 += q[i] * q[i];
   if (n2 > 0.0f) {
     const float inv = rsqrtf(n2) * (q[0] < 0.0f ? -1.0f : 1.0f);
 #pragma unroll
@@ -368,48 +369,65 @@ __device__ __forceinline__ float adj_eigvec_f32(const float* A, float* q) {
   return bv;
 }
 
-// cyclic Jacobi fallback (FP32) for (nearly) degenerate top eigenvalues: top eigenvector
-static __device__ __noinline__ void jacobi_top_f32(const float* Kin, float* q) {
+// cyclic Jacobi fallback (FP32) for (nearly) degenerate top eigenvalues: top eigenvector.
+// The matrix comes by value and every inner loop is unrolled, so A and V stay in registers.
+struct Mat4f {
+  float v[16];
+};
+static __device__ __noinline__ float4 jacobi_top_f32(Mat4f Kin) {
   float A[16], V[16];
 #pragma unroll
   for (int e = 0; e < 16; ++e) {
-    A[e] = Kin[e];
+    A[e] = Kin.v[e];
     V[e] = (e % 5 == 0) ? 1.0f : 0.0f;
   }
   for (int sweep = 0; sweep < 12; ++sweep) {
     float off = 0.0f;
+#pragma unroll
     for (int i = 0; i < 4; ++i)
+#pragma unroll
       for (int j = i + 1; j < 4; ++j) off += A[4 * i + j] * A[4 * i + j];
     if (off < 1e-30f) break;
+#pragma unroll
     for (int p = 0; p < 3; ++p)
+#pragma unroll
       for (int r = p + 1; r < 4; ++r) {
         const float apr = A[4 * p + r];
-        if (apr == 0.0f) continue;
-        const float th = (A[5 * r] - A[5 * p]) / (2.0f * apr);
-        const float t = copysignf(1.0f, th) / (fabsf(th) + sqrtf(th * th + 1.0f));
-        const float c = rsqrtf(t * t + 1.0f), sn = t * c;
-        for (int k = 0; k < 4; ++k) {
-          const float akp = A[4 * k + p], akr = A[4 * k + r];
-          A[4 * k + p] = c * akp - sn * akr;
-          A[4 * k + r] = sn * akp + c * akr;
-        }
-        for (int k = 0; k < 4; ++k) {
-          const float apk = A[4 * p + k], ark = A[4 * r + k];
-          A[4 * p + k] = c * apk - sn * ark;
-          A[4 * r + k] = sn * apk + c * ark;
-        }
-        for (int k = 0; k < 4; ++k) {
-          const float vkp = V[4 * k + p], vkr = V[4 * k + r];
-          V[4 * k + p] = c * vkp - sn * vkr;
-          V[4 * k + r] = sn * vkp + c * vkr;
+        if (apr != 0.0f) {
+          const float th = (A[5 * r] - A[5 * p]) / (2.0f * apr);
+          const float t = copysignf(1.0f, th) / (fabsf(th) + sqrtf(th * th + 1.0f));
+          const float c = rsqrtf(t * t + 1.0f), sn = t * c;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float akp = A[4 * k + p], akr = A[4 * k + r];
+            A[4 * k + p] = c * akp - sn * akr;
+            A[4 * k + r] = sn * akp + c * akr;
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float apk = A[4 * p + k], ark = A[4 * r + k];
+            A[4 * p + k] = c * apk - sn * ark;
+            A[4 * r + k] = sn * apk + c * ark;
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float vkp = V[4 * k + p], vkr = V[4 * k + r];
+            V[4 * k + p] = c * vkp - sn * vkr;
+            V[4 * k + r] = sn * vkp + c * vkr;
+          }
         }
       }
   }
-  int best = 0;
-  for (int i = 1; i < 4; ++i)
-    if (A[5 * i] > A[5 * best]) best = i;
-  const float sg = V[best] < 0.0f ? -1.0f : 1.0f;
-  for (int i = 0; i < 4; ++i) q[i] = sg * V[4 * i + best];
+  float bv = A[0], q[4] = {V[0], V[4], V[8], V[12]};
+#pragma unroll
+  for (int c = 1; c < 4; ++c) {
+    const bool take = A[5 * c] > bv;
+    bv = take ? A[5 * c] : bv;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) q[i] = take ? V[4 * i + c] : q[i];
+  }
+  const float sg = q[0] < 0.0f ? -1.0f : 1.0f;
+  return make_float4(sg * q[0], sg * q[1], sg * q[2], sg * q[3]);
 }
 
 // Top eigenvector (unit quaternion, q[0] >= 0) of K(H) in FP32.  Returns false if the
@@ -452,7 +470,16 @@ __device__ __forceinline__ bool top_quat_f32(const float* Hin, float ub, float* 
   A[10] -= l;
   A[15] -= l;
   const float mag = adj_eigvec_f32(A, q);
-  if (!(mag > 1e-5f)) jacobi_top_f32(K, q);
+  if (!(mag > 1e-5f)) {
+    Mat4f kk;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) kk.v[e] = K[e];
+    const float4 r = jacobi_top_f32(kk);
+    q[0] = r.x;
+    q[1] = r.y;
+    q[2] = r.z;
+    q[3] = r.w;
+  }
   return ok;
 }
 
@@ -484,20 +511,20 @@ __device__ __forceinline__ void adj_eigvec_f64(const double* K, double lam, doub
       const double d = det3(m);
       cof[4 * r + c] = ((r + c) & 1) ? -d : d;
     }
-  int best = 0;
+  // column of the largest diagonal cofactor, chosen by compares (no run-time index)
   double bv = fabs(cof[0]);
 #pragma unroll
-  for (int i = 1; i < 4; ++i)
-    if (fabs(cof[5 * i]) > bv) {
-      bv = fabs(cof[5 * i]);
-      best = i;
-    }
+  for (int i = 0; i < 4; ++i) q[i] = cof[4 * i];
+#pragma unroll
+  for (int c = 1; c < 4; ++c) {
+    const bool take = fabs(cof[5 * c]) > bv;
+    bv = take ? fabs(cof[5 * c]) : bv;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) q[i] = take ? cof[4 * i + c] : q[i];
+  }
   double n2 = 0.0;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    q[i] = cof[4 * i + best];
-    n2 += q[i] * q[i];
-  }
+  for (int i = 0; i < 4; ++i) n2 += q[i] * q[i];
   if (!(n2 > 0.0)) {
     q[0] = 1.0;
     q[1] = q[2] = q[3] = 0.0;
@@ -653,9 +680,9 @@ __device__ __forceinline__ void adjoint_rotation_terms2(const T* H, const T* R, 
   quat_matrix(H, K);
   T q0[4];
   {
-    const T n = sqrt(q0in[0] * q0in[0] + q0in[1] * q0in[1] + q0in[2] * q0in[2] + q0in[3] * q0in[3]);
+    const T rn = T(1) / sqrt(q0in[0] * q0in[0] + q0in[1] * q0in[1] + q0in[2] * q0in[2] + q0in[3] * q0in[3]);
 #pragma unroll
-    for (int a = 0; a < 4; ++a) q0[a] = q0in[a] / n;
+    for (int a = 0; a < 4; ++a) q0[a] = q0in[a] * rn;
   }
   T l0 = 0;
 #pragma unroll
@@ -686,8 +713,9 @@ __device__ __forceinline__ void adjoint_rotation_terms2(const T* H, const T* R, 
 #pragma unroll
     for (int a = 0; a < 4; ++a) g[a] -= gq * q0[a];
   }
-  // Cholesky factor of l0 I - K + q0 q0^T, then two solves
-  T L[16];
+  // Cholesky factor of l0 I - K + q0 q0^T, then two solves (one reciprocal per diagonal
+  // entry, products instead of divisions on the serial chain)
+  T L[16], iL[4];
 #pragma unroll
   for (int e = 0; e < 16; ++e) L[e] = 0;
 #pragma unroll
@@ -697,10 +725,12 @@ __device__ __forceinline__ void adjoint_rotation_terms2(const T* H, const T* R, 
       T sum = (i == j ? l0 : T(0)) - K[4 * i + j] + q0[i] * q0[j];
 #pragma unroll
       for (int k = 0; k < j; ++k) sum -= L[4 * i + k] * L[4 * j + k];
-      if (i == j)
+      if (i == j) {
         L[4 * i + i] = sqrt(sum > T(0) ? sum : T(1e-30));
-      else
-        L[4 * i + j] = sum / L[4 * j + j];
+        iL[i] = T(1) / L[4 * i + i];
+      } else {
+        L[4 * i + j] = sum * iL[j];
+      }
     }
   }
   T pv[2][4];
@@ -712,14 +742,14 @@ __device__ __forceinline__ void adjoint_rotation_terms2(const T* H, const T* R, 
       T sum = g2[which][i];
 #pragma unroll
       for (int k = 0; k < i; ++k) sum -= L[4 * i + k] * y[k];
-      y[i] = sum / L[4 * i + i];
+      y[i] = sum * iL[i];
     }
 #pragma unroll
     for (int i = 3; i >= 0; --i) {
       T sum = y[i];
 #pragma unroll
       for (int k = i + 1; k < 4; ++k) sum -= L[4 * k + i] * pv[which][k];
-      pv[which][i] = sum / L[4 * i + i];
+      pv[which][i] = sum * iL[i];
     }
   }
 #pragma unroll

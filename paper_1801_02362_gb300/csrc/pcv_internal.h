@@ -70,10 +70,12 @@ void launch_frame_prep(Prec p, int F, const void* frames, const LandmarkDev& L, 
 void launch_align_band(Prec p, int F, int W, int t_lo, int t_hi, const void* frames, const LandmarkDev& L,
                        FrameInfo fi, double eps, AlignOut out, int* recheck_list, int* recheck_count,
                        cudaStream_t st);
-// chunk: for t in [t0, t1): D(x_t, ref) -> out[t]; ref_index >= 0 is a frame of the batch
+// chunk: for t in [t0, t1): D(x_t, ref) -> out[t]; ref_index >= 0 is a frame of the batch.
+// *stop (device int, set to t1 here) ends at the first frame that definitely exceeds eps;
+// frames past it may be left unaligned.
 void launch_align_chunk(Prec p, int t0, int t1, const void* frames, const LandmarkDev& L,
                         FrameInfo fi, int ref_index, const RefDesc& prior, double eps,
-                        AlignOut out, int* recheck_list, int* recheck_count, cudaStream_t st);
+                        AlignOut out, int* recheck_list, int* recheck_count, int* stop, cudaStream_t st);
 // FP64 re-check of the ambiguous alignments listed in `list` (entries encode slot kind)
 void launch_recheck(Prec p, int max_entries, const int* list, const int* count, int W,
                     const void* frames, const LandmarkDev& L, const RefDesc& prior, int chunk_ref,
@@ -85,8 +87,9 @@ void launch_recheck(Prec p, int max_entries, const int* list, const int* count, 
 struct FrameRec;
 void launch_xy_refine(Prec p, int F, const void* frames, const LandmarkDev& L, FrameInfo fi, const RefDesc& prior,
                       FrameRec rec, cudaStream_t st);
-// first t in [t0, t1) with chunk flag bit0 set -> *first (initialised to t1 by the kernel)
-void launch_first_exceed(int t0, int t1, const uint8_t* flag, int* first, cudaStream_t st);
+// first t in [t0, min(t1, *stop + 1)) with chunk flag bit0 set -> *first (initialised to t1;
+// stop may be null)
+void launch_first_exceed(int t0, int t1, const uint8_t* flag, const int* stop, int* first, cudaStream_t st);
 
 // per-frame decision records
 struct FrameRec {
