@@ -136,39 +136,49 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 // ---------------------------------------------------------------------------------------
 // gamma operand: for frame tile t (64 frames) and K chunk c, blocks hi | lo of 128 rows x 16
 // values (rows 0..63 gamma^s of frames 64t + r, rows 64..127 gamma^z), zero for landmarks
-// >= M and frames >= F; and Gamma^s_f, Gamma^z_f.  One warp per frame (Fp = frames rounded
-// up to 64).
+// >= M and frames >= F; and Gamma^s_f, Gamma^z_f.  One warp per 8 consecutive frames (a
+// row group of the core matrices): lane = 4 (frame in the group) + (landmark in a group of
+// 4), so every store of the warp is one whole 128-byte core matrix (Fp = frames rounded up
+// to 64).
 __global__ void gamma_split_kernel(int F, int Fp, int M, int Kp, const float* __restrict__ P,
                                    const float* __restrict__ q32, const double* __restrict__ s, float lambda,
                                    float* __restrict__ A, float* __restrict__ Gsum) {
-  const int lane = threadIdx.x & 31;
-  const int f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (f >= Fp) return;
+  const int lane = threadIdx.x & 31, rr = lane >> 2, k4 = lane & 3;
+  const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (g * 8 >= Fp) return;  // uniform over the warp
+  const int f = g * 8 + rr;
   const bool live = f < F;
   const float sf = live ? (float)s[f] : 0.0f;
   const int nck = Kp / MM_KC;
   const int t = f / MM_FRAMES, r = f % MM_FRAMES;
+  uint8_t* tileA = reinterpret_cast<uint8_t*>(A) + (size_t)t * nck * 2 * MM_A_BYTES;
+  const float* prow = P + (size_t)(live ? f : 0) * M;
   float ss = 0.0f, sz = 0.0f;
-  for (int i = lane; i < Kp; i += 32) {
+#pragma unroll 4
+  for (int i0 = 0; i0 < Kp; i0 += 4) {
+    const int i = i0 + k4;
     float gs = 0.0f, gz = 0.0f;
     if (live && i < M) {
-      const float p = P[(size_t)f * M + i];
+      const float p = prow[i];
       gz = p;
       gs = -lambda * p * (q32[i] - sf);
     }
     ss += gs;
     sz += gz;
     const int c = i / MM_KC, kk = i % MM_KC;
-    uint8_t* blk = reinterpret_cast<uint8_t*>(A) + ((size_t)t * nck + c) * 2 * MM_A_BYTES;
+    uint8_t* blk = tileA + (size_t)c * 2 * MM_A_BYTES;
     const float hs = tf32_hi(gs), hz = tf32_hi(gz);
     *reinterpret_cast<float*>(blk + canon_off(r, kk)) = hs;
     *reinterpret_cast<float*>(blk + canon_off(r + MM_FRAMES, kk)) = hz;
     *reinterpret_cast<float*>(blk + MM_A_BYTES + canon_off(r, kk)) = tf32_hi(gs - hs);
     *reinterpret_cast<float*>(blk + MM_A_BYTES + canon_off(r + MM_FRAMES, kk)) = tf32_hi(gz - hz);
   }
-  ss = warp_sum_float(ss);
-  sz = warp_sum_float(sz);
-  if (lane == 0 && live) {
+  // sums over the 4 lanes of the frame
+  ss += __shfl_xor_sync(0xffffffffu, ss, 1);
+  sz += __shfl_xor_sync(0xffffffffu, sz, 1);
+  ss += __shfl_xor_sync(0xffffffffu, ss, 2);
+  sz += __shfl_xor_sync(0xffffffffu, sz, 2);
+  if (k4 == 0 && live) {
     Gsum[2 * f] = ss;
     Gsum[2 * f + 1] = sz;
   }
@@ -440,7 +450,7 @@ MmaShape mma_shape(int F, int M, int N) {
 void launch_gamma_split(int F, const LandmarkDev& L, const MmaShape& sh, const float* P, const double* s,
                         double lambda, float* A, float* Gsum, cudaStream_t st) {
   if (F <= 0) return;
-  gamma_split_kernel<<<sh.Fp / 8, 256, 0, st>>>(F, sh.Fp, L.M, sh.Kp, P, L.q32, s, (float)lambda, A, Gsum);
+  gamma_split_kernel<<<sh.Fp / 64, 256, 0, st>>>(F, sh.Fp, L.M, sh.Kp, P, L.q32, s, (float)lambda, A, Gsum);
   note_launch();
 }
 

@@ -123,15 +123,18 @@ __global__ void materialize_landmarks_kernel(int s0, int M, int N, int N16, cons
 }
 
 // dx_k = R_xy^T (x_f - c_f) - y'(seg), f = alist[k], one row of N16 atoms per approximate
-// frame, and |dx_k|^2 in Nx[k].  Runs after materialize_landmarks (y' from Yc).
+// frame, and |dx_k|^2 in Nx[k].  Runs after materialize_landmarks (y' from Yc).  One warp
+// per frame; with VEC (N % 4 == 0 and 16-byte aligned frame rows) a lane moves 4 atoms as
+// three 16-byte loads of x and of y' and three 16-byte stores.
+template <bool VEC>
 __global__ void materialize_frames_kernel(int napp_max, const int* __restrict__ acount, const int* __restrict__ alist,
                                           const int* __restrict__ aseg, int seg_base, int N, int N16,
                                           const float* __restrict__ frames, const float4* __restrict__ c32,
                                           const double4* __restrict__ qxy, const float* __restrict__ Yc,
                                           float* __restrict__ Xr, float* __restrict__ Nx) {
-  __shared__ float red[32];
-  const int k = blockIdx.x;
-  if (k >= napp_max || k >= *acount) return;  // uniform over the block
+  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (k >= napp_max || k >= *acount) return;  // uniform over the warp
   const int f = alist[k];
   const float4 c = c32[f];
   const double4 qq = qxy[f];
@@ -142,21 +145,54 @@ __global__ void materialize_frames_kernel(int napp_max, const int* __restrict__ 
   const float* yc = Yc + (size_t)(aseg[k] - seg_base) * 3 * N;
   float* out = Xr + (size_t)k * N16 * 3;
   float nrm = 0.0f;
-  for (int j = threadIdx.x; j < N16; j += blockDim.x) {
-    float o0 = 0.0f, o1 = 0.0f, o2 = 0.0f;
-    if (j < N) {
-      const float v0 = x[3 * j] - c.x, v1 = x[3 * j + 1] - c.y, v2 = x[3 * j + 2] - c.z;
-      o0 = (R[0] * v0 + R[3] * v1 + R[6] * v2) - yc[3 * j];
-      o1 = (R[1] * v0 + R[4] * v1 + R[7] * v2) - yc[3 * j + 1];
-      o2 = (R[2] * v0 + R[5] * v1 + R[8] * v2) - yc[3 * j + 2];
+  auto atom = [&](float x0, float x1, float x2, float y0, float y1, float y2, float* o) {
+    const float v0 = x0 - c.x, v1 = x1 - c.y, v2 = x2 - c.z;
+    o[0] = (R[0] * v0 + R[3] * v1 + R[6] * v2) - y0;
+    o[1] = (R[1] * v0 + R[4] * v1 + R[7] * v2) - y1;
+    o[2] = (R[2] * v0 + R[5] * v1 + R[8] * v2) - y2;
+    nrm = fmaf(o[0], o[0], fmaf(o[1], o[1], fmaf(o[2], o[2], nrm)));
+  };
+  if (VEC) {
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    const float4* y4 = reinterpret_cast<const float4*>(yc);
+    float4* o4 = reinterpret_cast<float4*>(out);
+    for (int qd = lane; qd < N16 / 4; qd += 32) {  // atoms 4 qd .. 4 qd + 3 (all < N or all >= N)
+      float o[12];
+      if (4 * qd < N) {
+        float xv[12], yv[12];
+#pragma unroll
+        for (int h = 0; h < 3; ++h) {
+          const float4 a = x4[3 * qd + h], b = y4[3 * qd + h];
+          xv[4 * h] = a.x;
+          xv[4 * h + 1] = a.y;
+          xv[4 * h + 2] = a.z;
+          xv[4 * h + 3] = a.w;
+          yv[4 * h] = b.x;
+          yv[4 * h + 1] = b.y;
+          yv[4 * h + 2] = b.z;
+          yv[4 * h + 3] = b.w;
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+          atom(xv[3 * m], xv[3 * m + 1], xv[3 * m + 2], yv[3 * m], yv[3 * m + 1], yv[3 * m + 2], o + 3 * m);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 12; ++e) o[e] = 0.0f;
+      }
+#pragma unroll
+      for (int h = 0; h < 3; ++h) o4[3 * qd + h] = make_float4(o[4 * h], o[4 * h + 1], o[4 * h + 2], o[4 * h + 3]);
     }
-    out[3 * j] = o0;
-    out[3 * j + 1] = o1;
-    out[3 * j + 2] = o2;
-    nrm = fmaf(o0, o0, fmaf(o1, o1, fmaf(o2, o2, nrm)));
+  } else {
+    for (int j = lane; j < N16; j += 32) {
+      float o[3] = {0.0f, 0.0f, 0.0f};
+      if (j < N) atom(x[3 * j], x[3 * j + 1], x[3 * j + 2], yc[3 * j], yc[3 * j + 1], yc[3 * j + 2], o);
+      out[3 * j] = o[0];
+      out[3 * j + 1] = o[1];
+      out[3 * j + 2] = o[2];
+    }
   }
-  nrm = block_sum(nrm, red);
-  if (threadIdx.x == 0) Nx[k] = nrm;
+  nrm = warp_sum_float(nrm);
+  if (lane == 0) Nx[k] = nrm;
 }
 
 // gamma^s_fi = -lambda p_fi (q_i - s_f), gamma^z_fi = p_fi (Eqs. 5-6 differentiated), rows of
@@ -508,8 +544,17 @@ void launch_materialize_frames(int napp, const int* acount, const int* alist, co
                                const LandmarkDev& L, const void* frames, FrameInfo fi, const double4* qxy,
                                const float* Yc, float* Xr, float* Nx, cudaStream_t st) {
   if (napp <= 0) return;
-  materialize_frames_kernel<<<napp, 128, 0, st>>>(napp, acount, alist, aseg, seg_base, L.N, round_up16(L.N),
-                                                  (const float*)frames, fi.c32, qxy, Yc, Xr, Nx);
+  const bool vec = L.N % 4 == 0 && ((uintptr_t)frames % 16) == 0 && ((uintptr_t)Yc % 16) == 0 &&
+                   ((uintptr_t)Xr % 16) == 0;
+  const unsigned blocks = (unsigned)((napp + 7) / 8);  // 8 warps (frames) per block
+  if (vec)
+    materialize_frames_kernel<true><<<blocks, 256, 0, st>>>(napp, acount, alist, aseg, seg_base, L.N,
+                                                            round_up16(L.N), (const float*)frames, fi.c32, qxy, Yc,
+                                                            Xr, Nx);
+  else
+    materialize_frames_kernel<false><<<blocks, 256, 0, st>>>(napp, acount, alist, aseg, seg_base, L.N,
+                                                             round_up16(L.N), (const float*)frames, fi.c32, qxy, Yc,
+                                                             Xr, Nx);
   note_launch();
 }
 
