@@ -574,7 +574,8 @@ def run_ours(args):
     clocks.start()
     barrier(pg)
     torch.cuda.synchronize(dev)
-    launches0 = ctx.stats()["kernel_launches"]
+    st0 = ctx.stats()
+    launches0, syncs0 = st0["kernel_launches"], st0["host_syncs"]
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -698,7 +699,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args),
             "msds_per_s": msds, "exact_msds_per_step": exact_msds_step, "approx_msds_per_step": approx_msds_step,
-            "refreshes_per_step": st["refreshes_threshold"], "lambda": lam,
+            "refreshes_per_step": st["refreshes_threshold"], "fp64_rechecks_per_step": st["fp64_rechecks"],
+            "host_syncs_per_step": (st["host_syncs"] - syncs0) / args.steps, "lambda": lam,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "details": details,
         }

@@ -478,82 +478,103 @@ __global__ void xy_refine_kernel(int F, int N, const float* __restrict__ frames,
   }
 }
 
-// Full FP64 re-evaluation of D(x_t, y) from the raw FP32 coordinates: FP64 centres,
-// FP64 correlation and sums of squares, FP64 eigenvalue.  One warp per listed entry.
+// Full FP64 re-evaluation of D(x_t, y) from the raw FP32 coordinates: FP64 correlation
+// and sums of squares, FP64 eigenvalue.  One warp per listed entry.  Centres: when they
+// are weighted like the distance (no separate alignment weights) the frames' stored
+// centres c32 serve: at the exact centres sum_j w_j (x_j - c_x) = 0 = sum_j w_j (y_j - c_y),
+// so a centre error d enters G_x, G_y, H and hence D only at second order (|d|^2 sum w,
+// ~1e-13 nm^2 for FP32 centres from compensated sums).  With alignment weights w' != w
+// that first-order term does not vanish and the centres are summed in FP64 here.
 __global__ void recheck_kernel(const int* __restrict__ list, const int* __restrict__ count, int W,
                                int N, const float* __restrict__ frames, RefView prior, int chunk_ref,
                                const double* __restrict__ w64, double dscale, double eps,
                                double* bandD, uint8_t* bandFlag, double* chunkD, uint8_t* chunkFlag,
-                               unsigned long long* n_rechecks, const double* __restrict__ wc64) {
-  const int wid = warp_global();
-  if (wid >= *count) return;
+                               unsigned long long* n_rechecks, const double* __restrict__ wc64,
+                               const float4* __restrict__ c32) {
   const int lane = threadIdx.x & 31;
-  const int code = list[wid];
-  const int slot = code >> 1;
-  const bool is_chunk = code & 1;
-  int t, ref;
-  if (is_chunk) {
-    t = slot;
-    ref = chunk_ref;
-  } else {
-    t = slot / W;
-    ref = t - (slot % W + 1);
-  }
-  const float* x = frames + (size_t)t * N * 3;
-  const float* y = ref >= 0 ? frames + (size_t)ref * N * 3 : (const float*)prior.coords;
-  const double* cw = wc64 ? wc64 : w64;  // centres: alignment weights when given
-  double cx[3] = {0, 0, 0}, cy[3] = {0, 0, 0};
-  for (int j = lane; j < N; j += 32) {
-    const double wj = cw ? cw[j] : 1.0;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      cx[c] += wj * (double)x[3 * j + c];
-      cy[c] += wj * (double)y[3 * j + c];
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    cx[c] = warp_sum_double(cx[c]);
-    cy[c] = warp_sum_double(cy[c]);
-    if (!cw) {
-      cx[c] /= (double)N;
-      cy[c] /= (double)N;
-    }
-  }
-  double h[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, gx = 0.0, gy = 0.0;
-  for (int j = lane; j < N; j += 32) {
-    const double wj = w64 ? w64[j] : 1.0;
-    double u[3], v[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      u[c] = (double)y[3 * j + c] - cy[c];
-      v[c] = (double)x[3 * j + c] - cx[c];
-      gx += wj * v[c] * v[c];
-      gy += wj * u[c] * u[c];
-    }
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) h[3 * b + c] += wj * u[b] * v[c];
-  }
-#pragma unroll
-  for (int e = 0; e < 9; ++e) h[e] = warp_sum_double(h[e]);
-  gx = warp_sum_double(gx);
-  gy = warp_sum_double(gy);
-  if (lane == 0) {
-    bool ok = true;
-    const double lam = lambda_max_newton(h, 0.5 * (gx + gy), &ok);
-    double D = (gx + gy - 2.0 * lam) * dscale;
-    if (D < 0.0) D = 0.0;
-    const uint8_t fl = (uint8_t)(D > eps ? 1 : 0);
+  const int n = *count, nw = gridDim.x * (blockDim.x >> 5);
+  for (int wid = warp_global(); wid < n; wid += nw) {  // the list is short: a small grid loops over it
+    const int code = list[wid];
+    const int slot = code >> 1;
+    const bool is_chunk = code & 1;
+    int t, ref;
     if (is_chunk) {
-      chunkD[slot] = D;
-      chunkFlag[slot] = fl;
+      t = slot;
+      ref = chunk_ref;
     } else {
-      bandD[slot] = D;
-      bandFlag[slot] = fl;
+      t = slot / W;
+      ref = t - (slot % W + 1);
     }
-    atomicAdd(n_rechecks, 1ull);
+    const float* x = frames + (size_t)t * N * 3;
+    const float* y = ref >= 0 ? frames + (size_t)ref * N * 3 : (const float*)prior.coords;
+    double cx[3], cy[3];
+    if (!wc64) {
+      const float4 a = c32[t];
+      cx[0] = a.x;
+      cx[1] = a.y;
+      cx[2] = a.z;
+      if (ref >= 0) {
+        const float4 b = c32[ref];
+        cy[0] = b.x;
+        cy[1] = b.y;
+        cy[2] = b.z;
+      } else {
+        cy[0] = prior.c32.x;
+        cy[1] = prior.c32.y;
+        cy[2] = prior.c32.z;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) cx[c] = cy[c] = 0.0;
+      for (int j = lane; j < N; j += 32) {
+        const double wj = wc64[j];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          cx[c] += wj * (double)x[3 * j + c];
+          cy[c] += wj * (double)y[3 * j + c];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        cx[c] = warp_sum_double(cx[c]);
+        cy[c] = warp_sum_double(cy[c]);
+      }
+    }
+    double h[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, gx = 0.0, gy = 0.0;
+    for (int j = lane; j < N; j += 32) {
+      const double wj = w64 ? w64[j] : 1.0;
+      double u[3], v[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        u[c] = (double)y[3 * j + c] - cy[c];
+        v[c] = (double)x[3 * j + c] - cx[c];
+        gx += wj * v[c] * v[c];
+        gy += wj * u[c] * u[c];
+      }
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) h[3 * b + c] += wj * u[b] * v[c];
+    }
+#pragma unroll
+    for (int e = 0; e < 9; ++e) h[e] = warp_sum_double(h[e]);
+    gx = warp_sum_double(gx);
+    gy = warp_sum_double(gy);
+    if (lane == 0) {
+      bool ok = true;
+      const double lam = lambda_max_newton(h, 0.5 * (gx + gy), &ok);
+      double D = (gx + gy - 2.0 * lam) * dscale;
+      if (D < 0.0) D = 0.0;
+      const uint8_t fl = (uint8_t)(D > eps ? 1 : 0);
+      if (is_chunk) {
+        chunkD[slot] = D;
+        chunkFlag[slot] = fl;
+      } else {
+        bandD[slot] = D;
+        bandFlag[slot] = fl;
+      }
+      atomicAdd(n_rechecks, 1ull);
+    }
   }
 }
 
@@ -978,13 +999,16 @@ void launch_align_chunk(Prec p, int t0, int t1, const void* frames, const Landma
 }
 
 void launch_recheck(Prec p, int max_entries, const int* list, const int* count, int W, const void* frames,
-                    const LandmarkDev& L, const RefDesc& prior, int chunk_ref, double eps, AlignOut band,
-                    AlignOut chunk, unsigned long long* n_rechecks, cudaStream_t st) {
+                    const LandmarkDev& L, const float4* c32, const RefDesc& prior, int chunk_ref, double eps,
+                    AlignOut band, AlignOut chunk, unsigned long long* n_rechecks, cudaStream_t st) {
   if (p == P_F64 || max_entries <= 0) return;
-  const unsigned blocks = blocks_for((size_t)max_entries, WARPS_PER_BLOCK);
+  // the list holds the decisions within the FP32 error bound of eps, a few per chunk: a
+  // grid of at most 76 blocks whose warps loop over it (a grid sized for max_entries would
+  // spend its time starting and retiring empty blocks)
+  const unsigned blocks = std::min(blocks_for((size_t)max_entries, WARPS_PER_BLOCK), 76u);
   recheck_kernel<<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(list, count, W, L.N, (const float*)frames,
                                                           view_of(prior), chunk_ref, L.w64, L.dscale, eps, band.D,
-                                                          band.flag, chunk.D, chunk.flag, n_rechecks, L.wa64);
+                                                          band.flag, chunk.D, chunk.flag, n_rechecks, L.wa64, c32);
   note_launch();
 }
 

@@ -707,7 +707,7 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
       launch_align_band(c->prec, F, W, from, band_from, frames, L, fi, c->eps, band, rl, rc, st);
     }
     PROF(c, K_RECHECK);
-    launch_recheck(c->prec, (band_from - from) * W, rl, rc, W, frames, L, prior, -1, c->eps, band, chunk,
+    launch_recheck(c->prec, (band_from - from) * W, rl, rc, W, frames, L, fi.c32, prior, -1, c->eps, band, chunk,
                    (unsigned long long*)c->nrecheck.p, st);
     band_from = from;
   };
@@ -758,7 +758,7 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
     }
     {
       PROF(c, K_RECHECK);
-      launch_recheck(c->prec, t1 - t, rl, rc, W, frames, L, prior, ref, c->eps, band, chunk,
+      launch_recheck(c->prec, t1 - t, rl, rc, W, frames, L, fi.c32, prior, ref, c->eps, band, chunk,
                      (unsigned long long*)c->nrecheck.p, st);
     }
     {

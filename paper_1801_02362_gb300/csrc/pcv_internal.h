@@ -78,8 +78,8 @@ void launch_align_chunk(Prec p, int t0, int t1, const void* frames, const Landma
                         AlignOut out, int* recheck_list, int* recheck_count, int* stop, cudaStream_t st);
 // FP64 re-check of the ambiguous alignments listed in `list` (entries encode slot kind)
 void launch_recheck(Prec p, int max_entries, const int* list, const int* count, int W,
-                    const void* frames, const LandmarkDev& L, const RefDesc& prior, int chunk_ref,
-                    double eps, AlignOut band, AlignOut chunk, unsigned long long* n_rechecks,
+                    const void* frames, const LandmarkDev& L, const float4* c32, const RefDesc& prior,
+                    int chunk_ref, double eps, AlignOut band, AlignOut chunk, unsigned long long* n_rechecks,
                     cudaStream_t st);
 // recheck list entries: (slot << 1) | kind, kind 0 = band slot t*W + k-1, 1 = chunk slot t
 // accurate quaternions of R_xy for the approximate frames (FP32 modes; FP64 mode keeps the
