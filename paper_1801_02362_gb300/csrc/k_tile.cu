@@ -126,22 +126,48 @@ __global__ void materialize_landmarks_kernel(int s0, int M, int N, int N16, cons
 // frame, and |dx_k|^2 in Nx[k].  Runs after materialize_landmarks (y' from Yc).  One warp
 // per frame; with VEC (N % 4 == 0 and 16-byte aligned frame rows) a lane moves 4 atoms as
 // three 16-byte loads of x and of y' and three 16-byte stores.
-template <bool VEC>
+// REFINE: the accurate R_xy is formed here first (compensated FP32 correlation of x with its
+// close structure, FP32 eigen-solve; the arithmetic of the separate refinement kernel) and
+// its quaternion stored in qxy, so the frame is read once for both.
+struct RefineArgs {
+  const int* ref;           // close-structure frame of each frame (-1: the stored prior)
+  const float* prior;       // prior structure coordinates
+  float4 prior_c;           // and its centre
+  double prior_G;           // and its G
+  const double* fG;         // G of every frame
+  const float* wts;         // distance weights (null: uniform)
+};
+template <bool VEC, bool REFINE>
 __global__ void materialize_frames_kernel(int napp_max, const int* __restrict__ acount, const int* __restrict__ alist,
                                           const int* __restrict__ aseg, int seg_base, int N, int N16,
                                           const float* __restrict__ frames, const float4* __restrict__ c32,
-                                          const double4* __restrict__ qxy, const float* __restrict__ Yc,
-                                          float* __restrict__ Xr, float* __restrict__ Nx) {
+                                          double4* __restrict__ qxy, const float* __restrict__ Yc,
+                                          float* __restrict__ Xr, float* __restrict__ Nx, RefineArgs ra) {
   const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (k >= napp_max || k >= *acount) return;  // uniform over the warp
   const int f = alist[k];
   const float4 c = c32[f];
-  const double4 qq = qxy[f];
-  const float qf[4] = {(float)qq.x, (float)qq.y, (float)qq.z, (float)qq.w};
+  const float* x = frames + (size_t)f * N * 3;
+  float qf[4];
+  if (REFINE) {
+    const int ref = ra.ref[f];
+    const float* y = ref >= 0 ? frames + (size_t)ref * N * 3 : ra.prior;
+    const float4 cy = ref >= 0 ? c32[ref] : ra.prior_c;
+    float H[9];
+    warp_corr_pair_f32(N, x, c, y, cy, ra.wts, H);  // every lane holds H
+    const float Gx = (float)ra.fG[f], Gy = (float)(ref >= 0 ? ra.fG[ref] : ra.prior_G);
+    top_quat_f32(H, 0.5f * (Gx + Gy) * 1.00001f + 1e-30f, qf);
+    if (lane == 0) qxy[f] = make_double4(qf[0], qf[1], qf[2], qf[3]);
+  } else {
+    const double4 qq = qxy[f];
+    qf[0] = (float)qq.x;
+    qf[1] = (float)qq.y;
+    qf[2] = (float)qq.z;
+    qf[3] = (float)qq.w;
+  }
   float R[9];
   quat_to_rot(qf, R);
-  const float* x = frames + (size_t)f * N * 3;
   const float* yc = Yc + (size_t)(aseg[k] - seg_base) * 3 * N;
   float* out = Xr + (size_t)k * N16 * 3;
   float nrm = 0.0f;
@@ -541,20 +567,31 @@ void launch_materialize_landmarks(Prec p, int s0, int ns, const LandmarkDev& L, 
 }
 
 void launch_materialize_frames(int napp, const int* acount, const int* alist, const int* aseg, int seg_base,
-                               const LandmarkDev& L, const void* frames, FrameInfo fi, const double4* qxy,
-                               const float* Yc, float* Xr, float* Nx, cudaStream_t st) {
+                               const LandmarkDev& L, const void* frames, FrameInfo fi, double4* qxy,
+                               const float* Yc, float* Xr, float* Nx, const int* refine_ref, const RefDesc& prior,
+                               cudaStream_t st) {
   if (napp <= 0) return;
   const bool vec = L.N % 4 == 0 && ((uintptr_t)frames % 16) == 0 && ((uintptr_t)Yc % 16) == 0 &&
                    ((uintptr_t)Xr % 16) == 0;
   const unsigned blocks = (unsigned)((napp + 7) / 8);  // 8 warps (frames) per block
-  if (vec)
-    materialize_frames_kernel<true><<<blocks, 256, 0, st>>>(napp, acount, alist, aseg, seg_base, L.N,
-                                                            round_up16(L.N), (const float*)frames, fi.c32, qxy, Yc,
-                                                            Xr, Nx);
-  else
-    materialize_frames_kernel<false><<<blocks, 256, 0, st>>>(napp, acount, alist, aseg, seg_base, L.N,
-                                                             round_up16(L.N), (const float*)frames, fi.c32, qxy, Yc,
-                                                             Xr, Nx);
+  RefineArgs ra{refine_ref, (const float*)prior.coords, prior.c32, prior.G, fi.G, L.w};
+  const float* fr = (const float*)frames;
+  const int N16 = round_up16(L.N);
+  if (refine_ref) {
+    if (vec)
+      materialize_frames_kernel<true, true><<<blocks, 256, 0, st>>>(napp, acount, alist, aseg, seg_base, L.N, N16,
+                                                                    fr, fi.c32, qxy, Yc, Xr, Nx, ra);
+    else
+      materialize_frames_kernel<false, true><<<blocks, 256, 0, st>>>(napp, acount, alist, aseg, seg_base, L.N, N16,
+                                                                     fr, fi.c32, qxy, Yc, Xr, Nx, ra);
+  } else {
+    if (vec)
+      materialize_frames_kernel<true, false><<<blocks, 256, 0, st>>>(napp, acount, alist, aseg, seg_base, L.N, N16,
+                                                                     fr, fi.c32, qxy, Yc, Xr, Nx, ra);
+    else
+      materialize_frames_kernel<false, false><<<blocks, 256, 0, st>>>(napp, acount, alist, aseg, seg_base, L.N,
+                                                                      N16, fr, fi.c32, qxy, Yc, Xr, Nx, ra);
+  }
   note_launch();
 }
 

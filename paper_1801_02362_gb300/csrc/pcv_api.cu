@@ -783,10 +783,6 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
       t = t1;
     }
   }
-  {
-    PROF(c, K_XY_REFINE);
-    launch_xy_refine(c->prec, F, frames, L, fi, prior, rec, st);
-  }
   // compaction and per-segment work
   {
     PROF(c, K_COMPACT);
@@ -870,8 +866,14 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
     if (mma)
       launch_delta_split(c->prec, seg_base, nseg, L, msh, (const float*)c->Bseg.p, frames, fi,
                          (const int*)c->reflist.p, prior, (float*)c->Bmma.p, (float*)c->Yc.p, st);
+    // the accurate R_xy of the approximate frames is formed while their deviations are
+    // materialised (one read of each frame)
     launch_materialize_frames(napp, &sm->approx_count, (const int*)c->alist.p, (const int*)c->aseg.p, seg_base, L,
-                              frames, fi, rec.qxy, (const float*)c->Yc.p, (float*)c->Xr.p, (float*)c->Nx.p, st);
+                              frames, fi, rec.qxy, (const float*)c->Yc.p, (float*)c->Xr.p, (float*)c->Nx.p, rec.ref,
+                              prior, st);
+  } else {
+    PROF(c, K_XY_REFINE);
+    launch_xy_refine(c->prec, F, frames, L, fi, prior, rec, st);
   }
   // FP32 / FP16 storage: tiles of up to 16 frames sharing a list (and a close structure)
   const bool nl_tiled = nl && c->prec != P_F64;

@@ -222,10 +222,13 @@ void launch_materialize_landmarks(Prec p, int s0, int ns, const LandmarkDev& L, 
                                   FrameInfo fi, const int* refresh_list, const RefDesc& prior, float* Bm, float* Nb,
                                   float* Yc, cudaStream_t st);
 // dx_k = R_xy^T (x - c) - y' for approximate frames k < *acount (Xr), |dx_k|^2 (Nx); after
-// launch_materialize_landmarks
+// launch_materialize_landmarks.  refine_ref (the frames' close-structure index, FrameRec.ref)
+// non-null: R_xy is formed here from the frame and its close structure (prior: the stored
+// one) and its quaternion written to qxy, in place of launch_xy_refine; null: qxy is read.
 void launch_materialize_frames(int napp, const int* acount, const int* alist, const int* aseg, int seg_base,
-                               const LandmarkDev& L, const void* frames, FrameInfo fi, const double4* qxy,
-                               const float* Yc, float* Xr, float* Nx, cudaStream_t st);
+                               const LandmarkDev& L, const void* frames, FrameInfo fi, double4* qxy,
+                               const float* Yc, float* Xr, float* Nx, const int* refine_ref, const RefDesc& prior,
+                               cudaStream_t st);
 // gamma^s, gamma^z rows (round_up16(M) entries each, tile_bytes_gamma bytes per kind) from
 // the softmax weights P, and Gamma^s_f, Gamma^z_f (Gsum, 2F floats)
 void launch_gamma(int F, const LandmarkDev& L, const float* P, const double* s, double lambda, float* GS, float* GZ,
