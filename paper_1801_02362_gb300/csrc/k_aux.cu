@@ -540,6 +540,11 @@ __global__ void recheck_kernel(const int* __restrict__ list, const int* __restri
 }
 
 __global__ void set_int_kernel(int* p, int v) { *p = v; }
+__global__ void set_chunk_round_kernel(int* recheck_count, int* stop, int* first, int t1) {
+  *recheck_count = 0;
+  *stop = t1;
+  *first = t1;
+}
 
 // frames past *stop may not have been aligned by the chunk kernel: the scan ends at *stop
 __global__ void first_exceed_kernel(int t0, int t1, const uint8_t* __restrict__ flag, const int* __restrict__ stop,
@@ -681,14 +686,27 @@ __global__ void __launch_bounds__(SCAN_THREADS) compact_kernel(int F, const uint
                                                                int* refresh_list, int* refresh_count,
                                                                int* seg_of_frame, int* approx_list,
                                                                int* approx_count, int* approx_seg, int prior_seg) {
+  // 4 consecutive frames per thread, 4096 per block scan.  The approximate frames of a
+  // round are compacted into shared memory first and copied out by the whole block, so the
+  // global stores stay contiguous across the warp; seg_of_frame goes out as one 16-byte
+  // store per thread.
+  constexpr int CI = 4;
   __shared__ int s_r[32], s_a[32];
+  __shared__ int s_list[SCAN_THREADS * CI], s_seg[SCAN_THREADS * CI];
   const int tid = threadIdx.x, lane = tid & 31, wrp = tid >> 5;
   int nref = 0, napp = 0;
-  for (int base = 0; base < F; base += SCAN_THREADS) {
-    const int t = base + tid;
-    const int isr = (t < F && flag[t] != 0) ? 1 : 0;
-    const int isa = (t < F && flag[t] == 0) ? 1 : 0;
-    int r = isr, a = isa;
+  for (int base = 0; base < F; base += SCAN_THREADS * CI) {
+    const int t0 = base + tid * CI;
+    uint8_t fl[CI];
+    int cr = 0, ca = 0;
+#pragma unroll
+    for (int k = 0; k < CI; ++k) {
+      const bool in = t0 + k < F;
+      fl[k] = in ? flag[t0 + k] : (uint8_t)0;
+      cr += (in && fl[k] != 0) ? 1 : 0;
+      ca += (in && fl[k] == 0) ? 1 : 0;
+    }
+    int r = cr, a = ca;  // inclusive scans over the block
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
       const int ro = __shfl_up_sync(0xffffffffu, r, d);
@@ -722,17 +740,33 @@ __global__ void __launch_bounds__(SCAN_THREADS) compact_kernel(int F, const uint
       r += s_r[wrp - 1];
       a += s_a[wrp - 1];
     }
-    if (t < F) {
-      const int seg = prior_seg + nref + r;  // inclusive count of reassignments
-      seg_of_frame[t] = seg;
-      if (isr) refresh_list[nref + r - 1] = t;
-      if (isa) {
-        approx_list[napp + a - 1] = t;
-        approx_seg[napp + a - 1] = seg;
+    const int tot_r = s_r[31], tot_a = s_a[31];
+    int pr = nref + r - cr, pa = a - ca;  // refreshes before t0 (global), approximate (block-local)
+    int seg[CI];
+#pragma unroll
+    for (int k = 0; k < CI; ++k) {
+      const int t = t0 + k;
+      if (t < F && fl[k] != 0) refresh_list[pr++] = t;
+      seg[k] = prior_seg + pr;  // inclusive count of reassignments
+      if (t < F && fl[k] == 0) {
+        s_list[pa] = t;
+        s_seg[pa] = seg[k];
+        ++pa;
       }
     }
-    nref += s_r[31];
-    napp += s_a[31];
+    if (t0 + CI <= F)
+      *reinterpret_cast<int4*>(seg_of_frame + t0) = make_int4(seg[0], seg[1], seg[2], seg[3]);
+    else
+#pragma unroll
+      for (int k = 0; k < CI; ++k)
+        if (t0 + k < F) seg_of_frame[t0 + k] = seg[k];
+    __syncthreads();
+    for (int i = tid; i < tot_a; i += SCAN_THREADS) {
+      approx_list[napp + i] = s_list[i];
+      approx_seg[napp + i] = s_seg[i];
+    }
+    nref += tot_r;
+    napp += tot_a;
     __syncthreads();
   }
   if (tid == 0) {
@@ -944,8 +978,6 @@ unsigned align_chunk_grid() {
 void launch_align_chunk(Prec p, int t0, int t1, const void* frames, const LandmarkDev& L, FrameInfo fi,
                         int ref_index, const RefDesc& prior, double eps, AlignOut out, int* recheck_list,
                         int* recheck_count, int* stop, cudaStream_t st) {
-  set_int_kernel<<<1, 1, 0, st>>>(stop, t1);
-  note_launch();
   if (t1 <= t0) return;
   const unsigned need = blocks_for((size_t)(t1 - t0), WARPS_PER_BLOCK);
   if (p == P_F64)
@@ -983,8 +1015,12 @@ void launch_xy_refine(Prec p, int F, const void* frames, const LandmarkDev& L, F
 
 void launch_set_int(int* p, int v, cudaStream_t st) { set_int_kernel<<<1, 1, 0, st>>>(p, v); note_launch(); }
 
+void launch_chunk_round_init(int* recheck_count, int* stop, int* first, int t1, cudaStream_t st) {
+  set_chunk_round_kernel<<<1, 1, 0, st>>>(recheck_count, stop, first, t1);
+  note_launch();
+}
+
 void launch_first_exceed(int t0, int t1, const uint8_t* flag, const int* stop, int* first, cudaStream_t st) {
-  set_int_kernel<<<1, 1, 0, st>>>(first, t1); note_launch();
   if (t1 <= t0) return;
   first_exceed_kernel<<<blocks_for((size_t)(t1 - t0), 256), 256, 0, st>>>(t0, t1, flag, stop, first); note_launch();
 }

@@ -751,7 +751,7 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
     // frames in flight beyond it: four times the observed gap makes a second round rare
     if (c->gap_estimate > 0.0) B = (int)std::fmin(std::fmax((double)B, 4.0 * c->gap_estimate), 1e9);
     const int t1 = (int)std::min<long long>((long long)F, (long long)t + B);
-    launch_set_int(rc, 0, st);
+    launch_chunk_round_init(rc, &sm->stop, &sm->first, t1, st);
     {
       PROF(c, K_CHUNK);
       launch_align_chunk(c->prec, t, t1, frames, L, fi, ref, prior, c->eps, chunk, rl, rc, &sm->stop, st);

@@ -71,8 +71,8 @@ void launch_align_band(Prec p, int F, int W, int t_lo, int t_hi, const void* fra
                        FrameInfo fi, double eps, AlignOut out, int* recheck_list, int* recheck_count,
                        cudaStream_t st);
 // chunk: for t in [t0, t1): D(x_t, ref) -> out[t]; ref_index >= 0 is a frame of the batch.
-// *stop (device int, set to t1 here) ends at the first frame that definitely exceeds eps;
-// frames past it may be left unaligned.
+// *stop (device int, t1 on entry: launch_chunk_round_init) ends at the first frame that
+// definitely exceeds eps; frames past it may be left unaligned.
 void launch_align_chunk(Prec p, int t0, int t1, const void* frames, const LandmarkDev& L,
                         FrameInfo fi, int ref_index, const RefDesc& prior, double eps,
                         AlignOut out, int* recheck_list, int* recheck_count, int* stop, cudaStream_t st);
@@ -87,9 +87,11 @@ void launch_recheck(Prec p, int max_entries, const int* list, const int* count, 
 struct FrameRec;
 void launch_xy_refine(Prec p, int F, const void* frames, const LandmarkDev& L, FrameInfo fi, const RefDesc& prior,
                       FrameRec rec, cudaStream_t st);
-// first t in [t0, min(t1, *stop + 1)) with chunk flag bit0 set -> *first (initialised to t1;
-// stop may be null)
+// first t in [t0, min(t1, *stop + 1)) with chunk flag bit0 set -> *first (t1 on entry:
+// launch_chunk_round_init; stop may be null)
 void launch_first_exceed(int t0, int t1, const uint8_t* flag, const int* stop, int* first, cudaStream_t st);
+// start of a speculative chunk [.., t1): recheck count 0, stop and first t1 (one launch)
+void launch_chunk_round_init(int* recheck_count, int* stop, int* first, int t1, cudaStream_t st);
 
 // per-frame decision records
 struct FrameRec {
