@@ -34,6 +34,7 @@ __device__ __forceinline__ void frame_prep_warp_f32(int f, int N, const float* _
   const float* x = frames + (size_t)f * N * 3;
   const float* cw = wc ? wc : wts;
   float hi[3] = {0, 0, 0}, lo[3] = {0, 0, 0};
+#pragma unroll 4
   for (int j = lane; j < N; j += 32) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -58,6 +59,7 @@ __device__ __forceinline__ void frame_prep_warp_f32(int f, int N, const float* _
     cf[k] = cw ? hi[k] + lo[k] : (hi[k] + lo[k]) * invn;
   }
   float gh = 0.0f, gl = 0.0f;
+#pragma unroll 4
   for (int j = lane; j < N; j += 32) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -286,6 +288,7 @@ __device__ __forceinline__ double warp_direct_f32(int N, const float* __restrict
   float h[9];
 #pragma unroll
   for (int e = 0; e < 9; ++e) h[e] = 0.0f;
+#pragma unroll 4
   for (int j = lane; j < N; j += 32) {
     float u[3] = {y[3 * j] - cy.x, y[3 * j + 1] - cy.y, y[3 * j + 2] - cy.z};
     const float v[3] = {x[3 * j] - cx.x, x[3 * j + 1] - cx.y, x[3 * j + 2] - cx.z};
@@ -306,6 +309,7 @@ __device__ __forceinline__ double warp_direct_f32(int N, const float* __restrict
   top_quat_f32(h, (float)(0.5 * (Gx + Gy)) * 1.00001f + 1e-30f, q);
   quat_to_rot(q, R);
   float dsum = 0.0f;
+#pragma unroll 4
   for (int j = lane; j < N; j += 32) {
     const float u0 = y[3 * j] - cy.x, u1 = y[3 * j + 1] - cy.y, u2 = y[3 * j + 2] - cy.z;
     const float v0 = x[3 * j] - cx.x, v1 = x[3 * j + 1] - cx.y, v2 = x[3 * j + 2] - cx.z;

@@ -329,6 +329,7 @@ __device__ __forceinline__ void warp_corr_pair_f32(int N, const float* __restric
 #pragma unroll
   for (int e = 0; e < 9; ++e) p[e] = hi[e] = lo[e] = 0.0f;
   int cnt = 0;
+#pragma unroll 4
   for (int j = lane; j < N; j += 32) {
     float u0 = y[3 * j] - cy.x, u1 = y[3 * j + 1] - cy.y, u2 = y[3 * j + 2] - cy.z;
     const float v0 = x[3 * j] - cx.x, v1 = x[3 * j + 1] - cx.y, v2 = x[3 * j + 2] - cx.z;
