@@ -181,6 +181,16 @@ PCV_API pcv_status pcv_evaluate(pcv_ctx* ctx, int F, const void* frames, double*
 PCV_API pcv_status pcv_evaluate_host(pcv_ctx* ctx, int F, const void* frames, double* s, double* z,
                              void* dsdx, void* dzdx, double* msd, uint8_t* refreshed);
 
+/* Chunk plan of pcv_evaluate_host for F frames with the options PCV_OPT_HOST_CHUNKS = n
+ * (0: automatic, about one chunk per 16k frames, 1..8) and PCV_OPT_HOST_END_SHARE =
+ * end_share (1..100): the chunk sizes in order, first and last end_share percent of a middle
+ * one, every chunk at least 2048 frames (the number of chunks is lowered to F / 2048 when
+ * needed).  Writes min(count, cap) sizes into sizes (host array; may be NULL with cap 0) and
+ * the number of chunks into *count.  Pure host computation, no device needed.
+ * Errors: PCV_EINVAL (F < 0, n outside 0..64, end_share outside 1..100, count NULL, or
+ * sizes NULL with cap > 0). */
+PCV_API pcv_status pcv_host_chunk_plan(int F, int n, int end_share, int* sizes, int cap, int* count);
+
 /* Chain rule for a scalar loss L(s, z): out[t] = g_s[t] * dsdx[t] + g_z[t] * dzdx[t] for
  * every frame t (device buffers; element type of dsdx/dzdx/out as in pcv_evaluate; g_s,
  * g_z device doubles, either may be NULL for zero). */

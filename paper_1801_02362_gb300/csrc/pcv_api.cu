@@ -1345,6 +1345,19 @@ std::vector<int> host_chunk_plan(int F, int n, int end_share) {
   return plan;
 }
 
+pcv_status pcv_host_chunk_plan(int F, int n, int end_share, int* sizes, int cap, int* count) {
+  if (F < 0 || n < 0 || n > 64 || end_share < 1 || end_share > 100 || !count || (cap > 0 && !sizes))
+    return fail(nullptr, PCV_EINVAL, "bad chunk-plan arguments");
+  if (F == 0) {
+    *count = 0;
+    return PCV_OK;
+  }
+  const std::vector<int> plan = host_chunk_plan(F, n, end_share);
+  *count = (int)plan.size();
+  for (int k = 0; k < (int)plan.size() && k < cap; ++k) sizes[k] = plan[k];
+  return PCV_OK;
+}
+
 pcv_status pcv_evaluate_host(pcv_ctx* c, int F, const void* frames, double* s, double* z, void* dsdx, void* dzdx,
                              double* msd, uint8_t* refreshed) {
   if (!c) return fail(nullptr, PCV_EINVAL, "NULL context");

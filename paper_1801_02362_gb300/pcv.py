@@ -62,6 +62,7 @@ SIGNATURES = {
     "pcv_set_neighbor_list": (_i, [_vp, _i, _i]),
     "pcv_evaluate": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "pcv_evaluate_host": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "pcv_host_chunk_plan": (_i, [_i, _i, _i, _vp, _i, _vp]),
     "pcv_combine_grad": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp]),
     "pcv_reset_close_state": (_i, [_vp]),
     "pcv_save_state": (_i, [_vp, _vp, ctypes.POINTER(ctypes.c_size_t)]),
@@ -174,6 +175,15 @@ def pcv_set_option(ctx, key: int, value: int):
 def pcv_evaluate(ctx, F: int, frames_ptr, s_ptr, z_ptr, dsdx_ptr=None, dzdx_ptr=None, msd_ptr=None,
                  refreshed_ptr=None):
     _check(ctx, load().pcv_evaluate(ctx, F, frames_ptr, s_ptr, z_ptr, dsdx_ptr, dzdx_ptr, msd_ptr, refreshed_ptr))
+
+
+def pcv_host_chunk_plan(F: int, chunks: int = 0, end_share: int = 25) -> list[int]:
+    """Chunk sizes pcv_evaluate_host uses for F frames with these options (host only)."""
+    count = ctypes.c_int()
+    _check(None, load().pcv_host_chunk_plan(F, chunks, end_share, None, 0, ctypes.byref(count)))
+    sizes = (ctypes.c_int * max(count.value, 1))()
+    _check(None, load().pcv_host_chunk_plan(F, chunks, end_share, sizes, count.value, ctypes.byref(count)))
+    return list(sizes[:count.value])
 
 
 def pcv_evaluate_host(ctx, F: int, frames_ptr, s_ptr, z_ptr, dsdx_ptr=None, dzdx_ptr=None, msd_ptr=None,

@@ -65,3 +65,30 @@ def test_new_entry_points_reject_null_without_gpu(lib):
     h = ctypes.c_void_p()
     assert lib.pcv_metad_create(ctypes.byref(h), 0, None, 1.0, 0.0, 1.0, 1, 10) == pcv.PCV_EINVAL
     assert h.value is None
+
+
+def test_host_chunk_plan(lib):
+    """The chunk plan of pcv_evaluate_host (host logic, no device): the chunks cover the
+    batch in order, each holds at least 2048 frames, the count follows the option (or about
+    one chunk per 16k frames, at most 8), and the first and last chunk hold end_share percent
+    of a middle one unless the 2048-frame floor lifts them."""
+    for F in (1, 2047, 4096, 9000, 16384, 16385, 100000, 1000003):
+        for n, e in ((0, 25), (1, 25), (2, 25), (3, 100), (4, 1), (7, 25), (8, 100), (64, 50)):
+            plan = pcv.pcv_host_chunk_plan(F, n, e)
+            want_n = n if n > 0 else min(8, max(1, -(-F // 16384)))
+            want_n = min(want_n, max(1, F // 2048))
+            assert len(plan) == want_n, (F, n, e, plan)
+            assert sum(plan) == F and all(x > 0 for x in plan)
+            if len(plan) > 1:
+                assert min(plan) >= 2048, (F, n, e, plan)
+            if len(plan) >= 3:
+                mid = plan[1]
+                assert max(plan[1:-1]) - min(plan[1:-1]) <= 1
+                assert plan[0] == plan[-1]
+                assert plan[0] == max(2048, int(F / ((len(plan) - 2) + 2 * e / 100) * e / 100)), (F, n, e, plan)
+                assert plan[0] <= mid + 1
+    assert pcv.pcv_host_chunk_plan(0) == []
+    for bad in ((-1, 0, 25), (10, -1, 25), (10, 65, 25), (10, 0, 0), (10, 0, 101)):
+        with pytest.raises(pcv.PcvError) as err:
+            pcv.pcv_host_chunk_plan(*bad)
+        assert err.value.status == pcv.PCV_EINVAL
