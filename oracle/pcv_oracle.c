@@ -105,7 +105,11 @@ void orc_quat_to_rot(const double* q, double* R) {
 /* Cyclic Jacobi eigen-solver for a symmetric 4x4 matrix.  On return evals[0..3] are
  * sorted in descending order and column k of evecs (evecs[4*i + k]) is the unit
  * eigenvector of evals[k].  Returns the number of sweeps, or -1 if 60 sweeps did not
- * bring the off-diagonal part to zero. */
+ * bring the off-diagonal norm below 1e-15 of the diagonal's.  That stopping rule sits at the
+ * FP64 rounding floor: the eigenvalues are then exact to ~1e-30 relative (second order in
+ * the off-diagonal part), and the eigenvectors are exact up to mixing within a nearly
+ * degenerate eigenspace, where every vector is optimal.  A stricter rule cannot be met when
+ * the top eigenvalue is (nearly) double, e.g. for collinear structures. */
 int orc_jacobi4(const double* Kin, double* evals, double* evecs) {
   double A[4][4], V[4][4];
   for (int i = 0; i < 4; ++i)
@@ -120,7 +124,7 @@ int orc_jacobi4(const double* Kin, double* evals, double* evecs) {
       diag += A[i][i] * A[i][i];
       for (int j = i + 1; j < 4; ++j) off += A[i][j] * A[i][j];
     }
-    if (off == 0.0 || off <= 1e-36 * diag) {
+    if (off == 0.0 || off <= 1e-30 * diag) {
       converged = 1;
       break;
     }

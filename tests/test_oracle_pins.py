@@ -55,6 +55,40 @@ def test_align_matches_kabsch_svd(n):
         assert np.max(np.abs(r["R"] @ r["R"].T - np.eye(3))) < 1e-12
 
 
+def collinear(rng, n, scale=1.0):
+    """n atoms on a random line through a random point, unevenly spaced."""
+    d = rng.normal(size=3)
+    d /= np.linalg.norm(d)
+    t = np.sort(rng.normal(size=n)) * scale
+    return rng.normal(size=3) + t[:, None] * d[None, :]
+
+
+def test_degenerate_top_eigenvalue_collinear():
+    """Collinear structures: H has rank one, the top eigenvalue of K is double and the
+    optimal rotation is not unique (any turn about the line).  D is unique: the oracle's
+    equals the SVD superposition's and the one-dimensional closed form
+    sum w s'^2 + sum w t'^2 - 2 |sum w s' t'| (s', t' the centred positions along each
+    line), and the rotation the oracle returns attains it."""
+    rng = np.random.default_rng(77)
+    for trial in range(12):
+        n = 3 + trial
+        x, a = collinear(rng, n), collinear(rng, n, scale=1.3)
+        w = None if trial % 2 else rng.uniform(0.3, 2.0, size=n)
+        r = oracle.align(x, a, w)
+        Dk, _ = kabsch(x, a, w)
+        ww = np.full(n, 1.0 / n) if w is None else w / w.sum()
+        xc, ac = x - ww @ x, a - ww @ a
+        s1 = xc @ (xc[-1] - xc[0]) / np.linalg.norm(xc[-1] - xc[0])
+        t1 = ac @ (ac[-1] - ac[0]) / np.linalg.norm(ac[-1] - ac[0])
+        Dc = float(ww @ s1 ** 2 + ww @ t1 ** 2 - 2.0 * abs(ww @ (s1 * t1)))
+        scale = r["Gx"] + r["Ga"]
+        assert abs(r["D"] - Dk) <= 1e-12 * scale
+        assert abs(r["D"] - Dc) <= 1e-12 * scale
+        assert (r["evals"][0] - r["evals"][1]) <= 1e-9 * abs(r["evals"][0])  # degenerate
+        Dr = float(ww @ np.sum((xc - ac @ r["R"].T) ** 2, axis=1))
+        assert abs(Dr - r["D"]) <= 1e-12 * scale
+
+
 @pytest.mark.parametrize("n", [3, 4, 5])
 def test_align_brute_force_rotation_search(n):
     """The oracle's D is the minimum over SO(3): no rotation of a coarse grid plus local
