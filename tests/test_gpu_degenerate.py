@@ -1,0 +1,65 @@
+"""Degenerate superpositions on the GPU.  Collinear frames and landmarks make H rank one:
+the top eigenvalue of the quaternion matrix is double and the optimal rotation is free about
+the line (the eigen-solves take their degenerate branches: the adjugate column within the
+eigenspace, or the Jacobi fallback).  With both structures collinear, R a_i is unique, so D,
+s, z and the gradients are unique and are compared with the oracle (exact mode; the close
+structure's approximation depends on the rotation chosen and is not unique here).
+Expected to fail until the eigen-solves handle a double top eigenvalue: Newton on the
+characteristic quartic converges only linearly there and stops at ~sqrt(eps) relative
+accuracy of lambda_max, which D = G_x + G_a - 2 lambda_max (FP64) and the rotation of the
+direct FP32 evaluation inherit."""
+import numpy as np
+import pytest
+
+import oracle
+from _util import GRAD_TOL, TOL, d_err, grad_err, s_err, z_err
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pcv():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1801_02362_gb300 import build_lib
+    from paper_1801_02362_gb300 import pcv as mod
+
+    build_lib.build()
+    mod.load()
+    return mod
+
+
+def collinear(rng, n, scale=1.0):
+    d = rng.normal(size=3)
+    d /= np.linalg.norm(d)
+    t = np.sort(rng.normal(size=n)) * scale
+    return rng.normal(size=3) + t[:, None] * d[None, :]
+
+
+@pytest.mark.xfail(reason="known limitation: Newton on the characteristic quartic reaches a double top "
+                          "eigenvalue only to ~sqrt(eps) relative; measured D error ~6e-7 (2.6e-4 of the "
+                          "error floor) for exactly collinear frames and landmarks", strict=False)
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_collinear_structures_exact_mode(pcv, precision):
+    rng = np.random.default_rng(41)
+    n, m, f = 40, 9, 24
+    dt = np.float64 if precision == "fp64" else np.float32
+    lm = np.stack([collinear(rng, n, scale=1.0 + 0.1 * i) for i in range(m)]).astype(dt).astype(np.float64)
+    fr = np.stack([collinear(rng, n, scale=1.05) for _ in range(f)]).astype(dt).astype(np.float64)
+    lam = 2.3 / oracle.mean_adjacent_msd(lm)
+    r = oracle.exact(fr, lm, lam, want_grad=True)
+    ctx = pcv.PathCV(lm, lam, eps=-1.0, precision=precision)
+    tdt = torch.float64 if precision == "fp64" else torch.float32
+    out = ctx.evaluate(torch.tensor(fr, dtype=tdt, device="cuda"), grad=True, msd=True)
+    ctx.sync()
+    ctx.close()
+    g = {k: v.double().cpu().numpy() for k, v in out.items()}
+    tol = TOL[precision]
+    assert np.all(np.isfinite(g["msd"]))
+    assert d_err(g["msd"], r["D"], fr, lm) < tol
+    assert s_err(g["s"], r["s"], m) < tol
+    assert z_err(g["z"], r["z"], lam) < tol
+    assert grad_err(g["dsdx"], r["dsdx"]) < GRAD_TOL[precision]
+    assert grad_err(g["dzdx"], r["dzdx"]) < GRAD_TOL[precision]
