@@ -505,6 +505,12 @@ __device__ __forceinline__ bool top_quat_f32(const float* Hin, float ub, float* 
     }
     prev = a;
   }
+  // P'(l) = prod_k (l - lambda_k) over the other eigenvalues: below 0.002 l^3 the top
+  // eigenvalue is (nearly) double (relative gap below ~5e-4).  Newton then converges only
+  // linearly and l carries an error of ~sqrt(u) relative, which the adjugate column
+  // inherits; the Jacobi iteration does not degrade there.
+  const float dpl = fmaf(fmaf(4.0f * l, l, 2.0f * c2), l, c1);
+  const bool near_double = !(dpl > 0.002f * l * l * l);
   float A[16];
 #pragma unroll
   for (int e = 0; e < 16; ++e) A[e] = K[e];
@@ -512,7 +518,7 @@ __device__ __forceinline__ bool top_quat_f32(const float* Hin, float ub, float* 
   A[5] -= l;
   A[10] -= l;
   A[15] -= l;
-  const float mag = adj_eigvec_f32(A, q);
+  const float mag = near_double ? 0.0f : adj_eigvec_f32(A, q);
   if (!(mag > 1e-5f)) {
     Mat4f kk;
 #pragma unroll
