@@ -55,6 +55,33 @@ def test_align_matches_kabsch_svd(n):
         assert np.max(np.abs(r["R"] @ r["R"].T - np.eye(3))) < 1e-12
 
 
+def test_mirror_images_are_not_superimposable():
+    """A mirror image (det H < 0) cannot be superimposed by a rotation: the oracle's D is the
+    SVD superposition's with the reflection fix, strictly positive for a chiral structure,
+    reached by a proper rotation, and never below the (improper) orthogonal Procrustes
+    minimum, which is zero."""
+    rng = np.random.default_rng(91)
+    for n in (4, 7, 30):
+        a = rng.normal(size=(n, 3))
+        M = np.diag([1.0, 1.0, -1.0])
+        x = (a @ M) @ synth.random_rotation(rng).T + 2.0
+        r = oracle.align(x, a)
+        Dk, Rk = kabsch(x, a)
+        scale = r["Gx"] + r["Ga"]
+        assert abs(r["D"] - Dk) <= 1e-12 * scale
+        assert abs(np.linalg.det(r["R"]) - 1.0) < 1e-12
+        assert r["D"] > 1e-3 * scale  # chiral: no rotation maps it onto its mirror image
+        # the improper orthogonal fit (reflections allowed) is exact
+        w = np.full(n, 1.0 / n)
+        xc, ac = x - w @ x, a - w @ a
+        U, S, Vt = np.linalg.svd((ac * w[:, None]).T @ xc)
+        Q = Vt.T @ U.T
+        assert abs(np.linalg.det(Q) + 1.0) < 1e-9
+        assert float(w @ np.sum((xc - ac @ Q.T) ** 2, axis=1)) < 1e-20 * scale + 1e-24
+        # and the proper rotation's D is the paper's formula G_x + G_a - 2 lambda_max
+        assert abs(r["D_formula"] - r["D"]) <= 1e-12 * scale
+
+
 def collinear(rng, n, scale=1.0):
     """n atoms on a random line through a random point, unevenly spaced."""
     d = rng.normal(size=3)
