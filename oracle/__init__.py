@@ -5,7 +5,7 @@ reference legs of ``bench.py`` are the only users.  The CUDA library never impor
 links this package, and this package never touches the CUDA library.
 
 See ``pcv_oracle.c`` for the paper passages each routine follows.  ``build()`` compiles
-the C source with gcc (OpenMP over frames in the exact driver).
+the C source with gcc (OpenMP over the frames of the exact-mode loop).
 """
 from __future__ import annotations
 
