@@ -104,30 +104,6 @@ __device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
   return d;
 }
-__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
-  f2 d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
-  f2 d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-// (hi, lo) += v element-wise without losing the rounding error of the addition (TwoSum)
-__device__ __forceinline__ void f2_two_sum_acc(f2& hi, f2& lo, f2 v) {
-  const f2 s = f2_add(hi, v);
-  const f2 bp = f2_sub(s, hi);
-  const f2 err = f2_add(f2_sub(hi, f2_sub(s, bp)), f2_sub(v, bp));
-  hi = s;
-  lo = f2_add(lo, err);
-}
-
-// ---------------------------------------------------------------------------------------
-// storage conversions
-__device__ __forceinline__ float to_f32(float v) { return v; }
-__device__ __forceinline__ float to_f32(__half v) { return __half2float(v); }
-__device__ __forceinline__ float to_f32(double v) { return (float)v; }
 
 // ---------------------------------------------------------------------------------------
 // Quaternion matrix.  For the correlation H[b][c] = sum_j w_j a_jb x_jc of a structure a
@@ -245,60 +221,6 @@ __device__ __forceinline__ double lambda_max_newton(const double* H, double ub, 
   return l;
 }
 
-// Unit eigenvector of K for eigenvalue lam (FP32 accuracy): the adjugate of A = K - lam I
-// has rank one, proportional to q q^T; take its column with the largest diagonal entry.
-__device__ __forceinline__ void adj_eigvec(const double* K, double lam, float* q) {
-  float A[16];
-#pragma unroll
-  for (int e = 0; e < 16; ++e) A[e] = (float)K[e];
-  // subtract lam on the diagonal in FP64 before rounding (the diagonal can cancel)
-  A[0] = (float)(K[0] - lam);
-  A[5] = (float)(K[5] - lam);
-  A[10] = (float)(K[10] - lam);
-  A[15] = (float)(K[15] - lam);
-  // 2x2 minors of rows 2,3 and rows 0,1 (columns i<j)
-  // cofactor C[r][c] = (-1)^(r+c) det(A without row r, column c)
-  float cof[16];
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      float m[9];
-      int k = 0;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        if (i == r) continue;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          if (j == c) continue;
-          m[k++] = A[4 * i + j];
-        }
-      }
-      const float d = m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6]) +
-                      m[2] * (m[3] * m[7] - m[4] * m[6]);
-      cof[4 * r + c] = ((r + c) & 1) ? -d : d;
-    }
-  int best = 0;
-  float bv = fabsf(cof[0]);
-#pragma unroll
-  for (int i = 1; i < 4; ++i)
-    if (fabsf(cof[5 * i]) > bv) {
-      bv = fabsf(cof[5 * i]);
-      best = i;
-    }
-  float v[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) v[i] = cof[4 * i + best];
-  float n2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
-  if (!(n2 > 0.0f)) {
-    v[0] = 1.0f;
-    v[1] = v[2] = v[3] = 0.0f;
-    n2 = 1.0f;
-  }
-  const float inv = rsqrtf(n2) * (v[0] < 0.0f ? -1.0f : 1.0f);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) q[i] = v[i] * inv;
-}
 
 // Rotation of a unit quaternion q = (s, v): R = (s^2 - |v|^2) I + 2 v v^T + 2 s [v]_x,
 // divided by |q|^2 so that rounding in q does not spoil orthogonality to first order.
