@@ -346,6 +346,33 @@ def test_close_refresh_flags_brute_force():
                 y = fr[t]
 
 
+def test_close_distance_matches_an_independent_superposition():
+    """Eq. (close_dist) recomputed with SVD superpositions: for an approximate frame x with
+    close structure y, D~(x, a_i) = sum_j w_j |R_xy^T (x_j - c_x) - R_{a_i y} (a_ij - c_a)|^2,
+    R_xy fitting y onto x and R_{a_i y} fitting a_i onto y."""
+    lm, fr, lam = _close_problem(noise=0.02, f=30)
+    r = oracle.close(fr, lm, lam, 0.003)
+    flags = r["refreshed"]
+    assert 0 < int((flags == 0).sum())
+    n = fr.shape[1]
+    w = np.full(n, 1.0 / n)
+    y = fr[0]
+    checked = 0
+    for t in range(fr.shape[0]):
+        if flags[t] != 0:
+            y = fr[t]
+            continue
+        _, Rxy = kabsch(fr[t], y)
+        xp = (fr[t] - w @ fr[t]) @ Rxy  # R_xy^T (x - c_x), row-wise
+        for i in range(lm.shape[0]):
+            _, Ray = kabsch(y, lm[i])
+            b = (lm[i] - w @ lm[i]) @ Ray.T
+            Dt = float(w @ np.sum((xp - b) ** 2, axis=1))
+            assert abs(Dt - r["D"][t, i]) <= 1e-11 * (1.0 + Dt), (t, i)
+            checked += 1
+    assert checked > 0
+
+
 def test_close_equals_exact_at_refresh_and_dominates_elsewhere():
     lm, fr, lam = _close_problem(noise=0.02, f=40)
     ex = oracle.exact(fr, lm, lam)
