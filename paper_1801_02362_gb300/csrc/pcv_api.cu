@@ -1330,17 +1330,13 @@ std::vector<int> host_chunk_plan(int F, int n, int end_share) {
   if (n <= 0) n = std::min(8, std::max(1, (F + 16383) / 16384));
   n = std::min(n, std::max(1, F / 2048));
   if (n <= 1) return {F};
+  if (n == 2) return {F / 2, F - F / 2};  // no middle chunk to scale the ends by
   const double we = end_share / 100.0;
-  const double unit = F / ((n - 2) + 2.0 * we);
+  const double unit = F / ((n - 2) + 2.0 * we);  // a middle chunk
   const int e = std::max(2048, (int)(unit * we));
   std::vector<int> plan(n, 0);
   plan[0] = plan[n - 1] = e;
   const int rest = F - 2 * e, mid = n - 2;
-  if (mid == 0) {
-    plan[0] = F / 2;
-    plan[1] = F - F / 2;
-    return plan;
-  }
   for (int k = 0; k < mid; ++k) plan[1 + k] = rest / mid + (k < rest % mid ? 1 : 0);
   return plan;
 }
