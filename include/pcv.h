@@ -370,8 +370,9 @@ PCV_API pcv_status pcv_evaluate_exact_noalloc(int F, int M, int N, const float* 
  * and their derivatives that turns them into a bias potential and a bias force.
  *
  * A hill of height `height` and widths sigma_s, sigma_z (in s and z units) is deposited at
- * (s_t, z_t) at every step t whose index is a multiple of `stride` (tau_G).  The bias of a
- * step sums the hills of the steps before it:
+ * (s_t, z_t) at the steps t' = tau_G, 2 tau_G, ... (tau_G = `stride`; steps are numbered
+ * from 0, so the first hill lands at step tau_G).  The bias of a step sums the hills of the
+ * steps before it:
  *   V_t = sum_k height exp(-(s_t - s_k)^2 / (2 sigma_s^2) - (z_t - z_k)^2 / (2 sigma_z^2)),
  * and its force is F_t = -dV_t/dx = -(dV/ds ds/dx + dV/dz dz/dx).  Steps are counted from
  * creation (or pcv_metad_set_hills) across calls; each call evaluates F consecutive steps.

@@ -241,8 +241,9 @@ class MetadState:
 
 
 def metad(s, z, w, sigma_s, sigma_z, stride, state: MetadState | None = None, dsdx=None, dzdx=None):
-    """Bias V of each frame (hills of earlier steps) and force -dV/dx; deposits hills every
-    `stride` steps at (s_t, z_t) after frame t is evaluated."""
+    """Bias V of each frame (hills of earlier steps) and force -dV/dx; after frame t is
+    evaluated a hill is deposited at (s_t, z_t) when the step index t (counted from 0 across
+    calls) is a positive multiple of `stride`: Eq. (vbias) sums over t' = tau_G, 2 tau_G, ..."""
     s, z = _f64(s), _f64(z)
     f = s.shape[0]
     if state is None:

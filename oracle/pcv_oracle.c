@@ -739,12 +739,14 @@ void orc_hills_value(int n_hills, const double* hills, double w, double sigma_s,
 }
 
 /* Metadynamics over F time-ordered frames with path CVs s, z and their derivatives (N x 3
- * per frame, optional).  Frame t sees the hills deposited at earlier steps; after it is
- * evaluated, a hill is deposited at (s_t, z_t) when its step index (state[1]) is a multiple
- * of the stride tau_G (Eq. vbias: hills every tau_G steps, the bias of a step summing the
- * hills of the steps before it).  Outputs V (F), and force = -dV/dx = -(dV/ds ds/dx + dV/dz
- * dz/dx) (F x N x 3, optional).  hills: capacity cap pairs (s_k, z_k); state[0] = hills
- * held, state[1] = steps done.  Returns ORC_EINVAL when the capacity would be exceeded. */
+ * per frame, optional).  Eq. (vbias) sums over the deposition times t' = tau_G, 2 tau_G, ...
+ * that lie before t: steps are numbered from 0 (state[1] = steps done), a hill is deposited
+ * at (s_t, z_t) after step t is evaluated when t is a positive multiple of the stride tau_G,
+ * and step t sees the hills of the steps t' < t.  The first hill therefore lands at step
+ * tau_G and the bias is zero up to and including that step.  Outputs V (F), and force =
+ * -dV/dx = -(dV/ds ds/dx + dV/dz dz/dx) (F x N x 3, optional).  hills: capacity cap pairs
+ * (s_k, z_k); state[0] = hills held.  Returns ORC_EINVAL when the capacity would be
+ * exceeded. */
 int orc_metad(int f, int n, const double* s, const double* z, const double* dsdx, const double* dzdx, double w,
               double sigma_s, double sigma_z, int stride, int cap, double* hills, int64_t* state, double* V,
               double* force) {
@@ -755,7 +757,7 @@ int orc_metad(int f, int n, const double* s, const double* z, const double* dsdx
     if (force && dsdx && dzdx)
       for (int e = 0; e < 3 * n; ++e)
         force[(size_t)t * 3 * n + e] = -(dVds * dsdx[(size_t)t * 3 * n + e] + dVdz * dzdx[(size_t)t * 3 * n + e]);
-    if (state[1] % stride == 0) {
+    if (state[1] > 0 && state[1] % stride == 0) {
       if (state[0] >= cap) return ORC_EINVAL;
       hills[2 * state[0]] = s[t];
       hills[2 * state[0] + 1] = z[t];

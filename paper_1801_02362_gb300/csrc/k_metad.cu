@@ -4,7 +4,8 @@
 // CV values; the bias of a step is the sum of the hills of the steps before it, and the
 // bias force is its coordinate derivative through the CVs (Eq. vbias, Section 2).  The
 // batched form evaluates F consecutive steps at once: this call's hills are known from its
-// own s and z (deposited at the steps whose index is a multiple of tau_G), so step t sums
+// own s and z (deposited at the steps t' = tau_G, 2 tau_G, ... of Eq. vbias: step indices
+// counted from 0 that are positive multiples of tau_G), so step t sums
 // the hills held before the call plus this call's hills of steps before t -- a prefix of
 // one hill array.  Kernels:
 //   metad_deposit_kernel  appends this call's hills (s_t, z_t);
@@ -61,8 +62,9 @@ pcv_status mfail(pcv_metad* m, pcv_status st, const char* fmt, ...) {
 
 // first step of the call that deposits a hill, and how many of the call's F steps do
 void deposits(int64_t step0, int stride, int F, int* t0, int* nd) {
-  const int64_t r = step0 % stride;
-  *t0 = (int)(r == 0 ? 0 : stride - r);
+  // the smallest positive multiple of the stride at or after step0 (step 0 deposits nothing)
+  const int64_t first = step0 == 0 ? (int64_t)stride : ((step0 + stride - 1) / stride) * stride;
+  *t0 = (int)(first - step0);
   *nd = *t0 < F ? (F - 1 - *t0) / stride + 1 : 0;
 }
 

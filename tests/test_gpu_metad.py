@@ -105,13 +105,15 @@ def _state(hills0, steps):
 
 def test_metad_capacity_and_arguments(pcv):
     mt = pcv.Metad(1.0, 0.1, 0.1, 1, max_hills=10)
-    s = torch.zeros(11, dtype=torch.float64, device="cuda")
+    s = torch.zeros(12, dtype=torch.float64, device="cuda")
     with pytest.raises(pcv.PcvError) as e:
-        mt.apply(s, s)
+        mt.apply(s, s)  # steps 1..11 would deposit 11 hills
     assert e.value.status == pcv.PCV_EINVAL
-    out = mt.apply(s[:10], s[:10])  # exactly fills the capacity
+    out = mt.apply(s[:11], s[:11])  # steps 1..10 deposit: exactly fills the capacity
     assert mt.hills()[0].shape == (10, 2)
-    assert float(out["bias"][0]) == 0.0 and abs(float(out["bias"][9]) - 9.0) < 1e-6
+    # no hill before step 1 is evaluated; step t >= 1 sees the hills of steps 1..t-1
+    assert float(out["bias"][0]) == 0.0 and float(out["bias"][1]) == 0.0
+    assert abs(float(out["bias"][10]) - 9.0) < 1e-6
     mt.close()
     with pytest.raises(pcv.PcvError):
         pcv.Metad(1.0, 0.0, 0.1, 1)
@@ -134,9 +136,9 @@ def test_path_cv_to_bias_chain(pcv):
     V = b["bias"].cpu().numpy()
     # first-order bound: |dV/ds| |ds| + |dV/dz| |dz| summed over the hills (each moved too)
     bound = np.zeros(len(V))
-    hs = gs[::stride]
+    hs = gs[stride::stride]
     for t in range(len(V)):
-        k = np.arange(0, t, stride)
+        k = np.arange(stride, t, stride)  # deposition steps t' = tau_G, 2 tau_G, ... below t
         if len(k) == 0:
             continue
         d_s = gs[t] - r["s"][t] - (gs[k] - r["s"][k])

@@ -33,8 +33,9 @@ def test_hills_value_and_derivatives():
 
 
 def test_deposition_schedule_and_split_calls():
-    """A hill every `stride` steps at (s_t, z_t), deposited after step t is evaluated: the bias
-    of step t sums the hills of the steps t' < t with t' a multiple of the stride."""
+    """Eq. (vbias) sums over the deposition times t' = tau_G, 2 tau_G, ... with t' < t, the
+    hill of time t' sitting at (s(t'), z(t')).  The expected bias below enumerates exactly
+    those times, k * tau_G for k = 1, 2, ..., and stops below t; steps are numbered from 0."""
     rng = np.random.default_rng(2)
     f, stride = 50, 7
     s = np.cumsum(rng.normal(size=f)) * 0.3 + 5.0
@@ -42,10 +43,19 @@ def test_deposition_schedule_and_split_calls():
     w, ss, sz = 0.9, 0.5, 0.004
     r = oracle.metad(s, z, w, ss, sz, stride)
     for t in range(f):
-        steps = [u for u in range(t) if u % stride == 0]
-        expect = _gauss_sum([[s[u], z[u]] for u in steps], w, ss, sz, s[t], z[t]) if steps else 0.0
+        times = []
+        k = 1
+        while k * stride < t:
+            times.append(k * stride)
+            k += 1
+        expect = _gauss_sum([[s[u], z[u]] for u in times], w, ss, sz, s[t], z[t]) if times else 0.0
         assert abs(r["V"][t] - expect) < 1e-13 * max(1.0, expect)
-    assert r["state"].n_hills == len(range(0, f, stride))
+    # no hill acts before the first deposition time has passed: V = 0 for t <= tau_G
+    assert np.all(r["V"][:stride + 1] == 0.0) and r["V"][stride + 1] > 0.0
+    # the run deposits at tau_G, 2 tau_G, ... up to its last step f - 1
+    assert r["state"].n_hills == (f - 1) // stride
+    np.testing.assert_array_equal(r["state"].hills[:r["state"].n_hills],
+                                  np.stack([s[stride::stride], z[stride::stride]], axis=1))
     st = oracle.MetadState()
     a = oracle.metad(s[:23], z[:23], w, ss, sz, stride, state=st)
     b = oracle.metad(s[23:], z[23:], w, ss, sz, stride, state=st)
