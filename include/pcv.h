@@ -245,10 +245,21 @@ enum {
   PCV_OPT_HOST_CHUNKS = 8,  /* pcv_evaluate_host: number of chunks the batch is split into
                               so that copies overlap evaluation (0 = automatic, default;
                               1 = no overlap; at most 64)                               */
-  PCV_OPT_HOST_END_SHARE = 9 /* pcv_evaluate_host: size of the first and the last chunk in
+  PCV_OPT_HOST_END_SHARE = 9, /* pcv_evaluate_host: size of the first and the last chunk in
                               percent of a middle chunk (1..100; default 25): a small first
                               chunk starts the evaluation early and a small last chunk
                               shortens the copy-out that follows it                     */
+  PCV_OPT_NEWTON_CAP = 10,  /* iteration cap of the Newton eigen-solves in the exact pair
+                              kernels (1..60, default 60).  A pair that reaches the cap sets
+                              the status word: pcv_sync then returns PCV_ENOCONV.  Lower
+                              values exist to exercise that report.                      */
+  PCV_OPT_WAIT_CYCLES = 11  /* clock budget (SM cycles) of each bounded wait inside the
+                              tensor-core kernels (0 = default, 4e9, about 2 s at the maximum
+                              clock; else 1..4e9).  A wait that runs out sets the status
+                              word, the kernel waits for its own copies and MMAs within the
+                              default budget, frees its tensor memory and returns; pcv_sync
+                              then returns PCV_ETIMEOUT.  Small values exist to exercise
+                              that report.                                                */
 };
 PCV_API pcv_status pcv_set_option(pcv_ctx* ctx, int key, int64_t value);
 
@@ -360,7 +371,10 @@ PCV_API pcv_status pcv_shard_unpack_host(int precision, int F, int N, double lam
  *     overlap on the GPU (different streams, threads or processes on the same device)
  *     race and must be serialised by the caller;
  *   - the call waits for its own stream and reports PCV_ENOCONV if an eigen-solve hit its
- *     iteration cap; other errors: PCV_EINVAL, PCV_ECUDA. */
+ *     iteration cap; other errors: PCV_EINVAL, PCV_ECUDA;
+ *   - the coordinates are not checked for NaN or infinity (pcv_set_landmarks checks its
+ *     landmarks; here they arrive in device memory): non-finite inputs give non-finite or
+ *     meaningless outputs, with no error status. */
 #define PCV_NOALLOC_SCRATCH_BYTES (16u << 20)
 PCV_API pcv_status pcv_evaluate_exact_noalloc(int F, int M, int N, const float* frames, const float* landmarks,
                                               const double* q, double lambda, double* s, double* z, double* msd,

@@ -258,13 +258,10 @@ __device__ __forceinline__ void finish_alignment(const double* H, double Gx, dou
                                                  double eps, bool amb_check, double* outD, double4* outQ,
                                                  uint8_t* outFlag, bool* amb_out) {
   bool ok = true;
-  const double lam = lambda_max_newton(H, 0.5 * (Gx + Gy), &ok);
+  double q[4];
+  const double lam = top_eig_f64(H, 0.5 * (Gx + Gy), &ok, q);
   double D = (Gx + Gy - 2.0 * lam) * dscale;
   if (D < 0.0) D = 0.0;
-  double K[16];
-  quat_matrix(H, K);
-  double q[4];
-  adj_eigvec_f64(K, lam, q);
   *outD = D;
   *outQ = make_double4(q[0], q[1], q[2], q[3]);
   // Worst-case error of the compensated FP32 correlation: chunks of 16 products are
@@ -527,7 +524,7 @@ __global__ void recheck_kernel(const int* __restrict__ list, const int* __restri
     gy = warp_sum_double(gy);
     if (lane == 0) {
       bool ok = true;
-      const double lam = lambda_max_newton(h, 0.5 * (gx + gy), &ok);
+      const double lam = top_eig_f64(h, 0.5 * (gx + gy), &ok, nullptr);
       double D = (gx + gy - 2.0 * lam) * dscale;
       if (D < 0.0) D = 0.0;
       const uint8_t fl = (uint8_t)(D > eps ? 1 : 0);

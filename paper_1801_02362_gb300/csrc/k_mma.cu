@@ -41,7 +41,9 @@ constexpr int MM_THREADS = 128;
 constexpr int MM_STAGES = 2;   // two CTAs per SM: one's epilogue overlaps the other's MMAs
 constexpr int MM_TMEM_COLS = 256;
 constexpr int MM_A_BYTES = MM_ROWS * MM_KC * 4;  // one operand part (hi or lo) of one K chunk
-constexpr long long MM_WAIT_CYCLES = 4000000000LL;  // about 2 s at the maximum SM clock
+constexpr long long MM_WAIT_CYCLES = 4000000000LL;  // about 2 s at the maximum SM clock: the
+                                                    // budget of the waits for copies and MMAs
+                                                    // already issued after a failure
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -100,8 +102,8 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
       : "memory");
 }
 
-// bounded wait for the phase with the given parity; false after the clock budget
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+// bounded wait for the phase with the given parity; false after `budget` clock cycles
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long budget = MM_WAIT_CYCLES) {
   const long long t0 = clock64();
   while (true) {
     uint32_t done;
@@ -112,7 +114,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
         : "r"(mbar), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > MM_WAIT_CYCLES) return false;
+    if (clock64() - t0 > budget) return false;
   }
 }
 
@@ -243,6 +245,7 @@ struct MmaArgs {
   const int* seg_of_frame;
   float *gs, *gz;
   unsigned* status;
+  long long wait_cycles;  // budget of each wait of the pipeline (the context's option)
 };
 
 __global__ void __launch_bounds__(MM_THREADS, 2) adjoint_beta_mma(MmaArgs p) {
@@ -313,7 +316,8 @@ __global__ void __launch_bounds__(MM_THREADS, 2) adjoint_beta_mma(MmaArgs p) {
       if (lane == 0) {  // producer
         for (int c = 0; c < nck; ++c) {
           const int g = g0 + c, st = g % MM_STAGES;
-          if (g >= MM_STAGES && !mbar_wait(smem_u32(&empty[st]), (uint32_t)((g / MM_STAGES - 1) & 1))) {
+          if (g >= MM_STAGES &&
+              !mbar_wait(smem_u32(&empty[st]), (uint32_t)((g / MM_STAGES - 1) & 1), p.wait_cycles)) {
             s_fail = 1;
             break;
           }
@@ -329,7 +333,7 @@ __global__ void __launch_bounds__(MM_THREADS, 2) adjoint_beta_mma(MmaArgs p) {
       if (lane == 0) {  // MMA issuer
         for (int c = 0; c < nck; ++c) {
           const int g = g0 + c, st = g % MM_STAGES;
-          if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((g / MM_STAGES) & 1))) {
+          if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((g / MM_STAGES) & 1), p.wait_cycles)) {
             s_fail = 1;
             break;
           }
@@ -352,7 +356,7 @@ __global__ void __launch_bounds__(MM_THREADS, 2) adjoint_beta_mma(MmaArgs p) {
       __syncwarp();
     }
     // all warps: wait for the run's MMAs, then the epilogue beta = D + Gamma_f y'
-    const bool ok = mbar_wait(smem_u32(&done), (uint32_t)(run & 1));
+    const bool ok = mbar_wait(smem_u32(&done), (uint32_t)(run & 1), p.wait_cycles);
     if (!ok) s_fail = 1;
     __syncthreads();
     if (s_fail) {
@@ -409,12 +413,11 @@ __global__ void __launch_bounds__(MM_THREADS, 2) adjoint_beta_mma(MmaArgs p) {
   }
   if (s_fail) {
     // Copies and MMAs already issued still land in this CTA's memory: wait for them, within
-    // the same budget, before the tensor memory is released.  The extra commit arrives once
-    // every MMA issued so far is done; the producer waits for the last copy of each stage.
-    if (tid == 0) {
-      atomicOr(p.status, STATUS_TIMEOUT);
-      mma_commit(smem_u32(&done));
-    }
+    // the full budget MM_WAIT_CYCLES, before the tensor memory is released.  The MMA issuer
+    // (thread 0) committed `done` after its last MMA of the failed run, whether its loop
+    // ended or broke off, so that phase completes once every MMA issued is done; the
+    // producer (thread 32) waits for the last copy into each stage.
+    if (tid == 0) atomicOr(p.status, STATUS_TIMEOUT);
     if (tid == 32) {
       const int last = s_issued;
       for (int g = std::max(0, last - MM_STAGES); g < last; ++g)
@@ -491,6 +494,7 @@ void launch_adjoint_beta_mma(int F, const LandmarkDev& L, const MmaShape& sh, in
   a.gs = gs;
   a.gz = gz;
   a.status = status;
+  a.wait_cycles = L.wait_cycles;
   const size_t smem = (size_t)MM_STAGES * (2 * MM_A_BYTES + 2 * MM_BN_MAX * MM_KC * 4);
   cudaFuncSetAttribute(adjoint_beta_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int tiles = sh.Fp / MM_FRAMES;

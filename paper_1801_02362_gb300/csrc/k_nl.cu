@@ -327,13 +327,12 @@ nl_exact_f64(const int* __restrict__ nlist, const int* __restrict__ counts, cons
     if (lane == 0) {
       const double Ga = lG[i];
       bool ok = true;
-      const double lam = lambda_max_newton(h, 0.5 * (Gx + Ga), &ok);
+      double q[4];
+      const double lam = top_eig_f64(h, 0.5 * (Gx + Ga), &ok, Rnl ? q : nullptr);
       double d = (Gx + Ga - 2.0 * lam) * dscale;
       row[i] = d < 0.0 ? 0.0 : d;
       if (Rnl) {
-        double K[16], q[4], Rm[9];
-        quat_matrix(h, K);
-        adj_eigvec_f64(K, lam, q);
+        double Rm[9];
         quat_to_rot(q, Rm);
         double* dst = Rnl + ((size_t)f * Mnl + r) * 9;
 #pragma unroll

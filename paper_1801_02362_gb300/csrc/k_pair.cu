@@ -179,7 +179,7 @@ __device__ __forceinline__ void exact_tile_f32(int rows, const int* __restrict__
                                                const int* __restrict__ cols = nullptr, int ncol = 0,
                                                const double4* __restrict__ qxy = nullptr,
                                                const float* __restrict__ Bseg = nullptr,
-                                               const int* __restrict__ segof = nullptr) {
+                                               const int* __restrict__ segof = nullptr, int cap = 60) {
   constexpr int TF = EX_TF, TM = EX_TM, KC = 32;
   constexpr int PF = TF + 2, PM = TM + 2;
   __shared__ __align__(16) float Xs[KC * 3][PF];
@@ -260,7 +260,7 @@ __device__ __forceinline__ void exact_tile_f32(int rows, const int* __restrict__
       if (f >= 0 && (cols ? ci < ncol : ci < M)) {
         const int i = cols ? cols[ci] : ci;
         const float ub = (float)(0.5 * (fG[f] + lG[i])) * 1.00001f + 1e-30f;
-        all_ok &= top_quat_f32(h[u][v], ub, q);
+        all_ok &= top_quat_f32(h[u][v], ub, q, cap);
       }
       quat_to_rot(q, R[u][v]);
     }
@@ -327,9 +327,9 @@ exact_pair_f32(int rows, const int* __restrict__ row_frame, const float* __restr
                const float4* __restrict__ c32, const double* __restrict__ fG, const LT* __restrict__ lm,
                const float* __restrict__ lmoff, const double* __restrict__ lG, const float* __restrict__ wts, int M,
                int N, double dscale, float* __restrict__ Dout, float* __restrict__ Rout,
-               unsigned* __restrict__ status) {
+               unsigned* __restrict__ status, int cap) {
   exact_tile_f32<LT>(rows, row_frame, frames, c32, fG, lm, lmoff, lG, wts, M, N, dscale, Dout, Rout, status,
-                     blockIdx.y * EX_TF, blockIdx.x * EX_TM);
+                     blockIdx.y * EX_TF, blockIdx.x * EX_TM, nullptr, 0, nullptr, nullptr, nullptr, cap);
 }
 
 // Many instances in one persistent launch: CTA b takes tiles b, b + grid, ...
@@ -376,12 +376,15 @@ approx_rows_f32(const int* __restrict__ row_frame, const int* __restrict__ count
 }
 
 // FP64 mode: one pass, FP64 correlation, FP64 eigenvalue and D = G_x + G_a - 2 lambda_max
-// (FP64 sums carry ~1e-16 relative error, far below the cancellation's needs).
+// (FP64 sums carry ~1e-16 relative error, far below the cancellation's needs).  A pair whose
+// top eigenvalue is (nearly) double (near_double_f64) gets D = -1 as a mark and is redone by
+// exact_redo_f64 with the Jacobi iteration, which keeps the Jacobi code out of this tile's
+// registers.
 __global__ void __launch_bounds__(EX_THREADS, 3)
 exact_pair_f64(int rows, const int* __restrict__ row_frame, const double* __restrict__ frames,
                const double4* __restrict__ c64, const double* __restrict__ fG, const double* __restrict__ lm,
                const double* __restrict__ lG, const double* __restrict__ wts, int M, int N, double dscale,
-               double* __restrict__ Dout, double* __restrict__ Rout, unsigned* __restrict__ status) {
+               double* __restrict__ Dout, double* __restrict__ Rout, unsigned* __restrict__ status, int cap) {
   const float* lmoff = nullptr;  // FP64 storage has no block offsets
   constexpr int TF = EX_TF, TM = EX_TM, KC = 16;
   constexpr int PF = TF + 2, PM = TM + 2;
@@ -440,7 +443,13 @@ exact_pair_f64(int rows, const int* __restrict__ row_frame, const double* __rest
       if (f < 0 || i >= M) continue;
       const double Gx = fG[f], Ga = lG[i];
       bool ok = true;
-      const double lam = lambda_max_newton(h[u][v], 0.5 * (Gx + Ga), &ok);
+      double dp = 0.0;
+      const double ub = 0.5 * (Gx + Ga);
+      const double lam = lambda_max_newton(h[u][v], ub, &ok, &dp, cap);
+      if (near_double_f64(dp, ub)) {
+        Dout[(size_t)f * M + i] = -1.0;  // redone by exact_redo_f64
+        continue;
+      }
       double D = (Gx + Ga - 2.0 * lam) * dscale;
       if (D < 0.0) D = 0.0;
       Dout[(size_t)f * M + i] = D;
@@ -455,6 +464,72 @@ exact_pair_f64(int rows, const int* __restrict__ row_frame, const double* __rest
       }
       if (!ok) atomicOr(status, STATUS_NOCONV);
     }
+}
+
+// The pairs exact_pair_f64 marked with D = -1 (a (nearly) double top eigenvalue): the
+// correlation is summed again, one warp per pair in FP64, and the top eigenpair comes from
+// the Jacobi iteration.  Each warp scans 32 consecutive (row, landmark) entries at a time;
+// marked pairs are rare, so the scan of rows x M values is the usual cost.
+constexpr int REDO_THREADS = 256;
+__global__ void __launch_bounds__(REDO_THREADS)
+exact_redo_f64(int rows, const int* __restrict__ row_frame, const double* __restrict__ frames,
+               const double4* __restrict__ c64, const double* __restrict__ fG, const double* __restrict__ lm,
+               const double* __restrict__ lG, const double* __restrict__ wts, int M, int N, double dscale,
+               double* __restrict__ Dout, double* __restrict__ Rout, unsigned* __restrict__ status) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const long long total = (long long)rows * M;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long base = warp * 32; base < total; base += nwarps * 32) {
+    const long long e = base + lane;
+    int r = 0, i = 0, f = -1;
+    bool mark = false;
+    if (e < total) {
+      r = (int)(e / M);
+      i = (int)(e - (long long)r * M);
+      f = row_frame ? row_frame[r] : r;
+      mark = f >= 0 && Dout[(size_t)f * M + i] < 0.0;
+    }
+    unsigned bal = __ballot_sync(full, mark);
+    while (bal) {
+      const int src = __ffs(bal) - 1;
+      bal &= bal - 1;
+      const int rr = __shfl_sync(full, r, src), ii = __shfl_sync(full, i, src), ff = __shfl_sync(full, f, src);
+      const double* x = frames + (size_t)ff * N * 3;
+      const double* a = lm + (size_t)ii * N * 3;
+      const double4 c = c64[ff];
+      double h[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) h[k] = 0.0;
+      for (int j = lane; j < N; j += 32) {
+        const double wj = wts ? wts[j] : 1.0;
+        const double xv[3] = {wj * (x[3 * j] - c.x), wj * (x[3 * j + 1] - c.y), wj * (x[3 * j + 2] - c.z)};
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+          for (int cc = 0; cc < 3; ++cc) h[3 * b + cc] = fma(a[3 * j + b], xv[cc], h[3 * b + cc]);
+      }
+#pragma unroll
+      for (int k = 0; k < 9; ++k) h[k] = warp_sum_double(h[k]);
+      if (lane == 0) {
+        Mat4d km;
+        quat_matrix(h, km.v);
+        const TopEig4d ev = jacobi_top_f64(km);
+        double D = (fG[ff] + lG[ii] - 2.0 * ev.lam) * dscale;
+        if (D < 0.0) D = 0.0;
+        Dout[(size_t)ff * M + ii] = D;
+        if (Rout) {
+          double Rm[9];
+          quat_to_rot(ev.q, Rm);
+          double* dst = Rout + ((size_t)rr * M + ii) * 9;
+#pragma unroll
+          for (int k = 0; k < 9; ++k) dst[k] = Rm[k];
+        }
+        if (!ev.ok) atomicOr(status, STATUS_NOCONV);
+      }
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -859,19 +934,28 @@ void launch_exact_pairs(Prec p, int rows, const int* row_frame, const int* rows_
     case P_F64:
       exact_pair_f64<<<grid, EX_THREADS, 0, st>>>(rows, row_frame, (const double*)frames, fi.c64, fi.G,
                                                   (const double*)L.coords, L.G, L.w64, L.M, L.N, L.dscale,
-                                                  (double*)D, (double*)Rout, status); note_launch();
+                                                  (double*)D, (double*)Rout, status, L.newton_cap); note_launch();
+      {
+        const long long warps = ((long long)rows * L.M + 31) / 32;
+        const int blocks = (int)std::min<long long>((warps + REDO_THREADS / 32 - 1) / (REDO_THREADS / 32), 152 * 8);
+        exact_redo_f64<<<blocks, REDO_THREADS, 0, st>>>(rows, row_frame, (const double*)frames, fi.c64, fi.G,
+                                                         (const double*)L.coords, L.G, L.w64, L.M, L.N, L.dscale,
+                                                         (double*)D, (double*)Rout, status); note_launch();
+      }
       break;
     case P_F32:
       exact_pair_f32<float><<<grid, EX_THREADS, 0, st>>>(rows, row_frame, (const float*)frames, fi.c32, fi.G,
                                                          (const float*)L.coords, L.off, L.G, L.w, L.M, L.N,
                                                          L.dscale,
-                                                         (float*)D, (float*)Rout, status); note_launch();
+                                                         (float*)D, (float*)Rout, status, L.newton_cap);
+      note_launch();
       break;
     case P_F16:
       exact_pair_f32<__half><<<grid, EX_THREADS, 0, st>>>(rows, row_frame, (const float*)frames, fi.c32, fi.G,
                                                           (const __half*)L.coords, L.off, L.G, L.w, L.M, L.N,
                                                           L.dscale,
-                                                          (float*)D, (float*)Rout, status); note_launch();
+                                                          (float*)D, (float*)Rout, status, L.newton_cap);
+      note_launch();
       break;
   }
 }

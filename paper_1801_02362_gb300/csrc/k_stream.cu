@@ -75,7 +75,8 @@ __global__ void __launch_bounds__(ST_THREADS)
 exact_stream_f32(int rows, const int* __restrict__ row_frame, const float* __restrict__ frames,
                  const float4* __restrict__ c32, const double* __restrict__ fG, const LT* __restrict__ lm,
                  const float* __restrict__ lmoff, const double* __restrict__ lG, const float* __restrict__ wts, int M, int N, double dscale,
-                 bool aligned, float* __restrict__ Dout, float* __restrict__ Rout, unsigned* __restrict__ status) {
+                 bool aligned, float* __restrict__ Dout, float* __restrict__ Rout, unsigned* __restrict__ status,
+                 int cap) {
   extern __shared__ __align__(16) unsigned char stream_sm[];
   LT* As = reinterpret_cast<LT*>(stream_sm);
   constexpr int K = STREAM_FRAMES * 9;
@@ -121,7 +122,7 @@ exact_stream_f32(int rows, const int* __restrict__ row_frame, const float* __res
 #pragma unroll
     for (int e = 0; e < 9; ++e) H[e] = red[32 * K + 9 * r + e];
     const float ub = (float)(0.5 * (fG[s_f[r]] + lG[i])) * 1.00001f + 1e-30f;
-    if (!top_quat_f32(H, ub, q)) atomicOr(status, STATUS_NOCONV);
+    if (!top_quat_f32(H, ub, q, cap)) atomicOr(status, STATUS_NOCONV);
     quat_to_rot(q, R);
 #pragma unroll
     for (int e = 0; e < 9; ++e) s_R[r][e] = R[e];
@@ -406,12 +407,14 @@ void launch_exact_stream(Prec p, int rows, const int* row_frame, const void* fra
     allow_smem(exact_stream_f32<__half>, smem);
     exact_stream_f32<__half><<<L.M, ST_THREADS, smem, st>>>(rows, row_frame, (const float*)frames, fi.c32, fi.G,
                                                             (const __half*)L.coords, L.off, L.G, L.w, L.M, L.N, L.dscale,
-                                                            aligned, (float*)D, (float*)Rout, status);
+                                                            aligned, (float*)D, (float*)Rout, status,
+                                                            L.newton_cap);
   } else {
     allow_smem(exact_stream_f32<float>, smem);
     exact_stream_f32<float><<<L.M, ST_THREADS, smem, st>>>(rows, row_frame, (const float*)frames, fi.c32, fi.G,
                                                            (const float*)L.coords, L.off, L.G, L.w, L.M, L.N, L.dscale,
-                                                           aligned, (float*)D, (float*)Rout, status);
+                                                           aligned, (float*)D, (float*)Rout, status,
+                                                           L.newton_cap);
   }
   note_launch();
 }

@@ -90,6 +90,8 @@ void note_launch(int n) { t_launches += n; }
 
 struct pcv_ctx {
   int device = 0;
+  int newton_cap = 60;                  // PCV_OPT_NEWTON_CAP
+  long long wait_cycles = 4000000000LL;  // PCV_OPT_WAIT_CYCLES
   cudaStream_t stream = nullptr;
   Prec prec = P_F32;
   // landmarks
@@ -250,6 +252,8 @@ LandmarkDev lm_view(const pcv_ctx* c) {
   L.off = c->prec == P_F16 ? (const float*)c->lmoff.p : nullptr;
   L.wa = c->split_w ? (const float*)c->wa32.p : nullptr;
   L.wa64 = c->split_w ? (const double*)c->wa64.p : nullptr;
+  L.newton_cap = c->newton_cap;
+  L.wait_cycles = c->wait_cycles;
   return L;
 }
 
@@ -394,6 +398,14 @@ pcv_status pcv_set_option(pcv_ctx* c, int key, int64_t value) {
     case PCV_OPT_HOST_END_SHARE:
       if (value < 1 || value > 100) return fail(c, PCV_EINVAL, "host end share must be in 1..100");
       c->host_end_share = (int)value;
+      return PCV_OK;
+    case PCV_OPT_NEWTON_CAP:
+      if (value < 1 || value > 60) return fail(c, PCV_EINVAL, "Newton cap must be in 1..60");
+      c->newton_cap = (int)value;
+      return PCV_OK;
+    case PCV_OPT_WAIT_CYCLES:
+      if (value < 0 || value > 4000000000LL) return fail(c, PCV_EINVAL, "wait budget must be in 0..4e9 cycles");
+      c->wait_cycles = value == 0 ? 4000000000LL : (long long)value;
       return PCV_OK;
     case PCV_OPT_EXACT_TILE:
     case PCV_OPT_APPROX_TILE:

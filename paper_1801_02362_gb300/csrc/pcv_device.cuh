@@ -174,8 +174,11 @@ __device__ __forceinline__ void char_poly(const T* H, const T* K, T& c2, T& c1, 
 // FP32 iterations first (cheap); the FP64 iterations restart slightly above the FP32
 // estimate (by 4e-6 ub, well above its rounding error) so that they also approach from
 // above, and stop once a step is below 1e-13 ub.
-// Returns lambda_max; sets *ok = false if the iteration caps were reached.
-__device__ __forceinline__ double lambda_max_newton(const double* H, double ub, bool* ok) {
+// Returns lambda_max; sets *ok = false if the iteration caps were reached.  dp_out (optional)
+// receives P'(l) of the last iteration, which tells a (nearly) double root (near_double_f64).
+// cap: iterations of the FP64 phase (the FP32 phase takes at most 40).
+__device__ __forceinline__ double lambda_max_newton(const double* H, double ub, bool* ok,
+                                                    double* dp_out = nullptr, int cap = 60) {
   double K[16];
   quat_matrix(H, K);
   double c2, c1, c0;
@@ -198,11 +201,12 @@ __device__ __forceinline__ double lambda_max_newton(const double* H, double ub, 
   if (!(l <= ub) || !(l == l)) l = ub;
   const double tol = 1e-13 * fabs(ub) + 1e-300;
   *ok = false;
-  double prev = 1.0e300;
-  for (int it = 0; it < 60; ++it) {
+  double prev = 1.0e300, dp_last = 0.0;
+  for (int it = 0; it < cap; ++it) {
     const double l2 = l * l;
     const double p = fma(fma(l2 + c2, l, c1), l, c0);
     const double dp = fma(fma(4.0 * l, l, 2.0 * c2), l, c1);
+    dp_last = dp;
     if (!(dp > 0.0)) {
       *ok = true;  // at (or numerically on) the root
       break;
@@ -218,8 +222,15 @@ __device__ __forceinline__ double lambda_max_newton(const double* H, double ub, 
     }
     prev = a;
   }
+  if (dp_out) *dp_out = dp_last;
   return l;
 }
+
+// P'(l) = prod_k (l - lambda_k) over the other three eigenvalues.  The rounding of P near its
+// top root moves l by about 10 u ub^4 / P'(l) (u = 2^-53); D = G_x + G_a - 2 l must stay
+// within 1e-9 of 1e-3 (G_x + G_a) = 2e-3 ub, so P'(l) must exceed ~1e-3 ub^3.  Below that the
+// top eigenvalue is (nearly) double and the Jacobi iteration takes over.
+__device__ __forceinline__ bool near_double_f64(double dp, double ub) { return !(dp > 1e-3 * ub * ub * ub); }
 
 
 // Rotation of a unit quaternion q = (s, v): R = (s^2 - |v|^2) I + 2 v v^T + 2 s [v]_x,
@@ -396,8 +407,8 @@ static __device__ __noinline__ float4 jacobi_top_f32(Mat4f Kin) {
 }
 
 // Top eigenvector (unit quaternion, q[0] >= 0) of K(H) in FP32.  Returns false if the
-// Newton iteration hit its cap (the result is still usable).
-__device__ __forceinline__ bool top_quat_f32(const float* Hin, float ub, float* q) {
+// Newton iteration hit its cap of `cap` iterations (the result is still usable).
+__device__ __forceinline__ bool top_quat_f32(const float* Hin, float ub, float* q, int cap = 60) {
   const float sc = 1.0f / ub;
   float H[9];
 #pragma unroll
@@ -409,7 +420,7 @@ __device__ __forceinline__ bool top_quat_f32(const float* Hin, float ub, float* 
   float l = 1.0f;
   bool ok = false;
   float prev = 3.0e38f;
-  for (int it = 0; it < 60; ++it) {
+  for (int it = 0; it < cap; ++it) {
     const float p = fmaf(fmaf(fmaf(l, l, c2), l, c1), l, c0);
     const float dp = fmaf(fmaf(4.0f * l, l, 2.0f * c2), l, c1);
     if (!(dp > 0.0f)) {
@@ -504,6 +515,112 @@ __device__ __forceinline__ void adj_eigvec_f64(const double* K, double lam, doub
   const double inv = (q[0] < 0.0 ? -1.0 : 1.0) / sqrt(n2);
 #pragma unroll
   for (int i = 0; i < 4; ++i) q[i] *= inv;
+}
+
+// FP64 cyclic Jacobi for the symmetric 4x4 K: the top eigenvalue and its unit eigenvector
+// (q[0] >= 0), for (nearly) double top eigenvalues, where Newton on the characteristic
+// quartic converges only linearly and the adjugate column is ill-conditioned.  Jacobi
+// rotations keep the eigenvalues accurate to ~u |K|_F whatever the gap.  Stops when the
+// off-diagonal mass is below 1e-32 of |K|_F^2; ok = 0 if 30 sweeps do not get there.
+// The matrix comes by value and the function is not inlined, so the callers' registers do
+// not grow with it.
+struct Mat4d {
+  double v[16];
+};
+struct TopEig4d {
+  double lam;
+  double q[4];
+  int ok;
+};
+static __device__ __noinline__ TopEig4d jacobi_top_f64(Mat4d Kin) {
+  double A[16], V[16], fro = 0.0;
+#pragma unroll
+  for (int e = 0; e < 16; ++e) {
+    A[e] = Kin.v[e];
+    V[e] = (e % 5 == 0) ? 1.0 : 0.0;
+    fro += A[e] * A[e];
+  }
+  TopEig4d out;
+  out.ok = 0;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    double off = 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = i + 1; j < 4; ++j) off += A[4 * i + j] * A[4 * i + j];
+    if (!(off > 1e-32 * fro)) {
+      out.ok = 1;
+      break;
+    }
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+      for (int r = p + 1; r < 4; ++r) {
+        const double apr = A[4 * p + r];
+        if (apr != 0.0) {
+          const double th = (A[5 * r] - A[5 * p]) / (2.0 * apr);
+          const double t = copysign(1.0, th) / (fabs(th) + sqrt(th * th + 1.0));
+          const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const double akp = A[4 * k + p], akr = A[4 * k + r];
+            A[4 * k + p] = c * akp - sn * akr;
+            A[4 * k + r] = sn * akp + c * akr;
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const double apk = A[4 * p + k], ark = A[4 * r + k];
+            A[4 * p + k] = c * apk - sn * ark;
+            A[4 * r + k] = sn * apk + c * ark;
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const double vkp = V[4 * k + p], vkr = V[4 * k + r];
+            V[4 * k + p] = c * vkp - sn * vkr;
+            V[4 * k + r] = sn * vkp + c * vkr;
+          }
+        }
+      }
+  }
+  double bv = A[0], q[4] = {V[0], V[4], V[8], V[12]};
+#pragma unroll
+  for (int c = 1; c < 4; ++c) {
+    const bool take = A[5 * c] > bv;
+    bv = take ? A[5 * c] : bv;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) q[i] = take ? V[4 * i + c] : q[i];
+  }
+  const double sg = q[0] < 0.0 ? -1.0 : 1.0;
+  out.lam = bv;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) out.q[i] = sg * q[i];
+  return out;
+}
+
+// Top eigenpair of K(H) in FP64 for one pair: Newton on the characteristic quartic from the
+// upper bound ub and (when q is requested) the adjugate column; at a (nearly) double top
+// eigenvalue (near_double_f64) the Jacobi iteration gives both instead.  Returns lambda_max;
+// *ok = false if an iteration cap was reached.
+__device__ __forceinline__ double top_eig_f64(const double* H, double ub, bool* ok, double* q) {
+  double dp = 0.0;
+  const double lam = lambda_max_newton(H, ub, ok, &dp);
+  if (near_double_f64(dp, ub)) {
+    Mat4d k;
+    quat_matrix(H, k.v);
+    const TopEig4d e = jacobi_top_f64(k);
+    *ok = e.ok != 0;
+    if (q) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) q[a] = e.q[a];
+    }
+    return e.lam;
+  }
+  if (q) {
+    double K[16];
+    quat_matrix(H, K);
+    adj_eigvec_f64(K, lam, q);
+  }
+  return lam;
 }
 
 // Solve the 4x4 symmetric positive definite system A p = g by Cholesky.

@@ -30,6 +30,11 @@ struct LandmarkDev {
   // alignment weights w' (normalised; they set the centres), or nullptr when w' = w
   const float* wa = nullptr;
   const double* wa64 = nullptr;
+  // per-context solver limits, carried with the landmark view to the launches: the Newton
+  // iteration cap of the exact pair kernels' eigen-solves, and the clock budget of each
+  // bounded wait in the tensor-core kernels (cycles)
+  int newton_cap = 60;
+  long long wait_cycles = 4000000000LL;
 };
 // FP16 storage keeps, per landmark and block of 16 consecutive atoms, an FP32 offset (the
 // block's mean centred coordinate) and the FP16 residuals: coordinate = offset + residual

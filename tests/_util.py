@@ -3,7 +3,7 @@
 Metrics (readings of the required accuracy):
   D: |D_gpu - D_ref| / max(D_ref, 1e-3 (G_x + G_a))   -- FP32 inputs cannot support a
      relative accuracy finer than ~eps32 (G_x + G_a) / D on the cancelling form;
-  s: |s_gpu - s_ref| / M;
+  s: |s_gpu - s_ref| / max(|s_ref|, 1)  (s >= 1 with q_i = i, so this is |ds| / s);
   z: |z_gpu - z_ref| / max(|z_ref|, 1/lambda);
   gradients: max_k |g_gpu - g_ref| / max_k |g_ref| per frame.
 Tolerances: FP64 mode 1e-9, FP32 1e-5, FP16 storage 1e-3 (gradients: FP64 1e-8,
@@ -46,8 +46,34 @@ def d_err(D_gpu, D_ref, frames, landmarks, w=None):
     return np.max(np.abs(D_gpu - D_ref) / np.maximum(D_ref, 1e-3 * (gx + ga)))
 
 
-def s_err(s_gpu, s_ref, m):
-    return np.max(np.abs(s_gpu - s_ref)) / m
+def s_err(s_gpu, s_ref, m=None, kappa=None):
+    """Relative error of s per frame, |s_gpu - s_ref| / max(|s_ref|, 1) (m, the landmark
+    count, is accepted for the callers' convenience and not used).  kappa (per frame, optional)
+    divides the error by 1 + kappa: the first-order condition number of s with respect to
+    relative changes of the D_i (s_kappa), for storage whose rounding moves every D by up to
+    the D tolerance itself."""
+    s_gpu = np.asarray(s_gpu, dtype=np.float64)
+    s_ref = np.asarray(s_ref, dtype=np.float64)
+    if s_ref.size == 0:
+        return 0.0
+    den = np.maximum(np.abs(s_ref), 1.0)
+    if kappa is not None:
+        den = den * (1.0 + np.asarray(kappa))
+    return float(np.max(np.abs(s_gpu - s_ref) / den))
+
+
+def s_kappa(D_ref, lam, frames, landmarks, w=None):
+    """First-order condition number of s = sum_i i p_i (p = softmax(-lam D)) with respect to
+    relative changes of the distances, each D_i measured against its error floor
+    max(D_i, 1e-3 (G_x + G_a)) as d_err does: ds = -lam sum_i p_i (i - s) dD_i, so
+    kappa = lam sum_i p_i |i - s| max(D_i, 1e-3 (G_x + G_a)) / max(|s|, 1)."""
+    D = np.asarray(D_ref, dtype=np.float64)
+    e = np.exp(-lam * (D - D.min(axis=1, keepdims=True)))
+    p = e / e.sum(axis=1, keepdims=True)
+    q = np.arange(1, D.shape[1] + 1, dtype=np.float64)
+    s = p @ q
+    floor = np.maximum(D, 1e-3 * (gsum(frames, w)[:, None] + gsum(landmarks, w)[None, :]))
+    return lam * np.sum(p * np.abs(q[None, :] - s[:, None]) * floor, axis=1) / np.maximum(np.abs(s), 1.0)
 
 
 def z_err(z_gpu, z_ref, lam):

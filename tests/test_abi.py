@@ -37,9 +37,29 @@ def test_library_exports_every_declared_symbol(lib):
     assert set(declared_symbols()) <= set(pcv.SIGNATURES)
 
 
-def test_binary_targets_sm_103a(lib):
-    data = build_lib.LIB.read_bytes()
-    assert b"sm_103a" in data or b"sm_103" in data
+def test_build_targets_sm_103a_only(monkeypatch, tmp_path):
+    """Every nvcc command of the build (each translation unit and the link) carries the one
+    -gencode for sm_103a and no other architecture.  The commands are recorded by a stand-in
+    for subprocess.run that creates the outputs it is asked for."""
+    cmds = []
+
+    class Done:
+        returncode, stdout, stderr = 0, "", ""
+
+    def fake_run(cmd, **kw):
+        cmds.append(list(cmd))
+        Path(cmd[cmd.index("-o") + 1]).write_bytes(b"")
+        return Done()
+
+    monkeypatch.setattr(build_lib.subprocess, "run", fake_run)
+    monkeypatch.setattr(build_lib, "BUILD", tmp_path)
+    monkeypatch.setattr(build_lib, "LIB", tmp_path / "libpcv.so")
+    build_lib.build(force=True)
+    assert len(cmds) == len(build_lib.SOURCES) + 1
+    for cmd in cmds:
+        gencodes = [cmd[k + 1] for k, a in enumerate(cmd) if a == "-gencode"]
+        assert gencodes == ["arch=compute_103a,code=sm_103a"], cmd
+        assert not any(a.startswith(("-arch", "--gpu-architecture")) for a in cmd), cmd
 
 
 def test_null_context_is_rejected_without_gpu(lib):

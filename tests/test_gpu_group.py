@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
-from _util import TOL, d_err, problem, s_err, z_err
+from _util import TOL, d_err, problem, s_err, s_kappa, z_err
 
 pytestmark = pytest.mark.gpu
 
@@ -62,7 +62,10 @@ def _check(insts, bufs, precision):
             continue
         r = oracle.exact(fr, lm, lam)
         assert d_err(b["msd"].cpu().numpy(), r["D"], fr, lm) < TOL[precision]
-        assert s_err(b["s"].cpu().numpy(), r["s"], lm.shape[0]) < TOL[precision]
+        # FP16 storage: the instances of a few atoms take D errors up to the D tolerance from
+        # the rounding of the landmarks alone, and s inherits them with its condition number
+        kappa = s_kappa(r["D"], lam, fr, lm) if precision == "fp16" else None
+        assert s_err(b["s"].cpu().numpy(), r["s"], lm.shape[0], kappa=kappa) < TOL[precision]
         assert z_err(b["z"].cpu().numpy(), r["z"], lam) < TOL[precision]
 
 

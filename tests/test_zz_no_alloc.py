@@ -64,6 +64,28 @@ def test_noalloc_matches_regular_entry_point_twice(pcv):
     assert z_err(z, r["z"], lam) < TOL["fp32"]
 
 
+@pytest.mark.parametrize("F", [1, 4])
+def test_noalloc_few_frames_match_regular_entry_point(pcv, F):
+    """One to four frames per call take the call's few-frame branch (one CTA per landmark);
+    two calls in a row, each against the regular entry point and the oracle."""
+    lm, fr, lam = problem(43, 300, 200, 2 * F)
+    stream = torch.cuda.current_stream().cuda_stream
+    ctx = pcv.PathCV(lm, lam, eps=-1.0, precision="fp32")
+    for part in (fr[:F], fr[F:]):
+        s, z, msd = noalloc(pcv, part, lm, lam, stream)
+        ref = ctx.evaluate(torch.tensor(part, dtype=torch.float32, device="cuda"), msd=True)
+        torch.cuda.synchronize()
+        rs, rz, rmsd = (ref[k].cpu().numpy() for k in ("s", "z", "msd"))
+        assert d_err(msd, rmsd, part, lm) < TOL["fp32"]
+        assert s_err(s, rs) < TOL["fp32"]
+        assert z_err(z, rz, lam) < TOL["fp32"]
+        r = oracle.exact(part, lm, lam)
+        assert d_err(msd, r["D"], part, lm) < TOL["fp32"]
+        assert s_err(s, r["s"]) < TOL["fp32"]
+        assert z_err(z, r["z"], lam) < TOL["fp32"]
+    ctx.close()
+
+
 def test_noalloc_rejects_problems_beyond_the_fixed_scratch(pcv):
     err = ctypes.create_string_buffer(256)
     big_f = (16 << 20) // (4 * 200) + 1
