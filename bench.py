@@ -1,16 +1,19 @@
 #!/usr/bin/env python
 """Benchmark of the path-CV hot path on one GB300 (or N independent walkers on N GPUs).
 
-Workload (the configuration the headline metric is quoted on): N = 300 atoms, M = 200
-landmarks along a synthetic path, a batch of F = 100,000 FP32 frames drifting along the
-path with N(0, 0.05 nm) noise; floating close structure with eps = 0.05 nm^2 (Algorithm 2);
-one step evaluates s, z and their coordinate derivatives ds/dx, dz/dx for the whole batch
-(every step of the path: frame centring, close-structure decisions, exact alignments at
-reassignments, approximate MSDs, path CVs, adjoint).  The close-structure state is reset
-at the start of every step so each step does the same work.
+Workload (the headline: the largest configuration that fits one GPU): N = 5000 atoms,
+M = 2000 landmarks along a synthetic path (120 MB in FP32 storage, beyond what L2 holds
+with the frames streaming through), a batch of F = 10,000 FP32 frames (600 MB) drifting
+along the path with N(0, 0.05 nm) noise; floating close structure with eps = 0.05 nm^2
+(Algorithm 2).  One step evaluates s, z and their coordinate derivatives ds/dx, dz/dx for
+the whole batch: frame centring, close-structure decisions, exact alignments at
+reassignments, approximate MSDs, path CVs and the adjoint.  The close-structure state is
+reset at the start of every step so each step does the same work.  The step is timed with
+per-kernel profiling off; a separate pass of the same steps with per-launch CUDA events
+gives the kernel shares and the dominant kernel's roofline.
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on the box's
-host cores on a bounded sample of the same workload.
+host cores (OpenMP) on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -30,8 +33,9 @@ ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
 METRIC = "path-CV frames/s and aligned MSDs/s on 1 GB300; % of HBM/L2 roofline"
-N_ATOMS, N_LANDMARKS, N_FRAMES = 300, 200, 100_000
-SEED = 1
+# headline workload: N atoms, M landmarks, F frames per step, eps, frame noise, seed
+N_ATOMS, N_LANDMARKS, N_FRAMES = 5000, 2000, 10_000
+EPS, SEED = 0.05, 5
 
 # FP32 ALU peak of one GB300: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.070 GHz (max SM clock)
 SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.070
@@ -85,6 +89,10 @@ DETAILS = {
     "c5_batched_fp16": ("config", dict(label="close-structure path CV, N=5000, M=2000, F=10000, fp16 landmark storage",
                                        seed=5, n=5000, m=2000, f=10_000, eps=0.05, grad=False, precision="fp16",
                                        steps=1)),
+    # the headline workload with FP16-stored landmarks (the headline itself is FP32 storage)
+    "c5_batched_fp16_grad": ("config", dict(label="close-structure path CV with gradients, N=5000, M=2000, F=10000, "
+                                                  "fp16 landmark storage", seed=5, n=5000, m=2000, f=10_000,
+                                            eps=0.05, grad=True, precision="fp16", steps=2)),
     # the paper's second data set in size (304 atoms, 2120 landmarks, a neighbour list of 50
     # updated every 50 steps): the original method with and without the list, and the
     # close structure with the list
@@ -123,7 +131,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--eps", type=float, default=0.05)
+    ap.add_argument("--eps", type=float, default=EPS)
     ap.add_argument("--frames", type=int, default=N_FRAMES)
     ap.add_argument("--no-details", action="store_true", help="skip the exact-mode / eps-sweep side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -135,12 +143,15 @@ def parse():
 
 
 def workload_config(args):
+    lm_mb = N_LANDMARKS * N_ATOMS * 3 * 4 / 1e6
+    fr_mb = args.frames * N_ATOMS * 3 * 4 / 1e6
     return {
-        "workload": f"close-structure path CV, N={N_ATOMS} atoms, M={N_LANDMARKS} landmarks, F={args.frames} "
-                    f"frames per step, FP32, eps={args.eps} nm^2, s/z + ds/dx, dz/dx",
+        "workload": f"close-structure path CV with gradients, N={N_ATOMS} atoms, M={N_LANDMARKS} landmarks "
+                    f"(FP32 storage), F={args.frames} frames per step, eps={args.eps} nm^2: s, z, ds/dx, dz/dx",
         "atoms": N_ATOMS, "landmarks": N_LANDMARKS, "frames_per_step": args.frames, "eps_nm2": args.eps,
         "precision": "fp32 (compensated sums, FP32 eigen-solve + direct MSD; FP64 refresh re-checks)",
-        "l2": "inputs larger than L2: frames 360 MB per step vs 126 MB L2 (landmarks 0.72 MB stay L2-resident)",
+        "l2": f"inputs larger than L2: frames {fr_mb:.0f} MB per step and landmarks {lm_mb:.0f} MB vs 126 MB L2 "
+              "(no flush needed)",
         "data": "synthetic: seeded self-avoiding chains, interpolated path, drift + N(0,0.05) noise",
     }
 
@@ -265,8 +276,6 @@ def time_config(pcv, label: str, seed: int, n: int, m: int, f: int, eps: float, 
     stream = torch.cuda.current_stream()
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
-    ctx.set_profiling(True)
-    ctx.profile()
     a.record(stream)
     for _ in range(steps):
         pcv.pcv_reset_close_state(ctx.ctx)
@@ -274,6 +283,12 @@ def time_config(pcv, label: str, seed: int, n: int, m: int, f: int, eps: float, 
     b.record(stream)
     torch.cuda.synchronize()
     t = a.elapsed_time(b) / steps
+    # kernel times from a separate pass with per-launch events
+    ctx.set_profiling(True)
+    ctx.profile()
+    for _ in range(steps):
+        pcv.pcv_reset_close_state(ctx.ctx)
+        ctx.evaluate(frames, grad=grad)
     pr = ctx.profile()
     st = ctx.stats()
     ctx.close()
@@ -310,6 +325,8 @@ def time_config(pcv, label: str, seed: int, n: int, m: int, f: int, eps: float, 
         out["list_kernels"] = roof
     # expensive distance computations per step (the cost model of the paper's Section 6.2)
     out["expensive_per_step"] = (st["xy_alignments"] + st["landmark_alignments"]) / f
+    if nl is None and any(k in pr for k in FLOPS_PER_UNIT):
+        out["roofline"] = kernel_roofline(pr, steps, f, n, m, st["landmark_alignments"], st["approx_msds"])
     return out
 
 
@@ -484,21 +501,41 @@ def time_group(pcv, n_inst: int = 256, f: int = 512, seed: int = 7, steps: int =
             "frac_of_fp32_peak": flops / (t / 1e3) / 1e12 / FP32_PEAK_TFLOPS}
 
 
-def cpu_baseline(lm, fr, lam, eps, seconds: float) -> dict:
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def oracle_sample(lm, fr, lam, eps, seconds: float, probe: int = 4):
+    """Frames n such that the oracle's close-structure run over fr[:n] (with gradients)
+    takes about `seconds`: the run from frame 0 includes the initial assignment and the
+    reassignments in proportion to the workload's own rate once n spans a few gaps."""
     import oracle
 
-    oracle.build()
-    probe = 50
     t0 = time.perf_counter()
     oracle.close(fr[:probe], lm, lam, eps, want_grad=True, want_D=False)
     per = (time.perf_counter() - t0) / probe
-    n = int(max(probe, min(len(fr), seconds / max(per, 1e-9))))
+    return int(max(probe, min(len(fr), seconds / max(per, 1e-9))))
+
+
+def cpu_baseline(lm, fr, lam, eps, seconds: float) -> dict:
+    """The FP64 oracle as it stands on the host cores (OpenMP over the landmarks and atoms of
+    each frame; Algorithm 2 itself is sequential over frames), on the first frames of the
+    workload."""
+    import oracle
+
+    oracle.build()
+    n = oracle_sample(lm, fr, lam, eps, seconds)
     t0 = time.perf_counter()
-    oracle.close(fr[:n], lm, lam, eps, want_grad=True, want_D=False)
+    r = oracle.close(fr[:n], lm, lam, eps, want_grad=True, want_D=False)
     dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "frames/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {n} frames of the workload, close structure eps={eps} with gradients, "
-                      f"{dt:.1f} s (Algorithm 2 is sequential: one thread)"}
+    n_ref = int((r["refreshed"] == 1).sum())
+    return {"value": n / dt, "unit": "frames/s", "cores": oracle.threads(), "host_cores": host_cores(),
+            "kind": "oracle",
+            "sample": f"first {n} frames of the workload ({n_ref} reassignments + the initial assignment), close "
+                      f"structure eps={eps} with gradients, {dt:.1f} s on {oracle.threads()} OpenMP threads"}
 
 
 def run_reference(args):
@@ -508,14 +545,10 @@ def run_reference(args):
     import oracle
 
     oracle.build()
-    lm, fr = make_inputs(min(args.frames, 20000))
+    lm, fr = make_inputs(min(args.frames, 2000))
     lam = 2.3 / oracle.mean_adjacent_msd(lm)
-    # bounded sample per step: ~2 s of oracle time
-    probe = 40
-    t0 = time.perf_counter()
-    oracle.close(fr[:probe], lm, lam, args.eps, want_grad=True, want_D=False)
-    per = (time.perf_counter() - t0) / probe
-    n = int(max(probe, min(len(fr), 2.0 / max(per, 1e-9))))
+    # bounded sample per step: ~2 s of oracle time from frame 0 of the workload
+    n = oracle_sample(lm, fr, lam, args.eps, 2.0)
     for _ in range(args.warmup):
         oracle.close(fr[:n], lm, lam, args.eps, want_grad=True, want_D=False)
     t0 = time.perf_counter()
@@ -528,11 +561,111 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(args),
-        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": 1, "kind": "oracle",
-                         "sample": f"first {n} frames of the workload per step (Algorithm 2 is sequential)"},
+        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": oracle.threads(), "host_cores": host_cores(),
+                         "kind": "oracle",
+                         "sample": f"first {n} frames of the workload per step, close structure with gradients "
+                                   f"(Algorithm 2 is sequential over frames; OpenMP over landmarks and atoms)"},
         "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def kernel_roofline(prof: dict, steps: int, F: int, n: int, m: int, exact_msds: int, approx_msds: int) -> dict:
+    """Roofline of the dominant kernel (by device time among the kernels with a work model)
+    from a profiled pass of `steps` steps: algorithmic flops per launch / average launch
+    time against the FP32 pipe or the TF32 tensor peak."""
+    share = {k: v[0] for k, v in prof.items()}
+    total_ms = sum(share.values())
+    dom = max((k for k in prof if k in FLOPS_PER_UNIT), key=lambda k: prof[k][0])
+    dom_ms, dom_launches = prof[dom]
+    per_launch_ms = dom_ms / dom_launches
+    launches_per_step = dom_launches / steps
+    if dom == "approx_pair":
+        units = approx_msds / launches_per_step * n
+    elif dom == "exact_pair":
+        units = exact_msds / launches_per_step * n
+    else:
+        units = F * m * n / launches_per_step
+    flops = FLOPS_PER_UNIT[dom] * units
+    achieved = flops / (per_launch_ms / 1e3) / 1e12
+    if dom in TENSOR_KERNELS:
+        peaks = measured_peaks()
+        bf16 = peaks.get("bf16_tflops_sustained")
+        peak = (bf16 if bf16 else 1700.0) * TF32_PER_BF16
+        bound = "tensor"
+        peak_source = ("TF32 dense: " + ("measured" if bf16 else "fallback") + " sustained bf16 cuBLAS rate x 1.1/2.25 "
+                       "(nominal TF32/bf16); 3xTF32 issues 3 MMAs per algorithmic product, so frac <= 1/3")
+    else:
+        peak, bound = FP32_PEAK_TFLOPS, "alu"
+        peak_source = "152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz max clock (derived; FP32 FMA pipe)"
+    traffic = None
+    per_unit = DRAM_BYTES_PER_UNIT.get(dom)
+    if per_unit is not None:
+        traffic = per_unit * (approx_msds / launches_per_step if dom == "approx_pair" else F / launches_per_step)
+    return {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic, "peak_source": peak_source,
+            "per_launch_ms": per_launch_ms, "flops_per_launch": flops,
+            "timing": "per-launch CUDA events on the library's stream, in a separate pass of the same steps "
+                      "(the headline's timed region runs without them)",
+            "kernel_share": {k: round(v / total_ms, 4) for k, v in sorted(share.items(), key=lambda kv: -kv[1])}}
+
+
+def c2_details(pcv, dev, stream) -> dict:
+    """The 300-atom, 200-landmark, 100k-frame workload (FP32, gradients) across the
+    close-structure thresholds and in exact mode, each with its dominant kernel's roofline."""
+    import torch
+    from paper_1801_02362_gb300 import synth
+
+    n, m, F = 300, 200, 100_000
+    lm, fr = synth.make_problem(1, n_atoms=n, n_landmarks=m, n_frames=F, frame_noise=0.05)
+    fr = np.ascontiguousarray(fr, dtype=np.float32)
+    lam = lambda_from_gpu(pcv, lm)
+    frames = torch.from_numpy(fr).to(dev)
+    ctx = pcv.PathCV(lm, lam, eps=0.05, precision="fp32", device=dev.index)
+    pcv.pcv_set_stream(ctx.ctx, stream.cuda_stream)
+    s = torch.empty(F, dtype=torch.float64, device=dev)
+    z = torch.empty(F, dtype=torch.float64, device=dev)
+    gs = torch.empty_like(frames)
+    gz = torch.empty_like(frames)
+    P = pcv._ptr
+    out = {}
+    for label, eps, grad in (("c2_close_eps0.05_grad", 0.05, True), ("c2_close_eps0.01_grad", 0.01, True),
+                             ("c2_close_eps0.1_grad", 0.1, True), ("c2_close_eps0.05_fwd_only", 0.05, False),
+                             ("c2_exact_grad", -1.0, True)):
+        pcv.pcv_set_close_threshold(ctx.ctx, eps)
+
+        def step():
+            pcv.pcv_reset_close_state(ctx.ctx)
+            pcv.pcv_evaluate(ctx.ctx, F, P(frames), P(s), P(z), P(gs) if grad else None, P(gz) if grad else None,
+                             None, None)
+
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        k = 3
+        a.record(stream)
+        for _ in range(k):
+            step()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        t = a.elapsed_time(b) / k
+        ctx.set_profiling(True)
+        ctx.profile()
+        for _ in range(k):
+            step()
+        pr = ctx.profile()
+        ctx.set_profiling(False)
+        st = ctx.stats()
+        out[label] = {"workload": f"N={n}, M={m}, F={F}, FP32, eps={eps}" + (", gradients" if grad else ""),
+                      "ms_per_step": t, "frames_per_s": F / (t / 1e3),
+                      "refreshes": st["refreshes_threshold"], "exact_msds": st["landmark_alignments"],
+                      "approx_msds": st["approx_msds"],
+                      "roofline": kernel_roofline(pr, k, F, n, m, st["landmark_alignments"], st["approx_msds"]),
+                      "kernel_ms": {kk: round(v[0] / k, 4) for kk, v in pr.items()}}
+    ctx.close()
+    return out
 
 
 def run_ours(args):
@@ -568,8 +701,6 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)
-    ctx.set_profiling(True)
-    ctx.profile()  # clear
     clocks = ClockSampler(local)
     clocks.start()
     barrier(pg)
@@ -586,52 +717,26 @@ def run_ours(args):
     barrier(pg)
     clk = clocks.stop()
     ms_local = e0.elapsed_time(e1)
-    prof = ctx.profile()
-    ctx.set_profiling(False)
     st = ctx.stats()
     launches = st["kernel_launches"] - launches0
     ms = max_over_ranks(ms_local, pg, dev)
     frames_total = F * args.steps * world
     value = frames_total / (ms / 1e3)
-    msds = F * N_LANDMARKS * args.steps * world / (ms / 1e3)
     # per-step counts of exact and approximate MSDs (the stats reset with the state each step)
     exact_msds_step = st["landmark_alignments"]
     approx_msds_step = st["approx_msds"]
+    msds = (exact_msds_step + approx_msds_step) * args.steps * world / (ms / 1e3)
 
-    # roofline of the dominant kernel (by measured share of device time)
-    share = {k: v[0] for k, v in prof.items()}
-    total_ms = sum(share.values())
-    dom = max((k for k in prof if k in FLOPS_PER_UNIT), key=lambda k: prof[k][0])
-    dom_ms, dom_launches = prof[dom]
-    per_launch_ms = dom_ms / dom_launches
-    launches_per_step = dom_launches / args.steps
-    if dom == "approx_pair":
-        units = approx_msds_step / launches_per_step * N_ATOMS
-    elif dom == "exact_pair":
-        units = exact_msds_step / launches_per_step * N_ATOMS
-    else:
-        units = F * N_LANDMARKS * N_ATOMS / launches_per_step
-    flops = FLOPS_PER_UNIT[dom] * units
-    achieved = flops / (per_launch_ms / 1e3) / 1e12
-    if dom in TENSOR_KERNELS:
-        peaks = measured_peaks()
-        peak = peaks.get("bf16_tflops_sustained", 1700.0) * TF32_PER_BF16
-        bound, peak_source = "tensor", ("TF32 dense: measured sustained bf16 cuBLAS rate x 1.1/2.25 (nominal TF32/bf16); "
-                                        "3xTF32 issues 3 MMAs per algorithmic product, so frac <= 1/3")
-    else:
-        peak, bound = FP32_PEAK_TFLOPS, "alu"
-        peak_source = "152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz max clock (derived; FP32 FMA pipe)"
-    traffic = None
-    if dom == "approx_pair":
-        traffic = DRAM_BYTES_PER_UNIT[dom] * approx_msds_step / launches_per_step
-    elif dom == "adjoint_beta_mma":
-        traffic = DRAM_BYTES_PER_UNIT[dom] * F / launches_per_step
-    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "peak_source": peak_source,
-                "per_launch_ms": per_launch_ms,
-                "flops_per_launch": flops,
-                "kernel_share": {k: round(v / total_ms, 4) for k, v in sorted(share.items(), key=lambda kv: -kv[1])}}
+    # kernel shares and the dominant kernel's roofline: a separate pass of the same steps
+    # with per-launch events on the library's stream
+    prof_steps = max(1, min(args.steps, 5))
+    ctx.set_profiling(True)
+    ctx.profile()  # clear
+    for _ in range(prof_steps):
+        step()
+    prof = ctx.profile()
+    ctx.set_profiling(False)
+    roofline = kernel_roofline(prof, prof_steps, F, N_ATOMS, N_LANDMARKS, exact_msds_step, approx_msds_step)
 
     # end to end through the host entry point: H2D of the frames, evaluation, D2H of s, z, gradients
     host_fr = torch.from_numpy(fr).pin_memory()
@@ -650,38 +755,11 @@ def run_ours(args):
     e2e_s = max_over_ranks(time.perf_counter() - t0, pg, dev)
     e2e = {"value": F * e2e_steps * world / e2e_s, "unit": "frames/s", "h2d_bytes_per_step": int(fr.nbytes),
            "d2h_bytes_per_step": int(2 * F * 8 + 2 * fr.nbytes), "api": "pcv_evaluate_host"}
+    ctx.close()
 
     details = {}
     if not args.no_details and rank == 0:
-        for label, eps, grad in (("exact_fwd_grad", -1.0, True), ("close_eps0.01", 0.01, True),
-                                 ("close_eps0.1", 0.1, True), ("close_eps0.05_fwd_only", 0.05, False)):
-            pcv.pcv_set_close_threshold(ctx.ctx, eps)
-            for _ in range(2):
-                pcv.pcv_reset_close_state(ctx.ctx)
-                pcv.pcv_evaluate(ctx.ctx, F, P(frames), P(s), P(z), P(gs) if grad else None, P(gz) if grad else None,
-                                 None, None)
-            torch.cuda.synchronize(dev)
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            n = 3
-            pcv.pcv_set_option(ctx.ctx, pcv.PCV_OPT_PROFILE, 1)
-            pcv.pcv_get_profile(ctx.ctx)
-            a.record(stream)
-            for _ in range(n):
-                pcv.pcv_reset_close_state(ctx.ctx)
-                pcv.pcv_evaluate(ctx.ctx, F, P(frames), P(s), P(z), P(gs) if grad else None, P(gz) if grad else None,
-                                 None, None)
-            b.record(stream)
-            torch.cuda.synchronize(dev)
-            t = a.elapsed_time(b) / n
-            pr = pcv.pcv_get_profile(ctx.ctx)
-            pcv.pcv_set_option(ctx.ctx, pcv.PCV_OPT_PROFILE, 0)
-            st2 = ctx.stats()
-            details[label] = {"ms_per_step": t, "frames_per_s": F / (t / 1e3),
-                              "refreshes": st2["refreshes_threshold"], "exact_msds": st2["landmark_alignments"],
-                              "approx_msds": st2["approx_msds"],
-                              "kernel_ms": {k: round(v[0] / n, 4) for k, v in pr.items()}}
-        pcv.pcv_set_close_threshold(ctx.ctx, args.eps)
+        details.update(c2_details(pcv, dev, stream))
         for name in DETAILS:
             details[name] = run_detail(pcv, name, args.calls)
         if "c5_stream_fp32" in details and "c5_stream_fp16" in details:
@@ -705,7 +783,6 @@ def run_ours(args):
             "clocks": clk, "details": details,
         }
         print(json.dumps(line), flush=True)
-    ctx.close()
     if pg is not None:
         pg.destroy_process_group()
 

@@ -5,7 +5,8 @@ reference legs of ``bench.py`` are the only users.  The CUDA library never impor
 links this package, and this package never touches the CUDA library.
 
 See ``pcv_oracle.c`` for the paper passages each routine follows.  ``build()`` compiles
-the C source with gcc (OpenMP over the frames of the exact-mode loop).
+the C source with gcc (OpenMP over frames in exact mode, over landmarks and atoms within a
+frame; the results do not depend on the thread count).
 """
 from __future__ import annotations
 
@@ -66,8 +67,20 @@ def lib():
         for name in ("orc_cost_original", "orc_cost_close", "orc_amdahl"):
             getattr(L, name).argtypes = [c_double] * (3 if name == "orc_cost_original" else 2)
             getattr(L, name).restype = c_double
+        L.orc_threads.restype = c_int
+        L.orc_set_threads.argtypes = [c_int]
         _lib = L
     return _lib
+
+
+def threads() -> int:
+    """Threads the oracle's OpenMP loops use."""
+    return int(lib().orc_threads())
+
+
+def set_threads(n: int) -> None:
+    """Set the oracle's OpenMP thread count (the results do not depend on it)."""
+    lib().orc_set_threads(int(n))
 
 
 def _p(a, ctype=ctypes.c_double):

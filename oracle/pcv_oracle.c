@@ -26,7 +26,10 @@
  *     path-CV derivatives;
  *   - cost model of Section 6.2 ("Theoretical Speedup") and Amdahl's law, Eq. (ahmdal).
  *
- * Everything is double precision, plain loops, one frame / one landmark at a time.
+ * Everything is double precision, plain loops.  OpenMP threads share out independent
+ * work only (frames of the exact-mode loop; within a frame the landmarks, then the atoms,
+ * each output summed in the same order as a single thread would), so the results do not
+ * depend on the thread count.
  * Conventions: coordinates are row-major (structure, atom, xyz).  R is row-major 3x3.
  * Two weight sets (Section 3.1, after Eq. der_dist): displacement weights w, the
  * contribution of each atom's displacement to the distance, and alignment weights w', the
@@ -39,6 +42,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_OK 0
 #define ORC_EINVAL -1
@@ -360,42 +366,60 @@ int orc_frame_exact(int m, int n, const double* w, const double* wa, const doubl
   if (!sel) msel = m;
   double* R = (double*)calloc((size_t)9 * m, sizeof(double));
   for (int i = 0; i < m; ++i) D[i] = INFINITY;
+  /* the landmarks are independent: OpenMP threads take them in parallel */
+  int bad = 0;
+#pragma omp parallel for schedule(dynamic, 4) reduction(| : bad)
   for (int k = 0; k < msel; ++k) {
     const int i = member(sel, k);
     orc_align_t al;
-    if (orc_align_centered(n, w, xc, lmc + (size_t)i * n * 3, &al) != ORC_OK) st = ORC_ENOCONV;
+    if (orc_align_centered(n, w, xc, lmc + (size_t)i * n * 3, &al) != ORC_OK) bad = 1;
     D[i] = al.D;
     memcpy(R + 9 * i, al.R, sizeof(al.R));
   }
+  if (bad) st = ORC_ENOCONV;
   double* p = (double*)malloc(sizeof(double) * msel);
   members_cv(msel, sel, D, qprop, lambda, s, z, p);
   if (dsdx || dzdx) {
-    /* Eq. (der_dist): dD_i/dx_k = 2 w_k d_k + w'_k sum_j (-2 w_j d_j) + (rotation term).
-     * With R optimal for D the rotation term vanishes (stationarity of D in R); the centre
-     * term vanishes only when w' = w. */
-    if (dsdx) memset(dsdx, 0, sizeof(double) * 3 * n);
-    if (dzdx) memset(dzdx, 0, sizeof(double) * 3 * n);
-    double* d = (double*)malloc(sizeof(double) * 3 * n);
+    /* Eq. (der_dist): dD_i/dx_k = 2 w_k d_ik + w'_k sum_j (-2 w_j d_ij) + (rotation term),
+     * d_ij = x_j - R_i a_ij.  With R optimal for D the rotation term vanishes (stationarity
+     * of D in R); the centre term vanishes only when w' = w.  First the centre sums of every
+     * landmark (independent landmarks), then each atom's derivative summed over the
+     * landmarks in order (independent atoms). */
+    double* dsum = (double*)calloc((size_t)3 * (msel > 0 ? msel : 1), sizeof(double));
+#pragma omp parallel for schedule(dynamic, 4)
     for (int k0 = 0; k0 < msel; ++k0) {
       const int i = member(sel, k0);
       const double* a = lmc + (size_t)i * n * 3;
       const double* Ri = R + 9 * i;
-      double dsum[3] = {0, 0, 0};
+      double* ds3 = dsum + 3 * k0;
       for (int j = 0; j < n; ++j)
         for (int b = 0; b < 3; ++b) {
-          d[3 * j + b] = xc[3 * j + b] - (Ri[3 * b] * a[3 * j] + Ri[3 * b + 1] * a[3 * j + 1] + Ri[3 * b + 2] * a[3 * j + 2]);
-          dsum[b] += -2.0 * w[j] * d[3 * j + b];
-        }
-      const double gs = -lambda * p[k0] * (qprop[i] - *s); /* ds/dD_i */
-      const double gz = p[k0];                           /* dz/dD_i */
-      for (int k = 0; k < n; ++k)
-        for (int b = 0; b < 3; ++b) {
-          const double dDi = 2.0 * w[k] * d[3 * k + b] + wa[k] * dsum[b];
-          if (dsdx) dsdx[3 * k + b] += gs * dDi;
-          if (dzdx) dzdx[3 * k + b] += gz * dDi;
+          const double d = xc[3 * j + b] - (Ri[3 * b] * a[3 * j] + Ri[3 * b + 1] * a[3 * j + 1] + Ri[3 * b + 2] * a[3 * j + 2]);
+          ds3[b] += -2.0 * w[j] * d;
         }
     }
-    free(d);
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < n; ++k) {
+      double gsk[3] = {0, 0, 0}, gzk[3] = {0, 0, 0};
+      for (int k0 = 0; k0 < msel; ++k0) {
+        const int i = member(sel, k0);
+        const double* a = lmc + (size_t)i * n * 3;
+        const double* Ri = R + 9 * i;
+        const double gs = -lambda * p[k0] * (qprop[i] - *s); /* ds/dD_i */
+        const double gz = p[k0];                           /* dz/dD_i */
+        for (int b = 0; b < 3; ++b) {
+          const double d = xc[3 * k + b] - (Ri[3 * b] * a[3 * k] + Ri[3 * b + 1] * a[3 * k + 1] + Ri[3 * b + 2] * a[3 * k + 2]);
+          const double dDi = 2.0 * w[k] * d + wa[k] * dsum[3 * k0 + b];
+          gsk[b] += gs * dDi;
+          gzk[b] += gz * dDi;
+        }
+      }
+      for (int b = 0; b < 3; ++b) {
+        if (dsdx) dsdx[3 * k + b] = gsk[b];
+        if (dzdx) dzdx[3 * k + b] = gzk[b];
+      }
+    }
+    free(dsum);
   }
   if (Rout) memcpy(Rout, R, sizeof(double) * 9 * m);
   free(p);
@@ -414,6 +438,8 @@ int orc_frame_approx(int m, int n, const double* w, const double* wa, const doub
   if (!sel) msel = m;
   double* Q = (double*)calloc((size_t)9 * m, sizeof(double));
   for (int i = 0; i < m; ++i) D[i] = INFINITY;
+  /* the landmarks are independent: OpenMP threads take them in parallel */
+#pragma omp parallel for schedule(dynamic, 4)
   for (int k0 = 0; k0 < msel; ++k0) {
     const int i = member(sel, k0);
     const double* Bi = B + 9 * i;
@@ -433,42 +459,60 @@ int orc_frame_approx(int m, int n, const double* w, const double* wa, const doub
   double* p = (double*)malloc(sizeof(double) * msel);
   members_cv(msel, sel, D, qprop, lambda, s, z, p);
   if (dsdx || dzdx) {
-    if (dsdx) memset(dsdx, 0, sizeof(double) * 3 * n);
-    if (dzdx) memset(dzdx, 0, sizeof(double) * 3 * n);
-    double* dt = (double*)malloc(sizeof(double) * 3 * n);
-    double Gs[9] = {0}, Gz[9] = {0}; /* sum_i (dL/dD_i) G_i for L = s and L = z */
+    /* Eq. (close_der_dist) with d~_ij = x_j - Q_i a_ij: the direct and centre terms as in
+     * the exact case, plus the rotation term through R_xy.  First, per landmark
+     * (independent landmarks), the centre sum and G_i = sum_j -2 w_j d~_ij (R_{a_i y} a_ij)^T;
+     * then G^s, G^z summed over the landmarks in order; then each atom's derivative summed
+     * over the landmarks in order, plus its rotation term (independent atoms). */
+    const int ms = msel > 0 ? msel : 1;
+    double* dsum = (double*)calloc((size_t)3 * ms, sizeof(double));
+    double* Gi = (double*)calloc((size_t)9 * ms, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 4)
     for (int k0 = 0; k0 < msel; ++k0) {
       const int i = member(sel, k0);
       const double* a = lmc + (size_t)i * n * 3;
       const double* Qi = Q + 9 * i;
       const double* Bi = B + 9 * i;
-      double dsum[3] = {0, 0, 0};
-      double G[9] = {0}; /* G_i = sum_j -2 w_j d~_j (R_{a_i y} a_ij)^T */
+      double* ds3 = dsum + 3 * k0;
+      double* G = Gi + 9 * k0;
       for (int j = 0; j < n; ++j) {
-        double bj[3];
+        double bj[3], dt[3];
         for (int b = 0; b < 3; ++b) bj[b] = Bi[3 * b] * a[3 * j] + Bi[3 * b + 1] * a[3 * j + 1] + Bi[3 * b + 2] * a[3 * j + 2];
         for (int b = 0; b < 3; ++b) {
-          dt[3 * j + b] = xc[3 * j + b] - (Qi[3 * b] * a[3 * j] + Qi[3 * b + 1] * a[3 * j + 1] + Qi[3 * b + 2] * a[3 * j + 2]);
-          dsum[b] += -2.0 * w[j] * dt[3 * j + b];
+          dt[b] = xc[3 * j + b] - (Qi[3 * b] * a[3 * j] + Qi[3 * b + 1] * a[3 * j + 1] + Qi[3 * b + 2] * a[3 * j + 2]);
+          ds3[b] += -2.0 * w[j] * dt[b];
         }
         for (int b = 0; b < 3; ++b)
-          for (int c = 0; c < 3; ++c) G[3 * b + c] += -2.0 * w[j] * dt[3 * j + b] * bj[c];
-      }
-      const double gs = -lambda * p[k0] * (qprop[i] - *s);
-      const double gz = p[k0];
-      for (int k = 0; k < n; ++k)
-        for (int b = 0; b < 3; ++b) {
-          const double dDi = 2.0 * w[k] * dt[3 * k + b] + wa[k] * dsum[b];
-          if (dsdx) dsdx[3 * k + b] += gs * dDi;
-          if (dzdx) dzdx[3 * k + b] += gz * dDi;
-        }
-      for (int e = 0; e < 9; ++e) {
-        Gs[e] += gs * G[e];
-        Gz[e] += gz * G[e];
+          for (int c = 0; c < 3; ++c) G[3 * b + c] += -2.0 * w[j] * dt[b] * bj[c];
       }
     }
-    /* rotation term: sum_ab G_ab dR_{x y,ab}/dx_kc for every atom k and component c */
-    for (int k = 0; k < n; ++k)
+    double Gs[9] = {0}, Gz[9] = {0}; /* sum_i (dL/dD_i) G_i for L = s and L = z */
+    for (int k0 = 0; k0 < msel; ++k0) {
+      const int i = member(sel, k0);
+      const double gs = -lambda * p[k0] * (qprop[i] - *s);
+      const double gz = p[k0];
+      for (int e = 0; e < 9; ++e) {
+        Gs[e] += gs * Gi[9 * k0 + e];
+        Gz[e] += gz * Gi[9 * k0 + e];
+      }
+    }
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < n; ++k) {
+      double gsk[3] = {0, 0, 0}, gzk[3] = {0, 0, 0};
+      for (int k0 = 0; k0 < msel; ++k0) {
+        const int i = member(sel, k0);
+        const double* a = lmc + (size_t)i * n * 3;
+        const double* Qi = Q + 9 * i;
+        const double gs = -lambda * p[k0] * (qprop[i] - *s);
+        const double gz = p[k0];
+        for (int b = 0; b < 3; ++b) {
+          const double dt = xc[3 * k + b] - (Qi[3 * b] * a[3 * k] + Qi[3 * b + 1] * a[3 * k + 1] + Qi[3 * b + 2] * a[3 * k + 2]);
+          const double dDi = 2.0 * w[k] * dt + wa[k] * dsum[3 * k0 + b];
+          gsk[b] += gs * dDi;
+          gzk[b] += gz * dDi;
+        }
+      }
+      /* rotation term: sum_ab G_ab dR_{x y,ab}/dx_kc for each component c */
       for (int c = 0; c < 3; ++c) {
         double dR[9];
         rot_derivative_wrt_x(n, w, wa, yc, al, k, c, dR);
@@ -477,10 +521,16 @@ int orc_frame_approx(int m, int n, const double* w, const double* wa, const doub
           ts += Gs[e] * dR[e];
           tz += Gz[e] * dR[e];
         }
-        if (dsdx) dsdx[3 * k + c] += ts;
-        if (dzdx) dzdx[3 * k + c] += tz;
+        gsk[c] += ts;
+        gzk[c] += tz;
       }
-    free(dt);
+      for (int b = 0; b < 3; ++b) {
+        if (dsdx) dsdx[3 * k + b] = gsk[b];
+        if (dzdx) dzdx[3 * k + b] = gzk[b];
+      }
+    }
+    free(Gi);
+    free(dsum);
   }
   free(p);
   free(Q);
@@ -780,3 +830,19 @@ double orc_cost_close(double n_ref, double k_interval) { return 1.0 + n_ref / k_
 
 /* Amdahl's law, Eq. (ahmdal): S = 1 / ((1 - p) + p/s). */
 double orc_amdahl(double p, double s) { return 1.0 / ((1.0 - p) + p / s); }
+
+/* Threads the OpenMP loops use (1 without OpenMP), and a way to set them (n >= 1). */
+int orc_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}

@@ -129,9 +129,10 @@ def test_c4_full_size_exact_gradients_sampled(pcv):
 
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])
 def test_c5_full_size_close_batched_sampled(pcv, precision):
-    """N=5000, M=2000 (120 MB FP32 / 64 MB FP16 storage), F=10000 drifting frames, eps=0.05:
-    the batched close-structure step on materialised deviations (4.2 GB of rotated
-    landmarks for ~35 close structures); every refresh decision and 6 frames in full."""
+    """N=5000, M=2000 (120 MB FP32 / 64 MB FP16 storage), F=10000 drifting frames, eps=0.05,
+    s, z and both gradients (the benchmark's step, FP32 storage): the batched close-structure
+    step on materialised deviations (4.2 GB of rotated landmarks for ~35 close structures)
+    and the tensor-core segment adjoint; every refresh decision and 6 frames in full."""
     from paper_1801_02362_gb300 import synth
 
     lm, fr = synth.make_problem(5, n_atoms=5000, n_landmarks=2000, n_frames=10_000, frame_noise=0.05)
@@ -141,12 +142,13 @@ def test_c5_full_size_close_batched_sampled(pcv, precision):
     eps = 0.05
     ctx = pcv.PathCV(lm, lam, eps=eps, precision=precision)
     ctx.set_profiling(True)
-    out = ctx.evaluate(torch.from_numpy(fr).cuda(), msd=True, refreshed=True)
+    out = ctx.evaluate(torch.from_numpy(fr).cuda(), grad=True, msd=True, refreshed=True)
     ctx.sync()
     prof = ctx.profile()
     res = {k: v.cpu().numpy() for k, v in out.items()}
     ctx.close()
     assert "materialize" in prof  # the tiled path on materialised deviations ran
+    assert "adjoint_beta_mma" in prof  # and the segment adjoint on the tensor cores
     flags = res["refreshed"]
     assert 10 <= int((flags > 0).sum()) < 200
     _check_refresh_sequence(flags, fr.astype(np.float64), eps)
@@ -154,17 +156,19 @@ def test_c5_full_size_close_batched_sampled(pcv, precision):
     ts = [1, 777, 4321, 9999, int(refreshed[len(refreshed) // 2]), int(refreshed[len(refreshed) // 2]) + 1]
     for t in ts:
         if flags[t]:
-            r = oracle.exact(fr[t:t + 1], lm, lam)
+            r = oracle.exact(fr[t:t + 1], lm, lam, want_grad=True)
             row = 0
         else:
             y_idx = int(np.nonzero(flags[:t + 1])[0][-1])
-            r = oracle.close(np.stack([fr[y_idx], fr[t]]), lm, lam, eps)
+            r = oracle.close(np.stack([fr[y_idx], fr[t]]), lm, lam, eps, want_grad=True)
             assert r["refreshed"][1] == 0
             row = 1
         sl = slice(t, t + 1)
         assert d_err(res["msd"][sl], r["D"][row:row + 1], fr[sl], lm) < TOL[precision]
         assert s_err(res["s"][sl], r["s"][row:row + 1], lm.shape[0]) < TOL[precision]
         assert z_err(res["z"][sl], r["z"][row:row + 1], lam) < TOL[precision]
+        assert grad_err(res["dsdx"][sl], r["dsdx"][row:row + 1]) < GRAD_TOL[precision]
+        assert grad_err(res["dzdx"][sl], r["dzdx"][row:row + 1]) < GRAD_TOL[precision]
 
 
 def test_c2_full_size_host_entry_point(pcv):

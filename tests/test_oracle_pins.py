@@ -11,6 +11,7 @@ from scipy.spatial.transform import Rotation
 from scipy.special import logsumexp
 
 import oracle
+from _util import problem
 from paper_1801_02362_gb300 import synth
 
 GOLDEN = Path(__file__).parent / "golden"
@@ -439,3 +440,26 @@ def test_cost_model_matches_paper_worked_numbers():
         assert round(S, ds["S_digits"]) == ds["S_MSD"]
     # Amdahl's law limits: s -> infinity gives 1/(1-p); p = 0.9 caps at 10 (Section 6.2)
     assert abs(oracle.amdahl(0.9, 1e300) - 10.0) < 1e-9
+
+
+def test_results_do_not_depend_on_the_thread_count():
+    """The OpenMP loops share out independent landmarks and atoms only, each output summed in
+    the single-thread order: one thread and several give bit-identical results (exact and
+    close-structure mode, both weight sets, gradients)."""
+    lm, fr, lam = problem(17, 33, 21, 40, noise=0.02, schedule="walk", ou_rho=0.9)
+    rng = np.random.default_rng(3)
+    w, wa = rng.uniform(0.5, 1.5, 33), rng.uniform(0.5, 1.5, 33)
+    n0 = oracle.threads()
+    runs = []
+    try:
+        for t in (1, 4):
+            oracle.set_threads(t)
+            assert oracle.threads() == t
+            runs.append((oracle.exact(fr, lm, lam, w=w, wa=wa, want_grad=True),
+                         oracle.close(fr, lm, lam, 0.002, w=w, wa=wa, want_grad=True)))
+    finally:
+        oracle.set_threads(n0)
+    assert int((runs[0][1]["refreshed"] == 1).sum()) >= 2
+    for a, b in zip(*runs):
+        for k in ("s", "z", "D", "dsdx", "dzdx"):
+            np.testing.assert_array_equal(a[k], b[k])
