@@ -238,10 +238,13 @@ enum {
                               kernels then rotate while staging; so they also do when the
                               device cannot allocate the operands).  Results agree within
                               the mode's tolerance either way.                          */
-  PCV_OPT_TENSOR_CORES = 7, /* 1 (default): with materialised operands, the segment adjoint
-                              beta = sum_i gamma_i (R_{a_i y} a_i) runs on the tensor cores
-                              (TF32 operands split hi + lo, three products per term, on
-                              deviations from the close structure); 0: FP32 CUDA cores.   */
+  PCV_OPT_TENSOR_CORES = 7, /* 1 (default): with materialised operands, the approximate MSDs'
+                              cross terms dx . d_i run on the tensor cores (FP16 operands
+                              split h + l after a 2^8 scale, three products per term, FP32
+                              accumulation in short groups) and so does the segment adjoint
+                              beta = sum_i gamma_i (R_{a_i y} a_i) (TF32 operands split hi +
+                              lo, three products per term, on deviations from the close
+                              structure); 0: FP32 CUDA cores for both.                    */
   PCV_OPT_HOST_CHUNKS = 8,  /* pcv_evaluate_host: number of chunks the batch is split into
                               so that copies overlap evaluation (0 = automatic, default;
                               1 = no overlap; at most 64)                               */
@@ -253,13 +256,19 @@ enum {
                               kernels (1..60, default 60).  A pair that reaches the cap sets
                               the status word: pcv_sync then returns PCV_ENOCONV.  Lower
                               values exist to exercise that report.                      */
-  PCV_OPT_WAIT_CYCLES = 11  /* clock budget (SM cycles) of each bounded wait inside the
+  PCV_OPT_WAIT_CYCLES = 11, /* clock budget (SM cycles) of each bounded wait inside the
                               tensor-core kernels (0 = default, 4e9, about 2 s at the maximum
                               clock; else 1..4e9).  A wait that runs out sets the status
                               word, the kernel waits for its own copies and MMAs within the
                               default budget, frees its tensor memory and returns; pcv_sync
                               then returns PCV_ETIMEOUT.  Small values exist to exercise
                               that report.                                                */
+  PCV_OPT_MMA_GROUP = 12    /* tensor-core approximate MSDs (PCV_OPT_TENSOR_CORES = 1): chunks
+                              of 16 deviation components summed in tensor memory before the
+                              partial sums are added into FP32 totals (1..8, default 2).
+                              Each accumulation step can lose about one unit in the last
+                              place of the running sum, so shorter groups are more accurate
+                              and cost more folding work.                                 */
 };
 PCV_API pcv_status pcv_set_option(pcv_ctx* ctx, int key, int64_t value);
 
@@ -268,7 +277,7 @@ PCV_API pcv_status pcv_set_option(pcv_ctx* ctx, int key, int64_t value);
  * between events recorded around each launch on the context's stream, and launch counts.
  * ms and launches are host arrays of n entries (n <= PCV_PROFILE_KERNELS).  Synchronises
  * the stream, then clears the collected timings. */
-#define PCV_PROFILE_KERNELS 24
+#define PCV_PROFILE_KERNELS 25
 PCV_API pcv_status pcv_get_profile(pcv_ctx* ctx, int n, double* ms, int64_t* launches);
 
 /* Name of kernel family `id` ("" outside 0..PCV_PROFILE_KERNELS-1). */

@@ -18,7 +18,7 @@ ROOT = PKG.parent
 CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = BUILD / "libpcv.so"
-SOURCES = ["k_pair.cu", "k_aux.cu", "k_adjoint.cu", "pcv_api.cu", "k_noalloc.cu", "k_tile.cu", "k_mma.cu", "k_shard.cu", "k_stream.cu", "k_nl.cu", "k_metad.cu"]
+SOURCES = ["k_pair.cu", "k_aux.cu", "k_adjoint.cu", "pcv_api.cu", "k_noalloc.cu", "k_tile.cu", "k_mma.cu", "k_shard.cu", "k_stream.cu", "k_nl.cu", "k_metad.cu", "k_xmma.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

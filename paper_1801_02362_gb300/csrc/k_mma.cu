@@ -29,6 +29,7 @@
 
 #include "pcv_device.cuh"
 #include "pcv_internal.h"
+#include "tc_sm100.cuh"
 
 namespace pcv {
 namespace {
@@ -45,8 +46,6 @@ constexpr long long MM_WAIT_CYCLES = 4000000000LL;  // about 2 s at the maximum 
                                                     // budget of the waits for copies and MMAs
                                                     // already issued after a failure
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
 __device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
 
 // byte offset of (row r, K value kk < 16) inside one canonical K-major block
@@ -54,86 +53,8 @@ __host__ __device__ __forceinline__ uint32_t canon_off(int r, int kk) {
   return (uint32_t)((r >> 3) * 512 + (kk >> 2) * 128 + (r & 7) * 16 + (kk & 3) * 4);
 }
 
-// shared-memory matrix descriptor: K-major, no swizzling
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version for this architecture
-  return d;                // base offset 0, absolute LBO mode, layout type 0 (no swizzle)
-}
-
 // instruction descriptor: kind::tf32, FP32 accumulator, A and B TF32 and K-major, M x N
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
-  return (1u << 4)                      // D format: F32
-         | (2u << 7)                    // A format: TF32
-         | (2u << 10)                   // B format: TF32
-         | ((uint32_t)(N >> 3) << 17)   // N / 8
-         | ((uint32_t)(M >> 4) << 24);  // M / 16
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-      "l"(src), "r"(bytes), "r"(mbar)
-      : "memory");
-}
-
-// bounded wait for the phase with the given parity; false after `budget` clock cycles
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long budget = MM_WAIT_CYCLES) {
-  const long long t0 = clock64();
-  while (true) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (clock64() - t0 > budget) return false;
-  }
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// 16 consecutive FP32 columns of this thread's TMEM lane
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
-}
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) { return idesc_make(M, N, 2u); }
 
 // ---------------------------------------------------------------------------------------
 // gamma operand: for frame tile t (64 frames) and K chunk c, blocks hi | lo of 128 rows x 16
@@ -421,9 +342,9 @@ __global__ void __launch_bounds__(MM_THREADS, 2) adjoint_beta_mma(MmaArgs p) {
     if (tid == 32) {
       const int last = s_issued;
       for (int g = std::max(0, last - MM_STAGES); g < last; ++g)
-        mbar_wait(smem_u32(&full[g % MM_STAGES]), (uint32_t)((g / MM_STAGES) & 1));
+        mbar_wait(smem_u32(&full[g % MM_STAGES]), (uint32_t)((g / MM_STAGES) & 1), MM_WAIT_CYCLES);
     }
-    mbar_wait(smem_u32(&done), (uint32_t)(s_fail_run & 1));
+    mbar_wait(smem_u32(&done), (uint32_t)(s_fail_run & 1), MM_WAIT_CYCLES);
   }
   tc_fence_before();
   __syncthreads();

@@ -1,0 +1,524 @@
+// k_xmma.cu -- the approximate MSDs of Eq. (close_dist) on the tensor cores.
+//
+// On materialised deviations (see k_tile.cu) the approximate MSD of frame k and landmark i
+// of the frame's segment is
+//   D~_ki = (|dx_k|^2 + |d_i|^2 - 2 dx_k . d_i) / N,
+// and the cross terms dx_k . d_i of a segment form a dense product: approximate frames x
+// landmarks, contracted over K = 3 N16 deviation components.  It runs as tcgen05.mma
+// kind::f16 with two measures for FP32 accuracy:
+//   * split operands: every deviation v is scaled by 2^8 (exact) and split v' = h + l with
+//     h = fp16(v') and l = fp16(v' - h), so h + l carries ~22 significant bits; the product
+//     is h h' + h l' + l h' (three MMAs, products exact in the FP32 accumulator; the dropped
+//     l l' is ~2^-22 relative).  The 2^8 scale keeps l out of the FP16 subnormal range for
+//     deviations above ~5e-4 nm and the largest deviations (up to 256 nm) finite;
+//   * short accumulation chains: each accumulation into the tensor-memory accumulator
+//     loses up to about one unit in the last place of the running sum, so the accumulator
+//     only ever sums a group of a few chunks of 16 components (three MMAs each); then fold
+//     warps add it into Kahan-compensated FP32 totals in registers (total and running
+//     correction, so the hundreds of folds of a long row add no rounding of the running
+//     total: four FP32 operations per column, which keeps the fold as fast as the MMAs)
+//     while the other accumulator buffer takes the next group, so the MMAs never wait for
+//     a fold.  Two registers per column limit a tile to 128 landmarks.
+// Operands are packed once per step in the canonical K-major layout without swizzling
+// (core matrices of 8 rows x 8 halves = 128 contiguous bytes; LBO 128 B along K, SBO 256 B
+// between 8-row groups): per chunk of 16 components a block of rows x 16 holding the h part
+// then the l part.  A (approximate frames) is tiled in 128 consecutive rows of the
+// approximate list, B (landmarks) per segment in column tiles of BN landmarks.  One thread
+// moves a stage (A block and B block) with two cp.async.bulk copies counted on an
+// mbarrier; one thread issues the MMAs; tcgen05.commit releases a stage, and marks an
+// accumulator full.  A tile whose frames span several segments takes them as runs, each a
+// full pass over K with its segment's landmarks.  Every wait is bounded by the context's
+// clock budget; on expiry the kernel records STATUS_TIMEOUT, waits for its own copies and
+// MMAs within the default budget, frees its tensor memory and returns.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "pcv_device.cuh"
+#include "pcv_internal.h"
+#include "tc_sm100.cuh"
+
+namespace pcv {
+namespace {
+
+constexpr int XM_ROWS = 128;     // MMA M: approximate frames per tile
+constexpr int XM_BN_MAX = 128;   // landmarks per tile (MMA N), multiple of 16
+constexpr int XM_KC = 16;        // components per chunk: one MMA (K = 16) per product
+constexpr int XM_STAGES = 12;    // 16 KB each: about 1.3 us of MMAs in flight
+constexpr int XM_GROUP_MAX = 8;  // chunks summed in tensor memory before a fold (the
+                                 // context's PCV_OPT_MMA_GROUP, 1..8)
+constexpr int XM_FOLD_WARPS = 8;  // two per tensor-memory lane quarter (column halves)
+constexpr int XM_THREADS = 32 * (XM_FOLD_WARPS + 2);  // + the copy warp and the MMA warp
+constexpr int XM_TMEM_COLS = 2 * XM_BN_MAX;           // two accumulators
+constexpr uint32_t XM_A_PART = XM_ROWS * XM_KC * 2;   // bytes of the h (or l) part of an A block
+constexpr uint32_t XM_STAGE_BYTES = 2 * XM_A_PART + 2 * XM_BN_MAX * XM_KC * 2;
+constexpr float XM_SCALE = 256.0f;              // 2^8 on every operand
+constexpr float XM_UNSCALE2 = 1.0f / 65536.0f;  // 2^-16 on the products
+constexpr long long XM_DRAIN_CYCLES = 4000000000LL;
+
+// byte offset, inside the h part of a block, of row r and components 8 (p & 1) .. +7 of the
+// block (a 16-byte core-matrix row)
+__host__ __device__ __forceinline__ uint32_t xpiece_off(int r, int p) {
+  return (uint32_t)((r >> 3) * 256 + (p & 1) * 128 + (r & 7) * 16);
+}
+
+// eight deviations -> h and l parts (scaled by 2^8), eight halves each
+__device__ __forceinline__ void xsplit8(const float* v, uint4& hi, uint4& lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float s0 = v[2 * e] * XM_SCALE, s1 = v[2 * e + 1] * XM_SCALE;
+    const __half h0 = __float2half_rn(s0), h1 = __float2half_rn(s1);
+    const __half l0 = __float2half_rn(s0 - __half2float(h0)), l1 = __float2half_rn(s1 - __half2float(h1));
+    h[e] = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
+    l[e] = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// squared-norm partials of the 8 rows handled by a block of 256 threads (row = tid & 7):
+// lanes rr, rr + 8, rr + 16, rr + 24 of each warp, then the 8 warps
+__device__ __forceinline__ float rows8_sum(float v, float (*red)[8]) {
+  v += __shfl_xor_sync(0xffffffffu, v, 8);
+  v += __shfl_xor_sync(0xffffffffu, v, 16);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane < 8) red[w][lane] = v;
+  __syncthreads();
+  float s = 0.0f;
+  if (threadIdx.x < 8)
+    for (int k = 0; k < 8; ++k) s += red[k][threadIdx.x];
+  return s;
+}
+
+// A operand: dx_k = R_xy^T (x_f - c_f) - y'(segment), f = alist[k], for rows 8 g .. 8 g + 7
+// of the approximate list (block g), and |dx_k|^2 in Nx[k].  Thread (rr = tid & 7, pq =
+// tid >> 3) writes the 16-byte pieces pq, pq + 32, ... of row 8 g + rr: the 8 threads of
+// one piece index fill a whole 128-byte core matrix.
+__global__ void __launch_bounds__(256)
+pack_frames_kernel(const int* __restrict__ acount, const int* __restrict__ alist, const int* __restrict__ aseg,
+                   int seg_base, int N, int N16, const float* __restrict__ frames, const float4* __restrict__ c32,
+                   const double4* __restrict__ qxy, const float* __restrict__ Yc, uint8_t* __restrict__ Ap,
+                   float* __restrict__ Nx) {
+  __shared__ float red[8][8];
+  const int count = *acount;
+  const int g = blockIdx.x;
+  if (8 * g >= count) return;  // uniform over the block
+  const int tid = threadIdx.x, rr = tid & 7, pq = tid >> 3;
+  const int k = 8 * g + rr;
+  const bool live = k < count;
+  float R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float* x = frames;
+  const float* y = Yc;
+  if (live) {
+    const int f = alist[k];
+    const double4 qq = qxy[f];
+    const float qf[4] = {(float)qq.x, (float)qq.y, (float)qq.z, (float)qq.w};
+    quat_to_rot(qf, R);
+    c = c32[f];
+    x = frames + (size_t)f * N * 3;
+    y = Yc + (size_t)(aseg[k] - seg_base) * 3 * N;
+  }
+  const int K = 3 * N16, P = K / 8, nck = K / XM_KC;
+  uint8_t* tile = Ap + (size_t)(k / XM_ROWS) * nck * 2 * XM_A_PART;
+  const int r = k % XM_ROWS;
+  float nrm = 0.0f;
+  for (int pp = pq; pp < P && live; pp += 32) {
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int kk = 8 * pp + e, j = kk / 3, cc = kk - 3 * j;
+      float o = 0.0f;
+      if (j < N) {
+        const float v0 = x[3 * j] - c.x, v1 = x[3 * j + 1] - c.y, v2 = x[3 * j + 2] - c.z;
+        o = (R[cc] * v0 + R[3 + cc] * v1 + R[6 + cc] * v2) - y[3 * j + cc];
+      }
+      v[e] = o;
+      nrm = fmaf(o, o, nrm);
+    }
+    uint4 hi, lo;
+    xsplit8(v, hi, lo);
+    uint8_t* blk = tile + (size_t)(pp >> 1) * 2 * XM_A_PART;
+    *reinterpret_cast<uint4*>(blk + xpiece_off(r, pp)) = hi;
+    *reinterpret_cast<uint4*>(blk + XM_A_PART + xpiece_off(r, pp)) = lo;
+  }
+  const float s = rows8_sum(nrm, red);
+  if (tid < 8 && 8 * g + tid < count) Nx[8 * g + tid] = s;
+}
+
+// B operand: d_i = R_{a_i y(s)} a_i - y'(s) of segment slot s = blockIdx.y (segment
+// s0 + s; y is the prior structure for segment 0, else frame refresh_list[seg - 1]) for
+// landmarks 8 g .. 8 g + 7 (block g = blockIdx.x; landmarks >= M, up to the last column
+// tile's end, are written as zeros), |d_i|^2 in Nb[s * M + i], and y'(s) in Yc[s] (block 0).
+template <typename LT>
+__global__ void __launch_bounds__(256)
+pack_landmarks_kernel(int s0, int M, int N, int N16, int BN, int NT, const LT* __restrict__ lm,
+                      const float* __restrict__ lmoff, const float* __restrict__ Bseg,
+                      const float* __restrict__ frames, const float4* __restrict__ c32,
+                      const int* __restrict__ refresh_list, const float* __restrict__ prior, float4 prior_c,
+                      uint8_t* __restrict__ Bp, float* __restrict__ Nb, float* __restrict__ Yc) {
+  __shared__ float red[8][8];
+  const int g = blockIdx.x, slot = blockIdx.y, seg = s0 + slot;
+  const int tid = threadIdx.x, rr = tid & 7, pq = tid >> 3;
+  const int i = 8 * g + rr;
+  const bool live = i < M;
+  const float* y;
+  float4 c;
+  if (seg == 0) {
+    y = prior;
+    c = prior_c;
+  } else {
+    const int f = refresh_list[seg - 1];
+    y = frames + (size_t)f * 3 * N;
+    c = c32[f];
+  }
+  float R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  if (live) {
+    const float* B = Bseg + ((size_t)seg * M + i) * 9;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) R[e] = B[e];
+  }
+  const int K = 3 * N16, P = K / 8, nck = K / XM_KC;
+  const uint32_t bpart = (uint32_t)BN * XM_KC * 2;
+  uint8_t* tile = Bp + (((size_t)slot * NT + i / BN) * nck) * 2 * bpart;
+  const int r = i % BN;
+  const bool write_y = g == 0 && rr == 0;
+  float nrm = 0.0f;
+  for (int pp = pq; pp < P; pp += 32) {
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int kk = 8 * pp + e, j = kk / 3, cc = kk - 3 * j;
+      float o = 0.0f;
+      if (j < N) {
+        const float yv = y[3 * j + cc] - (cc == 0 ? c.x : (cc == 1 ? c.y : c.z));
+        if (write_y) Yc[(size_t)slot * 3 * N + kk] = yv;
+        if (live) {
+          const float a0 = lm_coord<float, LT>(lm, lmoff, N, i, j, 0);
+          const float a1 = lm_coord<float, LT>(lm, lmoff, N, i, j, 1);
+          const float a2 = lm_coord<float, LT>(lm, lmoff, N, i, j, 2);
+          o = (R[3 * cc] * a0 + R[3 * cc + 1] * a1 + R[3 * cc + 2] * a2) - yv;
+        }
+      }
+      v[e] = o;
+      nrm = fmaf(o, o, nrm);
+    }
+    uint4 hi, lo;
+    xsplit8(v, hi, lo);
+    uint8_t* blk = tile + (size_t)(pp >> 1) * 2 * bpart;
+    *reinterpret_cast<uint4*>(blk + xpiece_off(r, pp)) = hi;
+    *reinterpret_cast<uint4*>(blk + bpart + xpiece_off(r, pp)) = lo;
+  }
+  const float s = rows8_sum(nrm, red);
+  if (tid < 8 && 8 * g + tid < M) Nb[(size_t)slot * M + 8 * g + tid] = s;
+}
+
+struct XmmaArgs {
+  const int* alist;
+  const int* aseg;
+  const int* acount;
+  int seg_base, M, nck, BN, NT;
+  const uint8_t* Ap;
+  const uint8_t* Bp;
+  const float* Nx;
+  const float* Nb;
+  float dscale;
+  float* Dout;
+  unsigned* status;
+  long long wait_cycles;
+  int group;  // chunks per accumulator group (1..XM_GROUP_MAX)
+};
+
+// Tile (column tile blockIdx.x of BN landmarks, row tile blockIdx.y of 128 approximate
+// frames).  Warps 0-7 fold the accumulators and write D~ (warp w: tensor-memory lanes
+// 32 (w & 3) .. + 31, i.e. those rows, and column half w >> 2); warp 8 lane 0 moves the
+// operands; warp 9 lane 0 issues the MMAs.
+__global__ void __launch_bounds__(XM_THREADS, 1) approx_cross_mma(XmmaArgs p) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t full[XM_STAGES], empty[XM_STAGES], accf[2], acce[2], done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_seg[XM_ROWS], s_frame[XM_ROWS], s_run[XM_ROWS + 1];
+  __shared__ int s_nrun, s_fail, s_fail_run, s_issued;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n = blockIdx.x, t = blockIdx.y;
+  const int count = *p.acount;
+  const int row0 = t * XM_ROWS;
+  if (row0 >= count) return;  // uniform over the block, before any allocation
+  const int BN = p.BN, nck = p.nck;
+  const int G = p.group;
+  const int ngrp = (nck + G - 1) / G;
+  const uint32_t b_part = (uint32_t)BN * XM_KC * 2;
+  const uint32_t idesc = idesc_make(XM_ROWS, BN, 0u);  // kind::f16, F16 operands
+
+  if (warp == 0) tmem_alloc(&tmem_slot, XM_TMEM_COLS);
+  if (tid == 0) {
+    for (int s = 0; s < XM_STAGES; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&accf[b]), 1);
+      mbar_init(smem_u32(&acce[b]), XM_FOLD_WARPS);
+    }
+    mbar_init(smem_u32(&done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_fail = 0;
+    s_issued = 0;
+  }
+  if (tid < XM_ROWS) {
+    const int r = row0 + tid;
+    s_seg[tid] = r < count ? p.aseg[r] : -1;
+    s_frame[tid] = r < count ? p.alist[r] : -1;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  if (tid == 0) {  // runs of equal segment among the tile's rows
+    int nr = 0, k = 0;
+    while (k < XM_ROWS && s_seg[k] >= 0) {
+      s_run[nr++] = k;
+      int e = k;
+      while (e < XM_ROWS && s_seg[e] == s_seg[k]) ++e;
+      k = e;
+    }
+    s_run[nr] = k;
+    s_nrun = nr;
+  }
+  __syncthreads();
+  const int nrun = s_nrun;
+  const uint32_t sbase = smem_u32(smem);
+  const uint8_t* Ab = p.Ap + (size_t)t * nck * 2 * XM_A_PART;
+  // fold warps: lane quarter and column range
+  const int q = warp & 3;
+  const int cw = ((BN / 2) + 15) / 16 * 16;
+  const int col0 = (warp >> 2) ? cw : 0;
+  const int ncol = (warp >> 2) ? BN - cw : cw;
+
+  for (int run = 0; run < nrun; ++run) {
+    const int k = s_run[run], kend = s_run[run + 1];
+    const int slot = s_seg[k] - p.seg_base;
+    const uint8_t* Bb = p.Bp + (((size_t)slot * p.NT + n) * nck) * 2 * b_part;
+    const int g0 = run * nck;    // chunks before this run (stage / phase bookkeeping)
+    const int gg0 = run * ngrp;  // accumulator groups before this run
+    if (warp == XM_FOLD_WARPS) {
+      if (lane == 0) {  // copies
+        for (int c = 0; c < nck; ++c) {
+          const int g = g0 + c, st = g % XM_STAGES;
+          if (g >= XM_STAGES &&
+              !mbar_wait(smem_u32(&empty[st]), (uint32_t)((g / XM_STAGES - 1) & 1), p.wait_cycles)) {
+            s_fail = 1;
+            break;
+          }
+          const uint32_t dst = sbase + st * XM_STAGE_BYTES;
+          mbar_expect_tx(smem_u32(&full[st]), 2 * XM_A_PART + 2 * b_part);
+          bulk_g2s(dst, Ab + (size_t)c * 2 * XM_A_PART, 2 * XM_A_PART, smem_u32(&full[st]));
+          bulk_g2s(dst + 2 * XM_A_PART, Bb + (size_t)c * 2 * b_part, 2 * b_part, smem_u32(&full[st]));
+          s_issued = g + 1;
+        }
+      }
+      __syncwarp();
+    } else if (warp == XM_FOLD_WARPS + 1) {
+      if (lane == 0) {  // MMA issue
+        bool failed = false;
+        for (int gr = 0; gr < ngrp && !failed; ++gr) {
+          const int gg = gg0 + gr, buf = gg & 1;
+          // the fold of group gg - 2 has emptied this accumulator
+          if (gg >= 2 && !mbar_wait(smem_u32(&acce[buf]), (uint32_t)(((gg >> 1) - 1) & 1), p.wait_cycles)) {
+            s_fail = 1;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t acc = tmem + (uint32_t)(buf * XM_BN_MAX);
+          const int c0 = gr * G, c1 = min(nck, c0 + G);
+          for (int c = c0; c < c1; ++c) {
+            const int g = g0 + c, st = g % XM_STAGES;
+            if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((g / XM_STAGES) & 1), p.wait_cycles)) {
+              s_fail = 1;
+              failed = true;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t ah = sbase + st * XM_STAGE_BYTES, al = ah + XM_A_PART;
+            const uint32_t bh = ah + 2 * XM_A_PART, bl = bh + b_part;
+            const uint64_t dah = smem_desc(ah, 128, 256), dal = smem_desc(al, 128, 256);
+            const uint64_t dbh = smem_desc(bh, 128, 256), dbl = smem_desc(bl, 128, 256);
+            // the two small correction products first, the main product last: in a group of
+            // one chunk only its addition is rounded at the scale of the chunk's sum
+            mma_f16(acc, dah, dbl, idesc, c > c0 ? 1u : 0u);
+            mma_f16(acc, dal, dbh, idesc, 1u);
+            mma_f16(acc, dah, dbh, idesc, 1u);
+            mma_commit(smem_u32(&empty[st]));
+          }
+          if (!failed) mma_commit(smem_u32(&accf[buf]));
+        }
+        mma_commit(smem_u32(&done));  // once every MMA issued so far is complete
+      }
+      __syncwarp();
+    } else {  // fold warps
+      // Kahan totals of column pairs: sum and the correction (minus the lost low part),
+      // packed FP32 pairs so that each step of the fold is one instruction per two columns
+      f2 ksum[XM_BN_MAX / 4], kcor[XM_BN_MAX / 4];
+#pragma unroll
+      for (int e = 0; e < XM_BN_MAX / 4; ++e) ksum[e] = kcor[e] = 0ull;
+      const f2 one2 = f2_pack(1.0f, 1.0f), mone2 = f2_pack(-1.0f, -1.0f);
+      for (int gr = 0; gr < ngrp; ++gr) {
+        const int gg = gg0 + gr, buf = gg & 1;
+        bool ok = mbar_wait(smem_u32(&accf[buf]), (uint32_t)((gg >> 1) & 1), p.wait_cycles);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) {
+          if (lane == 0) s_fail = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * XM_BN_MAX + col0);
+#pragma unroll
+        for (int b = 0; b < XM_BN_MAX / 32; ++b) {
+          if (b * 16 < ncol) {
+            float v[16];
+            tmem_ld16(ta + b * 16, v);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              // y = v - cor; t = sum + y; cor = (t - sum) - y; sum = t (a - b as fma(b, -1, a),
+              // a + b as fma(a, 1, b): single roundings, as the scalar operations)
+              f2& sum = ksum[b * 8 + e];
+              f2& cor = kcor[b * 8 + e];
+              const f2 y = f2_fma(cor, mone2, f2_pack(v[2 * e], v[2 * e + 1]));
+              const f2 t2 = f2_fma(sum, one2, y);
+              cor = f2_fma(y, mone2, f2_fma(sum, mone2, t2));
+              sum = t2;
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&acce[buf]));
+      }
+      // rows of this run: D~ = (|dx|^2 + |d|^2 - 2 dx.d) / N (kernel units times dscale)
+      const int rrow = q * 32 + lane;
+      if (!s_fail && rrow >= k && rrow < kend) {
+        const int f = s_frame[rrow];
+        const float nx = p.Nx[row0 + rrow];
+        const float* nb = p.Nb + (size_t)slot * p.M;
+        float* out = p.Dout + (size_t)f * p.M;
+        const int i0 = n * BN + col0;
+#pragma unroll
+        for (int e2 = 0; e2 < XM_BN_MAX / 4; ++e2) {
+          float th[2], tl[2];
+          f2_unpack(ksum[e2], th[0], th[1]);
+          f2_unpack(kcor[e2], tl[0], tl[1]);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int e = 2 * e2 + h, i = i0 + e;
+            if (e < ncol && i < p.M)  // the compensated cross term sum - cor, its low part last
+              out[i] = (((nx + nb[i]) - 2.0f * XM_UNSCALE2 * th[h]) + 2.0f * XM_UNSCALE2 * tl[h]) * p.dscale;
+          }
+        }
+      }
+    }
+    const bool ok = mbar_wait(smem_u32(&done), (uint32_t)(run & 1), p.wait_cycles);
+    if (!ok) s_fail = 1;
+    __syncthreads();
+    if (s_fail) {
+      s_fail_run = run;  // every thread writes the same value
+      break;
+    }
+  }
+  if (s_fail) {
+    // copies and MMAs already issued still land in this CTA's memory: wait for them within
+    // the default budget before the tensor memory is released.  The MMA thread committed
+    // `done` after its last MMA of the failed run whether its loop ended or broke off.
+    if (tid == 0) atomicOr(p.status, STATUS_TIMEOUT);
+    if (tid == XM_FOLD_WARPS * 32) {
+      const int last = s_issued;
+      for (int g = std::max(0, last - XM_STAGES); g < last; ++g)
+        mbar_wait(smem_u32(&full[g % XM_STAGES]), (uint32_t)((g / XM_STAGES) & 1), XM_DRAIN_CYCLES);
+    }
+    mbar_wait(smem_u32(&done), (uint32_t)(s_fail_run & 1), XM_DRAIN_CYCLES);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, XM_TMEM_COLS);
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+XmmaShape xmma_shape(int M, int N) {
+  XmmaShape s;
+  const int K = 3 * round_up16(N);
+  s.nck = K / XM_KC;
+  s.NT = (M + XM_BN_MAX - 1) / XM_BN_MAX;
+  s.BN = ((M + s.NT - 1) / s.NT + 15) / 16 * 16;
+  s.a_bytes_per_tile = (size_t)s.nck * 2 * XM_A_PART;
+  s.b_bytes_per_seg = (size_t)s.NT * s.nck * 2 * ((size_t)s.BN * XM_KC * 2);
+  return s;
+}
+
+size_t xmma_a_bytes(const XmmaShape& sh, int napp) {
+  return (size_t)((napp + XM_ROWS - 1) / XM_ROWS) * sh.a_bytes_per_tile;
+}
+
+void launch_pack_landmarks(Prec p, int s0, int ns, const LandmarkDev& L, const XmmaShape& sh, const float* Bseg,
+                           const void* frames, FrameInfo fi, const int* refresh_list, const RefDesc& prior,
+                           uint8_t* Bp, float* Nb, float* Yc, cudaStream_t st) {
+  if (ns <= 0 || L.M <= 0) return;
+  const dim3 grid((sh.NT * sh.BN) / 8, ns);
+  const int N16 = round_up16(L.N);
+  if (p == P_F16)
+    pack_landmarks_kernel<__half><<<grid, 256, 0, st>>>(s0, L.M, L.N, N16, sh.BN, sh.NT, (const __half*)L.coords,
+                                                        L.off, Bseg, (const float*)frames, fi.c32, refresh_list,
+                                                        (const float*)prior.coords, prior.c32, Bp, Nb, Yc);
+  else
+    pack_landmarks_kernel<float><<<grid, 256, 0, st>>>(s0, L.M, L.N, N16, sh.BN, sh.NT, (const float*)L.coords,
+                                                       L.off, Bseg, (const float*)frames, fi.c32, refresh_list,
+                                                       (const float*)prior.coords, prior.c32, Bp, Nb, Yc);
+  note_launch();
+}
+
+void launch_pack_frames(int napp, const int* acount, const int* alist, const int* aseg, int seg_base,
+                        const LandmarkDev& L, const void* frames, FrameInfo fi, const double4* qxy, const float* Yc,
+                        uint8_t* Ap, float* Nx, cudaStream_t st) {
+  if (napp <= 0) return;
+  pack_frames_kernel<<<(napp + 7) / 8, 256, 0, st>>>(acount, alist, aseg, seg_base, L.N, round_up16(L.N),
+                                                     (const float*)frames, fi.c32, qxy, Yc, Ap, Nx);
+  note_launch();
+}
+
+void launch_approx_cross_mma(int napp, const int* alist, const int* aseg, const int* acount, int seg_base,
+                             const LandmarkDev& L, const XmmaShape& sh, const uint8_t* Ap, const uint8_t* Bp,
+                             const float* Nx, const float* Nb, float* D, unsigned* status, cudaStream_t st) {
+  if (napp <= 0 || L.M <= 0) return;
+  XmmaArgs a;
+  a.alist = alist;
+  a.aseg = aseg;
+  a.acount = acount;
+  a.seg_base = seg_base;
+  a.M = L.M;
+  a.nck = sh.nck;
+  a.BN = sh.BN;
+  a.NT = sh.NT;
+  a.Ap = Ap;
+  a.Bp = Bp;
+  a.Nx = Nx;
+  a.Nb = Nb;
+  a.dscale = (float)L.dscale;
+  a.Dout = D;
+  a.status = status;
+  a.wait_cycles = L.wait_cycles;
+  a.group = std::min(std::max(L.mma_group, 1), XM_GROUP_MAX);
+  const size_t smem = (size_t)XM_STAGES * XM_STAGE_BYTES;
+  cudaFuncSetAttribute(approx_cross_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int tiles = (napp + XM_ROWS - 1) / XM_ROWS;
+  const dim3 grid(sh.NT, tiles);
+  approx_cross_mma<<<grid, XM_THREADS, smem, st>>>(a);
+  note_launch();
+}
+
+}  // namespace pcv

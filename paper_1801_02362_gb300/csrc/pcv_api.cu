@@ -68,13 +68,13 @@ thread_local int64_t t_launches = 0;
 enum KernelId {
   K_PREP = 0, K_BAND, K_RECHECK, K_SCAN, K_CHUNK, K_FIRST, K_RECORDS, K_COMPACT, K_EXACT, K_APPROX,
   K_FINAL, K_ADJ_BETA, K_ADJ_FINISH, K_COMBINE, K_XY_REFINE, K_ADJ_BETA_SEG, K_MATERIALIZE, K_GAMMA, K_ADJ_MMA, K_SEG_MOMENTS,
-  K_NL_SCHEDULE, K_NL_SELECT, K_NL_PAIR, K_NL_BETA, K_COUNT
+  K_NL_SCHEDULE, K_NL_SELECT, K_NL_PAIR, K_NL_BETA, K_APPROX_MMA, K_COUNT
 };
 const char* const kKernelNames[PCV_PROFILE_KERNELS] = {
     "frame_prep", "align_band", "recheck_fp64", "band_scan", "align_chunk", "first_exceed", "records",
     "compact", "exact_pair", "approx_pair", "finalize", "adjoint_beta_pair", "adjoint_finish", "combine_grad", "xy_refine",
     "adjoint_beta_seg", "materialize", "gamma", "adjoint_beta_mma", "seg_moments", "nl_schedule", "nl_select",
-    "nl_pair", "nl_beta"};
+    "nl_pair", "nl_beta", "approx_pair_mma"};
 static_assert(K_COUNT <= PCV_PROFILE_KERNELS, "profiler table");
 
 struct ProfEvent {
@@ -91,6 +91,7 @@ void note_launch(int n) { t_launches += n; }
 struct pcv_ctx {
   int device = 0;
   int newton_cap = 60;                  // PCV_OPT_NEWTON_CAP
+  int mma_group = 2;                    // PCV_OPT_MMA_GROUP
   long long wait_cycles = 4000000000LL;  // PCV_OPT_WAIT_CYCLES
   cudaStream_t stream = nullptr;
   Prec prec = P_F32;
@@ -126,6 +127,7 @@ struct pcv_ctx {
   DevBuf c32, c64, fG, bandD, bandQ, bandF, chD, chQ, chF, rlist, rcount, recF, recRef, recD, recQ, reflist,
       segof, alist, aseg, Dbuf, Rpair, Bseg, mstat, status, nrecheck, small;
   DevBuf Xr, Bm, GSb, GZb;  // materialised x', b and the gamma rows
+  DevBuf Apk, Bpk;          // the same deviations packed for the tensor cores (FP16 h + l)
   DevBuf Nx, Nb, Yc, Gsum;       // |dx|^2, |d|^2, centred close structures, Gamma sums
   DevBuf Amma, Bmma;              // tensor-core adjoint operands
   DevBuf S6;                      // per-segment landmark moments R A R^T of the finish
@@ -254,6 +256,7 @@ LandmarkDev lm_view(const pcv_ctx* c) {
   L.wa64 = c->split_w ? (const double*)c->wa64.p : nullptr;
   L.newton_cap = c->newton_cap;
   L.wait_cycles = c->wait_cycles;
+  L.mma_group = c->mma_group;
   return L;
 }
 
@@ -321,7 +324,7 @@ pcv_status pcv_destroy(pcv_ctx* c) {
                     &c->wa64, &c->y, &c->Bprior, &c->c32, &c->c64,
                     &c->fG, &c->bandD, &c->bandQ, &c->bandF, &c->chD, &c->chQ, &c->chF, &c->rlist, &c->rcount,
                     &c->recF, &c->recRef, &c->recD, &c->recQ, &c->reflist, &c->segof, &c->alist, &c->aseg,
-                    &c->Dbuf, &c->Rpair, &c->Bseg, &c->Xr, &c->Bm, &c->GSb, &c->GZb, &c->Nx, &c->Nb, &c->Yc, &c->Gsum, &c->Amma, &c->Bmma, &c->S6, &c->mstat, &c->status, &c->nrecheck, &c->small, &c->h_frames,
+                    &c->Dbuf, &c->Rpair, &c->Bseg, &c->Xr, &c->Bm, &c->Apk, &c->Bpk, &c->GSb, &c->GZb, &c->Nx, &c->Nb, &c->Yc, &c->Gsum, &c->Amma, &c->Bmma, &c->S6, &c->mstat, &c->status, &c->nrecheck, &c->small, &c->h_frames,
                     &c->h_s, &c->h_z, &c->h_gs, &c->h_gz, &c->h_msd, &c->h_ref, &c->grp_inst, &c->grp_tiles,
                     &c->nl_keep, &c->nlSlot, &c->nlUpd, &c->nlU, &c->nlUA, &c->nlUAseg, &c->nlN, &c->NLtab,
                     &c->Rupd, &c->Rnl, &c->nlTiles, &c->nlPart, &c->betaPart};
@@ -406,6 +409,10 @@ pcv_status pcv_set_option(pcv_ctx* c, int key, int64_t value) {
     case PCV_OPT_WAIT_CYCLES:
       if (value < 0 || value > 4000000000LL) return fail(c, PCV_EINVAL, "wait budget must be in 0..4e9 cycles");
       c->wait_cycles = value == 0 ? 4000000000LL : (long long)value;
+      return PCV_OK;
+    case PCV_OPT_MMA_GROUP:
+      if (value < 1 || value > 8) return fail(c, PCV_EINVAL, "MMA group must be in 1..8");
+      c->mma_group = (int)value;
       return PCV_OK;
     case PCV_OPT_EXACT_TILE:
     case PCV_OPT_APPROX_TILE:
@@ -835,10 +842,15 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
   const bool seg_form = (int64_t)(nref + 1) * 16 <= (int64_t)F && !nl;
   const int seg_base = had_prior ? 0 : 1;  // without a prior structure segment 0 is empty
   const int nseg = nref + 1 - seg_base;
-  bool tiled = false, mma = false;
+  bool tiled = false, mma = false, xmma = false;
   const MmaShape msh = mma_shape(F, M, c->N);
+  const XmmaShape xsh = xmma_shape(M, c->N);
   if (c->prec != P_F64 && c->uniform && !c->split_w && seg_form && nseg > 0) {
-    const size_t xb = tile_bytes_frames(napp, c->N), bb = tile_bytes_landmarks(nseg, M, c->N);
+    // with the tensor cores the deviations are packed for the MMAs (FP16 h + l), else
+    // stored as FP32 rows for the CUDA-core tiles
+    xmma = c->tensor_cores;
+    const size_t xb = xmma ? xmma_a_bytes(xsh, napp) : tile_bytes_frames(napp, c->N);
+    const size_t bb = xmma ? xsh.b_bytes_per_seg * (size_t)nseg : tile_bytes_landmarks(nseg, M, c->N);
     const size_t nb = sizeof(float) * ((size_t)napp + (size_t)nseg * M + (size_t)nseg * 3 * c->N + 2 * (size_t)F);
     const size_t gb = grads ? tile_bytes_gamma(F, M) : 0;  // per gamma kind
     const size_t mb = msh.a_bytes + msh.b_bytes_per_seg * nseg;
@@ -846,7 +858,9 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
     if ((int64_t)(xb + bb + nb + (mma ? mb : 2 * gb)) <= c->mat_cap) {
       // the materialised operands are an optimisation: when the device cannot hold them the
       // kernels that rotate while staging take over
-      bool ok = ensure(c, c->Xr, xb) == PCV_OK && ensure(c, c->Bm, bb) == PCV_OK &&
+      DevBuf& xbuf = xmma ? c->Apk : c->Xr;
+      DevBuf& bbuf = xmma ? c->Bpk : c->Bm;
+      bool ok = ensure(c, xbuf, xb) == PCV_OK && ensure(c, bbuf, bb) == PCV_OK &&
                 ensure(c, c->Nx, sizeof(float) * (size_t)napp) == PCV_OK &&
                 ensure(c, c->Nb, sizeof(float) * (size_t)nseg * M) == PCV_OK &&
                 ensure(c, c->Yc, sizeof(float) * 3 * (size_t)c->N * nseg) == PCV_OK &&
@@ -858,12 +872,14 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
       if (ok) {
         tiled = true;
       } else {
-        for (DevBuf* b : {&c->Xr, &c->Bm, &c->Amma, &c->Bmma, &c->GSb, &c->GZb}) release(*b);
+        for (DevBuf* b : {&c->Xr, &c->Bm, &c->Apk, &c->Bpk, &c->Amma, &c->Bmma, &c->GSb, &c->GZb}) release(*b);
         c->err = "no error";
         mma = false;
+        xmma = false;
       }
     } else {
       mma = false;
+      xmma = false;
     }
   }
   {
@@ -871,7 +887,17 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
     launch_exact_pairs(c->prec, nref, (const int*)c->reflist.p, nullptr, frames, L, fi, c->Dbuf.p, Bseg1,
                        (unsigned*)c->status.p, st);
   }
-  if (tiled) {
+  if (tiled && xmma) {
+    PROF(c, K_MATERIALIZE);
+    launch_pack_landmarks(c->prec, seg_base, nseg, L, xsh, (const float*)c->Bseg.p, frames, fi,
+                          (const int*)c->reflist.p, prior, (uint8_t*)c->Bpk.p, (float*)c->Nb.p, (float*)c->Yc.p, st);
+    if (mma)
+      launch_delta_split(c->prec, seg_base, nseg, L, msh, (const float*)c->Bseg.p, frames, fi,
+                         (const int*)c->reflist.p, prior, (float*)c->Bmma.p, (float*)c->Yc.p, st);
+    launch_xy_refine(c->prec, F, frames, L, fi, prior, rec, st);
+    launch_pack_frames(napp, &sm->approx_count, (const int*)c->alist.p, (const int*)c->aseg.p, seg_base, L, frames,
+                       fi, rec.qxy, (const float*)c->Yc.p, (uint8_t*)c->Apk.p, (float*)c->Nx.p, st);
+  } else if (tiled) {
     PROF(c, K_MATERIALIZE);
     launch_materialize_landmarks(c->prec, seg_base, nseg, L, (const float*)c->Bseg.p, frames, fi,
                                  (const int*)c->reflist.p, prior, (float*)c->Bm.p, (float*)c->Nb.p, (float*)c->Yc.p, st);
@@ -924,6 +950,11 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
     PROF(c, K_NL_PAIR);
     launch_nl_approx(c->prec, nl_between, nll, (const int*)c->NLtab.p, Mnl, frames, L, fi, rec.qxy, c->Bseg.p,
                      (const int*)c->segof.p, c->Dbuf.p, st);
+  } else if (xmma) {
+    PROF(c, K_APPROX_MMA);
+    launch_approx_cross_mma(napp, (const int*)c->alist.p, (const int*)c->aseg.p, &sm->approx_count, seg_base, L, xsh,
+                            (const uint8_t*)c->Apk.p, (const uint8_t*)c->Bpk.p, (const float*)c->Nx.p,
+                            (const float*)c->Nb.p, (float*)c->Dbuf.p, (unsigned*)c->status.p, st);
   } else {
     PROF(c, K_APPROX);
     if (tiled)

@@ -35,6 +35,9 @@ struct LandmarkDev {
   // bounded wait in the tensor-core kernels (cycles)
   int newton_cap = 60;
   long long wait_cycles = 4000000000LL;
+  // chunks of 16 deviation components the tensor-core MSD kernel sums in tensor memory
+  // before folding them into its FP32 totals
+  int mma_group = 2;
 };
 // FP16 storage keeps, per landmark and block of 16 consecutive atoms, an FP32 offset (the
 // block's mean centred coordinate) and the FP16 residuals: coordinate = offset + residual
@@ -246,6 +249,32 @@ void launch_approx_pairs_tile(int napp, const int* alist, const int* aseg, const
 void launch_adjoint_beta_tile(int F, const LandmarkDev& L, int seg_base, const float* GS, const float* GZ,
                               const float* Bm, const float* Gsum, const float* Yc, const int* seg_of_frame, float* gs,
                               float* gz, cudaStream_t st);
+
+// ---------------------------------------------------------------------------------------
+// approximate MSDs on the tensor cores (k_xmma.cu; FP32 and FP16-storage modes, uniform
+// weights, materialised deviations): packed FP16 h + l operands, kind::f16 MMAs.
+struct XmmaShape {
+  int nck = 0, BN = 0, NT = 0;   // chunks of 16 components, landmark tile width, landmark tiles
+  size_t a_bytes_per_tile = 0;   // packed frames, per tile of 128 approximate frames
+  size_t b_bytes_per_seg = 0;    // packed landmarks, per segment
+};
+XmmaShape xmma_shape(int M, int N);
+size_t xmma_a_bytes(const XmmaShape& sh, int napp);
+// d_i = R_{a_i y} a_i - y' of segment slots [0, ns) (segments s0 + slot) packed into Bp,
+// |d_i|^2 (Nb, ns*M floats), y' (Yc, ns*3N floats)
+void launch_pack_landmarks(Prec p, int s0, int ns, const LandmarkDev& L, const XmmaShape& sh, const float* Bseg,
+                           const void* frames, FrameInfo fi, const int* refresh_list, const RefDesc& prior,
+                           uint8_t* Bp, float* Nb, float* Yc, cudaStream_t st);
+// dx_k = R_xy^T (x - c) - y' of approximate frames k < *acount packed into Ap, |dx_k|^2 (Nx);
+// after launch_pack_landmarks (y') and with the frames' R_xy in qxy
+void launch_pack_frames(int napp, const int* acount, const int* alist, const int* aseg, int seg_base,
+                        const LandmarkDev& L, const void* frames, FrameInfo fi, const double4* qxy, const float* Yc,
+                        uint8_t* Ap, float* Nx, cudaStream_t st);
+// D~ of every approximate frame and landmark from the packed operands (STATUS_TIMEOUT in
+// *status if a bounded wait expired)
+void launch_approx_cross_mma(int napp, const int* alist, const int* aseg, const int* acount, int seg_base,
+                             const LandmarkDev& L, const XmmaShape& sh, const uint8_t* Ap, const uint8_t* Bp,
+                             const float* Nx, const float* Nb, float* D, unsigned* status, cudaStream_t st);
 
 // ---------------------------------------------------------------------------------------
 // tensor-core segment adjoint (k_mma.cu; FP32 and FP16-storage modes, uniform weights)

@@ -22,8 +22,8 @@ PCV_OPT_BAND, PCV_OPT_CHUNK, PCV_OPT_EXACT_TILE, PCV_OPT_APPROX_TILE, PCV_OPT_PR
 PCV_OPT_MATERIALIZE = 6
 PCV_OPT_TENSOR_CORES = 7
 PCV_OPT_HOST_CHUNKS, PCV_OPT_HOST_END_SHARE = 8, 9
-PCV_OPT_NEWTON_CAP, PCV_OPT_WAIT_CYCLES = 10, 11
-PCV_PROFILE_KERNELS = 24
+PCV_OPT_NEWTON_CAP, PCV_OPT_WAIT_CYCLES, PCV_OPT_MMA_GROUP = 10, 11, 12
+PCV_PROFILE_KERNELS = 25
 
 _STATUS_NAMES = {0: "PCV_OK", -1: "PCV_EINVAL", -2: "PCV_ECUDA", -3: "PCV_ENOMEM", -4: "PCV_ENOCONV",
                  -5: "PCV_ESTATE", -6: "PCV_ETIMEOUT"}

@@ -227,6 +227,7 @@ def test_close_materialized_operands(pcv, precision, n, m, variant):
     ctx.close()
     assert ("materialize" in prof) == (cap is None), prof
     assert ("adjoint_beta_mma" in prof) == (variant == "tensor_cores"), prof
+    assert ("approx_pair_mma" in prof) == (variant == "tensor_cores"), prof
     np.testing.assert_array_equal(np.concatenate([p["refreshed"] for p in parts]), r["refreshed"])
     g = {k: np.concatenate([p[k] for p in parts]) for k in ("s", "z", "msd", "dsdx", "dzdx")}
     check_values(g, r, fr, lm, lam, precision)
