@@ -109,17 +109,20 @@ __global__ void gamma_split_kernel(int F, int Fp, int M, int Kp, const float* __
 
 // deviation operand: for segment slot s (segment seg_base + s), column tile nt (BN values of
 // n = 3j + c) and K chunk c, blocks hi | lo of BN rows x 16 values holding
-// delta_i[n] = b_i[n] - y'[n].  The buffer is zeroed beforehand (rows n >= 3N, landmarks
-// >= M).  Block (i, s) also writes y'[s][n] when i == 0.  y is the prior structure for
-// segment 0, else the frame refresh_list[seg - 1].
+// delta_i[n] = b_i[n] - y'[n].  A thread handles four consecutive landmarks 4g .. 4g + 3
+// (block g) at atom j: per component n = 3j + c one 16-byte core-matrix row of each part
+// (the four landmarks are consecutive along K).  Rows n >= 3N up to the last column tile's
+// end and landmarks >= M up to Kp are written as zeros, so the buffer needs no clearing.
+// Block (g = 0, s) also writes y'[s][n].  y is the prior structure for segment 0, else the
+// frame refresh_list[seg - 1].
 template <typename LT>
 __global__ void delta_split_kernel(int seg_base, int M, int N, int Kp, int BN, int NT, const LT* __restrict__ lm,
                                    const float* __restrict__ lmoff, const float* __restrict__ Bseg, const float* __restrict__ frames,
                                    const float4* __restrict__ c32, const int* __restrict__ refresh_list,
                                    const float* __restrict__ prior, float4 prior_c, float* __restrict__ B,
                                    float* __restrict__ Yc) {
-  const int i = blockIdx.x, slot = blockIdx.y, seg = seg_base + slot;
-  const int NB = 3 * N;
+  const int g = blockIdx.x, slot = blockIdx.y, seg = seg_base + slot;
+  const int NB = 3 * N, NR = NT * BN;
   const int nck = Kp / MM_KC;
   const float* y;
   float4 c;
@@ -131,27 +134,49 @@ __global__ void delta_split_kernel(int seg_base, int M, int N, int Kp, int BN, i
     y = frames + (size_t)f * NB;
     c = c32[f];
   }
-  float R[9];
+  float R[4][9];
 #pragma unroll
-  for (int e = 0; e < 9; ++e) R[e] = Bseg[((size_t)seg * M + i) * 9 + e];
+  for (int u = 0; u < 4; ++u) {
+    const int i = 4 * g + u;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) R[u][e] = i < M ? Bseg[((size_t)seg * M + i) * 9 + e] : 0.0f;
+  }
   const size_t bblk = (size_t)BN * MM_KC * 4;  // bytes of one part of one block
-  const int ck = i / MM_KC, kk = i % MM_KC;
-  for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    const float yv[3] = {y[3 * j] - c.x, y[3 * j + 1] - c.y, y[3 * j + 2] - c.z};
-    const float a0 = lm_coord<float, LT>(lm, lmoff, N, i, j, 0);
-    const float a1 = lm_coord<float, LT>(lm, lmoff, N, i, j, 1);
-    const float a2 = lm_coord<float, LT>(lm, lmoff, N, i, j, 2);
-    const float d[3] = {(R[0] * a0 + R[1] * a1 + R[2] * a2) - yv[0], (R[3] * a0 + R[4] * a1 + R[5] * a2) - yv[1],
-                        (R[6] * a0 + R[7] * a1 + R[8] * a2) - yv[2]};
+  const int ck = (4 * g) / MM_KC, kk0 = (4 * g) % MM_KC;
+  uint8_t* slot_base = reinterpret_cast<uint8_t*>(B) + ((size_t)slot * NT * nck + ck) * 2 * bblk;
+  for (int j = threadIdx.x; 3 * j < NR; j += blockDim.x) {
+    const bool atom = j < N;
+    float yv[3] = {0.0f, 0.0f, 0.0f}, a[4][3];
+    if (atom) {
+      yv[0] = y[3 * j] - c.x;
+      yv[1] = y[3 * j + 1] - c.y;
+      yv[2] = y[3 * j + 2] - c.z;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = 4 * g + u;
+      const bool live = atom && i < M;
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) a[u][cc] = live ? lm_coord<float, LT>(lm, lmoff, N, i, j, cc) : 0.0f;
+    }
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) {
       const int n = 3 * j + cc;
+      if (n >= NR) break;
+      float h[4], l[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool live = atom && 4 * g + u < M;
+        const float d = live ? (R[u][3 * cc] * a[u][0] + R[u][3 * cc + 1] * a[u][1] + R[u][3 * cc + 2] * a[u][2]) - yv[cc]
+                             : 0.0f;
+        h[u] = tf32_hi(d);
+        l[u] = tf32_hi(d - h[u]);
+      }
       const int nt = n / BN, r = n % BN;
-      uint8_t* blk = reinterpret_cast<uint8_t*>(B) + (((size_t)slot * NT + nt) * nck + ck) * 2 * bblk;
-      const float h = tf32_hi(d[cc]);
-      *reinterpret_cast<float*>(blk + canon_off(r, kk)) = h;
-      *reinterpret_cast<float*>(blk + bblk + canon_off(r, kk)) = tf32_hi(d[cc] - h);
-      if (i == 0) Yc[(size_t)slot * NB + n] = yv[cc];
+      uint8_t* blk = slot_base + (size_t)nt * nck * 2 * bblk;
+      *reinterpret_cast<float4*>(blk + canon_off(r, kk0)) = make_float4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<float4*>(blk + bblk + canon_off(r, kk0)) = make_float4(l[0], l[1], l[2], l[3]);
+      if (g == 0 && atom) Yc[(size_t)slot * NB + n] = yv[cc];
     }
   }
 }
@@ -382,8 +407,7 @@ void launch_delta_split(Prec p, int seg_base, int nseg, const LandmarkDev& L, co
                         const void* frames, FrameInfo fi, const int* refresh_list, const RefDesc& prior, float* B,
                         float* Yc, cudaStream_t st) {
   if (nseg <= 0 || L.M <= 0) return;
-  cudaMemsetAsync(B, 0, sh.b_bytes_per_seg * nseg, st);
-  const dim3 grid(L.M, nseg);
+  const dim3 grid(sh.Kp / 4, nseg);
   if (p == P_F16)
     delta_split_kernel<__half><<<grid, 128, 0, st>>>(seg_base, L.M, L.N, sh.Kp, sh.BN, sh.NT, (const __half*)L.coords,
                                                      L.off, Bseg, (const float*)frames, fi.c32, refresh_list,
