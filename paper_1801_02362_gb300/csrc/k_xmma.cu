@@ -22,12 +22,13 @@
 // Operands are packed once per step in the canonical K-major layout without swizzling
 // (core matrices of 8 rows x 8 halves = 128 contiguous bytes; LBO 128 B along K, SBO 256 B
 // between 8-row groups): per chunk of 16 components a block of rows x 16 holding the h part
-// then the l part.  A (approximate frames) is tiled in 128 consecutive rows of the
-// approximate list, B (landmarks) per segment in column tiles of BN landmarks.  One thread
-// moves a stage (A block and B block) with two cp.async.bulk copies counted on an
-// mbarrier; one thread issues the MMAs; tcgen05.commit releases a stage, and marks an
-// accumulator full.  A tile whose frames span several segments takes them as runs, each a
-// full pass over K with its segment's landmarks.  Every wait is bounded by the context's
+// then the l part.  A (approximate frames) is tiled per segment: the approximate frames of
+// a segment (consecutive in the approximate list) fill tiles of up to 128 rows, listed by
+// xmma_tiles_kernel; B (landmarks) per segment in column tiles of BN landmarks.  So every
+// tile is one segment's product and takes one pass over K.  One thread moves a stage (A
+// block and B block) with two cp.async.bulk copies counted on an mbarrier; one thread
+// issues the MMAs; tcgen05.commit releases a stage, and marks an accumulator full.  Every
+// wait is bounded by the context's
 // clock budget; on expiry the kernel records STATUS_TIMEOUT, waits for its own copies and
 // MMAs within the default budget, frees its tensor memory and returns.
 #include <cuda_fp16.h>
@@ -92,15 +93,76 @@ __device__ __forceinline__ float rows8_sum(float v, float (*red)[8]) {
   return s;
 }
 
+// Tiles of the approximate frames, per segment: segment slot s holds the rows
+// [first_s, first_s + n_s) of the approximate list (aseg is non-decreasing), which fill
+// ceil(n_s / 128) tiles numbered from tile_start[s].  One block: binary searches for the
+// ranges, then an exclusive scan of the tile counts over the slots.
+constexpr int XT_THREADS = 1024;
+__global__ void __launch_bounds__(XT_THREADS)
+xmma_tiles_kernel(const int* __restrict__ acount, const int* __restrict__ aseg, int seg_base, int nseg,
+                  int* __restrict__ seg_first, int* __restrict__ tile_start, XTile* __restrict__ tiles,
+                  int* __restrict__ ntiles) {
+  __shared__ int scan[XT_THREADS];
+  __shared__ int s_carry;
+  const int count = *acount, tid = threadIdx.x;
+  if (tid == 0) s_carry = 0;
+  __syncthreads();
+  for (int s0 = 0; s0 < nseg; s0 += XT_THREADS) {
+    const int slot = s0 + tid;
+    int first = 0, n = 0;
+    if (slot < nseg) {
+      const int seg = seg_base + slot;
+      int lo = 0, hi = count;  // lower bound of seg
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (aseg[mid] < seg) lo = mid + 1; else hi = mid;
+      }
+      first = lo;
+      hi = count;  // lower bound of seg + 1
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (aseg[mid] < seg + 1) lo = mid + 1; else hi = mid;
+      }
+      n = lo - first;
+    }
+    const int nt = (n + XM_ROWS - 1) / XM_ROWS;
+    scan[tid] = nt;
+    __syncthreads();
+    for (int off = 1; off < XT_THREADS; off <<= 1) {  // inclusive scan
+      const int v = tid >= off ? scan[tid - off] : 0;
+      __syncthreads();
+      scan[tid] += v;
+      __syncthreads();
+    }
+    const int t0 = s_carry + scan[tid] - nt;
+    if (slot < nseg) {
+      seg_first[slot] = first;
+      tile_start[slot] = t0;
+      for (int q = 0; q < nt; ++q) {
+        XTile tl;
+        tl.slot = slot;
+        tl.k0 = first + q * XM_ROWS;
+        tl.k1 = min(first + n, tl.k0 + XM_ROWS);
+        tiles[t0 + q] = tl;
+      }
+    }
+    __syncthreads();
+    if (tid == XT_THREADS - 1) s_carry += scan[tid];
+    __syncthreads();
+  }
+  if (tid == 0) *ntiles = s_carry;
+}
+
 // A operand: dx_k = R_xy^T (x_f - c_f) - y'(segment), f = alist[k], for rows 8 g .. 8 g + 7
-// of the approximate list (block g), and |dx_k|^2 in Nx[k].  Thread (rr = tid & 7, pq =
-// tid >> 3) writes the 16-byte pieces pq, pq + 32, ... of row 8 g + rr: the 8 threads of
-// one piece index fill a whole 128-byte core matrix.
+// of the approximate list (block g), and |dx_k|^2 in Nx[k].  Row k of segment slot s goes
+// to tile tile_start[s] + (k - first_s) / 128, row (k - first_s) % 128.  Thread (rr = tid &
+// 7, pq = tid >> 3) writes the 16-byte pieces pq, pq + 32, ... of row 8 g + rr: the 8
+// threads of one piece index fill a whole 128-byte core matrix (rows of one segment).
 __global__ void __launch_bounds__(256)
 pack_frames_kernel(const int* __restrict__ acount, const int* __restrict__ alist, const int* __restrict__ aseg,
                    int seg_base, int N, int N16, const float* __restrict__ frames, const float4* __restrict__ c32,
-                   const double4* __restrict__ qxy, const float* __restrict__ Yc, uint8_t* __restrict__ Ap,
-                   float* __restrict__ Nx) {
+                   const double4* __restrict__ qxy, const float* __restrict__ Yc, const int* __restrict__ seg_first,
+                   const int* __restrict__ tile_start, uint8_t* __restrict__ Ap, float* __restrict__ Nx) {
   __shared__ float red[8][8];
   const int count = *acount;
   const int g = blockIdx.x;
@@ -122,8 +184,13 @@ pack_frames_kernel(const int* __restrict__ acount, const int* __restrict__ alist
     y = Yc + (size_t)(aseg[k] - seg_base) * 3 * N;
   }
   const int K = 3 * N16, P = K / 8, nck = K / XM_KC;
-  uint8_t* tile = Ap + (size_t)(k / XM_ROWS) * nck * 2 * XM_A_PART;
-  const int r = k % XM_ROWS;
+  int ti = 0, r = 0;
+  if (live) {
+    const int slot = aseg[k] - seg_base, off = k - seg_first[slot];
+    ti = tile_start[slot] + off / XM_ROWS;
+    r = off % XM_ROWS;
+  }
+  uint8_t* tile = Ap + (size_t)ti * nck * 2 * XM_A_PART;
   float nrm = 0.0f;
   for (int pp = pq; pp < P && live; pp += 32) {
     float v[8];
@@ -217,9 +284,9 @@ pack_landmarks_kernel(int s0, int M, int N, int N16, int BN, int NT, const LT* _
 
 struct XmmaArgs {
   const int* alist;
-  const int* aseg;
-  const int* acount;
-  int seg_base, M, nck, BN, NT;
+  const XTile* tiles;
+  const int* ntiles;
+  int M, nck, BN, NT;
   const uint8_t* Ap;
   const uint8_t* Bp;
   const float* Nx;
@@ -231,22 +298,22 @@ struct XmmaArgs {
   int group;  // chunks per accumulator group (1..XM_GROUP_MAX)
 };
 
-// Tile (column tile blockIdx.x of BN landmarks, row tile blockIdx.y of 128 approximate
-// frames).  Warps 0-7 fold the accumulators and write D~ (warp w: tensor-memory lanes
+// Tile (column tile blockIdx.x of BN landmarks, row tile blockIdx.y: entry blockIdx.y of
+// the per-segment tile list, up to 128 approximate frames of one segment).  Warps 0-7 fold the accumulators and write D~ (warp w: tensor-memory lanes
 // 32 (w & 3) .. + 31, i.e. those rows, and column half w >> 2); warp 8 lane 0 moves the
 // operands; warp 9 lane 0 issues the MMAs.
 __global__ void __launch_bounds__(XM_THREADS, 1) approx_cross_mma(XmmaArgs p) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t full[XM_STAGES], empty[XM_STAGES], accf[2], acce[2], done;
   __shared__ uint32_t tmem_slot;
-  __shared__ int s_seg[XM_ROWS], s_frame[XM_ROWS], s_run[XM_ROWS + 1];
-  __shared__ int s_nrun, s_fail, s_fail_run, s_issued;
+  __shared__ int s_frame[XM_ROWS];
+  __shared__ int s_fail, s_fail_run, s_issued;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n = blockIdx.x, t = blockIdx.y;
-  const int count = *p.acount;
-  const int row0 = t * XM_ROWS;
-  if (row0 >= count) return;  // uniform over the block, before any allocation
+  if (t >= *p.ntiles) return;  // uniform over the block, before any allocation
+  const XTile tl = p.tiles[t];
+  const int row0 = tl.k0, nrows = tl.k1 - tl.k0;
   const int BN = p.BN, nck = p.nck;
   const int G = p.group;
   const int ngrp = (nck + G - 1) / G;
@@ -268,28 +335,12 @@ __global__ void __launch_bounds__(XM_THREADS, 1) approx_cross_mma(XmmaArgs p) {
     s_fail = 0;
     s_issued = 0;
   }
-  if (tid < XM_ROWS) {
-    const int r = row0 + tid;
-    s_seg[tid] = r < count ? p.aseg[r] : -1;
-    s_frame[tid] = r < count ? p.alist[r] : -1;
-  }
+  if (tid < XM_ROWS) s_frame[tid] = tid < nrows ? p.alist[row0 + tid] : -1;
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
-  if (tid == 0) {  // runs of equal segment among the tile's rows
-    int nr = 0, k = 0;
-    while (k < XM_ROWS && s_seg[k] >= 0) {
-      s_run[nr++] = k;
-      int e = k;
-      while (e < XM_ROWS && s_seg[e] == s_seg[k]) ++e;
-      k = e;
-    }
-    s_run[nr] = k;
-    s_nrun = nr;
-  }
-  __syncthreads();
-  const int nrun = s_nrun;
+  const int nrun = 1;  // the tile's rows share one segment: one pass over K
   const uint32_t sbase = smem_u32(smem);
   const uint8_t* Ab = p.Ap + (size_t)t * nck * 2 * XM_A_PART;
   // fold warps: lane quarter and column range
@@ -299,8 +350,8 @@ __global__ void __launch_bounds__(XM_THREADS, 1) approx_cross_mma(XmmaArgs p) {
   const int ncol = (warp >> 2) ? BN - cw : cw;
 
   for (int run = 0; run < nrun; ++run) {
-    const int k = s_run[run], kend = s_run[run + 1];
-    const int slot = s_seg[k] - p.seg_base;
+    const int k = 0, kend = nrows;
+    const int slot = tl.slot;
     const uint8_t* Bb = p.Bp + (((size_t)slot * p.NT + n) * nck) * 2 * b_part;
     const int g0 = run * nck;    // chunks before this run (stage / phase bookkeeping)
     const int gg0 = run * ngrp;  // accumulator groups before this run
@@ -401,7 +452,7 @@ __global__ void __launch_bounds__(XM_THREADS, 1) approx_cross_mma(XmmaArgs p) {
       const int rrow = q * 32 + lane;
       if (!s_fail && rrow >= k && rrow < kend) {
         const int f = s_frame[rrow];
-        const float nx = p.Nx[row0 + rrow];
+        const float nx = p.Nx[row0 + rrow];  // rows of the approximate list
         const float* nb = p.Nb + (size_t)slot * p.M;
         float* out = p.Dout + (size_t)f * p.M;
         const int i0 = n * BN + col0;
@@ -461,8 +512,16 @@ XmmaShape xmma_shape(int M, int N) {
   return s;
 }
 
-size_t xmma_a_bytes(const XmmaShape& sh, int napp) {
-  return (size_t)((napp + XM_ROWS - 1) / XM_ROWS) * sh.a_bytes_per_tile;
+int xmma_max_tiles(int napp, int nseg) { return (napp + XM_ROWS - 1) / XM_ROWS + nseg; }
+
+size_t xmma_a_bytes(const XmmaShape& sh, int napp, int nseg) {
+  return (size_t)xmma_max_tiles(napp, nseg) * sh.a_bytes_per_tile;
+}
+
+void launch_xmma_tiles(const int* acount, const int* aseg, int seg_base, int nseg, int* seg_first, int* tile_start,
+                       XTile* tiles, int* ntiles, cudaStream_t st) {
+  xmma_tiles_kernel<<<1, XT_THREADS, 0, st>>>(acount, aseg, seg_base, nseg, seg_first, tile_start, tiles, ntiles);
+  note_launch();
 }
 
 void launch_pack_landmarks(Prec p, int s0, int ns, const LandmarkDev& L, const XmmaShape& sh, const float* Bseg,
@@ -484,22 +543,22 @@ void launch_pack_landmarks(Prec p, int s0, int ns, const LandmarkDev& L, const X
 
 void launch_pack_frames(int napp, const int* acount, const int* alist, const int* aseg, int seg_base,
                         const LandmarkDev& L, const void* frames, FrameInfo fi, const double4* qxy, const float* Yc,
-                        uint8_t* Ap, float* Nx, cudaStream_t st) {
+                        const int* seg_first, const int* tile_start, uint8_t* Ap, float* Nx, cudaStream_t st) {
   if (napp <= 0) return;
   pack_frames_kernel<<<(napp + 7) / 8, 256, 0, st>>>(acount, alist, aseg, seg_base, L.N, round_up16(L.N),
-                                                     (const float*)frames, fi.c32, qxy, Yc, Ap, Nx);
+                                                     (const float*)frames, fi.c32, qxy, Yc, seg_first, tile_start,
+                                                     Ap, Nx);
   note_launch();
 }
 
-void launch_approx_cross_mma(int napp, const int* alist, const int* aseg, const int* acount, int seg_base,
+void launch_approx_cross_mma(int napp, int nseg, const int* alist, const XTile* tiles, const int* ntiles,
                              const LandmarkDev& L, const XmmaShape& sh, const uint8_t* Ap, const uint8_t* Bp,
                              const float* Nx, const float* Nb, float* D, unsigned* status, cudaStream_t st) {
   if (napp <= 0 || L.M <= 0) return;
   XmmaArgs a;
   a.alist = alist;
-  a.aseg = aseg;
-  a.acount = acount;
-  a.seg_base = seg_base;
+  a.tiles = tiles;
+  a.ntiles = ntiles;
   a.M = L.M;
   a.nck = sh.nck;
   a.BN = sh.BN;
@@ -515,8 +574,7 @@ void launch_approx_cross_mma(int napp, const int* alist, const int* aseg, const 
   a.group = std::min(std::max(L.mma_group, 1), XM_GROUP_MAX);
   const size_t smem = (size_t)XM_STAGES * XM_STAGE_BYTES;
   cudaFuncSetAttribute(approx_cross_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const int tiles = (napp + XM_ROWS - 1) / XM_ROWS;
-  const dim3 grid(sh.NT, tiles);
+  const dim3 grid(sh.NT, xmma_max_tiles(napp, nseg));
   approx_cross_mma<<<grid, XM_THREADS, smem, st>>>(a);
   note_launch();
 }

@@ -128,6 +128,7 @@ struct pcv_ctx {
       segof, alist, aseg, Dbuf, Rpair, Bseg, mstat, status, nrecheck, small;
   DevBuf Xr, Bm, GSb, GZb;  // materialised x', b and the gamma rows
   DevBuf Apk, Bpk;          // the same deviations packed for the tensor cores (FP16 h + l)
+  DevBuf xtiles;            // their per-segment tile list, first rows, first tiles, count
   DevBuf Nx, Nb, Yc, Gsum;       // |dx|^2, |d|^2, centred close structures, Gamma sums
   DevBuf Amma, Bmma;              // tensor-core adjoint operands
   DevBuf S6;                      // per-segment landmark moments R A R^T of the finish
@@ -324,7 +325,7 @@ pcv_status pcv_destroy(pcv_ctx* c) {
                     &c->wa64, &c->y, &c->Bprior, &c->c32, &c->c64,
                     &c->fG, &c->bandD, &c->bandQ, &c->bandF, &c->chD, &c->chQ, &c->chF, &c->rlist, &c->rcount,
                     &c->recF, &c->recRef, &c->recD, &c->recQ, &c->reflist, &c->segof, &c->alist, &c->aseg,
-                    &c->Dbuf, &c->Rpair, &c->Bseg, &c->Xr, &c->Bm, &c->Apk, &c->Bpk, &c->GSb, &c->GZb, &c->Nx, &c->Nb, &c->Yc, &c->Gsum, &c->Amma, &c->Bmma, &c->S6, &c->mstat, &c->status, &c->nrecheck, &c->small, &c->h_frames,
+                    &c->Dbuf, &c->Rpair, &c->Bseg, &c->Xr, &c->Bm, &c->Apk, &c->Bpk, &c->xtiles, &c->GSb, &c->GZb, &c->Nx, &c->Nb, &c->Yc, &c->Gsum, &c->Amma, &c->Bmma, &c->S6, &c->mstat, &c->status, &c->nrecheck, &c->small, &c->h_frames,
                     &c->h_s, &c->h_z, &c->h_gs, &c->h_gz, &c->h_msd, &c->h_ref, &c->grp_inst, &c->grp_tiles,
                     &c->nl_keep, &c->nlSlot, &c->nlUpd, &c->nlU, &c->nlUA, &c->nlUAseg, &c->nlN, &c->NLtab,
                     &c->Rupd, &c->Rnl, &c->nlTiles, &c->nlPart, &c->betaPart};
@@ -849,7 +850,7 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
     // with the tensor cores the deviations are packed for the MMAs (FP16 h + l), else
     // stored as FP32 rows for the CUDA-core tiles
     xmma = c->tensor_cores;
-    const size_t xb = xmma ? xmma_a_bytes(xsh, napp) : tile_bytes_frames(napp, c->N);
+    const size_t xb = xmma ? xmma_a_bytes(xsh, napp, nseg) : tile_bytes_frames(napp, c->N);
     const size_t bb = xmma ? xsh.b_bytes_per_seg * (size_t)nseg : tile_bytes_landmarks(nseg, M, c->N);
     const size_t nb = sizeof(float) * ((size_t)napp + (size_t)nseg * M + (size_t)nseg * 3 * c->N + 2 * (size_t)F);
     const size_t gb = grads ? tile_bytes_gamma(F, M) : 0;  // per gamma kind
@@ -865,6 +866,9 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
                 ensure(c, c->Nb, sizeof(float) * (size_t)nseg * M) == PCV_OK &&
                 ensure(c, c->Yc, sizeof(float) * 3 * (size_t)c->N * nseg) == PCV_OK &&
                 (!grads || ensure(c, c->Gsum, 2 * sizeof(float) * (size_t)F) == PCV_OK);
+      if (ok && xmma)
+        ok = ensure(c, c->xtiles, sizeof(int) * (2 * (size_t)nseg + 3 * (size_t)xmma_max_tiles(napp, nseg) + 1)) ==
+             PCV_OK;
       if (ok && mma)
         ok = ensure(c, c->Amma, msh.a_bytes) == PCV_OK && ensure(c, c->Bmma, msh.b_bytes_per_seg * nseg) == PCV_OK;
       else if (ok && grads)
@@ -872,7 +876,8 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
       if (ok) {
         tiled = true;
       } else {
-        for (DevBuf* b : {&c->Xr, &c->Bm, &c->Apk, &c->Bpk, &c->Amma, &c->Bmma, &c->GSb, &c->GZb}) release(*b);
+        for (DevBuf* b : {&c->Xr, &c->Bm, &c->Apk, &c->Bpk, &c->xtiles, &c->Amma, &c->Bmma, &c->GSb, &c->GZb})
+          release(*b);
         c->err = "no error";
         mma = false;
         xmma = false;
@@ -887,8 +892,19 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
     launch_exact_pairs(c->prec, nref, (const int*)c->reflist.p, nullptr, frames, L, fi, c->Dbuf.p, Bseg1,
                        (unsigned*)c->status.p, st);
   }
+  // per-segment tile list of the tensor-core MSDs: [seg_first | tile_start | tiles | count]
+  int *xt_first = nullptr, *xt_start = nullptr, *xt_count = nullptr;
+  XTile* xt_tiles = nullptr;
+  if (tiled && xmma) {
+    xt_first = (int*)c->xtiles.p;
+    xt_start = xt_first + nseg;
+    xt_tiles = (XTile*)(xt_start + nseg);
+    xt_count = (int*)(xt_tiles + xmma_max_tiles(napp, nseg));
+  }
   if (tiled && xmma) {
     PROF(c, K_MATERIALIZE);
+    launch_xmma_tiles(&sm->approx_count, (const int*)c->aseg.p, seg_base, nseg, xt_first, xt_start, xt_tiles, xt_count,
+                      st);
     launch_pack_landmarks(c->prec, seg_base, nseg, L, xsh, (const float*)c->Bseg.p, frames, fi,
                           (const int*)c->reflist.p, prior, (uint8_t*)c->Bpk.p, (float*)c->Nb.p, (float*)c->Yc.p, st);
     if (mma)
@@ -896,7 +912,8 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
                          (const int*)c->reflist.p, prior, (float*)c->Bmma.p, (float*)c->Yc.p, st);
     launch_xy_refine(c->prec, F, frames, L, fi, prior, rec, st);
     launch_pack_frames(napp, &sm->approx_count, (const int*)c->alist.p, (const int*)c->aseg.p, seg_base, L, frames,
-                       fi, rec.qxy, (const float*)c->Yc.p, (uint8_t*)c->Apk.p, (float*)c->Nx.p, st);
+                       fi, rec.qxy, (const float*)c->Yc.p, xt_first, xt_start, (uint8_t*)c->Apk.p, (float*)c->Nx.p,
+                       st);
   } else if (tiled) {
     PROF(c, K_MATERIALIZE);
     launch_materialize_landmarks(c->prec, seg_base, nseg, L, (const float*)c->Bseg.p, frames, fi,
@@ -952,9 +969,9 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
                      (const int*)c->segof.p, c->Dbuf.p, st);
   } else if (xmma) {
     PROF(c, K_APPROX_MMA);
-    launch_approx_cross_mma(napp, (const int*)c->alist.p, (const int*)c->aseg.p, &sm->approx_count, seg_base, L, xsh,
-                            (const uint8_t*)c->Apk.p, (const uint8_t*)c->Bpk.p, (const float*)c->Nx.p,
-                            (const float*)c->Nb.p, (float*)c->Dbuf.p, (unsigned*)c->status.p, st);
+    launch_approx_cross_mma(napp, nseg, (const int*)c->alist.p, xt_tiles, xt_count, L, xsh, (const uint8_t*)c->Apk.p,
+                            (const uint8_t*)c->Bpk.p, (const float*)c->Nx.p, (const float*)c->Nb.p, (float*)c->Dbuf.p,
+                            (unsigned*)c->status.p, st);
   } else {
     PROF(c, K_APPROX);
     if (tiled)

@@ -259,7 +259,17 @@ struct XmmaShape {
   size_t b_bytes_per_seg = 0;    // packed landmarks, per segment
 };
 XmmaShape xmma_shape(int M, int N);
-size_t xmma_a_bytes(const XmmaShape& sh, int napp);
+// a tile of up to 128 approximate frames of one segment: rows [k0, k1) of the approximate
+// list, segment slot `slot`
+struct XTile {
+  int slot, k0, k1;
+};
+int xmma_max_tiles(int napp, int nseg);
+size_t xmma_a_bytes(const XmmaShape& sh, int napp, int nseg);
+// the per-segment tile list (*ntiles entries, at most xmma_max_tiles), each slot's first
+// row in the approximate list and first tile
+void launch_xmma_tiles(const int* acount, const int* aseg, int seg_base, int nseg, int* seg_first, int* tile_start,
+                       XTile* tiles, int* ntiles, cudaStream_t st);
 // d_i = R_{a_i y} a_i - y' of segment slots [0, ns) (segments s0 + slot) packed into Bp,
 // |d_i|^2 (Nb, ns*M floats), y' (Yc, ns*3N floats)
 void launch_pack_landmarks(Prec p, int s0, int ns, const LandmarkDev& L, const XmmaShape& sh, const float* Bseg,
@@ -269,10 +279,10 @@ void launch_pack_landmarks(Prec p, int s0, int ns, const LandmarkDev& L, const X
 // after launch_pack_landmarks (y') and with the frames' R_xy in qxy
 void launch_pack_frames(int napp, const int* acount, const int* alist, const int* aseg, int seg_base,
                         const LandmarkDev& L, const void* frames, FrameInfo fi, const double4* qxy, const float* Yc,
-                        uint8_t* Ap, float* Nx, cudaStream_t st);
+                        const int* seg_first, const int* tile_start, uint8_t* Ap, float* Nx, cudaStream_t st);
 // D~ of every approximate frame and landmark from the packed operands (STATUS_TIMEOUT in
 // *status if a bounded wait expired)
-void launch_approx_cross_mma(int napp, const int* alist, const int* aseg, const int* acount, int seg_base,
+void launch_approx_cross_mma(int napp, int nseg, const int* alist, const XTile* tiles, const int* ntiles,
                              const LandmarkDev& L, const XmmaShape& sh, const uint8_t* Ap, const uint8_t* Bp,
                              const float* Nx, const float* Nb, float* D, unsigned* status, cudaStream_t st);
 
