@@ -44,18 +44,18 @@ FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
 # algorithmic FP32 flops per (frame, landmark, atom) of each pair kernel (FMA = 2 flops)
 FLOPS_PER_UNIT = {
     "approx_pair": 6,         # deviation form: dx . d (3 FMA); the norms are O(N) per frame / landmark
+    "approx_pair_mma": 6,     # the same cross term on the tensor cores (3 FP16 MMAs per product, h h' + h l' + l h')
     "exact_pair": 45,         # pass 1: 9 FMA; pass 2: R a (9 FMA), 3 sub, 3 FMA
     "adjoint_beta_pair": 36,  # beta^s, beta^z += gamma R_i a (2 x 9 FMA), per-pair rotations
     "adjoint_beta_seg": 12,   # beta^s, beta^z += gamma b_i (2 x 3 FMA), b_i shared by a segment
     "adjoint_beta_mma": 12,   # the same product on the tensor cores (3 TF32 MMAs per product)
 }
-TENSOR_KERNELS = {"adjoint_beta_mma"}
-# DRAM bytes per unit of work from ncu captures of the current kernels (profiles/
-# c2_close_kernels_f50k.md, F=50000, scaled here by the units one launch processes):
-# approx_pair per approximate MSD, adjoint_beta_mma per frame
-DRAM_BYTES_PER_UNIT = {"approx_pair": (191.970816e6 + 30.303232e6) / 9_997_600,
-                       "adjoint_beta_mma": (186.908672e6 + 305.802752e6) / 50_000}
-# TF32 tensor peak: measured bf16 cuBLAS rate x the nominal TF32/bf16 ratio (1.1 / 2.25 PFLOP/s)
+# tensor-core kernels: operand kind (the peak is the measured bf16 rate, scaled for TF32)
+TENSOR_KERNELS = {"adjoint_beta_mma": "tf32", "approx_pair_mma": "f16"}
+# DRAM bytes per unit of work from ncu captures of the current kernels, with the workload
+# geometry they were taken on (atoms, landmarks); used only on that geometry (the units:
+# approximate MSDs for the MSD kernels, frames for the adjoint)
+DRAM_BYTES_PER_UNIT = {}
 TF32_PER_BF16 = 1.1 / 2.25
 
 
@@ -89,6 +89,11 @@ DETAILS = {
     "c5_batched_fp16": ("config", dict(label="close-structure path CV, N=5000, M=2000, F=10000, fp16 landmark storage",
                                        seed=5, n=5000, m=2000, f=10_000, eps=0.05, grad=False, precision="fp16",
                                        steps=1)),
+    # the headline's geometry on 2000 frames (about 1.5 GB on the device): the case the ncu
+    # captures of its kernels run on
+    "c5_f2000_grad": ("config", dict(label="close-structure path CV with gradients, N=5000, M=2000, F=2000, fp32 "
+                                           "landmark storage", seed=5, n=5000, m=2000, f=2000, eps=0.05, grad=True,
+                                     precision="fp32", steps=1)),
     # the headline workload with FP16-stored landmarks (the headline itself is FP32 storage)
     "c5_batched_fp16_grad": ("config", dict(label="close-structure path CV with gradients, N=5000, M=2000, F=10000, "
                                                   "fp16 landmark storage", seed=5, n=5000, m=2000, f=10_000,
@@ -112,6 +117,10 @@ DETAILS = {
                                                    "FP32, eps=0.05, no neighbour list", seed=8, n=304, m=2120,
                                              f=10_000, eps=0.05, grad=True, precision="fp32")),
 }
+
+
+# details run only on request (--detail NAME): the small cases of the profiler captures
+PROFILE_ONLY = {"c5_f2000_grad"}
 
 
 def run_detail(pcv, name: str, calls: int = 200) -> dict:
@@ -580,7 +589,7 @@ def kernel_roofline(prof: dict, steps: int, F: int, n: int, m: int, exact_msds: 
     dom_ms, dom_launches = prof[dom]
     per_launch_ms = dom_ms / dom_launches
     launches_per_step = dom_launches / steps
-    if dom == "approx_pair":
+    if dom.startswith("approx_pair"):
         units = approx_msds / launches_per_step * n
     elif dom == "exact_pair":
         units = exact_msds / launches_per_step * n
@@ -591,17 +600,24 @@ def kernel_roofline(prof: dict, steps: int, F: int, n: int, m: int, exact_msds: 
     if dom in TENSOR_KERNELS:
         peaks = measured_peaks()
         bf16 = peaks.get("bf16_tflops_sustained")
-        peak = (bf16 if bf16 else 1700.0) * TF32_PER_BF16
+        src = "measured" if bf16 else "fallback"
         bound = "tensor"
-        peak_source = ("TF32 dense: " + ("measured" if bf16 else "fallback") + " sustained bf16 cuBLAS rate x 1.1/2.25 "
-                       "(nominal TF32/bf16); 3xTF32 issues 3 MMAs per algorithmic product, so frac <= 1/3")
+        if TENSOR_KERNELS[dom] == "tf32":
+            peak = (bf16 if bf16 else 1700.0) * TF32_PER_BF16
+            peak_source = (f"TF32 dense: {src} sustained bf16 cuBLAS rate x 1.1/2.25 (nominal TF32/bf16); 3xTF32 issues "
+                           "3 MMAs per algorithmic product, so frac <= 1/3")
+        else:
+            peak = bf16 if bf16 else 1700.0
+            peak_source = (f"FP16 dense = bf16 dense: {src} sustained bf16 cuBLAS rate; the split operands issue 3 MMAs "
+                           "per algorithmic product, so frac <= 1/3")
     else:
         peak, bound = FP32_PEAK_TFLOPS, "alu"
         peak_source = "152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz max clock (derived; FP32 FMA pipe)"
     traffic = None
-    per_unit = DRAM_BYTES_PER_UNIT.get(dom)
+    per_unit = DRAM_BYTES_PER_UNIT.get((dom, n, m))
     if per_unit is not None:
-        traffic = per_unit * (approx_msds / launches_per_step if dom == "approx_pair" else F / launches_per_step)
+        work = approx_msds if dom.startswith("approx_pair") else F
+        traffic = per_unit * work / launches_per_step
     return {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic, "peak_source": peak_source,
             "per_launch_ms": per_launch_ms, "flops_per_launch": flops,
@@ -761,7 +777,8 @@ def run_ours(args):
     if not args.no_details and rank == 0:
         details.update(c2_details(pcv, dev, stream))
         for name in DETAILS:
-            details[name] = run_detail(pcv, name, args.calls)
+            if name not in PROFILE_ONLY:
+                details[name] = run_detail(pcv, name, args.calls)
         if "c5_stream_fp32" in details and "c5_stream_fp16" in details:
             details["c5_fp16_vs_fp32_speedup"] = {
                 "stream_per_call": details["c5_stream_fp32"]["ms_per_call"] / details["c5_stream_fp16"]["ms_per_call"],
