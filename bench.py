@@ -89,11 +89,11 @@ DETAILS = {
     "c5_batched_fp16": ("config", dict(label="close-structure path CV, N=5000, M=2000, F=10000, fp16 landmark storage",
                                        seed=5, n=5000, m=2000, f=10_000, eps=0.05, grad=False, precision="fp16",
                                        steps=1)),
-    # the headline's geometry on 2000 frames (about 1.5 GB on the device): the case the ncu
-    # captures of its kernels run on
-    "c5_f2000_grad": ("config", dict(label="close-structure path CV with gradients, N=5000, M=2000, F=2000, fp32 "
-                                           "landmark storage", seed=5, n=5000, m=2000, f=2000, eps=0.05, grad=True,
-                                     precision="fp32", steps=1)),
+    # the first 2000 frames of the headline workload (its geometry and segment lengths; about
+    # 2 GB on the device): the case the ncu captures of its kernels run on
+    "c5_f2000_grad": ("config", dict(label="close-structure path CV with gradients, N=5000, M=2000, the first 2000 "
+                                           "of 10000 frames, fp32 landmark storage", seed=5, n=5000, m=2000, f=2000,
+                                     f_gen=10_000, eps=0.05, grad=True, precision="fp32", steps=1)),
     # the headline workload with FP16-stored landmarks (the headline itself is FP32 storage)
     "c5_batched_fp16_grad": ("config", dict(label="close-structure path CV with gradients, N=5000, M=2000, F=10000, "
                                                   "fp16 landmark storage", seed=5, n=5000, m=2000, f=10_000,
@@ -263,18 +263,21 @@ def lambda_from_gpu(pcv, lm):
 
 
 def time_config(pcv, label: str, seed: int, n: int, m: int, f: int, eps: float, grad: bool, precision: str,
-                noise: float = 0.05, steps: int = 3, schedule: str = "drift", nl=None) -> dict:
+                noise: float = 0.05, steps: int = 3, schedule: str = "drift", nl=None, f_gen: int | None = None) -> dict:
     """One side measurement: a fresh context on seeded synthetic inputs of the given sizes,
     2 untimed evaluations, then `steps` timed ones (CUDA events on the context's stream).
-    nl = (M_nl, L): neighbour list of M_nl landmarks updated every L steps."""
+    nl = (M_nl, L): neighbour list of M_nl landmarks updated every L steps.  f_gen: generate
+    that many frames of trajectory and evaluate the first f (the same drift rate, hence the
+    same close-structure segments, as the f_gen-frame workload)."""
     import torch
     from paper_1801_02362_gb300 import synth
 
     dt = torch.float64 if precision == "fp64" else torch.float32
     sdt = np.float64 if precision == "fp64" else np.float32
     ldt = np.float16 if precision == "fp16" else sdt
-    lm, fr = synth.make_problem(seed, n_atoms=n, n_landmarks=m, n_frames=f, frame_noise=noise, schedule=schedule,
-                                frame_dtype=sdt, landmark_dtype=ldt)
+    lm, fr = synth.make_problem(seed, n_atoms=n, n_landmarks=m, n_frames=f_gen or f, frame_noise=noise,
+                                schedule=schedule, frame_dtype=sdt, landmark_dtype=ldt)
+    fr = fr[:f]
     lam = lambda_from_gpu(pcv, lm)
     ctx = pcv.PathCV(lm, lam, eps=eps, precision=precision, neighbor_list=nl)
     frames = torch.tensor(np.ascontiguousarray(fr), dtype=dt, device="cuda")
