@@ -42,6 +42,7 @@ constexpr int MM_THREADS = 128;
 constexpr int MM_STAGES = 2;   // two CTAs per SM: one's epilogue overlaps the other's MMAs
 constexpr int MM_TMEM_COLS = 256;
 constexpr int MM_A_BYTES = MM_ROWS * MM_KC * 4;  // one operand part (hi or lo) of one K chunk
+constexpr int MM_GROUP_TILES = 16;  // frame tiles per group of the raster order
 constexpr long long MM_WAIT_CYCLES = 4000000000LL;  // about 2 s at the maximum SM clock: the
                                                     // budget of the waits for copies and MMAs
                                                     // already issued after a failure
@@ -121,7 +122,8 @@ __global__ void delta_split_kernel(int seg_base, int M, int N, int Kp, int BN, i
                                    const float4* __restrict__ c32, const int* __restrict__ refresh_list,
                                    const float* __restrict__ prior, float4 prior_c, float* __restrict__ B,
                                    float* __restrict__ Yc) {
-  const int g = blockIdx.x, slot = blockIdx.y, seg = seg_base + slot;
+  // segments fastest: the blocks resident together share one group's landmark rows
+  const int g = blockIdx.y, slot = blockIdx.x, seg = seg_base + slot;
   const int NB = 3 * N, NR = NT * BN;
   const int nck = Kp / MM_KC;
   const float* y;
@@ -186,7 +188,7 @@ __global__ void delta_split_kernel(int seg_base, int M, int N, int Kp, int BN, i
 // taken in runs of equal segment; each run accumulates from zero over all K chunks with its
 // segment's deviations and writes the rows of its own frames.
 struct MmaArgs {
-  int F, M, N, Kp, BN, NT, seg_base, tile0;
+  int F, M, N, Kp, BN, NT, seg_base, ntiles;
   const float *A, *Gsum, *B, *Yc;
   const int* seg_of_frame;
   float *gs, *gz;
@@ -206,9 +208,16 @@ __global__ void __launch_bounds__(MM_THREADS, 2) adjoint_beta_mma(MmaArgs p) {
   __shared__ int s_issued;  // chunks whose copies the producer started (global counter)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int tile = p.tile0 + blockIdx.y;
+  // grouped raster order: blocks take, group by group, MM_GROUP_TILES consecutive frame
+  // tiles x all column tiles with the frame tiles fastest, so the resident blocks share one
+  // group's gamma tiles (kept in L2 for the whole group) and each column tile's deviation
+  // block of a segment is read once by the group's frame tiles of that segment
+  const int gsz = MM_GROUP_TILES * p.NT;
+  const int grp = (int)blockIdx.x / gsz, rem = (int)blockIdx.x - grp * gsz;
+  const int g0t = grp * MM_GROUP_TILES, gtiles = min(MM_GROUP_TILES, p.ntiles - g0t);
+  const int tile = g0t + rem % gtiles, ncol = rem / gtiles;
   const int f0 = tile * MM_FRAMES;
-  const int n0 = blockIdx.x * p.BN;
+  const int n0 = ncol * p.BN;
   const int NB = 3 * p.N;
   const int nck = p.Kp / MM_KC;
   const uint32_t idesc = idesc_tf32(MM_ROWS, p.BN);
@@ -256,7 +265,7 @@ __global__ void __launch_bounds__(MM_THREADS, 2) adjoint_beta_mma(MmaArgs p) {
     const int k = s_run[run], kend = s_run[run + 1];
     const int slot = s_seg[k] - p.seg_base;
     const uint8_t* Bb =
-        reinterpret_cast<const uint8_t*>(p.B) + (((size_t)slot * p.NT + blockIdx.x) * nck) * 2 * b_bytes;
+        reinterpret_cast<const uint8_t*>(p.B) + (((size_t)slot * p.NT + ncol) * nck) * 2 * b_bytes;
     const int g0 = run * nck;  // global chunk counter: stage and phase bookkeeping across runs
     if (warp == 1) {
       if (lane == 0) {  // producer
@@ -407,7 +416,7 @@ void launch_delta_split(Prec p, int seg_base, int nseg, const LandmarkDev& L, co
                         const void* frames, FrameInfo fi, const int* refresh_list, const RefDesc& prior, float* B,
                         float* Yc, cudaStream_t st) {
   if (nseg <= 0 || L.M <= 0) return;
-  const dim3 grid(sh.Kp / 4, nseg);
+  const dim3 grid(nseg, sh.Kp / 4);
   if (p == P_F16)
     delta_split_kernel<__half><<<grid, 128, 0, st>>>(seg_base, L.M, L.N, sh.Kp, sh.BN, sh.NT, (const __half*)L.coords,
                                                      L.off, Bseg, (const float*)frames, fi.c32, refresh_list,
@@ -443,12 +452,10 @@ void launch_adjoint_beta_mma(int F, const LandmarkDev& L, const MmaShape& sh, in
   const size_t smem = (size_t)MM_STAGES * (2 * MM_A_BYTES + 2 * MM_BN_MAX * MM_KC * 4);
   cudaFuncSetAttribute(adjoint_beta_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int tiles = sh.Fp / MM_FRAMES;
-  for (int t0 = 0; t0 < tiles; t0 += 65535) {
-    a.tile0 = t0;
-    const dim3 grid(sh.NT, std::min(tiles - t0, 65535));
-    adjoint_beta_mma<<<grid, MM_THREADS, smem, st>>>(a);
-    note_launch();
-  }
+  a.ntiles = tiles;
+  // the last group may hold fewer frame tiles: exactly tiles x NT blocks in all
+  adjoint_beta_mma<<<(unsigned)((size_t)tiles * sh.NT), MM_THREADS, smem, st>>>(a);
+  note_launch();
 }
 
 }  // namespace pcv

@@ -215,9 +215,9 @@ pack_frames_kernel(const int* __restrict__ acount, const int* __restrict__ alist
   if (tid < 8 && 8 * g + tid < count) Nx[8 * g + tid] = s;
 }
 
-// B operand: d_i = R_{a_i y(s)} a_i - y'(s) of segment slot s = blockIdx.y (segment
+// B operand: d_i = R_{a_i y(s)} a_i - y'(s) of segment slot s = blockIdx.x (segment
 // s0 + s; y is the prior structure for segment 0, else frame refresh_list[seg - 1]) for
-// landmarks 8 g .. 8 g + 7 (block g = blockIdx.x; landmarks >= M, up to the last column
+// landmarks 8 g .. 8 g + 7 (block g = blockIdx.y; landmarks >= M, up to the last column
 // tile's end, are written as zeros), |d_i|^2 in Nb[s * M + i], and y'(s) in Yc[s] (block 0).
 template <typename LT>
 __global__ void __launch_bounds__(256)
@@ -227,7 +227,8 @@ pack_landmarks_kernel(int s0, int M, int N, int N16, int BN, int NT, const LT* _
                       const int* __restrict__ refresh_list, const float* __restrict__ prior, float4 prior_c,
                       uint8_t* __restrict__ Bp, float* __restrict__ Nb, float* __restrict__ Yc) {
   __shared__ float red[8][8];
-  const int g = blockIdx.x, slot = blockIdx.y, seg = s0 + slot;
+  // segments fastest: the blocks resident together share one group's landmark rows
+  const int g = blockIdx.y, slot = blockIdx.x, seg = s0 + slot;
   const int tid = threadIdx.x, rr = tid & 7, pq = tid >> 3;
   const int i = 8 * g + rr;
   const bool live = i < M;
@@ -528,7 +529,7 @@ void launch_pack_landmarks(Prec p, int s0, int ns, const LandmarkDev& L, const X
                            const void* frames, FrameInfo fi, const int* refresh_list, const RefDesc& prior,
                            uint8_t* Bp, float* Nb, float* Yc, cudaStream_t st) {
   if (ns <= 0 || L.M <= 0) return;
-  const dim3 grid((sh.NT * sh.BN) / 8, ns);
+  const dim3 grid(ns, (sh.NT * sh.BN) / 8);
   const int N16 = round_up16(L.N);
   if (p == P_F16)
     pack_landmarks_kernel<__half><<<grid, 256, 0, st>>>(s0, L.M, L.N, N16, sh.BN, sh.NT, (const __half*)L.coords,
