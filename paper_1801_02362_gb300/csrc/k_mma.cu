@@ -1,25 +1,28 @@
-// k_mma.cu -- the segment adjoint as a tensor-core GEMM (tcgen05, TF32 inputs split 3 ways).
+// k_mma.cu -- the segment adjoint as a tensor-core GEMM (tcgen05, split FP16 operands).
 //
 // For frames sharing the close structure y of a segment, the adjoint needs
 //   beta_f = sum_i gamma_fi b_i,   b_i = R_{a_i y} a_i  (3N values per landmark)
 // for gamma^s and gamma^z (the derivatives of Eqs. 5-6 with respect to the MSDs).  Per
 // segment this is a dense product: rows (frame, s|z) x K = landmarks x columns 3N.  It runs
-// on the 5th-generation tensor cores (tcgen05.mma, kind::tf32, accumulator in tensor
+// on the 5th-generation tensor cores (tcgen05.mma, kind::f16, accumulator in tensor
 // memory) with two measures for FP32 accuracy:
 //   * deviations: the product uses delta_i = b_i - y' (y' = the centred close structure),
 //     and the epilogue adds Gamma_f y' (Gamma_f = sum_i gamma_fi).  The weights gamma are
 //     concentrated on landmarks near the frame, hence near y, so the accumulated terms are
 //     small compared with beta itself;
-//   * 3xTF32: every operand is split v = hi + lo, hi = v truncated to TF32 (10 mantissa bits),
-//     lo = v - hi truncated likewise, and the product is hi*hi + hi*lo + lo*hi (relative
-//     error about 2^-21 per product instead of 2^-11).
+//   * split operands: every operand value is scaled by a power of two (2^8 for the
+//     deviations; for each gamma row one that puts its largest entry in [2^13, 2^14)) and
+//     split v = h + l with h = fp16(v), l = fp16(v - h); the product is h h' + h l' + l h'
+//     (relative error about 2^-22 per product; FP16 products are exact in the accumulator).
+//     The epilogue multiplies each row by its inverse scale.
 //
 // The producers write both operands pre-tiled in the canonical K-major shared-memory layout
-// without swizzling: core matrices of 8 rows x 16 bytes (4 TF32 values) stored as 128
-// contiguous bytes, the 4 core matrices of a 16-value K chunk 128 bytes apart (LBO) and the
-// 8-row groups 512 bytes apart (SBO).  So one stage of operands is four contiguous blocks
-// moved by cp.async.bulk (one producer thread, completion counted in bytes on an mbarrier);
-// one thread issues the MMAs and tcgen05.commit releases each stage when its MMAs are done.
+// without swizzling: core matrices of 8 rows x 16 bytes (8 halves) stored as 128 contiguous
+// bytes, the 2 core matrices of a 16-value K block 128 bytes apart (LBO) and the 8-row
+// groups 256 bytes apart (SBO), the h part of a block followed by its l part.  So one stage
+// (two K blocks) of operands is two contiguous runs moved by cp.async.bulk (one producer
+// thread, completion counted in bytes on an mbarrier); one thread issues the MMAs and
+// tcgen05.commit releases each stage when its MMAs are done.
 // Every wait is bounded by a clock budget: on expiry the kernel records STATUS_TIMEOUT,
 // waits for its copies and MMAs within a second budget, frees its tensor memory and returns.
 #include <cuda_fp16.h>
@@ -36,96 +39,138 @@ namespace {
 
 constexpr int MM_ROWS = 128;  // MMA M: 64 frames x {gamma^s, gamma^z}
 constexpr int MM_FRAMES = 64;
-constexpr int MM_KC = 16;       // K values (landmarks) per stage
+constexpr int MM_KB = 16;       // K values (landmarks) per block: one MMA (K = 16) per product
+constexpr int MM_KC = 32;       // K values per stage: two blocks
 constexpr int MM_BN_MAX = 256;  // columns per CTA (MMA N), multiple of 16
 constexpr int MM_THREADS = 128;
 constexpr int MM_STAGES = 2;   // two CTAs per SM: one's epilogue overlaps the other's MMAs
 constexpr int MM_TMEM_COLS = 256;
-constexpr int MM_A_BYTES = MM_ROWS * MM_KC * 4;  // one operand part (hi or lo) of one K chunk
+constexpr int MM_A_BYTES = MM_ROWS * MM_KB * 2;  // one part (h or l) of one A block
+constexpr float MM_DSCALE = 256.0f;              // 2^8 on the deviations
 constexpr int MM_GROUP_TILES = 16;  // frame tiles per group of the raster order
 constexpr long long MM_WAIT_CYCLES = 4000000000LL;  // about 2 s at the maximum SM clock: the
                                                     // budget of the waits for copies and MMAs
                                                     // already issued after a failure
 
-__device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
-
-// byte offset of (row r, K value kk < 16) inside one canonical K-major block
+// byte offset of (row r, K value kk < 16) inside the h part of one canonical K-major block
+// of FP16 values
 __host__ __device__ __forceinline__ uint32_t canon_off(int r, int kk) {
-  return (uint32_t)((r >> 3) * 512 + (kk >> 2) * 128 + (r & 7) * 16 + (kk & 3) * 4);
+  return (uint32_t)((r >> 3) * 256 + (kk >> 3) * 128 + (r & 7) * 16 + (kk & 7) * 2);
 }
 
-// instruction descriptor: kind::tf32, FP32 accumulator, A and B TF32 and K-major, M x N
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) { return idesc_make(M, N, 2u); }
+// a scaled value v (|v| < 65504) split into FP16 h + l
+__device__ __forceinline__ void split_h(float v, __half& h, __half& l) {
+  h = __float2half_rn(v);
+  l = __float2half_rn(v - __half2float(h));
+}
+__device__ __forceinline__ uint32_t pack_h2(__half a, __half b) {
+  return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+}
+// power of two putting the largest magnitude m of a row in [2^13, 2^14) (1 for m = 0)
+__device__ __forceinline__ float row_scale(float m) {
+  if (!(m > 0.0f)) return 1.0f;
+  int e;
+  frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
+  return ldexpf(1.0f, 14 - e);
+}
 
 // ---------------------------------------------------------------------------------------
-// gamma operand: for frame tile t (64 frames) and K chunk c, blocks hi | lo of 128 rows x 16
-// values (rows 0..63 gamma^s of frames 64t + r, rows 64..127 gamma^z), zero for landmarks
-// >= M and frames >= F; and Gamma^s_f, Gamma^z_f.  One warp per 8 consecutive frames (a
-// row group of the core matrices): lane = 4 (frame in the group) + (landmark in a group of
-// 4), so every store of the warp is one whole 128-byte core matrix (Fp = frames rounded up
-// to 64).
+// gamma operand: for frame tile t (64 frames) and K block c (16 landmarks), blocks h | l of
+// 128 rows x 16 values (rows 0..63 gamma^s of frames 64t + r, rows 64..127 gamma^z), each
+// row scaled by its power of two (row_scale), zero for landmarks >= M and frames >= F;
+// Gamma^s_f, Gamma^z_f in Gsum[2f], Gsum[2f + 1] and the rows' inverse scales (including the
+// deviations' 2^-8) in Gsum[2Fp + 2f], Gsum[2Fp + 2f + 1].  One warp per 8 consecutive frames
+// (a row group of the core matrices): lane = 4 (frame in the group) + (pair of landmarks in
+// a group of 8), so every 4-byte store of the warp lands in one whole 128-byte core matrix.
 __global__ void gamma_split_kernel(int F, int Fp, int M, int Kp, const float* __restrict__ P,
                                    const float* __restrict__ q32, const double* __restrict__ s, float lambda,
-                                   float* __restrict__ A, float* __restrict__ Gsum) {
-  const int lane = threadIdx.x & 31, rr = lane >> 2, k4 = lane & 3;
+                                   uint8_t* __restrict__ A, float* __restrict__ Gsum) {
+  const int lane = threadIdx.x & 31, rr = lane >> 2, kq = lane & 3;
   const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (g * 8 >= Fp) return;  // uniform over the warp
   const int f = g * 8 + rr;
   const bool live = f < F;
   const float sf = live ? (float)s[f] : 0.0f;
-  const int nck = Kp / MM_KC;
+  const int nkb = Kp / MM_KB;
   const int t = f / MM_FRAMES, r = f % MM_FRAMES;
-  uint8_t* tileA = reinterpret_cast<uint8_t*>(A) + (size_t)t * nck * 2 * MM_A_BYTES;
+  uint8_t* tileA = A + (size_t)t * nkb * 2 * MM_A_BYTES;
   const float* prow = P + (size_t)(live ? f : 0) * M;
-  float ss = 0.0f, sz = 0.0f;
-#pragma unroll 4
-  for (int i0 = 0; i0 < Kp; i0 += 4) {
-    const int i = i0 + k4;
-    float gs = 0.0f, gz = 0.0f;
+  auto gam = [&](int i, float& gs, float& gz) {
+    gs = gz = 0.0f;
     if (live && i < M) {
-      const float p = prow[i];
-      gz = p;
-      gs = -lambda * p * (q32[i] - sf);
+      const float pv = prow[i];
+      gz = pv;
+      gs = -lambda * pv * (q32[i] - sf);
     }
-    ss += gs;
-    sz += gz;
-    const int c = i / MM_KC, kk = i % MM_KC;
+  };
+  // pass 1: the rows' largest magnitudes (the 4 lanes of a frame)
+  float ms = 0.0f, mz = 0.0f;
+  for (int i0 = 0; i0 < Kp; i0 += 8) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      float gs, gz;
+      gam(i0 + 2 * kq + u, gs, gz);
+      ms = fmaxf(ms, fabsf(gs));
+      mz = fmaxf(mz, fabsf(gz));
+    }
+  }
+  ms = fmaxf(ms, __shfl_xor_sync(0xffffffffu, ms, 1));
+  mz = fmaxf(mz, __shfl_xor_sync(0xffffffffu, mz, 1));
+  ms = fmaxf(ms, __shfl_xor_sync(0xffffffffu, ms, 2));
+  mz = fmaxf(mz, __shfl_xor_sync(0xffffffffu, mz, 2));
+  const float scs = row_scale(ms), scz = row_scale(mz);
+  // pass 2: sums and the split, scaled values
+  float ss = 0.0f, sz = 0.0f;
+#pragma unroll 2
+  for (int i0 = 0; i0 < Kp; i0 += 8) {
+    float gs[2], gz[2];
+    __half hs[2], ls[2], hz[2], lz[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      gam(i0 + 2 * kq + u, gs[u], gz[u]);
+      ss += gs[u];
+      sz += gz[u];
+      split_h(gs[u] * scs, hs[u], ls[u]);
+      split_h(gz[u] * scz, hz[u], lz[u]);
+    }
+    const int c = i0 / MM_KB, kk = (i0 % MM_KB) + 2 * kq;
     uint8_t* blk = tileA + (size_t)c * 2 * MM_A_BYTES;
-    const float hs = tf32_hi(gs), hz = tf32_hi(gz);
-    *reinterpret_cast<float*>(blk + canon_off(r, kk)) = hs;
-    *reinterpret_cast<float*>(blk + canon_off(r + MM_FRAMES, kk)) = hz;
-    *reinterpret_cast<float*>(blk + MM_A_BYTES + canon_off(r, kk)) = tf32_hi(gs - hs);
-    *reinterpret_cast<float*>(blk + MM_A_BYTES + canon_off(r + MM_FRAMES, kk)) = tf32_hi(gz - hz);
+    *reinterpret_cast<uint32_t*>(blk + canon_off(r, kk)) = pack_h2(hs[0], hs[1]);
+    *reinterpret_cast<uint32_t*>(blk + canon_off(r + MM_FRAMES, kk)) = pack_h2(hz[0], hz[1]);
+    *reinterpret_cast<uint32_t*>(blk + MM_A_BYTES + canon_off(r, kk)) = pack_h2(ls[0], ls[1]);
+    *reinterpret_cast<uint32_t*>(blk + MM_A_BYTES + canon_off(r + MM_FRAMES, kk)) = pack_h2(lz[0], lz[1]);
   }
   // sums over the 4 lanes of the frame
   ss += __shfl_xor_sync(0xffffffffu, ss, 1);
   sz += __shfl_xor_sync(0xffffffffu, sz, 1);
   ss += __shfl_xor_sync(0xffffffffu, ss, 2);
   sz += __shfl_xor_sync(0xffffffffu, sz, 2);
-  if (k4 == 0 && live) {
+  if (kq == 0 && live) {
     Gsum[2 * f] = ss;
     Gsum[2 * f + 1] = sz;
+    Gsum[2 * (size_t)Fp + 2 * f] = 1.0f / (scs * MM_DSCALE);
+    Gsum[2 * (size_t)Fp + 2 * f + 1] = 1.0f / (scz * MM_DSCALE);
   }
 }
 
 // deviation operand: for segment slot s (segment seg_base + s), column tile nt (BN values of
-// n = 3j + c) and K chunk c, blocks hi | lo of BN rows x 16 values holding
-// delta_i[n] = b_i[n] - y'[n].  A thread handles four consecutive landmarks 4g .. 4g + 3
-// (block g) at atom j: per component n = 3j + c one 16-byte core-matrix row of each part
-// (the four landmarks are consecutive along K).  Rows n >= 3N up to the last column tile's
-// end and landmarks >= M up to Kp are written as zeros, so the buffer needs no clearing.
-// Block (g = 0, s) also writes y'[s][n].  y is the prior structure for segment 0, else the
-// frame refresh_list[seg - 1].
+// n = 3j + c) and K block c (16 landmarks), blocks h | l of BN rows x 16 values holding
+// 2^8 delta_i[n] = 2^8 (b_i[n] - y'[n]) split into FP16 h + l.  A thread handles eight
+// consecutive landmarks 8g .. 8g + 7 (block g) at atom j: per component n = 3j + c one
+// 16-byte core-matrix row of each part (the eight landmarks are consecutive along K).  Rows
+// n >= 3N up to the last column tile's end and landmarks >= M up to Kp are written as zeros,
+// so the buffer needs no clearing.  Block (g = 0, s) also writes y'[s][n].  y is the prior
+// structure for segment 0, else the frame refresh_list[seg - 1].  Segments are the fastest
+// grid index, so the blocks resident together share one group's landmark rows.
 template <typename LT>
 __global__ void delta_split_kernel(int seg_base, int M, int N, int Kp, int BN, int NT, const LT* __restrict__ lm,
                                    const float* __restrict__ lmoff, const float* __restrict__ Bseg, const float* __restrict__ frames,
                                    const float4* __restrict__ c32, const int* __restrict__ refresh_list,
-                                   const float* __restrict__ prior, float4 prior_c, float* __restrict__ B,
+                                   const float* __restrict__ prior, float4 prior_c, uint8_t* __restrict__ B,
                                    float* __restrict__ Yc) {
-  // segments fastest: the blocks resident together share one group's landmark rows
   const int g = blockIdx.y, slot = blockIdx.x, seg = seg_base + slot;
   const int NB = 3 * N, NR = NT * BN;
-  const int nck = Kp / MM_KC;
+  const int nkb = Kp / MM_KB;
   const float* y;
   float4 c;
   if (seg == 0) {
@@ -136,48 +181,54 @@ __global__ void delta_split_kernel(int seg_base, int M, int N, int Kp, int BN, i
     y = frames + (size_t)f * NB;
     c = c32[f];
   }
-  float R[4][9];
+  float R[8][9];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int i = 4 * g + u;
+  for (int u = 0; u < 8; ++u) {
+    const int i = 8 * g + u;
 #pragma unroll
     for (int e = 0; e < 9; ++e) R[u][e] = i < M ? Bseg[((size_t)seg * M + i) * 9 + e] : 0.0f;
   }
-  const size_t bblk = (size_t)BN * MM_KC * 4;  // bytes of one part of one block
-  const int ck = (4 * g) / MM_KC, kk0 = (4 * g) % MM_KC;
-  uint8_t* slot_base = reinterpret_cast<uint8_t*>(B) + ((size_t)slot * NT * nck + ck) * 2 * bblk;
+  const size_t bpart = (size_t)BN * MM_KB * 2;  // bytes of one part of one block
+  const int cb = (8 * g) / MM_KB, kk0 = (8 * g) % MM_KB;
+  uint8_t* slot_base = B + ((size_t)slot * NT * nkb + cb) * 2 * bpart;
   for (int j = threadIdx.x; 3 * j < NR; j += blockDim.x) {
     const bool atom = j < N;
-    float yv[3] = {0.0f, 0.0f, 0.0f}, a[4][3];
+    float yv[3] = {0.0f, 0.0f, 0.0f};
     if (atom) {
       yv[0] = y[3 * j] - c.x;
       yv[1] = y[3 * j + 1] - c.y;
       yv[2] = y[3 * j + 2] - c.z;
     }
+    float d[3][8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = 4 * g + u;
+    for (int u = 0; u < 8; ++u) {
+      const int i = 8 * g + u;
       const bool live = atom && i < M;
+      float a[3];
 #pragma unroll
-      for (int cc = 0; cc < 3; ++cc) a[u][cc] = live ? lm_coord<float, LT>(lm, lmoff, N, i, j, cc) : 0.0f;
+      for (int cc = 0; cc < 3; ++cc) a[cc] = live ? lm_coord<float, LT>(lm, lmoff, N, i, j, cc) : 0.0f;
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc)
+        d[cc][u] = live ? ((R[u][3 * cc] * a[0] + R[u][3 * cc + 1] * a[1] + R[u][3 * cc + 2] * a[2]) - yv[cc]) * MM_DSCALE
+                        : 0.0f;
     }
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) {
       const int n = 3 * j + cc;
       if (n >= NR) break;
-      float h[4], l[4];
+      uint32_t h[4], l[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const bool live = atom && 4 * g + u < M;
-        const float d = live ? (R[u][3 * cc] * a[u][0] + R[u][3 * cc + 1] * a[u][1] + R[u][3 * cc + 2] * a[u][2]) - yv[cc]
-                             : 0.0f;
-        h[u] = tf32_hi(d);
-        l[u] = tf32_hi(d - h[u]);
+      for (int e = 0; e < 4; ++e) {
+        __half h0, l0, h1, l1;
+        split_h(d[cc][2 * e], h0, l0);
+        split_h(d[cc][2 * e + 1], h1, l1);
+        h[e] = pack_h2(h0, h1);
+        l[e] = pack_h2(l0, l1);
       }
       const int nt = n / BN, r = n % BN;
-      uint8_t* blk = slot_base + (size_t)nt * nck * 2 * bblk;
-      *reinterpret_cast<float4*>(blk + canon_off(r, kk0)) = make_float4(h[0], h[1], h[2], h[3]);
-      *reinterpret_cast<float4*>(blk + bblk + canon_off(r, kk0)) = make_float4(l[0], l[1], l[2], l[3]);
+      uint8_t* blk = slot_base + (size_t)nt * nkb * 2 * bpart;
+      *reinterpret_cast<uint4*>(blk + canon_off(r, kk0)) = make_uint4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<uint4*>(blk + bpart + canon_off(r, kk0)) = make_uint4(l[0], l[1], l[2], l[3]);
       if (g == 0 && atom) Yc[(size_t)slot * NB + n] = yv[cc];
     }
   }
@@ -189,7 +240,8 @@ __global__ void delta_split_kernel(int seg_base, int M, int N, int Kp, int BN, i
 // segment's deviations and writes the rows of its own frames.
 struct MmaArgs {
   int F, M, N, Kp, BN, NT, seg_base, ntiles;
-  const float *A, *Gsum, *B, *Yc;
+  const uint8_t *A, *B;
+  const float *Gsum, *Yc;
   const int* seg_of_frame;
   float *gs, *gz;
   unsigned* status;
@@ -219,10 +271,12 @@ __global__ void __launch_bounds__(MM_THREADS, 2) adjoint_beta_mma(MmaArgs p) {
   const int f0 = tile * MM_FRAMES;
   const int n0 = ncol * p.BN;
   const int NB = 3 * p.N;
-  const int nck = p.Kp / MM_KC;
-  const uint32_t idesc = idesc_tf32(MM_ROWS, p.BN);
-  const uint32_t a_bytes = MM_A_BYTES, b_bytes = (uint32_t)p.BN * MM_KC * 4;
-  const uint32_t stage_bytes = 2 * a_bytes + 2 * (uint32_t)MM_BN_MAX * MM_KC * 4;
+  const int nck = p.Kp / MM_KC;  // stages of two K blocks
+  const uint32_t idesc = idesc_make(MM_ROWS, p.BN, 0u);  // kind::f16, F16 operands
+  // bytes of one part of one block, and of a stage's A and B runs (two blocks, h and l)
+  const uint32_t a_bytes = MM_A_BYTES, b_bytes = (uint32_t)p.BN * MM_KB * 2;
+  const uint32_t a_stage = 2 * 2 * a_bytes, b_stage = 2 * 2 * b_bytes;
+  const uint32_t stage_bytes = a_stage + 2 * 2 * (uint32_t)MM_BN_MAX * MM_KB * 2;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
@@ -259,13 +313,12 @@ __global__ void __launch_bounds__(MM_THREADS, 2) adjoint_beta_mma(MmaArgs p) {
   __syncthreads();
   const int nrun = s_nrun;
   const uint32_t sbase = smem_u32(smem);
-  const uint8_t* Ab = reinterpret_cast<const uint8_t*>(p.A) + (size_t)tile * nck * 2 * a_bytes;
+  const uint8_t* Ab = p.A + (size_t)tile * nck * a_stage;
 
   for (int run = 0; run < nrun; ++run) {
     const int k = s_run[run], kend = s_run[run + 1];
     const int slot = s_seg[k] - p.seg_base;
-    const uint8_t* Bb =
-        reinterpret_cast<const uint8_t*>(p.B) + (((size_t)slot * p.NT + ncol) * nck) * 2 * b_bytes;
+    const uint8_t* Bb = p.B + (((size_t)slot * p.NT + ncol) * nck) * b_stage;
     const int g0 = run * nck;  // global chunk counter: stage and phase bookkeeping across runs
     if (warp == 1) {
       if (lane == 0) {  // producer
@@ -277,9 +330,9 @@ __global__ void __launch_bounds__(MM_THREADS, 2) adjoint_beta_mma(MmaArgs p) {
             break;
           }
           const uint32_t dst = sbase + st * stage_bytes;
-          mbar_expect_tx(smem_u32(&full[st]), 2 * a_bytes + 2 * b_bytes);
-          bulk_g2s(dst, Ab + (size_t)c * 2 * a_bytes, 2 * a_bytes, smem_u32(&full[st]));
-          bulk_g2s(dst + 2 * a_bytes, Bb + (size_t)c * 2 * b_bytes, 2 * b_bytes, smem_u32(&full[st]));
+          mbar_expect_tx(smem_u32(&full[st]), a_stage + b_stage);
+          bulk_g2s(dst, Ab + (size_t)c * a_stage, a_stage, smem_u32(&full[st]));
+          bulk_g2s(dst + a_stage, Bb + (size_t)c * b_stage, b_stage, smem_u32(&full[st]));
           s_issued = g + 1;
         }
       }
@@ -293,16 +346,17 @@ __global__ void __launch_bounds__(MM_THREADS, 2) adjoint_beta_mma(MmaArgs p) {
             break;
           }
           tc_fence_after();
-          const uint32_t ah = sbase + st * stage_bytes, al = ah + a_bytes;
-          const uint32_t bh = ah + 2 * a_bytes, bl = bh + b_bytes;
+          const uint32_t a0 = sbase + st * stage_bytes, b0 = a0 + a_stage;
 #pragma unroll
-          for (int ks = 0; ks < MM_KC / 8; ++ks) {  // 8 TF32 values per MMA: 2 core matrices, 256 bytes
-            const uint32_t off = ks * 256;
-            const uint64_t dah = smem_desc(ah + off, 128, 512), dal = smem_desc(al + off, 128, 512);
-            const uint64_t dbh = smem_desc(bh + off, 128, 512), dbl = smem_desc(bl + off, 128, 512);
-            mma_tf32(tmem, dah, dbh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
-            mma_tf32(tmem, dah, dbl, idesc, 1u);
-            mma_tf32(tmem, dal, dbh, idesc, 1u);
+          for (int ks = 0; ks < MM_KC / MM_KB; ++ks) {  // one block of 16 K values per MMA
+            const uint32_t ah = a0 + ks * 2 * a_bytes, al = ah + a_bytes;
+            const uint32_t bh = b0 + ks * 2 * b_bytes, bl = bh + b_bytes;
+            const uint64_t dah = smem_desc(ah, 128, 256), dal = smem_desc(al, 128, 256);
+            const uint64_t dbh = smem_desc(bh, 128, 256), dbl = smem_desc(bl, 128, 256);
+            // the two small correction products first, the main product last
+            mma_f16(tmem, dah, dbl, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+            mma_f16(tmem, dal, dbh, idesc, 1u);
+            mma_f16(tmem, dah, dbh, idesc, 1u);
           }
           mma_commit(smem_u32(&empty[st]));
         }
@@ -328,6 +382,8 @@ __global__ void __launch_bounds__(MM_THREADS, 2) adjoint_beta_mma(MmaArgs p) {
     const int f = f0 + ff;
     const int mine = (ff >= k && ff < kend && f < p.F) ? 1 : 0;
     const float Gam = mine ? p.Gsum[2 * f + (zrow ? 1 : 0)] : 0.0f;
+    // the row's inverse scale (gamma row scale and the deviations' 2^8)
+    const float usc = mine ? p.Gsum[2 * (size_t)p.ntiles * MM_FRAMES + 2 * f + (zrow ? 1 : 0)] : 0.0f;
     const float* yrow = p.Yc + (size_t)slot * NB;
     float* outb = zrow ? p.gz : p.gs;
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
@@ -340,7 +396,7 @@ __global__ void __launch_bounds__(MM_THREADS, 2) adjoint_beta_mma(MmaArgs p) {
         float v[16];
         tmem_ld16(trow + c0 + cb, v);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) stg[lane * ld + cb + e] = v[e];
+        for (int e = 0; e < 16; ++e) stg[lane * ld + cb + e] = v[e] * usc;
       }
       __syncwarp();
       float yv[8];
@@ -399,16 +455,18 @@ MmaShape mma_shape(int F, int M, int N) {
   const int nt = (NB + MM_BN_MAX - 1) / MM_BN_MAX;
   s.BN = ((NB + nt - 1) / nt + 15) / 16 * 16;
   s.NT = (NB + s.BN - 1) / s.BN;
-  s.a_bytes = (size_t)s.Fp * 2 * s.Kp * 2 * sizeof(float);
-  s.b_bytes_per_seg = (size_t)s.NT * s.BN * s.Kp * 2 * sizeof(float);
+  s.a_bytes = (size_t)s.Fp * 2 * s.Kp * 2 * sizeof(__half);            // rows s, z; parts h, l
+  s.b_bytes_per_seg = (size_t)s.NT * s.BN * s.Kp * 2 * sizeof(__half);  // parts h, l
   s.y_bytes_per_seg = (size_t)NB * sizeof(float);
+  s.gsum_floats = 4 * (size_t)s.Fp;  // Gamma sums and the rows' inverse scales
   return s;
 }
 
 void launch_gamma_split(int F, const LandmarkDev& L, const MmaShape& sh, const float* P, const double* s,
                         double lambda, float* A, float* Gsum, cudaStream_t st) {
   if (F <= 0) return;
-  gamma_split_kernel<<<sh.Fp / 64, 256, 0, st>>>(F, sh.Fp, L.M, sh.Kp, P, L.q32, s, (float)lambda, A, Gsum);
+  gamma_split_kernel<<<sh.Fp / 64, 256, 0, st>>>(F, sh.Fp, L.M, sh.Kp, P, L.q32, s, (float)lambda,
+                                                 reinterpret_cast<uint8_t*>(A), Gsum);
   note_launch();
 }
 
@@ -416,15 +474,16 @@ void launch_delta_split(Prec p, int seg_base, int nseg, const LandmarkDev& L, co
                         const void* frames, FrameInfo fi, const int* refresh_list, const RefDesc& prior, float* B,
                         float* Yc, cudaStream_t st) {
   if (nseg <= 0 || L.M <= 0) return;
-  const dim3 grid(nseg, sh.Kp / 4);
+  const dim3 grid(nseg, sh.Kp / 8);
+  uint8_t* Bb = reinterpret_cast<uint8_t*>(B);
   if (p == P_F16)
     delta_split_kernel<__half><<<grid, 128, 0, st>>>(seg_base, L.M, L.N, sh.Kp, sh.BN, sh.NT, (const __half*)L.coords,
                                                      L.off, Bseg, (const float*)frames, fi.c32, refresh_list,
-                                                     (const float*)prior.coords, prior.c32, B, Yc);
+                                                     (const float*)prior.coords, prior.c32, Bb, Yc);
   else
     delta_split_kernel<float><<<grid, 128, 0, st>>>(seg_base, L.M, L.N, sh.Kp, sh.BN, sh.NT, (const float*)L.coords,
                                                     L.off, Bseg, (const float*)frames, fi.c32, refresh_list,
-                                                    (const float*)prior.coords, prior.c32, B, Yc);
+                                                    (const float*)prior.coords, prior.c32, Bb, Yc);
   note_launch();
 }
 
@@ -440,16 +499,16 @@ void launch_adjoint_beta_mma(int F, const LandmarkDev& L, const MmaShape& sh, in
   a.BN = sh.BN;
   a.NT = sh.NT;
   a.seg_base = seg_base;
-  a.A = A;
+  a.A = reinterpret_cast<const uint8_t*>(A);
   a.Gsum = Gsum;
-  a.B = B;
+  a.B = reinterpret_cast<const uint8_t*>(B);
   a.Yc = Yc;
   a.seg_of_frame = seg_of_frame;
   a.gs = gs;
   a.gz = gz;
   a.status = status;
   a.wait_cycles = L.wait_cycles;
-  const size_t smem = (size_t)MM_STAGES * (2 * MM_A_BYTES + 2 * MM_BN_MAX * MM_KC * 4);
+  const size_t smem = (size_t)MM_STAGES * (2 * 2 * MM_A_BYTES + 2 * 2 * MM_BN_MAX * MM_KB * 2);
   cudaFuncSetAttribute(adjoint_beta_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int tiles = sh.Fp / MM_FRAMES;
   a.ntiles = tiles;

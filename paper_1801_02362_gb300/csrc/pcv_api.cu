@@ -865,7 +865,7 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
                 ensure(c, c->Nx, sizeof(float) * (size_t)napp) == PCV_OK &&
                 ensure(c, c->Nb, sizeof(float) * (size_t)nseg * M) == PCV_OK &&
                 ensure(c, c->Yc, sizeof(float) * 3 * (size_t)c->N * nseg) == PCV_OK &&
-                (!grads || ensure(c, c->Gsum, 2 * sizeof(float) * (size_t)F) == PCV_OK);
+                (!grads || ensure(c, c->Gsum, sizeof(float) * std::max(2 * (size_t)F, msh.gsum_floats)) == PCV_OK);
       if (ok && xmma)
         ok = ensure(c, c->xtiles, sizeof(int) * (2 * (size_t)nseg + 3 * (size_t)xmma_max_tiles(napp, nseg) + 1)) ==
              PCV_OK;

@@ -293,6 +293,7 @@ struct MmaShape {
   size_t a_bytes = 0;                  // gamma operand (hi and lo, s and z) for Fp frames
   size_t b_bytes_per_seg = 0;          // deviation operand per segment
   size_t y_bytes_per_seg = 0;          // centred close structure per segment
+  size_t gsum_floats = 0;              // Gamma sums and the gamma rows' inverse scales
 };
 MmaShape mma_shape(int F, int M, int N);
 // gamma operand pre-tiled for the MMA, and Gamma^s_f, Gamma^z_f (Gsum, 2F floats)
