@@ -48,10 +48,10 @@ FLOPS_PER_UNIT = {
     "exact_pair": 45,         # pass 1: 9 FMA; pass 2: R a (9 FMA), 3 sub, 3 FMA
     "adjoint_beta_pair": 36,  # beta^s, beta^z += gamma R_i a (2 x 9 FMA), per-pair rotations
     "adjoint_beta_seg": 12,   # beta^s, beta^z += gamma b_i (2 x 3 FMA), b_i shared by a segment
-    "adjoint_beta_mma": 12,   # the same product on the tensor cores (3 TF32 MMAs per product)
+    "adjoint_beta_mma": 12,   # the same product on the tensor cores (3 FP16 MMAs per product, h l' + l h' + h h')
 }
 # tensor-core kernels: operand kind (the peak is the measured bf16 rate, scaled for TF32)
-TENSOR_KERNELS = {"adjoint_beta_mma": "tf32", "approx_pair_mma": "f16"}
+TENSOR_KERNELS = {"adjoint_beta_mma": "f16", "approx_pair_mma": "f16"}
 # DRAM bytes per unit of work from ncu captures of the current kernels, with the workload
 # geometry they were taken on (atoms, landmarks); used only on that geometry (the units:
 # approximate MSDs for the MSD kernels, frames for the adjoint)

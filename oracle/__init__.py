@@ -55,7 +55,7 @@ def lib():
         L.orc_exact.argtypes = [c_int, c_int, c_int, dp, dp, dp, dp, dp, c_double, dp, dp, dp, dp, dp]
         i32p = ctypes.POINTER(ctypes.c_int32)
         L.orc_close.argtypes = [c_int, c_int, c_int, dp, dp, dp, dp, dp, c_double, c_double, dp, dp,
-                                c_int, c_int, i32p, i64p, dp, dp, dp, u8p, dp, dp, dp]
+                                c_int, c_int, i32p, i64p, dp, dp, dp, u8p, dp, dp, dp, dp]
         L.orc_exact_nl.argtypes = [c_int, c_int, c_int, dp, dp, dp, dp, dp, c_double, c_int, c_int, i32p, i64p,
                                    dp, dp, dp, dp, dp]
         L.orc_nl_select.argtypes = [c_int, dp, c_int, i32p]
@@ -205,11 +205,13 @@ class CloseState:
 
 
 def close(frames, landmarks, lam, eps, state: CloseState | None = None, w=None, q=None,
-          want_D=True, want_grad=False, nl=None, wa=None):
+          want_D=True, want_grad=False, nl=None, wa=None, D_in=None):
     """Floating close structure (Algorithm 2) over F time-ordered frames.
 
     nl = (M_nl, L): neighbour list chosen at reassignments (exact distances) and every L
-    steps (approximate distances), used in between.  D of unlisted landmarks is +inf."""
+    steps (approximate distances), used in between.  D of unlisted landmarks is +inf.
+    D_in (F x M, NaN = the oracle's own): distances at which s, z and the derivative
+    weights are formed instead of the oracle's (the geometry stays the oracle's)."""
     fr, lm = _f64(frames), _f64(landmarks)
     f, n = fr.shape[0], fr.shape[1]
     m = lm.shape[0]
@@ -226,7 +228,7 @@ def close(frames, landmarks, lam, eps, state: CloseState | None = None, w=None, 
     st = lib().orc_close(f, m, n, _p(_f64(w)), _p(_f64(wa)), _p(fr), _p(lm), _p(_f64(q)), float(lam), float(eps),
                          _p(state.y), _p(state.B), m_nl, stride, _p(state.nl, ctypes.c_int32),
                          _p(state.ctr, ctypes.c_int64), _p(s), _p(z), _p(D), _p(ref, ctypes.c_uint8), _p(dxy),
-                         _p(gs), _p(gz))
+                         _p(gs), _p(gz), _p(_f64(D_in)))
     if st != 0:
         raise RuntimeError(f"oracle close: status {st}")
     return dict(s=s, z=z, D=D, refreshed=ref, dxy=dxy, dsdx=gs, dzdx=gz, state=state)

@@ -358,10 +358,18 @@ static void members_cv(int msel, const int* sel, const double* D, const double* 
 
 /* Exact evaluation of one frame (Algorithm 1 over the landmarks of sel, or all).
  * xc: centred frame; lmc: centred landmarks (M x N x 3).  Outputs D (M), R (M x 9,
- * optional), s, z, and gradients ds/dx, dz/dx (N x 3, optional), Eq. (der_dist). */
+ * optional), s, z, and gradients ds/dx, dz/dx (N x 3, optional), Eq. (der_dist).
+ * D_given (M, optional): distances that replace the computed ones where not NaN, before
+ * s, z and the weights of the gradient are formed (the geometry stays the oracle's own);
+ * used to evaluate the derivatives at another evaluation's distances. */
+static void take_given(int m, const double* D_given, double* D) {
+  if (D_given)
+    for (int i = 0; i < m; ++i)
+      if (!isnan(D_given[i])) D[i] = D_given[i];
+}
 int orc_frame_exact(int m, int n, const double* w, const double* wa, const double* xc, const double* lmc,
                     const double* qprop, double lambda, const int* sel, int msel, double* s, double* z,
-                    double* D, double* Rout, double* dsdx, double* dzdx) {
+                    double* D, double* Rout, double* dsdx, double* dzdx, const double* D_given) {
   int st = ORC_OK;
   if (!sel) msel = m;
   double* R = (double*)calloc((size_t)9 * m, sizeof(double));
@@ -377,6 +385,7 @@ int orc_frame_exact(int m, int n, const double* w, const double* wa, const doubl
     memcpy(R + 9 * i, al.R, sizeof(al.R));
   }
   if (bad) st = ORC_ENOCONV;
+  take_given(m, D_given, D);
   double* p = (double*)malloc(sizeof(double) * msel);
   members_cv(msel, sel, D, qprop, lambda, s, z, p);
   if (dsdx || dzdx) {
@@ -433,7 +442,7 @@ int orc_frame_exact(int m, int n, const double* w, const double* wa, const doubl
 int orc_frame_approx(int m, int n, const double* w, const double* wa, const double* xc, const double* yc,
                      const double* B, const double* lmc, const double* qprop, double lambda,
                      const orc_align_t* al, const int* sel, int msel, double* s, double* z, double* D,
-                     double* dsdx, double* dzdx) {
+                     double* dsdx, double* dzdx, const double* D_given) {
   const double* Rxy = al->R;
   if (!sel) msel = m;
   double* Q = (double*)calloc((size_t)9 * m, sizeof(double));
@@ -456,6 +465,7 @@ int orc_frame_approx(int m, int n, const double* w, const double* wa, const doub
       }
     D[i] = dd;
   }
+  take_given(m, D_given, D);
   double* p = (double*)malloc(sizeof(double) * msel);
   members_cv(msel, sel, D, qprop, lambda, s, z, p);
   if (dsdx || dzdx) {
@@ -571,7 +581,7 @@ int orc_exact(int f, int m, int n, const double* w_in, const double* wa_in, cons
     double* Dt = (double*)malloc(sizeof(double) * m);
     orc_center(n, wa, frames + (size_t)t * n * 3, xc);
     int st_t = orc_frame_exact(m, n, w, wa, xc, lmc, q, lambda, NULL, 0, s + t, z + t, Dt, NULL,
-                               dsdx ? dsdx + (size_t)t * n * 3 : NULL, dzdx ? dzdx + (size_t)t * n * 3 : NULL);
+                               dsdx ? dsdx + (size_t)t * n * 3 : NULL, dzdx ? dzdx + (size_t)t * n * 3 : NULL, NULL);
     if (D) memcpy(D + (size_t)t * m, Dt, sizeof(double) * m);
     if (st_t != ORC_OK) {
 #pragma omp critical
@@ -639,7 +649,8 @@ int orc_exact_nl(int f, int m, int n, const double* w_in, const double* wa_in, c
     const int* sel = update ? NULL : nl_state;
     const int msel = update ? m : m_nl;
     if (orc_frame_exact(m, n, w, wa, xc, lmc, q, lambda, sel, msel, s + t, z + t, Dt, NULL,
-                        dsdx ? dsdx + (size_t)t * n * 3 : NULL, dzdx ? dzdx + (size_t)t * n * 3 : NULL) != ORC_OK)
+                        dsdx ? dsdx + (size_t)t * n * 3 : NULL, dzdx ? dzdx + (size_t)t * n * 3 : NULL,
+                        NULL) != ORC_OK)
       st = ORC_ENOCONV;
     if (use_nl && update) {
       orc_nl_select(m, Dt, m_nl, nl_state);
@@ -666,11 +677,16 @@ int orc_exact_nl(int f, int m, int n, const double* w_in, const double* wa_in, c
  * and the list is chosen from them; at the other update steps (every l_stride steps) the
  * distances to all landmarks are the approximate ones of Eq. (close_dist) and the list is
  * chosen from those (end of Section 3.2); in between only the listed landmarks are
- * evaluated.  nl_state: m_nl indices carried between calls. */
+ * evaluated.  nl_state: m_nl indices carried between calls.
+ * D_in (F x M, optional): distances that replace the frame's own (where not NaN) before
+ * s, z and the derivative weights are formed; the decisions, rotations and geometry of the
+ * derivatives stay the oracle's.  It evaluates the derivatives at another evaluation's
+ * distances, which separates the error of a derivative computation from that of the
+ * distances it was given. */
 int orc_close(int f, int m, int n, const double* w_in, const double* wa_in, const double* frames, const double* lm,
               const double* q_in, double lambda, double eps, double* y_state, double* B_state,
               int m_nl, int l_stride, int* nl_state, int64_t* ctr, double* s, double* z, double* D,
-              uint8_t* refreshed, double* dxy, double* dsdx, double* dzdx) {
+              uint8_t* refreshed, double* dxy, double* dsdx, double* dzdx, const double* D_in) {
   if (f < 0 || m < 1 || n < 1 || !(lambda > 0.0) || !(eps >= 0.0) || l_stride < 1) return ORC_EINVAL;
   const int use_nl = m_nl > 0 && m_nl < m;
   double* w = (double*)malloc(sizeof(double) * n);
@@ -688,6 +704,7 @@ int orc_close(int f, int m, int n, const double* w_in, const double* wa_in, cons
     orc_center(n, wa, frames + (size_t)t * n * 3, xc);
     double* gs = dsdx ? dsdx + (size_t)t * n * 3 : NULL;
     double* gz = dzdx ? dzdx + (size_t)t * n * 3 : NULL;
+    const double* Dg = D_in ? D_in + (size_t)t * m : NULL;
     int refresh = 0;
     orc_align_t al;
     if (!ctr[C_HAS_Y]) {
@@ -703,7 +720,7 @@ int orc_close(int f, int m, int n, const double* w_in, const double* wa_in, cons
     const int update = !use_nl || refresh || nl_update_step(ctr[C_FRAMES], l_stride, ctr);
     if (refresh) {
       /* reassign: exact distances to all landmarks, save R_{a_i x}, y <- x */
-      if (orc_frame_exact(m, n, w, wa, xc, lmc, q, lambda, NULL, m, s + t, z + t, Dt, Rt, gs, gz) != ORC_OK)
+      if (orc_frame_exact(m, n, w, wa, xc, lmc, q, lambda, NULL, m, s + t, z + t, Dt, Rt, gs, gz, Dg) != ORC_OK)
         st = ORC_ENOCONV;
       memcpy(B_state, Rt, sizeof(double) * 9 * m);
       memcpy(y_state, xc, sizeof(double) * 3 * n);
@@ -713,7 +730,8 @@ int orc_close(int f, int m, int n, const double* w_in, const double* wa_in, cons
     } else {
       const int* sel = update ? NULL : nl_state;
       const int msel = update ? m : m_nl;
-      orc_frame_approx(m, n, w, wa, xc, y_state, B_state, lmc, q, lambda, &al, sel, msel, s + t, z + t, Dt, gs, gz);
+      orc_frame_approx(m, n, w, wa, xc, y_state, B_state, lmc, q, lambda, &al, sel, msel, s + t, z + t, Dt, gs, gz,
+                       Dg);
       ctr[C_APPROX] += msel;
     }
     if (use_nl && update) {

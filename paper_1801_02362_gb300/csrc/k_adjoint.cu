@@ -31,11 +31,12 @@ __device__ __forceinline__ float lm_at<float, __half>(const __half* p) {
   return __half2float(*p);
 }
 
-// gamma^s, gamma^z of one (frame, landmark) pair from the softmax weight p
+// gamma^s, gamma^z of one (frame, landmark) pair from the softmax weight p; s = sh + sl
+// (s_low)
 template <typename ST>
-__device__ __forceinline__ void gammas(ST p, ST lambda, ST qi, ST sf, ST& gs, ST& gz) {
+__device__ __forceinline__ void gammas(ST p, ST lambda, ST qi, ST sh, ST sl, ST& gs, ST& gz) {
   gz = p;
-  gs = -lambda * p * (qi - sf);
+  gs = -lambda * p * ((qi - sh) - sl);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -77,7 +78,8 @@ adjoint_beta_pair(int F, int M, int N, const LT* __restrict__ lm, const float* _
       for (int c = 0; c < 9; ++c) rot[c] = 0;
       if (f < F && i < iend) {
         const ST qi = sizeof(ST) == 8 ? (ST)q[i] : (ST)q32[i];
-        gammas<ST>(P[(size_t)f * M + i], lam, qi, (ST)s[f], gsv, gzv);
+        const ST sh = (ST)s[f];
+        gammas<ST>(P[(size_t)f * M + i], lam, qi, sh, s_low<ST>(s[f], sh), gsv, gzv);
         const ST* R = Rpair ? Rpair + ((size_t)f * M + i) * 9 : Bseg + ((size_t)seg_of_frame[f] * M + i) * 9;
 #pragma unroll
         for (int c = 0; c < 9; ++c) rot[c] = R[c];
@@ -190,6 +192,7 @@ adjoint_beta_list(int mode, const NlTile* __restrict__ tiles, const int* __restr
   __shared__ __align__(16) float As[BL_KL * 3][BL_TJ];
   __shared__ int s_frame[BL_TF];
   __shared__ float s_s[BL_TF];
+  __shared__ float s_l[BL_TF];
   int p0, rows, ncol;
   const int* fl;
   const int* cols;
@@ -219,6 +222,7 @@ adjoint_beta_list(int mode, const NlTile* __restrict__ tiles, const int* __restr
     const int f = tid < rows ? fl[p0 + tid] : -1;
     s_frame[tid] = f;
     s_s[tid] = f >= 0 ? (float)s[f] : 0.0f;
+    s_l[tid] = f >= 0 ? s_low<float>(s[f], s_s[tid]) : 0.0f;
   }
   __syncthreads();
   float bs[3][8], bz[3][8];
@@ -236,7 +240,7 @@ adjoint_beta_list(int mode, const NlTile* __restrict__ tiles, const int* __restr
       for (int k = 0; k < 9; ++k) rot[k] = 0.0f;
       if (f >= 0 && c < cend) {
         const int i = cols ? cols[c] : c;
-        gammas<float>(P[(size_t)f * M + i], lambda, q32[i], s_s[ff], gsv, gzv);
+        gammas<float>(P[(size_t)f * M + i], lambda, q32[i], s_s[ff], s_l[ff], gsv, gzv);
         const float* R = Bseg ? Bseg + ((size_t)segof[f] * M + i) * 9
                               : (mode == 0 ? Rupd + ((size_t)(p0 + ff) * M + i) * 9 : Rnl + ((size_t)f * Mnl + c) * 9);
 #pragma unroll
@@ -338,12 +342,14 @@ adjoint_beta_seg(int F, int M, int N, const LT* __restrict__ lm, const float* __
   __shared__ float s_B[BS_KL][9];
   __shared__ int s_seg[BS_TF];
   __shared__ float s_s[BS_TF];
+  __shared__ float s_l[BS_TF];
   const int f0 = blockIdx.y * BS_TF, j0 = blockIdx.x * BS_TJ;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;  // atoms j0 + 2 tx + {0,1}; frames 4 ty + {0..3}
   if (tid < BS_TF) {
     const int f = f0 + tid;
     s_seg[tid] = f < F ? seg_of_frame[f] : -1;
     s_s[tid] = f < F ? (float)s[f] : 0.0f;
+    s_l[tid] = f < F ? s_low<float>(s[f], s_s[tid]) : 0.0f;
   }
   float acs[4][6], acz[4][6];
 #pragma unroll
@@ -366,7 +372,8 @@ adjoint_beta_seg(int F, int M, int N, const LT* __restrict__ lm, const float* __
         const int ff = e / BS_KL, ii = e - ff * BS_KL;
         const int f = f0 + ff, i = i0 + ii;
         float gsv = 0.0f, gzv = 0.0f;
-        if (ff >= k && ff < kend && i < M) gammas<float>(P[(size_t)f * M + i], lambda, q32[i], s_s[ff], gsv, gzv);
+        if (ff >= k && ff < kend && i < M)
+          gammas<float>(P[(size_t)f * M + i], lambda, q32[i], s_s[ff], s_l[ff], gsv, gzv);
         Gs[ii][ff] = gsv;
         Gz[ii][ff] = gzv;
       }
@@ -484,12 +491,12 @@ adjoint_finish_warp(int F, int M, int N, const FT* __restrict__ frames, const fl
   // Gamma^s = 0 and Gamma^z = 1, but the FP32 value of s and the p-weighted sum of q differ
   // by ~u s, which lambda ~ 1e3 amplifies: keeping the term makes the gradient exactly that
   // of sum_i gamma_i D_i for the gammas used.
-  const ST sf = (ST)s[f], lamw = (ST)lambda;
+  const ST sf = (ST)s[f], sl = s_low<ST>(s[f], sf), lamw = (ST)lambda;
   ST Gs = 0, Gz = 0;
   for (int i = lane; i < M; i += 32) {
     ST gsv, gzv;
     const ST qi = f64 ? (ST)q[i] : (ST)q32[i];
-    gammas<ST>(P[(size_t)f * M + i], lamw, qi, sf, gsv, gzv);
+    gammas<ST>(P[(size_t)f * M + i], lamw, qi, sf, sl, gsv, gzv);
     Gs += gsv;
     Gz += gzv;
   }
@@ -584,7 +591,7 @@ adjoint_finish_warp(int F, int M, int N, const FT* __restrict__ frames, const fl
   for (int i = lane; i < M; i += 32) {
     ST gsv, gzv;
     const ST qi = f64 ? (ST)q[i] : (ST)q32[i];
-    gammas<ST>(P[(size_t)f * M + i], lamw, qi, sf, gsv, gzv);
+    gammas<ST>(P[(size_t)f * M + i], lamw, qi, sf, sl, gsv, gzv);
     const ST* B = Bseg + ((size_t)seg * M + i) * 9;
     ST A6[6];
 #pragma unroll
@@ -731,7 +738,7 @@ adjoint_finish_staged(int F, int M, int N, const float* __restrict__ frames, con
   }
   const bool approx = rec.flag && rec.flag[f] == 0;
   const int r = rec.flag ? rec.ref[f] : 0;
-  const float sf = (float)s[f];
+  const float sf = (float)s[f], sl = s_low<float>(s[f], sf);
   float Gs = 0.0f, Gz = 0.0f;
   if (Gsum) {
     Gs = Gsum[2 * f];
@@ -806,7 +813,7 @@ adjoint_finish_staged(int F, int M, int N, const float* __restrict__ frames, con
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         float gsv, gzv;
-        gammas<float>(pv[u], lambda, qv[u], sf, gsv, gzv);  // zero for i >= M (p = 0)
+        gammas<float>(pv[u], lambda, qv[u], sf, sl, gsv, gzv);  // zero for i >= M (p = 0)
         if (!Gsum) {
           Gs += gsv;
           Gz += gzv;

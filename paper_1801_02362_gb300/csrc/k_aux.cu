@@ -778,8 +778,12 @@ __global__ void __launch_bounds__(SCAN_THREADS) compact_kernel(int F, const uint
 
 // ---------------------------------------------------------------------------------------
 // Path CVs: m = min D, l = sum exp(-lambda (D - m)), s = sum q e / l, z = m - ln(l)/lambda.
-// FP32 modes: exponentials in FP32 (relative error ~1e-7, far inside the tolerance),
-// lane partials combined in FP64.  One warp per frame.
+// FP32 modes: exponentials and sums in FP32 (relative error ~1e-7, far inside the
+// tolerance).  s is accumulated about q_m, the index of a landmark at the minimum:
+// s = q_m + sum (q_i - q_m) e_i / l, so that its FP32 error is relative to the spread of the
+// weights (a few landmarks) instead of to s itself (up to M): the adjoint's gamma^s_i =
+// -lambda p_i (q_i - s) carries any error of s as a shift of every term.  One warp per
+// frame.
 // With want_p the distances are overwritten by the softmax weights p_i = exp(-lambda (D_i -
 // m)) / l that the adjoint consumes (gamma^z_i = p_i, gamma^s_i = -lambda p_i (q_i - s)).
 // s, z of frame f from its MSD row (Eqs. 5-6, shifted log-sum-exp), one warp
@@ -788,16 +792,28 @@ __device__ __forceinline__ void finalize_warp_f32(int f, int M, float* __restric
                                                   float* __restrict__ mstat, double* __restrict__ msd, int want_p) {
   const int lane = threadIdx.x & 31;
   float* d = D + (size_t)f * M;
-  float m = 3.4e38f;
-  for (int i = lane; i < M; i += 32) m = fminf(m, d[i]);
+  float m = 3.4e38f, qm = 0.0f;  // the minimum and the q of a landmark attaining it
+  for (int i = lane; i < M; i += 32) {
+    const float v = d[i];
+    if (v < m) {
+      m = v;
+      qm = q[i];
+    }
+  }
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, off));
+  for (int off = 16; off > 0; off >>= 1) {  // (m, qm) in lexicographic order: one result on all lanes
+    const float m2 = __shfl_xor_sync(0xffffffffu, m, off), q2 = __shfl_xor_sync(0xffffffffu, qm, off);
+    if (m2 < m || (m2 == m && q2 < qm)) {
+      m = m2;
+      qm = q2;
+    }
+  }
   // l >= 1 and every term is in (0, 1]: FP32 sums are accurate to ~1e-7 relative
   float l = 0.0f, sq = 0.0f;
   for (int i = lane; i < M; i += 32) {
     const float e = expf(-lambda * (d[i] - m));
     l += e;
-    sq = fmaf(q[i], e, sq);
+    sq = fmaf(q[i] - qm, e, sq);
     if (msd) msd[(size_t)f * M + i] = (double)d[i];
   }
   l = warp_sum_float(l);
@@ -807,7 +823,7 @@ __device__ __forceinline__ void finalize_warp_f32(int f, int M, float* __restric
     for (int i = lane; i < M; i += 32) d[i] = expf(-lambda * (d[i] - m)) * il;
   }
   if (lane == 0) {
-    s[f] = (double)(sq / l);
+    s[f] = (double)qm + (double)(sq / l);
     z[f] = (double)(m - __logf(l) / lambda);
     mstat[2 * f] = m;
     mstat[2 * f + 1] = l;

@@ -90,7 +90,7 @@ __global__ void gamma_split_kernel(int F, int Fp, int M, int Kp, const float* __
   if (g * 8 >= Fp) return;  // uniform over the warp
   const int f = g * 8 + rr;
   const bool live = f < F;
-  const float sf = live ? (float)s[f] : 0.0f;
+  const float sf = live ? (float)s[f] : 0.0f, sl = live ? s_low<float>(s[f], sf) : 0.0f;
   const int nkb = Kp / MM_KB;
   const int t = f / MM_FRAMES, r = f % MM_FRAMES;
   uint8_t* tileA = A + (size_t)t * nkb * 2 * MM_A_BYTES;
@@ -100,7 +100,7 @@ __global__ void gamma_split_kernel(int F, int Fp, int M, int Kp, const float* __
     if (live && i < M) {
       const float pv = prow[i];
       gz = pv;
-      gs = -lambda * pv * (q32[i] - sf);
+      gs = -lambda * pv * ((q32[i] - sf) - sl);
     }
   };
   // pass 1: the rows' largest magnitudes (the 4 lanes of a frame)
@@ -150,87 +150,6 @@ __global__ void gamma_split_kernel(int F, int Fp, int M, int Kp, const float* __
     Gsum[2 * f + 1] = sz;
     Gsum[2 * (size_t)Fp + 2 * f] = 1.0f / (scs * MM_DSCALE);
     Gsum[2 * (size_t)Fp + 2 * f + 1] = 1.0f / (scz * MM_DSCALE);
-  }
-}
-
-// deviation operand: for segment slot s (segment seg_base + s), column tile nt (BN values of
-// n = 3j + c) and K block c (16 landmarks), blocks h | l of BN rows x 16 values holding
-// 2^8 delta_i[n] = 2^8 (b_i[n] - y'[n]) split into FP16 h + l.  A thread handles eight
-// consecutive landmarks 8g .. 8g + 7 (block g) at atom j: per component n = 3j + c one
-// 16-byte core-matrix row of each part (the eight landmarks are consecutive along K).  Rows
-// n >= 3N up to the last column tile's end and landmarks >= M up to Kp are written as zeros,
-// so the buffer needs no clearing.  Block (g = 0, s) also writes y'[s][n].  y is the prior
-// structure for segment 0, else the frame refresh_list[seg - 1].  Segments are the fastest
-// grid index, so the blocks resident together share one group's landmark rows.
-template <typename LT>
-__global__ void delta_split_kernel(int seg_base, int M, int N, int Kp, int BN, int NT, const LT* __restrict__ lm,
-                                   const float* __restrict__ lmoff, const float* __restrict__ Bseg, const float* __restrict__ frames,
-                                   const float4* __restrict__ c32, const int* __restrict__ refresh_list,
-                                   const float* __restrict__ prior, float4 prior_c, uint8_t* __restrict__ B,
-                                   float* __restrict__ Yc) {
-  const int g = blockIdx.y, slot = blockIdx.x, seg = seg_base + slot;
-  const int NB = 3 * N, NR = NT * BN;
-  const int nkb = Kp / MM_KB;
-  const float* y;
-  float4 c;
-  if (seg == 0) {
-    y = prior;
-    c = prior_c;
-  } else {
-    const int f = refresh_list[seg - 1];
-    y = frames + (size_t)f * NB;
-    c = c32[f];
-  }
-  float R[8][9];
-#pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    const int i = 8 * g + u;
-#pragma unroll
-    for (int e = 0; e < 9; ++e) R[u][e] = i < M ? Bseg[((size_t)seg * M + i) * 9 + e] : 0.0f;
-  }
-  const size_t bpart = (size_t)BN * MM_KB * 2;  // bytes of one part of one block
-  const int cb = (8 * g) / MM_KB, kk0 = (8 * g) % MM_KB;
-  uint8_t* slot_base = B + ((size_t)slot * NT * nkb + cb) * 2 * bpart;
-  for (int j = threadIdx.x; 3 * j < NR; j += blockDim.x) {
-    const bool atom = j < N;
-    float yv[3] = {0.0f, 0.0f, 0.0f};
-    if (atom) {
-      yv[0] = y[3 * j] - c.x;
-      yv[1] = y[3 * j + 1] - c.y;
-      yv[2] = y[3 * j + 2] - c.z;
-    }
-    float d[3][8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int i = 8 * g + u;
-      const bool live = atom && i < M;
-      float a[3];
-#pragma unroll
-      for (int cc = 0; cc < 3; ++cc) a[cc] = live ? lm_coord<float, LT>(lm, lmoff, N, i, j, cc) : 0.0f;
-#pragma unroll
-      for (int cc = 0; cc < 3; ++cc)
-        d[cc][u] = live ? ((R[u][3 * cc] * a[0] + R[u][3 * cc + 1] * a[1] + R[u][3 * cc + 2] * a[2]) - yv[cc]) * MM_DSCALE
-                        : 0.0f;
-    }
-#pragma unroll
-    for (int cc = 0; cc < 3; ++cc) {
-      const int n = 3 * j + cc;
-      if (n >= NR) break;
-      uint32_t h[4], l[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        __half h0, l0, h1, l1;
-        split_h(d[cc][2 * e], h0, l0);
-        split_h(d[cc][2 * e + 1], h1, l1);
-        h[e] = pack_h2(h0, h1);
-        l[e] = pack_h2(l0, l1);
-      }
-      const int nt = n / BN, r = n % BN;
-      uint8_t* blk = slot_base + (size_t)nt * nkb * 2 * bpart;
-      *reinterpret_cast<uint4*>(blk + canon_off(r, kk0)) = make_uint4(h[0], h[1], h[2], h[3]);
-      *reinterpret_cast<uint4*>(blk + bpart + canon_off(r, kk0)) = make_uint4(l[0], l[1], l[2], l[3]);
-      if (g == 0 && atom) Yc[(size_t)slot * NB + n] = yv[cc];
-    }
   }
 }
 
@@ -467,23 +386,6 @@ void launch_gamma_split(int F, const LandmarkDev& L, const MmaShape& sh, const f
   if (F <= 0) return;
   gamma_split_kernel<<<sh.Fp / 64, 256, 0, st>>>(F, sh.Fp, L.M, sh.Kp, P, L.q32, s, (float)lambda,
                                                  reinterpret_cast<uint8_t*>(A), Gsum);
-  note_launch();
-}
-
-void launch_delta_split(Prec p, int seg_base, int nseg, const LandmarkDev& L, const MmaShape& sh, const float* Bseg,
-                        const void* frames, FrameInfo fi, const int* refresh_list, const RefDesc& prior, float* B,
-                        float* Yc, cudaStream_t st) {
-  if (nseg <= 0 || L.M <= 0) return;
-  const dim3 grid(nseg, sh.Kp / 8);
-  uint8_t* Bb = reinterpret_cast<uint8_t*>(B);
-  if (p == P_F16)
-    delta_split_kernel<__half><<<grid, 128, 0, st>>>(seg_base, L.M, L.N, sh.Kp, sh.BN, sh.NT, (const __half*)L.coords,
-                                                     L.off, Bseg, (const float*)frames, fi.c32, refresh_list,
-                                                     (const float*)prior.coords, prior.c32, Bb, Yc);
-  else
-    delta_split_kernel<float><<<grid, 128, 0, st>>>(seg_base, L.M, L.N, sh.Kp, sh.BN, sh.NT, (const float*)L.coords,
-                                                    L.off, Bseg, (const float*)frames, fi.c32, refresh_list,
-                                                    (const float*)prior.coords, prior.c32, Bb, Yc);
   note_launch();
 }
 

@@ -448,7 +448,7 @@ nl_beta_kernel(int F, int M, int N, int Mnl, const uint8_t* __restrict__ upd, co
   const bool u = upd[f] != 0;
   const int cnt = u ? M : Mnl;
   const int* members = u ? nullptr : NLtab + (size_t)slot[f] * Mnl;
-  const ST sf = (ST)s[f], lam = (ST)lambda;
+  const ST sf = (ST)s[f], sl = s_low<ST>(s[f], sf), lam = (ST)lambda;
   for (int j0 = 0; j0 < N; j0 += blockDim.x) {
     const int j = j0 + threadIdx.x;
     ST bs[3] = {0, 0, 0}, bz[3] = {0, 0, 0};
@@ -463,7 +463,7 @@ nl_beta_kernel(int F, int M, int N, int Mnl, const uint8_t* __restrict__ upd, co
           i = members ? members[kk] : kk;
           const ST p = P[(size_t)f * M + i];
           gzv = p;
-          gsv = -lam * p * ((ST)q[i] - sf);
+          gsv = -lam * p * (((ST)q[i] - sf) - sl);
           const ST* src = Bseg ? Bseg + ((size_t)segof[f] * M + i) * 9
                                : (u ? Rupd + ((size_t)(slot[f] - 1) * M + i) * 9 : Rnl + ((size_t)f * Mnl + kk) * 9);
 #pragma unroll

@@ -229,14 +229,14 @@ __global__ void gamma_kernel(int F, int M, int Mp, const float* __restrict__ P, 
   const int lane = threadIdx.x & 31;
   const int f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (f >= F) return;
-  const float sf = (float)s[f];
+  const float sf = (float)s[f], sl = s_low<float>(s[f], sf);
   float ss = 0.0f, sz = 0.0f;
   for (int i = lane; i < Mp; i += 32) {
     float gs = 0.0f, gz = 0.0f;
     if (i < M) {
       const float p = P[(size_t)f * M + i];
       gz = p;
-      gs = -lambda * p * (q32[i] - sf);
+      gs = -lambda * p * ((q32[i] - sf) - sl);
     }
     GS[(size_t)f * Mp + i] = gs;
     GZ[(size_t)f * Mp + i] = gz;

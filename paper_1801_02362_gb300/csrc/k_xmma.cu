@@ -19,7 +19,9 @@
 //     total: four FP32 operations per column, which keeps the fold as fast as the MMAs)
 //     while the other accumulator buffer takes the next group, so the MMAs never wait for
 //     a fold.  Two registers per column limit a tile to 128 landmarks.
-// Operands are packed once per step in the canonical K-major layout without swizzling
+// Operands are packed once per step (pack_deviations_kernel writes the landmarks' operand
+// together with the segment adjoint's, pack_frames_kernel the frames') in the canonical
+// K-major layout without swizzling
 // (core matrices of 8 rows x 8 halves = 128 contiguous bytes; LBO 128 B along K, SBO 256 B
 // between 8-row groups): per chunk of 16 components a block of rows x 16 holding the h part
 // then the l part.  A (approximate frames) is tiled per segment: the approximate frames of
@@ -215,23 +217,36 @@ pack_frames_kernel(const int* __restrict__ acount, const int* __restrict__ alist
   if (tid < 8 && 8 * g + tid < count) Nx[8 * g + tid] = s;
 }
 
-// B operand: d_i = R_{a_i y(s)} a_i - y'(s) of segment slot s = blockIdx.x (segment
-// s0 + s; y is the prior structure for segment 0, else frame refresh_list[seg - 1]) for
-// landmarks 8 g .. 8 g + 7 (block g = blockIdx.y; landmarks >= M, up to the last column
-// tile's end, are written as zeros), |d_i|^2 in Nb[s * M + i], and y'(s) in Yc[s] (block 0).
+// Landmark deviations of every segment for both tensor-core products, computed once:
+// d_i = R_{a_i y(s)} a_i - y'(s) of segment slot s = blockIdx.x (segment s0 + s; y is the
+// prior structure for segment 0, else frame refresh_list[seg - 1]) for the landmarks
+// 8 g .. 8 g + 7 (g = blockIdx.y), scaled by 2^8 and split into FP16 h + l, written as
+//   * Bx, the approximate MSDs' landmark operand (rows landmarks, K components: column tile
+//     i / BNx, row i % BNx), with |d_i|^2 in Nb[s * M + i];
+//   * Ba (when not null), the adjoint's deviation operand (rows components, K landmarks:
+//     column tile n / BNa, row n % BNa, K block i / 16);
+// and y'(s) in Yc[s] (block g = 0).  Per slice of 128 atoms the block computes the 8 x 384
+// values into shared memory, then writes the 16-byte core-matrix rows of both layouts (8
+// components of one landmark; 8 landmarks of one component), eight threads to a 128-byte
+// core matrix.  Landmarks >= M and components beyond 3N are written as zeros up to each
+// layout's padded extent, so neither buffer needs clearing.  Segments are the fastest grid
+// index, so the blocks resident together share one group's landmark rows.
+// smem row stride 392 halves (784 B): 16-byte aligned rows, and the 8 rows of a column fall
+// in 8 distinct banks
+constexpr int PD_ATOMS = 128, PD_COMP = 3 * PD_ATOMS, PD_LD = PD_COMP + 8;
 template <typename LT>
 __global__ void __launch_bounds__(256)
-pack_landmarks_kernel(int s0, int M, int N, int N16, int BN, int NT, const LT* __restrict__ lm,
-                      const float* __restrict__ lmoff, const float* __restrict__ Bseg,
-                      const float* __restrict__ frames, const float4* __restrict__ c32,
-                      const int* __restrict__ refresh_list, const float* __restrict__ prior, float4 prior_c,
-                      uint8_t* __restrict__ Bp, float* __restrict__ Nb, float* __restrict__ Yc) {
+pack_deviations_kernel(int s0, int M, int N, int N16, int BNx, int NTx, int BNa, int NTa, int Kpa,
+                       const LT* __restrict__ lm, const float* __restrict__ lmoff, const float* __restrict__ Bseg,
+                       const float* __restrict__ frames, const float4* __restrict__ c32,
+                       const int* __restrict__ refresh_list, const float* __restrict__ prior, float4 prior_c,
+                       uint8_t* __restrict__ Bx, float* __restrict__ Nb, uint8_t* __restrict__ Ba,
+                       float* __restrict__ Yc) {
+  __shared__ __align__(16) __half sh[8][PD_LD], sl[8][PD_LD];
+  __shared__ float sR[8][9];
   __shared__ float red[8][8];
-  // segments fastest: the blocks resident together share one group's landmark rows
-  const int g = blockIdx.y, slot = blockIdx.x, seg = s0 + slot;
-  const int tid = threadIdx.x, rr = tid & 7, pq = tid >> 3;
-  const int i = 8 * g + rr;
-  const bool live = i < M;
+  const int slot = blockIdx.x, g = blockIdx.y, seg = s0 + slot;
+  const int tid = threadIdx.x;
   const float* y;
   float4 c;
   if (seg == 0) {
@@ -242,45 +257,96 @@ pack_landmarks_kernel(int s0, int M, int N, int N16, int BN, int NT, const LT* _
     y = frames + (size_t)f * 3 * N;
     c = c32[f];
   }
-  float R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
-  if (live) {
-    const float* B = Bseg + ((size_t)seg * M + i) * 9;
-#pragma unroll
-    for (int e = 0; e < 9; ++e) R[e] = B[e];
+  if (tid < 72) {
+    const int u = tid / 9, e = tid % 9, i = 8 * g + u;
+    sR[u][e] = i < M ? Bseg[((size_t)seg * M + i) * 9 + e] : 0.0f;
   }
-  const int K = 3 * N16, P = K / 8, nck = K / XM_KC;
-  const uint32_t bpart = (uint32_t)BN * XM_KC * 2;
-  uint8_t* tile = Bp + (((size_t)slot * NT + i / BN) * nck) * 2 * bpart;
-  const int r = i % BN;
-  const bool write_y = g == 0 && rr == 0;
-  float nrm = 0.0f;
-  for (int pp = pq; pp < P; pp += 32) {
-    float v[8];
+  const int Kx = 3 * N16, NRa = NTa * BNa;
+  const int KX = max(Kx, Ba ? NRa : 0);  // components covered
+  const bool wx = 8 * g < NTx * BNx, wa = Ba != nullptr && 8 * g < Kpa;
+  const int nckx = Kx / XM_KC, nkba = Kpa / 16;
+  const uint32_t bpx = (uint32_t)BNx * XM_KC * 2, bpa = (uint32_t)BNa * 16 * 2;  // bytes of one part of a block
+  float nrm[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // shares of |d|^2 of landmarks 2 it + (tid >> 7)
+  __syncthreads();
+  for (int c0 = 0; c0 < KX; c0 += PD_COMP) {
+    const int j0 = c0 / 3;
+    // 8 landmarks x 128 atoms: thread -> (landmark 2 it + (tid >> 7), atom tid & 127)
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int kk = 8 * pp + e, j = kk / 3, cc = kk - 3 * j;
-      float o = 0.0f;
+    for (int it = 0; it < 4; ++it) {
+      const int u = 2 * it + (tid >> 7), a = tid & 127, j = j0 + a, i = 8 * g + u;
+      float d[3] = {0.0f, 0.0f, 0.0f};
       if (j < N) {
-        const float yv = y[3 * j + cc] - (cc == 0 ? c.x : (cc == 1 ? c.y : c.z));
-        if (write_y) Yc[(size_t)slot * 3 * N + kk] = yv;
-        if (live) {
+        const float yv[3] = {y[3 * j] - c.x, y[3 * j + 1] - c.y, y[3 * j + 2] - c.z};
+        if (g == 0 && u == 0 && Yc) {
+#pragma unroll
+          for (int cc = 0; cc < 3; ++cc) Yc[(size_t)slot * 3 * N + 3 * j + cc] = yv[cc];
+        }
+        if (i < M) {
           const float a0 = lm_coord<float, LT>(lm, lmoff, N, i, j, 0);
           const float a1 = lm_coord<float, LT>(lm, lmoff, N, i, j, 1);
           const float a2 = lm_coord<float, LT>(lm, lmoff, N, i, j, 2);
-          o = (R[3 * cc] * a0 + R[3 * cc + 1] * a1 + R[3 * cc + 2] * a2) - yv;
+#pragma unroll
+          for (int cc = 0; cc < 3; ++cc)
+            d[cc] = (sR[u][3 * cc] * a0 + sR[u][3 * cc + 1] * a1 + sR[u][3 * cc + 2] * a2) - yv[cc];
         }
       }
-      v[e] = o;
-      nrm = fmaf(o, o, nrm);
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) {
+        nrm[it] = fmaf(d[cc], d[cc], nrm[it]);
+        const float v = d[cc] * XM_SCALE;
+        const __half h = __float2half_rn(v);
+        sh[u][3 * a + cc] = h;
+        sl[u][3 * a + cc] = __float2half_rn(v - __half2float(h));
+      }
     }
-    uint4 hi, lo;
-    xsplit8(v, hi, lo);
-    uint8_t* blk = tile + (size_t)(pp >> 1) * 2 * bpart;
-    *reinterpret_cast<uint4*>(blk + xpiece_off(r, pp)) = hi;
-    *reinterpret_cast<uint4*>(blk + bpart + xpiece_off(r, pp)) = lo;
+    __syncthreads();
+    // the approximate MSDs' layout: piece (landmark rr, 8 components pp of the slice)
+    if (wx) {
+      for (int e = tid; e < 8 * (PD_COMP / 8); e += 256) {
+        const int rr = e & 7, pp = e >> 3, comp = c0 + 8 * pp;
+        if (comp >= Kx) continue;
+        const int i = 8 * g + rr, gp = comp / 8;  // global piece index of the row
+        const uint4 hv = *reinterpret_cast<const uint4*>(&sh[rr][8 * pp]);
+        const uint4 lv = *reinterpret_cast<const uint4*>(&sl[rr][8 * pp]);
+        uint8_t* blk = Bx + (((size_t)slot * NTx + i / BNx) * nckx + gp / 2) * 2 * bpx;
+        *reinterpret_cast<uint4*>(blk + xpiece_off(i % BNx, gp)) = hv;
+        *reinterpret_cast<uint4*>(blk + bpx + xpiece_off(i % BNx, gp)) = lv;
+      }
+    }
+    // the adjoint's layout: piece (component n, the 8 landmarks)
+    if (wa) {
+      for (int e = tid; e < PD_COMP; e += 256) {
+        const int n = c0 + e;
+        if (n >= NRa) continue;
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          hw[q] = (uint32_t)__half_as_ushort(sh[2 * q][e]) | ((uint32_t)__half_as_ushort(sh[2 * q + 1][e]) << 16);
+          lw[q] = (uint32_t)__half_as_ushort(sl[2 * q][e]) | ((uint32_t)__half_as_ushort(sl[2 * q + 1][e]) << 16);
+        }
+        const int nt = n / BNa, r = n % BNa, kk0 = (8 * g) % 16;
+        uint8_t* blk = Ba + (((size_t)slot * NTa + nt) * nkba + (8 * g) / 16) * 2 * bpa;
+        const uint32_t off = (uint32_t)((r >> 3) * 256 + (kk0 >> 3) * 128 + (r & 7) * 16);
+        *reinterpret_cast<uint4*>(blk + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4*>(blk + bpa + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+      }
+    }
+    __syncthreads();
   }
-  const float s = rows8_sum(nrm, red);
-  if (tid < 8 && 8 * g + tid < M) Nb[(size_t)slot * M + 8 * g + tid] = s;
+  // |d_i|^2: warps 0-3 held landmarks 0, 2, 4, 6 (one per it), warps 4-7 landmarks 1, 3, 5, 7
+  const int w = tid >> 5, lane = tid & 31;
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    const float v = warp_sum_float(nrm[it]);
+    if (lane == 0) red[w][it] = v;
+  }
+  __syncthreads();
+  if (tid < 8) {
+    const int it = tid >> 1, hw = tid & 1, i = 8 * g + tid;
+    float sum = 0.0f;
+    for (int k = 0; k < 4; ++k) sum += red[4 * hw + k][it];
+    if (i < M) Nb[(size_t)slot * M + i] = sum;
+  }
 }
 
 struct XmmaArgs {
@@ -525,20 +591,24 @@ void launch_xmma_tiles(const int* acount, const int* aseg, int seg_base, int nse
   note_launch();
 }
 
-void launch_pack_landmarks(Prec p, int s0, int ns, const LandmarkDev& L, const XmmaShape& sh, const float* Bseg,
-                           const void* frames, FrameInfo fi, const int* refresh_list, const RefDesc& prior,
-                           uint8_t* Bp, float* Nb, float* Yc, cudaStream_t st) {
+void launch_pack_deviations(Prec p, int s0, int ns, const LandmarkDev& L, const XmmaShape& xs, const MmaShape* ms,
+                            const float* Bseg, const void* frames, FrameInfo fi, const int* refresh_list,
+                            const RefDesc& prior, uint8_t* Bx, float* Nb, uint8_t* Ba, float* Yc, cudaStream_t st) {
   if (ns <= 0 || L.M <= 0) return;
-  const dim3 grid(ns, (sh.NT * sh.BN) / 8);
+  const int rows = std::max(xs.NT * xs.BN, ms ? ms->Kp : 0);  // landmark rows of the two layouts
+  const dim3 grid(ns, (rows + 7) / 8);
   const int N16 = round_up16(L.N);
+  const int BNa = ms ? ms->BN : 16, NTa = ms ? ms->NT : 1, Kpa = ms ? ms->Kp : 16;
   if (p == P_F16)
-    pack_landmarks_kernel<__half><<<grid, 256, 0, st>>>(s0, L.M, L.N, N16, sh.BN, sh.NT, (const __half*)L.coords,
-                                                        L.off, Bseg, (const float*)frames, fi.c32, refresh_list,
-                                                        (const float*)prior.coords, prior.c32, Bp, Nb, Yc);
+    pack_deviations_kernel<__half><<<grid, 256, 0, st>>>(s0, L.M, L.N, N16, xs.BN, xs.NT, BNa, NTa, Kpa,
+                                                         (const __half*)L.coords, L.off, Bseg, (const float*)frames,
+                                                         fi.c32, refresh_list, (const float*)prior.coords, prior.c32,
+                                                         Bx, Nb, ms ? Ba : nullptr, Yc);
   else
-    pack_landmarks_kernel<float><<<grid, 256, 0, st>>>(s0, L.M, L.N, N16, sh.BN, sh.NT, (const float*)L.coords,
-                                                       L.off, Bseg, (const float*)frames, fi.c32, refresh_list,
-                                                       (const float*)prior.coords, prior.c32, Bp, Nb, Yc);
+    pack_deviations_kernel<float><<<grid, 256, 0, st>>>(s0, L.M, L.N, N16, xs.BN, xs.NT, BNa, NTa, Kpa,
+                                                        (const float*)L.coords, L.off, Bseg, (const float*)frames,
+                                                        fi.c32, refresh_list, (const float*)prior.coords, prior.c32,
+                                                        Bx, Nb, ms ? Ba : nullptr, Yc);
   note_launch();
 }
 

@@ -905,11 +905,9 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
     PROF(c, K_MATERIALIZE);
     launch_xmma_tiles(&sm->approx_count, (const int*)c->aseg.p, seg_base, nseg, xt_first, xt_start, xt_tiles, xt_count,
                       st);
-    launch_pack_landmarks(c->prec, seg_base, nseg, L, xsh, (const float*)c->Bseg.p, frames, fi,
-                          (const int*)c->reflist.p, prior, (uint8_t*)c->Bpk.p, (float*)c->Nb.p, (float*)c->Yc.p, st);
-    if (mma)
-      launch_delta_split(c->prec, seg_base, nseg, L, msh, (const float*)c->Bseg.p, frames, fi,
-                         (const int*)c->reflist.p, prior, (float*)c->Bmma.p, (float*)c->Yc.p, st);
+    launch_pack_deviations(c->prec, seg_base, nseg, L, xsh, mma ? &msh : nullptr, (const float*)c->Bseg.p, frames,
+                           fi, (const int*)c->reflist.p, prior, (uint8_t*)c->Bpk.p, (float*)c->Nb.p,
+                           (uint8_t*)c->Bmma.p, (float*)c->Yc.p, st);
     launch_xy_refine(c->prec, F, frames, L, fi, prior, rec, st);
     launch_pack_frames(napp, &sm->approx_count, (const int*)c->alist.p, (const int*)c->aseg.p, seg_base, L, frames,
                        fi, rec.qxy, (const float*)c->Yc.p, xt_first, xt_start, (uint8_t*)c->Apk.p, (float*)c->Nx.p,
@@ -918,9 +916,6 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
     PROF(c, K_MATERIALIZE);
     launch_materialize_landmarks(c->prec, seg_base, nseg, L, (const float*)c->Bseg.p, frames, fi,
                                  (const int*)c->reflist.p, prior, (float*)c->Bm.p, (float*)c->Nb.p, (float*)c->Yc.p, st);
-    if (mma)
-      launch_delta_split(c->prec, seg_base, nseg, L, msh, (const float*)c->Bseg.p, frames, fi,
-                         (const int*)c->reflist.p, prior, (float*)c->Bmma.p, (float*)c->Yc.p, st);
     // the accurate R_xy of the approximate frames is formed while their deviations are
     // materialised (one read of each frame)
     launch_materialize_frames(napp, &sm->approx_count, (const int*)c->alist.p, (const int*)c->aseg.p, seg_base, L,

@@ -16,6 +16,18 @@
 namespace pcv {
 
 // ---------------------------------------------------------------------------------------
+// the low part of s held as hi + lo, hi = s rounded to ST: q - s is then formed as
+// (q - hi) - lo, exact up to one rounding of the difference (q - hi is exact for q within a
+// factor two of hi, Sterbenz).  Forming q - (ST)s instead carries the rounding of s itself,
+// up to half an ulp of s (6e-5 at s ~ 2000 in FP32), into every gamma^s_i; the shift moves
+// the s-gradient by lambda (s - hi) sum_i p_i dD_i/dx, far above the FP32 rounding of the
+// terms once s is large.  Zero for ST = double.
+template <typename ST>
+__device__ __forceinline__ ST s_low(double s, ST hi) {
+  return (ST)(s - (double)hi);
+}
+
+// ---------------------------------------------------------------------------------------
 // compensated FP32 accumulation: (hi, lo) += v without losing the rounding error of the
 // addition (TwoSum).  Valid without FMA contraction concerns: no products involved.
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {

@@ -270,13 +270,15 @@ size_t xmma_a_bytes(const XmmaShape& sh, int napp, int nseg);
 // row in the approximate list and first tile
 void launch_xmma_tiles(const int* acount, const int* aseg, int seg_base, int nseg, int* seg_first, int* tile_start,
                        XTile* tiles, int* ntiles, cudaStream_t st);
-// d_i = R_{a_i y} a_i - y' of segment slots [0, ns) (segments s0 + slot) packed into Bp,
-// |d_i|^2 (Nb, ns*M floats), y' (Yc, ns*3N floats)
-void launch_pack_landmarks(Prec p, int s0, int ns, const LandmarkDev& L, const XmmaShape& sh, const float* Bseg,
-                           const void* frames, FrameInfo fi, const int* refresh_list, const RefDesc& prior,
-                           uint8_t* Bp, float* Nb, float* Yc, cudaStream_t st);
+struct MmaShape;
+// d_i = R_{a_i y} a_i - y' of segment slots [0, ns) (segments s0 + slot), computed once and
+// packed for the approximate MSDs (Bx, with |d_i|^2 in Nb, ns*M floats) and, when ms is not
+// null, for the segment adjoint (Ba); y' in Yc (ns*3N floats)
+void launch_pack_deviations(Prec p, int s0, int ns, const LandmarkDev& L, const XmmaShape& xs, const MmaShape* ms,
+                            const float* Bseg, const void* frames, FrameInfo fi, const int* refresh_list,
+                            const RefDesc& prior, uint8_t* Bx, float* Nb, uint8_t* Ba, float* Yc, cudaStream_t st);
 // dx_k = R_xy^T (x - c) - y' of approximate frames k < *acount packed into Ap, |dx_k|^2 (Nx);
-// after launch_pack_landmarks (y') and with the frames' R_xy in qxy
+// after launch_pack_deviations (y') and with the frames' R_xy in qxy
 void launch_pack_frames(int napp, const int* acount, const int* alist, const int* aseg, int seg_base,
                         const LandmarkDev& L, const void* frames, FrameInfo fi, const double4* qxy, const float* Yc,
                         const int* seg_first, const int* tile_start, uint8_t* Ap, float* Nx, cudaStream_t st);
@@ -299,10 +301,6 @@ MmaShape mma_shape(int F, int M, int N);
 // gamma operand pre-tiled for the MMA, and Gamma^s_f, Gamma^z_f (Gsum, 2F floats)
 void launch_gamma_split(int F, const LandmarkDev& L, const MmaShape& sh, const float* P, const double* s,
                         double lambda, float* A, float* Gsum, cudaStream_t st);
-// deviation operand delta_i = R_{a_i y} a_i - y' of segments [seg_base, seg_base + nseg), and y'
-void launch_delta_split(Prec p, int seg_base, int nseg, const LandmarkDev& L, const MmaShape& sh, const float* Bseg,
-                        const void* frames, FrameInfo fi, const int* refresh_list, const RefDesc& prior, float* B,
-                        float* Yc, cudaStream_t st);
 // beta^s, beta^z for all F frames into gs, gz (STATUS_TIMEOUT in *status if a wait expired)
 void launch_adjoint_beta_mma(int F, const LandmarkDev& L, const MmaShape& sh, int seg_base, const float* A,
                              const float* Gsum, const float* B, const float* Yc, const int* seg_of_frame, float* gs,

@@ -13,7 +13,9 @@ import numpy as np
 import pytest
 
 import oracle
-from _util import GRAD_TOL, TOL, d_err, grad_err, s_err, z_err
+from _util import GRAD_TOL, TOL, check_grads_at_given_distances, d_err, grad_err, s_err, z_err
+
+S_AT_D = {"fp64": 1e-9, "fp32": 2e-5, "fp16": 2e-5}  # absolute
 
 pytestmark = pytest.mark.gpu
 
@@ -32,23 +34,35 @@ def pcv():
     return mod
 
 
-def _check_frame_samples(res, fr, lm, lam, eps, ts, precision="fp32"):
+def _sample_refs(res, fr, lm, lam, eps, t):
+    """The oracle's evaluation of frame t as the GPU took it (a reassignment: Algorithm 1
+    on x_t; else the second frame of [y, x_t]), on its own distances and on the GPU's."""
     flags = res["refreshed"]
+    if flags[t]:
+        seq, row = fr[t:t + 1], 0
+    else:
+        y_idx = int(np.nonzero(flags[:t + 1])[0][-1])
+        seq, row = np.stack([fr[y_idx], fr[t]]), 1
+    r = oracle.close(seq, lm, lam, eps, want_grad=True)
+    assert r["refreshed"][row] == (2 if row == 0 else 0)
+    D_in = np.full((seq.shape[0], lm.shape[0]), np.nan)
+    D_in[row] = res["msd"][t]
+    r_at = oracle.close(seq, lm, lam, eps, want_grad=True, D_in=D_in)
+    sl = slice(row, row + 1)
+    return {k: r[k][sl] for k in ("D", "s", "z", "dsdx", "dzdx")}, {k: r_at[k][sl] for k in ("s", "dsdx", "dzdx")}
+
+
+def _check_frame_samples(res, fr, lm, lam, eps, ts, precision="fp32"):
     for t in ts:
-        if flags[t]:
-            r = oracle.exact(fr[t:t + 1], lm, lam, want_grad=True)
-            row = 0
-        else:
-            y_idx = int(np.nonzero(flags[:t + 1])[0][-1])
-            r = oracle.close(np.stack([fr[y_idx], fr[t]]), lm, lam, eps, want_grad=True)
-            assert r["refreshed"][1] == 0
-            row = 1
+        r, r_at = _sample_refs(res, fr, lm, lam, eps, t)
         sl = slice(t, t + 1)
-        assert d_err(res["msd"][sl], r["D"][row:row + 1], fr[sl], lm) < TOL[precision]
-        assert s_err(res["s"][sl], r["s"][row:row + 1], lm.shape[0]) < TOL[precision]
-        assert z_err(res["z"][sl], r["z"][row:row + 1], lam) < TOL[precision]
-        assert grad_err(res["dsdx"][sl], r["dsdx"][row:row + 1]) < GRAD_TOL[precision]
-        assert grad_err(res["dzdx"][sl], r["dzdx"][row:row + 1]) < GRAD_TOL[precision]
+        assert d_err(res["msd"][sl], r["D"], fr[sl], lm) < TOL[precision]
+        assert s_err(res["s"][sl], r["s"], lm.shape[0]) < TOL[precision]
+        assert z_err(res["z"][sl], r["z"], lam) < TOL[precision]
+        # at its own distances s is off by the FP32 rounding of the weights times their spread
+        # (a few landmarks), not by the rounding of s itself (1e-4 at s ~ 2000)
+        assert abs(res["s"][t] - r_at["s"][0]) < S_AT_D[precision], (t, res["s"][t] - r_at["s"][0])
+        check_grads_at_given_distances(res["dsdx"][sl], res["dzdx"][sl], r, r_at, precision)
 
 
 def _check_refresh_sequence(flags, fr, eps):
@@ -154,21 +168,7 @@ def test_c5_full_size_close_batched_sampled(pcv, precision):
     _check_refresh_sequence(flags, fr.astype(np.float64), eps)
     refreshed = np.nonzero(flags)[0]
     ts = [1, 777, 4321, 9999, int(refreshed[len(refreshed) // 2]), int(refreshed[len(refreshed) // 2]) + 1]
-    for t in ts:
-        if flags[t]:
-            r = oracle.exact(fr[t:t + 1], lm, lam, want_grad=True)
-            row = 0
-        else:
-            y_idx = int(np.nonzero(flags[:t + 1])[0][-1])
-            r = oracle.close(np.stack([fr[y_idx], fr[t]]), lm, lam, eps, want_grad=True)
-            assert r["refreshed"][1] == 0
-            row = 1
-        sl = slice(t, t + 1)
-        assert d_err(res["msd"][sl], r["D"][row:row + 1], fr[sl], lm) < TOL[precision]
-        assert s_err(res["s"][sl], r["s"][row:row + 1], lm.shape[0]) < TOL[precision]
-        assert z_err(res["z"][sl], r["z"][row:row + 1], lam) < TOL[precision]
-        assert grad_err(res["dsdx"][sl], r["dsdx"][row:row + 1]) < GRAD_TOL[precision]
-        assert grad_err(res["dzdx"][sl], r["dzdx"][row:row + 1]) < GRAD_TOL[precision]
+    _check_frame_samples(res, fr, lm, lam, eps, ts, precision)
 
 
 def test_c2_full_size_host_entry_point(pcv):

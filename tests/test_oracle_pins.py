@@ -463,3 +463,32 @@ def test_results_do_not_depend_on_the_thread_count():
     for a, b in zip(*runs):
         for k in ("s", "z", "D", "dsdx", "dzdx"):
             np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_given_distances_enter_only_through_the_weights():
+    """The oracle's distance injection (used to separate a derivative's error from that of
+    the distances it was evaluated at): the path CVs of Eq. (property_map_cv) are invariant
+    to a uniform shift of every distance except z, which moves by the shift; so injecting
+    D + c must give the same s and derivatives and z + c, and injecting the oracle's own D
+    must change nothing."""
+    lm, fr, lam = problem(23, 29, 17, 30, noise=0.02, schedule="walk", ou_rho=0.9)
+    eps = 0.002
+    r = oracle.close(fr, lm, lam, eps, want_grad=True)
+    assert int((r["refreshed"] == 1).sum()) >= 2
+    same = oracle.close(fr, lm, lam, eps, want_grad=True, D_in=r["D"])
+    for k in ("s", "z", "D", "dsdx", "dzdx"):
+        np.testing.assert_array_equal(same[k], r[k])
+    c = 0.0123
+    shifted = oracle.close(fr, lm, lam, eps, want_grad=True, D_in=r["D"] + c)
+    np.testing.assert_allclose(shifted["s"], r["s"], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(shifted["z"], r["z"] + c, rtol=1e-12, atol=1e-12)
+    for k in ("dsdx", "dzdx"):
+        np.testing.assert_allclose(shifted[k], r[k], rtol=1e-9, atol=1e-12 * np.abs(r[k]).max())
+    np.testing.assert_array_equal(shifted["refreshed"], r["refreshed"])  # decisions are not distances
+    # NaN entries keep the oracle's own values
+    part = r["D"] + c
+    part[:, ::2] = np.nan
+    mixed = oracle.close(fr, lm, lam, eps, want_grad=True, D_in=part)
+    Dm = r["D"].copy()
+    Dm[:, 1::2] += c
+    np.testing.assert_array_equal(mixed["D"], Dm)
