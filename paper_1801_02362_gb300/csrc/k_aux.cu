@@ -415,6 +415,112 @@ __global__ void align_kernel(int mode, int F, int W, int t0, int t1, int ref_ind
   }
 }
 
+// Chunk mode for large structures in FP32: one block of AT_THREADS per frame.  A round of
+// the search lasts as long as one frame's alignment (the frames run side by side), and with
+// one warp per frame that is two passes over N atoms by 32 lanes; here 256 threads share
+// them.  The decision, its bound and the outputs are those of align_frame<false>, with the
+// summation term of the bound counting ceil(N / 256) terms per thread, the 5-level warp
+// tree and the sum over the 8 warps: (N / 256 + 16) u D.
+constexpr int AT_WARPS = 8, AT_THREADS = 32 * AT_WARPS;
+constexpr int AT_MIN_ATOMS = 1024;  // below this a warp per frame keeps more frames in flight
+
+__global__ void __launch_bounds__(AT_THREADS)
+align_chunk_block(int t0, int t1, int ref_index, int N, const float* __restrict__ frames, RefView prior,
+                  const float4* __restrict__ c32, const double* __restrict__ fG, const float* __restrict__ wts,
+                  double dscale, double eps, double* __restrict__ outD, uint8_t* __restrict__ outFlag,
+                  int* __restrict__ recheck_list, int* __restrict__ recheck_count, int* __restrict__ stop) {
+  __shared__ float red[AT_WARPS][9];
+  __shared__ float sR[9];
+  __shared__ int s_lim;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const float* y = ref_index >= 0 ? frames + (size_t)ref_index * N * 3 : (const float*)prior.coords;
+  const float4 cy = ref_index >= 0 ? c32[ref_index] : prior.c32;
+  const double Gy = ref_index >= 0 ? fG[ref_index] : prior.G;
+  for (int t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
+    if (tid == 0) s_lim = *(volatile int*)stop;
+    __syncthreads();
+    if (t > s_lim) return;  // the same value for the whole block
+    const float* x = frames + (size_t)t * N * 3;
+    const float4 cx = c32[t];
+    // pass 1: correlation of y onto x
+    float h[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) h[e] = 0.0f;
+#pragma unroll 4
+    for (int j = tid; j < N; j += AT_THREADS) {
+      float u[3] = {y[3 * j] - cy.x, y[3 * j + 1] - cy.y, y[3 * j + 2] - cy.z};
+      const float v[3] = {x[3 * j] - cx.x, x[3 * j + 1] - cx.y, x[3 * j + 2] - cx.z};
+      if (wts) {
+        const float wj = wts[j];
+        u[0] *= wj;
+        u[1] *= wj;
+        u[2] *= wj;
+      }
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) h[3 * b + c] = fmaf(u[b], v[c], h[3 * b + c]);
+    }
+#pragma unroll
+    for (int e = 0; e < 9; ++e) h[e] = warp_sum_float(h[e]);
+    if (lane == 0)
+#pragma unroll
+      for (int e = 0; e < 9; ++e) red[warp][e] = h[e];
+    __syncthreads();
+    const double Gx = fG[t];
+    if (tid == 0) {
+      float H[9], q[4], R[9];
+#pragma unroll
+      for (int e = 0; e < 9; ++e) {
+        float v = 0.0f;
+        for (int w = 0; w < AT_WARPS; ++w) v += red[w][e];
+        H[e] = v;
+      }
+      top_quat_f32(H, (float)(0.5 * (Gx + Gy)) * 1.00001f + 1e-30f, q);
+      quat_to_rot(q, R);
+#pragma unroll
+      for (int e = 0; e < 9; ++e) sR[e] = R[e];
+    }
+    __syncthreads();
+    float R[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) R[e] = sR[e];
+    // pass 2: D = sum_j w_j |x_j - R y_j|^2
+    float dsum = 0.0f;
+#pragma unroll 4
+    for (int j = tid; j < N; j += AT_THREADS) {
+      const float u0 = y[3 * j] - cy.x, u1 = y[3 * j + 1] - cy.y, u2 = y[3 * j + 2] - cy.z;
+      const float v0 = x[3 * j] - cx.x, v1 = x[3 * j + 1] - cx.y, v2 = x[3 * j + 2] - cx.z;
+      const float d0 = v0 - fmaf(R[0], u0, fmaf(R[1], u1, R[2] * u2));
+      const float d1 = v1 - fmaf(R[3], u0, fmaf(R[4], u1, R[5] * u2));
+      const float d2 = v2 - fmaf(R[6], u0, fmaf(R[7], u1, R[8] * u2));
+      const float tt = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+      dsum = wts ? fmaf(wts[j], tt, dsum) : dsum + tt;
+    }
+    dsum = warp_sum_float(dsum);
+    if (lane == 0) red[warp][0] = dsum;  // red's pass-1 values were consumed before the last barrier
+    __syncthreads();
+    if (tid == 0) {
+      float ds = 0.0f;
+      for (int w = 0; w < AT_WARPS; ++w) ds += red[w][0];
+      const double D = (double)ds * dscale;
+      const double u32 = 5.9604644775390625e-8;
+      const double G = (Gx + Gy) * dscale;
+      const double bound =
+          4.0 * (((double)N / AT_THREADS + 16.0) * u32 * D + 20.0 * u32 * sqrt(fmax(D, 0.0) * G)) + 1e-30;
+      const bool amb = fabs(D - eps) <= bound;
+      outD[t] = D;
+      outFlag[t] = (uint8_t)((D > eps ? 1 : 0) | (amb ? 2 : 0));
+      if (amb) {
+        const int pos = atomicAdd(recheck_count, 1);
+        recheck_list[pos] = (t << 1) | 1;
+      }
+      if (D > eps && !amb) atomicMin(stop, t);
+    }
+    __syncthreads();  // red and sR are reused by the next frame
+  }
+}
+
 // Accurate R_xy for the approximate frames (FP32 modes): compensated correlation, FP64
 // eigenvalue and FP64 eigenvector.  The approximate MSD of Eq. (close_dist) is not
 // stationary in R_xy, so R_xy must be accurate to FP32 rounding.  One warp per frame.
@@ -441,50 +547,160 @@ __global__ void xy_refine_kernel(int F, int N, const float* __restrict__ frames,
 }
 
 // Full FP64 re-evaluation of D(x_t, y) from the raw FP32 coordinates: FP64 correlation
-// and sums of squares, FP64 eigenvalue.  One warp per listed entry.  Centres: when they
-// are weighted like the distance (no separate alignment weights) the frames' stored
-// centres c32 serve: at the exact centres sum_j w_j (x_j - c_x) = 0 = sum_j w_j (y_j - c_y),
-// so a centre error d enters G_x, G_y, H and hence D only at second order (|d|^2 sum w,
-// ~1e-13 nm^2 for FP32 centres from compensated sums).  With alignment weights w' != w
-// that first-order term does not vanish and the centres are summed in FP64 here.
-__global__ void recheck_kernel(const int* __restrict__ list, const int* __restrict__ count, int W,
-                               int N, const float* __restrict__ frames, RefView prior, int chunk_ref,
-                               const double* __restrict__ w64, double dscale, double eps,
-                               double* bandD, uint8_t* bandFlag, double* chunkD, uint8_t* chunkFlag,
-                               unsigned long long* n_rechecks, const double* __restrict__ wc64,
-                               const float4* __restrict__ c32) {
-  const int lane = threadIdx.x & 31;
-  const int n = *count, nw = gridDim.x * (blockDim.x >> 5);
-  for (int wid = warp_global(); wid < n; wid += nw) {  // the list is short: a small grid loops over it
-    const int code = list[wid];
-    const int slot = code >> 1;
-    const bool is_chunk = code & 1;
-    int t, ref;
-    if (is_chunk) {
-      t = slot;
-      ref = chunk_ref;
-    } else {
-      t = slot / W;
-      ref = t - (slot % W + 1);
+// and sums of squares, FP64 eigenvalue.  Centres: when they are weighted like the distance
+// (no separate alignment weights) the frames' stored centres c32 serve: at the exact
+// centres sum_j w_j (x_j - c_x) = 0 = sum_j w_j (y_j - c_y), so a centre error d enters
+// G_x, G_y, H and hence D only at second order (|d|^2 sum w, ~1e-13 nm^2 for FP32 centres
+// from compensated sums).  With alignment weights w' != w that first-order term does not
+// vanish and the centres are summed in FP64 first.
+//
+// FP64 issues at a small fraction of the FP32 rate on this part, so one warp per entry
+// would leave a 5000-atom structure's ~1.5e5 FP64 operations to one SM (~0.2 ms, and an
+// entry ends a search round).  The first RC_CAP entries are therefore shared by all the
+// blocks of the launch: block b sums its slice of the atoms and stores its 11 partials
+// (H, G_x, G_y), and the entry's last block -- found by an atomic count after a fence;
+// nothing waits -- adds the partials in block order, solves for the eigenvalue and writes
+// the decision.  Entries past RC_CAP, and all entries with FP64 centres, take one warp each.
+constexpr int RC_CAP = 32;         // entries shared by the blocks
+constexpr int RC_BLOCKS_MAX = 76;  // grid cap (the partial buffer holds RC_CAP x this)
+constexpr int RC_THREADS = 128;
+constexpr int RC_PARTS = 11;  // H (9), G_x, G_y
+
+__device__ __forceinline__ void recheck_decode(int code, int W, int chunk_ref, int& t, int& ref, int& slot,
+                                               bool& is_chunk) {
+  slot = code >> 1;
+  is_chunk = code & 1;
+  if (is_chunk) {
+    t = slot;
+    ref = chunk_ref;
+  } else {
+    t = slot / W;
+    ref = t - (slot % W + 1);
+  }
+}
+
+// the decision from the FP64 sums (one thread)
+__device__ __forceinline__ void recheck_finish(const double* h, double gx, double gy, double dscale, double eps,
+                                               int slot, bool is_chunk, double* bandD, uint8_t* bandFlag,
+                                               double* chunkD, uint8_t* chunkFlag,
+                                               unsigned long long* n_rechecks) {
+  bool ok = true;
+  const double lam = top_eig_f64(h, 0.5 * (gx + gy), &ok, nullptr);
+  double D = (gx + gy - 2.0 * lam) * dscale;
+  if (D < 0.0) D = 0.0;
+  const uint8_t fl = (uint8_t)(D > eps ? 1 : 0);
+  if (is_chunk) {
+    chunkD[slot] = D;
+    chunkFlag[slot] = fl;
+  } else {
+    bandD[slot] = D;
+    bandFlag[slot] = fl;
+  }
+  atomicAdd(n_rechecks, 1ull);
+}
+
+// FP64 sums over atoms j = j0 + k * stride < j1 of one entry (this thread's share)
+__device__ __forceinline__ void recheck_sums(int j0, int j1, int stride, const float* __restrict__ x,
+                                             const float* __restrict__ y, const double* cx, const double* cy,
+                                             const double* __restrict__ w64, double* h, double& gx, double& gy) {
+  for (int j = j0; j < j1; j += stride) {
+    const double wj = w64 ? w64[j] : 1.0;
+    double u[3], v[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      u[c] = (double)y[3 * j + c] - cy[c];
+      v[c] = (double)x[3 * j + c] - cx[c];
+      gx += wj * v[c] * v[c];
+      gy += wj * u[c] * u[c];
     }
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) h[3 * b + c] += wj * u[b] * v[c];
+  }
+}
+
+__device__ __forceinline__ void recheck_centres_c32(int t, int ref, const float4* __restrict__ c32,
+                                                    const RefView& prior, double* cx, double* cy) {
+  const float4 a = c32[t];
+  const float4 b = ref >= 0 ? c32[ref] : prior.c32;
+  cx[0] = a.x;
+  cx[1] = a.y;
+  cx[2] = a.z;
+  cy[0] = b.x;
+  cy[1] = b.y;
+  cy[2] = b.z;
+}
+
+__global__ void __launch_bounds__(RC_THREADS)
+recheck_kernel(const int* __restrict__ list, const int* __restrict__ count, int W, int N,
+               const float* __restrict__ frames, RefView prior, int chunk_ref, const double* __restrict__ w64,
+               double dscale, double eps, double* bandD, uint8_t* bandFlag, double* chunkD, uint8_t* chunkFlag,
+               unsigned long long* n_rechecks, const double* __restrict__ wc64, const float4* __restrict__ c32,
+               double* __restrict__ part, int* __restrict__ done) {
+  __shared__ double red[RC_THREADS / 32][RC_PARTS];
+  __shared__ int s_last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = *count, nb = gridDim.x, blk = blockIdx.x;
+  const int nshared = wc64 ? 0 : min(n, RC_CAP);
+  const int per = (N + nb - 1) / nb, j0 = blk * per, j1 = min(N, j0 + per);
+  for (int e = 0; e < nshared; ++e) {
+    int t, ref, slot;
+    bool is_chunk;
+    recheck_decode(list[e], W, chunk_ref, t, ref, slot, is_chunk);
+    const float* x = frames + (size_t)t * N * 3;
+    const float* y = ref >= 0 ? frames + (size_t)ref * N * 3 : (const float*)prior.coords;
+    double cx[3], cy[3];
+    recheck_centres_c32(t, ref, c32, prior, cx, cy);
+    double h[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, gx = 0.0, gy = 0.0;
+    recheck_sums(j0 + tid, j1, RC_THREADS, x, y, cx, cy, w64, h, gx, gy);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) h[k] = warp_sum_double(h[k]);
+    gx = warp_sum_double(gx);
+    gy = warp_sum_double(gy);
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) red[warp][k] = h[k];
+      red[warp][9] = gx;
+      red[warp][10] = gy;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double* my = part + ((size_t)e * RC_BLOCKS_MAX + blk) * RC_PARTS;
+      for (int k = 0; k < RC_PARTS; ++k) {
+        double v = 0.0;
+        for (int w = 0; w < RC_THREADS / 32; ++w) v += red[w][k];
+        my[k] = v;
+      }
+      __threadfence();  // the partials are visible before the count says so
+      s_last = atomicAdd(&done[e], 1) == nb - 1;
+    }
+    __syncthreads();
+    if (s_last && tid == 0) {
+      __threadfence();
+      double acc[RC_PARTS];
+      for (int k = 0; k < RC_PARTS; ++k) acc[k] = 0.0;
+      for (int bb = 0; bb < nb; ++bb) {  // block order: the same sums whichever block is last
+        const double* pp = part + ((size_t)e * RC_BLOCKS_MAX + bb) * RC_PARTS;
+        for (int k = 0; k < RC_PARTS; ++k) acc[k] += __ldcg(pp + k);
+      }
+      recheck_finish(acc, acc[9], acc[10], dscale, eps, slot, is_chunk, bandD, bandFlag, chunkD, chunkFlag,
+                     n_rechecks);
+      done[e] = 0;  // ready for the next launch
+    }
+    __syncthreads();  // red and s_last are reused by the next entry
+  }
+  // the rest: one warp per entry
+  const int nw = nb * (RC_THREADS / 32);
+  for (int wid = nshared + blk * (RC_THREADS / 32) + warp; wid < n; wid += nw) {
+    int t, ref, slot;
+    bool is_chunk;
+    recheck_decode(list[wid], W, chunk_ref, t, ref, slot, is_chunk);
     const float* x = frames + (size_t)t * N * 3;
     const float* y = ref >= 0 ? frames + (size_t)ref * N * 3 : (const float*)prior.coords;
     double cx[3], cy[3];
     if (!wc64) {
-      const float4 a = c32[t];
-      cx[0] = a.x;
-      cx[1] = a.y;
-      cx[2] = a.z;
-      if (ref >= 0) {
-        const float4 b = c32[ref];
-        cy[0] = b.x;
-        cy[1] = b.y;
-        cy[2] = b.z;
-      } else {
-        cy[0] = prior.c32.x;
-        cy[1] = prior.c32.y;
-        cy[2] = prior.c32.z;
-      }
+      recheck_centres_c32(t, ref, c32, prior, cx, cy);
     } else {
 #pragma unroll
       for (int c = 0; c < 3; ++c) cx[c] = cy[c] = 0.0;
@@ -503,40 +719,13 @@ __global__ void recheck_kernel(const int* __restrict__ list, const int* __restri
       }
     }
     double h[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, gx = 0.0, gy = 0.0;
-    for (int j = lane; j < N; j += 32) {
-      const double wj = w64 ? w64[j] : 1.0;
-      double u[3], v[3];
+    recheck_sums(lane, N, 32, x, y, cx, cy, w64, h, gx, gy);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        u[c] = (double)y[3 * j + c] - cy[c];
-        v[c] = (double)x[3 * j + c] - cx[c];
-        gx += wj * v[c] * v[c];
-        gy += wj * u[c] * u[c];
-      }
-#pragma unroll
-      for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) h[3 * b + c] += wj * u[b] * v[c];
-    }
-#pragma unroll
-    for (int e = 0; e < 9; ++e) h[e] = warp_sum_double(h[e]);
+    for (int k = 0; k < 9; ++k) h[k] = warp_sum_double(h[k]);
     gx = warp_sum_double(gx);
     gy = warp_sum_double(gy);
-    if (lane == 0) {
-      bool ok = true;
-      const double lam = top_eig_f64(h, 0.5 * (gx + gy), &ok, nullptr);
-      double D = (gx + gy - 2.0 * lam) * dscale;
-      if (D < 0.0) D = 0.0;
-      const uint8_t fl = (uint8_t)(D > eps ? 1 : 0);
-      if (is_chunk) {
-        chunkD[slot] = D;
-        chunkFlag[slot] = fl;
-      } else {
-        bandD[slot] = D;
-        bandFlag[slot] = fl;
-      }
-      atomicAdd(n_rechecks, 1ull);
-    }
+    if (lane == 0)
+      recheck_finish(h, gx, gy, dscale, eps, slot, is_chunk, bandD, bandFlag, chunkD, chunkFlag, n_rechecks);
   }
 }
 
@@ -996,6 +1185,24 @@ void launch_align_chunk(Prec p, int t0, int t1, const void* frames, const Landma
                         int ref_index, const RefDesc& prior, double eps, AlignOut out, int* recheck_list,
                         int* recheck_count, int* stop, cudaStream_t st) {
   if (t1 <= t0) return;
+  if (p != P_F64 && L.N >= AT_MIN_ATOMS) {
+    thread_local int dev = -1;
+    thread_local unsigned grid = 0;
+    int d = 0;
+    cudaGetDevice(&d);
+    if (d != dev || grid == 0) {
+      int sms = 0, per = 0;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, align_chunk_block, AT_THREADS, 0);
+      grid = (unsigned)std::max(1, sms * std::max(per, 1));
+      dev = d;
+    }
+    align_chunk_block<<<std::min((unsigned)(t1 - t0), grid), AT_THREADS, 0, st>>>(
+        t0, t1, ref_index, L.N, (const float*)frames, view_of(prior), fi.c32, fi.G, L.w, L.dscale, eps, out.D,
+        out.flag, recheck_list, recheck_count, stop);
+    note_launch();
+    return;
+  }
   const unsigned need = blocks_for((size_t)(t1 - t0), WARPS_PER_BLOCK);
   if (p == P_F64)
     align_kernel<true><<<std::min(need, align_chunk_grid<true>()), 32 * WARPS_PER_BLOCK, 0, st>>>(
@@ -1010,16 +1217,29 @@ void launch_align_chunk(Prec p, int t0, int t1, const void* frames, const Landma
 
 void launch_recheck(Prec p, int max_entries, const int* list, const int* count, int W, const void* frames,
                     const LandmarkDev& L, const float4* c32, const RefDesc& prior, int chunk_ref, double eps,
-                    AlignOut band, AlignOut chunk, unsigned long long* n_rechecks, cudaStream_t st) {
+                    AlignOut band, AlignOut chunk, unsigned long long* n_rechecks, RecheckScratch scr,
+                    cudaStream_t st) {
   if (p == P_F64 || max_entries <= 0) return;
-  // the list holds the decisions within the FP32 error bound of eps, a few per chunk: a
-  // grid of at most 76 blocks whose warps loop over it (a grid sized for max_entries would
-  // spend its time starting and retiring empty blocks)
-  const unsigned blocks = std::min(blocks_for((size_t)max_entries, WARPS_PER_BLOCK), 76u);
-  recheck_kernel<<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(list, count, W, L.N, (const float*)frames,
-                                                          view_of(prior), chunk_ref, L.w64, L.dscale, eps, band.D,
-                                                          band.flag, chunk.D, chunk.flag, n_rechecks, L.wa64, c32);
+  // the list holds the decisions within the FP32 error bound of eps, a few per round: the
+  // blocks share each of the first RC_CAP entries (a slice of ~256 atoms or more each) and
+  // loop over the rest one warp per entry; at most RC_BLOCKS_MAX blocks (a grid sized for
+  // max_entries would spend its time starting and retiring empty blocks)
+  const unsigned by_atoms = blocks_for((size_t)L.N, 256);
+  const unsigned by_list = blocks_for((size_t)max_entries, RC_THREADS / 32);
+  const unsigned blocks = std::max(1u, std::min((unsigned)RC_BLOCKS_MAX, std::max(by_atoms, by_list)));
+  recheck_kernel<<<blocks, RC_THREADS, 0, st>>>(list, count, W, L.N, (const float*)frames, view_of(prior), chunk_ref,
+                                                L.w64, L.dscale, eps, band.D, band.flag, chunk.D, chunk.flag,
+                                                n_rechecks, L.wa64, c32, scr.part, scr.done);
   note_launch();
+}
+
+size_t recheck_scratch_bytes() {
+  return sizeof(double) * (size_t)RC_CAP * RC_BLOCKS_MAX * RC_PARTS + sizeof(int) * (size_t)RC_CAP;
+}
+
+RecheckScratch recheck_scratch_at(void* base) {
+  double* part = (double*)base;
+  return RecheckScratch{part, (int*)(part + (size_t)RC_CAP * RC_BLOCKS_MAX * RC_PARTS)};
 }
 
 void launch_xy_refine(Prec p, int F, const void* frames, const LandmarkDev& L, FrameInfo fi, const RefDesc& prior,

@@ -126,6 +126,7 @@ struct pcv_ctx {
   // workspace
   DevBuf c32, c64, fG, bandD, bandQ, bandF, chD, chQ, chF, rlist, rcount, recF, recRef, recD, recQ, reflist,
       segof, alist, aseg, Dbuf, Rpair, Bseg, mstat, status, nrecheck, small;
+  DevBuf rcScr;  // the FP64 re-check's partial sums and completion counts
   DevBuf Xr, Bm, GSb, GZb;  // materialised x', b and the gamma rows
   DevBuf Apk, Bpk;          // the same deviations packed for the tensor cores (FP16 h + l)
   DevBuf xtiles;            // their per-segment tile list, first rows, first tiles, count
@@ -301,10 +302,12 @@ pcv_status pcv_create(pcv_ctx** out, int device, void* cuda_stream, int precisio
   pcv_status st = ensure(c, c->small, sizeof(Small));
   if (st == PCV_OK) st = ensure(c, c->status, 16);
   if (st == PCV_OK) st = ensure(c, c->nrecheck, 16);
+  if (st == PCV_OK) st = ensure(c, c->rcScr, recheck_scratch_bytes());
   if (st == PCV_OK && (cudaHostAlloc((void**)&c->small_host, sizeof(Small), cudaHostAllocMapped) != cudaSuccess ||
                        cudaHostGetDevicePointer((void**)&c->small_host_dev, c->small_host, 0) != cudaSuccess))
     st = fail(nullptr, PCV_ENOMEM, "cudaHostAlloc (mapped) failed");
-  if (st == PCV_OK && (cudaMemset(c->status.p, 0, 16) != cudaSuccess || cudaMemset(c->nrecheck.p, 0, 16) != cudaSuccess))
+  if (st == PCV_OK && (cudaMemset(c->status.p, 0, 16) != cudaSuccess || cudaMemset(c->nrecheck.p, 0, 16) != cudaSuccess ||
+                       cudaMemset(c->rcScr.p, 0, recheck_scratch_bytes()) != cudaSuccess))
     st = fail(nullptr, PCV_ECUDA, "cudaMemset failed");
   if (st != PCV_OK) {
     g_err = c->err.empty() ? g_err : c->err;
@@ -325,7 +328,7 @@ pcv_status pcv_destroy(pcv_ctx* c) {
                     &c->wa64, &c->y, &c->Bprior, &c->c32, &c->c64,
                     &c->fG, &c->bandD, &c->bandQ, &c->bandF, &c->chD, &c->chQ, &c->chF, &c->rlist, &c->rcount,
                     &c->recF, &c->recRef, &c->recD, &c->recQ, &c->reflist, &c->segof, &c->alist, &c->aseg,
-                    &c->Dbuf, &c->Rpair, &c->Bseg, &c->Xr, &c->Bm, &c->Apk, &c->Bpk, &c->xtiles, &c->GSb, &c->GZb, &c->Nx, &c->Nb, &c->Yc, &c->Gsum, &c->Amma, &c->Bmma, &c->S6, &c->mstat, &c->status, &c->nrecheck, &c->small, &c->h_frames,
+                    &c->Dbuf, &c->Rpair, &c->Bseg, &c->Xr, &c->Bm, &c->Apk, &c->Bpk, &c->xtiles, &c->GSb, &c->GZb, &c->Nx, &c->Nb, &c->Yc, &c->Gsum, &c->Amma, &c->Bmma, &c->S6, &c->mstat, &c->status, &c->nrecheck, &c->rcScr, &c->small, &c->h_frames,
                     &c->h_s, &c->h_z, &c->h_gs, &c->h_gz, &c->h_msd, &c->h_ref, &c->grp_inst, &c->grp_tiles,
                     &c->nl_keep, &c->nlSlot, &c->nlUpd, &c->nlU, &c->nlUA, &c->nlUAseg, &c->nlN, &c->NLtab,
                     &c->Rupd, &c->Rnl, &c->nlTiles, &c->nlPart, &c->betaPart};
@@ -693,6 +696,8 @@ pcv_status nl_stage_carried(pcv_ctx* c) {
 
 // Algorithm 2 over F frames: decide every frame (reassignment / approximate and its close
 // structure), then evaluate reassignment frames exactly and the rest approximately.
+RecheckScratch rc_scratch(pcv_ctx* c) { return recheck_scratch_at(c->rcScr.p); }
+
 pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, double* z, void* gs, void* gz,
                           double* msd, uint8_t* refreshed) {
   const cudaStream_t st = c->stream;
@@ -728,7 +733,7 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
     }
     PROF(c, K_RECHECK);
     launch_recheck(c->prec, (band_from - from) * W, rl, rc, W, frames, L, fi.c32, prior, -1, c->eps, band, chunk,
-                   (unsigned long long*)c->nrecheck.p, st);
+                   (unsigned long long*)c->nrecheck.p, rc_scratch(c), st);
     band_from = from;
   };
   // host-driven refresh search
@@ -779,7 +784,7 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
     {
       PROF(c, K_RECHECK);
       launch_recheck(c->prec, t1 - t, rl, rc, W, frames, L, fi.c32, prior, ref, c->eps, band, chunk,
-                     (unsigned long long*)c->nrecheck.p, st);
+                     (unsigned long long*)c->nrecheck.p, rc_scratch(c), st);
     }
     {
       PROF(c, K_FIRST);

@@ -84,11 +84,19 @@ void launch_align_band(Prec p, int F, int W, int t_lo, int t_hi, const void* fra
 void launch_align_chunk(Prec p, int t0, int t1, const void* frames, const LandmarkDev& L,
                         FrameInfo fi, int ref_index, const RefDesc& prior, double eps,
                         AlignOut out, int* recheck_list, int* recheck_count, int* stop, cudaStream_t st);
-// FP64 re-check of the ambiguous alignments listed in `list` (entries encode slot kind)
+// FP64 re-check of the ambiguous alignments listed in `list` (entries encode slot kind).
+// Scratch: the blocks' partial sums of the shared entries and their completion counts
+// (recheck_scratch_bytes(); the counts zero on first use, and every launch leaves them zero).
+struct RecheckScratch {
+  double* part;
+  int* done;
+};
+size_t recheck_scratch_bytes();
+RecheckScratch recheck_scratch_at(void* base);  // views of a buffer of that size
 void launch_recheck(Prec p, int max_entries, const int* list, const int* count, int W,
                     const void* frames, const LandmarkDev& L, const float4* c32, const RefDesc& prior,
                     int chunk_ref, double eps, AlignOut band, AlignOut chunk, unsigned long long* n_rechecks,
-                    cudaStream_t st);
+                    RecheckScratch scr, cudaStream_t st);
 // recheck list entries: (slot << 1) | kind, kind 0 = band slot t*W + k-1, 1 = chunk slot t
 // accurate quaternions of R_xy for the approximate frames (FP32 modes; FP64 mode keeps the
 // FP64 band / chunk quaternions)
