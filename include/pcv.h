@@ -264,11 +264,11 @@ enum {
                               then returns PCV_ETIMEOUT.  Small values exist to exercise
                               that report.                                                */
   PCV_OPT_MMA_GROUP = 12    /* tensor-core approximate MSDs (PCV_OPT_TENSOR_CORES = 1): chunks
-                              of 16 deviation components summed in tensor memory before the
-                              partial sums are added into FP32 totals (1..8, default 2).
-                              Each accumulation step can lose about one unit in the last
-                              place of the running sum, so shorter groups are more accurate
-                              and cost more folding work.                                 */
+                              of 16 deviation components whose main products are summed in
+                              tensor memory before the partial sums are added into FP32
+                              totals (1..16, default 4).  Each accumulation step can lose
+                              about one unit in the last place of the running sum, so
+                              shorter groups are more accurate and cost more folding work.  */
 };
 PCV_API pcv_status pcv_set_option(pcv_ctx* ctx, int key, int64_t value);
 

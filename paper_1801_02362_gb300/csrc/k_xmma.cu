@@ -11,14 +11,18 @@
 //     is h h' + h l' + l h' (three MMAs, products exact in the FP32 accumulator; the dropped
 //     l l' is ~2^-22 relative).  The 2^8 scale keeps l out of the FP16 subnormal range for
 //     deviations above ~5e-4 nm and the largest deviations (up to 256 nm) finite;
-//   * short accumulation chains: each accumulation into the tensor-memory accumulator
-//     loses up to about one unit in the last place of the running sum, so the accumulator
-//     only ever sums a group of a few chunks of 16 components (three MMAs each); then fold
-//     warps add it into Kahan-compensated FP32 totals in registers (total and running
-//     correction, so the hundreds of folds of a long row add no rounding of the running
-//     total: four FP32 operations per column, which keeps the fold as fast as the MMAs)
-//     while the other accumulator buffer takes the next group, so the MMAs never wait for
-//     a fold.  Two registers per column limit a tile to 128 landmarks.
+//   * short accumulation chains: each accumulation into a tensor-memory accumulator
+//     loses up to about one unit in the last place of the running sum, so the main
+//     products h h' go to an accumulator that only ever sums a group of a few chunks of 16
+//     components (one MMA each); then fold warps add it into Kahan-compensated FP32 totals
+//     in registers (total and running correction, so the hundreds of folds of a long row
+//     add no rounding of the running total) while the other accumulator buffer takes the
+//     next group.  The correction products h l' + l h', 2^-11 of the main ones, go to a
+//     third accumulator that sums the whole row and is folded once at the end: its
+//     roundings are 2^-11 smaller, and the main accumulator takes one addition per chunk
+//     instead of three, so a group can be three times as long for the same accuracy and
+//     the fold (four FP32 operations per column) runs a third as often.  Two registers per
+//     column limit a tile to 128 landmarks.
 // Operands are packed once per step (pack_deviations_kernel writes the landmarks' operand
 // together with the segment adjoint's, pack_frames_kernel the frames') in the canonical
 // K-major layout without swizzling
@@ -49,11 +53,12 @@ constexpr int XM_ROWS = 128;     // MMA M: approximate frames per tile
 constexpr int XM_BN_MAX = 128;   // landmarks per tile (MMA N), multiple of 16
 constexpr int XM_KC = 16;        // components per chunk: one MMA (K = 16) per product
 constexpr int XM_STAGES = 12;    // 16 KB each: about 1.3 us of MMAs in flight
-constexpr int XM_GROUP_MAX = 8;  // chunks summed in tensor memory before a fold (the
+constexpr int XM_GROUP_MAX = 16;  // chunks summed in tensor memory before a fold (the
                                  // context's PCV_OPT_MMA_GROUP, 1..8)
 constexpr int XM_FOLD_WARPS = 8;  // two per tensor-memory lane quarter (column halves)
 constexpr int XM_THREADS = 32 * (XM_FOLD_WARPS + 2);  // + the copy warp and the MMA warp
-constexpr int XM_TMEM_COLS = 2 * XM_BN_MAX;           // two accumulators
+constexpr int XM_TMEM_COLS = 4 * XM_BN_MAX;           // two main accumulators, the corrections'
+                                                      // (and one unused: a power of two)
 constexpr uint32_t XM_A_PART = XM_ROWS * XM_KC * 2;   // bytes of the h (or l) part of an A block
 constexpr uint32_t XM_STAGE_BYTES = 2 * XM_A_PART + 2 * XM_BN_MAX * XM_KC * 2;
 constexpr float XM_SCALE = 256.0f;              // 2^8 on every operand
@@ -450,7 +455,7 @@ __global__ void __launch_bounds__(XM_THREADS, 1) approx_cross_mma(XmmaArgs p) {
             break;
           }
           tc_fence_after();
-          const uint32_t acc = tmem + (uint32_t)(buf * XM_BN_MAX);
+          const uint32_t acc = tmem + (uint32_t)(buf * XM_BN_MAX), cacc = tmem + (uint32_t)(2 * XM_BN_MAX);
           const int c0 = gr * G, c1 = min(nck, c0 + G);
           for (int c = c0; c < c1; ++c) {
             const int g = g0 + c, st = g % XM_STAGES;
@@ -464,11 +469,11 @@ __global__ void __launch_bounds__(XM_THREADS, 1) approx_cross_mma(XmmaArgs p) {
             const uint32_t bh = ah + 2 * XM_A_PART, bl = bh + b_part;
             const uint64_t dah = smem_desc(ah, 128, 256), dal = smem_desc(al, 128, 256);
             const uint64_t dbh = smem_desc(bh, 128, 256), dbl = smem_desc(bl, 128, 256);
-            // the two small correction products first, the main product last: in a group of
-            // one chunk only its addition is rounded at the scale of the chunk's sum
-            mma_f16(acc, dah, dbl, idesc, c > c0 ? 1u : 0u);
-            mma_f16(acc, dal, dbh, idesc, 1u);
-            mma_f16(acc, dah, dbh, idesc, 1u);
+            // the two small correction products into the row's correction accumulator, the
+            // main product into the group's
+            mma_f16(cacc, dah, dbl, idesc, c > 0 ? 1u : 0u);
+            mma_f16(cacc, dal, dbh, idesc, 1u);
+            mma_f16(acc, dah, dbh, idesc, c > c0 ? 1u : 0u);
             mma_commit(smem_u32(&empty[st]));
           }
           if (!failed) mma_commit(smem_u32(&accf[buf]));
@@ -492,7 +497,9 @@ __global__ void __launch_bounds__(XM_THREADS, 1) approx_cross_mma(XmmaArgs p) {
           break;
         }
         tc_fence_after();
-        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * XM_BN_MAX + col0);
+        // the last group's commit also covers every correction MMA: fold that accumulator too
+        for (int pass = 0; pass < (gr == ngrp - 1 ? 2 : 1); ++pass) {
+        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((pass ? 2 : buf) * XM_BN_MAX + col0);
 #pragma unroll
         for (int b = 0; b < XM_BN_MAX / 32; ++b) {
           if (b * 16 < ncol) {
@@ -510,6 +517,7 @@ __global__ void __launch_bounds__(XM_THREADS, 1) approx_cross_mma(XmmaArgs p) {
               sum = t2;
             }
           }
+        }
         }
         tc_fence_before();
         __syncwarp();

@@ -91,7 +91,7 @@ void note_launch(int n) { t_launches += n; }
 struct pcv_ctx {
   int device = 0;
   int newton_cap = 60;                  // PCV_OPT_NEWTON_CAP
-  int mma_group = 2;                    // PCV_OPT_MMA_GROUP
+  int mma_group = 4;                    // PCV_OPT_MMA_GROUP
   long long wait_cycles = 4000000000LL;  // PCV_OPT_WAIT_CYCLES
   cudaStream_t stream = nullptr;
   Prec prec = P_F32;
@@ -217,6 +217,10 @@ pcv_status fail(pcv_ctx* c, pcv_status st, const char* fmt, ...) {
 pcv_status ensure(pcv_ctx* c, DevBuf& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (b.bytes >= bytes) return PCV_OK;
+  // a launch error still pending is reported here: a failed allocation below clears the
+  // runtime's error state, which would hide it from the caller's final check
+  const cudaError_t pending = cudaGetLastError();
+  if (pending != cudaSuccess) return fail(c, PCV_ECUDA, "kernel launch: %s", cudaGetErrorString(pending));
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
   b.bytes = 0;
@@ -415,7 +419,7 @@ pcv_status pcv_set_option(pcv_ctx* c, int key, int64_t value) {
       c->wait_cycles = value == 0 ? 4000000000LL : (long long)value;
       return PCV_OK;
     case PCV_OPT_MMA_GROUP:
-      if (value < 1 || value > 8) return fail(c, PCV_EINVAL, "MMA group must be in 1..8");
+      if (value < 1 || value > 16) return fail(c, PCV_EINVAL, "MMA group must be in 1..16");
       c->mma_group = (int)value;
       return PCV_OK;
     case PCV_OPT_EXACT_TILE:

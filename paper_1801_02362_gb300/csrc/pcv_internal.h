@@ -37,7 +37,7 @@ struct LandmarkDev {
   long long wait_cycles = 4000000000LL;
   // chunks of 16 deviation components the tensor-core MSD kernel sums in tensor memory
   // before folding them into its FP32 totals
-  int mma_group = 2;
+  int mma_group = 4;
 };
 // FP16 storage keeps, per landmark and block of 16 consecutive atoms, an FP32 offset (the
 // block's mean centred coordinate) and the FP16 residuals: coordinate = offset + residual

@@ -208,8 +208,8 @@ def test_close_split_calls_and_saved_state(pcv):
 def test_close_materialized_operands(pcv, precision, n, m, variant):
     """Long segments (20 refreshes in 700 frames): the rotated frames x' and the rotated
     landmarks b of each segment are materialised and both heavy loops run as plain tiles;
-    the segment adjoint runs on the tensor cores (3xTF32 on deviations from the close
-    structure) or on the CUDA cores.  N = 140 pads to 144 atoms (a half tile of 32 at the
+    the approximate MSDs and the segment adjoint run on the tensor cores (split FP16 operands
+    on deviations from the close structure) or on the CUDA cores.  N = 140 pads to 144 atoms (a half tile of 32 at the
     end) and 420 adjoint columns (two column tiles of 224); N = 61 to 64 atoms and 183
     columns (one tile of 192); M = 45 and 200 take the two landmark tile widths and pad the
     tensor-core K to 48 and 208; 700 frames end in a ragged tile of 64.  The second call
@@ -233,6 +233,29 @@ def test_close_materialized_operands(pcv, precision, n, m, variant):
     check_values(g, r, fr, lm, lam, precision)
     assert grad_err(g["dsdx"], r["dsdx"]) < GRAD_TOL[precision]
     assert grad_err(g["dzdx"], r["dzdx"]) < GRAD_TOL[precision]
+
+
+@pytest.mark.parametrize("group", [1, 4, 8])
+def test_close_mma_fold_groups(pcv, group):
+    """Tensor-core approximate MSDs with 1, 4 (the default) and 8 chunks of main products
+    summed in tensor memory per fold, on 300 atoms and 200 landmarks, where each extra
+    accumulation step shows in the MSD error: all within the FP32 tolerance of the oracle.
+    The option rejects groups outside 1..16."""
+    lm, fr, lam = problem(7, 300, 200, 1500)
+    eps = 0.05
+    r = oracle.close(fr, lm, lam, eps)
+    ctx = pcv.PathCV(lm, lam, eps=eps, precision="fp32", tensor_cores=True)
+    pcv.pcv_set_option(ctx.ctx, pcv.PCV_OPT_MMA_GROUP, group)
+    ctx.set_profiling(True)
+    g = run(pcv, lm, fr, lam, ctx=ctx)
+    assert "approx_pair_mma" in ctx.profile()
+    np.testing.assert_array_equal(g["refreshed"], r["refreshed"])
+    check_values(g, r, fr, lm, lam, "fp32")
+    for bad in (0, 17):
+        with pytest.raises(pcv.PcvError) as e:
+            pcv.pcv_set_option(ctx.ctx, pcv.PCV_OPT_MMA_GROUP, bad)
+        assert e.value.status == pcv.PCV_EINVAL
+    ctx.close()
 
 
 def test_close_fp64_workload_c1(pcv):
