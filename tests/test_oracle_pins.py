@@ -465,6 +465,46 @@ def test_results_do_not_depend_on_the_thread_count():
             np.testing.assert_array_equal(a[k], b[k])
 
 
+def test_given_distances_enter_the_derivatives_only_through_the_weights():
+    """With fixed geometry the derivatives of Eqs. 5-6 are linear in the weights:
+    dz/dx = sum_i p_i dD_i/dx and ds/dx = -lambda sum_i p_i (q_i - s) dD_i/dx (softmax
+    derivative), with dD_i/dx set by the structures alone.  With two landmarks one set of
+    given distances fixes dD_1/dx and dD_2/dx (a 2 x 2 system per coordinate, determinant
+    -lambda p_1 p_2 (q_2 - q_1)); a second set must then give exactly the predicted
+    gradients, and so must the oracle's own distances.  A derivative that used the computed
+    instead of the given distances, or dropped the softmax's mean term, fails this."""
+    lm, fr, lam = problem(29, 13, 2, 8, noise=0.02, schedule="walk", ou_rho=0.9)
+    eps = 0.002
+    q = np.array([1.0, 2.0])
+    rng = np.random.default_rng(5)
+
+    def run(D_in):
+        r = oracle.close(fr, lm, lam, eps, want_grad=True, D_in=D_in)
+        e = np.exp(-lam * (r["D"] - r["D"].min(axis=1, keepdims=True)))
+        pw = e / e.sum(axis=1, keepdims=True)
+        sv = pw @ q
+        return r, pw, -lam * pw * (q[None, :] - sv[:, None])
+
+    def given():
+        base = rng.uniform(0.01, 0.02, (fr.shape[0], 1))
+        return base + np.concatenate([np.zeros_like(base), rng.uniform(-1.5, 1.5, base.shape) / lam], axis=1)
+
+    rA, pA, gA = run(given())
+    assert np.all(rA["refreshed"] == oracle.close(fr, lm, lam, eps)["refreshed"])
+    G = np.empty((fr.shape[0], 2, fr.shape[1] * 3))
+    for t in range(fr.shape[0]):
+        A = np.array([pA[t], gA[t]])
+        rhs = np.stack([rA["dzdx"][t].ravel(), rA["dsdx"][t].ravel()])
+        G[t] = np.linalg.solve(A, rhs)
+    for D_in in (given(), None):
+        r, pw, gs = run(D_in)
+        np.testing.assert_allclose(r["s"], pw @ q, rtol=1e-13, atol=0)
+        for t in range(fr.shape[0]):
+            scale = np.abs(G[t]).max()
+            np.testing.assert_allclose(r["dzdx"][t].ravel(), pw[t] @ G[t], rtol=0, atol=1e-10 * scale)
+            np.testing.assert_allclose(r["dsdx"][t].ravel(), gs[t] @ G[t], rtol=0, atol=1e-10 * lam * scale)
+
+
 def test_given_distances_enter_only_through_the_weights():
     """The oracle's distance injection (used to separate a derivative's error from that of
     the distances it was evaluated at): the path CVs of Eq. (property_map_cv) are invariant
