@@ -9,9 +9,11 @@
 //     reassignments): 18 FMA per (frame, landmark, atom) for s and z together;
 //   adjoint_beta_seg: frames that share a close structure share Rot_i, so b_i = Rot_i a_i
 //     is formed once per tile and beta = sum_i gamma_i b_i is a plain GEMM: 6 FMA.
-// adjoint_finish_warp (one warp per frame) turns beta into gradients and adds, at
-// approximate frames, the rotation term of Eq. (close_der_dist) (derivation in
-// pcv_device.cuh: adjoint_rotation_term).
+// The finish kernels turn beta into gradients and add, at approximate frames, the rotation
+// term of Eq. (close_der_dist) (derivation in pcv_device.cuh: adjoint_rotation_term):
+// adjoint_finish_staged (FP32 modes, a warp per frame staged in shared memory),
+// adjoint_finish_block (FP32 modes, structures too large to stage: a block per frame) and
+// adjoint_finish_warp (FP64: a warp per frame).
 #include <algorithm>
 
 #include <cuda_fp16.h>
@@ -665,6 +667,273 @@ adjoint_finish_warp(int F, int M, int N, const FT* __restrict__ frames, const fl
 }
 
 // ---------------------------------------------------------------------------------------
+// Per-frame finish for the FP32 modes on structures too large to stage (12 N floats over
+// 200 KB: N > 4266 atoms): one block of FB_THREADS per frame, in a persistent grid of
+// FB_BLOCKS_PER_SM blocks per SM.  A warp per frame left each 5000-atom frame's passes to
+// 32 lanes (17% of the warps active, 25% of the DRAM peak); here 128 threads share them,
+// and four blocks per SM let one frame's reductions and 4x4 algebra overlap the other
+// frames' passes (5000 atoms, 2000 landmarks, 10k frames: 1.65 -> 1.41 ms).  256-thread
+// blocks, 2 per SM, took 1.71 ms; staging the rows through shared memory in coalesced
+// chunks, 1.49 ms; unrolling the atom loops, no change.  Gamma comes from Gsum and Phi
+// from the segment moments S6 when given (else from P, Bseg and A32); the arithmetic is
+// that of adjoint_finish_staged, with block sums in place of warp sums.
+constexpr int FB_THREADS = 128, FB_WARPS = FB_THREADS / 32, FB_BLOCKS_PER_SM = 4;
+constexpr int FB_SUMS = 51;  // 27 (X^s, X^z, H_xy) + 12 (Phi) + 12 (alignment-weight sums)
+
+// totals of the K per-thread values v over the block, in tot[0..K) (every thread calls it;
+// two barriers; red holds FB_WARPS x FB_SUMS floats)
+template <int K>
+__device__ __forceinline__ void fb_block_sums(const float* v, float (*red)[FB_SUMS], float* tot) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float t = wsum(v[k]);
+    if (lane == 0) red[w][k] = t;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < K) {
+    float t = 0.0f;
+    for (int ww = 0; ww < FB_WARPS; ++ww) t += red[ww][threadIdx.x];
+    tot[threadIdx.x] = t;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(FB_THREADS)
+adjoint_finish_block(int F, int M, int N, const float* __restrict__ frames, const float4* __restrict__ c32,
+                     const float* __restrict__ wts, const float* __restrict__ wa, float wuni,
+                     const float* __restrict__ A32, const float* __restrict__ q32, const float* __restrict__ P,
+                     const double* __restrict__ s, float lambda, const float* __restrict__ Gsum,
+                     const float* __restrict__ S6, int seg_base, const float* __restrict__ Bseg,
+                     const int* __restrict__ seg_of_frame, FrameRec rec, const float* __restrict__ prior_coords,
+                     float4 prior_c, float* __restrict__ gs, float* __restrict__ gz) {
+  __shared__ float red[FB_WARPS][FB_SUMS];
+  __shared__ float tot[FB_SUMS + 2];  // the sums, then Gamma^s, Gamma^z when not given
+  __shared__ float s_T[24];           // Ts, Tz, Cs, Cz
+  const int tid = threadIdx.x, N3 = 3 * N;
+  for (int f = blockIdx.x; f < F; f += gridDim.x) {
+    const float4 c = c32[f];
+    const float cx[3] = {c.x, c.y, c.z};
+    const float* x = frames + (size_t)f * N3;
+    float* gsp = gs + (size_t)f * N3;
+    float* gzp = gz + (size_t)f * N3;
+    const bool approx = rec.flag && rec.flag[f] == 0;
+    const int r = rec.flag ? rec.ref[f] : 0;
+    const int seg = rec.flag ? seg_of_frame[f] : 0;
+    const float sf = (float)s[f], sl = s_low<float>(s[f], sf);
+    // landmarks: Gamma when not given; Phi = sum_i gamma_i S_i at approximate frames
+    float lv[14];
+#pragma unroll
+    for (int e = 0; e < 14; ++e) lv[e] = 0.0f;
+    if (approx || !Gsum) {
+      for (int i = tid; i < M; i += FB_THREADS) {
+        float gsv, gzv;
+        gammas<float>(P[(size_t)f * M + i], lambda, q32[i], sf, sl, gsv, gzv);
+        lv[12] += gsv;
+        lv[13] += gzv;
+        if (approx) {
+          float S[6];
+          if (S6) {
+            const float* sp = S6 + ((size_t)(seg - seg_base) * M + i) * 6;
+#pragma unroll
+            for (int e = 0; e < 6; ++e) S[e] = sp[e];
+          } else {
+            const float* B = Bseg + ((size_t)seg * M + i) * 9;
+            const float* a = A32 + (size_t)i * 6;
+            const float A[9] = {a[0], a[1], a[2], a[1], a[3], a[4], a[2], a[4], a[5]};
+            float BA[9];
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+#pragma unroll
+              for (int cc = 0; cc < 3; ++cc)
+                BA[3 * b + cc] = B[3 * b] * A[cc] + B[3 * b + 1] * A[3 + cc] + B[3 * b + 2] * A[6 + cc];
+            const int ib[6] = {0, 0, 0, 1, 1, 2}, ic[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+            for (int e = 0; e < 6; ++e) {
+              const int b = ib[e], cc = ic[e];
+              S[e] = BA[3 * b] * B[3 * cc] + BA[3 * b + 1] * B[3 * cc + 1] + BA[3 * b + 2] * B[3 * cc + 2];
+            }
+          }
+#pragma unroll
+          for (int e = 0; e < 6; ++e) {
+            lv[e] = fmaf(gsv, S[e], lv[e]);
+            lv[6 + e] = fmaf(gzv, S[e], lv[6 + e]);
+          }
+        }
+      }
+    }
+    if (!approx) {
+      // exact frame: Gamma, and with alignment weights the centre term's sums
+      float v[8] = {lv[12], lv[13], 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+      if (wa) {
+        for (int j = tid; j < N; j += FB_THREADS) {
+          const float wj = wts ? wts[j] : wuni;
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            v[2 + b] = fmaf(wj, x[3 * j + b] - cx[b], v[2 + b]);
+            v[5 + b] = fmaf(wj, gsp[3 * j + b], v[5 + b]);
+          }
+        }
+      }
+      fb_block_sums<8>(v, red, tot);
+      const float Gs = Gsum ? Gsum[2 * f] : tot[0];
+      const float Gz = Gsum ? Gsum[2 * f + 1] : tot[1];
+      float Ss[3] = {0.0f, 0.0f, 0.0f}, Sz[3] = {0.0f, 0.0f, 0.0f};
+      if (wa) {
+        float xw[3], bws[3], vz[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          xw[b] = tot[2 + b];
+          bws[b] = tot[5 + b];
+        }
+        // beta^z's weighted sums: a second reduction (tot is rewritten after the barrier)
+        for (int j = tid; j < N; j += FB_THREADS) {
+          const float wj = wts ? wts[j] : wuni;
+#pragma unroll
+          for (int b = 0; b < 3; ++b) vz[b] = fmaf(wj, gzp[3 * j + b], vz[b]);
+        }
+        __syncthreads();  // every thread has read tot
+        fb_block_sums<3>(vz, red, tot);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          Ss[b] = Gs * xw[b] - bws[b];
+          Sz[b] = Gz * xw[b] - tot[b];
+        }
+      }
+      for (int e = tid; e < N3; e += FB_THREADS) {
+        const float wj = wts ? wts[e / 3] : wuni, w2 = wa ? wa[e / 3] : 0.0f;
+        const int b = e - 3 * (e / 3);
+        const float xv = x[e] - cx[b];
+        gsp[e] = 2.0f * wj * (Gs * xv - gsp[e]) - 2.0f * w2 * Ss[b];
+        gzp[e] = 2.0f * wj * (Gz * xv - gzp[e]) - 2.0f * w2 * Sz[b];
+      }
+      __syncthreads();  // tot is reused by the next frame
+      continue;
+    }
+    const float* y = r >= 0 ? frames + (size_t)r * N3 : prior_coords;
+    const float4 cyv = r >= 0 ? c32[r] : prior_c;
+    const float cy[3] = {cyv.x, cyv.y, cyv.z};
+    // pass 1: X = sum_j w x_j beta_j^T (s, z), H_xy = sum_j w y_j x_j^T, centred, true
+    // weights; with alignment weights also X_w, Y_w and the weighted beta sums
+    float v[FB_SUMS];
+#pragma unroll
+    for (int e = 0; e < FB_SUMS; ++e) v[e] = 0.0f;
+#pragma unroll
+    for (int e = 0; e < 12; ++e) v[27 + e] = lv[e];
+#pragma unroll 2
+    for (int j = tid; j < N; j += FB_THREADS) {
+      const float wj = wts ? wts[j] : wuni;
+      float xv[3], u[3], bs[3], bz[3];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        xv[b] = x[3 * j + b] - cx[b];
+        u[b] = y[3 * j + b] - cy[b];
+        bs[b] = gsp[3 * j + b];
+        bz[b] = gzp[3 * j + b];
+      }
+      if (wa) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          v[39 + b] = fmaf(wj, xv[b], v[39 + b]);
+          v[42 + b] = fmaf(wj, u[b], v[42 + b]);
+          v[45 + b] = fmaf(wj, bs[b], v[45 + b]);
+          v[48 + b] = fmaf(wj, bz[b], v[48 + b]);
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const float wv = wj * xv[b], wu = wj * u[b];
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+          v[3 * b + cc] = fmaf(wv, bs[cc], v[3 * b + cc]);
+          v[9 + 3 * b + cc] = fmaf(wv, bz[cc], v[9 + 3 * b + cc]);
+          v[18 + 3 * b + cc] = fmaf(wu, xv[cc], v[18 + 3 * b + cc]);
+        }
+      }
+    }
+    fb_block_sums<FB_SUMS>(v, red, tot);
+    if (!Gsum) {
+      const float g2[2] = {lv[12], lv[13]};
+      fb_block_sums<2>(g2, red, tot + FB_SUMS);
+    }
+    const float Gs = Gsum ? Gsum[2 * f] : tot[FB_SUMS];
+    const float Gz = Gsum ? Gsum[2 * f + 1] : tot[FB_SUMS + 1];
+    const double4 qq = rec.qxy[f];
+    const float qxy[4] = {(float)qq.x, (float)qq.y, (float)qq.z, (float)qq.w};
+    float R[9];
+    quat_to_rot(qxy, R);
+    if (tid == 0) {
+      float acc[27], Ts[9], Tz[9];
+#pragma unroll
+      for (int e = 0; e < 27; ++e) acc[e] = tot[e];
+      const float Ps[9] = {tot[27], tot[28], tot[29], tot[28], tot[30], tot[31], tot[29], tot[31], tot[32]};
+      const float Pz[9] = {tot[33], tot[34], tot[35], tot[34], tot[36], tot[37], tot[35], tot[37], tot[38]};
+      adjoint_rotation_terms2<float>(acc + 18, R, qxy, acc, acc + 9, Ps, Pz, Ts, Tz);
+      float Cs[3] = {0.0f, 0.0f, 0.0f}, Cz[3] = {0.0f, 0.0f, 0.0f};
+      if (wa) {
+        // alignment weights: -w'_k (2 S + T^T Y_w), S = Gamma X_w - R sum_j w_j beta^y_j
+        const float* xw = tot + 39;
+        const float* yw = tot + 42;
+        const float* bws = tot + 45;
+        const float* bwz = tot + 48;
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+          const float Rbs = R[3 * cc] * bws[0] + R[3 * cc + 1] * bws[1] + R[3 * cc + 2] * bws[2];
+          const float Rbz = R[3 * cc] * bwz[0] + R[3 * cc + 1] * bwz[1] + R[3 * cc + 2] * bwz[2];
+          Cs[cc] = 2.0f * (Gs * xw[cc] - Rbs) + Ts[cc] * yw[0] + Ts[3 + cc] * yw[1] + Ts[6 + cc] * yw[2];
+          Cz[cc] = 2.0f * (Gz * xw[cc] - Rbz) + Tz[cc] * yw[0] + Tz[3 + cc] * yw[1] + Tz[6 + cc] * yw[2];
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 9; ++e) {
+        s_T[e] = Ts[e];
+        s_T[9 + e] = Tz[e];
+      }
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        s_T[18 + e] = Cs[e];
+        s_T[21 + e] = Cz[e];
+      }
+    }
+    __syncthreads();
+    float Ts[9], Tz[9], Cs[3], Cz[3];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      Ts[e] = s_T[e];
+      Tz[e] = s_T[9 + e];
+    }
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      Cs[e] = s_T[18 + e];
+      Cz[e] = s_T[21 + e];
+    }
+    // pass 2: the gradient rows over beta
+#pragma unroll 2
+    for (int j = tid; j < N; j += FB_THREADS) {
+      const float wj = wts ? wts[j] : wuni, w2 = wa ? wa[j] : 0.0f;
+      float xv[3], u[3], bsj[3], bzj[3];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        xv[b] = x[3 * j + b] - cx[b];
+        u[b] = y[3 * j + b] - cy[b];
+        bsj[b] = gsp[3 * j + b];
+        bzj[b] = gzp[3 * j + b];
+      }
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) {
+        const float Rbs = R[3 * cc] * bsj[0] + R[3 * cc + 1] * bsj[1] + R[3 * cc + 2] * bsj[2];
+        const float Rbz = R[3 * cc] * bzj[0] + R[3 * cc + 1] * bzj[1] + R[3 * cc + 2] * bzj[2];
+        const float ts = Ts[cc] * u[0] + Ts[3 + cc] * u[1] + Ts[6 + cc] * u[2];
+        const float tz = Tz[cc] * u[0] + Tz[3 + cc] * u[1] + Tz[6 + cc] * u[2];
+        gsp[3 * j + cc] = 2.0f * wj * (Gs * xv[cc] - Rbs) + wj * ts - w2 * Cs[cc];
+        gzp[3 * j + cc] = 2.0f * wj * (Gz * xv[cc] - Rbz) + wj * tz - w2 * Cz[cc];
+      }
+    }
+    __syncthreads();  // red, tot and s_T are reused by the next frame
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // S_i = R_{a_i y} A_i R_{a_i y}^T (xx xy xz yy yz zz) for every landmark of the segments
 // [seg_base, seg_base + nseg): the per-landmark part of Phi, shared by a segment's frames.
 __global__ void seg_moments_kernel(int seg_base, int nseg, int M, const float* __restrict__ Bseg,
@@ -1122,17 +1391,23 @@ void launch_adjoint_finish(Prec p, int F, const void* frames, const LandmarkDev&
     note_launch();
     return;
   }
-  const unsigned blocks = (unsigned)((F + 3) / 4);
-  if (p == P_F64)
-    adjoint_finish_warp<double, double><<<blocks, 128, 0, st>>>(
-        F, L.M, L.N, (const double*)frames, fi.c32, fi.c64, L.w, L.w64, L.wa, L.wa64, L.A32, L.A, L.q, L.q32, L.dscale,
-        (const double*)P, s, lambda, (const double*)Bseg, seg_of_frame, rec, (const double*)prior.coords, prior.c64,
-        (double*)gs, (double*)gz);
-  else
-    adjoint_finish_warp<float, float><<<blocks, 128, 0, st>>>(
-        F, L.M, L.N, (const float*)frames, fi.c32, fi.c64, L.w, L.w64, L.wa, L.wa64, L.A32, L.A, L.q, L.q32, L.dscale,
-        (const float*)P, s, lambda, (const float*)Bseg, seg_of_frame, rec, (const float*)prior.coords,
-        make_double4(prior.c32.x, prior.c32.y, prior.c32.z, 0.0), (float*)gs, (float*)gz);
+  if (p != P_F64) {  // too large to stage: a block per frame
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned blocks = (unsigned)std::min<long long>(F, (long long)FB_BLOCKS_PER_SM * std::max(sms, 1));
+    adjoint_finish_block<<<blocks, FB_THREADS, 0, st>>>(
+        F, L.M, L.N, (const float*)frames, fi.c32, L.w, L.wa, (float)L.dscale, L.A32, L.q32, (const float*)P, s,
+        (float)lambda, Gsum, S6, seg_base, (const float*)Bseg, seg_of_frame, rec, (const float*)prior.coords,
+        prior.c32, (float*)gs, (float*)gz);
+    note_launch();
+    return;
+  }
+  const unsigned blocks = (unsigned)((F + 3) / 4);  // FP64: a warp per frame
+  adjoint_finish_warp<double, double><<<blocks, 128, 0, st>>>(
+      F, L.M, L.N, (const double*)frames, fi.c32, fi.c64, L.w, L.w64, L.wa, L.wa64, L.A32, L.A, L.q, L.q32, L.dscale,
+      (const double*)P, s, lambda, (const double*)Bseg, seg_of_frame, rec, (const double*)prior.coords, prior.c64,
+      (double*)gs, (double*)gz);
   note_launch();
 }
 

@@ -186,6 +186,11 @@ __device__ __forceinline__ void exact_tile_f32(int rows, const int* __restrict__
   __shared__ __align__(16) float As[KC * 3][PM];
   __shared__ int s_frame[TF];
   __shared__ float s_c[TF][3];
+  // per-thread totals of the correlation sums: each KC-atom chunk is summed in registers
+  // and then added here, so the longest rounding chain is KC + N / KC terms instead of N
+  // (at 4400 atoms the single chain put ~1e-4 into H, hence into R and the exact frames'
+  // gradients; the MSD itself is stationary in R)
+  __shared__ float Hs[36][EX_THREADS];
 
   if (row0 >= rows) return;
   const int tid = threadIdx.x;
@@ -204,6 +209,9 @@ __device__ __forceinline__ void exact_tile_f32(int rows, const int* __restrict__
     for (int v = 0; v < 2; ++v)
 #pragma unroll
       for (int e = 0; e < 9; ++e) h[u][v][e] = 0.0f;
+  if (!APPROX)
+#pragma unroll
+    for (int e = 0; e < 36; ++e) Hs[e][tid] = 0.0f;
 
   for (int j0 = 0; j0 < (APPROX ? 0 : N); j0 += KC) {
     stage_exact<float, LT, float, TF, TM, KC, PF, PM>(j0, N, M, i0, frames, lm, lmoff, wts, 1, s_frame, s_c, Xs, As,
@@ -226,8 +234,24 @@ __device__ __forceinline__ void exact_tile_f32(int rows, const int* __restrict__
 #pragma unroll
             for (int c = 0; c < 3; ++c) h[u][v][3 * b + c] = fmaf(a[v][b], x[u][c], h[u][v][3 * b + c]);
     }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int v = 0; v < 2; ++v)
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+          Hs[(2 * u + v) * 9 + e][tid] += h[u][v][e];
+          h[u][v][e] = 0.0f;
+        }
     __syncthreads();
   }
+  if (!APPROX)
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int v = 0; v < 2; ++v)
+#pragma unroll
+        for (int e = 0; e < 9; ++e) h[u][v][e] = Hs[(2 * u + v) * 9 + e][tid];
 
   // rotations of the four pairs
   float R[2][2][9];

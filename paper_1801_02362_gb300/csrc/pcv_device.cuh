@@ -450,12 +450,16 @@ __device__ __forceinline__ bool top_quat_f32(const float* Hin, float ub, float* 
     }
     prev = a;
   }
-  // P'(l) = prod_k (l - lambda_k) over the other eigenvalues: below 0.002 l^3 the top
-  // eigenvalue is (nearly) double (relative gap below ~5e-4).  Newton then converges only
-  // linearly and l carries an error of ~sqrt(u) relative, which the adjugate column
-  // inherits; the Jacobi iteration does not degrade there.
+  // P'(l) = prod_k (l - lambda_k) over the other eigenvalues: small when the top eigenvalue
+  // is (nearly) double.  Newton then converges only linearly and stops at its noise floor,
+  // |l - lambda| ~ sqrt(u) ~ 3e-4 of the bound, which the adjugate column inherits; there
+  // P'(l) ~ 2 |l - lambda| prod_{k > 2} (lambda - lambda_k) reaches a few 1e-3 l^3
+  // (eigenvalues in [-1, 1] after the scaling).  Below 0.02 l^3 (a double root at the noise floor,
+  // or a relative gap below ~5e-3) the eigenvector comes from the Jacobi iteration, which
+  // does not degrade there.  (A bar of 0.002 let collinear pairs through to the adjugate,
+  // depending on the rounding of H.)
   const float dpl = fmaf(fmaf(4.0f * l, l, 2.0f * c2), l, c1);
-  const bool near_double = !(dpl > 0.002f * l * l * l);
+  const bool near_double = !(dpl > 0.02f * l * l * l);
   float A[16];
 #pragma unroll
   for (int e = 0; e < 16; ++e) A[e] = K[e];

@@ -97,3 +97,25 @@ def test_equal_sets_match_the_single_set(pcv):
     b = run(pcv, lm, fr, lam, 0.004, "fp32", w, w)
     for key in ("s", "z", "msd", "dsdx", "dzdx", "refreshed"):
         np.testing.assert_array_equal(a[key], b[key])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+@pytest.mark.parametrize("mode", ["exact", "close"])
+def test_alignment_weights_large_structures(pcv, precision, mode):
+    """N=4400 atoms, M=16: the structures are too large to stage per warp, so the finish
+    runs one block per frame, here with separate alignment weights (the centre terms' block
+    sums) and, in close mode, at 80 approximate frames among 79 reassignments (Gamma and Phi
+    from the softmax weights and the segments' rotations)."""
+    lm, fr, lam = problem(93, 4400, 16, 160 if mode == "close" else 40, noise=0.01, schedule="drift",
+                          precision=precision)
+    rng = np.random.default_rng(3)
+    w, wa = rng.uniform(0.3, 3.0, 4400), rng.uniform(0.3, 3.0, 4400)
+    if mode == "close":
+        r = oracle.close(fr, lm, lam, 0.004, w=w, wa=wa, want_grad=True)
+        assert int((r["refreshed"] == 0).sum()) >= 40
+        g = run(pcv, lm, fr, lam, 0.004, precision, w, wa)
+        np.testing.assert_array_equal(g["refreshed"], r["refreshed"])
+    else:
+        r = oracle.exact(fr, lm, lam, w=w, wa=wa, want_grad=True)
+        g = run(pcv, lm, fr, lam, -1.0, precision, w, wa)
+    check(g, r, fr, lm, lam, precision, w)
