@@ -505,6 +505,7 @@ def time_group(pcv, n_inst: int = 256, f: int = 512, seed: int = 7, steps: int =
         b.record(stream)
         torch.cuda.synchronize()
         out[name] = a.elapsed_time(b) / steps
+    tuned = pcv.pcv_group_tuning(handles[0])
     for c in ctxs:
         c.close()
     t = out["group_persistent_graph"]
@@ -515,7 +516,8 @@ def time_group(pcv, n_inst: int = 256, f: int = 512, seed: int = 7, steps: int =
             "ms_per_step_group": t, "ms_per_step_per_instance": out["per_instance_launches"],
             "group_speedup": out["per_instance_launches"] / t, "frames_per_s": n_inst * f / (t / 1e3),
             "achieved_TFLOP_s": flops / (t / 1e3) / 1e12, "fp32_peak_TFLOP_s": FP32_PEAK_TFLOPS,
-            "frac_of_fp32_peak": flops / (t / 1e3) / 1e12 / FP32_PEAK_TFLOPS}
+            "frac_of_fp32_peak": flops / (t / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+            "autotuned": {"tile_frames": tuned[0], "tile_landmarks": tuned[1], "persistent_ctas": tuned[2]}}
 
 
 def host_cores() -> int:

@@ -225,7 +225,11 @@ enum {
   PCV_OPT_BAND = 1,        /* frames compared with each of the previous BAND frames
                               ahead of the refresh search (1..6, default 2)           */
   PCV_OPT_CHUNK = 2,       /* minimum frames per speculative x-y alignment chunk       */
-  PCV_OPT_EXACT_TILE = 3,  /* tile variant index of the exact pair kernel              */
+  PCV_OPT_EXACT_TILE = 3,  /* shape of the exact pair kernel's tile (FP32 / FP16 storage):
+                              0 = automatic (16 frames x 32 landmarks per CTA; the group
+                              launch's autotuner tries every shape), 1 = 16 x 32,
+                              2 = 32 x 16, 3 = 8 x 64.  On ctxs[0] of pcv_evaluate_group a
+                              nonzero value fixes the shape the autotuner uses.           */
   PCV_OPT_APPROX_TILE = 4, /* tile variant index of the approximate pair kernel        */
   PCV_OPT_PROFILE = 5,     /* 1: time every kernel launch with CUDA events on the
                               context's stream (see pcv_get_profile), 0: off (default)  */
@@ -297,10 +301,12 @@ PCV_API const char* pcv_profile_name(int id);
  * gradients, the step runs as three launches over all
  * instances: frame preparation (one warp per frame), the exact pair tiles of every instance
  * in one persistent kernel, and the path CVs (one warp per frame).  The first call with a
- * given set of contexts, sizes and buffers times persistent grids of 1, 2, 3, 4 and 8 CTAs
- * per SM (and one CTA per tile), keeps the fastest, and captures the three launches in a
- * CUDA graph on a stream the first context owns; later calls with the same contexts, sizes,
- * buffers and lambdas replay the graph.  Otherwise the batches are evaluated one after
+ * given set of contexts, sizes and buffers runs the autotuner: for each exact tile shape
+ * (16 x 32, 32 x 16, 8 x 64 frames x landmarks; or the one PCV_OPT_EXACT_TILE sets on
+ * ctxs[0]) it lists the instances' tiles and times persistent grids of 1, 2, 3, 4 and 8
+ * CTAs per SM and one CTA per tile, keeps the fastest shape and grid (pcv_group_tuning),
+ * and captures the three launches in a CUDA graph on a stream the first context owns; later
+ * calls with the same contexts, sizes, buffers, lambdas and shape option replay the graph.  Otherwise the batches are evaluated one after
  * another with pcv_evaluate.  Errors: PCV_EINVAL / PCV_ESTATE as pcv_evaluate, reported on
  * ctxs[0] (pcv_last_error(ctxs[0])); device-side failures are reported by pcv_sync of the
  * context concerned.  The paper evaluates one structure per call; this is the batched
@@ -316,6 +322,10 @@ typedef struct pcv_batch_io {
   uint8_t* refreshed;
 } pcv_batch_io;
 PCV_API pcv_status pcv_evaluate_group(pcv_ctx* const* ctxs, int n, const pcv_batch_io* io, void* stream);
+/* What the group launch's autotuner chose for the groups whose first context is ctx: the
+ * exact tile (frames x landmarks) and the persistent grid's CTAs, from the last call that
+ * tuned (zeros before any).  Errors: PCV_EINVAL for a NULL pointer. */
+PCV_API pcv_status pcv_group_tuning(const pcv_ctx* ctx, int* tile_frames, int* tile_landmarks, int* blocks);
 
 /* Landmark shards (one GPU per shard, or several contexts on one GPU).
  *

@@ -138,12 +138,12 @@ __device__ __forceinline__ void stage_exact(int j0, int N, int M, int i0, const 
   }
 }
 
-template <typename FT, typename ST>
+template <typename FT, typename ST, int TF = EX_TF>
 __device__ __forceinline__ void load_tile_frames(int rows, const int* __restrict__ row_frame, int row0,
                                                  const float4* __restrict__ c32, const double4* __restrict__ c64,
                                                  int* s_frame, ST (*s_c)[3]) {
   const int tid = threadIdx.x;
-  if (tid < EX_TF) {
+  if (tid < TF) {
     const int r = row0 + tid;
     int f = -1;
     if (r < rows) f = row_frame ? row_frame[r] : r;
@@ -156,19 +156,21 @@ __device__ __forceinline__ void load_tile_frames(int rows, const int* __restrict
   }
 }
 
-// FP32 modes: two passes over the atoms of a 16 x 32 tile.
+// FP32 modes: two passes over the atoms of a TF x TM tile (frames x landmarks; 16 x 32 by
+// default, 32 x 16 and 8 x 64 for the group launch's autotuner), 128 threads, each on 2
+// frames x 2 landmarks.
 //  pass 1: H = sum_j w_j a_j x_j^T in FP32 (2 frames x 2 landmarks x 9 sums per thread);
 //          per pair, the top eigenvector of the quaternion matrix in FP32 -> R_{a x};
 //  pass 2: D = sum_j w_j |x_j - R a_j|^2 directly in FP32 (Eq. dist): positive terms, no
 //          cancellation, stationary in R -- so D is accurate to ~1e-7 relative although
 //          every operation is FP32.
-// one 16-frame x 32-landmark tile with origin (row0, i0); the per-call kernel, the
+// one TF-frame x TM-landmark tile with origin (row0, i0); the per-call kernel, the
 // persistent group kernel and the neighbour-list kernels (column list cols of ncol
 // landmarks; rotations then go to Rout[(f * ncol + column) * 9]) run it.
 // APPROX: the approximate MSD of Eq. (close_dist) instead: no pass 1, the rotation of each
 // pair is R_xy R_{a_i y} from the frame's alignment quaternion qxy[f] and the stored
 // rotations Bseg[segof[f] * M + i], then the direct pass 2.
-template <typename LT, bool APPROX = false>
+template <typename LT, bool APPROX = false, int TF = EX_TF, int TM = EX_TM>
 __device__ __forceinline__ void exact_tile_f32(int rows, const int* __restrict__ row_frame,
                                                const float* __restrict__ frames, const float4* __restrict__ c32,
                                                const double* __restrict__ fG, const LT* __restrict__ lm,
@@ -180,8 +182,9 @@ __device__ __forceinline__ void exact_tile_f32(int rows, const int* __restrict__
                                                const double4* __restrict__ qxy = nullptr,
                                                const float* __restrict__ Bseg = nullptr,
                                                const int* __restrict__ segof = nullptr, int cap = 60) {
-  constexpr int TF = EX_TF, TM = EX_TM, KC = 32;
+  constexpr int KC = 32;
   constexpr int PF = TF + 2, PM = TM + 2;
+  static_assert(TF * TM == 4 * EX_THREADS && 64 % TM == 0 && TF % 2 == 0, "tile shape: 128 threads of 2 x 2 pairs");
   __shared__ __align__(16) float Xs[KC * 3][PF];
   __shared__ __align__(16) float As[KC * 3][PM];
   __shared__ int s_frame[TF];
@@ -194,13 +197,13 @@ __device__ __forceinline__ void exact_tile_f32(int rows, const int* __restrict__
 
   if (row0 >= rows) return;
   const int tid = threadIdx.x;
-  const int tx = tid & 15;  // landmark pair: i0 + 2 tx + {0,1}
-  const int ty = tid >> 4;  // frame pair: rows 2 ty + {0,1}
-  load_tile_frames<float, float>(rows, row_frame, row0, c32, nullptr, s_frame, s_c);
+  const int tx = tid % (TM / 2);  // landmark pair: i0 + 2 tx + {0,1}
+  const int ty = tid / (TM / 2);  // frame pair: rows 2 ty + {0,1}
+  load_tile_frames<float, float, TF>(rows, row_frame, row0, c32, nullptr, s_frame, s_c);
   __syncthreads();
-  // a warp holds the rows row0 + 4 w .. row0 + 4 w + 3: warps wholly past the rows skip the
-  // products (a tile of few frames, e.g. one MD step)
-  const int kc_live = row0 + (tid >> 5) * 4 < rows ? KC : 0;
+  // a warp holds the rows row0 + (128 / TM) w onwards (128 / TM of them): warps wholly past
+  // the rows skip the products (a tile of few frames, e.g. one MD step)
+  const int kc_live = row0 + (tid >> 5) * (128 / TM) < rows ? KC : 0;
 
   float h[2][2][9];
 #pragma unroll
@@ -345,26 +348,28 @@ __device__ __forceinline__ void exact_tile_f32(int rows, const int* __restrict__
   if (!all_ok) atomicOr(status, STATUS_NOCONV);
 }
 
-template <typename LT>
+template <typename LT, int TF = EX_TF, int TM = EX_TM>
 __global__ void __launch_bounds__(EX_THREADS, 4)
 exact_pair_f32(int rows, const int* __restrict__ row_frame, const float* __restrict__ frames,
                const float4* __restrict__ c32, const double* __restrict__ fG, const LT* __restrict__ lm,
                const float* __restrict__ lmoff, const double* __restrict__ lG, const float* __restrict__ wts, int M,
                int N, double dscale, float* __restrict__ Dout, float* __restrict__ Rout,
                unsigned* __restrict__ status, int cap) {
-  exact_tile_f32<LT>(rows, row_frame, frames, c32, fG, lm, lmoff, lG, wts, M, N, dscale, Dout, Rout, status,
-                     blockIdx.y * EX_TF, blockIdx.x * EX_TM, nullptr, 0, nullptr, nullptr, nullptr, cap);
+  exact_tile_f32<LT, false, TF, TM>(rows, row_frame, frames, c32, fG, lm, lmoff, lG, wts, M, N, dscale, Dout, Rout,
+                                    status, blockIdx.y * TF, blockIdx.x * TM, nullptr, 0, nullptr, nullptr, nullptr,
+                                    cap);
 }
 
-// Many instances in one persistent launch: CTA b takes tiles b, b + grid, ...
-template <typename LT>
+// Many instances in one persistent launch: CTA b takes tiles b, b + grid, ... (tiles of
+// TF x TM: the host lists them for the shape it launches)
+template <typename LT, int TF = EX_TF, int TM = EX_TM>
 __global__ void __launch_bounds__(EX_THREADS, 4)
 exact_group_f32(const GroupInst* __restrict__ I, const GroupTile* __restrict__ tiles, int ntiles) {
   for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
     const GroupTile w = tiles[k];
     const GroupInst& t = I[w.inst];
-    exact_tile_f32<LT>(t.F, nullptr, t.frames, t.c32, t.fG, (const LT*)t.lm, t.lmoff, t.lG, t.w, t.M, t.N, t.dscale,
-                       t.D, nullptr, t.status, w.row0, w.i0);
+    exact_tile_f32<LT, false, TF, TM>(t.F, nullptr, t.frames, t.c32, t.fG, (const LT*)t.lm, t.lmoff, t.lG, t.w, t.M,
+                                      t.N, t.dscale, t.D, nullptr, t.status, w.row0, w.i0);
     __syncthreads();  // the tile's shared staging is reused by the next tile
   }
 }
@@ -953,6 +958,30 @@ void launch_exact_pairs(Prec p, int rows, const int* row_frame, const int* rows_
     launch_exact_stream(p, rows, row_frame, frames, L, fi, D, Rout, status, st);
     return;
   }
+  const int shape = L.exact_tile > 0 && L.exact_tile <= EXACT_SHAPES ? L.exact_tile - 1 : 0;
+  if (p != P_F64 && shape > 0) {  // a chosen shape (FP32 / FP16 storage)
+    const ExactShape sh = kExactShape[shape];
+    const dim3 g((L.M + sh.tm - 1) / sh.tm, (rows + sh.tf - 1) / sh.tf);
+    const bool h = p == P_F16;
+#define PCV_EXACT_SHAPED(TF, TM)                                                                                   \
+  if (h)                                                                                                           \
+    exact_pair_f32<__half, TF, TM><<<g, EX_THREADS, 0, st>>>(rows, row_frame, (const float*)frames, fi.c32, fi.G,  \
+                                                             (const __half*)L.coords, L.off, L.G, L.w, L.M, L.N,   \
+                                                             L.dscale, (float*)D, (float*)Rout, status,            \
+                                                             L.newton_cap);                                         \
+  else                                                                                                             \
+    exact_pair_f32<float, TF, TM><<<g, EX_THREADS, 0, st>>>(rows, row_frame, (const float*)frames, fi.c32, fi.G,   \
+                                                            (const float*)L.coords, L.off, L.G, L.w, L.M, L.N,     \
+                                                            L.dscale, (float*)D, (float*)Rout, status, L.newton_cap);
+    if (shape == 1) {
+      PCV_EXACT_SHAPED(32, 16)
+    } else {
+      PCV_EXACT_SHAPED(8, 64)
+    }
+#undef PCV_EXACT_SHAPED
+    note_launch();
+    return;
+  }
   dim3 grid((L.M + EX_TM - 1) / EX_TM, (rows + EX_TF - 1) / EX_TF);
   switch (p) {
     case P_F64:
@@ -984,14 +1013,27 @@ void launch_exact_pairs(Prec p, int rows, const int* row_frame, const int* rows_
   }
 }
 
-void launch_exact_group(bool fp16, const GroupInst* I, const GroupTile* tiles, int ntiles, int blocks,
+template <int TF, int TM>
+static void exact_group_launch(bool fp16, const GroupInst* I, const GroupTile* tiles, int ntiles, int blocks,
+                               cudaStream_t st) {
+  if (fp16)
+    exact_group_f32<__half, TF, TM><<<blocks, EX_THREADS, 0, st>>>(I, tiles, ntiles);
+  else
+    exact_group_f32<float, TF, TM><<<blocks, EX_THREADS, 0, st>>>(I, tiles, ntiles);
+}
+
+void launch_exact_group(bool fp16, int shape, const GroupInst* I, const GroupTile* tiles, int ntiles, int blocks,
                         cudaStream_t st) {
   if (ntiles <= 0) return;
-  static_assert(GROUP_TILE_F == EX_TF && GROUP_TILE_M == EX_TM, "group tiles are the exact tiles");
-  if (fp16)
-    exact_group_f32<__half><<<blocks, EX_THREADS, 0, st>>>(I, tiles, ntiles);
-  else
-    exact_group_f32<float><<<blocks, EX_THREADS, 0, st>>>(I, tiles, ntiles);
+  static_assert(kExactShape[0].tf == EX_TF && kExactShape[0].tm == EX_TM, "shape 0 is the default tile");
+  static_assert(kExactShape[1].tf == 32 && kExactShape[1].tm == 16 && kExactShape[2].tf == 8 &&
+                    kExactShape[2].tm == 64,
+                "the shapes instantiated below");
+  switch (shape) {
+    case 1: exact_group_launch<32, 16>(fp16, I, tiles, ntiles, blocks, st); break;
+    case 2: exact_group_launch<8, 64>(fp16, I, tiles, ntiles, blocks, st); break;
+    default: exact_group_launch<16, 32>(fp16, I, tiles, ntiles, blocks, st); break;
+  }
   note_launch();
 }
 

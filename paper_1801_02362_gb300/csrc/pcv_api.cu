@@ -92,6 +92,7 @@ struct pcv_ctx {
   int device = 0;
   int newton_cap = 60;                  // PCV_OPT_NEWTON_CAP
   int mma_group = 4;                    // PCV_OPT_MMA_GROUP
+  int exact_tile = 0;                   // PCV_OPT_EXACT_TILE
   long long wait_cycles = 4000000000LL;  // PCV_OPT_WAIT_CYCLES
   cudaStream_t stream = nullptr;
   Prec prec = P_F32;
@@ -146,6 +147,8 @@ struct pcv_ctx {
   cudaStream_t grp_stream = nullptr;   // the library's own stream: graphs cannot be captured on stream 0
   cudaEvent_t grp_ev[2] = {nullptr, nullptr};
   int grp_blocks = 0;                  // persistent grid chosen by the autotuner
+  int grp_shape = 0;                   // exact tile shape chosen by the autotuner
+  int grp_ntiles = 0;                  // tiles of that shape
   pcv_stats stats{};
   std::string err;
   // profiler
@@ -263,6 +266,7 @@ LandmarkDev lm_view(const pcv_ctx* c) {
   L.newton_cap = c->newton_cap;
   L.wait_cycles = c->wait_cycles;
   L.mma_group = c->mma_group;
+  L.exact_tile = c->exact_tile;
   return L;
 }
 
@@ -423,6 +427,9 @@ pcv_status pcv_set_option(pcv_ctx* c, int key, int64_t value) {
       c->mma_group = (int)value;
       return PCV_OK;
     case PCV_OPT_EXACT_TILE:
+      if (value < 0 || value > EXACT_SHAPES) return fail(c, PCV_EINVAL, "exact tile shape must be in 0..%d", EXACT_SHAPES);
+      c->exact_tile = (int)value;
+      return PCV_OK;
     case PCV_OPT_APPROX_TILE:
       if (value != 0) return fail(c, PCV_EINVAL, "only tile variant 0 is built");
       return PCV_OK;
@@ -1267,7 +1274,7 @@ pcv_status pcv_evaluate_group(pcv_ctx* const* ctxs, int n, const pcv_batch_io* i
   }
   // workspaces and descriptors
   std::vector<GroupInst> inst(n);
-  std::vector<GroupTile> tiles;
+  std::vector<GroupTile> tiles_of[EXACT_SHAPES];  // the tile list of every shape
   int Ftot = 0;
   std::vector<uint64_t> sig = {(uint64_t)n};
   for (int k = 0; k < n; ++k) {
@@ -1297,8 +1304,9 @@ pcv_status pcv_evaluate_group(pcv_ctx* const* ctxs, int n, const pcv_batch_io* i
     t.z = b.z;
     t.msd = b.msd;
     t.status = (unsigned*)c->status.p;
-    for (int r0 = 0; r0 < b.F; r0 += GROUP_TILE_F)
-      for (int i0 = 0; i0 < c->M; i0 += GROUP_TILE_M) tiles.push_back(GroupTile{k, r0, i0, 0});
+    for (int sh = 0; sh < EXACT_SHAPES; ++sh)
+      for (int r0 = 0; r0 < b.F; r0 += kExactShape[sh].tf)
+        for (int i0 = 0; i0 < c->M; i0 += kExactShape[sh].tm) tiles_of[sh].push_back(GroupTile{k, r0, i0, 0});
     Ftot += b.F;
     const uint64_t lam_bits = *reinterpret_cast<const uint64_t*>(&c->lambda);
     for (uint64_t v : {(uint64_t)(uintptr_t)c, (uint64_t)b.F, (uint64_t)(uintptr_t)b.frames, (uint64_t)(uintptr_t)b.s,
@@ -1313,50 +1321,66 @@ pcv_status pcv_evaluate_group(pcv_ctx* const* ctxs, int n, const pcv_batch_io* i
     CUDA_TRY(lead, cudaEventCreateWithFlags(&lead->grp_ev[1], cudaEventDisableTiming));
   }
   const cudaStream_t gs = lead->grp_stream;
-  const int ntiles = (int)tiles.size();
   const bool fp16 = lead->prec == P_F16;
+  size_t max_tiles = 1;
+  for (int sh = 0; sh < EXACT_SHAPES; ++sh) max_tiles = std::max(max_tiles, tiles_of[sh].size());
+  sig.push_back((uint64_t)lead->exact_tile);
   // order the group's work after the caller's earlier work
   CUDA_TRY(lead, cudaEventRecord(lead->grp_ev[0], user));
   CUDA_TRY(lead, cudaStreamWaitEvent(gs, lead->grp_ev[0], 0));
   if (sig != lead->grp_sig) {
     pcv_status r;
     if ((r = ensure(lead, lead->grp_inst, sizeof(GroupInst) * n)) != PCV_OK) return r;
-    if ((r = ensure(lead, lead->grp_tiles, sizeof(GroupTile) * (ntiles > 0 ? ntiles : 1))) != PCV_OK) return r;
+    if ((r = ensure(lead, lead->grp_tiles, sizeof(GroupTile) * max_tiles)) != PCV_OK) return r;
     CUDA_TRY(lead, cudaMemcpyAsync(lead->grp_inst.p, inst.data(), sizeof(GroupInst) * n, cudaMemcpyHostToDevice, gs));
-    if (ntiles > 0)
-      CUDA_TRY(lead, cudaMemcpyAsync(lead->grp_tiles.p, tiles.data(), sizeof(GroupTile) * ntiles,
-                                     cudaMemcpyHostToDevice, gs));
-    CUDA_TRY(lead, cudaStreamSynchronize(gs));  // the host vectors are released on return
     const GroupInst* I = (const GroupInst*)lead->grp_inst.p;
     const GroupTile* T = (const GroupTile*)lead->grp_tiles.p;
     launch_frame_prep_group(I, n, Ftot, gs);
-    // autotuner: persistent grids of 1..8 CTAs per SM (and one CTA per tile), each timed once
-    // after the first run has warmed the caches; the fastest is kept for this group
+    // autotuner: for every tile shape (or the one PCV_OPT_EXACT_TILE fixes on ctxs[0]), its
+    // tile list, then persistent grids of 1, 2, 3, 4 and 8 CTAs per SM and one CTA per tile,
+    // each timed once after a first run of the shape has warmed the caches; the fastest
+    // (shape, grid) is kept for this group
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, lead->device);
-    const int cands[] = {sms, 2 * sms, 3 * sms, 4 * sms, 8 * sms, ntiles};
     cudaEvent_t t0, t1;
     CUDA_TRY(lead, cudaEventCreate(&t0));
     CUDA_TRY(lead, cudaEventCreate(&t1));
-    launch_exact_group(fp16, I, T, ntiles, 4 * sms, gs);
     float best = 3.4e38f;
-    int best_blocks = 4 * sms;
-    for (int cand : cands) {
-      const int blocks = cand < 1 ? 1 : (cand > ntiles && ntiles > 0 ? ntiles : cand);
-      cudaEventRecord(t0, gs);
-      launch_exact_group(fp16, I, T, ntiles, blocks, gs);
-      cudaEventRecord(t1, gs);
-      cudaEventSynchronize(t1);
-      float ms = 0.0f;
-      cudaEventElapsedTime(&ms, t0, t1);
-      if (ms < best) {
-        best = ms;
-        best_blocks = blocks;
+    int best_blocks = 4 * sms, best_shape = lead->exact_tile > 0 ? lead->exact_tile - 1 : 0;
+    for (int sh = 0; sh < EXACT_SHAPES; ++sh) {
+      if (lead->exact_tile > 0 && sh != lead->exact_tile - 1) continue;
+      const std::vector<GroupTile>& tl = tiles_of[sh];
+      const int ntiles = (int)tl.size();
+      if (ntiles == 0) continue;
+      CUDA_TRY(lead, cudaMemcpyAsync(lead->grp_tiles.p, tl.data(), sizeof(GroupTile) * ntiles,
+                                     cudaMemcpyHostToDevice, gs));
+      launch_exact_group(fp16, sh, I, T, ntiles, 4 * sms, gs);
+      const int cands[] = {sms, 2 * sms, 3 * sms, 4 * sms, 8 * sms, ntiles};
+      for (int cand : cands) {
+        const int blocks = cand < 1 ? 1 : (cand > ntiles ? ntiles : cand);
+        cudaEventRecord(t0, gs);
+        launch_exact_group(fp16, sh, I, T, ntiles, blocks, gs);
+        cudaEventRecord(t1, gs);
+        cudaEventSynchronize(t1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, t0, t1);
+        if (ms < best) {
+          best = ms;
+          best_blocks = blocks;
+          best_shape = sh;
+        }
       }
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     lead->grp_blocks = best_blocks;
+    lead->grp_shape = best_shape;
+    const int ntiles = (int)tiles_of[best_shape].size();
+    if (ntiles > 0)
+      CUDA_TRY(lead, cudaMemcpyAsync(lead->grp_tiles.p, tiles_of[best_shape].data(), sizeof(GroupTile) * ntiles,
+                                     cudaMemcpyHostToDevice, gs));
+    CUDA_TRY(lead, cudaStreamSynchronize(gs));  // the host vectors are released on return
+    lead->grp_ntiles = ntiles;
     // capture the step: frame preparation, exact tiles, path CVs
     if (lead->grp_exec) {
       cudaGraphExecDestroy(lead->grp_exec);
@@ -1365,7 +1389,7 @@ pcv_status pcv_evaluate_group(pcv_ctx* const* ctxs, int n, const pcv_batch_io* i
     cudaGraph_t graph = nullptr;
     CUDA_TRY(lead, cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
     launch_frame_prep_group(I, n, Ftot, gs);
-    launch_exact_group(fp16, I, T, ntiles, lead->grp_blocks, gs);
+    launch_exact_group(fp16, lead->grp_shape, I, T, ntiles, lead->grp_blocks, gs);
     launch_finalize_group(I, n, Ftot, gs);
     CUDA_TRY(lead, cudaStreamEndCapture(gs, &graph));
     const cudaError_t ie = cudaGraphInstantiate(&lead->grp_exec, graph, 0);
@@ -1385,6 +1409,15 @@ pcv_status pcv_evaluate_group(pcv_ctx* const* ctxs, int n, const pcv_batch_io* i
   lead->stats.kernel_launches += 3;
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(lead, PCV_ECUDA, "group launch: %s", cudaGetErrorString(e));
+  return PCV_OK;
+}
+
+pcv_status pcv_group_tuning(const pcv_ctx* ctx, int* tile_frames, int* tile_landmarks, int* blocks) {
+  if (!ctx || !tile_frames || !tile_landmarks || !blocks) return fail(nullptr, PCV_EINVAL, "NULL argument");
+  const bool tuned = ctx->grp_blocks > 0;
+  *tile_frames = tuned ? kExactShape[ctx->grp_shape].tf : 0;
+  *tile_landmarks = tuned ? kExactShape[ctx->grp_shape].tm : 0;
+  *blocks = ctx->grp_blocks;
   return PCV_OK;
 }
 

@@ -34,6 +34,7 @@ struct LandmarkDev {
   // iteration cap of the exact pair kernels' eigen-solves, and the clock budget of each
   // bounded wait in the tensor-core kernels (cycles)
   int newton_cap = 60;
+  int exact_tile = 0;  // exact tile shape: 0 the default, k > 0 kExactShape[k - 1]
   long long wait_cycles = 4000000000LL;
   // chunks of 16 deviation components the tensor-core MSD kernel sums in tensor memory
   // before folding them into its FP32 totals
@@ -210,11 +211,18 @@ struct GroupInst {
 struct GroupTile {
   int inst, row0, i0, pad;
 };
-constexpr int GROUP_TILE_F = 16, GROUP_TILE_M = 32;  // the exact tile (k_pair.cu)
+// shapes of the exact tile (frames x landmarks, 128 threads of 2 x 2 pairs; k_pair.cu):
+// index 0 is the default; the group launch's autotuner times all of them
+struct ExactShape {
+  int tf, tm;
+};
+constexpr int EXACT_SHAPES = 3;
+constexpr ExactShape kExactShape[EXACT_SHAPES] = {{16, 32}, {32, 16}, {8, 64}};
 void launch_frame_prep_group(const GroupInst* I, int n, int Ftot, cudaStream_t st);
 void launch_finalize_group(const GroupInst* I, int n, int Ftot, cudaStream_t st);
 // persistent grid of `blocks` CTAs over the tiles; fp16: landmarks in FP16 storage
-void launch_exact_group(bool fp16, const GroupInst* I, const GroupTile* tiles, int ntiles, int blocks, cudaStream_t st);
+void launch_exact_group(bool fp16, int shape, const GroupInst* I, const GroupTile* tiles, int ntiles, int blocks,
+                        cudaStream_t st);
 
 // ---------------------------------------------------------------------------------------
 // landmark-parallel kernels for up to STREAM_FRAMES frames per call (k_stream.cu; FP32

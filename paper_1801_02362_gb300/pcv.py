@@ -77,6 +77,7 @@ SIGNATURES = {
     "pcv_evaluate_exact_noalloc": (_i, [_i, _i, _i, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, ctypes.c_char_p,
                                        ctypes.c_size_t]),
     "pcv_evaluate_group": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(pcv_batch_io), _vp]),
+    "pcv_group_tuning": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "pcv_metad_create": (_i, [ctypes.POINTER(_vp), _i, _vp, _d, _d, _d, _i, _i]),
     "pcv_metad_destroy": (_i, [_vp]),
     "pcv_metad_set_stream": (_i, [_vp, _vp]),
@@ -257,6 +258,14 @@ def pcv_shard_pack(precision: int, F: int, N: int, lam: float, zmin_ptr, s_ptr, 
     """Device pointers: shard values -> summable terms (see include/pcv.h)."""
     _check(None, load().pcv_shard_pack(precision, F, N, float(lam), zmin_ptr, s_ptr, z_ptr, dsdx_ptr, dzdx_ptr,
                                        scalars_ptr, elements_ptr, stream))
+
+
+def pcv_group_tuning(ctx) -> tuple[int, int, int]:
+    """(tile frames, tile landmarks, persistent CTAs) the group autotuner chose for the groups
+    whose first context is ctx; zeros before any tuned call."""
+    tf, tm, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(ctx, load().pcv_group_tuning(ctx, ctypes.byref(tf), ctypes.byref(tm), ctypes.byref(b)))
+    return tf.value, tm.value, b.value
 
 
 def pcv_shard_unpack(precision: int, F: int, N: int, lam: float, zmin_ptr, scalars_ptr, elements_ptr, s_ptr,

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
-from _util import TOL, d_err, problem, s_err, s_kappa, z_err
+from _util import GRAD_TOL, TOL, d_err, grad_err, problem, s_err, s_kappa, z_err
 
 pytestmark = pytest.mark.gpu
 
@@ -104,6 +104,49 @@ def test_group_ragged_exact_graph(pcv, precision):
         assert z_err(out["z"].cpu().numpy(), b["z"].cpu().numpy(), lam) < TOL[precision]
     for c in ctxs:
         c.close()
+
+
+@pytest.mark.parametrize("shape", [1, 2, 3])
+def test_group_each_tile_shape(pcv, shape):
+    """The autotuner's tile shapes one at a time (PCV_OPT_EXACT_TILE on the first context fixes
+    it): 16 x 32, 32 x 16 and 8 x 64 frames x landmarks, over the ragged instances (frame and
+    landmark counts that leave partial tiles in both directions), against the oracle; the
+    tuning query reports the shape used."""
+    insts = _instances("fp32")
+    ctxs = [pcv.PathCV(lm, lam, eps=-1.0, precision="fp32") for lm, fr, lam in insts]
+    pcv.pcv_set_option(ctxs[0].ctx, pcv.PCV_OPT_EXACT_TILE, shape)
+    bufs = [_buffers(fr, lm.shape[0]) for lm, fr, lam in insts]
+    assert pcv.pcv_group_tuning(ctxs[0].ctx) == (0, 0, 0)
+    pcv.pcv_evaluate_group([c.ctx for c in ctxs], [_io(b) for b in bufs])
+    torch.cuda.synchronize()
+    _check(insts, bufs, "fp32")
+    tf, tm, blocks = pcv.pcv_group_tuning(ctxs[0].ctx)
+    assert (tf, tm) == {1: (16, 32), 2: (32, 16), 3: (8, 64)}[shape] and blocks > 0
+    for c in ctxs:
+        c.close()
+
+
+@pytest.mark.parametrize("shape", [2, 3])
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_exact_pairs_each_tile_shape(pcv, shape, precision):
+    """The per-call exact kernel with the other tile shapes (PCV_OPT_EXACT_TILE): 70 frames x
+    45 landmarks leave partial tiles in both directions; values and both gradients (the
+    tiles' rotations) against the oracle."""
+    lm, fr, lam = problem(63, 37, 45, 70, noise=0.03, schedule="walk", precision=precision)
+    r = oracle.exact(fr, lm, lam, want_grad=True)
+    ctx = pcv.PathCV(lm, lam, eps=-1.0, precision=precision)
+    pcv.pcv_set_option(ctx.ctx, pcv.PCV_OPT_EXACT_TILE, shape)
+    out = ctx.evaluate(torch.tensor(fr, dtype=torch.float32, device="cuda"), grad=True, msd=True)
+    ctx.sync()
+    g = {k: v.double().cpu().numpy() for k, v in out.items()}
+    with pytest.raises(pcv.PcvError):
+        pcv.pcv_set_option(ctx.ctx, pcv.PCV_OPT_EXACT_TILE, 4)
+    ctx.close()
+    assert d_err(g["msd"], r["D"], fr, lm) < TOL[precision]
+    assert s_err(g["s"], r["s"], lm.shape[0]) < TOL[precision]
+    assert z_err(g["z"], r["z"], lam) < TOL[precision]
+    assert grad_err(g["dsdx"], r["dsdx"]) < GRAD_TOL[precision]
+    assert grad_err(g["dzdx"], r["dzdx"]) < GRAD_TOL[precision]
 
 
 def test_group_mixed_modes_fall_back(pcv):
