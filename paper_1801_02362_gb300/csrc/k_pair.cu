@@ -348,6 +348,201 @@ __device__ __forceinline__ void exact_tile_f32(int rows, const int* __restrict__
   if (!all_ok) atomicOr(status, STATUS_NOCONV);
 }
 
+// ---------------------------------------------------------------------------------------
+// The exact tiles with the atoms split over SPLITS slices (FP32 modes): for batches of few
+// frames against many landmarks (the reassignment frames of a batch: 34 frames x 2000
+// landmarks gave 189 tiles, one CTA each, a long serial chain per CTA on a mostly idle GPU).
+// exact_split_pass1: the 16 x 32 tile's correlation sums over its slice of the atoms, to
+//   Hp[((s * rows + r) * M + i) * 9 + e];
+// exact_split_pass2: every slice's CTA adds the partials in slice order (the same H, hence
+//   the same R, in every slice), solves for R (slice 0 writes it to Rout), and sums
+//   w |x - R a|^2 over its slice (compensated) to Dp[((s * rows + r) * M + i) * 2 + {0,1}];
+// exact_split_finish: D = the slices' (hi, lo) pairs added in slice order.
+// Arithmetic per atom as exact_tile_f32; the sums are split, not reordered within a chunk.
+// atoms [j_beg, j_end) of slice s: whole chunks of 32, the last slice ending at N
+__device__ __forceinline__ void split_range(int N, int nsplit, int s, int& j_beg, int& j_end) {
+  const int chunks = (N + 31) / 32, per = (chunks + nsplit - 1) / nsplit;
+  j_beg = min(N, s * per * 32);
+  j_end = min(N, (s + 1) * per * 32);
+}
+
+template <typename LT>
+__global__ void __launch_bounds__(EX_THREADS, 4)
+exact_split_pass1(int rows, const int* __restrict__ row_frame, const float* __restrict__ frames,
+                  const float4* __restrict__ c32, const LT* __restrict__ lm, const float* __restrict__ lmoff,
+                  const float* __restrict__ wts, int M, int N, int nsplit, float* __restrict__ Hp) {
+  constexpr int TF = EX_TF, TM = EX_TM, KC = 32, PF = TF + 2, PM = TM + 2;
+  __shared__ __align__(16) float Xs[KC * 3][PF];
+  __shared__ __align__(16) float As[KC * 3][PM];
+  __shared__ int s_frame[TF];
+  __shared__ float s_c[TF][3];
+  const int row0 = blockIdx.y * TF, i0 = blockIdx.x * TM, sp = blockIdx.z;
+  const int tid = threadIdx.x, tx = tid % (TM / 2), ty = tid / (TM / 2);
+  int j_beg, j_end;
+  split_range(N, nsplit, sp, j_beg, j_end);
+  load_tile_frames<float, float, TF>(rows, row_frame, row0, c32, nullptr, s_frame, s_c);
+  __syncthreads();
+  const int kc_live = row0 + (tid >> 5) * (128 / TM) < rows ? KC : 0;
+  float h[2][2][9], t[2][2][9];
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v)
+#pragma unroll
+      for (int e = 0; e < 9; ++e) h[u][v][e] = t[u][v][e] = 0.0f;
+  for (int j0 = j_beg; j0 < j_end; j0 += KC) {
+    stage_exact<float, LT, float, TF, TM, KC, PF, PM>(j0, N, M, i0, frames, lm, lmoff, wts, 1, s_frame, s_c, Xs,
+                                                      As);  // chunks never cross j_end (whole chunks per slice)
+    __syncthreads();
+#pragma unroll 4
+    for (int jj = 0; jj < kc_live; ++jj) {
+      float x[2][3], a[2][3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        load2<float>(&Xs[jj * 3 + c][ty * 2], x[0][c], x[1][c]);
+        load2<float>(&As[jj * 3 + c][tx * 2], a[0][c], a[1][c]);
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v)
+#pragma unroll
+          for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) h[u][v][3 * b + c] = fmaf(a[v][b], x[u][c], h[u][v][3 * b + c]);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int v = 0; v < 2; ++v)
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+          t[u][v][e] += h[u][v][e];  // chunk totals: chains of KC + chunks-per-slice terms
+          h[u][v][e] = 0.0f;
+        }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int r = row0 + ty * 2 + u, i = i0 + tx * 2 + v;
+      if (r >= rows || i >= M) continue;
+      float* dst = Hp + (((size_t)sp * rows + r) * M + i) * 9;
+#pragma unroll
+      for (int e = 0; e < 9; ++e) dst[e] = t[u][v][e];
+    }
+}
+
+template <typename LT>
+__global__ void __launch_bounds__(EX_THREADS, 4)
+exact_split_pass2(int rows, const int* __restrict__ row_frame, const float* __restrict__ frames,
+                  const float4* __restrict__ c32, const double* __restrict__ fG, const LT* __restrict__ lm,
+                  const float* __restrict__ lmoff, const double* __restrict__ lG, const float* __restrict__ wts, int M,
+                  int N, int nsplit, const float* __restrict__ Hp, float* __restrict__ Dp, float* __restrict__ Rout,
+                  unsigned* __restrict__ status, int cap) {
+  constexpr int TF = EX_TF, TM = EX_TM, KC = 32, PF = TF + 2, PM = TM + 2;
+  __shared__ __align__(16) float Xs[KC * 3][PF];
+  __shared__ __align__(16) float As[KC * 3][PM];
+  __shared__ int s_frame[TF];
+  __shared__ float s_c[TF][3];
+  const int row0 = blockIdx.y * TF, i0 = blockIdx.x * TM, sp = blockIdx.z;
+  const int tid = threadIdx.x, tx = tid % (TM / 2), ty = tid / (TM / 2);
+  int j_beg, j_end;
+  split_range(N, nsplit, sp, j_beg, j_end);
+  load_tile_frames<float, float, TF>(rows, row_frame, row0, c32, nullptr, s_frame, s_c);
+  __syncthreads();
+  const int kc_live = row0 + (tid >> 5) * (128 / TM) < rows ? KC : 0;
+  float R[2][2][9];
+  bool all_ok = true;
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int r = row0 + ty * 2 + u, i = i0 + tx * 2 + v;
+      const int f = s_frame[ty * 2 + u];
+      float q[4] = {1.0f, 0.0f, 0.0f, 0.0f};
+      if (f >= 0 && i < M) {
+        float H[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) H[e] = 0.0f;
+        for (int k = 0; k < nsplit; ++k) {  // slice order: the same H in every slice's CTA
+          const float* src = Hp + (((size_t)k * rows + r) * M + i) * 9;
+#pragma unroll
+          for (int e = 0; e < 9; ++e) H[e] += src[e];
+        }
+        const float ub = (float)(0.5 * (fG[f] + lG[i])) * 1.00001f + 1e-30f;
+        all_ok &= top_quat_f32(H, ub, q, cap);
+      }
+      quat_to_rot(q, R[u][v]);
+    }
+  float acc[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+  float thi[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}}, tlo[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+  for (int j0 = j_beg; j0 < j_end; j0 += KC) {
+    stage_exact<float, LT, float, TF, TM, KC, PF, PM>(j0, N, M, i0, frames, lm, lmoff, wts, 2, s_frame, s_c, Xs,
+                                                      As);  // chunks never cross j_end (whole chunks per slice)
+    __syncthreads();
+#pragma unroll 4
+    for (int jj = 0; jj < kc_live; ++jj) {
+      float x[2][3], a[2][3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        load2<float>(&Xs[jj * 3 + c][ty * 2], x[0][c], x[1][c]);
+        load2<float>(&As[jj * 3 + c][tx * 2], a[0][c], a[1][c]);
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+          const float* Rr = R[u][v];
+          const float d0 = x[u][0] - fmaf(Rr[0], a[v][0], fmaf(Rr[1], a[v][1], Rr[2] * a[v][2]));
+          const float d1 = x[u][1] - fmaf(Rr[3], a[v][0], fmaf(Rr[4], a[v][1], Rr[5] * a[v][2]));
+          const float d2 = x[u][2] - fmaf(Rr[6], a[v][0], fmaf(Rr[7], a[v][1], Rr[8] * a[v][2]));
+          acc[u][v] = fmaf(d0, d0, fmaf(d1, d1, fmaf(d2, d2, acc[u][v])));
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        two_sum_acc(thi[u][v], tlo[u][v], acc[u][v]);
+        acc[u][v] = 0.0f;
+      }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int r = row0 + ty * 2 + u, i = i0 + tx * 2 + v;
+      if (s_frame[ty * 2 + u] < 0 || i >= M) continue;
+      float* dp = Dp + (((size_t)sp * rows + r) * M + i) * 2;
+      dp[0] = thi[u][v];
+      dp[1] = tlo[u][v];
+      if (Rout && sp == 0) {
+        float* dst = Rout + ((size_t)r * M + i) * 9;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) dst[e] = R[u][v][e];
+      }
+    }
+  if (!all_ok && sp == 0) atomicOr(status, STATUS_NOCONV);
+}
+
+__global__ void exact_split_finish(int rows, const int* __restrict__ row_frame, int M, int nsplit, float dscale,
+                                   const float* __restrict__ Dp, float* __restrict__ Dout) {
+  const size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (k >= (size_t)rows * M) return;
+  const int r = (int)(k / M), i = (int)(k - (size_t)r * M);
+  const int f = row_frame ? row_frame[r] : r;
+  float hi = 0.0f, lo = 0.0f;
+  for (int sp = 0; sp < nsplit; ++sp) {
+    const float* d = Dp + (((size_t)sp * rows + r) * M + i) * 2;
+    two_sum_acc(hi, lo, d[0]);
+    lo += d[1];
+  }
+  Dout[(size_t)f * M + i] = (hi + lo) * dscale;
+}
+
 template <typename LT, int TF = EX_TF, int TM = EX_TM>
 __global__ void __launch_bounds__(EX_THREADS, 4)
 exact_pair_f32(int rows, const int* __restrict__ row_frame, const float* __restrict__ frames,
@@ -949,14 +1144,59 @@ approx_pair_f32t(const int* __restrict__ alist, const int* __restrict__ aseg, co
 }  // namespace
 
 // ---------------------------------------------------------------------------------------
+int exact_split_count(int rows, int M, int N) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long tiles = (long long)((M + EX_TM - 1) / EX_TM) * ((rows + EX_TF - 1) / EX_TF);
+  if (tiles >= 2LL * sms) return 1;  // the tiles alone fill two waves
+  const int chunks = (N + 31) / 32;
+  int k = 1;
+  while (k < 16 && tiles * k < 4LL * sms && chunks / (2 * k) >= 4) k *= 2;  // at least 4 chunks per slice
+  return k;
+}
+
+size_t exact_split_bytes(int rows, int M, int nsplit) {
+  return sizeof(float) * (size_t)nsplit * rows * M * (9 + 2);
+}
+
 void launch_exact_pairs(Prec p, int rows, const int* row_frame, const int* rows_dev, const void* frames,
                         const LandmarkDev& L, FrameInfo fi, void* D, void* Rout, unsigned* status,
-                        cudaStream_t st) {
+                        cudaStream_t st, const ScratchView* scr) {
   (void)rows_dev;
   if (rows <= 0) return;
   if (p != P_F64 && rows <= STREAM_FRAMES && stream_fits(p, L.N)) {  // a few frames: one CTA per landmark
     launch_exact_stream(p, rows, row_frame, frames, L, fi, D, Rout, status, st);
     return;
+  }
+  if (p != P_F64 && scr && L.exact_tile == 0) {
+    // few tiles: the atoms split over slices so that the grid fills the GPU
+    const int nsplit = exact_split_count(rows, L.M, L.N);
+    if (nsplit > 1 && scr->bytes >= exact_split_bytes(rows, L.M, nsplit)) {
+      float* Hp = (float*)scr->ptr;
+      float* Dp = Hp + (size_t)nsplit * rows * L.M * 9;
+      const dim3 g((L.M + EX_TM - 1) / EX_TM, (rows + EX_TF - 1) / EX_TF, nsplit);
+      const bool h = p == P_F16;
+      if (h)
+        exact_split_pass1<__half><<<g, EX_THREADS, 0, st>>>(rows, row_frame, (const float*)frames, fi.c32,
+                                                            (const __half*)L.coords, L.off, L.w, L.M, L.N, nsplit, Hp);
+      else
+        exact_split_pass1<float><<<g, EX_THREADS, 0, st>>>(rows, row_frame, (const float*)frames, fi.c32,
+                                                           (const float*)L.coords, L.off, L.w, L.M, L.N, nsplit, Hp);
+      if (h)
+        exact_split_pass2<__half><<<g, EX_THREADS, 0, st>>>(rows, row_frame, (const float*)frames, fi.c32, fi.G,
+                                                            (const __half*)L.coords, L.off, L.G, L.w, L.M, L.N, nsplit,
+                                                            Hp, Dp, (float*)Rout, status, L.newton_cap);
+      else
+        exact_split_pass2<float><<<g, EX_THREADS, 0, st>>>(rows, row_frame, (const float*)frames, fi.c32, fi.G,
+                                                           (const float*)L.coords, L.off, L.G, L.w, L.M, L.N, nsplit,
+                                                           Hp, Dp, (float*)Rout, status, L.newton_cap);
+      const size_t n = (size_t)rows * L.M;
+      exact_split_finish<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(rows, row_frame, L.M, nsplit, (float)L.dscale,
+                                                                     Dp, (float*)D);
+      note_launch(3);
+      return;
+    }
   }
   const int shape = L.exact_tile > 0 && L.exact_tile <= EXACT_SHAPES ? L.exact_tile - 1 : 0;
   if (p != P_F64 && shape > 0) {  // a chosen shape (FP32 / FP16 storage)

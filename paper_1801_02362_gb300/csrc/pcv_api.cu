@@ -128,6 +128,7 @@ struct pcv_ctx {
   DevBuf c32, c64, fG, bandD, bandQ, bandF, chD, chQ, chF, rlist, rcount, recF, recRef, recD, recQ, reflist,
       segof, alist, aseg, Dbuf, Rpair, Bseg, mstat, status, nrecheck, small;
   DevBuf rcScr;  // the FP64 re-check's partial sums and completion counts
+  DevBuf exSplit;  // partial sums of the exact pairs split over atom slices
   DevBuf Xr, Bm, GSb, GZb;  // materialised x', b and the gamma rows
   DevBuf Apk, Bpk;          // the same deviations packed for the tensor cores (FP16 h + l)
   DevBuf xtiles;            // their per-segment tile list, first rows, first tiles, count
@@ -336,7 +337,7 @@ pcv_status pcv_destroy(pcv_ctx* c) {
                     &c->wa64, &c->y, &c->Bprior, &c->c32, &c->c64,
                     &c->fG, &c->bandD, &c->bandQ, &c->bandF, &c->chD, &c->chQ, &c->chF, &c->rlist, &c->rcount,
                     &c->recF, &c->recRef, &c->recD, &c->recQ, &c->reflist, &c->segof, &c->alist, &c->aseg,
-                    &c->Dbuf, &c->Rpair, &c->Bseg, &c->Xr, &c->Bm, &c->Apk, &c->Bpk, &c->xtiles, &c->GSb, &c->GZb, &c->Nx, &c->Nb, &c->Yc, &c->Gsum, &c->Amma, &c->Bmma, &c->S6, &c->mstat, &c->status, &c->nrecheck, &c->rcScr, &c->small, &c->h_frames,
+                    &c->Dbuf, &c->Rpair, &c->Bseg, &c->Xr, &c->Bm, &c->Apk, &c->Bpk, &c->xtiles, &c->GSb, &c->GZb, &c->Nx, &c->Nb, &c->Yc, &c->Gsum, &c->Amma, &c->Bmma, &c->S6, &c->mstat, &c->status, &c->nrecheck, &c->rcScr, &c->exSplit, &c->small, &c->h_frames,
                     &c->h_s, &c->h_z, &c->h_gs, &c->h_gz, &c->h_msd, &c->h_ref, &c->grp_inst, &c->grp_tiles,
                     &c->nl_keep, &c->nlSlot, &c->nlUpd, &c->nlU, &c->nlUA, &c->nlUAseg, &c->nlN, &c->NLtab,
                     &c->Rupd, &c->Rnl, &c->nlTiles, &c->nlPart, &c->betaPart};
@@ -709,6 +710,19 @@ pcv_status nl_stage_carried(pcv_ctx* c) {
 // structure), then evaluate reassignment frames exactly and the rest approximately.
 RecheckScratch rc_scratch(pcv_ctx* c) { return recheck_scratch_at(c->rcScr.p); }
 
+// scratch for the exact pairs of `rows` frames split over atom slices (none when they do not split)
+pcv_status exact_split_scratch(pcv_ctx* c, int rows, ScratchView& scr) {
+  scr = ScratchView{nullptr, 0};
+  if (c->prec == P_F64 || rows <= 0 || c->exact_tile != 0) return PCV_OK;
+  const int k = exact_split_count(rows, c->M, c->N);
+  if (k <= 1) return PCV_OK;
+  const size_t bytes = exact_split_bytes(rows, c->M, k);
+  const pcv_status st = ensure(c, c->exSplit, bytes);
+  if (st != PCV_OK) return st;
+  scr = ScratchView{c->exSplit.p, c->exSplit.bytes};
+  return PCV_OK;
+}
+
 pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, double* z, void* gs, void* gz,
                           double* msd, uint8_t* refreshed) {
   const cudaStream_t st = c->stream;
@@ -904,9 +918,11 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
     }
   }
   {
+    ScratchView scr{nullptr, 0};
+    if ((ps = exact_split_scratch(c, nref, scr)) != PCV_OK) return ps;
     PROF(c, K_EXACT);
     launch_exact_pairs(c->prec, nref, (const int*)c->reflist.p, nullptr, frames, L, fi, c->Dbuf.p, Bseg1,
-                       (unsigned*)c->status.p, st);
+                       (unsigned*)c->status.p, st, &scr);
   }
   // per-segment tile list of the tensor-core MSDs: [seg_first | tile_start | tiles | count]
   int *xt_first = nullptr, *xt_start = nullptr, *xt_count = nullptr;
@@ -1175,9 +1191,12 @@ pcv_status evaluate_exact(pcv_ctx* c, int F, const void* frames, double* s, doub
     launch_frame_prep(c->prec, F, frames, L, fi, st);
   }
   {
+    ScratchView scr{nullptr, 0};
+    const pcv_status ps = exact_split_scratch(c, F, scr);
+    if (ps != PCV_OK) return ps;
     PROF(c, K_EXACT);
     launch_exact_pairs(c->prec, F, nullptr, nullptr, frames, L, fi, c->Dbuf.p, grads ? c->Rpair.p : nullptr,
-                       (unsigned*)c->status.p, st);
+                       (unsigned*)c->status.p, st, &scr);
   }
   {
     PROF(c, K_FINAL);

@@ -174,11 +174,20 @@ void launch_dev_copy(void* dst, const void* src, size_t bytes, cudaStream_t st);
 void launch_set_int(int* p, int v, cudaStream_t st);
 
 // ---- k_pair.cu ----
+// device scratch handed to a launcher: ptr and its size in bytes
+struct ScratchView {
+  void* ptr;
+  size_t bytes;
+};
 // exact pairs: rows r in [0, rows) are frames row_frame[r] (or r if null); D -> D[f*M+i]
-// (float in FP32 modes, double in FP64 mode); R (optional) -> Rout[(r*M + i)*9]
+// (float in FP32 modes, double in FP64 mode); R (optional) -> Rout[(r*M + i)*9].  With
+// scratch of exact_split_bytes(rows, M, exact_split_count(rows, M, N)) bytes, batches whose
+// tiles would not fill two waves of the GPU split the atoms over several CTAs per tile.
+int exact_split_count(int rows, int M, int N);  // 1: no split
+size_t exact_split_bytes(int rows, int M, int nsplit);
 void launch_exact_pairs(Prec p, int rows, const int* row_frame, const int* rows_dev, const void* frames,
                         const LandmarkDev& L, FrameInfo fi, void* D, void* Rout, unsigned* status,
-                        cudaStream_t st);
+                        cudaStream_t st, const ScratchView* scr = nullptr);
 // approximate pairs (form A): list entries k < *count: frame approx_list[k] of segment
 // approx_seg[k]; rotations Bseg[seg*M + i] (9 floats each), R_{x y} from rec.qxy
 void launch_approx_pairs(Prec p, int max_rows, const int* approx_list, const int* approx_seg,

@@ -258,6 +258,25 @@ def test_close_mma_fold_groups(pcv, group):
     ctx.close()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_exact_few_frames_split_over_atom_slices(pcv, precision):
+    """24 frames x 200 landmarks of 1000 atoms make 14 tiles, far from filling the GPU, so the
+    exact pairs split the atoms over 4 slices per tile (partial correlations added in slice
+    order, then the rotation, then partial MSDs): values, both gradients (the rotations) and
+    a second call of 9 frames (ragged tiles) against the oracle."""
+    lm, fr, lam = problem(64, 1000, 200, 33, noise=0.03, schedule="walk", precision=precision)
+    ctx = pcv.PathCV(lm, lam, eps=-1.0, precision=precision)
+    for a, b in ((0, 24), (24, 33)):
+        r = oracle.exact(fr[a:b], lm, lam, want_grad=True)
+        out = ctx.evaluate(torch.tensor(fr[a:b], dtype=torch.float32, device="cuda"), grad=True, msd=True)
+        ctx.sync()
+        g = {k: v.double().cpu().numpy() for k, v in out.items()}
+        check_values(g, r, fr[a:b], lm, lam, precision)
+        assert grad_err(g["dsdx"], r["dsdx"]) < GRAD_TOL[precision]
+        assert grad_err(g["dzdx"], r["dzdx"]) < GRAD_TOL[precision]
+    ctx.close()
+
+
 def test_close_fp64_workload_c1(pcv):
     lm, fr, lam = problem(11, 22, 20, 1000, noise=0.02, schedule="walk", precision="fp64")
     for eps in (0.001, 0.002, 0.004):

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import oracle
-from _util import TOL, d_err, problem, s_err, z_err
+from _util import TOL, d_err, problem, s_err, s_kappa, z_err
 
 pytestmark = pytest.mark.gpu
 
@@ -45,6 +45,11 @@ def noalloc(pcv, fr, lm, lam, stream):
 
 
 def test_noalloc_matches_regular_entry_point_twice(pcv):
+    """96 and then 80 frames.  The regular entry point may split the atom sums of a batch
+    this small over several CTAs per tile, so its distances carry a different rounding
+    (both within the distance tolerance); s amplifies a distance change by its condition
+    number, so s is compared with the tolerance scaled by it, as for any two evaluations
+    whose distances differ within tolerance."""
     lm, fr_a, lam = problem(41, 300, 200, 96)
     _, fr_b, _ = problem(42, 300, 200, 80)
     stream = torch.cuda.current_stream().cuda_stream
@@ -54,14 +59,16 @@ def test_noalloc_matches_regular_entry_point_twice(pcv):
         ref = ctx.evaluate(torch.tensor(fr, dtype=torch.float32, device="cuda"), msd=True)
         torch.cuda.synchronize()
         rs, rz, rmsd = (ref[k].cpu().numpy() for k in ("s", "z", "msd"))
+        r = oracle.exact(fr, lm, lam)
+        kappa = s_kappa(r["D"], lam, fr, lm)
         assert d_err(msd, rmsd, fr, lm) < TOL["fp32"]
-        assert s_err(s, rs, lm.shape[0]) < TOL["fp32"]
+        assert s_err(s, rs, kappa=kappa) < TOL["fp32"]
         assert z_err(z, rz, lam) < TOL["fp32"]
+        # and against the oracle
+        assert d_err(msd, r["D"], fr, lm) < TOL["fp32"]
+        assert s_err(s, r["s"], kappa=kappa) < TOL["fp32"]
+        assert z_err(z, r["z"], lam) < TOL["fp32"]
     ctx.close()
-    # and against the oracle on the last batch
-    r = oracle.exact(fr_b, lm, lam)
-    assert d_err(msd, r["D"], fr_b, lm) < TOL["fp32"]
-    assert z_err(z, r["z"], lam) < TOL["fp32"]
 
 
 @pytest.mark.parametrize("F", [1, 4])
