@@ -546,6 +546,76 @@ __global__ void xy_refine_kernel(int F, int N, const float* __restrict__ frames,
   }
 }
 
+// R_xy of few large frames (FP32 modes): xy_refine_kernel's arithmetic with one block of
+// XR_THREADS per frame instead of one warp (a single 5000-atom frame per call took 45 us on
+// one warp).  Each thread keeps compensated (hi, lo) totals of its atoms' products (chunks of
+// 16 folded by TwoSum), the warps add the pairs, and thread 0 adds the warps' pairs in order.
+constexpr int XR_THREADS = 256, XR_WARPS = XR_THREADS / 32;
+__global__ void __launch_bounds__(XR_THREADS, 2)
+xy_refine_block(int F, int N, const float* __restrict__ frames, RefView prior, const float4* __restrict__ c32,
+                const double* __restrict__ fG, const float* __restrict__ wts, FrameRec rec) {
+  __shared__ float red[XR_WARPS][18];
+  const int t = blockIdx.x;
+  if (t >= F || rec.flag[t] != 0) return;  // uniform over the block
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ref = rec.ref[t];
+  const float* y = ref >= 0 ? frames + (size_t)ref * N * 3 : (const float*)prior.coords;
+  const float4 cy = ref >= 0 ? c32[ref] : prior.c32;
+  const float* x = frames + (size_t)t * N * 3;
+  const float4 cx = c32[t];
+  float p[9], hi[9], lo[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) p[e] = hi[e] = lo[e] = 0.0f;
+  int cnt = 0;
+#pragma unroll 4
+  for (int j = tid; j < N; j += XR_THREADS) {
+    float u0 = y[3 * j] - cy.x, u1 = y[3 * j + 1] - cy.y, u2 = y[3 * j + 2] - cy.z;
+    const float v0 = x[3 * j] - cx.x, v1 = x[3 * j + 1] - cx.y, v2 = x[3 * j + 2] - cx.z;
+    if (wts) {
+      const float wj = wts[j];
+      u0 *= wj;
+      u1 *= wj;
+      u2 *= wj;
+    }
+    const float u[3] = {u0, u1, u2}, v[3] = {v0, v1, v2};
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) p[3 * b + c] = fmaf(u[b], v[c], p[3 * b + c]);
+    if (++cnt == 16) {
+      cnt = 0;
+#pragma unroll
+      for (int e = 0; e < 9; ++e) {
+        two_sum_acc(hi[e], lo[e], p[e]);
+        p[e] = 0.0f;
+      }
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    two_sum_acc(hi[e], lo[e], p[e]);
+    warp_sum_pair(hi[e], lo[e]);
+    if (lane == 0) {
+      red[warp][2 * e] = hi[e];
+      red[warp][2 * e + 1] = lo[e];
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float H[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      float h = red[0][2 * e], l = red[0][2 * e + 1];
+      for (int w = 1; w < XR_WARPS; ++w) two_sum_pair(h, l, red[w][2 * e], red[w][2 * e + 1]);
+      H[e] = h + l;
+    }
+    const float Gx = (float)fG[t], Gy = (float)(ref >= 0 ? fG[ref] : prior.G);
+    float q[4];
+    top_quat_f32(H, 0.5f * (Gx + Gy) * 1.00001f + 1e-30f, q);
+    rec.qxy[t] = make_double4(q[0], q[1], q[2], q[3]);
+  }
+}
+
 // Full FP64 re-evaluation of D(x_t, y) from the raw FP32 coordinates: FP64 correlation
 // and sums of squares, FP64 eigenvalue.  Centres: when they are weighted like the distance
 // (no separate alignment weights) the frames' stored centres c32 serve: at the exact
@@ -847,7 +917,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) band_scan_kernel(int F, int W, i
 }
 
 __global__ void chunk_records_kernel(int t0, int t_end, int t1, int ref, const double* __restrict__ cD,
-                                     const double4* __restrict__ cQ, FrameRec rec) {
+                                     const double4* __restrict__ cQ, FrameRec rec, const int* __restrict__ t_end_dev) {
+  if (t_end_dev) t_end = *t_end_dev;  // the first exceed as found on the device
   const int t = t0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= t1 || t > t_end) return;
   if (t < t_end) {
@@ -1012,6 +1083,80 @@ __device__ __forceinline__ void finalize_warp_f32(int f, int M, float* __restric
     for (int i = lane; i < M; i += 32) d[i] = expf(-lambda * (d[i] - m)) * il;
   }
   if (lane == 0) {
+    s[f] = (double)qm + (double)(sq / l);
+    z[f] = (double)(m - __logf(l) / lambda);
+    mstat[2 * f] = m;
+    mstat[2 * f + 1] = l;
+  }
+}
+
+// The path CVs of few frames against many landmarks (FP32 modes): finalize_warp_f32's
+// arithmetic with one block of FN_THREADS per frame (one 2000-landmark frame per call took
+// 29 us on one warp).  The minimum and q_m reduce in (value, q) order, the sums over the
+// block's warps in warp order.
+constexpr int FN_THREADS = 256, FN_WARPS = FN_THREADS / 32;
+__global__ void __launch_bounds__(FN_THREADS)
+finalize_block_f32(int F, int M, float* __restrict__ D, const float* __restrict__ q, float lambda,
+                   double* __restrict__ s, double* __restrict__ z, float* __restrict__ mstat,
+                   double* __restrict__ msd, int want_p) {
+  __shared__ float sm_m[FN_WARPS], sm_q[FN_WARPS], sm_l[FN_WARPS], sm_s[FN_WARPS];
+  const int f = blockIdx.x;
+  if (f >= F) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float* d = D + (size_t)f * M;
+  float m = 3.4e38f, qm = 0.0f;
+  for (int i = tid; i < M; i += FN_THREADS) {
+    const float v = d[i];
+    if (v < m) {
+      m = v;
+      qm = q[i];
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float m2 = __shfl_xor_sync(0xffffffffu, m, off), q2 = __shfl_xor_sync(0xffffffffu, qm, off);
+    if (m2 < m || (m2 == m && q2 < qm)) {
+      m = m2;
+      qm = q2;
+    }
+  }
+  if (lane == 0) {
+    sm_m[warp] = m;
+    sm_q[warp] = qm;
+  }
+  __syncthreads();
+  m = sm_m[0];
+  qm = sm_q[0];
+  for (int w = 1; w < FN_WARPS; ++w)
+    if (sm_m[w] < m || (sm_m[w] == m && sm_q[w] < qm)) {
+      m = sm_m[w];
+      qm = sm_q[w];
+    }
+  float l = 0.0f, sq = 0.0f;
+  for (int i = tid; i < M; i += FN_THREADS) {
+    const float e = expf(-lambda * (d[i] - m));
+    l += e;
+    sq = fmaf(q[i] - qm, e, sq);
+    if (msd) msd[(size_t)f * M + i] = (double)d[i];
+  }
+  l = warp_sum_float(l);
+  sq = warp_sum_float(sq);
+  if (lane == 0) {
+    sm_l[warp] = l;
+    sm_s[warp] = sq;
+  }
+  __syncthreads();
+  l = 0.0f;
+  sq = 0.0f;
+  for (int w = 0; w < FN_WARPS; ++w) {
+    l += sm_l[w];
+    sq += sm_s[w];
+  }
+  if (want_p) {
+    const float il = 1.0f / l;
+    for (int i = tid; i < M; i += FN_THREADS) d[i] = expf(-lambda * (d[i] - m)) * il;
+  }
+  if (tid == 0) {
     s[f] = (double)qm + (double)(sq / l);
     z[f] = (double)(m - __logf(l) / lambda);
     mstat[2 * f] = m;
@@ -1245,6 +1390,11 @@ RecheckScratch recheck_scratch_at(void* base) {
 void launch_xy_refine(Prec p, int F, const void* frames, const LandmarkDev& L, FrameInfo fi, const RefDesc& prior,
                       FrameRec rec, cudaStream_t st) {
   if (p == P_F64 || F <= 0) return;
+  if (F <= 152 && L.N >= 1024) {  // few large frames: a block per frame
+    xy_refine_block<<<F, XR_THREADS, 0, st>>>(F, L.N, (const float*)frames, view_of(prior), fi.c32, fi.G, L.w, rec);
+    note_launch();
+    return;
+  }
   xy_refine_kernel<<<blocks_for((size_t)F, WARPS_PER_BLOCK), 32 * WARPS_PER_BLOCK, 0, st>>>(
       F, L.N, (const float*)frames, view_of(prior), fi.c32, fi.G, L.w, L.dscale, rec);
   note_launch();
@@ -1271,7 +1421,16 @@ void launch_chunk_records(int t0, int t_end, int t1, int ref, const AlignOut chu
                           cudaStream_t st) {
   const int n = (t_end < t1 ? t_end + 1 : t1) - t0;
   if (n <= 0) return;
-  chunk_records_kernel<<<blocks_for((size_t)n, 256), 256, 0, st>>>(t0, t_end, t1, ref, chunk.D, chunk.q, rec); note_launch();
+  chunk_records_kernel<<<blocks_for((size_t)n, 256), 256, 0, st>>>(t0, t_end, t1, ref, chunk.D, chunk.q, rec,
+                                                                    nullptr); note_launch();
+}
+
+void launch_chunk_records_dev(int t0, const int* t_end_dev, int t1, int ref, const AlignOut chunk, FrameRec rec,
+                              cudaStream_t st) {
+  const int n = t1 - t0;
+  if (n <= 0) return;
+  chunk_records_kernel<<<blocks_for((size_t)n, 256), 256, 0, st>>>(t0, 0, t1, ref, chunk.D, chunk.q, rec, t_end_dev);
+  note_launch();
 }
 
 void launch_initial_record(FrameRec rec, cudaStream_t st) { initial_record_kernel<<<1, 1, 0, st>>>(rec); note_launch(); }
@@ -1289,6 +1448,9 @@ void launch_finalize(Prec p, int F, int M, void* D, const double* q, const float
   if (p == P_F64)
     finalize_f64<<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(F, M, (double*)D, q, lambda, s, z, mstat64, msd_out,
                                                           want_p ? 1 : 0);
+  else if (F <= 152 && M >= 1024)  // few frames against many landmarks: a block per frame
+    finalize_block_f32<<<F, FN_THREADS, 0, st>>>(F, M, (float*)D, q32, (float)lambda, s, z, mstat, msd_out,
+                                                 want_p ? 1 : 0);
   else
     finalize_f32<<<blocks, 32 * WARPS_PER_BLOCK, 0, st>>>(F, M, (float*)D, q32, (float)lambda, s, z, mstat, msd_out,
                                                           want_p ? 1 : 0);

@@ -131,6 +131,9 @@ void launch_band_scan(int F, int W, int t0, int o_init, const AlignOut band, Fra
 // refresh
 void launch_chunk_records(int t0, int t_end, int t1, int ref, const AlignOut chunk, FrameRec rec,
                           cudaStream_t st);
+// the same with the first exceeding frame read on the device (t_end_dev; t1 = none)
+void launch_chunk_records_dev(int t0, const int* t_end_dev, int t1, int ref, const AlignOut chunk, FrameRec rec,
+                              cudaStream_t st);
 void launch_initial_record(FrameRec rec, cudaStream_t st);
 
 // compaction of refresh / approximate frames (device lists, counts returned on device)
