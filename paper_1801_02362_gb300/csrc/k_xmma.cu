@@ -447,6 +447,10 @@ __global__ void __launch_bounds__(XM_THREADS, 1) approx_cross_mma(XmmaArgs p) {
     } else if (warp == XM_FOLD_WARPS + 1) {
       if (lane == 0) {  // MMA issue
         bool failed = false;
+        const uint64_t dA0 = smem_desc(sbase, 128, 256);
+        const uint32_t full_b = smem_u32(&full[0]);
+        int st_m = g0 % XM_STAGES;  // stage and phase of the next chunk, counted as we go
+        uint32_t ph_m = (uint32_t)((g0 / XM_STAGES) & 1);
         for (int gr = 0; gr < ngrp && !failed; ++gr) {
           const int gg = gg0 + gr, buf = gg & 1;
           // the fold of group gg - 2 has emptied this accumulator
@@ -458,17 +462,23 @@ __global__ void __launch_bounds__(XM_THREADS, 1) approx_cross_mma(XmmaArgs p) {
           const uint32_t acc = tmem + (uint32_t)(buf * XM_BN_MAX), cacc = tmem + (uint32_t)(2 * XM_BN_MAX);
           const int c0 = gr * G, c1 = min(nck, c0 + G);
           for (int c = c0; c < c1; ++c) {
-            const int g = g0 + c, st = g % XM_STAGES;
-            if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((g / XM_STAGES) & 1), p.wait_cycles)) {
+            const int g = g0 + c;
+            if (!mbar_wait(full_b + 8u * (uint32_t)st_m, ph_m, p.wait_cycles)) {
               s_fail = 1;
               failed = true;
               break;
             }
             tc_fence_after();
-            const uint32_t ah = sbase + st * XM_STAGE_BYTES, al = ah + XM_A_PART;
-            const uint32_t bh = ah + 2 * XM_A_PART, bl = bh + b_part;
-            const uint64_t dah = smem_desc(ah, 128, 256), dal = smem_desc(al, 128, 256);
-            const uint64_t dbh = smem_desc(bh, 128, 256), dbl = smem_desc(bl, 128, 256);
+            // descriptors of this stage: the stage-0 ones stepped by the stage offset (the
+            // address field counts 16-byte units; shared addresses stay below 256 KB)
+            const uint64_t dah = dA0 + (uint64_t)st_m * (XM_STAGE_BYTES >> 4), dal = dah + (XM_A_PART >> 4);
+            const uint64_t dbh = dah + ((2 * XM_A_PART) >> 4), dbl = dbh + (b_part >> 4);
+            const int st = st_m;
+            if (++st_m == XM_STAGES) {
+              st_m = 0;
+              ph_m ^= 1u;
+            }
+            (void)g;
             // the two small correction products into the row's correction accumulator, the
             // main product into the group's
             mma_f16(cacc, dah, dbl, idesc, c > 0 ? 1u : 0u);

@@ -82,18 +82,24 @@ static __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, u
       : "memory");
 }
 
-// bounded wait for the phase with the given parity; false after `budget` clock cycles
+static __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// bounded wait for the phase with the given parity; false after `budget` clock cycles (the
+// clock is read only once the first try has found the phase incomplete)
 static __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long budget) {
+  if (mbar_try(mbar, parity)) return true;
   const long long t0 = clock64();
   while (true) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    if (done) return true;
+    if (mbar_try(mbar, parity)) return true;
     if (clock64() - t0 > budget) return false;
   }
 }
