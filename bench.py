@@ -57,9 +57,9 @@ TENSOR_KERNELS = {"adjoint_beta_mma": "f16", "approx_pair_mma": "f16"}
 # approximate MSDs for the MSD kernels, frames for the adjoint)
 DRAM_BYTES_PER_UNIT = {
     # approx_cross_mma on the first 2000 frames of the 5000-atom / 2000-landmark trajectory:
-    # 1.208 GB read + 0.018 GB written for 3,986,000 approximate MSDs (the same segment
+    # 1.2077 GB read + 0.0182 GB written for 3,986,000 approximate MSDs (the same segment
     # lengths as the full step, so the same traffic per approximate MSD)
-    ("approx_pair_mma", 5000, 2000): 1.226263e9 / 3_986_000,
+    ("approx_pair_mma", 5000, 2000): 1.225962e9 / 3_986_000,
 }
 TF32_PER_BF16 = 1.1 / 2.25
 
