@@ -816,9 +816,9 @@ pcv_status evaluate_close(pcv_ctx* c, int F, const void* frames, double* s, doub
       launch_first_exceed(t, t1, chunk.flag, &sm->stop, &sm->first, st);
     }
     if (t1 == F && t1 - t == 1) {
-      // the batch's last frame in a round of its own (every call of one frame): the search
-      // ends with this round whatever the frame's decision, so its records take the first
-      // exceed from the device and the host does not wait for it
+      // the batch's last frame in a search round of its own (every call of one frame): the
+      // search ends with this round whatever the frame's decision, so its records take the
+      // first exceed from the device and the host does not wait for it
       PROF(c, K_RECORDS);
       launch_chunk_records_dev(t, &sm->first, t1, ref, chunk, rec, st);
       break;
