@@ -182,7 +182,9 @@ PCV_API pcv_status pcv_evaluate_host(pcv_ctx* ctx, int F, const void* frames, do
                              void* dsdx, void* dzdx, double* msd, uint8_t* refreshed);
 
 /* Chunk plan of pcv_evaluate_host for F frames with the options PCV_OPT_HOST_CHUNKS = n
- * (0: automatic, about one chunk per 16k frames, 1..8) and PCV_OPT_HOST_END_SHARE =
+ * (0: the frame rule, about one chunk per 16k frames, 1..8; pcv_evaluate_host raises the
+ * automatic count to one chunk per 128 MiB of frames when that gives more, and a plan for
+ * that count is this function with n set to it) and PCV_OPT_HOST_END_SHARE =
  * end_share (1..100): the chunk sizes in order, first and last end_share percent of a middle
  * one, every chunk at least 2048 frames (the number of chunks is lowered to F / 2048 when
  * needed).  Writes min(count, cap) sizes into sizes (host array; may be NULL with cap 0) and
@@ -250,8 +252,9 @@ enum {
                               lo, three products per term, on deviations from the close
                               structure); 0: FP32 CUDA cores for both.                    */
   PCV_OPT_HOST_CHUNKS = 8,  /* pcv_evaluate_host: number of chunks the batch is split into
-                              so that copies overlap evaluation (0 = automatic, default;
-                              1 = no overlap; at most 64)                               */
+                              so that copies overlap evaluation (0 = automatic, default:
+                              one per 16k frames or per 128 MiB of frames, whichever gives
+                              more, at most 8; 1 = no overlap; at most 64)               */
   PCV_OPT_HOST_END_SHARE = 9, /* pcv_evaluate_host: size of the first and the last chunk in
                               percent of a middle chunk (1..100; default 25): a small first
                               chunk starts the evaluation early and a small last chunk

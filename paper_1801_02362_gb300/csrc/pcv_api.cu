@@ -1504,7 +1504,14 @@ pcv_status pcv_evaluate_host(pcv_ctx* c, int F, const void* frames, double* s, d
   // out on another, while a chunk is evaluated on the context's stream.  The first and the
   // last chunk are smaller than the others: nothing overlaps the first chunk's copy-in or
   // the last chunk's copy-out.
-  const std::vector<int> plan = host_chunk_plan(F, c->host_chunks, c->host_end_share);
+  // automatic: the frame rule of host_chunk_plan, or one chunk per 128 MiB of frame
+  // coordinates when that gives more (large structures: 10k frames of 5000 atoms are 600 MB
+  // whose copy-in would otherwise precede the whole evaluation)
+  int nchunks = c->host_chunks;
+  if (nchunks == 0)
+    nchunks = std::max((int)host_chunk_plan(F, 0, c->host_end_share).size(),
+                       (int)std::min<size_t>(8, (fbytes + ((size_t)128 << 20) - 1) >> 27));
+  const std::vector<int> plan = host_chunk_plan(F, nchunks, c->host_end_share);
   const int nchunk = (int)plan.size();
   std::vector<size_t> first(nchunk + 1, 0);
   for (int k = 0; k < nchunk; ++k) first[k + 1] = first[k] + (size_t)plan[k];
