@@ -24,15 +24,6 @@
 namespace pcv {
 namespace {
 
-template <typename ST, typename LT>
-__device__ __forceinline__ ST lm_at(const LT* p) {
-  return (ST)(*p);
-}
-template <>
-__device__ __forceinline__ float lm_at<float, __half>(const __half* p) {
-  return __half2float(*p);
-}
-
 // gamma^s, gamma^z of one (frame, landmark) pair from the softmax weight p; s = sh + sl
 // (s_low)
 template <typename ST>

@@ -192,47 +192,6 @@ struct RefView {
   double G;
 };
 
-// FP32 frames: compensated correlation, returns H in FP64 on every lane
-__device__ __forceinline__ void warp_corr_f32(int N, const float* __restrict__ x, float4 cx,
-                                              const float* __restrict__ y, float4 cy,
-                                              const float* __restrict__ wts, double* H) {
-  const int lane = threadIdx.x & 31;
-  float p[9], hi[9], lo[9];
-#pragma unroll
-  for (int e = 0; e < 9; ++e) p[e] = hi[e] = lo[e] = 0.0f;
-  int cnt = 0;
-  for (int j = lane; j < N; j += 32) {
-    float u0 = y[3 * j] - cy.x, u1 = y[3 * j + 1] - cy.y, u2 = y[3 * j + 2] - cy.z;
-    const float v0 = x[3 * j] - cx.x, v1 = x[3 * j + 1] - cx.y, v2 = x[3 * j + 2] - cx.z;
-    if (wts) {
-      const float wj = wts[j];
-      u0 *= wj;
-      u1 *= wj;
-      u2 *= wj;
-    }
-    const float u[3] = {u0, u1, u2}, v[3] = {v0, v1, v2};
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) p[3 * b + c] = fmaf(u[b], v[c], p[3 * b + c]);
-    if (++cnt == 16) {
-      cnt = 0;
-#pragma unroll
-      for (int e = 0; e < 9; ++e) {
-        two_sum_acc(hi[e], lo[e], p[e]);
-        p[e] = 0.0f;
-      }
-    }
-  }
-#pragma unroll
-  for (int e = 0; e < 9; ++e) {
-    two_sum_acc(hi[e], lo[e], p[e]);
-    warp_sum_pair(hi[e], lo[e]);
-    H[e] = pair_to_double(hi[e], lo[e]);
-  }
-}
-
-
 __device__ __forceinline__ void warp_corr_f64(int N, const double* __restrict__ x, double4 cx,
                                               const double* __restrict__ y, double4 cy,
                                               const double* __restrict__ w64, double* H) {

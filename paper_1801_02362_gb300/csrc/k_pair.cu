@@ -20,15 +20,6 @@
 namespace pcv {
 namespace {
 
-template <typename ST, typename LT>
-__device__ __forceinline__ ST load_as(const LT* p) {
-  return (ST)(*p);
-}
-template <>
-__device__ __forceinline__ float load_as<float, __half>(const __half* p) {
-  return __half2float(*p);
-}
-
 template <typename ST>
 __device__ __forceinline__ void load2(const ST* p, ST& a, ST& b);
 template <>

@@ -41,15 +41,6 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory");
 }
 
-template <typename LT>
-__device__ __forceinline__ float lm_f(const LT* p) {
-  return (float)(*p);
-}
-template <>
-__device__ __forceinline__ float lm_f<__half>(const __half* p) {
-  return __half2float(*p);
-}
-
 // ---------------------------------------------------------------------------------------
 // block sum of one value per thread (blockDim.x a multiple of 32, at most 1024)
 __device__ __forceinline__ float block_sum(float v, float* red) {
