@@ -71,35 +71,6 @@ __host__ __device__ __forceinline__ uint32_t xpiece_off(int r, int p) {
   return (uint32_t)((r >> 3) * 256 + (p & 1) * 128 + (r & 7) * 16);
 }
 
-// eight deviations -> h and l parts (scaled by 2^8), eight halves each
-__device__ __forceinline__ void xsplit8(const float* v, uint4& hi, uint4& lo) {
-  uint32_t h[4], l[4];
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    const float s0 = v[2 * e] * XM_SCALE, s1 = v[2 * e + 1] * XM_SCALE;
-    const __half h0 = __float2half_rn(s0), h1 = __float2half_rn(s1);
-    const __half l0 = __float2half_rn(s0 - __half2float(h0)), l1 = __float2half_rn(s1 - __half2float(h1));
-    h[e] = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
-    l[e] = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
-  }
-  hi = make_uint4(h[0], h[1], h[2], h[3]);
-  lo = make_uint4(l[0], l[1], l[2], l[3]);
-}
-
-// squared-norm partials of the 8 rows handled by a block of 256 threads (row = tid & 7):
-// lanes rr, rr + 8, rr + 16, rr + 24 of each warp, then the 8 warps
-__device__ __forceinline__ float rows8_sum(float v, float (*red)[8]) {
-  v += __shfl_xor_sync(0xffffffffu, v, 8);
-  v += __shfl_xor_sync(0xffffffffu, v, 16);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane < 8) red[w][lane] = v;
-  __syncthreads();
-  float s = 0.0f;
-  if (threadIdx.x < 8)
-    for (int k = 0; k < 8; ++k) s += red[k][threadIdx.x];
-  return s;
-}
-
 // Tiles of the approximate frames, per segment: segment slot s holds the rows
 // [first_s, first_s + n_s) of the approximate list (aseg is non-decreasing), which fill
 // ceil(n_s / 128) tiles numbered from tile_start[s].  One block: binary searches for the
@@ -160,22 +131,26 @@ xmma_tiles_kernel(const int* __restrict__ acount, const int* __restrict__ aseg, 
   if (tid == 0) *ntiles = s_carry;
 }
 
-// A operand: dx_k = R_xy^T (x_f - c_f) - y'(segment), f = alist[k], for rows 8 g .. 8 g + 7
-// of the approximate list (block g), and |dx_k|^2 in Nx[k].  Row k of segment slot s goes
-// to tile tile_start[s] + (k - first_s) / 128, row (k - first_s) % 128.  Thread (rr = tid &
-// 7, pq = tid >> 3) writes the 16-byte pieces pq, pq + 32, ... of row 8 g + rr: the 8
-// threads of one piece index fill a whole 128-byte core matrix (rows of one segment).
+// Frame deviations dx_k = R_xy^T (x_k - c) - y'(s) of the approximate frames (rows of the
+// approximate list), scaled by 2^8 and split into FP16 h + l, in the tiles of their segments
+// (xmma_tiles_kernel), with |dx_k|^2 in Nx[k].  A block takes 8 consecutive rows, one warp
+// per row: per slice of 128 atoms each warp reads its frame's coordinates and its
+// segment's y' coalesced, writes the 384 split values into shared memory, and then the
+// block writes 16-byte core-matrix rows (8 components of one row), eight threads to a
+// 128-byte core matrix.  Components beyond 3N up to 3 N16 are zeros.
+constexpr int PF_ATOMS = 128, PF_COMP = 3 * PF_ATOMS, PF_LD = PF_COMP + 8;
 __global__ void __launch_bounds__(256)
 pack_frames_kernel(const int* __restrict__ acount, const int* __restrict__ alist, const int* __restrict__ aseg,
                    int seg_base, int N, int N16, const float* __restrict__ frames, const float4* __restrict__ c32,
                    const double4* __restrict__ qxy, const float* __restrict__ Yc, const int* __restrict__ seg_first,
                    const int* __restrict__ tile_start, uint8_t* __restrict__ Ap, float* __restrict__ Nx) {
-  __shared__ float red[8][8];
+  __shared__ __align__(16) __half sh[8][PF_LD], sl[8][PF_LD];
+  __shared__ int s_ti[8], s_r[8];
   const int count = *acount;
   const int g = blockIdx.x;
   if (8 * g >= count) return;  // uniform over the block
-  const int tid = threadIdx.x, rr = tid & 7, pq = tid >> 3;
-  const int k = 8 * g + rr;
+  const int tid = threadIdx.x, u = tid >> 5, lane = tid & 31;
+  const int k = 8 * g + u;
   const bool live = k < count;
   float R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
   float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -190,36 +165,54 @@ pack_frames_kernel(const int* __restrict__ acount, const int* __restrict__ alist
     x = frames + (size_t)f * N * 3;
     y = Yc + (size_t)(aseg[k] - seg_base) * 3 * N;
   }
-  const int K = 3 * N16, P = K / 8, nck = K / XM_KC;
-  int ti = 0, r = 0;
-  if (live) {
-    const int slot = aseg[k] - seg_base, off = k - seg_first[slot];
-    ti = tile_start[slot] + off / XM_ROWS;
-    r = off % XM_ROWS;
-  }
-  uint8_t* tile = Ap + (size_t)ti * nck * 2 * XM_A_PART;
-  float nrm = 0.0f;
-  for (int pp = pq; pp < P && live; pp += 32) {
-    float v[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int kk = 8 * pp + e, j = kk / 3, cc = kk - 3 * j;
-      float o = 0.0f;
-      if (j < N) {
-        const float v0 = x[3 * j] - c.x, v1 = x[3 * j + 1] - c.y, v2 = x[3 * j + 2] - c.z;
-        o = (R[cc] * v0 + R[3 + cc] * v1 + R[6 + cc] * v2) - y[3 * j + cc];
-      }
-      v[e] = o;
-      nrm = fmaf(o, o, nrm);
+  if (lane == 0) {
+    int ti = 0, r = 0;
+    if (live) {
+      const int slot = aseg[k] - seg_base, off = k - seg_first[slot];
+      ti = tile_start[slot] + off / XM_ROWS;
+      r = off % XM_ROWS;
     }
-    uint4 hi, lo;
-    xsplit8(v, hi, lo);
-    uint8_t* blk = tile + (size_t)(pp >> 1) * 2 * XM_A_PART;
-    *reinterpret_cast<uint4*>(blk + xpiece_off(r, pp)) = hi;
-    *reinterpret_cast<uint4*>(blk + XM_A_PART + xpiece_off(r, pp)) = lo;
+    s_ti[u] = live ? ti : -1;
+    s_r[u] = r;
   }
-  const float s = rows8_sum(nrm, red);
-  if (tid < 8 && 8 * g + tid < count) Nx[8 * g + tid] = s;
+  const int K = 3 * N16, nck = K / XM_KC;
+  float nrm = 0.0f;
+  __syncthreads();
+  for (int c0 = 0; c0 < K; c0 += PF_COMP) {
+    const int j0 = c0 / 3;
+#pragma unroll
+    for (int it = 0; it < PF_ATOMS / 32; ++it) {
+      const int a = lane + 32 * it, j = j0 + a;
+      float d[3] = {0.0f, 0.0f, 0.0f};
+      if (live && j < N) {
+        const float v0 = x[3 * j] - c.x, v1 = x[3 * j + 1] - c.y, v2 = x[3 * j + 2] - c.z;
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) d[cc] = (R[cc] * v0 + R[3 + cc] * v1 + R[6 + cc] * v2) - y[3 * j + cc];
+      }
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) {
+        nrm = fmaf(d[cc], d[cc], nrm);
+        const float v = d[cc] * XM_SCALE;
+        const __half h = __float2half_rn(v);
+        sh[u][3 * a + cc] = h;
+        sl[u][3 * a + cc] = __float2half_rn(v - __half2float(h));
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < 8 * (PF_COMP / 8); e += 256) {
+      const int rr = e & 7, pp = e >> 3, comp = c0 + 8 * pp;
+      const int ti = s_ti[rr];
+      if (comp >= K || ti < 0) continue;
+      const int gp = comp / 8;  // global piece index of the row
+      uint8_t* blk = Ap + ((size_t)ti * nck + gp / 2) * 2 * XM_A_PART;
+      *reinterpret_cast<uint4*>(blk + xpiece_off(s_r[rr], gp)) = *reinterpret_cast<const uint4*>(&sh[rr][8 * pp]);
+      *reinterpret_cast<uint4*>(blk + XM_A_PART + xpiece_off(s_r[rr], gp)) =
+          *reinterpret_cast<const uint4*>(&sl[rr][8 * pp]);
+    }
+    __syncthreads();
+  }
+  nrm = warp_sum_float(nrm);
+  if (lane == 0 && live) Nx[k] = nrm;
 }
 
 // Landmark deviations of every segment for both tensor-core products, computed once:
