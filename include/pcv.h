@@ -388,7 +388,7 @@ PCV_API pcv_status pcv_shard_unpack_host(int precision, int F, int N, double lam
  *     (plus alignment) <= PCV_NOALLOC_SCRATCH_BYTES; larger problems return PCV_EINVAL
  *     with a message, before any GPU work;
  *   - the first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture;
+ *     (cudaGetSymbolAddress) and keeps it for later calls;
  *   - every call shares the one array, which keeps the previous call's contents: calls that
  *     overlap on the GPU (different streams, threads or processes on the same device)
  *     race and must be serialised by the caller;
