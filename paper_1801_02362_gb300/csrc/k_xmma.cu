@@ -54,7 +54,7 @@ constexpr int XM_BN_MAX = 128;   // landmarks per tile (MMA N), multiple of 16
 constexpr int XM_KC = 16;        // components per chunk: one MMA (K = 16) per product
 constexpr int XM_STAGES = 12;    // 16 KB each: about 1.3 us of MMAs in flight
 constexpr int XM_GROUP_MAX = 16;  // chunks summed in tensor memory before a fold (the
-                                 // context's PCV_OPT_MMA_GROUP, 1..8)
+                                  // context's PCV_OPT_MMA_GROUP, 1..16)
 constexpr int XM_FOLD_WARPS = 8;  // two per tensor-memory lane quarter (column halves)
 constexpr int XM_THREADS = 32 * (XM_FOLD_WARPS + 2);  // + the copy warp and the MMA warp
 constexpr int XM_TMEM_COLS = 4 * XM_BN_MAX;           // two main accumulators, the corrections'
