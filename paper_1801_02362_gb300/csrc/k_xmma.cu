@@ -455,7 +455,6 @@ __global__ void __launch_bounds__(XM_THREADS, 1) approx_cross_mma(XmmaArgs p) {
           const uint32_t acc = tmem + (uint32_t)(buf * XM_BN_MAX), cacc = tmem + (uint32_t)(2 * XM_BN_MAX);
           const int c0 = gr * G, c1 = min(nck, c0 + G);
           for (int c = c0; c < c1; ++c) {
-            const int g = g0 + c;
             if (!mbar_wait(full_b + 8u * (uint32_t)st_m, ph_m, p.wait_cycles)) {
               s_fail = 1;
               failed = true;
@@ -471,7 +470,6 @@ __global__ void __launch_bounds__(XM_THREADS, 1) approx_cross_mma(XmmaArgs p) {
               st_m = 0;
               ph_m ^= 1u;
             }
-            (void)g;
             // the two small correction products into the row's correction accumulator, the
             // main product into the group's
             mma_f16(cacc, dah, dbl, idesc, c > 0 ? 1u : 0u);
