@@ -9,8 +9,10 @@
 //   * split operands: every deviation v is scaled by 2^8 (exact) and split v' = h + l with
 //     h = fp16(v') and l = fp16(v' - h), so h + l carries ~22 significant bits; the product
 //     is h h' + h l' + l h' (three MMAs, products exact in the FP32 accumulator; the dropped
-//     l l' is ~2^-22 relative).  The 2^8 scale keeps l out of the FP16 subnormal range for
-//     deviations above ~5e-4 nm and the largest deviations (up to 256 nm) finite;
+//     l l' is ~2^-22 relative).  With the 2^8 scale, h + l is within 2^-22 of v' for every
+//     deviation of at least ~5e-4 nm (l is often subnormal there: the absolute spacing 2^-24
+//     of FP16 subnormals is what bounds it), and deviations below ~255.9 nm stay finite
+//     (2^8 v below 65504, the largest FP16);
 //   * short accumulation chains: each accumulation into a tensor-memory accumulator
 //     loses up to about one unit in the last place of the running sum, so the main
 //     products h h' go to an accumulator that only ever sums a group of a few chunks of 16
