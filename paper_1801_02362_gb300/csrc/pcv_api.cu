@@ -1369,37 +1369,44 @@ pcv_status pcv_evaluate_group(pcv_ctx* const* ctxs, int n, const pcv_batch_io* i
     // (shape, grid) is kept for this group
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, lead->device);
-    cudaEvent_t t0, t1;
-    CUDA_TRY(lead, cudaEventCreate(&t0));
-    CUDA_TRY(lead, cudaEventCreate(&t1));
     float best = 3.4e38f;
     int best_blocks = 4 * sms, best_shape = lead->exact_tile > 0 ? lead->exact_tile - 1 : 0;
-    for (int sh = 0; sh < EXACT_SHAPES; ++sh) {
-      if (lead->exact_tile > 0 && sh != lead->exact_tile - 1) continue;
-      const std::vector<GroupTile>& tl = tiles_of[sh];
-      const int ntiles = (int)tl.size();
-      if (ntiles == 0) continue;
-      CUDA_TRY(lead, cudaMemcpyAsync(lead->grp_tiles.p, tl.data(), sizeof(GroupTile) * ntiles,
-                                     cudaMemcpyHostToDevice, gs));
-      launch_exact_group(fp16, sh, I, T, ntiles, 4 * sms, gs);
-      const int cands[] = {sms, 2 * sms, 3 * sms, 4 * sms, 8 * sms, ntiles};
-      for (int cand : cands) {
-        const int blocks = cand < 1 ? 1 : (cand > ntiles ? ntiles : cand);
-        cudaEventRecord(t0, gs);
-        launch_exact_group(fp16, sh, I, T, ntiles, blocks, gs);
-        cudaEventRecord(t1, gs);
-        cudaEventSynchronize(t1);
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, t0, t1);
-        if (ms < best) {
-          best = ms;
-          best_blocks = blocks;
-          best_shape = sh;
+    {  // the timing events live for the search only (released on every return, before any capture)
+      struct Events {
+        cudaEvent_t a = nullptr, b = nullptr;
+        ~Events() {
+          if (a) cudaEventDestroy(a);
+          if (b) cudaEventDestroy(b);
+        }
+      } ev;
+      CUDA_TRY(lead, cudaEventCreate(&ev.a));
+      CUDA_TRY(lead, cudaEventCreate(&ev.b));
+      const cudaEvent_t t0 = ev.a, t1 = ev.b;
+      for (int sh = 0; sh < EXACT_SHAPES; ++sh) {
+        if (lead->exact_tile > 0 && sh != lead->exact_tile - 1) continue;
+        const std::vector<GroupTile>& tl = tiles_of[sh];
+        const int ntiles = (int)tl.size();
+        if (ntiles == 0) continue;
+        CUDA_TRY(lead, cudaMemcpyAsync(lead->grp_tiles.p, tl.data(), sizeof(GroupTile) * ntiles,
+                                       cudaMemcpyHostToDevice, gs));
+        launch_exact_group(fp16, sh, I, T, ntiles, 4 * sms, gs);
+        const int cands[] = {sms, 2 * sms, 3 * sms, 4 * sms, 8 * sms, ntiles};
+        for (int cand : cands) {
+          const int blocks = cand < 1 ? 1 : (cand > ntiles ? ntiles : cand);
+          CUDA_TRY(lead, cudaEventRecord(t0, gs));
+          launch_exact_group(fp16, sh, I, T, ntiles, blocks, gs);
+          CUDA_TRY(lead, cudaEventRecord(t1, gs));
+          CUDA_TRY(lead, cudaEventSynchronize(t1));  // a failed run must not count as a fast one
+          float ms = 0.0f;
+          CUDA_TRY(lead, cudaEventElapsedTime(&ms, t0, t1));
+          if (ms < best) {
+            best = ms;
+            best_blocks = blocks;
+            best_shape = sh;
+          }
         }
       }
     }
-    cudaEventDestroy(t0);
-    cudaEventDestroy(t1);
     lead->grp_blocks = best_blocks;
     lead->grp_shape = best_shape;
     const int ntiles = (int)tiles_of[best_shape].size();
